@@ -1,0 +1,284 @@
+"""Seeded synthetic inputs: structures, velocities, masses and model parameters.
+
+This module holds no arithmetic of the method itself (no basis, cutoff,
+network or integrator): it only draws the numbers that the CUDA path and the
+FP64 oracle both consume, so that either side can be fed identical inputs.
+
+Units: Angstrom, eV, amu, fs.
+
+Species indices are model-local: water systems use 0 = H, 1 = O
+(``n_species = 2``); four-element systems use 0 = H, 1 = C, 2 = N, 3 = O.
+
+Parameter vector layout (flat float64, in this order; ``S`` species, ``F``
+features, ``K`` radial functions, ``Lr`` message-passing layers):
+
+    A    [S, F]            species embedding, h0_i = A[Z_i]
+    for each layer l < Lr:
+      W_in [F, F]          u_i = h_i @ W_in
+      W1   [K, F], b1 [F]  filter hidden layer (on the radial basis)
+      W2   [F, F], b2 [F]  filter output layer
+      U1   [F, F], c1 [F]  atom-update hidden layer (on the message)
+      U2   [F, F], c2 [F]  atom-update output layer (residual)
+    R1   [F, F], d1 [F]    readout hidden layer
+    R2   [F],    d2 [1]    readout output
+    e0   [S]               per-species energy offset
+
+Matrices are row-major with the input index first (``y = x @ W``).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Masses in amu (IUPAC standard atomic weights).
+MASS_H = 1.008
+MASS_C = 12.011
+MASS_N = 14.007
+MASS_O = 15.999
+
+# Boltzmann constant in eV/K and (eV/amu) -> (A/fs)^2 used only to draw
+# Maxwell-Boltzmann velocities.
+_KB_EV = 8.617333262e-5
+_EV_PER_AMU_TO_A2_PER_FS2 = 1.602176634e-19 / 1.66053906660e-27 * 1e-10
+
+
+@dataclasses.dataclass(frozen=True)
+class Arch:
+    """Architecture of one invariant message-passing potential."""
+
+    cutoff: float
+    n_radial: int
+    n_layers: int
+    n_feat: int
+    n_species: int
+
+    def param_count(self) -> int:
+        S, F, K, L = self.n_species, self.n_feat, self.n_radial, self.n_layers
+        per_layer = F * F + K * F + F + F * F + F + F * F + F + F * F + F
+        return S * F + L * per_layer + F * F + F + F + 1 + S
+
+
+# The two architectures of the distilled multi-time-step pair: the big model
+# (5.0 A cutoff, 16 radial functions, 2 layers, 64 features) and the distilled
+# small model (3.5 A cutoff, 8 radial functions, 1 layer, 32 features).
+def big_arch(n_species: int = 2) -> Arch:
+    return Arch(cutoff=5.0, n_radial=16, n_layers=2, n_feat=64, n_species=n_species)
+
+
+def small_arch(n_species: int = 2) -> Arch:
+    return Arch(cutoff=3.5, n_radial=8, n_layers=1, n_feat=32, n_species=n_species)
+
+
+def param_slices(arch: Arch) -> dict:
+    """Offsets of every named block in the flat parameter vector.
+
+    Keys: ``A``, ``R1``, ``d1``, ``R2``, ``d2``, ``e0`` and, per layer ``l``,
+    ``(l, name)`` for name in W_in, W1, b1, W2, b2, U1, c1, U2, c2. Values are
+    ``(offset, shape)``.
+    """
+    S, F, K = arch.n_species, arch.n_feat, arch.n_radial
+    out = {}
+    off = 0
+
+    def take(key, shape):
+        nonlocal off
+        out[key] = (off, shape)
+        off += int(np.prod(shape))
+
+    take("A", (S, F))
+    for l in range(arch.n_layers):
+        take((l, "W_in"), (F, F))
+        take((l, "W1"), (K, F))
+        take((l, "b1"), (F,))
+        take((l, "W2"), (F, F))
+        take((l, "b2"), (F,))
+        take((l, "U1"), (F, F))
+        take((l, "c1"), (F,))
+        take((l, "U2"), (F, F))
+        take((l, "c2"), (F,))
+    take("R1", (F, F))
+    take("d1", (F,))
+    take("R2", (F,))
+    take("d2", (1,))
+    take("e0", (S,))
+    assert off == arch.param_count()
+    return out
+
+
+# Readout scale: chosen so that the random-init big model gives RMS force
+# components of order 1 eV/A on liquid-density water (the scale of real
+# water forces), which is what the stated force tolerances assume.
+ENERGY_SCALE = 0.5
+BIAS_STD = 0.1
+
+
+def init_params(arch: Arch, seed: int, energy_scale: float = ENERGY_SCALE) -> np.ndarray:
+    """Random-init parameters (float64), drawn from PCG64(seed).
+
+    Weights ~ N(0, 1/fan_in); biases ~ N(0, BIAS_STD^2) (non-zero so that a
+    dropped bias term changes the result); A ~ N(0, 1); the readout output
+    layer, its bias and e0 are multiplied by ``energy_scale`` (eV).
+    """
+    rng = np.random.default_rng(seed)
+    sl = param_slices(arch)
+    p = np.empty(arch.param_count(), dtype=np.float64)
+    for key, (off, shape) in sl.items():
+        name = key[1] if isinstance(key, tuple) else key
+        n = int(np.prod(shape))
+        if name in ("b1", "b2", "c1", "c2", "d1"):
+            vals = rng.normal(0.0, BIAS_STD, n)
+        elif name == "A":
+            vals = rng.normal(0.0, 1.0, n)
+        elif name == "R2":
+            vals = rng.normal(0.0, 1.0 / math.sqrt(arch.n_feat), n) * energy_scale
+        elif name == "d2":
+            vals = rng.normal(0.0, BIAS_STD, n) * energy_scale
+        elif name == "e0":
+            vals = rng.normal(0.0, 1.0, n) * energy_scale
+        else:  # weight matrix, fan_in = first dimension
+            vals = rng.normal(0.0, 1.0 / math.sqrt(shape[0]), n)
+        p[off:off + n] = vals
+    return p
+
+
+def unpack_params(arch: Arch, p: np.ndarray) -> dict:
+    """View the flat vector as named arrays (no copy)."""
+    p = np.asarray(p, dtype=np.float64)
+    return {k: p[o:o + int(np.prod(s))].reshape(s) for k, (o, s) in param_slices(arch).items()}
+
+
+# --------------------------------------------------------------------------
+# Structures
+# --------------------------------------------------------------------------
+
+def _random_rotations(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Uniform random rotation matrices (Shoemake's subgroup algorithm)."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    q = np.stack([
+        np.sqrt(1 - u1) * np.sin(2 * np.pi * u2),
+        np.sqrt(1 - u1) * np.cos(2 * np.pi * u2),
+        np.sqrt(u1) * np.sin(2 * np.pi * u3),
+        np.sqrt(u1) * np.cos(2 * np.pi * u3),
+    ], axis=1)
+    x, y, z, w = q.T
+    R = np.empty((n, 3, 3))
+    R[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    R[:, 0, 1] = 2 * (x * y - z * w)
+    R[:, 0, 2] = 2 * (x * z + y * w)
+    R[:, 1, 0] = 2 * (x * y + z * w)
+    R[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    R[:, 1, 2] = 2 * (y * z - x * w)
+    R[:, 2, 0] = 2 * (x * z - y * w)
+    R[:, 2, 1] = 2 * (y * z + x * w)
+    R[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+@dataclasses.dataclass
+class System:
+    """One batch of independent systems (a single periodic box or molecules).
+
+    ``x`` [N, 3] float64; ``species`` [N] int32; ``mass`` [N] float64;
+    ``atom_offset`` [n_systems + 1] int32; ``box`` [n_systems] float64 cubic
+    edge length (<= 0 means non-periodic).
+    """
+
+    x: np.ndarray
+    species: np.ndarray
+    mass: np.ndarray
+    atom_offset: np.ndarray
+    box: np.ndarray
+    n_species: int
+    name: str = ""
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def n_systems(self) -> int:
+        return int(self.box.shape[0])
+
+
+def make_water(n_side: int, box: float, seed: int = 0) -> System:
+    """``n_side**3`` rigid water molecules (O-H 0.96 A, H-O-H 104.5 deg) with
+    O at the lattice sites ``(i + 1/2) * box / n_side`` and uniformly random
+    orientations, in a periodic cubic box; atoms ordered O, H, H per molecule
+    and wrapped into ``[0, box)``.
+
+    192 atoms: ``make_water(4, 12.42)``; 12,288 atoms: ``make_water(16, 49.7)``.
+    """
+    rng = np.random.default_rng(seed)
+    n_mol = n_side ** 3
+    a = box / n_side
+    g = (np.arange(n_side) + 0.5) * a
+    O = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    half = np.deg2rad(104.5) / 2
+    r_oh = 0.96
+    local = np.array([[0.0, 0.0, 0.0],
+                      [r_oh * np.sin(half), 0.0, r_oh * np.cos(half)],
+                      [-r_oh * np.sin(half), 0.0, r_oh * np.cos(half)]])
+    R = _random_rotations(rng, n_mol)
+    pos = O[:, None, :] + np.einsum("mab,kb->mka", R, local)
+    x = pos.reshape(-1, 3)
+    x = x - box * np.floor(x / box)
+    species = np.tile(np.array([1, 0, 0], dtype=np.int32), n_mol)
+    mass = np.where(species == 1, MASS_O, MASS_H).astype(np.float64)
+    return System(x=x, species=species, mass=mass,
+                  atom_offset=np.array([0, 3 * n_mol], dtype=np.int32),
+                  box=np.array([box], dtype=np.float64), n_species=2,
+                  name=f"water{3 * n_mol}")
+
+
+def water_192(seed: int = 0) -> System:
+    return make_water(4, 12.42, seed)
+
+
+def water_12288(seed: int = 0) -> System:
+    return make_water(16, 49.7, seed)
+
+
+def make_vacuum_batch(n_mol: int = 512, n_min: int = 10, n_max: int = 60,
+                      seed: int = 0) -> System:
+    """``n_mol`` independent non-periodic molecules of ``U{n_min..n_max}``
+    atoms: seeded random-walk chains with bond lengths ``U[1.1, 1.5]`` A in
+    uniformly random directions, each new atom at least 1.0 A from all earlier
+    atoms of its molecule; elements uniform over H/C/N/O."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_min, n_max + 1, n_mol)
+    xs, zs = [], []
+    for n in sizes:
+        pts = [np.zeros(3)]
+        while len(pts) < n:
+            v = rng.normal(size=3)
+            v /= np.linalg.norm(v)
+            p = pts[-1] + rng.uniform(1.1, 1.5) * v
+            if np.min(np.linalg.norm(np.asarray(pts) - p, axis=1)) >= 1.0:
+                pts.append(p)
+        xs.append(np.asarray(pts))
+        zs.append(rng.integers(0, 4, n))
+    masses = np.array([MASS_H, MASS_C, MASS_N, MASS_O])
+    species = np.concatenate(zs).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    return System(x=np.concatenate(xs), species=species, mass=masses[species],
+                  atom_offset=off, box=np.zeros(n_mol), n_species=4,
+                  name=f"vacuum{n_mol}")
+
+
+def maxwell_boltzmann(mass: np.ndarray, temperature: float, seed: int = 1,
+                      atom_offset: np.ndarray | None = None) -> np.ndarray:
+    """Velocities (A/fs) from the Maxwell-Boltzmann distribution at
+    ``temperature`` K, with the centre-of-mass momentum of every system
+    removed (no rescaling)."""
+    rng = np.random.default_rng(seed)
+    sigma = np.sqrt(_KB_EV * temperature / mass * _EV_PER_AMU_TO_A2_PER_FS2)
+    v = rng.normal(size=(mass.shape[0], 3)) * sigma[:, None]
+    if atom_offset is None:
+        atom_offset = np.array([0, mass.shape[0]])
+    for s in range(len(atom_offset) - 1):
+        a, b = atom_offset[s], atom_offset[s + 1]
+        p = (mass[a:b, None] * v[a:b]).sum(0)
+        v[a:b] -= p / mass[a:b].sum()
+    return v
