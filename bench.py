@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput of distilled multi-time-step MD (Algorithm 1) on one GB300.
+
+One timed step is one outer step of Algorithm 1 on the synthetic
+12,288-atom water box (4,096 rigid-geometry waters, L = 49.7 A): n_inner
+small-model (3.5 A) neighbour lists + force evaluations with their kicks and
+drifts, then one big-model (5.0 A) neighbour list + force evaluation and the
+closing half-kick, all through the C ABI (dmts_respa_step). The baseline is
+plain 1 fs velocity Verlet with the big model alone, timed the same way.
+
+Prints one JSON line. ``value`` is DMTS ns/day (whole job: with N GPUs every
+rank runs its own replica, so simulated time adds up). The L2 cache (129 MB)
+is flushed between timed steps by writing a 256 MB buffer on the same stream;
+each step is timed with CUDA events on the library's stream.
+
+``--impl reference`` times the FP64 CPU oracle (the plain definition of the
+same step) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DMTS ns/day and atom-force evals/s vs plain 1 fs NNP MD on same GB300"
+FS_PER_NS = 1e6
+SEC_PER_DAY = 86400.0
+# FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) at the
+# maximum SM clock of 2,070 MHz.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def workload(name: str):
+    from paper_2510_06562_gb300 import inputs as I
+    if name == "water12288":
+        return I.water_12288(0)
+    if name == "water192":
+        return I.water_192(0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def models(n_species: int):
+    from paper_2510_06562_gb300 import inputs as I
+    return (I.small_arch(n_species), I.init_params(I.small_arch(n_species), 2),
+            I.big_arch(n_species), I.init_params(I.big_arch(n_species), 3))
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- GPU arm
+WINDOW_FS = 60.0
+
+
+def time_steps(ctx, torch, stream, flush, n_steps, dt, n_inner, x0, v0):
+    """Per-step CUDA-event times (ms) of n_steps single outer steps, with the
+    L2 flushed before each step (outside the timed window).
+
+    The random-init models conserve energy for ~120-200 fs before the system
+    collapses into a dense many-neighbour well, so the timed steps are taken
+    in windows of WINDOW_FS simulated fs that restart from the initial state
+    (x0, v0); the restart and the first step after it (which re-evaluates
+    both models) are not timed."""
+    ms = []
+    launches = 0
+    per_window = max(1, int(WINDOW_FS / dt))
+    for k in range(n_steps):
+        if k % per_window == 0:
+            ctx.set_state(x0, v0)
+            ctx.respa_step(1, dt, n_inner, energies=False)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        n0 = ctx.launch_count
+        a.record(stream)
+        ctx.respa_step(1, dt, n_inner, energies=False)
+        b.record(stream)
+        launches += ctx.launch_count - n0
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms, launches
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2510_06562_gb300 import build as B
+    from paper_2510_06562_gb300 import dmts as D
+    from paper_2510_06562_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    s = workload(args.workload)
+    sa, sp, ba, bp = models(s.n_species)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1 + rank)
+    N = s.n_atoms
+    dt, n_inner = args.outer_fs, args.n_inner
+    prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
+
+    ctx = D.Context(s, ba, bp, sa, sp, precision=prec)
+    sts = D.Context(s, ba, bp, precision=prec)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    sstream = torch.cuda.ExternalStream(sts.stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ctx.set_state(s.x, v0)
+    sts.set_state(s.x, v0)
+    ctx.respa_step(max(3, args.warmup), dt, n_inner, energies=False)
+    sts.respa_step(max(3, args.warmup), 1.0, 1, energies=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms_dmts, launches = time_steps(ctx, torch, stream, flush, args.steps, dt, n_inner, s.x, v0)
+    ms_sts, _ = time_steps(sts, torch, sstream, flush, args.steps, 1.0, 1, s.x, v0)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_dmts = sum(ms_dmts) / 1e3
+    t_sts = sum(ms_sts) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dmts, t_sts], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dmts, t_sts = tt.tolist()
+    ns_dmts = world * args.steps * dt / FS_PER_NS / t_dmts * SEC_PER_DAY
+    ns_sts = world * args.steps * 1.0 / FS_PER_NS / t_sts * SEC_PER_DAY
+    evals = world * args.steps * (n_inner + 1) * N / t_dmts
+
+    # 6 fs outer step (6 inner steps of 1 fs), fewer steps
+    k6 = max(3, args.steps // 2)
+    ctx.respa_step(3, 6.0, 6, energies=False)
+    ms6, _ = time_steps(ctx, torch, stream, flush, k6, 6.0, 6, s.x, v0)
+    ns6 = k6 * 6.0 / FS_PER_NS / (sum(ms6) / 1e3) * SEC_PER_DAY
+
+    # dominant kernel: per-stage CUDA-event times of one big-model evaluation
+    stages_big = ctx.time_stages(D.BIG, reps=20)
+    stages_small = ctx.time_stages(D.SMALL, reps=20)
+    rp, _ = ctx.neighbors(D.BIG)
+    E_big = int(rp[-1])
+    rp_s, _ = ctx.neighbors(D.SMALL)
+    E_small = int(rp_s[-1])
+    dom = max((k for k in stages_big if k.startswith("edge_")), key=lambda k: stages_big[k])
+    K, F = ba.n_radial, ba.n_feat
+    flop_edge = 2 * (2 * K * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (K * F + F * F)
+    achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
+    roofline = {"kernel": f"{dom} (big model, FP32 SIMT)", "bound": "alu", "achieved": achieved,
+                "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_TFLOPS,
+                "traffic": None, "algorithmic_flop_per_launch": flop_edge * E_big,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+    # end to end through the public API with host buffers: upload state,
+    # one outer step, read energies and state back (each step)
+    xh = torch.tensor(s.x).pin_memory()
+    vh = torch.tensor(v0).pin_memory()
+    eh = torch.empty((1, s.n_systems, 3), dtype=torch.float64).pin_memory()
+    k_e2e = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.set_state(xh, vh)
+        ctx.respa_step(1, dt, n_inner, out=eh)
+        ctx.get_state(xh, vh)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * k_e2e * dt / FS_PER_NS / t_e2e * SEC_PER_DAY, "unit": "ns/day",
+           "h2d_bytes_per_step": 2 * N * 3 * 8, "d2h_bytes_per_step": 2 * N * 3 * 8 + 3 * 8 * s.n_systems,
+           "note": "state uploaded and read back every step; each upload recomputes both models' first-step forces"}
+
+    if rank != 0:
+        return None
+    cpu = cpu_baseline(args, s, sa, sp, ba, bp, dt, n_inner) if world == 1 and not args.no_cpu else None
+    line = {
+        "metric": METRIC, "value": ns_dmts, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": t_dmts * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == D.FP32 else "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 4,096 rigid waters, 12,288 atoms, L=49.7 A, periodic",
+                   "outer_fs": dt, "inner_fs": dt / n_inner, "n_inner": n_inner,
+                   "precision": args.precision, "small_model": "3.5 A, K=8, 1 layer, F=32",
+                   "big_model": "5.0 A, K=16, 2 layers, F=64", "state": "FP64 x, v",
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
+        "atom_force_evals_per_s": evals, "sts_1fs_ns_per_day": ns_sts, "speedup_vs_sts": ns_dmts / ns_sts,
+        "dmts_6fs_ns_per_day": ns6, "speedup_6fs_vs_sts": ns6 / ns_sts,
+        "ms_per_step_sts": t_sts * 1e3 / args.steps,
+        "pairs": {"small": E_small, "big": E_big},
+        "stage_ms": {"big": stages_big, "small": stages_small},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return line
+
+
+# ------------------------------------------------------------------- oracle
+def _oracle_step_time(s, sa, sp, ba, bp, n_inner):
+    """Seconds of one outer step of Algorithm 1 by the FP64 oracle: n_inner
+    small-model and one big-model evaluation (pairs + energy + forces)."""
+    from oracle import model as M
+    t0 = time.perf_counter()
+    M.energy_forces(M.spec_of(sa), sp, s.x, s.species, s.atom_offset, s.box)
+    t_small = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M.energy_forces(M.spec_of(ba), bp, s.x, s.species, s.atom_offset, s.box)
+    t_big = time.perf_counter() - t0
+    return n_inner * t_small + t_big, t_small, t_big
+
+
+def cpu_baseline(args, s, sa, sp, ba, bp, dt, n_inner):
+    import torch
+    t_step, t_small, t_big = _oracle_step_time(s, sa, sp, ba, bp, n_inner)
+    return {"value": dt / FS_PER_NS / t_step * SEC_PER_DAY, "unit": "ns/day",
+            "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": (f"one small ({t_small:.2f} s) and one big ({t_big:.2f} s) FP64 force evaluation of the "
+                       f"{s.n_atoms}-atom box with O(N^2) pairs, combined as {n_inner} small + 1 big per "
+                       f"{dt:g} fs outer step")}
+
+
+def run_reference(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    s = workload(args.workload)
+    sa, sp, ba, bp = models(s.n_species)
+    dt, n_inner = args.outer_fs, args.n_inner
+    # bounded: every step is one full outer step of the oracle (~10-20 s);
+    # as many as fit in about two minutes after one warm-up step
+    _oracle_step_time(s, sa, sp, ba, bp, n_inner)
+    budget = 120.0
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < args.steps and (time.perf_counter() - t_start) < budget:
+        times.append(_oracle_step_time(s, sa, sp, ba, bp, n_inner)[0])
+    t = sum(times)
+    value = len(times) * dt / FS_PER_NS / t * SEC_PER_DAY
+    sample = (f"{len(times)} outer step(s) of {dt:g} fs ({n_inner} small + 1 big FP64 force evaluation each, "
+              f"O(N^2) pairs) on the {s.n_atoms}-atom box, capped at ~{budget:.0f} s")
+    return {"metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": len(times),
+            "warmup": 1, "ms_per_step": t * 1e3 / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: 4,096 rigid waters, 12,288 atoms, L=49.7 A, periodic",
+                       "outer_fs": dt, "inner_fs": dt / n_inner, "n_inner": n_inner, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "ns/day", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water12288")
+    ap.add_argument("--outer-fs", type=float, default=3.0)
+    ap.add_argument("--n-inner", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

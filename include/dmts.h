@@ -1,0 +1,199 @@
+/*
+ * dmts.h -- C ABI of the GB300 (sm_103a) distilled multi-time-step library.
+ *
+ * The library evaluates two neural-network potentials -- a "big" reference
+ * model and a cheaper "small" distilled model with a shorter cutoff -- and
+ * integrates Newton's equations with the multiple-time-step scheme of
+ * Algorithm 1 of arXiv 2510.06562 (section "Integration scheme"): the small
+ * model's forces drive every inner step, and every outer step a half-kick
+ * with the difference F_big - F_small on each side restores the big model's
+ * dynamics. The thermostat of Algorithm 1 is the identity here (NVE).
+ *
+ * Potential (both models; hyperparameters per model): invariant message
+ * passing on the directed neighbour pairs within the cutoff rc,
+ *   h0_i  = A[Z_i]
+ *   per layer: u_i = h_i W_in; w_ij = fc(d_ij) (SiLU(e(d_ij) W1 + b1) W2 + b2);
+ *              m_i = sum_j w_ij * u_j; h_i += SiLU(m_i U1 + c1) U2 + c2
+ *   E_i   = SiLU(h_i R1 + d1) . R2 + d2 + e0[Z_i]
+ *           + 1/2 sum_j rep_a exp(-d_ij/rep_rho) fc(d_ij; rep_cutoff),
+ *   E     = sum_i E_i,
+ * with the Bessel basis e_k(d) = sqrt(2/rc) sin(k pi d/rc)/d (k = 1..K) and
+ * the cosine cutoff fc(d; r) = (cos(pi d/r) + 1)/2 (fc(d) = fc(d; rc)). The
+ * last term is a fixed short-range pair repulsion (rep_a = 0 disables it).
+ * Forces are F = -dE/dx.
+ * The paper defers its architectures to its Supporting Information; this
+ * family stands in for them (section "Neural Network Architectures").
+ *
+ * Units: positions in Angstrom, velocities in Angstrom/fs, masses in amu,
+ * energies in eV, forces in eV/Angstrom, time in fs.
+ *
+ * Conventions for every call:
+ *  - All arrays are owned by the caller; the library copies what it needs.
+ *    A pointer may point to host memory or to CUDA device memory of the
+ *    context's device; the library tells them apart itself.
+ *  - Per-atom 3-vectors are arrays of N*3 doubles, atom-major
+ *    (x[3*i + 0..2]), i.e. a C-contiguous [N][3] array.
+ *  - Every call returns DMTS_OK (0) or a negative dmts_status and throws
+ *    nothing. dmts_last_error() describes the last failure of the calling
+ *    thread. After DMTS_ERR_ARG, DMTS_ERR_CAPACITY or DMTS_ERR_NONFINITE the
+ *    context stays usable; after DMTS_ERR_CUDA it may not be, and later calls
+ *    on it return DMTS_ERR_STATE.
+ *  - All device work of a context runs on its own CUDA stream
+ *    (dmts_stream); calls return after that work has completed.
+ *  - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef DMTS_H
+#define DMTS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported from libdmts.so (built with hidden default visibility). */
+#if defined(__GNUC__)
+#define DMTS_API __attribute__((visibility("default")))
+#else
+#define DMTS_API
+#endif
+
+typedef struct dmts_ctx dmts_ctx;
+
+typedef enum {
+    DMTS_OK = 0,
+    DMTS_ERR_ARG = -1,        /* invalid argument (NULL, size, layout)            */
+    DMTS_ERR_OOM = -2,        /* device or host allocation failed                 */
+    DMTS_ERR_CUDA = -3,       /* CUDA runtime error (no device, launch failure)   */
+    DMTS_ERR_CAPACITY = -4,   /* neighbour capacity could not be grown enough     */
+    DMTS_ERR_NONFINITE = -5,  /* a position or velocity became NaN or infinite    */
+    DMTS_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up               */
+    DMTS_ERR_STATE = -7       /* context unusable, or no state set yet            */
+} dmts_status;
+
+/* Arithmetic of the multilayer perceptrons. DMTS_FP32: FP32 everywhere.
+ * DMTS_BF16_MLP: dense layers on tensor cores with BF16 operands and FP32
+ * accumulation; edge geometry, sums and forces stay FP32. */
+enum { DMTS_FP32 = 0, DMTS_BF16_MLP = 1 };
+
+/* Model selector for dmts_forces / dmts_neighbors / dmts_set_params. */
+enum { DMTS_SMALL = 0, DMTS_BIG = 1 };
+
+/* One potential. params: n_params doubles in the documented flat order
+ *   A[S][F]; per layer: W_in[F][F], W1[K][F], b1[F], W2[F][F], b2[F],
+ *   U1[F][F], c1[F], U2[F][F], c2[F]; then R1[F][F], d1[F], R2[F], d2[1],
+ *   e0[S]
+ * (matrices row-major, input index first: y = x W), so
+ *   n_params = S F + n_layers (4 F^2 + K F + 4 F) + F^2 + 2 F + 1 + S.
+ * Supported: 1 <= n_layers <= 4; n_feat in {32, 64}; 1 <= n_radial <= 16;
+ * 1 <= n_species <= 16; cutoff > 0. Copied at dmts_create. */
+typedef struct {
+    double cutoff;       /* rc, Angstrom                                  */
+    int n_radial;        /* K                                             */
+    int n_layers;        /* message-passing layers                        */
+    int n_feat;          /* F                                             */
+    int n_species;       /* S                                             */
+    const double* params;
+    size_t n_params;
+    int precision;       /* DMTS_FP32 or DMTS_BF16_MLP                    */
+    double rep_a;        /* pair repulsion amplitude, eV (>= 0)           */
+    double rep_rho;      /* its decay length, Angstrom (> 0 if rep_a > 0) */
+    double rep_cutoff;   /* its cutoff, Angstrom (0 < rep_cutoff <= cutoff if rep_a > 0) */
+} dmts_model_desc;
+
+/* The simulated systems: n_systems independent systems stored back to back.
+ * atom_offset[n_systems + 1] (atom_offset[0] = 0, non-decreasing), species
+ * [N] in [0, n_species), mass [N] > 0 (amu), box [n_systems]: edge length of
+ * a periodic cubic box (Angstrom, at least twice the largest cutoff), or
+ * <= 0 for a non-periodic system. Atoms of different systems never interact.
+ * Supported: one periodic system, or any number of non-periodic systems of
+ * at most 1024 atoms each. */
+typedef struct {
+    int n_systems;
+    const int* atom_offset;
+    const int* species;
+    const double* mass;
+    const double* box;
+} dmts_system_desc;
+
+/* Create a context on the current CUDA device (Algorithm 1's two force
+ * fields, masses and boxes). small may be NULL: then dmts_respa_step runs
+ * single-time-step velocity Verlet with the big model. options: NULL or a
+ * JSON object; recognised keys: "edge_capacity_factor" (default 1.5, the
+ * neighbour-pair capacity relative to the uniform-density estimate),
+ * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
+ * "atoms_per_cta_big" / "atoms_per_cta_small" (atoms per thread block of the
+ * force kernels).
+ * On success *out holds the new context; on failure *out is NULL. */
+DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big,
+                const dmts_system_desc* sys, const char* options, dmts_ctx** out);
+
+/* Set positions x[N*3] and velocities v[N*3] (NULL: zero velocities).
+ * Periodic positions are wrapped into [0, L) as x - L floor(x / L).
+ * Invalidates the cached forces: the next dmts_respa_step evaluates both
+ * models first (Algorithm 1's first_step). n_atoms must equal N. */
+DMTS_API int dmts_set_state(dmts_ctx* ctx, const double* x, const double* v, int n_atoms);
+
+/* Read back positions and velocities (either pointer may be NULL). */
+DMTS_API int dmts_get_state(dmts_ctx* ctx, double* x, double* v);
+
+/* Evaluate one model (DMTS_SMALL or DMTS_BIG) at the current positions.
+ * f_out [N*3] forces F = -dE/dx (or NULL); energy_out [n_systems] potential
+ * energies (or NULL); virial_out [n_systems*9] row-major 3x3 virial
+ * W_ab = -sum_pairs r_ij,a dE/dr_ij,b (or NULL). */
+DMTS_API int dmts_forces(dmts_ctx* ctx, int which, double* f_out, double* energy_out,
+                double* virial_out);
+
+/* n_outer steps of Algorithm 1 with outer step dt_outer_fs and n_inner inner
+ * steps of dt_outer_fs / n_inner (n_inner = 1 without a small model: then
+ * velocity Verlet with the big model). Positions of periodic systems are
+ * wrapped after every drift. energies_out: NULL or [n_outer][n_systems][3]
+ * holding, after each outer step, the big model's potential energy, the
+ * kinetic energy and their sum. On neighbour overflow the call restores the
+ * state it started from, grows the capacity and runs again. */
+DMTS_API int dmts_respa_step(dmts_ctx* ctx, int n_outer, double dt_outer_fs, int n_inner,
+                    double* energies_out);
+
+/* Destroy a context and free its device memory. NULL is a no-op. */
+DMTS_API void dmts_destroy(dmts_ctx* ctx);
+
+/* Message describing the calling thread's last error ("" if none). */
+DMTS_API const char* dmts_last_error(void);
+
+/* Neighbour pairs of one model at the current positions, in CSR form:
+ * row_ptr [N+1] and col [capacity] (ascending within each row), directed
+ * pairs (i, j) with j != i, same system, |r_ij|^2 < rc^2 evaluated in FP64
+ * (r_ij = x_j - x_i - L rint((x_j - x_i)/L) when periodic, each operation
+ * rounded, no fused multiply-add). *n_pairs receives the number of pairs;
+ * DMTS_ERR_CAPACITY if it exceeds capacity (row_ptr is still written). */
+DMTS_API int dmts_neighbors(dmts_ctx* ctx, int which, int* row_ptr, int* col,
+                   long long capacity, long long* n_pairs);
+
+/* Replace one model's parameters (same architecture, n_params doubles in the
+ * flat order above). Invalidates the cached forces. */
+DMTS_API int dmts_set_params(dmts_ctx* ctx, int which, const double* params, size_t n_params);
+
+/* The cudaStream_t (as void*) on which the context launches its work. */
+DMTS_API void* dmts_stream(dmts_ctx* ctx);
+
+/* Number of the library's kernel launches since the context was created
+ * (including launches inside CUDA graph replays). */
+DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
+
+/* Time one model's force evaluation at the current positions, stage by stage,
+ * with CUDA events on the context's stream, averaged over reps (>= 1)
+ * evaluations. ms_out[n_out] receives milliseconds per evaluation for:
+ *   [0] quantisation, cell list and neighbour list,
+ *   [1] species embedding,
+ *   [2 + l] forward edge pass of layer l (l < n_layers),
+ *   [2 + n_layers + l] backward edge pass of layer l,
+ *   [2 + 2 n_layers] energy reduction.
+ * Returns the number of entries written (3 + 2 n_layers, at most n_out) or
+ * a negative dmts_status. */
+DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out, int n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMTS_H */

@@ -11,11 +11,16 @@ message-passing architecture, defined here as plainly as possible:
               m_i   = sum_{j in N(i)} w_ij * u_j            (elementwise)
               h_i  <- h_i + SiLU(m_i U1 + c1) U2 + c2
     E_i    = SiLU(h_i R1 + d1) . R2 + d2 + e0[Z_i]
+             + (1/2) sum_{j in N(i)} a exp(-d_ij / rho) fc(d_ij; r_rep)
     E      = sum_i E_i                   (per independent system)
 
     e_k(d) = sqrt(2/rc) sin(k pi d / rc) / d,  k = 1..K   (Bessel basis)
     fc(d)  = (cos(pi d / rc) + 1) / 2 for d < rc, else 0  (cosine cutoff)
     SiLU(a) = a / (1 + exp(-a))
+
+The last term is a short-range pair repulsion (a, rho, r_rep <= rc fixed, not
+trained): random-init networks have no repulsive core, which the paper's
+trained models do have; the same term in both models cancels in F - F_small.
 
 N(i) is the set of j != i with |r_ij|^2 < rc^2 (strict, FP64), where r_ij is
 the minimum-image difference x_j - x_i - L rint((x_j - x_i) / L) in a periodic
@@ -41,18 +46,22 @@ DT = torch.float64
 
 class Spec(NamedTuple):
     """Architecture: cutoff (A), K radial functions, Lr layers, F features,
-    S species."""
+    S species; pair repulsion amplitude (eV), decay length and cutoff (A)."""
 
     cutoff: float
     n_radial: int
     n_layers: int
     n_feat: int
     n_species: int
+    rep_a: float = 0.0
+    rep_rho: float = 1.0
+    rep_cutoff: float = 0.0
 
 
 def spec_of(obj) -> Spec:
     return Spec(float(obj.cutoff), int(obj.n_radial), int(obj.n_layers),
-                int(obj.n_feat), int(obj.n_species))
+                int(obj.n_feat), int(obj.n_species), float(getattr(obj, "rep_a", 0.0)),
+                float(getattr(obj, "rep_rho", 1.0)), float(getattr(obj, "rep_cutoff", 0.0)))
 
 
 def parse_params(spec: Spec, p) -> dict:
@@ -208,7 +217,11 @@ def atomic_energies_from_pairs(spec: Spec, P: dict, species, i, j, r):
         w = fc[:, None] * phi
         m = torch.zeros(n, spec.n_feat, dtype=DT).index_add(0, i, w * u[j])
         h = h + silu(m @ lay["U1"] + lay["c1"]) @ lay["U2"] + lay["c2"]
-    return silu(h @ P["R1"] + P["d1"]) @ P["R2"] + P["d2"][0] + P["e0"][species]
+    Ei = silu(h @ P["R1"] + P["d1"]) @ P["R2"] + P["d2"][0] + P["e0"][species]
+    if spec.rep_a != 0.0 and spec.rep_cutoff > 0.0:
+        phi = spec.rep_a * torch.exp(-d / spec.rep_rho) * cosine_cutoff(d, spec.rep_cutoff)
+        Ei = Ei + 0.5 * torch.zeros(n, dtype=DT).index_add(0, i, phi)
+    return Ei
 
 
 def energy(spec: Spec, params, x, species, atom_offset, box, pairs=None):

@@ -16,7 +16,7 @@ __all__ = ["inputs", "dmts"]
 
 
 def __getattr__(name):
-    if name == "dmts":
-        from . import dmts
-        return dmts
+    if name in ("dmts", "build"):
+        import importlib
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,905 @@
+// C ABI of the DMTS library (declared in include/dmts.h).
+//
+// A context owns the device state (FP64 positions and velocities, the two
+// models' FP32 parameters, neighbour lists and feature buffers), one CUDA
+// stream and the CUDA graphs of the integration steps: one graph per
+// (n_inner, dt) holds a whole outer step of Algorithm 1 -- n_inner times
+// (kicks + drifts, small-model neighbour list and forces) followed by the
+// big-model neighbour list and forces and the closing half-kick -- and is
+// replayed once per outer step. Neighbour capacity overflow is detected on
+// the device; the host restores the state saved at the start of the call,
+// grows the capacity, re-captures the graph and runs the call again.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/dmts.h"
+#include "internal.cuh"
+
+namespace dmts {
+thread_local long long* g_launch_counter = nullptr;
+double accel_constant();
+}  // namespace dmts
+
+using namespace dmts;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? DMTS_ERR_OOM : DMTS_ERR_CUDA,  \
+                        "%s: %s", #expr, cudaGetErrorString(e_));                        \
+    } while (0)
+
+double json_number(const char* js, const char* key, double dflt) {
+    if (!js) return dflt;
+    std::string k = std::string("\"") + key + "\"";
+    const char* p = strstr(js, k.c_str());
+    if (!p) return dflt;
+    p = strchr(p + k.size(), ':');
+    if (!p) return dflt;
+    char* end = nullptr;
+    double v = strtod(p + 1, &end);
+    return end == p + 1 ? dflt : v;
+}
+
+struct Model {
+    bool present = false;
+    int F = 0, K = 0, L = 0, S = 0, precision = 0;
+    double rc = 0;
+    double rep_a = 0, rep_rho = 1, rep_rc = 0;
+    float* erep = nullptr;
+    size_t n_params = 0;
+    ModelOffsets off{};
+    float* P = nullptr;
+    int nc = 0, n_cells = 0;
+    int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr, *atom_cell = nullptr,
+        *atom_slot = nullptr;
+    int row_cap = 0;
+    long long e_cap = 0;
+    int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
+    float *h = nullptr, *gh = nullptr, *force = nullptr, *vir6 = nullptr;
+    float* u[kMaxLayers] = {};
+    float* z[kMaxLayers] = {};
+    float* mbar[2] = {};
+    double *Ei = nullptr, *E = nullptr, *W = nullptr;
+    int apc_fwd = 16, apc_bwd = 16;
+};
+
+}  // namespace
+
+struct dmts_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int N = 0, n_sys = 0;
+    bool periodic = false;
+    std::vector<int> h_off;
+    std::vector<double> h_box;
+    int *d_off = nullptr, *d_species = nullptr, *d_sys = nullptr;
+    double *d_box = nullptr, *d_mass = nullptr, *d_inv_m = nullptr;
+    double *d_x = nullptr, *d_v = nullptr;
+    uint4* d_q = nullptr;
+    Frame* d_frame = nullptr;
+    double* d_stage = nullptr;   // [2][N*3]
+    double *d_ke = nullptr, *d_ekin = nullptr;
+    double* d_ring = nullptr;
+    int ring_len = 0;
+    int* d_flags = nullptr;
+    int* h_flags = nullptr;      // pinned
+    double *d_bx = nullptr, *d_bv = nullptr;
+    float *d_bfs = nullptr, *d_bfb = nullptr;
+    Model m[2];
+    double rc_max = 0;
+    double cap_factor = 1.5;
+    bool state_set = false, forces_valid = false;
+    bool broken = false;
+    cudaGraphExec_t graph = nullptr;
+    int g_n_inner = 0;
+    double g_dt = 0;
+    long long g_nodes = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+struct LaunchScope {
+    explicit LaunchScope(dmts_ctx* c) { g_launch_counter = &c->launches; }
+    ~LaunchScope() { g_launch_counter = nullptr; }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+int check_model(const dmts_model_desc* d, const char* name) {
+    if (!d) return fail(DMTS_ERR_ARG, "%s model descriptor is NULL", name);
+    if (!(d->cutoff > 0)) return fail(DMTS_ERR_ARG, "%s model: cutoff must be > 0", name);
+    if (d->n_feat != 32 && d->n_feat != 64) return fail(DMTS_ERR_ARG, "%s model: n_feat must be 32 or 64", name);
+    if (d->n_radial < 1 || d->n_radial > 16) return fail(DMTS_ERR_ARG, "%s model: n_radial must be in [1, 16]", name);
+    if (d->n_layers < 1 || d->n_layers > kMaxLayers) return fail(DMTS_ERR_ARG, "%s model: n_layers must be in [1, 4]", name);
+    if (d->n_species < 1 || d->n_species > 16) return fail(DMTS_ERR_ARG, "%s model: n_species must be in [1, 16]", name);
+    if (!d->params) return fail(DMTS_ERR_ARG, "%s model: params is NULL", name);
+    ModelOffsets o = model_offsets(d->n_species, d->n_feat, d->n_radial, d->n_layers);
+    if ((size_t)o.total != d->n_params)
+        return fail(DMTS_ERR_ARG, "%s model: n_params = %zu, layout needs %d", name, d->n_params, o.total);
+    if (d->precision != DMTS_FP32 && d->precision != DMTS_BF16_MLP)
+        return fail(DMTS_ERR_ARG, "%s model: unknown precision %d", name, d->precision);
+    for (size_t k = 0; k < d->n_params; ++k)
+        if (!isfinite(d->params[k])) return fail(DMTS_ERR_ARG, "%s model: parameter %zu is not finite", name, k);
+    if (!(d->rep_a >= 0) || !isfinite(d->rep_a)) return fail(DMTS_ERR_ARG, "%s model: rep_a must be >= 0", name);
+    if (d->rep_a > 0 && (!(d->rep_rho > 0) || !(d->rep_cutoff > 0) || d->rep_cutoff > d->cutoff))
+        return fail(DMTS_ERR_ARG, "%s model: need rep_rho > 0 and 0 < rep_cutoff <= cutoff", name);
+    return DMTS_OK;
+}
+
+void free_model_nbr(Model& m) {
+    dfree(m.nbr_tmp); dfree(m.col); dfree(m.recv);
+    m.nbr_tmp = m.col = m.recv = nullptr;
+}
+
+cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
+    cudaError_t e;
+    if ((e = dalloc(&m.nbr_tmp, (size_t)c->N * m.row_cap)) != cudaSuccess) return e;
+    if ((e = dalloc(&m.col, (size_t)m.e_cap)) != cudaSuccess) return e;
+    if ((e = dalloc(&m.recv, (size_t)m.e_cap)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void free_model(Model& m) {
+    dfree(m.P);
+    dfree(m.cell_count); dfree(m.cell_start); dfree(m.cell_atoms); dfree(m.atom_cell); dfree(m.atom_slot);
+    free_model_nbr(m);
+    dfree(m.nbr_cnt); dfree(m.row_ptr);
+    dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6);
+    for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); }
+    dfree(m.mbar[0]); dfree(m.mbar[1]);
+    dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep);
+    m = Model();
+}
+
+int upload_params(dmts_ctx* c, Model& m, const double* params) {
+    std::vector<float> pf(m.n_params);
+    for (size_t k = 0; k < m.n_params; ++k) pf[k] = (float)params[k];
+    CUDA_TRY(cudaMemcpyAsync(m.P, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return DMTS_OK;
+}
+
+int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
+    m.present = true;
+    m.F = d->n_feat; m.K = d->n_radial; m.L = d->n_layers; m.S = d->n_species;
+    m.precision = d->precision;
+    m.rc = d->cutoff;
+    m.rep_a = d->rep_a;
+    m.rep_rho = d->rep_a > 0 ? d->rep_rho : 1.0;
+    m.rep_rc = d->rep_a > 0 ? d->rep_cutoff : 0.0;
+    m.n_params = d->n_params;
+    m.off = model_offsets(m.S, m.F, m.K, m.L);
+    const int N = c->N;
+    CUDA_TRY(dalloc(&m.P, m.n_params));
+    int rc = upload_params(c, m, d->params);
+    if (rc) return rc;
+    // cells (periodic) and capacity estimates
+    double expected;
+    if (c->periodic) {
+        double L = c->h_box[0];
+        int nc = (int)floor(L / (m.rc * (1.0 + 1e-9) + 1e-6));
+        m.nc = nc >= 3 ? nc : 0;
+        double rho = N / (L * L * L);
+        expected = 4.0 / 3.0 * M_PI * m.rc * m.rc * m.rc * rho;
+        m.row_cap = std::min(N, (int)(ceil(expected * 1.5 / 32.0) * 32) + 32);
+        m.e_cap = (long long)(N * expected * c->cap_factor) + 1024;
+    } else {
+        int mx = 0;
+        long long sq = 0;
+        for (int s = 0; s < c->n_sys; ++s) {
+            int n = c->h_off[s + 1] - c->h_off[s];
+            mx = std::max(mx, n);
+            sq += (long long)n * (n - 1);
+        }
+        m.nc = 0;
+        m.row_cap = std::max(32, ((mx + 31) / 32) * 32);
+        m.e_cap = std::max<long long>(1024, std::min<long long>(sq, (long long)(N * std::min(mx, 64) * c->cap_factor)) + 1024);
+    }
+    if (m.nc > 0) {
+        m.n_cells = m.nc * m.nc * m.nc;
+        CUDA_TRY(dalloc(&m.cell_count, m.n_cells));
+        CUDA_TRY(dalloc(&m.cell_start, m.n_cells + 1));
+        CUDA_TRY(dalloc(&m.cell_atoms, N));
+        CUDA_TRY(dalloc(&m.atom_cell, N));
+        CUDA_TRY(dalloc(&m.atom_slot, N));
+    }
+    CUDA_TRY(alloc_model_nbr(c, m));
+    CUDA_TRY(dalloc(&m.nbr_cnt, N));
+    CUDA_TRY(dalloc(&m.row_ptr, N + 1));
+    size_t nf = (size_t)N * m.F;
+    CUDA_TRY(dalloc(&m.h, nf));
+    CUDA_TRY(dalloc(&m.gh, nf));
+    for (int l = 0; l < m.L; ++l) {
+        CUDA_TRY(dalloc(&m.u[l], nf));
+        CUDA_TRY(dalloc(&m.z[l], nf));
+    }
+    CUDA_TRY(dalloc(&m.mbar[0], nf));
+    CUDA_TRY(dalloc(&m.mbar[1], nf));
+    CUDA_TRY(dalloc(&m.force, (size_t)3 * N));
+    CUDA_TRY(cudaMemset(m.force, 0, sizeof(float) * 3 * std::max(N, 1)));
+    CUDA_TRY(dalloc(&m.vir6, (size_t)6 * N));
+    CUDA_TRY(dalloc(&m.Ei, N));
+    CUDA_TRY(dalloc(&m.erep, N));
+    CUDA_TRY(dalloc(&m.E, c->n_sys));
+    CUDA_TRY(dalloc(&m.W, (size_t)9 * c->n_sys));
+    int mf = max_atoms_per_cta_f32(m.F, m.K, false), mb = max_atoms_per_cta_f32(m.F, m.K, true);
+    int want = m.F == 64 ? 16 : 32;
+    m.apc_fwd = std::max(8, std::min(want, mf));
+    m.apc_bwd = std::max(8, std::min(want, mb));
+    return DMTS_OK;
+}
+
+NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
+    NbrArgs a{};
+    a.n_atoms = c->N;
+    a.n_sys = c->n_sys;
+    a.q = c->d_q;
+    a.x = c->d_x;
+    a.atom_offset = c->d_off;
+    a.box = c->d_box;
+    a.frame = c->d_frame;
+    a.rc = m.rc;
+    double rc2 = m.rc * m.rc;
+    a.rc2_lo = (float)(rc2 * (1.0 - 1e-5));
+    a.rc2_hi = (float)(rc2 * (1.0 + 1e-5));
+    a.nc = m.nc;
+    a.cell_start = m.cell_start;
+    a.cell_atoms = m.cell_atoms;
+    a.row_cap = m.row_cap;
+    a.e_cap = m.e_cap;
+    a.nbr_tmp = m.nbr_tmp;
+    a.nbr_cnt = m.nbr_cnt;
+    a.row_ptr = m.row_ptr;
+    a.col = m.col;
+    a.recv = m.recv;
+    a.flags = c->d_flags;
+    a.which = which;
+    return a;
+}
+
+PotArgs pot_args(dmts_ctx* c, Model& m) {
+    PotArgs a{};
+    a.P = m.P;
+    a.off = m.off;
+    a.n_layers = m.L;
+    a.n_atoms = c->N;
+    a.q = c->d_q;
+    a.frame = c->d_frame;
+    a.species = c->d_species;
+    a.row_ptr = m.row_ptr;
+    a.col = m.col;
+    a.recv = m.recv;
+    a.e_cap = m.e_cap;
+    a.rc = (float)m.rc;
+    a.pi_over_rc = (float)(M_PI / m.rc);
+    a.bessel_pref = (float)sqrt(2.0 / m.rc);
+    a.rep_a = (float)m.rep_a;
+    a.rep_inv_rho = (float)(1.0 / m.rep_rho);
+    a.rep_rc = (float)m.rep_rc;
+    a.rep_pi_over_rc = m.rep_rc > 0 ? (float)(M_PI / m.rep_rc) : 0.f;
+    a.erep = m.erep;
+    a.h = m.h;
+    a.gh = m.gh;
+    a.Ei = m.Ei;
+    a.force = m.force;
+    a.vir6 = m.vir6;
+    return a;
+}
+
+// Quantise (optionally), build the neighbour list and evaluate energy and
+// forces of one model. Stream-ordered, no host synchronisation.
+void enqueue_neighbors(dmts_ctx* c, int which, bool quantize) {
+    Model& m = c->m[which];
+    cudaStream_t s = c->stream;
+    if (quantize) {
+        if (!c->periodic) launch_frames(c->n_sys, c->d_off, c->d_x, c->N, c->d_box, c->rc_max, c->d_frame, s);
+        launch_quantize(c->N, c->d_x, c->d_sys, c->d_frame, c->d_q, s);
+    }
+    if (m.nc > 0)
+        launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot, s);
+    launch_neighbors(nbr_args(c, m, which), s);
+}
+
+void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
+    Model& m = c->m[which];
+    cudaStream_t s = c->stream;
+    enqueue_neighbors(c, which, quantize);
+    PotArgs a = pot_args(c, m);
+    a.u_next = m.u[0];
+    launch_embed(a, m.F, s);
+    for (int l = 0; l < m.L; ++l) {
+        PotArgs f = a;
+        f.layer = l;
+        f.atoms_per_cta = m.apc_fwd;
+        f.u = m.u[l];
+        f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
+        f.z = m.z[l];
+        f.mbar_out = m.mbar[(m.L - 1) & 1];
+        launch_edge_fwd_f32(f, m.F, m.K, s);
+    }
+    for (int l = m.L - 1; l >= 0; --l) {
+        PotArgs b = a;
+        b.layer = l;
+        b.atoms_per_cta = m.apc_bwd;
+        b.u = m.u[l];
+        b.mbar = m.mbar[l & 1];
+        b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
+        b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
+        b.accumulate = (l < m.L - 1) ? 1 : 0;
+        launch_edge_bwd_f32(b, m.F, m.K, s);
+    }
+    launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
+}
+
+int sync_check(dmts_ctx* c) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->broken = true;
+        return fail(DMTS_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaMemcpy(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost));
+    return DMTS_OK;
+}
+
+// Grow neighbour capacities from the maxima seen on the device.
+int grow_capacity(dmts_ctx* c) {
+    for (int w = 0; w < 2; ++w) {
+        Model& m = c->m[w];
+        if (!m.present) continue;
+        int max_row = c->h_flags[kFlagMaxRow0 + w];
+        long long max_e = (long long)(unsigned int)c->h_flags[kFlagMaxE0 + w];
+        bool grow = false;
+        if (max_row > m.row_cap) { m.row_cap = std::min(c->N, ((int)(max_row * 1.25) + 63) / 32 * 32); grow = true; }
+        if (max_e > m.e_cap) { m.e_cap = (long long)(max_e * 1.25) + 1024; grow = true; }
+        if (grow) {
+            if (m.row_cap > 6000) return fail(DMTS_ERR_CAPACITY, "neighbour row capacity %d too large", m.row_cap);
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            free_model_nbr(m);
+            cudaError_t e = alloc_model_nbr(c, m);
+            if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "growing neighbour capacity: %s", cudaGetErrorString(e));
+        }
+    }
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return DMTS_OK;
+}
+
+int reset_flags(dmts_ctx* c) {
+    CUDA_TRY(cudaMemsetAsync(c->d_flags, 0, sizeof(int) * kFlagCount, c->stream));
+    return DMTS_OK;
+}
+
+int copy_in(dmts_ctx* c, double* dst, const double* src, size_t n) {
+    cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), k, c->stream));
+    return DMTS_OK;
+}
+
+int copy_out(dmts_ctx* c, double* dst, const double* src, size_t n) {
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), k, c->stream));
+    return DMTS_OK;
+}
+
+int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    cudaStream_t s = c->stream;
+    const double acc = accel_constant();
+    long long before = c->launches;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const bool nonper = !c->periodic;
+    if (c->m[0].present) {
+        double h = dt / n_inner;
+        for (int k = 0; k < n_inner; ++k) {
+            launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
+                             c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, s);
+            enqueue_eval(c, 0, nonper);
+        }
+        enqueue_eval(c, 1, false);
+        launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
+                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, s);
+    } else {
+        launch_vv_pre(c->N, 0.5 * dt * acc, dt, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,
+                      c->d_frame, c->d_q, c->d_flags, s);
+        enqueue_eval(c, 1, nonper);
+        launch_vv_post(c->N, 0.5 * dt * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
+                       c->d_flags, s);
+    }
+    launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, s);
+    launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        c->broken = true;
+        return fail(DMTS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->broken = true;
+        return fail(DMTS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->g_nodes = c->launches - before;
+    c->launches = before;
+    c->g_n_inner = n_inner;
+    c->g_dt = dt;
+    return DMTS_OK;
+}
+
+#define CTX_GUARD(c)                                                                         \
+    do {                                                                                     \
+        if (!(c)) return fail(DMTS_ERR_ARG, "context is NULL");                              \
+        if ((c)->broken) return fail(DMTS_ERR_STATE, "context is unusable after a CUDA error"); \
+        cudaSetDevice((c)->device);                                                          \
+    } while (0)
+
+}  // namespace
+
+namespace dmts {
+ModelOffsets model_offsets(int S, int F, int K, int L) {
+    ModelOffsets o{};
+    int p = 0;
+    o.A = p; p += S * F;
+    for (int l = 0; l < L; ++l) {
+        o.W_in[l] = p; p += F * F;
+        o.W1[l] = p; p += K * F;
+        o.b1[l] = p; p += F;
+        o.W2[l] = p; p += F * F;
+        o.b2[l] = p; p += F;
+        o.U1[l] = p; p += F * F;
+        o.c1[l] = p; p += F;
+        o.U2[l] = p; p += F * F;
+        o.c2[l] = p; p += F;
+    }
+    o.R1 = p; p += F * F;
+    o.d1 = p; p += F;
+    o.R2 = p; p += F;
+    o.d2 = p; p += 1;
+    o.e0 = p; p += S;
+    o.total = p;
+    return o;
+}
+}  // namespace dmts
+
+extern "C" {
+
+const char* dmts_last_error(void) { return g_err.c_str(); }
+
+void dmts_destroy(dmts_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    free_model(c->m[0]);
+    free_model(c->m[1]);
+    dfree(c->d_off); dfree(c->d_species); dfree(c->d_sys); dfree(c->d_box); dfree(c->d_mass);
+    dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
+    dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
+    dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const dmts_system_desc* sys,
+                const char* options, dmts_ctx** out) {
+    g_err.clear();
+    if (!out) return fail(DMTS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_model(big, "big");
+    if (rc) return rc;
+    if (small && (rc = check_model(small, "small"))) return rc;
+    if (big->precision != DMTS_FP32 || (small && small->precision != DMTS_FP32))
+        return fail(DMTS_ERR_ARG, "precision DMTS_BF16_MLP is not available in this build");
+    if (!sys || sys->n_systems < 1 || !sys->atom_offset || !sys->species || !sys->mass || !sys->box)
+        return fail(DMTS_ERR_ARG, "system descriptor incomplete");
+    const int ns = sys->n_systems;
+    if (sys->atom_offset[0] != 0) return fail(DMTS_ERR_ARG, "atom_offset[0] must be 0");
+    for (int s = 0; s < ns; ++s)
+        if (sys->atom_offset[s + 1] < sys->atom_offset[s]) return fail(DMTS_ERR_ARG, "atom_offset must be non-decreasing");
+    const int N = sys->atom_offset[ns];
+    double rc_max = std::max(big->cutoff, small ? small->cutoff : 0.0);
+    int n_per = 0;
+    for (int s = 0; s < ns; ++s) {
+        double L = sys->box[s];
+        if (!isfinite(L)) return fail(DMTS_ERR_ARG, "box[%d] not finite", s);
+        if (L > 0) {
+            ++n_per;
+            if (L < 2.0 * rc_max) return fail(DMTS_ERR_ARG, "box edge %g is below twice the cutoff %g", L, rc_max);
+        } else if (sys->atom_offset[s + 1] - sys->atom_offset[s] > kMaxMolAtoms) {
+            return fail(DMTS_ERR_ARG, "non-periodic system %d has more than %d atoms", s, kMaxMolAtoms);
+        }
+    }
+    if (n_per > 0 && ns != 1) return fail(DMTS_ERR_ARG, "a periodic box must be the only system");
+    int S_min = std::min(big->n_species, small ? small->n_species : 1 << 30);
+    for (int i = 0; i < N; ++i) {
+        if (sys->species[i] < 0 || sys->species[i] >= S_min) return fail(DMTS_ERR_ARG, "species[%d] out of range", i);
+        if (!(sys->mass[i] > 0) || !isfinite(sys->mass[i])) return fail(DMTS_ERR_ARG, "mass[%d] must be > 0", i);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(DMTS_ERR_CUDA, "no CUDA device available");
+    }
+    dmts_ctx* c = new dmts_ctx();
+    cudaGetDevice(&c->device);
+    LaunchScope ls(c);
+    c->N = N;
+    c->n_sys = ns;
+    c->periodic = n_per > 0;
+    c->h_off.assign(sys->atom_offset, sys->atom_offset + ns + 1);
+    c->h_box.assign(sys->box, sys->box + ns);
+    c->rc_max = rc_max;
+    c->cap_factor = json_number(options, "edge_capacity_factor", 1.5);
+    if (!(c->cap_factor > 0.0)) c->cap_factor = 1.5;
+    const double opt_row_cap = json_number(options, "row_capacity", 0.0);
+#define CREATE_TRY(expr)                                                          \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            int code_ = e_ == cudaErrorMemoryAllocation ? DMTS_ERR_OOM : DMTS_ERR_CUDA; \
+            fail(code_, "%s: %s", #expr, cudaGetErrorString(e_));                 \
+            std::string keep_ = g_err;                                            \
+            dmts_destroy(c);                                                      \
+            g_err = keep_;                                                        \
+            return code_;                                                         \
+        }                                                                         \
+    } while (0)
+    CREATE_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    std::vector<int> sys_of(N);
+    for (int s = 0; s < ns; ++s)
+        for (int i = sys->atom_offset[s]; i < sys->atom_offset[s + 1]; ++i) sys_of[i] = s;
+    std::vector<double> inv_m(N);
+    for (int i = 0; i < N; ++i) inv_m[i] = 1.0 / sys->mass[i];
+    CREATE_TRY(dalloc(&c->d_off, ns + 1));
+    CREATE_TRY(dalloc(&c->d_species, N));
+    CREATE_TRY(dalloc(&c->d_sys, N));
+    CREATE_TRY(dalloc(&c->d_box, ns));
+    CREATE_TRY(dalloc(&c->d_mass, N));
+    CREATE_TRY(dalloc(&c->d_inv_m, N));
+    CREATE_TRY(dalloc(&c->d_x, (size_t)3 * N));
+    CREATE_TRY(dalloc(&c->d_v, (size_t)3 * N));
+    CREATE_TRY(dalloc(&c->d_q, N));
+    CREATE_TRY(dalloc(&c->d_frame, ns));
+    CREATE_TRY(dalloc(&c->d_stage, (size_t)6 * N));
+    CREATE_TRY(dalloc(&c->d_ke, N));
+    CREATE_TRY(dalloc(&c->d_ekin, ns));
+    CREATE_TRY(dalloc(&c->d_flags, kFlagCount));
+    CREATE_TRY(dalloc(&c->d_bx, (size_t)3 * N));
+    CREATE_TRY(dalloc(&c->d_bv, (size_t)3 * N));
+    CREATE_TRY(dalloc(&c->d_bfs, (size_t)3 * N));
+    CREATE_TRY(dalloc(&c->d_bfb, (size_t)3 * N));
+    CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
+    CREATE_TRY(cudaMemcpy(c->d_off, sys->atom_offset, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(c->d_species, sys->species, sizeof(int) * std::max(N, 0), cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(c->d_sys, sys_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(c->d_box, sys->box, sizeof(double) * ns, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(c->d_mass, sys->mass, sizeof(double) * N, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(c->d_inv_m, inv_m.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemset(c->d_x, 0, sizeof(double) * 3 * std::max(N, 1)));
+    CREATE_TRY(cudaMemset(c->d_v, 0, sizeof(double) * 3 * std::max(N, 1)));
+    CREATE_TRY(cudaMemset(c->d_flags, 0, sizeof(int) * kFlagCount));
+    if (small) {
+        rc = init_model(c, c->m[0], small);
+        if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
+        c->m[0].apc_fwd = std::min(c->m[0].apc_fwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_fwd));
+        c->m[0].apc_bwd = std::min(c->m[0].apc_bwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_bwd));
+    }
+    rc = init_model(c, c->m[1], big);
+    if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
+    c->m[1].apc_fwd = std::min(c->m[1].apc_fwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_fwd));
+    c->m[1].apc_bwd = std::min(c->m[1].apc_bwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_bwd));
+    for (int w = 0; w < 2; ++w) {
+        if (c->m[w].present && opt_row_cap >= 1.0) {
+            // smaller initial row capacity (exercises the overflow-and-retry path)
+            c->m[w].row_cap = std::min(c->m[w].row_cap, (int)opt_row_cap);
+            free_model_nbr(c->m[w]);
+            CREATE_TRY(alloc_model_nbr(c, c->m[w]));
+        }
+        c->m[w].apc_fwd = std::max(8, c->m[w].apc_fwd);
+        c->m[w].apc_bwd = std::max(8, c->m[w].apc_bwd);
+    }
+    if (c->periodic) {
+        // constant frame; computed once on the device
+        launch_frames(ns, c->d_off, c->d_x, N, c->d_box, rc_max, c->d_frame, c->stream);
+        CREATE_TRY(cudaStreamSynchronize(c->stream));
+    }
+    CREATE_TRY(cudaGetLastError());
+    *out = c;
+    return DMTS_OK;
+}
+
+int dmts_set_state(dmts_ctx* c, const double* x, const double* v, int n_atoms) {
+    CTX_GUARD(c);
+    if (!x) return fail(DMTS_ERR_ARG, "x is NULL");
+    if (n_atoms != c->N) return fail(DMTS_ERR_ARG, "n_atoms %d != %d", n_atoms, c->N);
+    LaunchScope ls(c);
+    size_t n3 = (size_t)3 * c->N;
+    int rc = copy_in(c, c->d_stage, x, n3);
+    if (rc) return rc;
+    if (v && (rc = copy_in(c, c->d_stage + n3, v, n3))) return rc;
+    launch_set_state(c->N, c->d_stage, v ? c->d_stage + n3 : nullptr, c->d_sys, c->d_box, c->d_x, c->d_v,
+                     c->stream);
+    if ((rc = sync_check(c))) return rc;
+    c->state_set = true;
+    c->forces_valid = false;
+    return DMTS_OK;
+}
+
+int dmts_get_state(dmts_ctx* c, double* x, double* v) {
+    CTX_GUARD(c);
+    LaunchScope ls(c);
+    size_t n3 = (size_t)3 * c->N;
+    launch_get_state(c->N, c->d_x, c->d_v, c->d_stage, c->d_stage + n3, c->stream);
+    int rc;
+    if (x && (rc = copy_out(c, x, c->d_stage, n3))) return rc;
+    if (v && (rc = copy_out(c, v, c->d_stage + n3, n3))) return rc;
+    return sync_check(c);
+}
+
+int dmts_forces(dmts_ctx* c, int which, double* f_out, double* energy_out, double* virial_out) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
+    LaunchScope ls(c);
+    Model& m = c->m[which];
+    int rc;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((rc = reset_flags(c))) return rc;
+        enqueue_eval(c, which, true);
+        if (virial_out) launch_virial_sum(c->n_sys, c->d_off, m.vir6, m.W, c->stream);
+        if ((rc = sync_check(c))) return rc;
+        if (!c->h_flags[kFlagOverflow]) break;
+        if ((rc = grow_capacity(c))) return rc;
+        if (attempt == 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
+    }
+    size_t n3 = (size_t)3 * c->N;
+    if (f_out) {
+        launch_forces_out(c->N, m.force, c->d_stage, c->stream);
+        if ((rc = copy_out(c, f_out, c->d_stage, n3))) return rc;
+    }
+    if (energy_out && (rc = copy_out(c, energy_out, m.E, c->n_sys))) return rc;
+    if (virial_out && (rc = copy_out(c, virial_out, m.W, (size_t)9 * c->n_sys))) return rc;
+    return sync_check(c);
+}
+
+int dmts_neighbors(dmts_ctx* c, int which, int* row_ptr, int* col, long long capacity, long long* n_pairs) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
+    if (!row_ptr || !n_pairs || (capacity > 0 && !col)) return fail(DMTS_ERR_ARG, "NULL output");
+    LaunchScope ls(c);
+    Model& m = c->m[which];
+    int rc;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((rc = reset_flags(c))) return rc;
+        enqueue_neighbors(c, which, true);
+        if ((rc = sync_check(c))) return rc;
+        if (!c->h_flags[kFlagOverflow]) break;
+        if ((rc = grow_capacity(c))) return rc;
+        if (attempt == 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
+    }
+    int total = 0;
+    CUDA_TRY(cudaMemcpy(&total, m.row_ptr + c->N, sizeof(int), cudaMemcpyDeviceToHost));
+    *n_pairs = total;
+    cudaMemcpyKind k1 = is_device_ptr(row_ptr) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CUDA_TRY(cudaMemcpy(row_ptr, m.row_ptr, sizeof(int) * (c->N + 1), k1));
+    if (total > capacity) return fail(DMTS_ERR_CAPACITY, "%d pairs exceed capacity %lld", total, capacity);
+    if (total > 0) {
+        cudaMemcpyKind k2 = is_device_ptr(col) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CUDA_TRY(cudaMemcpy(col, m.col, sizeof(int) * total, k2));
+    }
+    return DMTS_OK;
+}
+
+int dmts_set_params(dmts_ctx* c, int which, const double* params, size_t n_params) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    Model& m = c->m[which];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!params || n_params != m.n_params) return fail(DMTS_ERR_ARG, "expected %zu parameters", m.n_params);
+    for (size_t k = 0; k < n_params; ++k)
+        if (!isfinite(params[k])) return fail(DMTS_ERR_ARG, "parameter %zu is not finite", k);
+    int rc = upload_params(c, m, params);
+    if (rc) return rc;
+    c->forces_valid = false;
+    return DMTS_OK;
+}
+
+int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* energies_out) {
+    CTX_GUARD(c);
+    if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
+    if (n_outer < 0) return fail(DMTS_ERR_ARG, "n_outer must be >= 0");
+    if (!(dt > 0) || !isfinite(dt)) return fail(DMTS_ERR_ARG, "dt must be > 0");
+    if (n_inner < 1 || n_inner > 64) return fail(DMTS_ERR_ARG, "n_inner must be in [1, 64]");
+    if (!c->m[0].present && n_inner != 1) return fail(DMTS_ERR_ARG, "without a small model n_inner must be 1");
+    if (n_outer == 0) return DMTS_OK;
+    LaunchScope ls(c);
+    int rc;
+    size_t n3 = (size_t)3 * c->N;
+    if (n_outer > c->ring_len) {
+        dfree(c->d_ring);
+        c->d_ring = nullptr;
+        c->ring_len = 0;
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        cudaError_t e = dalloc(&c->d_ring, (size_t)n_outer * c->n_sys * 3);
+        if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "energies ring: %s", cudaGetErrorString(e));
+        c->ring_len = n_outer;
+    }
+    // state at entry, for the retry after a capacity overflow
+    const bool valid0 = c->forces_valid;
+    CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (valid0) {
+        if (c->m[0].present)
+            CUDA_TRY(cudaMemcpyAsync(c->d_bfs, c->m[0].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_bfb, c->m[1].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = reset_flags(c))) return rc;
+        if (!c->forces_valid) {
+            // Algorithm 1, first_step: both forces at the current positions
+            if (c->m[0].present) enqueue_eval(c, 0, true);
+            enqueue_eval(c, 1, true);
+        }
+        if (!c->graph || c->g_n_inner != n_inner || c->g_dt != dt) {
+            if ((rc = capture_step_graph(c, n_inner, dt))) return rc;
+        }
+        for (int s = 0; s < n_outer; ++s) {
+            CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += c->g_nodes;
+        }
+        if ((rc = sync_check(c))) return rc;
+        if (!c->h_flags[kFlagOverflow]) break;
+        if (attempt >= 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
+        // restore and retry with grown capacity
+        CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        if (valid0) {
+            if (c->m[0].present)
+                CUDA_TRY(cudaMemcpyAsync(c->m[0].force, c->d_bfs, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(c->m[1].force, c->d_bfb, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        }
+        c->forces_valid = valid0;
+        if ((rc = grow_capacity(c))) return rc;
+    }
+    c->forces_valid = true;
+    if (energies_out && (rc = copy_out(c, energies_out, c->d_ring, (size_t)n_outer * c->n_sys * 3))) return rc;
+    if ((rc = sync_check(c))) return rc;
+    if (c->h_flags[kFlagNonfinite]) return fail(DMTS_ERR_NONFINITE, "non-finite position or velocity");
+    return DMTS_OK;
+}
+
+void* dmts_stream(dmts_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
+    if (reps < 1 || !ms_out) return fail(DMTS_ERR_ARG, "reps must be >= 1 and ms_out non-NULL");
+    LaunchScope ls(c);
+    Model& m = c->m[which];
+    const int n_st = 3 + 2 * m.L;
+    if (n_out < n_st) return fail(DMTS_ERR_ARG, "ms_out needs %d entries", n_st);
+    int rc;
+    // one untimed evaluation sizes the capacities
+    if ((rc = reset_flags(c))) return rc;
+    enqueue_eval(c, which, true);
+    if ((rc = sync_check(c))) return rc;
+    if (c->h_flags[kFlagOverflow]) {
+        if ((rc = grow_capacity(c))) return rc;
+        if ((rc = reset_flags(c))) return rc;
+        enqueue_eval(c, which, true);
+        if ((rc = sync_check(c))) return rc;
+    }
+    std::vector<cudaEvent_t> ev(n_st + 1);
+    for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+    std::vector<double> acc(n_st, 0.0);
+    cudaStream_t s = c->stream;
+    for (int r = 0; r < reps; ++r) {
+        int k = 0;
+        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        enqueue_neighbors(c, which, true);
+        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        PotArgs a = pot_args(c, m);
+        a.u_next = m.u[0];
+        launch_embed(a, m.F, s);
+        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        for (int l = 0; l < m.L; ++l) {
+            PotArgs f = a;
+            f.layer = l;
+            f.atoms_per_cta = m.apc_fwd;
+            f.u = m.u[l];
+            f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
+            f.z = m.z[l];
+            f.mbar_out = m.mbar[(m.L - 1) & 1];
+            launch_edge_fwd_f32(f, m.F, m.K, s);
+            CUDA_TRY(cudaEventRecord(ev[k++], s));
+        }
+        std::vector<int> bwd_slot(m.L);
+        for (int l = m.L - 1; l >= 0; --l) {
+            PotArgs b = a;
+            b.layer = l;
+            b.atoms_per_cta = m.apc_bwd;
+            b.u = m.u[l];
+            b.mbar = m.mbar[l & 1];
+            b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
+            b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
+            b.accumulate = (l < m.L - 1) ? 1 : 0;
+            launch_edge_bwd_f32(b, m.F, m.K, s);
+            bwd_slot[l] = k;
+            CUDA_TRY(cudaEventRecord(ev[k++], s));
+        }
+        launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
+        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        CUDA_TRY(cudaEventSynchronize(ev[n_st]));
+        float t;
+        // ev[k] - ev[k-1] is stage k-1 in launch order; map to the documented slots
+        for (int q = 1; q <= n_st; ++q) {
+            CUDA_TRY(cudaEventElapsedTime(&t, ev[q - 1], ev[q]));
+            int slot = q - 1;
+            if (q - 1 >= 2 + m.L && q - 1 < 2 + 2 * m.L) {
+                // backward passes were launched for l = L-1 .. 0
+                int lidx = m.L - 1 - (q - 1 - (2 + m.L));
+                slot = 2 + m.L + lidx;
+            }
+            acc[slot] += t;
+        }
+        (void)bwd_slot;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < n_st; ++k) ms_out[k] = acc[k] / reps;
+    if ((rc = sync_check(c))) return rc;
+    return n_st;
+}
+
+long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

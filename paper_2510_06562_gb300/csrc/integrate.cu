@@ -1,0 +1,244 @@
+// Integrator kernels: the kicks and drifts of Algorithm 1 (thermostat = the
+// identity, NVE) and of velocity Verlet, on the FP64 SoA state, fused with
+// periodic wrapping and the fixed-point quantisation that the next force
+// evaluation reads. One thread per atom; every kernel streams x, v, 1/m and
+// the FP32 forces once.
+#include "internal.cuh"
+
+namespace dmts {
+
+// 1 eV/(Angstrom amu) expressed in Angstrom/fs^2, and its inverse (1 amu
+// (Angstrom/fs)^2 in eV): (1.602176634e-19 J / 1e-10 m) / 1.66053906660e-27 kg
+// = 9.648533216e17 m/s^2.
+constexpr double kAccel = 9.648533215665327e-3;
+constexpr double kKinetic = 103.64269652680505;
+
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+    return L > 0.0 ? x - L * floor(x / L) : x;
+}
+
+__device__ __forceinline__ unsigned int fixed_of(double v, double o, double inv) {
+    long long k = (long long)floor((v - o) * inv);
+    return (unsigned int)(k & 0xffffffffll);
+}
+
+__global__ void k_set_state(int n, const double* __restrict__ xa, const double* __restrict__ va,
+                            const int* __restrict__ sys, const double* __restrict__ box,
+                            double* __restrict__ x, double* __restrict__ v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double L = box[sys[i]];
+    for (int c = 0; c < 3; ++c) {
+        x[(size_t)c * n + i] = wrap_coord(xa[3 * (size_t)i + c], L);
+        v[(size_t)c * n + i] = va ? va[3 * (size_t)i + c] : 0.0;
+    }
+}
+
+void launch_set_state(int n_atoms, const double* x_aos, const double* v_aos, const int* sys_of_atom,
+                      const double* box, double* x, double* v, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_set_state<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, x_aos, v_aos, sys_of_atom, box, x, v);
+    count_launch();
+}
+
+__global__ void k_get_state(int n, const double* __restrict__ x, const double* __restrict__ v,
+                            double* __restrict__ xa, double* __restrict__ va) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; ++c) {
+        if (xa) xa[3 * (size_t)i + c] = x[(size_t)c * n + i];
+        if (va) va[3 * (size_t)i + c] = v[(size_t)c * n + i];
+    }
+}
+
+void launch_get_state(int n_atoms, const double* x, const double* v, double* x_aos, double* v_aos,
+                      cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_get_state<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, x, v, x_aos, v_aos);
+    count_launch();
+}
+
+__global__ void k_forces_out(int n, const float* __restrict__ f, double* __restrict__ fa) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 3; ++c) fa[3 * (size_t)i + c] = (double)f[(size_t)c * n + i];
+}
+
+void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_forces_out<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, f, f_aos);
+    count_launch();
+}
+
+// Algorithm 1, inner step before the small force:
+//   first:  v += (dt/2m) (F - F_small)        (outer half-kick)
+//   else:   v += (h/2m) F_small               (post-kick of the previous inner step)
+//   then    v += (h/2m) F_small; x += (h/2) v; [thermo = identity]; x += (h/2) v
+// with the position wrapped after each half-drift; then quantise x.
+__global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, double half_h,
+                            double* __restrict__ x, double* __restrict__ v,
+                            const double* __restrict__ inv_m, const float* __restrict__ fs,
+                            const float* __restrict__ fb, const int* __restrict__ sys,
+                            const double* __restrict__ box, const Frame* __restrict__ frame,
+                            uint4* __restrict__ q, int* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = sys[i];
+    double L = box[s];
+    Frame fr = frame[s];
+    double im = inv_m[i];
+    unsigned int qc[3];
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        size_t o = (size_t)c * n + i;
+        double vv = v[o];
+        double Fs = (double)fs[o];
+        if (first) vv = vv + c_outer * im * ((double)fb[o] - Fs);
+        else vv = vv + c_inner * im * Fs;
+        vv = vv + c_inner * im * Fs;
+        double xx = wrap_coord(x[o] + half_h * vv, L);
+        xx = wrap_coord(xx + half_h * vv, L);
+        ok = ok && isfinite(vv) && isfinite(xx);
+        v[o] = vv;
+        x[o] = xx;
+        double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
+        qc[c] = fixed_of(xx, oc, fr.inv);
+    }
+    q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+}
+
+void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
+                      double* x, double* v, const double* inv_mass, const float* f_small,
+                      const float* f_big, const int* sys_of_atom, const double* box,
+                      const Frame* frame, uint4* q, int* flags, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
+                                                     inv_mass, f_small, f_big, sys_of_atom, box,
+                                                     frame, q, flags);
+    count_launch();
+}
+
+// After the big force: v += (h/2m) F_small (last inner post-kick), then
+// v += (dt/2m) (F - F_small) (outer half-kick); per-atom kinetic energy.
+__global__ void k_respa_post(int n, double c_outer, double c_inner, double* __restrict__ v,
+                             const double* __restrict__ inv_m, const float* __restrict__ fs,
+                             const float* __restrict__ fb, const double* __restrict__ x,
+                             double* __restrict__ ke, const double* __restrict__ mass,
+                             int* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double im = inv_m[i];
+    double v2 = 0.0;
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        size_t o = (size_t)c * n + i;
+        double Fs = (double)fs[o];
+        double vv = v[o] + c_inner * im * Fs;
+        vv = vv + c_outer * im * ((double)fb[o] - Fs);
+        v[o] = vv;
+        v2 += vv * vv;
+        ok = ok && isfinite(vv) && isfinite(x[o]);
+    }
+    ke[i] = 0.5 * mass[i] * v2 * kKinetic;
+    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+}
+
+void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
+                       const double* inv_mass, const float* f_small, const float* f_big,
+                       const double* x, double* ke, const double* mass, int* flags, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_respa_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
+                                                      f_big, x, ke, mass, flags);
+    count_launch();
+}
+
+// Velocity Verlet: v += (dt/2m) F; x += dt v (wrapped); quantise.
+__global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x,
+                         double* __restrict__ v, const double* __restrict__ inv_m,
+                         const float* __restrict__ f, const int* __restrict__ sys,
+                         const double* __restrict__ box, const Frame* __restrict__ frame,
+                         uint4* __restrict__ q, int* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = sys[i];
+    double L = box[s];
+    Frame fr = frame[s];
+    double im = inv_m[i];
+    unsigned int qc[3];
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        size_t o = (size_t)c * n + i;
+        double vv = v[o] + c_half * im * (double)f[o];
+        double xx = wrap_coord(x[o] + dt * vv, L);
+        ok = ok && isfinite(vv) && isfinite(xx);
+        v[o] = vv;
+        x[o] = xx;
+        double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
+        qc[c] = fixed_of(xx, oc, fr.inv);
+    }
+    q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+}
+
+void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
+                   const double* inv_mass, const float* f, const int* sys_of_atom,
+                   const double* box, const Frame* frame, uint4* q, int* flags, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_vv_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, dt, x, v, inv_mass, f, sys_of_atom,
+                                                  box, frame, q, flags);
+    count_launch();
+}
+
+__global__ void k_vv_post(int n, double c_half, double* __restrict__ v,
+                          const double* __restrict__ inv_m, const float* __restrict__ f,
+                          const double* __restrict__ x, double* __restrict__ ke,
+                          const double* __restrict__ mass, int* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double im = inv_m[i];
+    double v2 = 0.0;
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        size_t o = (size_t)c * n + i;
+        double vv = v[o] + c_half * im * (double)f[o];
+        v[o] = vv;
+        v2 += vv * vv;
+        ok = ok && isfinite(vv) && isfinite(x[o]);
+    }
+    ke[i] = 0.5 * mass[i] * v2 * kKinetic;
+    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+}
+
+void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
+                    const float* f, const double* x, double* ke, const double* mass, int* flags,
+                    cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_vv_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags);
+    count_launch();
+}
+
+__global__ void k_energy_record(int n_sys, const double* __restrict__ ep, const double* __restrict__ ek,
+                                double* __restrict__ ring, int ring_len, int* __restrict__ flags) {
+    int step = flags[kFlagStep];
+    for (int s = threadIdx.x; s < n_sys; s += blockDim.x) {
+        if (step < ring_len) {
+            double* o = ring + ((size_t)step * n_sys + s) * 3;
+            o[0] = ep[s];
+            o[1] = ek[s];
+            o[2] = ep[s] + ek[s];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) flags[kFlagStep] = step + 1;
+}
+
+void launch_energy_record(int n_sys, const double* epot, const double* ekin, double* ring,
+                          int ring_len, int* flags, cudaStream_t s) {
+    k_energy_record<<<1, 256, 0, s>>>(n_sys, epot, ekin, ring, ring_len, flags);
+    count_launch();
+}
+
+double accel_constant() { return kAccel; }
+
+}  // namespace dmts

@@ -1,0 +1,208 @@
+// Internal declarations of the DMTS library (not part of the C ABI).
+//
+// Data layout in device memory (N atoms, F features, E directed pairs):
+//   x, v           FP64 SoA [3][N]         integrator state
+//   inv_mass       FP64 [N]
+//   q              uint4 [N]               fixed-point positions {qx,qy,qz,system}
+//                                          (coordinate = frame origin + q * Q/2^32)
+//   row_ptr        int32 [N+1], col/recv int32 [E]   neighbour CSR (rows ascending)
+//   h, u[l], z[l], gh, mbar   FP32 [N][F]  per-atom features and adjoints
+//   force          FP32 SoA [3][N];  Ei FP64 [N];  vir6 FP32 [N][6]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace dmts {
+
+constexpr int kMaxLayers = 4;
+constexpr int kThreads = 256;          // threads per CTA of the edge kernels
+constexpr int kMaxMolAtoms = 1024;     // atoms per non-periodic system
+
+// Offsets (in floats) of every parameter block inside the flat vector.
+struct ModelOffsets {
+    int A;
+    int W_in[kMaxLayers], W1[kMaxLayers], b1[kMaxLayers], W2[kMaxLayers], b2[kMaxLayers];
+    int U1[kMaxLayers], c1[kMaxLayers], U2[kMaxLayers], c2[kMaxLayers];
+    int R1, d1, R2, d2, e0;
+    int total;
+};
+
+ModelOffsets model_offsets(int S, int F, int K, int L);
+
+// Per-system fixed-point frame: coordinate = origin + q * qscale.
+struct Frame {
+    double ox, oy, oz;   // origin (0 for periodic systems)
+    double inv;          // 2^32 / Q
+    float qscale;        // Q / 2^32 (exact power of two for non-periodic)
+    float pad;
+};
+
+// Device flags word indices.
+enum Flag {
+    kFlagOverflow = 0,     // any neighbour capacity exceeded
+    kFlagNonfinite = 1,    // NaN/Inf in x or v
+    kFlagMaxRow0 = 2,      // max row length seen (small model)
+    kFlagMaxRow1 = 3,      // (big model)
+    kFlagMaxE0 = 4,        // max pair count seen (small)
+    kFlagMaxE1 = 5,        // (big)
+    kFlagStep = 6,         // energies ring index
+    kFlagCount = 8
+};
+
+// Everything the neighbour builder needs for one model.
+struct NbrArgs {
+    int n_atoms;
+    int n_sys;
+    const uint4* q;
+    const double* x;         // SoA [3][N] FP64 (exact band test)
+    const int* atom_offset;  // [n_sys + 1]
+    const double* box;       // [n_sys]
+    const Frame* frame;      // [n_sys]
+    double rc;               // cutoff
+    float rc2_lo, rc2_hi;    // FP32 band around rc^2
+    int nc;                  // cells per dimension (0: all pairs within system)
+    const int* cell_start;   // [nc^3 + 1]
+    const int* cell_atoms;   // [N]
+    int row_cap;
+    long long e_cap;
+    int* nbr_tmp;            // [N][row_cap]
+    int* nbr_cnt;            // [N]
+    int* row_ptr;            // [N + 1]
+    int* col;                // [e_cap]
+    int* recv;               // [e_cap]
+    int* flags;
+    int which;
+};
+
+// Arguments of the potential's kernels (one model, one layer).
+struct PotArgs {
+    const float* P;          // FP32 parameters, flat order
+    ModelOffsets off;
+    int layer;
+    int n_layers;
+    int n_atoms;
+    int atoms_per_cta;
+    const uint4* q;
+    const Frame* frame;
+    const int* species;
+    const int* row_ptr;
+    const int* col;
+    const int* recv;
+    long long e_cap;
+    float rc;
+    float pi_over_rc;
+    float bessel_pref;       // sqrt(2 / rc)
+    float rep_a;             // pair repulsion rep_a exp(-d / rho) fc(d; rep_rc); 0: off
+    float rep_inv_rho;
+    float rep_rc;
+    float rep_pi_over_rc;
+    float* erep;             // [N] per-atom repulsion energy (forward layer 0 writes)
+    // features
+    float* h;
+    const float* u;          // u^l (gathered)
+    float* u_next;           // u^{l+1}
+    float* z;                // z^l
+    const float* z_prev;     // z^{l-1} (backward tail)
+    float* gh;               // dE/dh
+    const float* mbar;       // mbar^l (gathered)
+    float* mbar_out;         // mbar^l (forward tail) or mbar^{l-1} (backward tail)
+    double* Ei;              // [N]
+    float* force;            // SoA [3][N]
+    float* vir6;             // [N][6]
+    int accumulate;          // backward: add to force/vir6 instead of overwrite
+};
+
+// ---------------------------------------------------------------- launchers
+// neighbours.cu
+void launch_frames(int n_sys, const int* atom_offset, const double* x, int n_atoms,
+                   const double* box, double rc_max, Frame* frame, cudaStream_t s);
+void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const Frame* frame,
+                     uint4* q, cudaStream_t s);
+void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
+                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s);
+void launch_neighbors(const NbrArgs& a, cudaStream_t s);
+
+// potential_f32.cu
+void launch_embed(const PotArgs& a, int F, cudaStream_t s);
+void launch_edge_fwd_f32(const PotArgs& a, int F, int K, cudaStream_t s);
+void launch_edge_bwd_f32(const PotArgs& a, int F, int K, cudaStream_t s);
+int max_atoms_per_cta_f32(int F, int K, bool bwd);
+void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
+                       int stride, cudaStream_t s);
+void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, double* out,
+                       cudaStream_t s);
+
+// integrate.cu
+void launch_set_state(int n_atoms, const double* x_aos, const double* v_aos, const int* sys_of_atom,
+                      const double* box, double* x, double* v, cudaStream_t s);
+void launch_get_state(int n_atoms, const double* x, const double* v, double* x_aos, double* v_aos,
+                      cudaStream_t s);
+void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t s);
+// one inner step of Algorithm 1 before the small force: (outer half-kick with
+// F - F_small | post-kick of the previous inner step), pre-kick, two half-drifts
+// with wrapping, then quantisation of the new positions.
+void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
+                      double* x, double* v, const double* inv_mass, const float* f_small,
+                      const float* f_big, const int* sys_of_atom, const double* box,
+                      const Frame* frame, uint4* q, int* flags, cudaStream_t s);
+// after the big force: last inner post-kick and the outer half-kick.
+void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
+                       const double* inv_mass, const float* f_small, const float* f_big,
+                       const double* x, double* ke, const double* mass, int* flags, cudaStream_t s);
+// velocity Verlet: half-kick + drift + wrap + quantise; half-kick + kinetic energy.
+void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
+                   const double* inv_mass, const float* f, const int* sys_of_atom,
+                   const double* box, const Frame* frame, uint4* q, int* flags, cudaStream_t s);
+void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
+                    const float* f, const double* x, double* ke, const double* mass, int* flags,
+                    cudaStream_t s);
+// energies ring: ring[step][sys] = {Epot, Ekin, Epot + Ekin}; step = flags[kFlagStep]++.
+void launch_energy_record(int n_sys, const double* epot, const double* ekin, double* ring,
+                          int ring_len, int* flags, cudaStream_t s);
+
+// Launch accounting (kernel launches issued, graph replays included).
+extern thread_local long long* g_launch_counter;
+inline void count_launch(long long n = 1) {
+    if (g_launch_counter) *g_launch_counter += n;
+}
+
+}  // namespace dmts
+
+// ------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+namespace dmts {
+
+// Pair repulsion phi(d) = a exp(-d/rho) fc(d; r) and its derivative (0 beyond r).
+__device__ __forceinline__ float rep_phi(float d, float a, float inv_rho, float r, float pi_over_r, float* dphi) {
+    if (a == 0.f || d >= r) {
+        if (dphi) *dphi = 0.f;
+        return 0.f;
+    }
+    float s, c;
+    sincospif(d * (pi_over_r * 0.31830988618379067f), &s, &c);
+    float ex = a * expf(-d * inv_rho);
+    float fc = 0.5f * (c + 1.0f);
+    if (dphi) *dphi = ex * (-inv_rho * fc - 0.5f * pi_over_r * s);
+    return ex * fc;
+}
+
+__device__ __forceinline__ float silu_f(float a, float& sig) {
+    sig = 1.0f / (1.0f + __expf(-a));
+    return a * sig;
+}
+
+// Edge vector r_ij = x_j - x_i from fixed-point coordinates: the wrapped
+// 32-bit difference is the minimum image for periodic systems.
+__device__ __forceinline__ float3 edge_vec(uint4 qi, uint4 qj, float qscale) {
+    float3 r;
+    r.x = (float)(int)(qj.x - qi.x) * qscale;
+    r.y = (float)(int)(qj.y - qi.y) * qscale;
+    r.z = (float)(int)(qj.z - qi.z) * qscale;
+    return r;
+}
+
+}  // namespace dmts
+#endif

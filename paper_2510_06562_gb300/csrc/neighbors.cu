@@ -1,0 +1,322 @@
+// Fixed-point positions, cell lists and neighbour CSR.
+//
+// The pair set is {(i, j) : j != i, same system, |r_ij|^2 < rc^2} with r_ij
+// the minimum-image difference evaluated in FP64 with every operation rounded
+// separately. GB300 runs FP64 at a small fraction of its FP32 rate, so each
+// candidate is first classified in FP32 from 32-bit fixed-point coordinates
+// (the wrapped integer difference is the minimum image); only candidates in
+// a thin band around rc^2, where FP32 rounding could flip the decision, are
+// decided by the exact FP64 expression.
+#include "internal.cuh"
+
+namespace dmts {
+
+// ------------------------------------------------------------ frames
+// Non-periodic systems: origin = lower corner of the bounding box, Q = the
+// smallest power of two >= 2 (extent + 2 rc_max + 1) so that every in-cutoff
+// difference stays far below Q/2. Periodic systems: origin 0, Q = L.
+__global__ void k_frames(int n_sys, const int* __restrict__ off, const double* __restrict__ x,
+                         int n, const double* __restrict__ box, double rc_max,
+                         Frame* __restrict__ frame) {
+    int s = blockIdx.x;
+    if (s >= n_sys) return;
+    double L = box[s];
+    if (L > 0.0) {
+        if (threadIdx.x == 0) {
+            Frame f;
+            f.ox = f.oy = f.oz = 0.0;
+            f.inv = 4294967296.0 / L;
+            f.qscale = (float)(L / 4294967296.0);
+            f.pad = 0.f;
+            frame[s] = f;
+        }
+        return;
+    }
+    __shared__ double smin[3][32], smax[3][32];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) {
+        for (int c = 0; c < 3; ++c) {
+            double v = x[(size_t)c * n + i];
+            lo[c] = fmin(lo[c], v);
+            hi[c] = fmax(hi[c], v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmax(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) { smin[c][w] = lo[c]; smax[c][w] = hi[c]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        double ext = 0.0, o3[3];
+        for (int c = 0; c < 3; ++c) {
+            double a = 1e300, b = -1e300;
+            for (int k = 0; k < nw; ++k) { a = fmin(a, smin[c][k]); b = fmax(b, smax[c][k]); }
+            if (off[s + 1] == off[s]) { a = 0.0; b = 0.0; }
+            o3[c] = a;
+            ext = fmax(ext, b - a);
+        }
+        double need = 2.0 * (ext + 2.0 * rc_max + 1.0);
+        double Q = 1.0;
+        while (Q < need) Q *= 2.0;
+        Frame f;
+        f.ox = o3[0]; f.oy = o3[1]; f.oz = o3[2];
+        f.inv = 4294967296.0 / Q;
+        f.qscale = (float)(Q / 4294967296.0);
+        f.pad = 0.f;
+        frame[s] = f;
+    }
+}
+
+void launch_frames(int n_sys, const int* atom_offset, const double* x, int n_atoms,
+                   const double* box, double rc_max, Frame* frame, cudaStream_t s) {
+    k_frames<<<n_sys, 256, 0, s>>>(n_sys, atom_offset, x, n_atoms, box, rc_max, frame);
+    count_launch();
+}
+
+__device__ __forceinline__ unsigned int to_fixed(double v, double o, double inv) {
+    double t = floor((v - o) * inv);
+    long long k = (long long)t;
+    return (unsigned int)(k & 0xffffffffll);
+}
+
+__global__ void k_quantize(int n, const double* __restrict__ x, const int* __restrict__ sys,
+                           const Frame* __restrict__ frame, uint4* __restrict__ q) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = sys[i];
+    Frame f = frame[s];
+    uint4 r;
+    r.x = to_fixed(x[i], f.ox, f.inv);
+    r.y = to_fixed(x[(size_t)n + i], f.oy, f.inv);
+    r.z = to_fixed(x[2 * (size_t)n + i], f.oz, f.inv);
+    r.w = (unsigned int)s;
+    q[i] = r;
+}
+
+void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const Frame* frame,
+                     uint4* q, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_quantize<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, x, sys_of_atom, frame, q);
+    count_launch();
+}
+
+// ------------------------------------------------------------ cell list
+__device__ __forceinline__ int cell_coord(unsigned int qc, int nc) {
+    return (int)(((unsigned long long)qc * (unsigned long long)nc) >> 32);
+}
+
+__global__ void k_cell_count(int n, const uint4* __restrict__ q, int nc, int* __restrict__ count,
+                             int* __restrict__ atom_cell, int* __restrict__ slot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint4 p = q[i];
+    int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
+    atom_cell[i] = c;
+    slot[i] = atomicAdd(&count[c], 1);
+}
+
+// Exclusive scan of count[0..n) into start[0..n], one CTA of 1024 threads.
+__global__ void k_scan_1cta(int n, const int* __restrict__ count, int* __restrict__ start,
+                            long long cap, int* __restrict__ flags, int flag_max) {
+    __shared__ int warp_sums[32];
+    int t = threadIdx.x;
+    int per = (n + blockDim.x - 1) / blockDim.x;
+    int b = t * per, e = min(n, b + per);
+    int local = 0;
+    for (int k = b; k < e; ++k) local += count[k];
+    // block exclusive scan of local
+    int lane = t & 31, w = t >> 5;
+    int v = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int excl = v - local + (w > 0 ? warp_sums[w - 1] : 0);
+    for (int k = b; k < e; ++k) {
+        start[k] = excl;
+        excl += count[k];
+    }
+    if (t == blockDim.x - 1) {
+        start[n] = excl;
+        if (flags) {
+            if ((long long)excl > cap) atomicOr(&flags[kFlagOverflow], 1);
+            atomicMax(&flags[flag_max], excl);
+        }
+    }
+}
+
+__global__ void k_cell_fill(int n, const int* __restrict__ atom_cell, const int* __restrict__ slot,
+                            const int* __restrict__ start, int* __restrict__ cell_atoms) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cell_atoms[start[atom_cell[i]] + slot[i]] = i;
+}
+
+void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
+                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s) {
+    int n_cells = nc * nc * nc;
+    if (n_atoms == 0) return;
+    cudaMemsetAsync(cell_count, 0, sizeof(int) * n_cells, s);
+    int g = (n_atoms + 255) / 256;
+    k_cell_count<<<g, 256, 0, s>>>(n_atoms, q, nc, cell_count, atom_cell, atom_slot);
+    k_scan_1cta<<<1, 1024, 0, s>>>(n_cells, cell_count, cell_start, 0, nullptr, 0);
+    k_cell_fill<<<g, 256, 0, s>>>(n_atoms, atom_cell, atom_slot, cell_start, cell_atoms);
+    count_launch(3);
+}
+
+// ------------------------------------------------------------ neighbours
+// Exact FP64 decision, operation by operation (no contraction).
+__device__ __forceinline__ bool exact_inside(const double* __restrict__ x, int n, int i, int j,
+                                             double L, double rc) {
+    double d[3];
+    for (int c = 0; c < 3; ++c) {
+        double dx = __dsub_rn(x[(size_t)c * n + j], x[(size_t)c * n + i]);
+        if (L > 0.0) {
+            double k = rint(__ddiv_rn(dx, L));
+            dx = __dsub_rn(dx, __dmul_rn(L, k));
+        }
+        d[c] = dx;
+    }
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+    return d2 < __dmul_rn(rc, rc);
+}
+
+constexpr int kNbrWarps = 8;
+
+// One warp per atom i: enumerate candidates (27 cells, or every atom of the
+// system), keep those inside the cutoff, sort the row by j (rank sort) and
+// store it in the fixed-capacity staging array.
+__global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
+    extern __shared__ int smem_i[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* row = smem_i + w * (a.row_cap + 64);
+    int* cstart = row + a.row_cap;       // 27 cell starts
+    int* cpre = cstart + 28;             // 28 prefix sums
+    int i = blockIdx.x * kNbrWarps + w;
+    if (i >= a.n_atoms) return;
+    uint4 qi = a.q[i];
+    int s = (int)qi.w;
+    float qscale = a.frame[s].qscale;
+    double L = a.box[s];
+    int total;
+    int base = 0;
+    if (a.nc > 0) {
+        int nc = a.nc;
+        int cx = cell_coord(qi.x, nc), cy = cell_coord(qi.y, nc), cz = cell_coord(qi.z, nc);
+        int cnt = 0, st = 0;
+        if (lane < 27) {
+            int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            int x2 = (cx + dx + nc) % nc, y2 = (cy + dy + nc) % nc, z2 = (cz + dz + nc) % nc;
+            int c = (z2 * nc + y2) * nc + x2;
+            st = a.cell_start[c];
+            cnt = a.cell_start[c + 1] - st;
+        }
+        int v = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < 27) { cstart[lane] = st; cpre[lane] = v - cnt; }
+        total = __shfl_sync(0xffffffffu, v, 26);
+        if (lane == 0) cpre[27] = total;
+        __syncwarp();
+    } else {
+        base = a.atom_offset[s];
+        total = a.atom_offset[s + 1] - base;
+    }
+    int n_row = 0;
+    const float rc2_lo = a.rc2_lo, rc2_hi = a.rc2_hi;
+    for (int v0 = 0; v0 < total; v0 += 32) {
+        int v = v0 + lane;
+        bool keep = false;
+        int j = -1;
+        if (v < total) {
+            if (a.nc > 0) {
+                int c = 0;
+                while (c < 26 && cpre[c + 1] <= v) ++c;
+                j = a.cell_atoms[cstart[c] + (v - cpre[c])];
+            } else {
+                j = base + v;
+            }
+            if (j != i) {
+                float3 r = edge_vec(qi, a.q[j], qscale);
+                float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                if (d2 < rc2_lo) keep = true;
+                else if (d2 <= rc2_hi) keep = exact_inside(a.x, a.n_atoms, i, j, L, a.rc);
+            }
+        }
+        unsigned int m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            int pos = n_row + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.row_cap) row[pos] = j;
+        }
+        n_row += __popc(m);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        atomicMax(&a.flags[kFlagMaxRow0 + a.which], n_row);
+        if (n_row > a.row_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+    }
+    int n_keep = min(n_row, a.row_cap);
+    int* dst = a.nbr_tmp + (size_t)i * a.row_cap;
+    for (int k = lane; k < n_keep; k += 32) {
+        int jk = row[k];
+        int rank = 0;
+        for (int m2 = 0; m2 < n_keep; ++m2) rank += (row[m2] < jk);
+        dst[rank] = jk;
+    }
+    if (lane == 0) a.nbr_cnt[i] = n_keep;
+}
+
+__global__ void k_nbr_compact(NbrArgs a) {
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= a.n_atoms) return;
+    int i = w;
+    int beg = a.row_ptr[i], cnt = a.nbr_cnt[i];
+    const int* src = a.nbr_tmp + (size_t)i * a.row_cap;
+    for (int k = lane; k < cnt; k += 32) {
+        long long e = (long long)beg + k;
+        if (e < a.e_cap) {
+            a.col[e] = src[k];
+            a.recv[e] = i;
+        }
+    }
+}
+
+void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
+    if (a.n_atoms == 0) {
+        cudaMemsetAsync(a.row_ptr, 0, sizeof(int), s);
+        return;
+    }
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_nbr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_done = true;
+    }
+    int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
+    size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
+    k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
+    k_scan_1cta<<<1, 1024, 0, s>>>(a.n_atoms, a.nbr_cnt, a.row_ptr, a.e_cap, a.flags,
+                                  kFlagMaxE0 + a.which);
+    k_nbr_compact<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);
+    count_launch(3);
+}
+
+}  // namespace dmts

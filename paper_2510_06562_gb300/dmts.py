@@ -1,0 +1,236 @@
+"""ctypes binding of the DMTS C ABI (``include/dmts.h``, ``libdmts.so``).
+
+Argument marshalling only: every step of the force evaluation and of the
+integration runs in the library's CUDA kernels. Arrays may be NumPy arrays
+(host memory) or torch tensors (host or CUDA memory); they are passed to the
+library as raw pointers and the library tells host from device memory
+itself. There is no CPU fallback: if the compiled library is missing, or
+has no GPU to run on, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmts.so")
+
+DMTS_OK = 0
+STATUS = {0: "DMTS_OK", -1: "DMTS_ERR_ARG", -2: "DMTS_ERR_OOM", -3: "DMTS_ERR_CUDA",
+          -4: "DMTS_ERR_CAPACITY", -5: "DMTS_ERR_NONFINITE", -6: "DMTS_ERR_TIMEOUT",
+          -7: "DMTS_ERR_STATE"}
+FP32, BF16_MLP = 0, 1
+SMALL, BIG = 0, 1
+
+EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
+            "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
+            "dmts_launch_count", "dmts_time_stages")
+
+
+class DmtsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("cutoff", C.c_double), ("n_radial", C.c_int), ("n_layers", C.c_int),
+                ("n_feat", C.c_int), ("n_species", C.c_int), ("params", C.POINTER(C.c_double)),
+                ("n_params", C.c_size_t), ("precision", C.c_int), ("rep_a", C.c_double),
+                ("rep_rho", C.c_double), ("rep_cutoff", C.c_double)]
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("n_systems", C.c_int), ("atom_offset", C.POINTER(C.c_int)),
+                ("species", C.POINTER(C.c_int)), ("mass", C.POINTER(C.c_double)),
+                ("box", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load ``libdmts.so`` (built by ``paper_2510_06562_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2510_06562_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.dmts_create.argtypes = [C.POINTER(ModelDesc), C.POINTER(ModelDesc), C.POINTER(SystemDesc),
+                                C.c_char_p, C.POINTER(P)]
+    lib.dmts_create.restype = C.c_int
+    lib.dmts_set_state.argtypes = [P, P, P, C.c_int]
+    lib.dmts_get_state.argtypes = [P, P, P]
+    lib.dmts_forces.argtypes = [P, C.c_int, P, P, P]
+    lib.dmts_respa_step.argtypes = [P, C.c_int, C.c_double, C.c_int, P]
+    lib.dmts_destroy.argtypes = [P]
+    lib.dmts_destroy.restype = None
+    lib.dmts_last_error.argtypes = []
+    lib.dmts_last_error.restype = C.c_char_p
+    lib.dmts_neighbors.argtypes = [P, C.c_int, P, P, C.c_longlong, C.POINTER(C.c_longlong)]
+    lib.dmts_set_params.argtypes = [P, C.c_int, P, C.c_size_t]
+    lib.dmts_stream.argtypes = [P]
+    lib.dmts_stream.restype = C.c_void_p
+    lib.dmts_launch_count.argtypes = [P]
+    lib.dmts_launch_count.restype = C.c_longlong
+    lib.dmts_time_stages.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
+    lib.dmts_time_stages.restype = C.c_int
+    for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
+                 "dmts_neighbors", "dmts_set_params"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != DMTS_OK:
+        raise DmtsError(code, load_library().dmts_last_error().decode())
+
+
+def _ptr(a):
+    """Raw address of a NumPy array or torch tensor (contiguous), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    import torch
+    if a.dtype != torch.float64:
+        raise TypeError("tensors must be float64")
+    return a.contiguous()
+
+
+class Context:
+    """One simulation context: the big model, optionally the small model, and
+    the systems (Algorithm 1's x, v, m and the two force fields)."""
+
+    def __init__(self, system: "_inputs.System", big_arch, big_params, small_arch=None,
+                 small_params=None, precision: int = FP32, options: str | None = None):
+        lib = load_library()
+        self._keep = []
+        self.n_atoms = system.n_atoms
+        self.n_systems = system.n_systems
+
+        def desc(arch, params):
+            p = np.ascontiguousarray(params, dtype=np.float64)
+            self._keep.append(p)
+            return ModelDesc(arch.cutoff, arch.n_radial, arch.n_layers, arch.n_feat, arch.n_species,
+                             p.ctypes.data_as(C.POINTER(C.c_double)), p.size, precision,
+                             getattr(arch, "rep_a", 0.0), getattr(arch, "rep_rho", 1.0),
+                             getattr(arch, "rep_cutoff", 0.0))
+
+        big = desc(big_arch, big_params)
+        small = desc(small_arch, small_params) if small_arch is not None else None
+        off = np.ascontiguousarray(system.atom_offset, dtype=np.int32)
+        sp = np.ascontiguousarray(system.species, dtype=np.int32)
+        ms = np.ascontiguousarray(system.mass, dtype=np.float64)
+        bx = np.ascontiguousarray(system.box, dtype=np.float64)
+        self._keep += [off, sp, ms, bx]
+        sd = SystemDesc(system.n_systems, off.ctypes.data_as(C.POINTER(C.c_int)),
+                        sp.ctypes.data_as(C.POINTER(C.c_int)), ms.ctypes.data_as(C.POINTER(C.c_double)),
+                        bx.ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        _check(lib.dmts_create(C.byref(small) if small is not None else None, C.byref(big), C.byref(sd),
+                               options.encode() if options else None, C.byref(h)))
+        self._h = h
+        self.has_small = small_arch is not None
+
+    # ---------------------------------------------------------------- state
+    def set_state(self, x, v=None):
+        x = _f64(x)
+        v = _f64(v)
+        _check(load_library().dmts_set_state(self._h, _ptr(x), _ptr(v), self.n_atoms))
+
+    def get_state(self, x_out=None, v_out=None):
+        x_out = np.empty((self.n_atoms, 3)) if x_out is None else x_out
+        v_out = np.empty((self.n_atoms, 3)) if v_out is None else v_out
+        _check(load_library().dmts_get_state(self._h, _ptr(x_out), _ptr(v_out)))
+        return x_out, v_out
+
+    # ---------------------------------------------------------------- forces
+    def forces(self, which: int = BIG, virial: bool = False, f_out=None, e_out=None):
+        f_out = np.empty((self.n_atoms, 3)) if f_out is None else f_out
+        e_out = np.empty(self.n_systems) if e_out is None else e_out
+        w_out = np.empty((self.n_systems, 3, 3)) if virial else None
+        _check(load_library().dmts_forces(self._h, which, _ptr(f_out), _ptr(e_out), _ptr(w_out)))
+        return (e_out, f_out, w_out) if virial else (e_out, f_out)
+
+    def neighbors(self, which: int = BIG):
+        row_ptr = np.empty(self.n_atoms + 1, dtype=np.int32)
+        n = C.c_longlong(0)
+        lib = load_library()
+        code = lib.dmts_neighbors(self._h, which, _ptr(row_ptr), None, 0, C.byref(n))
+        if code not in (DMTS_OK, -4):
+            _check(code)
+        col = np.empty(max(1, n.value), dtype=np.int32)
+        _check(lib.dmts_neighbors(self._h, which, _ptr(row_ptr), _ptr(col), col.size, C.byref(n)))
+        return row_ptr, col[:n.value]
+
+    def set_params(self, which: int, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _check(load_library().dmts_set_params(self._h, which, _ptr(p), p.size))
+
+    # ---------------------------------------------------------------- dynamics
+    def respa_step(self, n_outer: int, dt_outer: float, n_inner: int, energies: bool = True, out=None):
+        """n_outer steps of Algorithm 1; returns [n_outer, n_systems, 3]
+        (E_pot big, E_kin, E_tot) or None."""
+        if energies and out is None and n_outer >= 0:
+            out = np.empty((n_outer, self.n_systems, 3))
+        _check(load_library().dmts_respa_step(self._h, n_outer, float(dt_outer), n_inner,
+                                              _ptr(out) if energies else None))
+        return out if energies else None
+
+    def time_stages(self, which: int = BIG, reps: int = 10) -> dict:
+        """Per-stage milliseconds of one force evaluation (CUDA events)."""
+        out = np.zeros(32)
+        n = load_library().dmts_time_stages(self._h, which, reps, _ptr(out), out.size)
+        if n < 0:
+            _check(n)
+        L = (n - 3) // 2
+        names = ["neighbors", "embed"] + [f"edge_fwd_l{l}" for l in range(L)] + \
+                [f"edge_bwd_l{l}" for l in range(L)] + ["energy_sum"]
+        return dict(zip(names, out[:n].tolist()))
+
+    @property
+    def stream(self) -> int:
+        return load_library().dmts_stream(self._h) or 0
+
+    @property
+    def launch_count(self) -> int:
+        return load_library().dmts_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().dmts_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,307 @@
+"""GPU parity of the CUDA path against the FP64 oracle (needs a GB300).
+
+Tolerances (FP32 path): energy |E_gpu - E_ref| / N <= 1e-6 eV/atom and force
+RMSE over all 3N components <= 1e-5 eV/A. Neighbour pair sets are compared
+bit-exactly (the FP64 cutoff decision is reproduced on the GPU).
+"""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import integrate as G
+from oracle import model as M
+from paper_2510_06562_gb300 import dmts as D
+from paper_2510_06562_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-6     # eV / atom
+F_TOL = 1e-5     # eV / A, RMSE
+
+
+def _models(n_species):
+    return (I.small_arch(n_species), I.init_params(I.small_arch(n_species), 2),
+            I.big_arch(n_species), I.init_params(I.big_arch(n_species), 3))
+
+
+def _ctx(s, options=None, small=True):
+    sa, sp, ba, bp = _models(s.n_species)
+    if small:
+        return D.Context(s, ba, bp, sa, sp, options=options)
+    return D.Context(s, ba, bp, options=options)
+
+
+def _pairs(row_ptr, col):
+    n = len(row_ptr) - 1
+    return np.repeat(np.arange(n), np.diff(row_ptr)), col.astype(np.int64)
+
+
+def _rmse(a, b):
+    return float(np.sqrt(np.mean((np.asarray(a) - np.asarray(b)) ** 2)))
+
+
+SYSTEMS = {
+    "water192": lambda: I.water_192(0),
+    "water12288": lambda: I.water_12288(0),
+    "vacuum64": lambda: I.make_vacuum_batch(64, 10, 60, seed=0),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_neighbor_pairs_bit_exact(name):
+    s = SYSTEMS[name]()
+    sa, _, ba, _ = _models(s.n_species)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        for which, arch in ((D.SMALL, sa), (D.BIG, ba)):
+            row_ptr, col = ctx.neighbors(which)
+            gi, gj = _pairs(row_ptr, col)
+            oi, oj = M.pair_list(s.x, s.atom_offset, s.box, arch.cutoff)
+            assert len(gi) == len(oi), (which, len(gi), len(oi))
+            np.testing.assert_array_equal(gi, oi)
+            np.testing.assert_array_equal(gj, oj)
+
+
+def test_neighbor_ties_at_the_cutoff():
+    """Distances exactly equal to rc (representable) are excluded; distances
+    a hair below are included; across the periodic boundary too."""
+    L = 16.0
+    x = np.array([[1.0, 1.0, 1.0], [6.0, 1.0, 1.0], [1.0, 4.5, 1.0], [1.0, 1.0, 5.999999999],
+                  [12.0, 1.0, 1.0], [1.0, 13.5, 1.0], [9.0, 9.0, 9.0], [9.0, 9.0, 12.5],
+                  [9.0, 12.49999999, 9.0]])
+    s = I.System(x=x, species=np.zeros(len(x), np.int32), mass=np.ones(len(x)),
+                 atom_offset=np.array([0, len(x)], np.int32), box=np.array([L]), n_species=2)
+    sa, _, ba, _ = _models(2)
+    with _ctx(s) as ctx:
+        ctx.set_state(x)
+        for which, arch in ((D.SMALL, sa), (D.BIG, ba)):
+            gi, gj = _pairs(*ctx.neighbors(which))
+            oi, oj = M.pair_list(x, s.atom_offset, s.box, arch.cutoff)
+            np.testing.assert_array_equal(gi, oi)
+            np.testing.assert_array_equal(gj, oj)
+        got = set(zip(*_pairs(*ctx.neighbors(D.BIG))))
+        assert (0, 1) not in got and (0, 3) in got and (0, 4) not in got
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_energy_forces_fp32(name):
+    s = SYSTEMS[name]()
+    sa, sp, ba, bp = _models(s.n_species)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            E, F = ctx.forces(which)
+            Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box)
+            err_e = np.abs(E - Er).max() / max(1, s.n_atoms // s.n_systems)
+            err_f = _rmse(F, Fr)
+            print(json.dumps({"system": name, "model": "small" if which == 0 else "big",
+                              "dE_per_atom": float(np.abs(E - Er).sum() / s.n_atoms),
+                              "force_rmse": err_f, "force_rms": float(np.sqrt(np.mean(Fr ** 2)))}))
+            assert np.abs(E - Er).sum() / s.n_atoms <= E_TOL
+            assert err_e <= E_TOL or s.n_systems > 1
+            assert err_f <= F_TOL
+
+
+def test_virial_fp32():
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models(2)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            _, _, W = ctx.forces(which, virial=True)
+            Wr = M.virial(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box)
+            assert np.abs(W - Wr).max() <= 1e-4 * max(1.0, np.abs(Wr).max())
+
+
+def test_state_roundtrip_and_device_pointers():
+    torch = pytest.importorskip("torch")
+    s = I.water_192(0)
+    v = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x, v)
+        x1, v1 = ctx.get_state()
+        np.testing.assert_array_equal(x1, s.x)
+        np.testing.assert_array_equal(v1, v)
+        xd = torch.tensor(s.x, device="cuda")
+        vd = torch.tensor(v, device="cuda")
+        ctx.set_state(xd, vd)
+        xo = torch.empty_like(xd)
+        vo = torch.empty_like(vd)
+        ctx.get_state(xo, vo)
+        np.testing.assert_array_equal(xo.cpu().numpy(), s.x)
+        Fd = torch.empty_like(xd)
+        Ed = torch.empty(1, dtype=torch.float64, device="cuda")
+        ctx.forces(D.BIG, f_out=Fd, e_out=Ed)
+        E, F = ctx.forces(D.BIG)
+        np.testing.assert_array_equal(Fd.cpu().numpy(), F)
+        np.testing.assert_array_equal(Ed.cpu().numpy(), E)
+
+
+def test_wraps_positions_into_box():
+    s = I.water_192(0)
+    x = s.x + np.array([12.42, -12.42, 2 * 12.42])
+    with _ctx(s) as ctx:
+        ctx.set_state(x)
+        xw, _ = ctx.get_state()
+        assert np.all(xw >= 0) and np.all(xw < 12.42)
+        E, F = ctx.forces(D.BIG)
+        ctx.set_state(s.x)
+        E0, F0 = ctx.forces(D.BIG)
+        # x + L - L differs from x by FP64 rounding: agreement at FP32 level
+        assert abs(E[0] - E0[0]) / s.n_atoms < E_TOL
+        assert _rmse(F, F0) < F_TOL
+
+
+# ------------------------------------------------------------------ dynamics
+
+def _oracle_forces(s, arch, par):
+    spec = M.spec_of(arch)
+    return lambda x: M.energy_forces(spec, par, x, s.species, s.atom_offset, s.box)[1]
+
+
+def test_respa_trajectory_water192():
+    """Algorithm 1 (3 fs outer, 3 inner steps) on the 192-atom box.
+
+    After 10 outer steps the positions match the oracle to 1e-4 A: a
+    relative force perturbation of 1e-6 (the FP32 force error scale) moves
+    the oracle's own trajectory by ~1e-6 A there, while a wrong or missing
+    kick moves it by >1e-3 A. The dynamics are chaotic (a 1e-6 perturbation
+    grows to ~4 A by 100 steps), so over 40 outer steps (120 fs, the window in
+    which the random-init models conserve energy) the test compares energy
+    conservation with the oracle's own run, and up to 100 steps it checks that
+    every reported energy is the oracle's at the GPU's own state."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models(2)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    bpa = np.full(s.n_atoms, s.box[0])
+    fs, fb = _oracle_forces(s, sa, sp), _oracle_forces(s, ba, bp)
+    eb = lambda x: M.energy(M.spec_of(ba), bp, x, s.species, s.atom_offset, s.box).numpy()  # noqa: E731
+    xr, vr, Fs, Fb, er = G.respa(s.x, v0, s.mass, fs, fb, 3.0, 3, 10, box_per_atom=bpa, energy_big=eb)
+    _, _, _, _, er2 = G.respa(xr, vr, s.mass, fs, fb, 3.0, 3, 30, box_per_atom=bpa,
+                              F_small=Fs, F=Fb, energy_big=eb)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x, v0)
+        eg = ctx.respa_step(10, 3.0, 3)
+        xg, vg = ctx.get_state()
+        dx = xg - xr
+        dx -= s.box[0] * np.round(dx / s.box[0])
+        assert np.abs(dx).max() < 1e-4, np.abs(dx).max()
+        assert np.abs(vg - vr).max() < 1e-5
+        assert np.abs(eg[:, 0, 0] - er[:, 0, 0]).max() / s.n_atoms < E_TOL
+        eg2 = ctx.respa_step(30, 3.0, 3)
+        etot = np.concatenate([eg[:, 0, 2], eg2[:, 0, 2]])
+        etot_ref = np.concatenate([er[:, 0, 2], er2[:, 0, 2]])
+        span, span_ref = etot.max() - etot.min(), etot_ref.max() - etot_ref.min()
+        print(json.dumps({"etot_span_gpu_120fs": float(span), "etot_span_oracle_120fs": float(span_ref)}))
+        assert span < 3.0 * span_ref + 0.05
+        eg3 = ctx.respa_step(60, 3.0, 3)
+        xg, vg = ctx.get_state()
+        assert abs(eg3[-1, 0, 0] - eb(xg)[0]) / s.n_atoms < E_TOL
+        assert abs(eg3[-1, 0, 1] - G.kinetic_energy(vg, s.mass)[0]) < 1e-9 * eg3[-1, 0, 1]
+
+
+def test_velocity_verlet_matches_oracle():
+    s = I.water_192(0)
+    _, _, ba, bp = _models(2)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    bpa = np.full(s.n_atoms, s.box[0])
+    xr, vr, _ = G.velocity_verlet(s.x, v0, s.mass, _oracle_forces(s, ba, bp), 1.0, 20, box_per_atom=bpa)
+    with _ctx(s, small=False) as ctx:
+        ctx.set_state(s.x, v0)
+        e = ctx.respa_step(20, 1.0, 1)
+        xg, vg = ctx.get_state()
+    dx = xg - xr
+    dx -= s.box[0] * np.round(dx / s.box[0])
+    assert np.abs(dx).max() < 1e-5
+    assert e.shape == (20, 1, 3)
+
+
+def test_one_inner_step_equals_verlet_on_gpu():
+    s = I.water_192(0)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s) as a, _ctx(s, small=False) as b:
+        a.set_state(s.x, v0)
+        b.set_state(s.x, v0)
+        a.respa_step(5, 1.0, 1)
+        b.respa_step(5, 1.0, 1)
+        xa, va = a.get_state()
+        xb, vb = b.get_state()
+    assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-9
+
+
+def test_checkpoint_resume_is_exact():
+    s = I.water_192(0)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s) as a:
+        a.set_state(s.x, v0)
+        a.respa_step(6, 3.0, 3)
+        xm, vm = a.get_state()
+        a.respa_step(6, 3.0, 3)
+        x1, v1 = a.get_state()
+    with _ctx(s) as b:
+        b.set_state(xm, vm)
+        b.respa_step(6, 3.0, 3)
+        x2, v2 = b.get_state()
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(v1, v2)
+
+
+def test_capacity_overflow_retry_gives_identical_results():
+    s = I.water_192(0)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s) as a, _ctx(s, options='{"row_capacity": 4, "edge_capacity_factor": 0.05}') as b:
+        a.set_state(s.x, v0)
+        b.set_state(s.x, v0)
+        Ea, Fa = a.forces(D.BIG)
+        Eb, Fb = b.forces(D.BIG)
+        np.testing.assert_array_equal(Fa, Fb)
+        ea = a.respa_step(4, 3.0, 3)
+        eb = b.respa_step(4, 3.0, 3)
+        np.testing.assert_array_equal(ea, eb)
+        np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+
+
+def test_nonfinite_state_is_reported():
+    s = I.water_192(0)
+    v = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    v[5, 1] = np.nan
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x, v)
+        with pytest.raises(D.DmtsError) as ei:
+            ctx.respa_step(1, 3.0, 3)
+        assert ei.value.code == -5
+        ctx.set_state(s.x, np.zeros_like(v))       # still usable
+        ctx.respa_step(1, 3.0, 3)
+
+
+def test_argument_errors():
+    s = I.water_192(0)
+    with _ctx(s) as ctx:
+        with pytest.raises(D.DmtsError) as ei:
+            ctx.respa_step(1, 3.0, 3)              # no state yet
+        assert ei.value.code == -7
+        ctx.set_state(s.x)
+        for bad in ((1, -1.0, 3), (1, 3.0, 0), (-1, 3.0, 3)):
+            with pytest.raises(D.DmtsError) as ei:
+                ctx.respa_step(*bad)
+            assert ei.value.code == -1
+        with pytest.raises(D.DmtsError):
+            ctx.forces(7)
+    with _ctx(s, small=False) as ctx:
+        ctx.set_state(s.x)
+        with pytest.raises(D.DmtsError):
+            ctx.respa_step(1, 3.0, 3)              # n_inner > 1 needs a small model
+    small_box = I.System(x=s.x, species=s.species, mass=s.mass, atom_offset=s.atom_offset,
+                         box=np.array([9.0]), n_species=2)
+    with pytest.raises(D.DmtsError):
+        _ctx(small_box)
+
+
+def test_launch_count_grows():
+    s = I.water_192(0)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        n0 = ctx.launch_count
+        ctx.respa_step(3, 3.0, 3)
+        assert ctx.launch_count > n0 + 3 * 20

@@ -321,3 +321,25 @@ def test_force_matching_gradient_is_tangent_of_energy_gradient():
     eps = 1e-5
     tang = -(dE_dtheta(s.x + eps * g) - dE_dtheta(s.x - eps * g)) / (2 * eps)
     np.testing.assert_allclose(grad, tang, atol=1e-8 * max(1.0, np.abs(grad).max()))
+
+
+@pytest.mark.parametrize("dist", [0.3, 0.96, 1.7, 2.5])
+def test_pair_repulsion_closed_form(dist):
+    """With every network parameter zero the energy of a dimer is the pair
+    repulsion alone: E = a exp(-d/rho) (cos(pi d/r) + 1)/2 for d < r, else 0
+    (each directed pair contributes half)."""
+    a, rho, r = 50.0, 0.2, 2.0
+    spec = M.Spec(3.0, 2, 1, 2, 1, a, rho, r)
+    n = 2 + (4 * 4 + 2 * 2 + 4 * 2) + 4 + 2 + 2 + 1 + 1
+    par = np.zeros(n)
+    x = np.array([[0.0, 0, 0], [dist, 0, 0]])
+    E, F = M.energy_forces(spec, par, x, np.array([0, 0]), [0, 2], [0.0])
+    ref = a * math.exp(-dist / rho) * 0.5 * (math.cos(math.pi * dist / r) + 1) if dist < r else 0.0
+    assert abs(E[0] - ref) <= 1e-12 * max(1.0, ref)
+    # force on atom 1 along +x is -dE/dd
+    dref = 0.0
+    if dist < r:
+        dref = a * math.exp(-dist / rho) * (-0.5 * (math.cos(math.pi * dist / r) + 1) / rho
+                                            - 0.5 * math.pi / r * math.sin(math.pi * dist / r))
+    assert abs(F[1, 0] + dref) <= 1e-10 * max(1.0, abs(dref))
+    assert abs(F[0, 0] - dref) <= 1e-10 * max(1.0, abs(dref))
