@@ -192,6 +192,42 @@ DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
  * a negative dmts_status. */
 DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out, int n_out);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free neighbour list. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- an MD engine
+ * that owns all device memory through its own pool and hands plug-ins
+ * pre-allocated buffers, or code running under a fixed memory budget or
+ * inside a stream capture, where cudaMalloc would synchronise the device or
+ * invalidate the capture.
+ *
+ * Computes the same pair set and row order as dmts_neighbors for one system
+ * without a context: directed pairs (i, j), j != i, |r_ij|^2 < cutoff^2 in
+ * FP64 (minimum image when box > 0, which must be >= 2 cutoff; box <= 0 for a
+ * non-periodic system), rows ascending by j.
+ *   x        device pointer, n_atoms*3 doubles (atom-major), positions
+ *   row_ptr  device pointer, n_atoms + 1 ints, output
+ *   col      device pointer, capacity ints, output (may be NULL if capacity 0)
+ *   n_pairs  host pointer, receives the number of pairs
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream); the
+ *            call returns after its work on that stream has finished.
+ * Its scratch (fixed-point positions, cell list, counts) is one static device
+ * array of about 0.8 MB, reserved on every GPU that loads the library until
+ * the process exits; no call allocates (no cudaMalloc, no cudaFree, no
+ * allocating library routine). Limits: n_atoms <= DMTS_NOALLOC_MAX_ATOMS and
+ * at most 256 neighbours per atom (else DMTS_ERR_ARG / DMTS_ERR_CAPACITY with
+ * a message in dmts_last_error). DMTS_ERR_CAPACITY is also returned when the
+ * pairs exceed capacity (row_ptr and *n_pairs are still written).
+ * The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array, so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race: issue
+ * them one at a time per device. */
+#define DMTS_NOALLOC_MAX_ATOMS 16384
+
+DMTS_API int dmts_neighbors_noalloc(const double* x, int n_atoms, double box, double cutoff,
+                                    int* row_ptr, int* col, long long capacity,
+                                    long long* n_pairs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

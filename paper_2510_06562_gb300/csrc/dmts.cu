@@ -480,6 +480,8 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
 }  // namespace
 
 namespace dmts {
+void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 ModelOffsets model_offsets(int S, int F, int K, int L) {
     ModelOffsets o{};
     int p = 0;

@@ -163,6 +163,9 @@ void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mas
 void launch_energy_record(int n_sys, const double* epot, const double* ekin, double* ring,
                           int ring_len, int* flags, cudaStream_t s);
 
+// Sets the calling thread's message returned by dmts_last_error().
+void set_error_message(const char* msg);
+
 // Launch accounting (kernel launches issued, graph replays included).
 extern thread_local long long* g_launch_counter;
 inline void count_launch(long long n = 1) {

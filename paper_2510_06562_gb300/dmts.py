@@ -28,7 +28,7 @@ SMALL, BIG = 0, 1
 
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
-            "dmts_launch_count", "dmts_time_stages")
+            "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc")
 
 
 class DmtsError(RuntimeError):
@@ -81,6 +81,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_launch_count.restype = C.c_longlong
     lib.dmts_time_stages.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
     lib.dmts_time_stages.restype = C.c_int
+    lib.dmts_neighbors_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_double, P, P, C.c_longlong,
+                                           C.POINTER(C.c_longlong), P]
+    lib.dmts_neighbors_noalloc.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
