@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmts.so")
-SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu"]
-HEADERS = ["internal.cuh"]
+SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu"]
+HEADERS = ["internal.cuh", "umma.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -266,8 +266,10 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     CUDA_TRY(dalloc(&m.erep, N));
     CUDA_TRY(dalloc(&m.E, c->n_sys));
     CUDA_TRY(dalloc(&m.W, (size_t)9 * c->n_sys));
-    int mf = max_atoms_per_cta_f32(m.F, m.K, false), mb = max_atoms_per_cta_f32(m.F, m.K, true);
-    int want = m.F == 64 ? 16 : 32;
+    const bool tc = m.precision == DMTS_BF16_MLP;
+    int mf = tc ? max_atoms_per_cta_bf16(m.F, false) : max_atoms_per_cta_f32(m.F, m.K, false);
+    int mb = tc ? max_atoms_per_cta_bf16(m.F, true) : max_atoms_per_cta_f32(m.F, m.K, true);
+    int want = tc ? (m.F == 64 ? 8 : 16) : (m.F == 64 ? 16 : 32);
     m.apc_fwd = std::max(8, std::min(want, mf));
     m.apc_bwd = std::max(8, std::min(want, mb));
     return DMTS_OK;
@@ -344,6 +346,16 @@ void enqueue_neighbors(dmts_ctx* c, int which, bool quantize) {
     launch_neighbors(nbr_args(c, m, which), s);
 }
 
+void launch_edge_fwd(dmts_ctx* c, Model& m, const PotArgs& a) {
+    if (m.precision == DMTS_BF16_MLP) launch_edge_fwd_bf16(a, m.F, m.K, c->d_flags + kFlagTimeout, c->stream);
+    else launch_edge_fwd_f32(a, m.F, m.K, c->stream);
+}
+
+void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
+    if (m.precision == DMTS_BF16_MLP) launch_edge_bwd_bf16(a, m.F, m.K, c->d_flags + kFlagTimeout, c->stream);
+    else launch_edge_bwd_f32(a, m.F, m.K, c->stream);
+}
+
 void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
@@ -359,7 +371,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
         f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
         f.z = m.z[l];
         f.mbar_out = m.mbar[(m.L - 1) & 1];
-        launch_edge_fwd_f32(f, m.F, m.K, s);
+        launch_edge_fwd(c, m, f);
     }
     for (int l = m.L - 1; l >= 0; --l) {
         PotArgs b = a;
@@ -370,7 +382,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
         b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
         b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
         b.accumulate = (l < m.L - 1) ? 1 : 0;
-        launch_edge_bwd_f32(b, m.F, m.K, s);
+        launch_edge_bwd(c, m, b);
     }
     launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
 }
@@ -383,6 +395,10 @@ int sync_check(dmts_ctx* c) {
         return fail(DMTS_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
     }
     CUDA_TRY(cudaMemcpy(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost));
+    if (c->h_flags[kFlagTimeout]) {
+        c->broken = true;
+        return fail(DMTS_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    }
     return DMTS_OK;
 }
 
@@ -535,8 +551,6 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     int rc = check_model(big, "big");
     if (rc) return rc;
     if (small && (rc = check_model(small, "small"))) return rc;
-    if (big->precision != DMTS_FP32 || (small && small->precision != DMTS_FP32))
-        return fail(DMTS_ERR_ARG, "precision DMTS_BF16_MLP is not available in this build");
     if (!sys || sys->n_systems < 1 || !sys->atom_offset || !sys->species || !sys->mass || !sys->box)
         return fail(DMTS_ERR_ARG, "system descriptor incomplete");
     const int ns = sys->n_systems;
@@ -862,7 +876,7 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
             f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
             f.z = m.z[l];
             f.mbar_out = m.mbar[(m.L - 1) & 1];
-            launch_edge_fwd_f32(f, m.F, m.K, s);
+            launch_edge_fwd(c, m, f);
             CUDA_TRY(cudaEventRecord(ev[k++], s));
         }
         std::vector<int> bwd_slot(m.L);
@@ -875,7 +889,7 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
             b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
             b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
             b.accumulate = (l < m.L - 1) ? 1 : 0;
-            launch_edge_bwd_f32(b, m.F, m.K, s);
+            launch_edge_bwd(c, m, b);
             bwd_slot[l] = k;
             CUDA_TRY(cudaEventRecord(ev[k++], s));
         }

@@ -49,6 +49,7 @@ enum Flag {
     kFlagMaxE0 = 4,        // max pair count seen (small)
     kFlagMaxE1 = 5,        // (big)
     kFlagStep = 6,         // energies ring index
+    kFlagTimeout = 7,      // a bounded device-side wait gave up
     kFlagCount = 8
 };
 
@@ -130,6 +131,11 @@ void launch_embed(const PotArgs& a, int F, cudaStream_t s);
 void launch_edge_fwd_f32(const PotArgs& a, int F, int K, cudaStream_t s);
 void launch_edge_bwd_f32(const PotArgs& a, int F, int K, cudaStream_t s);
 int max_atoms_per_cta_f32(int F, int K, bool bwd);
+
+// potential_bf16.cu (tensor cores; status receives 1 if a bounded wait gave up)
+void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
+void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
+int max_atoms_per_cta_bf16(int F, bool bwd);
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
                        int stride, cudaStream_t s);
 void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, double* out,

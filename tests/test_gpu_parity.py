@@ -305,3 +305,50 @@ def test_launch_count_grows():
         n0 = ctx.launch_count
         ctx.respa_step(3, 3.0, 3)
         assert ctx.launch_count > n0 + 3 * 20
+
+
+# ------------------------------------------------------------ BF16 tensor-core path
+
+F_TOL_BF16 = 5e-3   # eV / A, RMSE
+
+
+def _ctx_bf16(s, small=True):
+    sa, sp, ba, bp = _models(s.n_species)
+    if small:
+        return D.Context(s, ba, bp, sa, sp, precision=D.BF16_MLP)
+    return D.Context(s, ba, bp, precision=D.BF16_MLP)
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_energy_forces_bf16(name):
+    """Filter MLPs on tensor cores with BF16 operands and FP32 accumulation."""
+    s = SYSTEMS[name]()
+    sa, sp, ba, bp = _models(s.n_species)
+    with _ctx_bf16(s) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            E, F = ctx.forces(which)
+            Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box)
+            err_f = _rmse(F, Fr)
+            de = float(np.abs(E - Er).sum() / s.n_atoms)
+            print(json.dumps({"system": name, "model": "small" if which == 0 else "big", "precision": "bf16",
+                              "dE_per_atom": de, "force_rmse": err_f,
+                              "force_rms": float(np.sqrt(np.mean(Fr ** 2)))}))
+            assert err_f <= F_TOL_BF16
+            # energies: BF16 operands carry ~2^-9 relative rounding per product
+            assert de <= 5e-3
+
+
+def test_bf16_virial_and_dynamics():
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models(2)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx_bf16(s) as ctx:
+        ctx.set_state(s.x, v0)
+        _, _, W = ctx.forces(D.BIG, virial=True)
+        Wr = M.virial(M.spec_of(ba), bp, s.x, s.species, s.atom_offset, s.box)
+        assert np.abs(W - Wr).max() <= 2e-2 * max(1.0, np.abs(Wr).max())
+        e = ctx.respa_step(40, 3.0, 3)
+        span = float(e[:, 0, 2].max() - e[:, 0, 2].min())
+        print(json.dumps({"bf16_etot_span_120fs": span}))
+        assert np.all(np.isfinite(e)) and span < 5.0
