@@ -1,0 +1,35 @@
+"""Repeated force evaluations of one model on a synthetic system, for kernel
+profilers (no timing, no output besides a one-line summary).
+
+    python -m paper_2510_06562_gb300.profile_eval --precision bf16 --which big --evals 3
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+from . import dmts as D
+from . import inputs as I
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--which", default="big", choices=["small", "big"])
+    ap.add_argument("--system", default="water12288", choices=["water192", "water12288"])
+    ap.add_argument("--evals", type=int, default=3)
+    args = ap.parse_args()
+    s = I.water_12288(0) if args.system == "water12288" else I.water_192(0)
+    prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
+    sa, ba = I.small_arch(s.n_species), I.big_arch(s.n_species)
+    with D.Context(s, ba, I.init_params(ba, 3), sa, I.init_params(sa, 2), precision=prec) as ctx:
+        ctx.set_state(s.x)
+        which = D.BIG if args.which == "big" else D.SMALL
+        for _ in range(args.evals):
+            E, F = ctx.forces(which)
+    print(f"{args.system} {args.which} {args.precision}: E={E[0]:.6f} eV, rms F={np.sqrt(np.mean(F ** 2)):.4f} eV/A")
+
+
+if __name__ == "__main__":
+    main()
