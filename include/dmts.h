@@ -186,9 +186,11 @@ DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
  *   [0] quantisation, cell list and neighbour list,
  *   [1] species embedding,
  *   [2 + l] forward edge pass of layer l (l < n_layers),
- *   [2 + n_layers + l] backward edge pass of layer l,
- *   [2 + 2 n_layers] energy reduction.
- * Returns the number of entries written (3 + 2 n_layers, at most n_out) or
+ *   [2 + n_layers + l] per-atom MLPs after it,
+ *   [2 + 2 n_layers + l] backward edge pass of layer l,
+ *   [2 + 3 n_layers + l] per-atom adjoint MLPs after it (0 for l = 0),
+ *   [2 + 4 n_layers] energy reduction.
+ * Returns the number of entries written (3 + 4 n_layers, at most n_out) or
  * a negative dmts_status. */
 DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out, int n_out);
 

@@ -22,6 +22,7 @@
 
 #include "../../include/dmts.h"
 #include "internal.cuh"
+#include "umma.cuh"
 
 namespace dmts {
 thread_local long long* g_launch_counter = nullptr;
@@ -83,6 +84,9 @@ struct Model {
     float* u[kMaxLayers] = {};
     float* z[kMaxLayers] = {};
     float* mbar[2] = {};
+    float* msg = nullptr;              // [N][F] per-atom sums between edge and atom kernels
+    unsigned char* wt = nullptr;       // BF16 filter-weight operand tiles, per layer
+    size_t wt_layer_bytes = 0;
     double *Ei = nullptr, *E = nullptr, *W = nullptr;
     int apc_fwd = 16, apc_bwd = 16;
 };
@@ -191,14 +195,50 @@ void free_model(Model& m) {
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6);
     for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); }
     dfree(m.mbar[0]); dfree(m.mbar[1]);
-    dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep);
+    dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt);
     m = Model();
+}
+
+uint16_t bf16_bits(float x) {
+    // round to nearest even (inputs are finite)
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// BF16 operand tiles of the filter weights of every layer, in the K-major
+// tile layout the tensor-core kernels read: W1^T [F][16] (K zero-padded),
+// W2^T [F][F] and W2 [F][F].
+std::vector<uint16_t> build_weight_tiles(const Model& m, const std::vector<float>& pf) {
+    const int F = m.F, K = m.K;
+    const size_t per = m.wt_layer_bytes / 2;
+    std::vector<uint16_t> t(per * m.L, 0);
+    for (int l = 0; l < m.L; ++l) {
+        uint16_t* b = t.data() + per * l;
+        uint16_t* t1 = b;
+        uint16_t* t2 = b + (size_t)F * 16;
+        uint16_t* t3 = t2 + (size_t)F * F;
+        const float* W1 = pf.data() + m.off.W1[l];
+        const float* W2 = pf.data() + m.off.W2[l];
+        for (int n = 0; n < F; ++n)
+            for (int k = 0; k < 16; ++k)
+                t1[umma::tile_offset(n, k, 16) / 2] = k < K ? bf16_bits(W1[k * F + n]) : 0;
+        for (int n = 0; n < F; ++n)
+            for (int k = 0; k < F; ++k) {
+                t2[umma::tile_offset(n, k, F) / 2] = bf16_bits(W2[k * F + n]);
+                t3[umma::tile_offset(n, k, F) / 2] = bf16_bits(W2[n * F + k]);
+            }
+    }
+    return t;
 }
 
 int upload_params(dmts_ctx* c, Model& m, const double* params) {
     std::vector<float> pf(m.n_params);
     for (size_t k = 0; k < m.n_params; ++k) pf[k] = (float)params[k];
     CUDA_TRY(cudaMemcpyAsync(m.P, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    std::vector<uint16_t> tiles = build_weight_tiles(m, pf);
+    CUDA_TRY(cudaMemcpyAsync(m.wt, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return DMTS_OK;
 }
@@ -215,6 +255,8 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     m.off = model_offsets(m.S, m.F, m.K, m.L);
     const int N = c->N;
     CUDA_TRY(dalloc(&m.P, m.n_params));
+    m.wt_layer_bytes = bf16_weight_tile_bytes(m.F);
+    CUDA_TRY(dalloc(&m.wt, m.wt_layer_bytes * m.L));
     int rc = upload_params(c, m, d->params);
     if (rc) return rc;
     // cells (periodic) and capacity estimates
@@ -259,6 +301,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     }
     CUDA_TRY(dalloc(&m.mbar[0], nf));
     CUDA_TRY(dalloc(&m.mbar[1], nf));
+    CUDA_TRY(dalloc(&m.msg, nf));
     CUDA_TRY(dalloc(&m.force, (size_t)3 * N));
     CUDA_TRY(cudaMemset(m.force, 0, sizeof(float) * 3 * std::max(N, 1)));
     CUDA_TRY(dalloc(&m.vir6, (size_t)6 * N));
@@ -267,9 +310,11 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     CUDA_TRY(dalloc(&m.E, c->n_sys));
     CUDA_TRY(dalloc(&m.W, (size_t)9 * c->n_sys));
     const bool tc = m.precision == DMTS_BF16_MLP;
-    int mf = tc ? max_atoms_per_cta_bf16(m.F, false) : max_atoms_per_cta_f32(m.F, m.K, false);
-    int mb = tc ? max_atoms_per_cta_bf16(m.F, true) : max_atoms_per_cta_f32(m.F, m.K, true);
-    int want = tc ? (m.F == 64 ? 8 : 16) : (m.F == 64 ? 16 : 32);
+    // FP32: atoms per CTA (bounded by shared memory); BF16: atoms per chunk of
+    // the persistent kernels
+    int mf = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, false);
+    int mb = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, true);
+    int want = tc ? 8 : (m.F == 64 ? 16 : 32);
     m.apc_fwd = std::max(8, std::min(want, mf));
     m.apc_bwd = std::max(8, std::min(want, mb));
     return DMTS_OK;
@@ -324,6 +369,9 @@ PotArgs pot_args(dmts_ctx* c, Model& m) {
     a.rep_rc = (float)m.rep_rc;
     a.rep_pi_over_rc = m.rep_rc > 0 ? (float)(M_PI / m.rep_rc) : 0.f;
     a.erep = m.erep;
+    a.msg_out = m.msg;
+    a.wt = m.wt;
+    a.wt_layer_bytes = m.wt_layer_bytes;
     a.h = m.h;
     a.gh = m.gh;
     a.Ei = m.Ei;
@@ -372,6 +420,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
         f.z = m.z[l];
         f.mbar_out = m.mbar[(m.L - 1) & 1];
         launch_edge_fwd(c, m, f);
+        launch_atom_fwd(f, m.F, m.msg, s);
     }
     for (int l = m.L - 1; l >= 0; --l) {
         PotArgs b = a;
@@ -383,6 +432,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
         b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
         b.accumulate = (l < m.L - 1) ? 1 : 0;
         launch_edge_bwd(c, m, b);
+        if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
     }
     launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
 }
@@ -842,7 +892,8 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
     if (reps < 1 || !ms_out) return fail(DMTS_ERR_ARG, "reps must be >= 1 and ms_out non-NULL");
     LaunchScope ls(c);
     Model& m = c->m[which];
-    const int n_st = 3 + 2 * m.L;
+    const int L = m.L;
+    const int n_st = 3 + 4 * L;
     if (n_out < n_st) return fail(DMTS_ERR_ARG, "ms_out needs %d entries", n_st);
     int rc;
     // one untimed evaluation sizes the capacities
@@ -855,32 +906,37 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
         enqueue_eval(c, which, true);
         if ((rc = sync_check(c))) return rc;
     }
-    std::vector<cudaEvent_t> ev(n_st + 1);
+    cudaStream_t s = c->stream;
+    std::vector<cudaEvent_t> ev(2 * n_st);
     for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
     std::vector<double> acc(n_st, 0.0);
-    cudaStream_t s = c->stream;
     for (int r = 0; r < reps; ++r) {
-        int k = 0;
-        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        auto begin = [&](int slot) { cudaEventRecord(ev[2 * slot], s); };
+        auto end = [&](int slot) { cudaEventRecord(ev[2 * slot + 1], s); };
+        begin(0);
         enqueue_neighbors(c, which, true);
-        CUDA_TRY(cudaEventRecord(ev[k++], s));
+        end(0);
         PotArgs a = pot_args(c, m);
         a.u_next = m.u[0];
+        begin(1);
         launch_embed(a, m.F, s);
-        CUDA_TRY(cudaEventRecord(ev[k++], s));
-        for (int l = 0; l < m.L; ++l) {
+        end(1);
+        for (int l = 0; l < L; ++l) {
             PotArgs f = a;
             f.layer = l;
             f.atoms_per_cta = m.apc_fwd;
             f.u = m.u[l];
-            f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
+            f.u_next = (l + 1 < L) ? m.u[l + 1] : nullptr;
             f.z = m.z[l];
-            f.mbar_out = m.mbar[(m.L - 1) & 1];
+            f.mbar_out = m.mbar[(L - 1) & 1];
+            begin(2 + l);
             launch_edge_fwd(c, m, f);
-            CUDA_TRY(cudaEventRecord(ev[k++], s));
+            end(2 + l);
+            begin(2 + L + l);
+            launch_atom_fwd(f, m.F, m.msg, s);
+            end(2 + L + l);
         }
-        std::vector<int> bwd_slot(m.L);
-        for (int l = m.L - 1; l >= 0; --l) {
+        for (int l = L - 1; l >= 0; --l) {
             PotArgs b = a;
             b.layer = l;
             b.atoms_per_cta = m.apc_bwd;
@@ -888,27 +944,23 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
             b.mbar = m.mbar[l & 1];
             b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
             b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
-            b.accumulate = (l < m.L - 1) ? 1 : 0;
+            b.accumulate = (l < L - 1) ? 1 : 0;
+            begin(2 + 2 * L + l);
             launch_edge_bwd(c, m, b);
-            bwd_slot[l] = k;
-            CUDA_TRY(cudaEventRecord(ev[k++], s));
+            end(2 + 2 * L + l);
+            begin(2 + 3 * L + l);
+            if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
+            end(2 + 3 * L + l);
         }
+        begin(2 + 4 * L);
         launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
-        CUDA_TRY(cudaEventRecord(ev[k++], s));
-        CUDA_TRY(cudaEventSynchronize(ev[n_st]));
-        float t;
-        // ev[k] - ev[k-1] is stage k-1 in launch order; map to the documented slots
-        for (int q = 1; q <= n_st; ++q) {
-            CUDA_TRY(cudaEventElapsedTime(&t, ev[q - 1], ev[q]));
-            int slot = q - 1;
-            if (q - 1 >= 2 + m.L && q - 1 < 2 + 2 * m.L) {
-                // backward passes were launched for l = L-1 .. 0
-                int lidx = m.L - 1 - (q - 1 - (2 + m.L));
-                slot = 2 + m.L + lidx;
-            }
-            acc[slot] += t;
+        end(2 + 4 * L);
+        CUDA_TRY(cudaEventSynchronize(ev[2 * n_st - 1]));
+        for (int q = 0; q < n_st; ++q) {
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]));
+            acc[q] += t;
         }
-        (void)bwd_slot;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     for (int k = 0; k < n_st; ++k) ms_out[k] = acc[k] / reps;

@@ -101,6 +101,9 @@ struct PotArgs {
     float rep_rc;
     float rep_pi_over_rc;
     float* erep;             // [N] per-atom repulsion energy (forward layer 0 writes)
+    float* msg_out;          // [N][F] per-atom sums: messages m^l (forward) or ubar^l (backward)
+    const unsigned char* wt; // BF16 operand tiles of the filter weights, per layer
+    size_t wt_layer_bytes;
     // features
     float* h;
     const float* u;          // u^l (gathered)
@@ -135,7 +138,11 @@ int max_atoms_per_cta_f32(int F, int K, bool bwd);
 // potential_bf16.cu (tensor cores; status receives 1 if a bounded wait gave up)
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
-int max_atoms_per_cta_bf16(int F, bool bwd);
+size_t bf16_weight_tile_bytes(int F);
+
+// atom_mlp.cu: per-atom MLPs after the edge passes
+void launch_atom_fwd(const PotArgs& p, int F, const float* msg, cudaStream_t s);
+void launch_atom_bwd(const PotArgs& p, int F, const float* ubar, cudaStream_t s);
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
                        int stride, cudaStream_t s);
 void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, double* out,

@@ -3,9 +3,11 @@
 // shared memory, FP32 accumulators in tensor memory); edge geometry, message
 // sums, forces and the per-atom MLPs stay FP32.
 //
-// A CTA of 4 warps owns a contiguous range of atoms (whole CSR rows) and walks
-// its edges in tiles of 128: one edge per thread and per TMEM lane, so after
-// each MMA a thread loads its own edge's full feature row from TMEM.
+// A persistent CTA of 4 warps takes chunks of atoms (whole CSR rows) in turn
+// and walks each chunk's edges in tiles of 128: one edge per thread and per
+// TMEM lane, so after each MMA a thread loads its own edge's feature row from
+// TMEM. The per-atom sums (messages, or the adjoint ubar, forces and virial)
+// go to global memory; the per-atom MLPs run in their own kernels.
 //   forward, per tile:  A1 = basis (128 x 16)           D1 = A1 W1        (hidden pre-activation)
 //                       A2 = SiLU(D1 + b1) (128 x F)    D2 = A2 W2        (filter, w = fc (D2 + b2))
 //   backward, per tile: D1 = A1 W1, D4 = A1' W1 (basis derivative), D2 = SiLU(D1 + b1) W2,
@@ -14,6 +16,8 @@
 // The MMAs are issued by one thread; completion is signalled through an
 // mbarrier (bounded waits: a wait that gives up sets the timeout flag and the
 // kernel finishes without further MMAs, freeing its tensor memory).
+#include <algorithm>
+
 #include "internal.cuh"
 #include "umma.cuh"
 
@@ -33,6 +37,37 @@ __device__ __forceinline__ float sigmoid_fast(float x) {
     return fmaf(0.5f, t, 0.5f);
 }
 
+// Asynchronous 16-byte global -> shared copies (L1-cached); the issuing
+// thread waits for its own copies with cp_async_wait().
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Edge indices and fixed-point positions of one tile edge, loaded one tile ahead.
+struct EdgeIn {
+    int j, i;
+    uint4 qj, qi;
+};
+
+__device__ __forceinline__ void load_idx(const PotArgs& a, long long e, long long e_end, EdgeIn& x) {
+    if (e < e_end) {
+        x.j = __ldg(a.col + e);
+        x.i = __ldg(a.recv + e);
+    } else {
+        x.j = -1;
+        x.i = -1;
+    }
+}
+
+__device__ __forceinline__ void load_pos(const PotArgs& a, EdgeIn& x) {
+    if (x.j >= 0) {
+        x.qj = __ldg(a.q + x.j);
+        x.qi = __ldg(a.q + x.i);
+    }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -48,12 +83,14 @@ __device__ __forceinline__ void st_row8(unsigned char* tile, int r, int k0, int 
     *reinterpret_cast<uint4*>(tile + tile_offset(r, k0, Kc)) = q;
 }
 
-// Bessel basis (K <= 16 functions, padded with zeros to 16) and its derivative.
-__device__ __forceinline__ void basis16(float d, int K, float pi_over_rc, float pref, float* e, float* de,
-                                        float& fc, float& dfc) {
+// Bessel basis (K <= 16 functions, padded with zeros to 16) and its derivative,
+// from inv_d = 1/d. The angle pi d / rc lies in [0, pi], where the hardware
+// sine/cosine approximations are accurate to ~1e-6 absolute, far below the
+// BF16 rounding the basis undergoes next.
+__device__ __forceinline__ void basis16(float d, float inv_d, int K, float pi_over_rc, float pref, float* e,
+                                        float* de, float& fc, float& dfc) {
     float s1, c1;
-    sincospif(d * (pi_over_rc * 0.31830988618379067f), &s1, &c1);
-    float inv_d = 1.0f / d;
+    __sincosf(d * pi_over_rc, &s1, &c1);
     float sk = s1, skm1 = 0.f, ck = c1, ckm1 = 1.f;
 #pragma unroll
     for (int k = 0; k < kKP; ++k) {
@@ -80,676 +117,619 @@ __device__ void stage_b(unsigned char* tile, const float* __restrict__ W, int N,
     }
 }
 
-// ------------------------------------------------------------ per-atom tails (FP32)
+// ------------------------------------------------------------ segmented sums
+// Rows (receiving atoms) are contiguous runs of edges. Vector sums (F values
+// per edge, in sP[e][f]): every warp sums its 32 edges sequentially, one lane
+// per feature; rows that start and end inside the warp are complete and are
+// written to global memory directly, the warp's first and last row segments
+// go to two slots. Scalar sums (NV values per edge): a segmented shuffle scan
+// per warp, every row segment to a slot. The slots are then merged in edge
+// order by one thread per value, carrying the open row across tiles.
 template <int F>
-__device__ __forceinline__ void stage_w_t(float* Ws, const float* __restrict__ Wg) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < F * F; t += kT) Ws[(t / F) * (F + 1) + (t % F)] = __ldg(Wg + t);
-    __syncthreads();
-}
+struct VecSlots {
+    float v[4][2][F];
+    int row[4][2];
+};
 
 template <int F>
-__device__ __forceinline__ float dot_t(const float* in_row, const float* Ws, int f, bool trans) {
-    float acc = 0.f;
-    if (trans) {
-#pragma unroll 8
-        for (int k = 0; k < F; ++k) acc += in_row[k] * Ws[f * (F + 1) + k];
-    } else {
-#pragma unroll 8
-        for (int k = 0; k < F; ++k) acc += in_row[k] * Ws[k * (F + 1) + f];
+__device__ __forceinline__ void warp_vec_segments(const float* sP, const int* srow, VecSlots<F>* vs,
+                                                  float* __restrict__ out, int a0) {
+    constexpr int PS = F + 4;
+    constexpr int NF = F / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // row of every edge of the warp, segment starts and ends as warp-uniform bit masks
+    const int myrow = srow[32 * w + lane];
+    const int prev = __shfl_up_sync(0xffffffffu, myrow, 1);
+    const int next = __shfl_down_sync(0xffffffffu, myrow, 1);
+    const unsigned int valid = __ballot_sync(0xffffffffu, myrow >= 0);
+    const unsigned int starts = __ballot_sync(0xffffffffu, myrow >= 0 && (lane == 0 || prev != myrow));
+    const unsigned int ends = __ballot_sync(0xffffffffu, myrow >= 0 && (lane == 31 || next != myrow));
+    const int n_valid = __popc(valid);             // valid edges form a prefix
+    const int last_end = n_valid - 1;
+    if (lane == 0) {
+        vs->row[w][0] = -1;
+        vs->row[w][1] = -1;
     }
-    return acc;
+    const float* base = sP + (32 * w) * PS + lane;
+    float acc[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) acc[c] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        if (e < n_valid) {
+            const bool st = (starts >> e) & 1u;
+#pragma unroll
+            for (int c = 0; c < NF; ++c) {
+                const float v = base[e * PS + 32 * c];
+                acc[c] = st ? v : acc[c] + v;
+            }
+            if ((ends >> e) & 1u) {
+                const int r = __shfl_sync(0xffffffffu, myrow, e);
+                const bool first = (starts & ((2u << e) - 1u)) == (starts & 1u) && (starts & 1u);  // segment 0
+                if (first) {
+#pragma unroll
+                    for (int c = 0; c < NF; ++c) vs->v[w][0][lane + 32 * c] = acc[c];
+                    if (lane == 0) vs->row[w][0] = r;
+                } else if (e == last_end) {
+#pragma unroll
+                    for (int c = 0; c < NF; ++c) vs->v[w][1][lane + 32 * c] = acc[c];
+                    if (lane == 0) vs->row[w][1] = r;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NF; ++c) out[(size_t)(a0 + r) * F + lane + 32 * c] = acc[c];
+                }
+            }
+        }
+    }
 }
 
-__device__ __forceinline__ float silu_acc(float a, float& sig) {
-    sig = 1.0f / (1.0f + __expf(-a));
-    return a * sig;
-}
-
-// Shared-memory layout (bytes) of the forward kernel.
+// Merge the slots of one tile (thread f of the first F threads).
 template <int F>
-struct FwdLayout {
-    static constexpr int W1T = 0;                                 // [F][16] bf16
-    static constexpr int W2T = W1T + F * kKP * 2;                 // [F][F] bf16
-    static constexpr int B1 = W2T + F * F * 2;                    // [F] f32
-    static constexpr int B2 = B1 + F * 4;                         // [F] f32
-    static constexpr int A1 = B2 + F * 4;                         // [128][16] bf16
-    static constexpr int A2 = A1 + kT * kKP * 2;                  // [128][F] bf16
-    static constexpr int P = A2 + kT * F * 2;                     // [128][F+4] f32
-    static constexpr int FC = P + kT * (F + 4) * 4;               // [128] f32
-    static constexpr int J = FC + kT * 4;                         // [128] int
-    static constexpr int ROW = J + kT * 4;                        // [128] int
-    static constexpr int REP = ROW + kT * 4;                      // [128] f32
-    static constexpr int MBAR = REP + kT * 4;                     // 8 B (+ taddr)
-    static constexpr int ACC = MBAR + 16;                         // [A][F] f32
-    static int bytes(int A) { return ACC + A * F * 4; }
+__device__ __forceinline__ void merge_vec_slots(const VecSlots<F>* vs, int f, int& cur, float& run,
+                                                float* __restrict__ out, int a0) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            int r = vs->row[w][k];
+            if (r < 0) continue;
+            float v = vs->v[w][k][f];
+            if (r == cur) {
+                run += v;
+            } else {
+                if (cur >= 0) out[(size_t)(a0 + cur) * F + f] = run;
+                cur = r;
+                run = v;
+            }
+        }
+}
+
+template <int NV>
+struct ScalSlots {
+    float v[4][32][NV];
+    int row[4][32];
+    int n[4];
+};
+
+template <int NV>
+__device__ __forceinline__ void warp_scal_segments(float* val, int row, ScalSlots<NV>* ss) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int ro = __shfl_up_sync(0xffffffffu, row, off);
+        bool same = lane >= off && ro == row;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            float y = __shfl_up_sync(0xffffffffu, val[c], off);
+            if (same) val[c] += y;
+        }
+    }
+    int rn = __shfl_down_sync(0xffffffffu, row, 1);
+    bool seg_end = row >= 0 && (lane == 31 || rn != row);
+    unsigned int ends = __ballot_sync(0xffffffffu, seg_end);
+    if (seg_end) {
+        int k = __popc(ends & ((1u << lane) - 1u));
+        ss->row[w][k] = row;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) ss->v[w][k][c] = val[c];
+    }
+    if (lane == 0) ss->n[w] = __popc(ends);
+}
+
+// ------------------------------------------------------------ forward
+template <int F>
+struct FwdSmem {
+    unsigned char w1t[F * kKP * 2];
+    unsigned char w2t[F * F * 2];
+    unsigned char a1[kT * kKP * 2];
+    unsigned char a2[kT * F * 2];
+    float b1[F], b2[F];
+    float P[kT * (F + 4)];
+    int row[kT];
+    VecSlots<F> vs;
+    ScalSlots<1> ss;
+    uint64_t mbar;
+    uint32_t taddr;
 };
 
 template <int F>
 __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* status) {
-    using L = FwdLayout<F>;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float* sb1 = reinterpret_cast<float*>(sm + L::B1);
-    float* sb2 = reinterpret_cast<float*>(sm + L::B2);
-    float* sP = reinterpret_cast<float*>(sm + L::P);
-    float* sfc = reinterpret_cast<float*>(sm + L::FC);
-    int* sj = reinterpret_cast<int*>(sm + L::J);
-    int* srow = reinterpret_cast<int*>(sm + L::ROW);
-    float* srep = reinterpret_cast<float*>(sm + L::REP);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::MBAR);
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(sm + L::MBAR + 8);
-    float* sAcc = reinterpret_cast<float*>(sm + L::ACC);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
     constexpr int PS = F + 4;
-    const int A = a.atoms_per_cta;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
-    const int a0 = blockIdx.x * A;
-    const int a1 = min(a.n_atoms, a0 + A);
-    const int nA = a1 - a0;
-    if (nA <= 0) return;
+    const int A = a.atoms_per_cta;
+    const int n_chunks = (a.n_atoms + A - 1) / A;
+    if ((int)blockIdx.x >= n_chunks) return;
 
-    stage_b(sm + L::W1T, a.P + a.off.W1[l], F, kKP, K, true);
-    stage_b(sm + L::W2T, a.P + a.off.W2[l], F, F, F, true);
-    for (int t = tid; t < F; t += kT) {
-        sb1[t] = __ldg(a.P + a.off.b1[l] + t);
-        sb2[t] = __ldg(a.P + a.off.b2[l] + t);
+    // weights: pre-converted BF16 operand tiles (16-byte copies)
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wt + (size_t)l * a.wt_layer_bytes);
+        uint4* d1 = reinterpret_cast<uint4*>(S.w1t);
+        uint4* d2 = reinterpret_cast<uint4*>(S.w2t);
+        for (int t = tid; t < F * kKP * 2 / 16; t += kT) d1[t] = src[t];
+        src += F * kKP * 2 / 16;
+        for (int t = tid; t < F * F * 2 / 16; t += kT) d2[t] = src[t];
     }
-    for (int t = tid; t < A * F; t += kT) sAcc[t] = 0.f;
-    if (l == 0)
-        for (int t = tid; t < nA; t += kT) a.erep[a0 + t] = 0.f;
-    if (tid == 0) mbar_init(mbar, 1);
-    if (warp == 0) tmem_alloc(taddr_s, 2 * F);
+    for (int t = tid; t < F; t += kT) {
+        S.b1[t] = __ldg(a.P + a.off.b1[l] + t);
+        S.b2[t] = __ldg(a.P + a.off.b2[l] + t);
+    }
+    if (tid == 0) mbar_init(&S.mbar, 1);
+    if (warp == 0) tmem_alloc(&S.taddr, 2 * F);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = *taddr_s;
+    const uint32_t tmem = S.taddr;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const uint32_t idesc = idesc_bf16_f32(128, F);
-    const uint32_t sA1 = smem_u32(sm + L::A1), sA2 = smem_u32(sm + L::A2);
-    const uint32_t sW1T = smem_u32(sm + L::W1T), sW2T = smem_u32(sm + L::W2T);
+    const uint32_t sA1 = smem_u32(S.a1), sA2 = smem_u32(S.a2);
+    const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t);
     uint32_t phase = 0;
     bool ok = true;
 
-    const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
-    const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
-    int cur = -1;
-    float run = 0.f;
-
-    for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
-        // ---- edge geometry and basis: one edge per thread
-        {
-            long long e = t0 + tid;
-            float eb[kKP], fc = 0.f, dfc;
-            if (e < e_end) {
-                int j = a.col[e], i = a.recv[e];
-                uint4 qi = a.q[i], qj = a.q[j];
-                float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
-                float d = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-                basis16(d, K, a.pi_over_rc, a.bessel_pref, eb, nullptr, fc, dfc);
-                sj[tid] = j;
-                srow[tid] = i - a0;
-                srep[tid] = l == 0 ? 0.5f * rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, nullptr) : 0.f;
-            } else {
+    for (int chunk = blockIdx.x; chunk < n_chunks && ok; chunk += gridDim.x) {
+        const int a0 = chunk * A;
+        const int a1 = min(a.n_atoms, a0 + A);
+        // rows without edges must read as zero
+        for (int t = tid; t < (a1 - a0) * F; t += kT) a.msg_out[(size_t)a0 * F + t] = 0.f;
+        if (l == 0)
+            for (int t = tid; t < a1 - a0; t += kT) a.erep[a0 + t] = 0.f;
+        const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
+        const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
+        int cur = -1;          // open row of the merged sums (threads < F: messages, thread F: repulsion)
+        float run = 0.f;
+        EdgeIn nx;
+        load_idx(a, e_beg + tid, e_end, nx);
+        load_pos(a, nx);
+        for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
+            const EdgeIn ex = nx;
+            const bool valid = ex.j >= 0;
+            const int j = valid ? ex.j : a0;
+            const int row = valid ? ex.i - a0 : -1;
+            load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
+            // the message needs u_j: start its copy into this thread's row of P now
+            {
+                const float* uj = a.u + (size_t)j * F;
 #pragma unroll
-                for (int k = 0; k < kKP; ++k) eb[k] = 0.f;
-                sj[tid] = a0;
-                srow[tid] = -1;
-                srep[tid] = 0.f;
+                for (int c = 0; c < F; c += 4) cp_async16(S.P + tid * PS + c, uj + c);
+                cp_async_commit();
             }
-            sfc[tid] = fc;
-            st_row8(sm + L::A1, tid, 0, kKP, eb);
-            st_row8(sm + L::A1, tid, 8, kKP, eb + 8);
-        }
-        fence_proxy_async();
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-        if (tid == 0) {
-            mma_bf16(tmem, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
-            mma_commit(mbar);
-        }
-        ok = mbar_wait(mbar, phase, kWaitIter);
-        phase ^= 1;
-        fence_after_sync();
-        // ---- hidden = SiLU(D1 + b1) -> A2 (bf16)
+            float fc = 0.f, rep = 0.f;
+            {
+                float eb[kKP], dfc;
+                if (valid) {
+                    float3 r = edge_vec(ex.qi, ex.qj, a.frame[ex.qi.w].qscale);
+                    float r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    float inv_d = rsqrtf(r2);
+                    float d = r2 * inv_d;
+                    basis16(d, inv_d, K, a.pi_over_rc, a.bessel_pref, eb, nullptr, fc, dfc);
+                    if (l == 0) rep = 0.5f * rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, nullptr);
+                } else {
 #pragma unroll
-        for (int c = 0; c < F; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + lane_base + c, v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float x = v[q] + sb1[c + q];
-                v[q] = x * sigmoid_fast(x);
+                    for (int k = 0; k < kKP; ++k) eb[k] = 0.f;
+                }
+                S.row[tid] = row;
+                st_row8(S.a1, tid, 0, kKP, eb);
+                st_row8(S.a1, tid, 8, kKP, eb + 8);
             }
-            st_row8(sm + L::A2, tid, c, F, v);
-            st_row8(sm + L::A2, tid, c + 8, F, v + 8);
-        }
-        fence_proxy_async();
-        fence_before_sync();
-        ok = __syncthreads_and(ok);
-        fence_after_sync();
-        if (tid == 0 && ok) {
-#pragma unroll
-            for (int kk = 0; kk < F / 16; ++kk)
-                mma_bf16(tmem + F, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
-                         idesc, kk > 0);
-            mma_commit(mbar);
-        }
-        ok = ok && mbar_wait(mbar, phase, kWaitIter);
-        phase ^= 1;
-        fence_after_sync();
-        // ---- message w * u_j, w = fc (D2 + b2)
-        {
-            const float fc = sfc[tid];
-            const float* uj = a.u + (size_t)sj[tid] * F;
+            fence_proxy_async();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            if (tid == 0) {
+                mma_bf16(tmem, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
+                mma_commit(&S.mbar);
+            }
+            load_pos(a, nx);                               // next tile's positions
+            ok = mbar_wait(&S.mbar, phase, kWaitIter);
+            phase ^= 1;
+            fence_after_sync();
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
                 float v[16];
-                tmem_ld16(tmem + lane_base + F + c, v);
+                tmem_ld16(tmem + lane_base + c, v);
 #pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    float4 u4 = __ldg(reinterpret_cast<const float4*>(uj + c + q));
-                    float4 m;
-                    m.x = fc * (v[q] + sb2[c + q]) * u4.x;
-                    m.y = fc * (v[q + 1] + sb2[c + q + 1]) * u4.y;
-                    m.z = fc * (v[q + 2] + sb2[c + q + 2]) * u4.z;
-                    m.w = fc * (v[q + 3] + sb2[c + q + 3]) * u4.w;
-                    *reinterpret_cast<float4*>(sP + tid * PS + c + q) = m;
+                for (int q = 0; q < 16; ++q) {
+                    float x = v[q] + S.b1[c + q];
+                    v[q] = x * sigmoid_fast(x);
+                }
+                st_row8(S.a2, tid, c, F, v);
+                st_row8(S.a2, tid, c + 8, F, v + 8);
+            }
+            fence_proxy_async();
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk)
+                    mma_bf16(tmem + F, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
+                             idesc, kk > 0);
+                mma_commit(&S.mbar);
+            }
+            ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            phase ^= 1;
+            fence_after_sync();
+            cp_async_wait();                               // this thread's u_j row is in P
+            {
+                float* pr = S.P + tid * PS;
+#pragma unroll
+                for (int c = 0; c < F; c += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + F + c, v);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) {
+                        float4 u4 = *reinterpret_cast<const float4*>(pr + c + q);
+                        *reinterpret_cast<float4*>(pr + c + q) = make_float4(
+                            fc * (v[q] + S.b2[c + q]) * u4.x, fc * (v[q + 1] + S.b2[c + q + 1]) * u4.y,
+                            fc * (v[q + 2] + S.b2[c + q + 2]) * u4.z, fc * (v[q + 3] + S.b2[c + q + 3]) * u4.w);
+                    }
                 }
             }
+            if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss);
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, a0);
+            __syncthreads();
+            if (tid < F) {
+                merge_vec_slots<F>(&S.vs, tid, cur, run, a.msg_out, a0);
+            } else if (tid == F && l == 0) {
+                for (int w = 0; w < 4; ++w)
+                    for (int k = 0; k < S.ss.n[w]; ++k) {
+                        int r = S.ss.row[w][k];
+                        float v = S.ss.v[w][k][0];
+                        if (r == cur) run += v;
+                        else {
+                            if (cur >= 0) a.erep[a0 + cur] = run;
+                            cur = r;
+                            run = v;
+                        }
+                    }
+            }
+            // the slots are rewritten only after two more barriers (next tile)
         }
-        fence_before_sync();
-        ok = __syncthreads_and(ok);
-        // ---- row sums in edge order (thread F: pair repulsion energy)
-        if (tid < F) {
-            for (int e = 0; e < kT; ++e) {
-                int r = srow[e];
-                if (r < 0) break;
-                if (r != cur) {
-                    if (cur >= 0) sAcc[cur * F + tid] = run;
-                    cur = r;
-                    run = 0.f;
-                }
-                run += sP[e * PS + tid];
-            }
-        } else if (tid == F && l == 0) {
-            for (int e = 0; e < kT; ++e) {
-                int r = srow[e];
-                if (r < 0) break;
-                if (r != cur) {
-                    if (cur >= 0) a.erep[a0 + cur] = run;
-                    cur = r;
-                    run = 0.f;
-                }
-                run += srep[e];
-            }
+        if (cur >= 0) {
+            if (tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
+            else if (tid == F && l == 0) a.erep[a0 + cur] = run;
         }
-        __syncthreads();   // the next tile rewrites srow, srep and sP
+        __syncthreads();
     }
-    __syncthreads();
-    if (tid < F && cur >= 0) sAcc[cur * F + tid] = run;
-    if (tid == F && l == 0 && cur >= 0) a.erep[a0 + cur] = run;
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 2 * F);
-    if (!ok) {
-        if (tid == 0) atomicOr(status, 1);
-        return;
-    }
-
-    // ---------------- per-atom tail (FP32), scratch over A2 and P
-    float* tX = reinterpret_cast<float*>(sm + L::A2);
-    float* tY = tX + A * F;
-    float* Ws = tY + A * F;
-    const int f = tid % F, astep = kT / F;
-    const bool last = (l == a.n_layers - 1);
-    const float* P = a.P;
-    for (int t = tid; t < nA * F; t += kT) tX[t] = sAcc[t];
-    stage_w_t<F>(Ws, P + a.off.U1[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float z = dot_t<F>(tX + r * F, Ws, f, false) + __ldg(P + a.off.c1[l] + f);
-        a.z[(size_t)(a0 + r) * F + f] = z;
-        float sg;
-        tY[r * F + f] = silu_acc(z, sg);
-    }
-    stage_w_t<F>(Ws, P + a.off.U2[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        size_t o = (size_t)(a0 + r) * F + f;
-        float hn = a.h[o] + dot_t<F>(tY + r * F, Ws, f, false) + __ldg(P + a.off.c2[l] + f);
-        a.h[o] = hn;
-        tX[r * F + f] = hn;
-    }
-    if (!last) {
-        stage_w_t<F>(Ws, P + a.off.W_in[l + 1]);
-        for (int r = tid / F; r < nA; r += astep)
-            a.u_next[(size_t)(a0 + r) * F + f] = dot_t<F>(tX + r * F, Ws, f, false);
-        return;
-    }
-    stage_w_t<F>(Ws, P + a.off.R1);
-    for (int r = tid / F; r < nA; r += astep) {
-        float qv = dot_t<F>(tX + r * F, Ws, f, false) + __ldg(P + a.off.d1 + f);
-        float sg;
-        float s = silu_acc(qv, sg);
-        float r2 = __ldg(P + a.off.R2 + f);
-        tY[r * F + f] = sg * (1.f + qv * (1.f - sg)) * r2;
-        sAcc[r * F + f] = s * r2;
-    }
-    __syncthreads();
-    for (int r = tid; r < nA; r += kT) {
-        double e = 0.0;
-        for (int k = 0; k < F; ++k) e += (double)sAcc[r * F + k];
-        int i = a0 + r;
-        e += (double)__ldg(P + a.off.d2) + (double)__ldg(P + a.off.e0 + a.species[i]);
-        e += (double)a.erep[i];
-        a.Ei[i] = e;
-    }
-    for (int r = tid / F; r < nA; r += astep) {
-        float g = dot_t<F>(tY + r * F, Ws, f, true);
-        a.gh[(size_t)(a0 + r) * F + f] = g;
-        tX[r * F + f] = g;
-    }
-    stage_w_t<F>(Ws, P + a.off.U2[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float gy = dot_t<F>(tX + r * F, Ws, f, true);
-        float z = a.z[(size_t)(a0 + r) * F + f];
-        float sg;
-        (void)silu_acc(z, sg);
-        tY[r * F + f] = gy * sg * (1.f + z * (1.f - sg));
-    }
-    stage_w_t<F>(Ws, P + a.off.U1[l]);
-    for (int r = tid / F; r < nA; r += astep)
-        a.mbar_out[(size_t)(a0 + r) * F + f] = dot_t<F>(tY + r * F, Ws, f, true);
+    if (!ok && tid == 0) atomicOr(status, 1);
 }
 
 // ------------------------------------------------------------ backward
 template <int F>
-struct BwdLayout {
-    static constexpr int W1T = 0;                                 // [F][16] bf16, B[n][k] = W1[k][n]
-    static constexpr int W2T = W1T + F * kKP * 2;                 // [F][F] bf16, B[n][k] = W2[k][n]
-    static constexpr int W2N = W2T + F * F * 2;                   // [F][F] bf16, B[n][k] = W2[n][k]
-    static constexpr int B1 = W2N + F * F * 2;                    // [F] f32
-    static constexpr int B2 = B1 + F * 4;                         // [F] f32
-    static constexpr int A1 = B2 + F * 4;                         // [128][16] bf16 basis
-    static constexpr int A4 = A1 + kT * kKP * 2;                  // [128][16] bf16 basis derivative
-    static constexpr int A2 = A4 + kT * kKP * 2;                  // [128][F] bf16: SiLU hidden, then g
-    static constexpr int P = A2 + kT * F * 2;                     // [128][F+4] f32 ubar messages
-    static constexpr int J = P + kT * (F + 4) * 4;                // [128] int
-    static constexpr int ROW = J + kT * 4;                        // [128] int
-    static constexpr int SLOT = ROW + kT * 4;                     // [4][32][12] f32 warp partials
-    static constexpr int NSLOT = SLOT + 4 * 32 * 12 * 4;          // [4] int
-    static constexpr int MBAR = NSLOT + 16;                       // mbar + taddr
-    static constexpr int ACC = MBAR + 16;                         // [A][F] ubar
-    static int bytes(int A) { return ACC + A * F * 4 + A * 4 * 4 + A * 8 * 4; }
+struct BwdSmem {
+    unsigned char w1t[F * kKP * 2];     // B[n][k] = W1[k][n]
+    unsigned char w2t[F * F * 2];       // B[n][k] = W2[k][n]
+    unsigned char w2n[F * F * 2];       // B[n][k] = W2[n][k]
+    unsigned char a1[kT * kKP * 2];     // basis
+    unsigned char a4[kT * kKP * 2];     // basis derivative
+    unsigned char a2[kT * F * 2];       // SiLU hidden, then g
+    float b1[F], b2[F];
+    float P[kT * (F + 4)];              // ubar messages
+    int row[kT];
+    VecSlots<F> vs;
+    ScalSlots<9> ss;
+    uint64_t mbar;
+    uint32_t taddr;
 };
 
 template <int F>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
-    using L = BwdLayout<F>;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float* sb1 = reinterpret_cast<float*>(sm + L::B1);
-    float* sb2 = reinterpret_cast<float*>(sm + L::B2);
-    float* sP = reinterpret_cast<float*>(sm + L::P);
-    int* sj = reinterpret_cast<int*>(sm + L::J);
-    int* srow = reinterpret_cast<int*>(sm + L::ROW);
-    float* slot = reinterpret_cast<float*>(sm + L::SLOT);
-    int* nslot = reinterpret_cast<int*>(sm + L::NSLOT);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::MBAR);
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(sm + L::MBAR + 8);
-    const int A = a.atoms_per_cta;
-    float* sAcc = reinterpret_cast<float*>(sm + L::ACC);
-    float* sF = sAcc + A * F;      // [A][4]
-    float* sV = sF + A * 4;        // [A][8]
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    BwdSmem<F>& S = *reinterpret_cast<BwdSmem<F>*>(smraw);
     constexpr int PS = F + 4;
     constexpr int TCOLS = 4 * F;   // D1 | D4 | D2 | D3
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
-    const int a0 = blockIdx.x * A;
-    const int a1 = min(a.n_atoms, a0 + A);
-    const int nA = a1 - a0;
-    if (nA <= 0) return;
+    const int A = a.atoms_per_cta;
+    const int n_chunks = (a.n_atoms + A - 1) / A;
+    if ((int)blockIdx.x >= n_chunks) return;
     const bool need_ubar = (l > 0);
 
-    stage_b(sm + L::W1T, a.P + a.off.W1[l], F, kKP, K, true);
-    stage_b(sm + L::W2T, a.P + a.off.W2[l], F, F, F, true);
-    stage_b(sm + L::W2N, a.P + a.off.W2[l], F, F, F, false);
-    for (int t = tid; t < F; t += kT) {
-        sb1[t] = __ldg(a.P + a.off.b1[l] + t);
-        sb2[t] = __ldg(a.P + a.off.b2[l] + t);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wt + (size_t)l * a.wt_layer_bytes);
+        uint4* d1 = reinterpret_cast<uint4*>(S.w1t);
+        uint4* d2 = reinterpret_cast<uint4*>(S.w2t);
+        uint4* d3 = reinterpret_cast<uint4*>(S.w2n);
+        for (int t = tid; t < F * kKP * 2 / 16; t += kT) d1[t] = src[t];
+        src += F * kKP * 2 / 16;
+        for (int t = tid; t < F * F * 2 / 16; t += kT) d2[t] = src[t];
+        src += F * F * 2 / 16;
+        for (int t = tid; t < F * F * 2 / 16; t += kT) d3[t] = src[t];
     }
-    for (int t = tid; t < A * F; t += kT) sAcc[t] = 0.f;
-    for (int t = tid; t < A * 12; t += kT) sF[t] = 0.f;
-    if (tid == 0) mbar_init(mbar, 1);
-    if (warp == 0) tmem_alloc(taddr_s, TCOLS);
+    for (int t = tid; t < F; t += kT) {
+        S.b1[t] = __ldg(a.P + a.off.b1[l] + t);
+        S.b2[t] = __ldg(a.P + a.off.b2[l] + t);
+    }
+    if (tid == 0) mbar_init(&S.mbar, 1);
+    if (warp == 0) tmem_alloc(&S.taddr, TCOLS);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = *taddr_s;
+    const uint32_t tmem = S.taddr;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const uint32_t tD1 = tmem, tD4 = tmem + F, tD2 = tmem + 2 * F, tD3 = tmem + 3 * F;
     const uint32_t idesc = idesc_bf16_f32(128, F);
-    const uint32_t sA1 = smem_u32(sm + L::A1), sA4 = smem_u32(sm + L::A4), sA2 = smem_u32(sm + L::A2);
-    const uint32_t sW1T = smem_u32(sm + L::W1T), sW2T = smem_u32(sm + L::W2T), sW2N = smem_u32(sm + L::W2N);
+    const uint32_t sA1 = smem_u32(S.a1), sA4 = smem_u32(S.a4), sA2 = smem_u32(S.a2);
+    const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t), sW2N = smem_u32(S.w2n);
     uint32_t phase = 0;
     bool ok = true;
 
-    const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
-    const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
-    int cur = -1;          // running row of the ubar sums (threads < F) and force sums (threads F..F+8)
-    float run = 0.f;
-
-    for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
-        long long e = t0 + tid;
-        const bool valid = e < e_end;
-        int j = a0, row = -1;
-        float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
-        {
-            float eb[kKP], db[kKP];
-            if (valid) {
-                j = a.col[e];
-                int i = a.recv[e];
-                row = i - a0;
-                uint4 qi = a.q[i], qj = a.q[j];
-                float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
-                d = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-                float inv = 1.0f / d;
-                rx = r.x * inv; ry = r.y * inv; rz = r.z * inv;
-                basis16(d, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
-            } else {
-#pragma unroll
-                for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
+    for (int chunk = blockIdx.x; chunk < n_chunks && ok; chunk += gridDim.x) {
+        const int a0 = chunk * A;
+        const int a1 = min(a.n_atoms, a0 + A);
+        const int nA = a1 - a0;
+        if (need_ubar)
+            for (int t = tid; t < nA * F; t += kT) a.msg_out[(size_t)a0 * F + t] = 0.f;
+        const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
+        const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
+        int cur = -1;      // threads < F: ubar row; threads F..F+8: force / virial row
+        float run = 0.f;
+        // per-atom force and virial start at zero (or keep the later layer's value)
+        if (!a.accumulate)
+            for (int t = tid; t < nA * 9; t += kT) {
+                int r = t / 9, c = t % 9;
+                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + r] = 0.f;
+                else a.vir6[(size_t)(a0 + r) * 6 + c - 3] = 0.f;
             }
-            sj[tid] = j;
-            srow[tid] = row;
-            st_row8(sm + L::A1, tid, 0, kKP, eb);
-            st_row8(sm + L::A1, tid, 8, kKP, eb + 8);
-            st_row8(sm + L::A4, tid, 0, kKP, db);
-            st_row8(sm + L::A4, tid, 8, kKP, db + 8);
-        }
-        fence_proxy_async();
-        fence_before_sync();
         __syncthreads();
-        fence_after_sync();
-        if (tid == 0) {
-            mma_bf16(tD1, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
-            mma_bf16(tD4, make_desc(sA4, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
-            mma_commit(mbar);
-        }
-        ok = mbar_wait(mbar, phase, kWaitIter);
-        phase ^= 1;
-        fence_after_sync();
-        // ---- A2 = SiLU(D1 + b1)
+        EdgeIn nx;
+        load_idx(a, e_beg + tid, e_end, nx);
+        load_pos(a, nx);
+        for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
+            const EdgeIn ex = nx;
+            const bool valid = ex.j >= 0;
+            const int j = valid ? ex.j : a0;
+            const int row = valid ? ex.i - a0 : -1;
+            load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
+            // mbar_j is needed by g and the ubar message: copy it into this thread's row of P
+            {
+                const float* mj = a.mbar + (size_t)j * F;
 #pragma unroll
-        for (int c = 0; c < F; c += 16) {
-            float v[16];
-            tmem_ld16(tD1 + lane_base + c, v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float x = v[q] + sb1[c + q];
-                v[q] = x * sigmoid_fast(x);
+                for (int c = 0; c < F; c += 4) cp_async16(S.P + tid * PS + c, mj + c);
+                cp_async_commit();
             }
-            st_row8(sm + L::A2, tid, c, F, v);
-            st_row8(sm + L::A2, tid, c + 8, F, v + 8);
-        }
-        fence_proxy_async();
-        fence_before_sync();
-        ok = __syncthreads_and(ok);
-        fence_after_sync();
-        if (tid == 0 && ok) {
+            float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
+            {
+                float eb[kKP], db[kKP];
+                if (valid) {
+                    const uint4 qi = ex.qi, qj = ex.qj;
+                    float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
+                    float r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    float inv = rsqrtf(r2);
+                    d = r2 * inv;
+                    rx = r.x * inv; ry = r.y * inv; rz = r.z * inv;
+                    basis16(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+                } else {
 #pragma unroll
-            for (int kk = 0; kk < F / 16; ++kk)
-                mma_bf16(tD2, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
-                         idesc, kk > 0);
-            mma_commit(mbar);
-        }
-        ok = ok && mbar_wait(mbar, phase, kWaitIter);
-        phase ^= 1;
-        fence_after_sync();
-        // ---- phi = D2 + b2; g = mbar_i u_j + mbar_j u_i -> A2 (bf16); g . phi; ubar message
-        float gphi = 0.f;
-        {
-            const int i = row < 0 ? a0 : a0 + row;
-            const float* uj = a.u + (size_t)j * F;
-            const float* mj = a.mbar + (size_t)j * F;
-            const float* ui = a.u + (size_t)i * F;
-            const float* mi = a.mbar + (size_t)i * F;
+                    for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
+                }
+                S.row[tid] = row;
+                st_row8(S.a1, tid, 0, kKP, eb);
+                st_row8(S.a1, tid, 8, kKP, eb + 8);
+                st_row8(S.a4, tid, 0, kKP, db);
+                st_row8(S.a4, tid, 8, kKP, db + 8);
+            }
+            fence_proxy_async();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            if (tid == 0) {
+                mma_bf16(tD1, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
+                mma_bf16(tD4, make_desc(sA4, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
+                mma_commit(&S.mbar);
+            }
+            load_pos(a, nx);                               // next tile's positions
+            ok = mbar_wait(&S.mbar, phase, kWaitIter);
+            phase ^= 1;
+            fence_after_sync();
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
-                float v[16], g[16];
-                tmem_ld16(tD2 + lane_base + c, v);
+                float v[16];
+                tmem_ld16(tD1 + lane_base + c, v);
 #pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    float4 u4 = __ldg(reinterpret_cast<const float4*>(uj + c + q));
-                    float4 m4 = __ldg(reinterpret_cast<const float4*>(mj + c + q));
-                    float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
-                    float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
-                    float ph0 = v[q] + sb2[c + q], ph1 = v[q + 1] + sb2[c + q + 1];
-                    float ph2 = v[q + 2] + sb2[c + q + 2], ph3 = v[q + 3] + sb2[c + q + 3];
-                    g[q] = mi4.x * u4.x + m4.x * ui4.x;
-                    g[q + 1] = mi4.y * u4.y + m4.y * ui4.y;
-                    g[q + 2] = mi4.z * u4.z + m4.z * ui4.z;
-                    g[q + 3] = mi4.w * u4.w + m4.w * ui4.w;
-                    gphi += g[q] * ph0 + g[q + 1] * ph1 + g[q + 2] * ph2 + g[q + 3] * ph3;
-                    if (need_ubar)
-                        *reinterpret_cast<float4*>(sP + tid * PS + c + q) =
+                for (int q = 0; q < 16; ++q) {
+                    float x = v[q] + S.b1[c + q];
+                    v[q] = x * sigmoid_fast(x);
+                }
+                st_row8(S.a2, tid, c, F, v);
+                st_row8(S.a2, tid, c + 8, F, v + 8);
+            }
+            fence_proxy_async();
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk)
+                    mma_bf16(tD2, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
+                             idesc, kk > 0);
+                mma_commit(&S.mbar);
+            }
+            ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            phase ^= 1;
+            fence_after_sync();
+            cp_async_wait();                               // this thread's mbar_j row is in P
+            float gphi = 0.f;
+            {
+                const int i = row < 0 ? a0 : a0 + row;
+                const float* uj = a.u + (size_t)j * F;
+                float* pr = S.P + tid * PS;
+                const float* ui = a.u + (size_t)i * F;
+                const float* mi = a.mbar + (size_t)i * F;
+#pragma unroll
+                for (int c = 0; c < F; c += 16) {
+                    float v[16], g[16];
+                    tmem_ld16(tD2 + lane_base + c, v);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) {
+                        float4 u4 = __ldg(reinterpret_cast<const float4*>(uj + c + q));
+                        float4 m4 = *reinterpret_cast<const float4*>(pr + c + q);
+                        float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
+                        float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
+                        float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
+                        float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
+                        g[q] = mi4.x * u4.x + m4.x * ui4.x;
+                        g[q + 1] = mi4.y * u4.y + m4.y * ui4.y;
+                        g[q + 2] = mi4.z * u4.z + m4.z * ui4.z;
+                        g[q + 3] = mi4.w * u4.w + m4.w * ui4.w;
+                        gphi += g[q] * ph0 + g[q + 1] * ph1 + g[q + 2] * ph2 + g[q + 3] * ph3;
+                        *reinterpret_cast<float4*>(pr + c + q) =
                             make_float4(fc * ph0 * m4.x, fc * ph1 * m4.y, fc * ph2 * m4.z, fc * ph3 * m4.w);
-                }
-                st_row8(sm + L::A2, tid, c, F, g);
-                st_row8(sm + L::A2, tid, c + 8, F, g + 8);
-            }
-        }
-        fence_proxy_async();
-        fence_before_sync();
-        ok = __syncthreads_and(ok);
-        fence_after_sync();
-        if (tid == 0 && ok) {
-#pragma unroll
-            for (int kk = 0; kk < F / 16; ++kk)
-                mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
-                         idesc, kk > 0);
-            mma_commit(mbar);
-        }
-        ok = ok && mbar_wait(mbar, phase, kWaitIter);
-        phase ^= 1;
-        fence_after_sync();
-        // ---- dE/dd = fc' (g . phi) + fc sum_k D3_k SiLU'(a_k) D4_k (+ repulsion on layer 0)
-        float s2 = 0.f;
-#pragma unroll
-        for (int c = 0; c < F; c += 16) {
-            float ab[16], av[16], tv[16];
-            tmem_ld16(tD3 + lane_base + c, ab);
-            tmem_ld16(tD1 + lane_base + c, av);
-            tmem_ld16(tD4 + lane_base + c, tv);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float x = av[q] + sb1[c + q];
-                float sg = sigmoid_fast(x);
-                s2 += ab[q] * (sg * (1.f + x * (1.f - sg))) * tv[q];
-            }
-        }
-        float se = dfc * gphi + fc * s2;
-        if (l == 0 && valid) {
-            float dphi;
-            (void)rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, &dphi);
-            se += dphi;
-        }
-        // ---- force (3) and virial (6) per edge: warp segmented scan, then per-row partials
-        {
-            float val[9];
-            val[0] = se * rx; val[1] = se * ry; val[2] = se * rz;
-            float hv = -0.5f * se * d;
-            val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
-            val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                int ro = __shfl_up_sync(0xffffffffu, row, off);
-                bool same = lane >= off && ro == row;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    float y = __shfl_up_sync(0xffffffffu, val[c], off);
-                    if (same) val[c] += y;
-                }
-            }
-            int rn = __shfl_down_sync(0xffffffffu, row, 1);
-            bool seg_end = row >= 0 && (lane == 31 || rn != row);
-            unsigned int ends = __ballot_sync(0xffffffffu, seg_end);
-            if (seg_end) {
-                int k = __popc(ends & ((1u << lane) - 1u));
-                float* o = slot + (warp * 32 + k) * 12;
-                o[0] = __int_as_float(row);
-#pragma unroll
-                for (int c = 0; c < 9; ++c) o[1 + c] = val[c];
-            }
-            if (lane == 0) nslot[warp] = __popc(ends);
-        }
-        fence_before_sync();
-        ok = __syncthreads_and(ok);
-        // ---- combine in edge order: ubar row sums (threads < F), force/virial (threads F..F+8)
-        if (need_ubar && tid < F) {
-            for (int ee = 0; ee < kT; ++ee) {
-                int r = srow[ee];
-                if (r < 0) break;
-                if (r != cur) {
-                    if (cur >= 0) sAcc[cur * F + tid] = run;
-                    cur = r;
-                    run = 0.f;
-                }
-                run += sP[ee * PS + tid];
-            }
-        } else if (tid >= F && tid < F + 9) {
-            const int c = tid - F;
-            for (int w = 0; w < 4; ++w) {
-                const int ns = nslot[w];
-                for (int k = 0; k < ns; ++k) {
-                    const float* o = slot + (w * 32 + k) * 12;
-                    int r = __float_as_int(o[0]);
-                    if (r != cur) {
-                        if (cur >= 0) {
-                            if (c < 3) sF[cur * 4 + c] = run;
-                            else sV[cur * 8 + c - 3] = run;
-                        }
-                        cur = r;
-                        run = 0.f;
                     }
-                    run += o[1 + c];
+                    st_row8(S.a2, tid, c, F, g);
+                    st_row8(S.a2, tid, c + 8, F, g + 8);
                 }
             }
+            fence_proxy_async();
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk)
+                    mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
+                             idesc, kk > 0);
+                mma_commit(&S.mbar);
+            }
+            ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            phase ^= 1;
+            fence_after_sync();
+            float s2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < F; c += 16) {
+                float ab[16], av[16], tv[16];
+                tmem_ld16(tD3 + lane_base + c, ab);
+                tmem_ld16(tD1 + lane_base + c, av);
+                tmem_ld16(tD4 + lane_base + c, tv);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float x = av[q] + S.b1[c + q];
+                    float sg = sigmoid_fast(x);
+                    s2 += ab[q] * (sg * (1.f + x * (1.f - sg))) * tv[q];
+                }
+            }
+            float se = dfc * gphi + fc * s2;
+            if (l == 0 && valid) {
+                float dphi;
+                (void)rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, &dphi);
+                se += dphi;
+            }
+            {
+                float val[9];
+                val[0] = se * rx; val[1] = se * ry; val[2] = se * rz;
+                float hv = -0.5f * se * d;
+                val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
+                val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
+                warp_scal_segments<9>(val, row, &S.ss);
+            }
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            if (need_ubar) warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, a0);
+            __syncthreads();
+            if (need_ubar && tid < F) {
+                merge_vec_slots<F>(&S.vs, tid, cur, run, a.msg_out, a0);
+            } else if (tid >= F && tid < F + 9) {
+                const int c = tid - F;
+                for (int w = 0; w < 4; ++w)
+                    for (int k = 0; k < S.ss.n[w]; ++k) {
+                        int r = S.ss.row[w][k];
+                        float v = S.ss.v[w][k][c];
+                        if (r == cur) run += v;
+                        else {
+                            if (cur >= 0) {
+                                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + cur] += run;
+                                else a.vir6[(size_t)(a0 + cur) * 6 + c - 3] += run;
+                            }
+                            cur = r;
+                            run = v;
+                        }
+                    }
+            }
         }
-        __syncthreads();   // the next tile rewrites srow, sP and the slots
-    }
-    __syncthreads();
-    if (cur >= 0) {
-        if (need_ubar && tid < F) sAcc[cur * F + tid] = run;
-        else if (tid >= F && tid < F + 9) {
-            const int c = tid - F;
-            if (c < 3) sF[cur * 4 + c] = run;
-            else sV[cur * 8 + c - 3] = run;
+        if (cur >= 0) {
+            if (need_ubar && tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
+            else if (tid >= F && tid < F + 9) {
+                const int c = tid - F;
+                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + cur] += run;
+                else a.vir6[(size_t)(a0 + cur) * 6 + c - 3] += run;
+            }
         }
+        __syncthreads();
     }
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TCOLS);
-    if (!ok) {
-        if (tid == 0) atomicOr(status, 1);
-        return;
-    }
-    for (int t = tid; t < nA * 3; t += kT) {
-        int r = t / 3, c = t % 3;
-        size_t o = (size_t)c * a.n_atoms + a0 + r;
-        a.force[o] = a.accumulate ? a.force[o] + sF[r * 4 + c] : sF[r * 4 + c];
-    }
-    for (int t = tid; t < nA * 6; t += kT) {
-        int r = t / 6, c = t % 6;
-        size_t o = (size_t)(a0 + r) * 6 + c;
-        a.vir6[o] = a.accumulate ? a.vir6[o] + sV[r * 8 + c] : sV[r * 8 + c];
-    }
-    if (!need_ubar) return;
-    float* tX = reinterpret_cast<float*>(sm + L::A2);
-    float* tY = tX + A * F;
-    float* Ws = tY + A * F;
-    const int f = tid % F, astep = kT / F;
-    const float* P = a.P;
-    for (int t = tid; t < nA * F; t += kT) tX[t] = sAcc[t];
-    stage_w_t<F>(Ws, P + a.off.W_in[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        size_t o = (size_t)(a0 + r) * F + f;
-        float g = a.gh[o] + dot_t<F>(tX + r * F, Ws, f, true);
-        a.gh[o] = g;
-        tY[r * F + f] = g;
-    }
-    stage_w_t<F>(Ws, P + a.off.U2[l - 1]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float gy = dot_t<F>(tY + r * F, Ws, f, true);
-        float z = a.z_prev[(size_t)(a0 + r) * F + f];
-        float sg;
-        (void)silu_acc(z, sg);
-        tX[r * F + f] = gy * sg * (1.f + z * (1.f - sg));
-    }
-    stage_w_t<F>(Ws, P + a.off.U1[l - 1]);
-    for (int r = tid / F; r < nA; r += astep)
-        a.mbar_out[(size_t)(a0 + r) * F + f] = dot_t<F>(tX + r * F, Ws, f, true);
+    if (!ok && tid == 0) atomicOr(status, 1);
 }
 
-template <int F>
-int fwd_max_atoms() {
-    // tail scratch 2 A F + F (F + 1) floats must fit in the A2 + P region
-    const int region = (FwdLayout<F>::FC - FwdLayout<F>::A2) / 4;
-    int best = 0;
-    for (int A = 8; A <= 256; A += 8)
-        if (2 * A * F + F * (F + 1) <= region && FwdLayout<F>::bytes(A) <= 227 * 1024) best = A;
-    return best;
-}
-
-template <int F>
-int bwd_max_atoms() {
-    const int region = (BwdLayout<F>::J - BwdLayout<F>::A2) / 4;
-    int best = 0;
-    for (int A = 8; A <= 256; A += 8)
-        if (2 * A * F + F * (F + 1) <= region && BwdLayout<F>::bytes(A) <= 227 * 1024) best = A;
-    return best;
-}
-
-template <int F>
-void fwd_go(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_edge_fwd_bf16<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
+template <int F, bool Bwd>
+void go(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    auto kern = Bwd ? k_edge_bwd_bf16<F> : k_edge_fwd_bf16<F>;
+    const int smem = Bwd ? (int)sizeof(BwdSmem<F>) : (int)sizeof(FwdSmem<F>);
+    static int grid_cap = 0;
+    if (!grid_cap) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // resident CTAs per SM: shared memory (1 KB reserved per CTA) and the
+        // 512 tensor-memory columns (each CTA holds 2F or 4F of them)
+        const int by_smem = smem_sm / (smem + 1024);
+        const int by_tmem = 512 / (Bwd ? 4 * F : 2 * F);
+        grid_cap = std::max(1, sms * std::max(1, std::min(by_smem, by_tmem)));
     }
-    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
-    k_edge_fwd_bf16<F><<<grid, kT, FwdLayout<F>::bytes(a.atoms_per_cta), s>>>(a, K, status);
-}
-
-template <int F>
-void bwd_go(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_edge_bwd_bf16<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
-    }
-    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
-    k_edge_bwd_bf16<F><<<grid, kT, BwdLayout<F>::bytes(a.atoms_per_cta), s>>>(a, K, status);
+    int n_chunks = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
+    kern<<<std::min(n_chunks, grid_cap), kT, smem, s>>>(a, K, status);
 }
 
 }  // namespace
 
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    if (F == 64) fwd_go<64>(a, K, status, s);
-    else fwd_go<32>(a, K, status, s);
+    if (F == 64) go<64, false>(a, K, status, s);
+    else go<32, false>(a, K, status, s);
     count_launch();
 }
 
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    if (F == 64) bwd_go<64>(a, K, status, s);
-    else bwd_go<32>(a, K, status, s);
+    if (F == 64) go<64, true>(a, K, status, s);
+    else go<32, true>(a, K, status, s);
     count_launch();
 }
 
-int max_atoms_per_cta_bf16(int F, bool bwd) {
-    if (F == 64) return bwd ? bwd_max_atoms<64>() : fwd_max_atoms<64>();
-    if (F == 32) return bwd ? bwd_max_atoms<32>() : fwd_max_atoms<32>();
-    return 0;
+size_t bf16_weight_tile_bytes(int F) {
+    // per layer: W1^T [F][16], W2^T [F][F], W2 [F][F], each BF16 in the K-major tile layout
+    return (size_t)F * kKP * 2 + 2 * (size_t)F * F * 2;
 }
 
 }  // namespace dmts

@@ -6,8 +6,8 @@
 // TE edges; within a tile the filter MLP is a register-blocked GEMM (each of
 // the 256 threads owns 4 edges x 4 features), and the per-row sums are taken
 // in edge order by one thread per feature, so results are deterministic and
-// atomic-free. After the last tile the CTA runs the per-atom MLPs of its own
-// atoms (update, readout, and the first adjoint steps).
+// atomic-free. The per-atom sums (messages, or the adjoint ubar) are written
+// to global memory for the per-atom MLP kernels.
 //
 // Adjoint (F = -dE/dx): with g_ij = mbar_i * u_j + mbar_j * u_i (the filter
 // depends on d only, so w_ij = w_ji), dE/dd_ij = fc' (g . phi) +
@@ -62,29 +62,6 @@ __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<floa
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float f4(const float4& v, int c) {
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
-
-// ------------------------------------------------------------ per-atom tails
-// out[a][f] = sum_k in[a][k] W[k][f] (trans = false) or sum_k in[a][k] W[f][k]
-// (trans = true), W staged in shared memory with row stride F+1.
-template <int F>
-__device__ __forceinline__ void stage_w(float* Ws, const float* __restrict__ Wg) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < F * F; t += kThreads) Ws[(t / F) * (F + 1) + (t % F)] = __ldg(Wg + t);
-    __syncthreads();
-}
-
-template <int F>
-__device__ __forceinline__ float tail_dot(const float* in_row, const float* Ws, int f, bool trans) {
-    float acc = 0.f;
-    if (trans) {
-#pragma unroll 8
-        for (int k = 0; k < F; ++k) acc += in_row[k] * Ws[f * (F + 1) + k];
-    } else {
-#pragma unroll 8
-        for (int k = 0; k < F; ++k) acc += in_row[k] * Ws[k * (F + 1) + f];
-    }
-    return acc;
 }
 
 // ------------------------------------------------------------ shared layout
@@ -280,76 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_fwd(PotArgs a) {
     if (tid < F && cur >= 0) sAcc[cur * F + tid] = run;
     if (tid == F && l == 0 && cur >= 0) a.erep[a0 + cur] = run;
 
-    // ---------------- per-atom tail (tile buffers reused)
-    float* tX = sST;                     // [A][F]
-    float* tY = tX + A * F;              // [A][F]
-    float* Ws = tY + A * F;              // [F][F+1]
-    const int f = tid % F, astep = kThreads / F;
-    const bool last = (l == a.n_layers - 1);
-    const float* P = a.P;
     __syncthreads();
-    for (int t = tid; t < nA * F; t += kThreads) tX[t] = sAcc[t];
-    // z = m U1 + c1
-    stage_w<F>(Ws, P + a.off.U1[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float z = tail_dot<F>(tX + r * F, Ws, f, false) + __ldg(P + a.off.c1[l] + f);
-        a.z[(size_t)(a0 + r) * F + f] = z;
-        float sg;
-        tY[r * F + f] = silu_f(z, sg);
-    }
-    // h' = h + SiLU(z) U2 + c2
-    stage_w<F>(Ws, P + a.off.U2[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        size_t o = (size_t)(a0 + r) * F + f;
-        float hn = a.h[o] + tail_dot<F>(tY + r * F, Ws, f, false) + __ldg(P + a.off.c2[l] + f);
-        a.h[o] = hn;
-        tX[r * F + f] = hn;
-    }
-    if (!last) {
-        // u^{l+1} = h' W_in^{l+1}
-        stage_w<F>(Ws, P + a.off.W_in[l + 1]);
-        for (int r = tid / F; r < nA; r += astep)
-            a.u_next[(size_t)(a0 + r) * F + f] = tail_dot<F>(tX + r * F, Ws, f, false);
-        return;
-    }
-    // readout: q = h' R1 + d1, E_i = SiLU(q) . R2 + d2 + e0[Z]; gq = SiLU'(q) * R2
-    stage_w<F>(Ws, P + a.off.R1);
-    for (int r = tid / F; r < nA; r += astep) {
-        float qv = tail_dot<F>(tX + r * F, Ws, f, false) + __ldg(P + a.off.d1 + f);
-        float sg;
-        float s = silu_f(qv, sg);
-        float r2 = __ldg(P + a.off.R2 + f);
-        tY[r * F + f] = sg * (1.f + qv * (1.f - sg)) * r2;   // dE/dq
-        sAcc[r * F + f] = s * r2;                            // energy terms
-    }
-    __syncthreads();
-    for (int r = tid; r < nA; r += kThreads) {
-        double e = 0.0;
-        for (int k = 0; k < F; ++k) e += (double)sAcc[r * F + k];
-        int i = a0 + r;
-        e += (double)__ldg(P + a.off.d2) + (double)__ldg(P + a.off.e0 + a.species[i]);
-        e += (double)a.erep[i];
-        a.Ei[i] = e;
-    }
-    // gh = gq R1^T
-    for (int r = tid / F; r < nA; r += astep) {
-        float g = tail_dot<F>(tY + r * F, Ws, f, true);
-        a.gh[(size_t)(a0 + r) * F + f] = g;
-        tX[r * F + f] = g;
-    }
-    // gy = gh U2^T, gz = gy * SiLU'(z)
-    stage_w<F>(Ws, P + a.off.U2[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float gy = tail_dot<F>(tX + r * F, Ws, f, true);
-        float z = a.z[(size_t)(a0 + r) * F + f];
-        float sg;
-        (void)silu_f(z, sg);
-        tY[r * F + f] = gy * sg * (1.f + z * (1.f - sg));
-    }
-    // mbar = gz U1^T
-    stage_w<F>(Ws, P + a.off.U1[l]);
-    for (int r = tid / F; r < nA; r += astep)
-        a.mbar_out[(size_t)(a0 + r) * F + f] = tail_dot<F>(tY + r * F, Ws, f, true);
+    for (int t = tid; t < nA * F; t += kThreads) a.msg_out[(size_t)a0 * F + t] = sAcc[t];
 }
 
 // ------------------------------------------------------------ backward edge pass
@@ -618,33 +527,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd(PotArgs a) {
         size_t o = (size_t)(a0 + r) * 6 + c;
         a.vir6[o] = a.accumulate ? a.vir6[o] + sV[r * 8 + c] : sV[r * 8 + c];
     }
-    if (!need_ubar) return;
-    // gh^l = gh^{l+1} + ubar W_in^T ; mbar^{l-1} = ((gh^l U2^T) * SiLU'(z^{l-1})) U1^T
-    float* tX = sST;
-    float* tY = tX + A * F;
-    float* Ws = tY + A * F;
-    const int f = tid % F, astep = kThreads / F;
-    const float* P = a.P;
-    __syncthreads();
-    for (int t = tid; t < nA * F; t += kThreads) tX[t] = sAcc[t];
-    stage_w<F>(Ws, P + a.off.W_in[l]);
-    for (int r = tid / F; r < nA; r += astep) {
-        size_t o = (size_t)(a0 + r) * F + f;
-        float g = a.gh[o] + tail_dot<F>(tX + r * F, Ws, f, true);
-        a.gh[o] = g;
-        tY[r * F + f] = g;
-    }
-    stage_w<F>(Ws, P + a.off.U2[l - 1]);
-    for (int r = tid / F; r < nA; r += astep) {
-        float gy = tail_dot<F>(tY + r * F, Ws, f, true);
-        float z = a.z_prev[(size_t)(a0 + r) * F + f];
-        float sg;
-        (void)silu_f(z, sg);
-        tX[r * F + f] = gy * sg * (1.f + z * (1.f - sg));
-    }
-    stage_w<F>(Ws, P + a.off.U1[l - 1]);
-    for (int r = tid / F; r < nA; r += astep)
-        a.mbar_out[(size_t)(a0 + r) * F + f] = tail_dot<F>(tX + r * F, Ws, f, true);
+    if (need_ubar)
+        for (int t = tid; t < nA * F; t += kThreads) a.msg_out[(size_t)a0 * F + t] = sAcc[t];
 }
 
 template <int F, int K>
@@ -674,10 +558,7 @@ void bwd_launch(const PotArgs& a, cudaStream_t s) {
 
 template <int F>
 int max_atoms(int K, bool bwd) {
-    // largest A whose shared memory fits, and whose tail scratch fits in the
-    // reused tile region: 2 A F + F (F + 1) <= F TE + TE (F + 4) (forward) or
-    // <= 2 F TE (backward)
-    const int TE = 4096 / F;
+    // largest A whose shared memory fits
     int best = 0;
     for (int A = 8; A <= 256; A += 8) {
         long long fl;
@@ -692,8 +573,9 @@ int max_atoms(int K, bool bwd) {
             DMTS_K(9) DMTS_K(10) DMTS_K(11) DMTS_K(12) DMTS_K(13) DMTS_K(14) DMTS_K(15) DMTS_K(16)
 #undef DMTS_K
         }
-        region = bwd ? 2LL * F * TE : (long long)F * TE + (long long)TE * (F + 4);
-        if (fl * 4 <= 227 * 1024 && 2LL * A * F + F * (F + 1) <= region) best = A;
+        (void)region;
+        region = 0;
+        if (fl * 4 <= 227 * 1024) best = A;
     }
     return best;
 }

@@ -208,9 +208,10 @@ class Context:
         n = load_library().dmts_time_stages(self._h, which, reps, _ptr(out), out.size)
         if n < 0:
             _check(n)
-        L = (n - 3) // 2
+        L = (n - 3) // 4
         names = ["neighbors", "embed"] + [f"edge_fwd_l{l}" for l in range(L)] + \
-                [f"edge_bwd_l{l}" for l in range(L)] + ["energy_sum"]
+                [f"atom_fwd_l{l}" for l in range(L)] + [f"edge_bwd_l{l}" for l in range(L)] + \
+                [f"atom_bwd_l{l}" for l in range(L)] + ["energy_sum"]
         return dict(zip(names, out[:n].tolist()))
 
     @property
