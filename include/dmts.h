@@ -194,6 +194,21 @@ DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
  * a negative dmts_status. */
 DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out, int n_out);
 
+/* Force-matching distillation loss of the small model and its parameter
+ * gradient (section "Training procedures": the distilled model is trained on
+ * data labelled by the reference model):
+ *   L(theta) = 1/(3 N M) sum_{m<M} sum_i |F_i(theta; x_m) - F_ref,m,i|^2,
+ * with F = -dE/dx, so dL/dtheta involves second derivatives of the energy;
+ * it is computed by hand-written adjoint kernels (FP32, whatever the model's
+ * precision setting). frames: [M][N*3] positions, f_ref: [M][N*3] reference
+ * forces (host or device). loss_out: scalar; grad_out: n_params doubles in
+ * the flat parameter order (gradients of d2 and e0 are exactly 0). Supported
+ * for a single-layer small model with n_feat 32 and n_radial 8 or 16. The
+ * context's positions and velocities are restored afterwards; the cached
+ * forces are invalidated. */
+DMTS_API int dmts_force_matching_grad(dmts_ctx* ctx, int n_frames, const double* frames,
+                                      const double* f_ref, double* loss_out, double* grad_out);
+
 /* ------------------------------------------------------------------------
  * Allocation-free neighbour list. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- an MD engine

@@ -1,0 +1,661 @@
+// Force-matching gradient of a single-layer model (FP32, hand-written
+// adjoints): the parameter gradient of the distillation loss
+//   L(theta) = 1/(3 N M) sum_frames sum_i |F_i(theta) - F_ref,i|^2
+// through the forces F = -dE/dx (a second derivative of the energy).
+//
+// With g = dL/dF = 2 (F - F_ref) / (3 N M) per frame and
+//   Psi(theta) = sum_i g_i . dE/dx_i = d/d eps E(x + eps g) |_{eps=0},
+// dL/dtheta = -dPsi/dtheta. Psi is the directional derivative of the energy
+// along x' = g, so it is the energy's forward pass carried with tangents:
+// only the pair distances move, d' = delta_ij = rhat_ij . (g_j - g_i), hence
+//   w'_ij = delta_ij dw/dd = delta (fc' phi + fc (SiLU'(a) * (e' W1)) W2),
+//   m'_i = sum_j w'_ij * u_j,  z' = m' U1,  h1' = (SiLU'(z) * z') U2,
+//   q' = h1' R1,  Psi = sum_i (SiLU'(q_i) * q'_i) . R2.
+// The kernels below take the reverse of this tangent graph with respect to
+// theta: a tangent edge pass (m'), a per-atom adjoint pass (dPsi/dm,
+// dPsi/dm' and the per-atom weight gradients), and an edge pass for the
+// filter-weight gradients and dPsi/du. Every gradient is summed per CTA and
+// the CTA partials are added in a fixed order (deterministic).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace dmts {
+
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + expf(-x)); }
+// SiLU, its first and second derivatives at a
+__device__ __forceinline__ void silu3(float a, float& s, float& d1, float& d2) {
+    float g = sgm(a);
+    s = a * g;
+    d1 = g * (1.f + a * (1.f - g));
+    d2 = g * (1.f - g) * (2.f + a * (1.f - 2.f * g));
+}
+
+template <int K>
+__device__ __forceinline__ void basis_pair(float d, float pi_over_rc, float pref, float* e, float* de, float& fc,
+                                           float& dfc) {
+    float s1, c1;
+    sincospif(d * (pi_over_rc * 0.31830988618379067f), &s1, &c1);
+    float inv_d = 1.0f / d;
+    float sk = s1, skm1 = 0.f, ck = c1, ckm1 = 1.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float kw = (float)(k + 1) * pi_over_rc;
+        e[k] = pref * sk * inv_d;
+        de[k] = pref * (kw * ck - sk * inv_d) * inv_d;
+        float sn = 2.f * c1 * sk - skm1, cn = 2.f * c1 * ck - ckm1;
+        skm1 = sk; sk = sn;
+        ckm1 = ck; ck = cn;
+    }
+    fc = 0.5f * (c1 + 1.0f);
+    dfc = -0.5f * pi_over_rc * s1;
+}
+
+// ------------------------------------------------------------ residual g
+// g_i = c (F_i - F_ref,i) (SoA), c = 2 / (3 N M); per-atom squared residual
+// (FP64) for the loss.
+__global__ void k_fm_residual(int n, const float* __restrict__ f, const double* __restrict__ f_ref_aos, double c,
+                              float* __restrict__ g, double* __restrict__ sq) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double r = (double)f[(size_t)k * n + i] - f_ref_aos[3 * (size_t)i + k];
+        g[(size_t)k * n + i] = (float)(c * r);
+        s += r * r;
+    }
+    sq[i] = s;
+}
+
+// ------------------------------------------------------------ edge tile (shared by both edge passes)
+// One CTA owns atoms [a0, a0 + A) and walks their CSR edges in tiles of TE
+// edges; thread (eg, fg) owns edges 4eg..4eg+3 and features 4fg..4fg+3 of
+// every [TE x F] tile.
+template <int F, int K>
+struct Geo {
+    static constexpr int TE = 4096 / F;
+    static constexpr int FG = F / 4;
+};
+
+// acc[r][c] = sum_k AT[k][e0 + r] W[k][f0 + c]
+template <int KIN, int TE, int F>
+__device__ __forceinline__ void tgemm(const float* AT, const float* W, int e0, int f0, float acc[4][4]) {
+#pragma unroll 8
+    for (int k = 0; k < KIN; ++k) {
+        float4 x = *reinterpret_cast<const float4*>(AT + k * TE + e0);
+        float4 w = *reinterpret_cast<const float4*>(W + k * F + f0);
+        float xa[4] = {x.x, x.y, x.z, x.w}, wf[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += xa[r] * wf[c];
+    }
+}
+
+template <int TE>
+__device__ __forceinline__ void store_tT(float* T, int f0, int e0, const float v[4][4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<float4*>(T + (f0 + c) * TE + e0) = make_float4(v[0][c], v[1][c], v[2][c], v[3][c]);
+}
+
+// Shared-memory carve of both edge passes (floats).
+template <int F, int K>
+struct EdgeSmem {
+    static constexpr int TE = Geo<F, K>::TE;
+    float W1[K * F], b1[F], W2[F * F], W2T[F * F], b2[F];
+    float BT[K * TE], DT[K * TE];        // basis, derivative, transposed
+    float ST[F * TE], PT[F * TE];        // SiLU(a), SiLU'(a) * T  (transposed)
+    float X[TE * (F + 4)], Y[TE * (F + 4)];   // per-edge rows (msg, phibar, gbar, abar, tbar)
+    float fc[TE], dfc[TE], delta[TE];
+    int j[TE], row[TE];
+    float acc[64 * F];                   // per-atom row sums of the CTA (A <= 64)
+};
+
+template <int F, int K>
+__device__ __forceinline__ void load_weights(EdgeSmem<F, K>& S, const PotArgs& a) {
+    for (int t = threadIdx.x; t < K * F; t += kT) S.W1[t] = __ldg(a.P + a.off.W1[0] + t);
+    for (int t = threadIdx.x; t < F * F; t += kT) {
+        float w = __ldg(a.P + a.off.W2[0] + t);
+        S.W2[t] = w;
+        S.W2T[(t % F) * F + t / F] = w;
+    }
+    for (int t = threadIdx.x; t < F; t += kT) {
+        S.b1[t] = __ldg(a.P + a.off.b1[0] + t);
+        S.b2[t] = __ldg(a.P + a.off.b2[0] + t);
+    }
+}
+
+// Per-edge setup (threads < TE): geometry, basis, delta = rhat . (g_j - g_i).
+template <int F, int K>
+__device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, const float* __restrict__ g,
+                                           long long t0, long long e_end, int a0) {
+    constexpr int TE = Geo<F, K>::TE;
+    const int tid = threadIdx.x;
+    if (tid >= TE) return;
+    long long e = t0 + tid;
+    float eb[K], db[K];
+    if (e < e_end) {
+        int j = a.col[e], i = a.recv[e];
+        uint4 qi = a.q[i], qj = a.q[j];
+        float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
+        float d = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+        float inv = 1.0f / d;
+        float fc, dfc;
+        basis_pair<K>(d, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+        const int n = a.n_atoms;
+        float dl = (r.x * (g[j] - g[i]) + r.y * (g[n + j] - g[n + i]) + r.z * (g[2 * n + j] - g[2 * n + i])) * inv;
+        S.fc[tid] = fc;
+        S.dfc[tid] = dfc;
+        S.delta[tid] = dl;
+        S.j[tid] = j;
+        S.row[tid] = i - a0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) { eb[k] = 0.f; db[k] = 0.f; }
+        S.fc[tid] = 0.f;
+        S.dfc[tid] = 0.f;
+        S.delta[tid] = 0.f;
+        S.j[tid] = a0;
+        S.row[tid] = -1;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        S.BT[k * TE + tid] = eb[k];
+        S.DT[k * TE + tid] = db[k];
+    }
+}
+
+// a = e W1 + b1, T = e' W1: writes SiLU(a) to ST and SiLU'(a) T to PT; keeps
+// SiLU'(a), SiLU''(a) and T of the thread's [4 x 4] block.
+template <int F, int K>
+__device__ __forceinline__ void filter_hidden(EdgeSmem<F, K>& S, int e0, int f0, float sp[4][4], float spp[4][4],
+                                              float tt[4][4]) {
+    constexpr int TE = Geo<F, K>::TE;
+    float av[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { av[r][c] = S.b1[f0 + c]; tt[r][c] = 0.f; }
+    tgemm<K, TE, F>(S.BT, S.W1, e0, f0, av);
+    tgemm<K, TE, F>(S.DT, S.W1, e0, f0, tt);
+    float s[4][4], p[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            silu3(av[r][c], s[r][c], sp[r][c], spp[r][c]);
+            p[r][c] = sp[r][c] * tt[r][c];
+        }
+    store_tT<TE>(S.ST, f0, e0, s);
+    store_tT<TE>(S.PT, f0, e0, p);
+}
+
+// Segmented row sums of X[e][f] into acc[row][f] (threads < F, edge order,
+// the open row carried across tiles in cur/run).
+template <int F, int TE>
+__device__ __forceinline__ void row_sums(const float* X, const int* srow, float* acc, int& cur, float& run) {
+    const int f = threadIdx.x;
+    if (f >= F) return;
+    for (int e = 0; e < TE; ++e) {
+        int r = srow[e];
+        if (r < 0) break;
+        if (r != cur) {
+            if (cur >= 0) acc[cur * F + f] = run;
+            cur = r;
+            run = 0.f;
+        }
+        run += X[e * (F + 4) + f];
+    }
+}
+
+// ------------------------------------------------------------ tangent edge pass: m'
+template <int F, int K>
+__global__ void __launch_bounds__(kT) k_fm_tangent(PotArgs a, const float* __restrict__ g, float* __restrict__ mdot) {
+    using G = Geo<F, K>;
+    constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
+    extern __shared__ float4 sm4[];
+    EdgeSmem<F, K>& S = *reinterpret_cast<EdgeSmem<F, K>*>(sm4);
+    const int tid = threadIdx.x, A = a.atoms_per_cta;
+    const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
+    if (nA <= 0) return;
+    load_weights(S, a);
+    for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
+    const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap), e_end = min((long long)a.row_ptr[a1], a.e_cap);
+    const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
+    int cur = -1;
+    float run = 0.f;
+    __syncthreads();
+    for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
+        edge_setup(S, a, g, t0, e_end, a0);
+        __syncthreads();
+        float sp[4][4], spp[4][4], tt[4][4];
+        filter_hidden(S, e0, f0, sp, spp, tt);
+        __syncthreads();
+        float phi[4][4], q[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { phi[r][c] = S.b2[f0 + c]; q[r][c] = 0.f; }
+        tgemm<F, TE, F>(S.ST, S.W2, e0, f0, phi);
+        tgemm<F, TE, F>(S.PT, S.W2, e0, f0, q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int e = e0 + r;
+            float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+            const float* uj = a.u + (size_t)S.j[e] * F + f0;
+            float4 o;
+            o.x = dl * (dfc * phi[r][0] + fc * q[r][0]) * uj[0];
+            o.y = dl * (dfc * phi[r][1] + fc * q[r][1]) * uj[1];
+            o.z = dl * (dfc * phi[r][2] + fc * q[r][2]) * uj[2];
+            o.w = dl * (dfc * phi[r][3] + fc * q[r][3]) * uj[3];
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = o;
+        }
+        __syncthreads();
+        row_sums<F, TE>(S.X, S.row, S.acc, cur, run);
+        __syncthreads();
+    }
+    if (tid < F && cur >= 0) S.acc[cur * F + tid] = run;
+    __syncthreads();
+    for (int t = tid; t < nA * F; t += kT) mdot[(size_t)a0 * F + t] = S.acc[t];
+}
+
+// ------------------------------------------------------------ per-atom adjoint pass
+// Warp per atom, lane = feature (F = 32). Gradient slots (floats) of the
+// per-CTA partial vector: the flat parameter layout (only the blocks this
+// pass touches are written).
+__device__ __forceinline__ float bcast(float v, int k) { return __shfl_sync(0xffffffffu, v, k); }
+
+// out[lane] = sum_k in_k W[k][lane] with in_k held by lane k
+__device__ __forceinline__ float gemv(float in, const float* W) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc += bcast(in, k) * W[k * 32 + (threadIdx.x & 31)];
+    return acc;
+}
+// out[lane] = sum_k in_k W[lane][k], W row-major with row stride 33 (x W^T)
+__device__ __forceinline__ float gemv_t(float in, const float* W) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc += bcast(in, k) * W[(threadIdx.x & 31) * 33 + k];
+    return acc;
+}
+
+constexpr int kAtomWarps = 8;
+
+__global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const float* __restrict__ m,
+                                                              const float* __restrict__ mdot,
+                                                              float* __restrict__ mbar_psi,
+                                                              float* __restrict__ mdotbar_psi,
+                                                              float* __restrict__ partial, int n_params) {
+    constexpr int F = 32;
+    __shared__ float U1[F * F], U2[F * F], R1[F * F];          // W[k][f], for x W
+    __shared__ float U1T[F * 33], U2T[F * 33], R1T[F * 33];    // W[k][f] padded, for x W^T
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const float* P = a.P;
+    for (int t = tid; t < F * F; t += blockDim.x) {
+        int r = t / F, c = t % F;
+        float u1 = P[a.off.U1[0] + t], u2 = P[a.off.U2[0] + t], r1 = P[a.off.R1 + t];
+        U1[t] = u1; U2[t] = u2; R1[t] = r1;
+        U1T[r * 33 + c] = u1; U2T[r * 33 + c] = u2; R1T[r * 33 + c] = r1;
+    }
+    __syncthreads();
+    const float c1 = P[a.off.c1[0] + lane], c2 = P[a.off.c2[0] + lane], d1 = P[a.off.d1 + lane],
+                r2 = P[a.off.R2 + lane];
+    // per-lane gradient accumulators: column `lane` of dR1, dU2, dU1 (k = 0..31), and vectors
+    float gR1[F], gU2[F], gU1[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) { gR1[k] = 0.f; gU2[k] = 0.f; gU1[k] = 0.f; }
+    float gR2 = 0.f, gd1 = 0.f, gc2 = 0.f, gc1 = 0.f;
+    const int S_species = a.off.W_in[0] - a.off.A;   // S * F entries of A
+    float gA[16];
+#pragma unroll
+    for (int z = 0; z < 16; ++z) gA[z] = 0.f;
+    const int n_sp = S_species / F;
+    for (int i = blockIdx.x * kAtomWarps + w; i < a.n_atoms; i += gridDim.x * kAtomWarps) {
+        const size_t o = (size_t)i * F + lane;
+        const float mv = m[o], md = mdot[o], h1 = a.h[o];
+        const float z = gemv(mv, U1) + c1;
+        const float zd = gemv(md, U1);
+        float sz, s1z, s2z;
+        silu3(z, sz, s1z, s2z);
+        const float yd = s1z * zd;                 // tangent of SiLU(z)
+        const float h1d = gemv(yd, U2);            // tangent of h1
+        const float q = gemv(h1, R1) + d1;
+        const float qd = gemv(h1d, R1);
+        float sq, s1q, s2q;
+        silu3(q, sq, s1q, s2q);
+        const float qdb = s1q * r2;                // dPsi/dq'
+        const float qb = s2q * qd * r2;            // dPsi/dq
+        gR2 += s1q * qd;
+        gd1 += qb;
+#pragma unroll
+        for (int k = 0; k < F; ++k) gR1[k] += bcast(h1, k) * qb + bcast(h1d, k) * qdb;
+        const float hb = gemv_t(qb, R1T);          // dPsi/dh1
+        const float hdb = gemv_t(qdb, R1T);        // dPsi/dh1'
+        gc2 += hb;
+#pragma unroll
+        for (int k = 0; k < F; ++k) gU2[k] += bcast(sz, k) * hb + bcast(yd, k) * hdb;
+        const float yb = gemv_t(hb, U2T);
+        const float ydb = gemv_t(hdb, U2T);
+        const float zb = yb * s1z + ydb * s2z * zd;
+        const float zdb = ydb * s1z;
+        gc1 += zb;
+#pragma unroll
+        for (int k = 0; k < F; ++k) gU1[k] += bcast(mv, k) * zb + bcast(md, k) * zdb;
+        mbar_psi[o] = gemv_t(zb, U1T);
+        mdotbar_psi[o] = gemv_t(zdb, U1T);
+        const int sp = a.species[i];
+#pragma unroll
+        for (int zz = 0; zz < 16; ++zz)
+            if (zz == sp) gA[zz] += hb;               // residual h1 = h0 + ... with h0 = A[Z]
+    }
+    // write this warp's partials: partial[(blockIdx * warps + w) * n_params + param]
+    float* out = partial + ((size_t)blockIdx.x * kAtomWarps + w) * n_params;
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+        out[a.off.R1 + k * F + lane] = gR1[k];
+        out[a.off.U2[0] + k * F + lane] = gU2[k];
+        out[a.off.U1[0] + k * F + lane] = gU1[k];
+    }
+    out[a.off.R2 + lane] = gR2;
+    out[a.off.d1 + lane] = gd1;
+    out[a.off.c2[0] + lane] = gc2;
+    out[a.off.c1[0] + lane] = gc1;
+    for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
+}
+
+// ------------------------------------------------------------ filter-weight gradient edge pass
+// Per directed edge (i, j): wbar = Mbar_i * u_j, wdbar = Mdbar_i * u_j (dPsi/dm,
+// dPsi/dm' of the receiver), phibar = fc wbar + delta fc' wdbar,
+// gbar = delta fc wdbar (adjoint of (SiLU'(a) T) W2),
+//   dW2 += SiLU(a)^T phibar + (SiLU'(a) T)^T gbar,  db2 += phibar,
+//   abar = (phibar W2^T) SiLU'(a) + (gbar W2^T) T SiLU''(a),  tbar = (gbar W2^T) SiLU'(a),
+//   dW1 += e^T abar + e'^T tbar,  db1 += abar;
+// and ubar_i = sum_j w_ij * Mbar_j + w'_ij * Mdbar_j (row gather, w symmetric).
+template <int F, int K>
+__global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __restrict__ g,
+                                                      const float* __restrict__ mb, const float* __restrict__ mdb,
+                                                      float* __restrict__ ubar, float* __restrict__ partial,
+                                                      int n_params) {
+    using G = Geo<F, K>;
+    constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
+    extern __shared__ float4 sm4[];
+    EdgeSmem<F, K>& S = *reinterpret_cast<EdgeSmem<F, K>*>(sm4);
+    const int tid = threadIdx.x, A = a.atoms_per_cta;
+    const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
+    float* out = partial + (size_t)blockIdx.x * n_params;
+    // gradient accumulators of this thread: dW2 entries (k, f) = (tid / (F/4)) .. and W1, biases
+    constexpr int NW2 = F * F / kT;      // dW2 entries per thread
+    float gW2[NW2 > 0 ? NW2 : 1];
+#pragma unroll
+    for (int q = 0; q < NW2; ++q) gW2[q] = 0.f;
+    constexpr int NW1 = (K * F + kT - 1) / kT;   // dW1 entries per thread
+    float gW1[NW1];
+#pragma unroll
+    for (int q = 0; q < NW1; ++q) gW1[q] = 0.f;
+    float gb = 0.f;                      // one bias entry (db2: tid < F, db1: the last F threads)
+    if (nA > 0) {
+        load_weights(S, a);
+        for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
+    }
+    const long long e_beg = nA > 0 ? min((long long)a.row_ptr[a0], a.e_cap) : 0;
+    const long long e_end = nA > 0 ? min((long long)a.row_ptr[a1], a.e_cap) : 0;
+    const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
+    int cur = -1;
+    float run = 0.f;
+    __syncthreads();
+    for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
+        edge_setup(S, a, g, t0, e_end, a0);
+        __syncthreads();
+        float sp[4][4], spp[4][4], tt[4][4];
+        filter_hidden(S, e0, f0, sp, spp, tt);
+        __syncthreads();
+        float phi[4][4], q[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { phi[r][c] = S.b2[f0 + c]; q[r][c] = 0.f; }
+        tgemm<F, TE, F>(S.ST, S.W2, e0, f0, phi);
+        tgemm<F, TE, F>(S.PT, S.W2, e0, f0, q);
+        // edge adjoints phibar, gbar (rows of X, Y) and the ubar message (into X after use)
+        float phb[4][4], gb4[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int e = e0 + r;
+            int row = S.row[e];
+            int i = row < 0 ? a0 : a0 + row;
+            float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+            const float* uj = a.u + (size_t)S.j[e] * F + f0;
+            const float* mbi = mb + (size_t)i * F + f0;
+            const float* mdbi = mdb + (size_t)i * F + f0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float wb = mbi[c] * uj[c], wdb = mdbi[c] * uj[c];
+                phb[r][c] = fc * wb + dl * dfc * wdb;
+                gb4[r][c] = dl * fc * wdb;
+            }
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(phb[r][0], phb[r][1], phb[r][2], phb[r][3]);
+            *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(gb4[r][0], gb4[r][1], gb4[r][2], gb4[r][3]);
+        }
+        __syncthreads();
+        // abar, tbar: need phibar W2^T and gbar W2^T (rows of X, Y as A operand, transposed access)
+        float sb[4][4], pb[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { sb[r][c] = 0.f; pb[r][c] = 0.f; }
+        for (int k = 0; k < F; ++k) {
+            float4 wv = *reinterpret_cast<const float4*>(S.W2T + k * F + f0);   // W2[f0..f0+3][k]
+            float wf[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                float xph = S.X[(e0 + r) * PS + k], xg = S.Y[(e0 + r) * PS + k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { sb[r][c] += xph * wf[c]; pb[r][c] += xg * wf[c]; }
+            }
+        }
+        float ab[4][4], tb[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ab[r][c] = sb[r][c] * sp[r][c] + pb[r][c] * tt[r][c] * spp[r][c];
+                tb[r][c] = pb[r][c] * sp[r][c];
+            }
+        // weight gradients of this tile: dW2 (ST, PT against X, Y), db2; then dW1 (BT, DT against abar, tbar), db1
+#pragma unroll
+        for (int qq = 0; qq < NW2; ++qq) {
+            int idx = tid + qq * kT;
+            int k = idx / F, f = idx % F;
+            float s = 0.f;
+            for (int e = 0; e < TE; ++e) s += S.ST[k * TE + e] * S.X[e * PS + f] + S.PT[k * TE + e] * S.Y[e * PS + f];
+            gW2[qq] += s;
+        }
+        if (tid < F) {
+            float s = 0.f;
+            for (int e = 0; e < TE; ++e) s += S.X[e * PS + tid];
+            gb += s;                                          // db2
+        }
+        __syncthreads();
+        // abar -> X, tbar -> Y (rows)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int e = e0 + r;
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(ab[r][0], ab[r][1], ab[r][2], ab[r][3]);
+            *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(tb[r][0], tb[r][1], tb[r][2], tb[r][3]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int qq = 0; qq < NW1; ++qq) {
+            int idx = tid + qq * kT;
+            if (idx < K * F) {
+                int k = idx / F, f = idx % F;
+                float s = 0.f;
+                for (int e = 0; e < TE; ++e)
+                    s += S.BT[k * TE + e] * S.X[e * PS + f] + S.DT[k * TE + e] * S.Y[e * PS + f];
+                gW1[qq] += s;
+            }
+        }
+        if (tid >= kT - F) {
+            int f = tid - (kT - F);
+            float s = 0.f;
+            for (int e = 0; e < TE; ++e) s += S.X[e * PS + f];
+            gb += s;                                          // db1 (threads kT-F .. kT-1)
+        }
+        __syncthreads();
+        // ubar message: w * Mbar_j + w' * Mdbar_j with w = fc phi, w' = delta (fc' phi + fc q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int e = e0 + r;
+            float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+            const float* mbj = mb + (size_t)S.j[e] * F + f0;
+            const float* mdbj = mdb + (size_t)S.j[e] * F + f0;
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) o[c] = fc * phi[r][c] * mbj[c] + dl * (dfc * phi[r][c] + fc * q[r][c]) * mdbj[c];
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncthreads();
+        row_sums<F, TE>(S.X, S.row, S.acc, cur, run);
+        __syncthreads();
+    }
+    if (nA > 0) {
+        if (tid < F && cur >= 0) S.acc[cur * F + tid] = run;
+        __syncthreads();
+        for (int t = tid; t < nA * F; t += kT) ubar[(size_t)a0 * F + t] = S.acc[t];
+    }
+    // CTA partials of the filter weights
+#pragma unroll
+    for (int qq = 0; qq < NW2; ++qq) out[a.off.W2[0] + tid + qq * kT] = gW2[qq];
+#pragma unroll
+    for (int qq = 0; qq < NW1; ++qq)
+        if (tid + qq * kT < K * F) out[a.off.W1[0] + tid + qq * kT] = gW1[qq];
+    if (tid < F) out[a.off.b2[0] + tid] = gb;
+    if (tid >= kT - F) out[a.off.b1[0] + tid - (kT - F)] = gb;
+}
+
+// dW_in += h0_i^T ubar_i, dA[Z_i] += ubar_i W_in^T (warp per atom, F = 32)
+__global__ void __launch_bounds__(kAtomWarps * 32) k_fm_input(PotArgs a, const float* __restrict__ ubar,
+                                                               float* __restrict__ partial, int n_params) {
+    constexpr int F = 32;
+    __shared__ float WinT[F * 33];     // W_in[k][f] padded, for x W_in^T
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < F * F; t += blockDim.x) WinT[(t / F) * 33 + t % F] = a.P[a.off.W_in[0] + t];
+    __syncthreads();
+    float gW[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) gW[k] = 0.f;
+    float gA[16];
+#pragma unroll
+    for (int z = 0; z < 16; ++z) gA[z] = 0.f;
+    const int n_sp = (a.off.W_in[0] - a.off.A) / F;
+    for (int i = blockIdx.x * kAtomWarps + w; i < a.n_atoms; i += gridDim.x * kAtomWarps) {
+        const int sp = a.species[i];
+        const float ub = ubar[(size_t)i * F + lane];
+        const float h0 = a.P[a.off.A + sp * F + lane];
+#pragma unroll
+        for (int k = 0; k < F; ++k) gW[k] += bcast(h0, k) * ub;
+        float t = gemv_t(ub, WinT);
+#pragma unroll
+        for (int zz = 0; zz < 16; ++zz)
+            if (zz == sp) gA[zz] += t;
+    }
+    float* out = partial + ((size_t)blockIdx.x * kAtomWarps + w) * n_params;
+#pragma unroll
+    for (int k = 0; k < F; ++k) out[a.off.W_in[0] + k * F + lane] = gW[k];
+    for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
+}
+
+// grad[p] (+)= -sum_c partial[c][p] for p in the listed range (fixed order).
+__global__ void k_fm_reduce(const float* __restrict__ partial, int n_rows, int n_params, int p0, int p1,
+                            double* __restrict__ grad) {
+    int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
+    double s = 0.0;
+    for (int c = 0; c < n_rows; ++c) s += (double)partial[(size_t)c * n_params + p];
+    grad[p] -= s;
+}
+
+__global__ void k_sum_all(int n, const double* __restrict__ v, double scale, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += scale * sh[0];
+}
+
+template <int F, int K>
+size_t edge_smem() { return sizeof(EdgeSmem<F, K>); }
+
+template <int F, int K>
+void tangent_go(const PotArgs& a, const float* g, float* mdot, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fm_tangent<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_smem<F, K>());
+        attr = true;
+    }
+    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
+    k_fm_tangent<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mdot);
+}
+
+template <int F, int K>
+void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
+                  int n_params, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fm_grad_edge<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_smem<F, K>());
+        attr = true;
+    }
+    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
+    k_fm_grad_edge<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mb, mdb, ubar, partial, n_params);
+}
+
+}  // namespace
+
+bool fm_supported(int F, int K, int L) { return F == 32 && (K == 8 || K == 16) && L == 1; }
+
+int fm_atoms_per_cta() { return 32; }
+
+int fm_edge_ctas(int n_atoms) { return (n_atoms + fm_atoms_per_cta() - 1) / fm_atoms_per_cta(); }
+
+int fm_atom_ctas(int n_atoms) { return std::max(1, std::min(152 * 2, (n_atoms + kAtomWarps - 1) / kAtomWarps)); }
+
+// One frame's contribution: g from the forces already in p.force, then the
+// three passes; grad_out accumulates -dPsi/dtheta, loss_out the loss.
+void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
+                     const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
+                     float* partial_a, int n_params, double* grad, double* loss, cudaStream_t s) {
+    const int n = p.n_atoms;
+    if (n == 0) return;
+    k_fm_residual<<<(n + 255) / 256, 256, 0, s>>>(n, p.force, f_ref, c_loss, g, sq);
+    k_sum_all<<<1, 256, 0, s>>>(n, sq, 0.5 * c_loss, loss);
+    PotArgs a = p;
+    a.atoms_per_cta = fm_atoms_per_cta();
+    if (K == 8) tangent_go<32, 8>(a, g, mdot, s);
+    else tangent_go<32, 16>(a, g, mdot, s);
+    const int ga = fm_atom_ctas(n);
+    cudaMemsetAsync(partial_a, 0, sizeof(float) * (size_t)ga * kAtomWarps * n_params, s);
+    k_fm_atom<<<ga, kAtomWarps * 32, 0, s>>>(a, m, mdot, mbar_psi, mdotbar_psi, partial_a, n_params);
+    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_a, ga * kAtomWarps, n_params, 0, n_params, grad);
+    const int ge = fm_edge_ctas(n);
+    cudaMemsetAsync(partial_e, 0, sizeof(float) * (size_t)ge * n_params, s);
+    if (K == 8) grad_edge_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
+    else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
+    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_e, ge, n_params, 0, n_params, grad);
+    cudaMemsetAsync(partial_a, 0, sizeof(float) * (size_t)ga * kAtomWarps * n_params, s);
+    k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
+    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_a, ga * kAtomWarps, n_params, 0, n_params, grad);
+    count_launch(11);
+}
+
+}  // namespace dmts

@@ -118,6 +118,10 @@ struct dmts_ctx {
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
     bool broken = false;
+    // force-matching buffers (allocated on first use)
+    float *fm_g = nullptr, *fm_m = nullptr, *fm_mdot = nullptr, *fm_mb = nullptr, *fm_mdb = nullptr,
+          *fm_ubar = nullptr, *fm_pe = nullptr, *fm_pa = nullptr;
+    double *fm_sq = nullptr, *fm_grad = nullptr, *fm_loss = nullptr, *fm_stage = nullptr;
     cudaGraphExec_t graph = nullptr;
     int g_n_inner = 0;
     double g_dt = 0;
@@ -588,6 +592,8 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
+    dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
+    dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -883,6 +889,78 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
 }
 
 void* dmts_stream(dmts_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int dmts_force_matching_grad(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref,
+                             double* loss_out, double* grad_out) {
+    CTX_GUARD(c);
+    Model& m = c->m[0];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!fm_supported(m.F, m.K, m.L))
+        return fail(DMTS_ERR_ARG, "force matching needs a single-layer small model with n_feat 32, n_radial 8 or 16");
+    if (n_frames < 1 || !frames || !f_ref || !loss_out || !grad_out) return fail(DMTS_ERR_ARG, "bad arguments");
+    LaunchScope ls(c);
+    const int N = c->N;
+    const size_t n3 = (size_t)3 * N, nf = (size_t)N * m.F;
+    const int np = (int)m.n_params;
+    if (!c->fm_g) {
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = dalloc(&c->fm_g, n3);
+        if (e == cudaSuccess) e = dalloc(&c->fm_m, nf);
+        if (e == cudaSuccess) e = dalloc(&c->fm_mdot, nf);
+        if (e == cudaSuccess) e = dalloc(&c->fm_mb, nf);
+        if (e == cudaSuccess) e = dalloc(&c->fm_mdb, nf);
+        if (e == cudaSuccess) e = dalloc(&c->fm_ubar, nf);
+        if (e == cudaSuccess) e = dalloc(&c->fm_pe, (size_t)fm_edge_ctas(N) * np);
+        if (e == cudaSuccess) e = dalloc(&c->fm_pa, (size_t)fm_atom_ctas(N) * 8 * np);
+        if (e == cudaSuccess) e = dalloc(&c->fm_sq, N);
+        if (e == cudaSuccess) e = dalloc(&c->fm_grad, np);
+        if (e == cudaSuccess) e = dalloc(&c->fm_loss, 1);
+        if (e == cudaSuccess) e = dalloc(&c->fm_stage, 2 * n3);
+        if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "force-matching buffers: %s", cudaGetErrorString(e));
+    }
+    int rc;
+    // keep the dynamical state
+    CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->fm_grad, 0, sizeof(double) * np, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->fm_loss, 0, sizeof(double), c->stream));
+    const int prec = m.precision;
+    m.precision = DMTS_FP32;                 // the adjoint passes are FP32; so is the force they differentiate
+    const double cl = 2.0 / (3.0 * (double)N * (double)n_frames);
+    for (int fr = 0; fr < n_frames && N > 0; ++fr) {
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            if ((rc = reset_flags(c))) { m.precision = prec; return rc; }
+            rc = copy_in(c, c->fm_stage, frames + (size_t)fr * n3, n3);
+            if (!rc) rc = copy_in(c, c->fm_stage + n3, f_ref + (size_t)fr * n3, n3);
+            if (rc) { m.precision = prec; return rc; }
+            // frame positions into x (velocities, saved above, are zeroed meanwhile)
+            launch_set_state(N, c->fm_stage, nullptr, c->d_sys, c->d_box, c->d_x, c->d_v, c->stream);
+            enqueue_eval(c, 0, true);
+            if ((rc = sync_check(c))) { m.precision = prec; return rc; }
+            if (!c->h_flags[kFlagOverflow]) break;
+            if ((rc = grow_capacity(c))) { m.precision = prec; return rc; }
+            if (attempt == 3) { m.precision = prec; return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists"); }
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->fm_m, m.msg, nf * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        PotArgs a = pot_args(c, m);
+        a.layer = 0;
+        a.u = m.u[0];                         // u^0 = h0 W_in (gathered per edge)
+        if (!a.u || !a.h || !a.force || !a.P || !a.row_ptr || !a.col || !a.recv || !a.q) {
+            m.precision = prec;
+            return fail(DMTS_ERR_STATE, "force matching: buffers missing");
+        }
+        launch_fm_frame(a, m.K, c->fm_stage + n3, cl, c->fm_g, c->fm_sq, c->fm_m, c->fm_mdot, c->fm_mb, c->fm_mdb,
+                        c->fm_ubar, c->fm_pe, c->fm_pa, np, c->fm_grad, c->fm_loss, c->stream);
+        if ((rc = sync_check(c))) { m.precision = prec; return rc; }
+    }
+    m.precision = prec;
+    CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->forces_valid = false;
+    if ((rc = copy_out(c, grad_out, c->fm_grad, np))) return rc;
+    if ((rc = copy_out(c, loss_out, c->fm_loss, 1))) return rc;
+    return sync_check(c);
+}
 
 int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out) {
     CTX_GUARD(c);

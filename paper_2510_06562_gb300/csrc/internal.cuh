@@ -140,6 +140,14 @@ void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
 size_t bf16_weight_tile_bytes(int F);
 
+// distill_f32.cu: force-matching gradient of a single-layer model
+bool fm_supported(int F, int K, int L);
+int fm_edge_ctas(int n_atoms);
+int fm_atom_ctas(int n_atoms);
+void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
+                     const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
+                     float* partial_a, int n_params, double* grad, double* loss, cudaStream_t s);
+
 // atom_mlp.cu: per-atom MLPs after the edge passes
 void launch_atom_fwd(const PotArgs& p, int F, const float* msg, cudaStream_t s);
 void launch_atom_bwd(const PotArgs& p, int F, const float* ubar, cudaStream_t s);

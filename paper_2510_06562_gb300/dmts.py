@@ -28,7 +28,8 @@ SMALL, BIG = 0, 1
 
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
-            "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc")
+            "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
+            "dmts_force_matching_grad")
 
 
 class DmtsError(RuntimeError):
@@ -84,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_neighbors_noalloc.argtypes = [P, C.c_int, C.c_double, C.c_double, P, P, C.c_longlong,
                                            C.POINTER(C.c_longlong), P]
     lib.dmts_neighbors_noalloc.restype = C.c_int
+    lib.dmts_force_matching_grad.argtypes = [P, C.c_int, P, P, P, P]
+    lib.dmts_force_matching_grad.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -156,6 +159,7 @@ class Context:
                                options.encode() if options else None, C.byref(h)))
         self._h = h
         self.has_small = small_arch is not None
+        self.small_n_params = small_arch.param_count() if small_arch is not None else 0
 
     # ---------------------------------------------------------------- state
     def set_state(self, x, v=None):
@@ -202,6 +206,21 @@ class Context:
                                               _ptr(out) if energies else None))
         return out if energies else None
 
+    def force_matching_grad(self, frames, f_ref, grad_out=None):
+        """Distillation loss of the small model against reference forces and
+        its parameter gradient: (loss, grad [n_params]). frames, f_ref:
+        [M, N, 3] float64 (NumPy or torch, host or device)."""
+        frames = _f64(frames)
+        f_ref = _f64(f_ref)
+        m = frames.shape[0]
+        if tuple(f_ref.shape) != tuple(frames.shape) or frames.shape[1:] != (self.n_atoms, 3):
+            raise ValueError("frames and f_ref must both be [M, N, 3]")
+        loss = np.zeros(1)
+        grad = np.empty(self.small_n_params) if grad_out is None else grad_out
+        _check(load_library().dmts_force_matching_grad(self._h, m, _ptr(frames), _ptr(f_ref), _ptr(loss),
+                                                       _ptr(grad)))
+        return float(loss[0]), grad
+
     def time_stages(self, which: int = BIG, reps: int = 10) -> dict:
         """Per-stage milliseconds of one force evaluation (CUDA events)."""
         out = np.zeros(32)
@@ -238,3 +257,34 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+class ForceMatchingLoss:
+    """torch.autograd.Function for the distillation loss of the small model:
+    ``loss = ForceMatchingLoss.apply(theta, ctx, frames, f_ref)`` with theta
+    the flat float64 parameter tensor of the small model; ``loss.backward()``
+    fills ``theta.grad`` from the library's adjoint kernels (gradient through
+    the forces). The context's small-model parameters are set to theta."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, theta, context, frames, f_ref):
+        if cls._fn is None:
+            import torch
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, th, ctx_obj, fr, fref):
+                    ctx_obj.set_params(SMALL, th.detach().cpu().numpy())
+                    loss, grad = ctx_obj.force_matching_grad(fr, fref)
+                    fctx.save_for_backward(torch.as_tensor(grad, dtype=th.dtype, device=th.device))
+                    return torch.tensor(loss, dtype=th.dtype, device=th.device)
+
+                @staticmethod
+                def backward(fctx, g_out):
+                    (grad,) = fctx.saved_tensors
+                    return g_out * grad, None, None, None
+
+            cls._fn = _Fn
+        return cls._fn.apply(theta, context, frames, f_ref)

@@ -352,3 +352,46 @@ def test_bf16_virial_and_dynamics():
         span = float(e[:, 0, 2].max() - e[:, 0, 2].min())
         print(json.dumps({"bf16_etot_span_120fs": span}))
         assert np.all(np.isfinite(e)) and span < 5.0
+
+
+# ------------------------------------------------------------ distillation gradient (double backward)
+
+def test_force_matching_gradient_matches_oracle():
+    """dL/dtheta of the force-matching loss through the forces, by the
+    library's adjoint kernels, against the FP64 oracle (autograd double
+    backward), on two frames of the 192-atom box with reference forces from
+    the big model."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models(2)
+    rng = np.random.default_rng(7)
+    frames = np.stack([s.x, s.x + rng.normal(scale=0.03, size=s.x.shape)])
+    frames = frames - s.box[0] * np.floor(frames / s.box[0])
+    f_ref = np.stack([M.energy_forces(M.spec_of(ba), bp, f, s.species, s.atom_offset, s.box)[1] for f in frames])
+    L_ref, g_ref = M.force_matching_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        L, g = ctx.force_matching_grad(frames, f_ref)
+    rel_L = abs(L - L_ref) / L_ref
+    err = np.abs(g - g_ref)
+    rel_g = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    print(json.dumps({"loss": L, "loss_ref": L_ref, "rel_loss_err": rel_L, "grad_rel_l2_err": rel_g,
+                      "grad_max_abs_err": float(err.max()), "grad_max_abs": float(np.abs(g_ref).max())}))
+    assert rel_L < 1e-5
+    assert rel_g < 1e-3
+    assert np.all(g[-2:] == 0.0)          # d2 and e0 do not move forces
+
+
+def test_force_matching_autograd_function():
+    torch = pytest.importorskip("torch")
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models(2)
+    frames = s.x[None].copy()
+    f_ref = M.energy_forces(M.spec_of(ba), bp, s.x, s.species, s.atom_offset, s.box)[1][None]
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        theta = torch.tensor(sp, requires_grad=True)
+        loss = D.ForceMatchingLoss.apply(theta, ctx, frames, f_ref)
+        loss.backward()
+        _, g = ctx.force_matching_grad(frames, f_ref)
+    np.testing.assert_allclose(theta.grad.numpy(), g, rtol=0, atol=0)
+    assert float(loss) > 0
