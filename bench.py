@@ -146,6 +146,69 @@ def time_steps(ctx, torch, stream, flush, n_steps, dt, n_inner, x0, v0):
     return ms, launches
 
 
+def max_over_ranks(values, dist, device="cpu"):
+    """Element-wise maximum of per-rank timings (every rank gets the result);
+    with one process, the values themselves."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_ns_per_day(world, steps, dt_fs, t_max_s):
+    """Whole-job simulated time per day of `world` independent replicas, each
+    running `steps` steps of dt_fs in at most t_max_s seconds."""
+    return world * steps * dt_fs / FS_PER_NS / t_max_s * SEC_PER_DAY
+
+
+def measure(D, I, torch, s, models_, prec, args, flush, dt, n_inner, seed):
+    """DMTS (dt / n_inner) and 1 fs STS throughput of one precision on one
+    system, per-stage times and the dominant kernel's roofline."""
+    sa, sp, ba, bp = models_
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, seed, s.atom_offset)
+    N = s.n_atoms
+    ctx = D.Context(s, ba, bp, sa, sp, precision=prec)
+    sts = D.Context(s, ba, bp, precision=prec)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    sstream = torch.cuda.ExternalStream(sts.stream)
+    ctx.set_state(s.x, v0)
+    sts.set_state(s.x, v0)
+    ctx.respa_step(args.warmup, dt, n_inner, energies=False)
+    sts.respa_step(args.warmup, 1.0, 1, energies=False)
+    torch.cuda.synchronize()
+    ms_dmts, launches = time_steps(ctx, torch, stream, flush, args.steps, dt, n_inner, s.x, v0)
+    ms_sts, _ = time_steps(sts, torch, sstream, flush, args.steps, 1.0, 1, s.x, v0)
+    k6 = max(3, args.steps // 2)
+    ctx.respa_step(3, 6.0, 6, energies=False)
+    ms6, _ = time_steps(ctx, torch, stream, flush, k6, 6.0, 6, s.x, v0)
+    out = {"t_dmts": sum(ms_dmts) / 1e3, "t_sts": sum(ms_sts) / 1e3, "t6": sum(ms6) / 1e3, "k6": k6,
+           "launches": launches, "ctx": ctx, "sts": sts, "v0": v0}
+    out["stages_big"] = ctx.time_stages(D.BIG, reps=20)
+    out["stages_small"] = ctx.time_stages(D.SMALL, reps=20)
+    out["pairs_big"] = int(ctx.neighbors(D.BIG)[0][-1])
+    out["pairs_small"] = int(ctx.neighbors(D.SMALL)[0][-1])
+    out["tuning"] = {"big": ctx.tuning(D.BIG), "small": ctx.tuning(D.SMALL)}
+    return out
+
+
+def roofline_of(D, prec, stages_big, E_big, ba):
+    dom = max((k for k in stages_big if k.startswith("edge_")), key=lambda k: stages_big[k])
+    K, F = ba.n_radial, ba.n_feat
+    if prec == D.FP32:
+        flop_edge = 2 * (2 * K * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (K * F + F * F)
+        peak, bound, src, kind = FP32_SIMT_TFLOPS, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "FP32 SIMT"
+    else:
+        # tensor-core MMAs issued (K padded to 16): forward 16F + F^2, backward 2 (16F) + 2 F^2 MACs per pair
+        flop_edge = 2 * (2 * 16 * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (16 * F + F * F)
+        peak, bound, src, kind = measured_peak("bf16_tflops"), "tensor", "MEASURED_PEAKS.json bf16_tflops (burst)", "BF16 tcgen05"
+    achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
+    return {"kernel": f"{dom} (big model, {kind})", "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "algorithmic_flop_per_launch": flop_edge * E_big, "launch_ms": stages_big[dom], "peak_source": src}
+
+
 def run_ours(args):
     import torch
 
@@ -166,107 +229,130 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     s = workload(args.workload)
-    sa, sp, ba, bp = models(s.n_species)
-    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1 + rank)
+    mdl = models(s.n_species)
+    sa, sp, ba, bp = mdl
     N = s.n_atoms
     dt, n_inner = args.outer_fs, args.n_inner
-    prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
-
-    ctx = D.Context(s, ba, bp, sa, sp, precision=prec)
-    sts = D.Context(s, ba, bp, precision=prec)
-    stream = torch.cuda.ExternalStream(ctx.stream)
-    sstream = torch.cuda.ExternalStream(sts.stream)
+    main_prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ctx.set_state(s.x, v0)
-    sts.set_state(s.x, v0)
-    ctx.respa_step(max(3, args.warmup), dt, n_inner, energies=False)
-    sts.respa_step(max(3, args.warmup), 1.0, 1, energies=False)
-    torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    ms_dmts, launches = time_steps(ctx, torch, stream, flush, args.steps, dt, n_inner, s.x, v0)
-    ms_sts, _ = time_steps(sts, torch, sstream, flush, args.steps, 1.0, 1, s.x, v0)
+    res = {main_prec: measure(D, I, torch, s, mdl, main_prec, args, flush, dt, n_inner, 1 + rank)}
+    other = D.FP32 if main_prec == D.BF16_MLP else D.BF16_MLP
+    if not args.single_precision:
+        res[other] = measure(D, I, torch, s, mdl, other, args, flush, dt, n_inner, 1 + rank)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_dmts = sum(ms_dmts) / 1e3
-    t_sts = sum(ms_sts) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_dmts, t_sts], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dmts, t_sts = tt.tolist()
-    ns_dmts = world * args.steps * dt / FS_PER_NS / t_dmts * SEC_PER_DAY
-    ns_sts = world * args.steps * 1.0 / FS_PER_NS / t_sts * SEC_PER_DAY
-    evals = world * args.steps * (n_inner + 1) * N / t_dmts
 
-    # 6 fs outer step (6 inner steps of 1 fs), fewer steps
-    k6 = max(3, args.steps // 2)
-    ctx.respa_step(3, 6.0, 6, energies=False)
-    ms6, _ = time_steps(ctx, torch, stream, flush, k6, 6.0, 6, s.x, v0)
-    ns6 = k6 * 6.0 / FS_PER_NS / (sum(ms6) / 1e3) * SEC_PER_DAY
+    def agg(r):
+        t_dmts, t_sts, t6 = max_over_ranks([r["t_dmts"], r["t_sts"], r["t6"]], dist, "cuda")
+        return {"dmts_ns_per_day": replica_ns_per_day(world, args.steps, dt, t_dmts),
+                "sts_1fs_ns_per_day": replica_ns_per_day(world, args.steps, 1.0, t_sts),
+                "dmts_6fs_ns_per_day": replica_ns_per_day(world, r["k6"], 6.0, t6),
+                "atom_force_evals_per_s": world * args.steps * (n_inner + 1) * N / t_dmts,
+                "ms_per_step": t_dmts * 1e3 / args.steps, "ms_per_step_sts": t_sts * 1e3 / args.steps}
 
-    # dominant kernel: per-stage CUDA-event times of one big-model evaluation
-    stages_big = ctx.time_stages(D.BIG, reps=20)
-    stages_small = ctx.time_stages(D.SMALL, reps=20)
-    rp, _ = ctx.neighbors(D.BIG)
-    E_big = int(rp[-1])
-    rp_s, _ = ctx.neighbors(D.SMALL)
-    E_small = int(rp_s[-1])
-    dom = max((k for k in stages_big if k.startswith("edge_")), key=lambda k: stages_big[k])
-    K, F = ba.n_radial, ba.n_feat
-    if prec == D.FP32:
-        flop_edge = 2 * (2 * K * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (K * F + F * F)
-        peak, bound, src, kind = FP32_SIMT_TFLOPS, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "FP32 SIMT"
-    else:
-        # tensor-core MMAs issued (K padded to 16): forward 16F + F^2, backward 2 (16F) + 2 F^2 MACs per pair
-        flop_edge = 2 * (2 * 16 * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (16 * F + F * F)
-        peak, bound, src, kind = measured_peak("bf16_tflops"), "tensor", "MEASURED_PEAKS.json bf16_tflops (burst)", "BF16 tcgen05"
-    achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
-    roofline = {"kernel": f"{dom} (big model, {kind})", "bound": bound, "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "algorithmic_flop_per_launch": flop_edge * E_big, "peak_source": src}
-
+    main = res[main_prec]
+    m = agg(main)
+    r = main["ctx"]
     # end to end through the public API with host buffers: upload state,
     # one outer step, read energies and state back (each step)
     xh = torch.tensor(s.x).pin_memory()
-    vh = torch.tensor(v0).pin_memory()
+    vh = torch.tensor(main["v0"]).pin_memory()
     eh = torch.empty((1, s.n_systems, 3), dtype=torch.float64).pin_memory()
     k_e2e = max(3, args.steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        ctx.set_state(xh, vh)
-        ctx.respa_step(1, dt, n_inner, out=eh)
-        ctx.get_state(xh, vh)
+        r.set_state(xh, vh)
+        r.respa_step(1, dt, n_inner, out=eh)
+        r.get_state(xh, vh)
     t_e2e = time.perf_counter() - t0
     e2e = {"value": world * k_e2e * dt / FS_PER_NS / t_e2e * SEC_PER_DAY, "unit": "ns/day",
            "h2d_bytes_per_step": 2 * N * 3 * 8, "d2h_bytes_per_step": 2 * N * 3 * 8 + 3 * 8 * s.n_systems,
            "note": "state uploaded and read back every step; each upload recomputes both models' first-step forces"}
 
+    extras = {}
+    if not args.single_precision:
+        o = agg(res[other])
+        o["stage_ms"] = {"big": res[other]["stages_big"], "small": res[other]["stages_small"]}
+        o["roofline"] = roofline_of(D, other, res[other]["stages_big"], res[other]["pairs_big"], ba)
+        o["speedup_vs_sts"] = o["dmts_ns_per_day"] / o["sts_1fs_ns_per_day"]
+        extras["fp32" if other == D.FP32 else "bf16"] = o
+    if args.extras and world == 1:
+        extras["vacuum512"] = vacuum_batch(D, I, torch, main_prec, args, flush)
+        extras["distill"] = distill_rate(D, I, torch, s, mdl)
+
     if rank != 0:
         return None
     cpu = cpu_baseline(args, s, sa, sp, ba, bp, dt, n_inner) if world == 1 and not args.no_cpu else None
     line = {
-        "metric": METRIC, "value": ns_dmts, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": t_dmts * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == D.FP32 else "bf16",
+        "metric": METRIC, "value": m["dmts_ns_per_day"], "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_prec == D.BF16_MLP else "f32",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: 4,096 rigid waters, 12,288 atoms, L=49.7 A, periodic",
                    "outer_fs": dt, "inner_fs": dt / n_inner, "n_inner": n_inner,
-                   "precision": args.precision, "small_model": "3.5 A, K=8, 1 layer, F=32",
-                   "big_model": "5.0 A, K=16, 2 layers, F=64", "state": "FP64 x, v",
+                   "precision": args.precision + (" (MLP operands; FP32 accumulation, geometry, sums)" if args.precision == "bf16" else ""),
+                   "small_model": "3.5 A, K=8, 1 layer, F=32", "big_model": "5.0 A, K=16, 2 layers, F=64",
+                   "state": "FP64 x, v",
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
-        "atom_force_evals_per_s": evals, "sts_1fs_ns_per_day": ns_sts, "speedup_vs_sts": ns_dmts / ns_sts,
-        "dmts_6fs_ns_per_day": ns6, "speedup_6fs_vs_sts": ns6 / ns_sts,
-        "ms_per_step_sts": t_sts * 1e3 / args.steps,
-        "pairs": {"small": E_small, "big": E_big},
-        "stage_ms": {"big": stages_big, "small": stages_small},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk,
+        "atom_force_evals_per_s": m["atom_force_evals_per_s"], "sts_1fs_ns_per_day": m["sts_1fs_ns_per_day"],
+        "speedup_vs_sts": m["dmts_ns_per_day"] / m["sts_1fs_ns_per_day"],
+        "dmts_6fs_ns_per_day": m["dmts_6fs_ns_per_day"],
+        "speedup_6fs_vs_sts": m["dmts_6fs_ns_per_day"] / m["sts_1fs_ns_per_day"],
+        "ms_per_step_sts": m["ms_per_step_sts"],
+        "pairs": {"small": main["pairs_small"], "big": main["pairs_big"]},
+        "tuning": main["tuning"],
+        "stage_ms": {"big": main["stages_big"], "small": main["stages_small"]},
+        "roofline": roofline_of(D, main_prec, main["stages_big"], main["pairs_big"], ba),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"], "clocks": clk,
     }
+    line.update(extras)
     return line
+
+
+def vacuum_batch(D, I, torch, prec, args, flush):
+    """512 independent non-periodic molecules of 10-60 atoms, one context,
+    DMTS 3 fs / 1 fs vs 1 fs STS (each CUDA graph covers all molecules)."""
+    s = I.make_vacuum_batch(512, 10, 60, seed=0)
+    mdl = models(4)
+    r = measure(D, I, torch, s, mdl, prec, argparse.Namespace(steps=max(10, args.steps // 2), warmup=3),
+                flush, 3.0, 3, 1)
+    k = max(10, args.steps // 2)
+    return {"workload": f"512 vacuum molecules, {s.n_atoms} atoms", "steps": k,
+            "dmts_ns_per_day_per_molecule_sum": k * 3.0 / FS_PER_NS / r["t_dmts"] * SEC_PER_DAY * 512,
+            "dmts_ns_per_day": k * 3.0 / FS_PER_NS / r["t_dmts"] * SEC_PER_DAY,
+            "sts_1fs_ns_per_day": k * 1.0 / FS_PER_NS / r["t_sts"] * SEC_PER_DAY,
+            "ms_per_step": r["t_dmts"] * 1e3 / k, "ms_per_step_sts": r["t_sts"] * 1e3 / k,
+            "pairs": {"small": r["pairs_small"], "big": r["pairs_big"]}}
+
+
+def distill_rate(D, I, torch, s, mdl, n_frames=4):
+    """Force-matching gradient (through the forces) of the small model on
+    frames of the water box against big-model reference forces."""
+    sa, sp, ba, bp = mdl
+    rng = np.random.default_rng(5)
+    frames = np.stack([s.x + rng.normal(scale=0.02, size=s.x.shape) for _ in range(n_frames)])
+    frames -= s.box[0] * np.floor(frames / s.box[0])
+    ctx = D.Context(s, ba, bp, sa, sp)
+    f_ref = []
+    for f in frames:
+        ctx.set_state(f)
+        f_ref.append(ctx.forces(D.BIG)[1])
+    f_ref = np.stack(f_ref)
+    fd = torch.tensor(frames, device="cuda")
+    rd = torch.tensor(f_ref, device="cuda")
+    ctx.force_matching_grad(fd, rd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, _ = ctx.force_matching_grad(fd, rd)
+    t = time.perf_counter() - t0
+    return {"workload": f"{n_frames} frames of the {s.n_atoms}-atom box", "frames_per_s": n_frames / t,
+            "ms_per_frame": t * 1e3 / n_frames, "loss": loss}
 
 
 # ------------------------------------------------------------------- oracle
@@ -328,13 +414,16 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water12288")
     ap.add_argument("--outer-fs", type=float, default=3.0)
     ap.add_argument("--n-inner", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--single-precision", action="store_true", help="measure only --precision")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the vacuum-batch and distillation measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

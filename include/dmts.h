@@ -122,6 +122,7 @@ typedef struct {
  * JSON object; recognised keys: "edge_capacity_factor" (default 1.5, the
  * neighbour-pair capacity relative to the uniform-density estimate),
  * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
+ * "autotune" (default 1: pick the kernels' work granularity by timing),
  * "atoms_per_cta_big" / "atoms_per_cta_small" (atoms per thread block of the
  * force kernels).
  * On success *out holds the new context; on failure *out is NULL. */
@@ -179,6 +180,14 @@ DMTS_API void* dmts_stream(dmts_ctx* ctx);
 /* Number of the library's kernel launches since the context was created
  * (including launches inside CUDA graph replays). */
 DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
+
+/* Work granularity of one model's force kernels: atoms per thread block
+ * (FP32) or atoms per work chunk (BF16), forward and backward. The tuner
+ * (option "autotune", default 1) times a few candidates at the context's
+ * first force evaluation and keeps the fastest. FP32 results do not depend on
+ * the choice; BF16 results can differ at the rounding level (partial sums are
+ * grouped by tile). Returns 1 if tuned, 0 if not yet, or a negative status. */
+DMTS_API int dmts_get_tuning(dmts_ctx* ctx, int which, int* atoms_fwd, int* atoms_bwd);
 
 /* Time one model's force evaluation at the current positions, stage by stage,
  * with CUDA events on the context's stream, averaged over reps (>= 1)

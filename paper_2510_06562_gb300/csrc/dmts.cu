@@ -118,6 +118,7 @@ struct dmts_ctx {
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
     bool broken = false;
+    bool autotune = true, tuned = false;
     // force-matching buffers (allocated on first use)
     float *fm_g = nullptr, *fm_m = nullptr, *fm_mdot = nullptr, *fm_mb = nullptr, *fm_mdb = nullptr,
           *fm_ubar = nullptr, *fm_pe = nullptr, *fm_pa = nullptr;
@@ -540,6 +541,62 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     return DMTS_OK;
 }
 
+// Autotuner: times one force evaluation of each model for a few work
+// granularities (atoms per CTA for the FP32 kernels, atoms per chunk for the
+// persistent tensor-core kernels) and keeps the fastest. The FP32 kernels sum
+// every atom's row in edge order whatever the granularity, so their results
+// do not change; the tensor-core kernels group a row's partial sums by tile,
+// so theirs can change at the rounding level. Runs once per context, at the
+// first evaluation.
+int autotune_models(dmts_ctx* c) {
+    if (!c->autotune || c->tuned) return DMTS_OK;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int rc = DMTS_OK;
+    for (int w = 0; w < 2 && rc == DMTS_OK; ++w) {
+        Model& m = c->m[w];
+        if (!m.present) continue;
+        const bool tc = m.precision == DMTS_BF16_MLP;
+        std::vector<int> cand = tc ? std::vector<int>{4, 8, 16, 32}
+                                   : (m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48});
+        const int lim_f = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, false);
+        const int lim_b = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, true);
+        float best = 1e30f;
+        int best_f = m.apc_fwd, best_b = m.apc_bwd;
+        for (int A : cand) {
+            m.apc_fwd = std::min(A, lim_f);
+            m.apc_bwd = std::min(A, lim_b);
+            if ((rc = reset_flags(c))) break;
+            enqueue_eval(c, w, true);                    // warm-up (sizes capacities)
+            if ((rc = sync_check(c))) break;
+            if (c->h_flags[kFlagOverflow]) {
+                if ((rc = grow_capacity(c))) break;
+                continue;
+            }
+            float total = 0.f;
+            for (int r = 0; r < 3; ++r) {
+                CUDA_TRY(cudaEventRecord(e0, c->stream));
+                enqueue_eval(c, w, true);
+                CUDA_TRY(cudaEventRecord(e1, c->stream));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+                total += t;
+            }
+            if ((rc = sync_check(c))) break;
+            if (total < best) { best = total; best_f = m.apc_fwd; best_b = m.apc_bwd; }
+        }
+        m.apc_fwd = best_f;
+        m.apc_bwd = best_b;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->tuned = true;
+    return rc;
+}
+
 #define CTX_GUARD(c)                                                                         \
     do {                                                                                     \
         if (!(c)) return fail(DMTS_ERR_ARG, "context is NULL");                              \
@@ -646,6 +703,7 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     c->h_off.assign(sys->atom_offset, sys->atom_offset + ns + 1);
     c->h_box.assign(sys->box, sys->box + ns);
     c->rc_max = rc_max;
+    c->autotune = json_number(options, "autotune", 1.0) != 0.0;
     c->cap_factor = json_number(options, "edge_capacity_factor", 1.5);
     if (!(c->cap_factor > 0.0)) c->cap_factor = 1.5;
     const double opt_row_cap = json_number(options, "row_capacity", 0.0);
@@ -761,6 +819,7 @@ int dmts_forces(dmts_ctx* c, int which, double* f_out, double* energy_out, doubl
     LaunchScope ls(c);
     Model& m = c->m[which];
     int rc;
+    if ((rc = autotune_models(c))) return rc;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = reset_flags(c))) return rc;
         enqueue_eval(c, which, true);
@@ -835,6 +894,7 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
     LaunchScope ls(c);
     int rc;
     size_t n3 = (size_t)3 * c->N;
+    if ((rc = autotune_models(c))) return rc;
     if (n_outer > c->ring_len) {
         dfree(c->d_ring);
         c->d_ring = nullptr;
@@ -1047,5 +1107,14 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
 }
 
 long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
+
+int dmts_get_tuning(dmts_ctx* c, int which, int* atoms_fwd, int* atoms_bwd) {
+    if (!c) return fail(DMTS_ERR_ARG, "context is NULL");
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (atoms_fwd) *atoms_fwd = c->m[which].apc_fwd;
+    if (atoms_bwd) *atoms_bwd = c->m[which].apc_bwd;
+    return c->tuned ? 1 : 0;
+}
 
 }  // extern "C"

@@ -29,7 +29,7 @@ SMALL, BIG = 0, 1
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
-            "dmts_force_matching_grad")
+            "dmts_force_matching_grad", "dmts_get_tuning")
 
 
 class DmtsError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_neighbors_noalloc.restype = C.c_int
     lib.dmts_force_matching_grad.argtypes = [P, C.c_int, P, P, P, P]
     lib.dmts_force_matching_grad.restype = C.c_int
+    lib.dmts_get_tuning.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.dmts_get_tuning.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -232,6 +234,14 @@ class Context:
                 [f"atom_fwd_l{l}" for l in range(L)] + [f"edge_bwd_l{l}" for l in range(L)] + \
                 [f"atom_bwd_l{l}" for l in range(L)] + ["energy_sum"]
         return dict(zip(names, out[:n].tolist()))
+
+    def tuning(self, which: int = BIG) -> dict:
+        """Chosen work granularity of one model's kernels."""
+        f, b = C.c_int(0), C.c_int(0)
+        code = load_library().dmts_get_tuning(self._h, which, C.byref(f), C.byref(b))
+        if code < 0:
+            _check(code)
+        return {"tuned": bool(code), "atoms_fwd": f.value, "atoms_bwd": b.value}
 
     @property
     def stream(self) -> int:
