@@ -285,6 +285,7 @@ def run_ours(args):
     if args.extras and world == 1:
         extras["vacuum512"] = vacuum_batch(D, I, torch, main_prec, args, flush)
         extras["distill"] = distill_rate(D, I, torch, s, mdl)
+        extras["polymer100k"] = polymer(D, I, torch, main_prec, args, flush)
 
     if rank != 0:
         return None
@@ -329,6 +330,24 @@ def vacuum_batch(D, I, torch, prec, args, flush):
             "sts_1fs_ns_per_day": k * 1.0 / FS_PER_NS / r["t_sts"] * SEC_PER_DAY,
             "ms_per_step": r["t_dmts"] * 1e3 / k, "ms_per_step_sts": r["t_sts"] * 1e3 / k,
             "pairs": {"small": r["pairs_small"], "big": r["pairs_big"]}}
+
+
+def polymer(D, I, torch, prec, args, flush):
+    """~100k-atom solvated polymer (4 species), DMTS 3 fs / 1 fs vs 1 fs STS,
+    with the dominant kernel's roofline at this size."""
+    s = I.make_solvated_polymer()
+    mdl = models(4)
+    k = max(10, args.steps // 4)
+    r = measure(D, I, torch, s, mdl, prec, argparse.Namespace(steps=k, warmup=3), flush, 3.0, 3, 1)
+    return {"workload": f"solvated polymer, {s.n_atoms} atoms, L={s.box[0]:.2f} A", "steps": k,
+            "dmts_ns_per_day": k * 3.0 / FS_PER_NS / r["t_dmts"] * SEC_PER_DAY,
+            "sts_1fs_ns_per_day": k * 1.0 / FS_PER_NS / r["t_sts"] * SEC_PER_DAY,
+            "ms_per_step": r["t_dmts"] * 1e3 / k, "ms_per_step_sts": r["t_sts"] * 1e3 / k,
+            "atom_force_evals_per_s": k * 4 * s.n_atoms / r["t_dmts"],
+            "pairs": {"small": r["pairs_small"], "big": r["pairs_big"]},
+            "stage_ms": {"big": r["stages_big"], "small": r["stages_small"]},
+            "roofline": roofline_of(D, prec, r["stages_big"], r["pairs_big"], mdl[2]),
+            "tuning": r["tuning"]}
 
 
 def distill_rate(D, I, torch, s, mdl, n_frames=4):

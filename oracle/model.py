@@ -161,6 +161,24 @@ def pair_list(x, atom_offset, box, cutoff, chunk: int = 1024):
     return I[order], J[order]
 
 
+def pair_row(x, i, atom_offset, box, cutoff):
+    """Row i of the pair list (sorted j), by the same FP64 expression as
+    ``pair_list``; for checking sampled rows of systems too large for the
+    full O(N^2) list."""
+    x = np.asarray(x, dtype=np.float64)
+    off = np.asarray(atom_offset, dtype=np.int64)
+    s = int(np.searchsorted(off, i, side="right") - 1)
+    a, b = int(off[s]), int(off[s + 1])
+    L = float(np.asarray(box, dtype=np.float64)[s])
+    dx = torch.as_tensor(x[a:b]) - torch.as_tensor(x[i])[None, :]
+    if L > 0:
+        dx = dx - L * torch.round(dx / L)
+    d2 = (dx[:, 0] * dx[:, 0] + dx[:, 1] * dx[:, 1]) + dx[:, 2] * dx[:, 2]
+    mask = d2 < float(cutoff) * float(cutoff)
+    mask[i - a] = False
+    return (torch.nonzero(mask)[:, 0] + a).numpy()
+
+
 def pair_vectors(x, i, j, atom_offset, box):
     """Minimum-image r_ij = x_j - x_i for the given pairs (differentiable in
     x; the integer image shift carries no derivative)."""

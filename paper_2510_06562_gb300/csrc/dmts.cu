@@ -409,7 +409,7 @@ void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
     else launch_edge_bwd_f32(a, m.F, m.K, c->stream);
 }
 
-void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
+void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true) {
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
     enqueue_neighbors(c, which, quantize);
@@ -439,7 +439,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize) {
         launch_edge_bwd(c, m, b);
         if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
     }
-    launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
+    if (energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
 }
 
 int sync_check(dmts_ctx* c) {
@@ -508,7 +508,7 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
         for (int k = 0; k < n_inner; ++k) {
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, s);
-            enqueue_eval(c, 0, nonper);
+            enqueue_eval(c, 0, nonper, false);       // the small model's energy is not reported
         }
         enqueue_eval(c, 1, false);
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
@@ -917,7 +917,7 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         if ((rc = reset_flags(c))) return rc;
         if (!c->forces_valid) {
             // Algorithm 1, first_step: both forces at the current positions
-            if (c->m[0].present) enqueue_eval(c, 0, true);
+            if (c->m[0].present) enqueue_eval(c, 0, true, false);
             enqueue_eval(c, 1, true);
         }
         if (!c->graph || c->g_n_inner != n_inner || c->g_dt != dt) {

@@ -656,15 +656,17 @@ int max_atoms_per_cta_f32(int F, int K, bool bwd) {
 // ------------------------------------------------------------ reductions
 // Per-system FP64 sums in a fixed order (deterministic): one CTA per system,
 // strided partial sums, then a fixed-shape tree.
-__global__ void k_system_sum(int n_sys, const int* __restrict__ off, const double* __restrict__ v,
-                             double* __restrict__ out, int stride) {
-    __shared__ double sh[256];
+template <int NT>
+__global__ void __launch_bounds__(NT) k_system_sum(int n_sys, const int* __restrict__ off,
+                                                  const double* __restrict__ v, double* __restrict__ out,
+                                                  int stride) {
+    __shared__ double sh[NT];
     int s = blockIdx.x;
     double acc = 0.0;
-    for (int i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) acc += v[i];
+    for (int i = off[s] + threadIdx.x; i < off[s + 1]; i += NT) acc += v[i];
     sh[threadIdx.x] = acc;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = NT / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
@@ -673,7 +675,9 @@ __global__ void k_system_sum(int n_sys, const int* __restrict__ off, const doubl
 
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
                        int stride, cudaStream_t s) {
-    k_system_sum<<<n_sys, 256, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
+    // one CTA per system: wide for a single large system, narrow for many molecules
+    if (n_sys <= 8) k_system_sum<1024><<<n_sys, 1024, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
+    else k_system_sum<64><<<n_sys, 64, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
     count_launch();
 }
 

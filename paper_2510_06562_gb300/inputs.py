@@ -286,6 +286,97 @@ def make_vacuum_batch(n_mol: int = 512, n_min: int = 10, n_max: int = 60,
                   name=f"vacuum{n_mol}")
 
 
+def make_solvated_polymer(n_heavy: int = 3000, n_total: int = 100_000, density: float = 1.0,
+                          seed: int = 0) -> System:
+    """A self-avoiding random-walk chain of ``n_heavy`` heavy atoms (C:N:O =
+    6:2:2 in seeded random order, bonds 1.5 A, no heavy atom within 2.0 A of
+    an earlier one except its chain neighbour), hydrogens added to fill each
+    heavy atom's valence (C 4, N 3, O 2, minus its chain bonds) at C-H 1.09,
+    N-H 1.01, O-H 0.96 A in random directions at least 1.0 A from every other
+    atom, then rigid waters (as in ``make_water``) on a cubic lattice with
+    random orientations, dropping sites within 2.5 A of the polymer, so that
+    the total is ~``n_total`` atoms at ``density`` g/cm^3 in a periodic
+    cubic box. Species: 0 = H, 1 = C, 2 = N, 3 = O."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    n_c = n_heavy * 6 // 10
+    n_n = n_heavy * 2 // 10
+    elem = rng.permutation(np.repeat(np.array([1, 2, 3]), [n_c, n_n, n_heavy - n_c - n_n]))
+    valence = np.array([1, 4, 3, 2])          # by species index H, C, N, O
+    chain_bonds = np.full(n_heavy, 2)
+    chain_bonds[0] = chain_bonds[-1] = 1
+    n_h = np.maximum(valence[elem] - chain_bonds, 0)
+    heavy_mass = np.array([MASS_H, MASS_C, MASS_N, MASS_O])
+    m_poly = heavy_mass[elem].sum() + n_h.sum() * MASS_H
+    n_poly = n_heavy + int(n_h.sum())
+    n_water = (n_total - n_poly) // 3
+    m_total = m_poly + n_water * (MASS_O + 2 * MASS_H)
+    L = (m_total * 1.66053906660 / density) ** (1.0 / 3.0)   # amu -> g is 1.6605e-24, A^3 -> cm^3 is 1e-24
+
+    def wrap(p):
+        return p - L * np.floor(p / L)
+
+    def min_image(d):
+        return d - L * np.round(d / L)
+
+    # heavy-atom chain
+    chain = np.empty((n_heavy, 3))
+    chain[0] = rng.uniform(0, L, 3)
+    k = 1
+    while k < n_heavy:
+        v = rng.normal(size=3)
+        p = chain[k - 1] + 1.5 * v / np.linalg.norm(v)
+        if k >= 2:
+            d = np.linalg.norm(min_image(chain[:k - 1] - p), axis=1)
+            if d.min() < 2.0:
+                continue
+        chain[k] = wrap(p)
+        k += 1
+    # hydrogens
+    bond_h = np.array([0.0, 1.09, 1.01, 0.96])
+    placed = [chain]
+    tree = cKDTree(chain, boxsize=L)
+    hs, h_parent = [], []
+    for a in range(n_heavy):
+        for _ in range(n_h[a]):
+            for _try in range(200):
+                v = rng.normal(size=3)
+                p = wrap(chain[a] + bond_h[elem[a]] * v / np.linalg.norm(v))
+                near = tree.query_ball_point(p, 1.0)
+                if any(j != a for j in near):
+                    continue
+                if hs and np.min(np.linalg.norm(min_image(np.asarray(hs) - p), axis=1)) < 1.0:
+                    continue
+                hs.append(p)
+                h_parent.append(a)
+                break
+            else:
+                raise RuntimeError("could not place a hydrogen")
+    poly = np.concatenate([chain, np.asarray(hs).reshape(-1, 3)])
+    poly_species = np.concatenate([elem, np.zeros(len(hs), dtype=elem.dtype)])
+    # waters on a lattice, away from the polymer
+    n_side = int(np.ceil((n_water * 1.15) ** (1.0 / 3.0)))
+    g = (np.arange(n_side) + 0.5) * (L / n_side)
+    sites = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    ptree = cKDTree(poly, boxsize=L)
+    free = np.array([len(x) == 0 for x in ptree.query_ball_point(sites, 2.5)])
+    sites = sites[free]
+    if len(sites) < n_water:
+        raise RuntimeError("not enough free lattice sites for the water")
+    sites = sites[rng.choice(len(sites), n_water, replace=False)]
+    half = np.deg2rad(104.5) / 2
+    local = np.array([[0.0, 0.0, 0.0], [0.96 * np.sin(half), 0.0, 0.96 * np.cos(half)],
+                      [-0.96 * np.sin(half), 0.0, 0.96 * np.cos(half)]])
+    R = _random_rotations(rng, n_water)
+    wat = wrap((sites[:, None, :] + np.einsum("mab,kb->mka", R, local)).reshape(-1, 3))
+    x = np.concatenate([poly, wat])
+    species = np.concatenate([poly_species, np.tile(np.array([3, 0, 0]), n_water)]).astype(np.int32)
+    mass = heavy_mass[species]
+    return System(x=x, species=species, mass=mass, atom_offset=np.array([0, len(x)], dtype=np.int32),
+                  box=np.array([L]), n_species=4, name=f"polymer{len(x)}")
+
+
 def maxwell_boltzmann(mass: np.ndarray, temperature: float, seed: int = 1,
                       atom_offset: np.ndarray | None = None) -> np.ndarray:
     """Velocities (A/fs) from the Maxwell-Boltzmann distribution at

@@ -2,6 +2,7 @@
 profilers (no timing, no output besides a one-line summary).
 
     python -m paper_2510_06562_gb300.profile_eval --precision bf16 --which big --evals 3
+    python -m paper_2510_06562_gb300.profile_eval --precision bf16 --respa 6 --evals 1
 """
 from __future__ import annotations
 
@@ -19,6 +20,7 @@ def main():
     ap.add_argument("--which", default="big", choices=["small", "big"])
     ap.add_argument("--system", default="water12288", choices=["water192", "water12288"])
     ap.add_argument("--evals", type=int, default=3)
+    ap.add_argument("--respa", type=int, default=0, help="instead: this many 3 fs / 1 fs outer steps")
     args = ap.parse_args()
     s = I.water_12288(0) if args.system == "water12288" else I.water_192(0)
     prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
@@ -26,6 +28,8 @@ def main():
     with D.Context(s, ba, I.init_params(ba, 3), sa, I.init_params(sa, 2), precision=prec) as ctx:
         ctx.set_state(s.x)
         which = D.BIG if args.which == "big" else D.SMALL
+        if args.respa:
+            ctx.respa_step(args.respa, 3.0, 3, energies=False)
         for _ in range(args.evals):
             E, F = ctx.forces(which)
     print(f"{args.system} {args.which} {args.precision}: E={E[0]:.6f} eV, rms F={np.sqrt(np.mean(F ** 2)):.4f} eV/A")

@@ -395,3 +395,62 @@ def test_force_matching_autograd_function():
         _, g = ctx.force_matching_grad(frames, f_ref)
     np.testing.assert_allclose(theta.grad.numpy(), g, rtol=0, atol=0)
     assert float(loss) > 0
+
+
+# ------------------------------------------------------------ solvated polymer (4 species)
+
+@pytest.mark.parametrize("prec", [D.FP32, D.BF16_MLP])
+def test_polymer6000_energy_forces(prec):
+    pytest.importorskip("scipy")
+    s = I.make_solvated_polymer(n_heavy=300, n_total=6000, seed=1)
+    sa, sp, ba, bp = _models(4)
+    with D.Context(s, ba, bp, sa, sp, precision=prec) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            gi, gj = _pairs(*ctx.neighbors(which))
+            oi, oj = M.pair_list(s.x, s.atom_offset, s.box, arch.cutoff)
+            np.testing.assert_array_equal(gi, oi)
+            np.testing.assert_array_equal(gj, oj)
+            E, F = ctx.forces(which)
+            Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box, (oi, oj))
+            de, err = float(abs(E[0] - Er[0]) / s.n_atoms), _rmse(F, Fr)
+            print(json.dumps({"system": "polymer6000", "precision": int(prec), "model": int(which),
+                              "dE_per_atom": de, "force_rmse": err}))
+            if prec == D.FP32:
+                assert de <= E_TOL and err <= F_TOL
+            else:
+                assert de <= 5e-3 and err <= F_TOL_BF16
+
+
+@pytest.mark.parametrize("prec", [D.FP32, D.BF16_MLP])
+def test_polymer100k_sampled_rows_and_invariants(prec):
+    """~100k atoms: too many for the O(N^2) oracle, so sampled neighbour rows
+    are compared bit-exactly with the oracle's row, and forces and energies
+    are checked against properties that hold at any size."""
+    pytest.importorskip("scipy")
+    s = I.make_solvated_polymer()
+    sa, sp, ba, bp = _models(4)
+    rng = np.random.default_rng(0)
+    sample = np.concatenate([[0, 1, 2999, 3000, s.n_atoms - 1], rng.choice(s.n_atoms, 40, replace=False)])
+    with D.Context(s, ba, bp, sa, sp, precision=prec) as ctx:
+        ctx.set_state(s.x)
+        for which, arch in ((D.SMALL, sa), (D.BIG, ba)):
+            rp, col = ctx.neighbors(which)
+            for i in sample:
+                np.testing.assert_array_equal(col[rp[i]:rp[i + 1]], M.pair_row(s.x, int(i), s.atom_offset, s.box, arch.cutoff))
+        E0, F0 = ctx.forces(D.BIG)
+        rms = float(np.sqrt(np.mean(F0 ** 2)))
+        net = np.abs(F0.sum(axis=0)).max()
+        shift = np.array([3.3, -1.7, 2.2])
+        xs = s.x + shift
+        xs -= s.box[0] * np.floor(xs / s.box[0])
+        ctx.set_state(xs)
+        E1, F1 = ctx.forces(D.BIG)
+        print(json.dumps({"system": "polymer100k", "precision": int(prec), "n_atoms": s.n_atoms,
+                          "net_force_rel": float(net / (s.n_atoms * rms)), "dE_shift_per_atom": float(abs(E1[0] - E0[0]) / s.n_atoms),
+                          "force_rmse_shift": _rmse(F1, F0)}))
+        assert net <= (1e-5 if prec == D.FP32 else 1e-3) * s.n_atoms * rms
+        assert abs(E1[0] - E0[0]) / s.n_atoms <= (E_TOL if prec == D.FP32 else 5e-4)
+        assert _rmse(F1, F0) <= (F_TOL if prec == D.FP32 else F_TOL_BF16)
+        e = ctx.respa_step(3, 3.0, 3)
+        assert np.all(np.isfinite(e))

@@ -74,3 +74,12 @@ def test_systems_do_not_interact_and_small_box_rejected():
 def test_empty_and_single_atom():
     i, j = M.pair_list(np.zeros((1, 3)), [0, 1], [0.0], 5.0)
     assert len(i) == 0 and len(j) == 0
+
+
+def test_pair_row_equals_rows_of_pair_list():
+    rng = np.random.default_rng(4)
+    L, rc = 12.0, 5.0
+    x = rng.uniform(0, L, size=(80, 3))
+    i, j = M.pair_list(x, [0, 80], [L], rc)
+    for a in (0, 17, 79):
+        np.testing.assert_array_equal(M.pair_row(x, a, [0, 80], [L], rc), j[i == a])
