@@ -45,6 +45,33 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Per-edge feature rows in shared memory: [kT][F] floats, unpadded, with the
+// 16-byte chunks of row e XOR-swizzled by (e mod 8). One thread reading its
+// own row chunk by chunk, and one warp reading 32 consecutive floats of one
+// row, both touch 32 distinct banks.
+template <int F>
+__device__ __forceinline__ int prow(int e, int f) {
+    return e * F + ((((f >> 2) ^ (e & 7))) << 2) + (f & 3);
+}
+
+// Gather row j of src (F floats per row) for each of the warp's 32 edges into
+// the swizzled buffer. Each row is copied by F/4 consecutive lanes, 16 bytes
+// each, so one warp instruction reads 32 / (F/4) whole rows: the loads are
+// coalesced per row instead of one scattered row per lane.
+template <int F>
+__device__ __forceinline__ void gather_rows(float* buf, const float* __restrict__ src, int j) {
+    constexpr int TPR = F / 4;
+    constexpr int RPI = 32 / TPR;
+    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
+    const int sub = lane / TPR, ch = lane % TPR;
+#pragma unroll
+    for (int rr = 0; rr < 32; rr += RPI) {
+        const int je = __shfl_sync(0xffffffffu, j, rr + sub);
+        const int e = w0 + rr + sub;
+        cp_async16(buf + e * F + ((ch ^ (e & 7)) << 2), src + (size_t)je * F + ch * 4);
+    }
+}
+
 // Edge indices and fixed-point positions of one tile edge, loaded one tile ahead.
 struct EdgeIn {
     int j, i;
@@ -134,7 +161,6 @@ struct VecSlots {
 template <int F>
 __device__ __forceinline__ void warp_vec_segments(const float* sP, const int* srow, VecSlots<F>* vs,
                                                   float* __restrict__ out, int a0) {
-    constexpr int PS = F + 4;
     constexpr int NF = F / 32;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // row of every edge of the warp, segment starts and ends as warp-uniform bit masks
@@ -150,7 +176,7 @@ __device__ __forceinline__ void warp_vec_segments(const float* sP, const int* sr
         vs->row[w][0] = -1;
         vs->row[w][1] = -1;
     }
-    const float* base = sP + (32 * w) * PS + lane;
+    const float* base = sP + (32 * w) * F;
     float acc[NF];
 #pragma unroll
     for (int c = 0; c < NF; ++c) acc[c] = 0.f;
@@ -160,7 +186,7 @@ __device__ __forceinline__ void warp_vec_segments(const float* sP, const int* sr
             const bool st = (starts >> e) & 1u;
 #pragma unroll
             for (int c = 0; c < NF; ++c) {
-                const float v = base[e * PS + 32 * c];
+                const float v = base[prow<F>(e, lane + 32 * c)];
                 acc[c] = st ? v : acc[c] + v;
             }
             if ((ends >> e) & 1u) {
@@ -244,7 +270,7 @@ struct FwdSmem {
     unsigned char a1[kT * kKP * 2];
     unsigned char a2[kT * F * 2];
     float b1[F], b2[F];
-    float P[kT * (F + 4)];
+    float P[kT * F];                    // u_j rows, then messages (swizzled rows)
     int row[kT];
     VecSlots<F> vs;
     ScalSlots<1> ss;
@@ -256,7 +282,6 @@ template <int F>
 __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
-    constexpr int PS = F + 4;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
     const int A = a.atoms_per_cta;
@@ -309,13 +334,9 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const int j = valid ? ex.j : a0;
             const int row = valid ? ex.i - a0 : -1;
             load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
-            // the message needs u_j: start its copy into this thread's row of P now
-            {
-                const float* uj = a.u + (size_t)j * F;
-#pragma unroll
-                for (int c = 0; c < F; c += 4) cp_async16(S.P + tid * PS + c, uj + c);
-                cp_async_commit();
-            }
+            // the message needs u_j: start copying the warp's rows into P now
+            gather_rows<F>(S.P, a.u, j);
+            cp_async_commit();
             float fc = 0.f, rep = 0.f;
             {
                 float eb[kKP], dfc;
@@ -372,17 +393,18 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
             phase ^= 1;
             fence_after_sync();
-            cp_async_wait();                               // this thread's u_j row is in P
+            cp_async_wait();                               // the warp's u_j rows are in P
+            __syncwarp();
             {
-                float* pr = S.P + tid * PS;
 #pragma unroll
                 for (int c = 0; c < F; c += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + F + c, v);
 #pragma unroll
                     for (int q = 0; q < 16; q += 4) {
-                        float4 u4 = *reinterpret_cast<const float4*>(pr + c + q);
-                        *reinterpret_cast<float4*>(pr + c + q) = make_float4(
+                        float* p4 = S.P + prow<F>(tid, c + q);
+                        float4 u4 = *reinterpret_cast<const float4*>(p4);
+                        *reinterpret_cast<float4*>(p4) = make_float4(
                             fc * (v[q] + S.b2[c + q]) * u4.x, fc * (v[q + 1] + S.b2[c + q + 1]) * u4.y,
                             fc * (v[q + 2] + S.b2[c + q + 2]) * u4.z, fc * (v[q + 3] + S.b2[c + q + 3]) * u4.w);
                     }
@@ -432,10 +454,10 @@ struct BwdSmem {
     unsigned char a4[kT * kKP * 2];     // basis derivative
     unsigned char a2[kT * F * 2];       // SiLU hidden, then g
     float b1[F], b2[F];
-    float P[kT * (F + 4)];              // ubar messages
+    float P[kT * F];                    // mbar_j rows, then ubar messages (swizzled rows)
+    float U[kT * F];                    // u_j rows (swizzled)
     int row[kT];
-    VecSlots<F> vs;
-    ScalSlots<9> ss;
+    ScalSlots<9> ss;                    // the vector slots live in a1 (free once D1 is complete)
     uint64_t mbar;
     uint32_t taddr;
 };
@@ -444,7 +466,8 @@ template <int F>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdSmem<F>& S = *reinterpret_cast<BwdSmem<F>*>(smraw);
-    constexpr int PS = F + 4;
+    static_assert(sizeof(VecSlots<F>) <= sizeof(S.a1), "vector slots must fit the basis tile");
+    VecSlots<F>* vs = reinterpret_cast<VecSlots<F>*>(S.a1);
     constexpr int TCOLS = 4 * F;   // D1 | D4 | D2 | D3
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
@@ -509,13 +532,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             const int j = valid ? ex.j : a0;
             const int row = valid ? ex.i - a0 : -1;
             load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
-            // mbar_j is needed by g and the ubar message: copy it into this thread's row of P
-            {
-                const float* mj = a.mbar + (size_t)j * F;
-#pragma unroll
-                for (int c = 0; c < F; c += 4) cp_async16(S.P + tid * PS + c, mj + c);
-                cp_async_commit();
-            }
+            // g needs mbar_j and u_j, the ubar message mbar_j: start the warp's row copies now
+            gather_rows<F>(S.P, a.mbar, j);
+            gather_rows<F>(S.U, a.u, j);
+            cp_async_commit();
             float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
             {
                 float eb[kKP], db[kKP];
@@ -576,12 +596,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
             phase ^= 1;
             fence_after_sync();
-            cp_async_wait();                               // this thread's mbar_j row is in P
+            cp_async_wait();                               // the warp's mbar_j and u_j rows are in P, U
+            __syncwarp();
             float gphi = 0.f;
             {
                 const int i = row < 0 ? a0 : a0 + row;
-                const float* uj = a.u + (size_t)j * F;
-                float* pr = S.P + tid * PS;
                 const float* ui = a.u + (size_t)i * F;
                 const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
@@ -590,8 +609,9 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     tmem_ld16(tD2 + lane_base + c, v);
 #pragma unroll
                     for (int q = 0; q < 16; q += 4) {
-                        float4 u4 = __ldg(reinterpret_cast<const float4*>(uj + c + q));
-                        float4 m4 = *reinterpret_cast<const float4*>(pr + c + q);
+                        const int o = prow<F>(tid, c + q);
+                        float4 u4 = *reinterpret_cast<const float4*>(S.U + o);
+                        float4 m4 = *reinterpret_cast<const float4*>(S.P + o);
                         float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
                         float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
                         float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
@@ -601,7 +621,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                         g[q + 2] = mi4.z * u4.z + m4.z * ui4.z;
                         g[q + 3] = mi4.w * u4.w + m4.w * ui4.w;
                         gphi += g[q] * ph0 + g[q + 1] * ph1 + g[q + 2] * ph2 + g[q + 3] * ph3;
-                        *reinterpret_cast<float4*>(pr + c + q) =
+                        *reinterpret_cast<float4*>(S.P + o) =
                             make_float4(fc * ph0 * m4.x, fc * ph1 * m4.y, fc * ph2 * m4.z, fc * ph3 * m4.w);
                     }
                     st_row8(S.a2, tid, c, F, g);
@@ -652,10 +672,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             }
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            if (need_ubar) warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, a0);
+            if (need_ubar) warp_vec_segments<F>(S.P, S.row, vs, a.msg_out, a0);
             __syncthreads();
             if (need_ubar && tid < F) {
-                merge_vec_slots<F>(&S.vs, tid, cur, run, a.msg_out, a0);
+                merge_vec_slots<F>(vs, tid, cur, run, a.msg_out, a0);
             } else if (tid >= F && tid < F + 9) {
                 const int c = tid - F;
                 for (int w = 0; w < 4; ++w)
@@ -673,6 +693,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                         }
                     }
             }
+            __syncthreads();                               // slots read before the next basis overwrites a1
         }
         if (cur >= 0) {
             if (need_ubar && tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
