@@ -124,7 +124,16 @@ typedef struct {
  * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
  * "autotune" (default 1: pick the kernels' work granularity by timing),
  * "atoms_per_cta_big" / "atoms_per_cta_small" (atoms per thread block of the
- * force kernels).
+ * force kernels), "skin" (default 1.0 Angstrom, in [0, 10]: Verlet-skin
+ * neighbour lists; 0 builds the pair list from scratch at every evaluation).
+ * With a skin, candidate rows of all j within rc + skin are kept from the
+ * last rebuild and filtered with the exact cutoff test at every evaluation,
+ * which yields the same pair set as a fresh build; both models' rows are
+ * rebuilt, on the device, once some atom has moved by skin / 2 since then
+ * (the model with the smaller cutoff filters its rows from the other's).
+ * The paper does not describe its neighbour search; this is an
+ * implementation choice that leaves every result unchanged up to the order
+ * of floating-point additions.
  * On success *out holds the new context; on failure *out is NULL. */
 DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big,
                 const dmts_system_desc* sys, const char* options, dmts_ctx** out);
@@ -181,6 +190,11 @@ DMTS_API void* dmts_stream(dmts_ctx* ctx);
  * (including launches inside CUDA graph replays). */
 DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
 
+/* Verlet-skin statistics since the context was created: displacement checks
+ * run (one per evaluation at new positions) and candidate-row rebuilds among
+ * them. Both 0 when the skin is 0. Synchronises the context's stream. */
+DMTS_API int dmts_neighbor_stats(dmts_ctx* ctx, long long* n_checks, long long* n_rebuilds);
+
 /* Work granularity of one model's force kernels: atoms per thread block
  * (FP32) or atoms per work chunk (BF16), forward and backward. The tuner
  * (option "autotune", default 1) times a few candidates at the context's
@@ -193,7 +207,8 @@ DMTS_API int dmts_get_tuning(dmts_ctx* ctx, int which, int* atoms_fwd, int* atom
  * with CUDA events on the context's stream, averaged over reps (>= 1)
  * evaluations. ms_out[n_out] receives milliseconds per evaluation for:
  *   [0] quantisation, cell list and neighbour list,
- *   [1] species embedding,
+ *   [1] species embedding (no work: h^0 and u^0 depend only on species and
+ *       parameters and are built once per parameter upload),
  *   [2 + l] forward edge pass of layer l (l < n_layers),
  *   [2 + n_layers + l] per-atom MLPs after it,
  *   [2 + 2 n_layers + l] backward edge pass of layer l,

@@ -9,80 +9,97 @@
 //   backward, layer l >= 1:  gh <- gh + ubar^l W_in^{l T};
 //                            mbar^{l-1} = ((gh U2^{l-1 T}) * SiLU'(z^{l-1})) U1^{l-1 T}
 //
-// A CTA of 256 threads takes A = 4096 / F atoms; every stage is an
-// [A x F] x [F x F] product with each thread owning 4 atoms x 4 features,
-// the input kept transposed in shared memory ([k][atom]) and the weight
-// matrix staged as W[k][f] (or its transpose).
+// Layer 0 reads h^0 = A[Z_i] from the per-atom copy built once per parameter
+// upload. A CTA takes A = 32 atoms; each stage is an [A x F] x [F x F]
+// product, each thread owning 4 atoms x 4 features. Inputs stay in their
+// natural [atom][k] layout in shared memory; the weight matrix of the next
+// stage (row-major; the transposed ones are copies prepared on the host)
+// streams in with cp.async while the current stage computes.
 #include "internal.cuh"
 
 namespace dmts {
 
 namespace {
 
-constexpr int kAT = 256;
-
 template <int F>
 struct AtomTile {
-    static constexpr int A = 4096 / F;      // atoms per CTA
-    static constexpr int AG = A / 4;        // atom groups
+    static constexpr int A = 32;            // atoms per CTA
     static constexpr int FG = F / 4;        // feature groups
-    static constexpr int IS = A + 4;        // row stride of transposed inputs [k][a]
+    static constexpr int NT = (A / 4) * FG; // threads per CTA: 128 (F = 64) or 64 (F = 32)
+    static constexpr int XS = F + 4;        // row stride of per-atom rows [a][k]
     static constexpr int WS = F + 4;        // row stride of staged weights [k][f]
-    static_assert(AG * FG == kAT, "tile");
+    static constexpr int SMEM = (2 * A * XS + 2 * F * WS) * 4;
 };
 
 __device__ __forceinline__ float sig(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// Start copying the row-major F x F matrix W into Ws [F][WS] (closes a commit group).
 template <int F>
-__device__ __forceinline__ void load_w(float* Ws, const float* __restrict__ W, bool transpose) {
+__device__ __forceinline__ void stage_w(float* Ws, const float* __restrict__ W) {
     using T = AtomTile<F>;
-    __syncthreads();
-    for (int t = threadIdx.x; t < F * F; t += kAT) {
-        int r = t / F, c = t % F;            // W[r][c], row-major
-        if (transpose) Ws[c * T::WS + r] = __ldg(W + t);
-        else Ws[r * T::WS + c] = __ldg(W + t);
+    for (int t = threadIdx.x; t < F * F / 4; t += T::NT) {
+        const int r = t / (F / 4), c = (t % (F / 4)) * 4;
+        cp_async16(Ws + r * T::WS + c, W + (size_t)r * F + c);
     }
-    __syncthreads();
+    cp_commit();
 }
 
-// acc[a][f] = sum_k inT[k][a0 + a] * Ws[k][f0 + f]
+// Start copying rows base .. base + A - 1 of the [N][F] array src into X [A][XS]
+// (rows past N are zero); joins the next commit group.
 template <int F>
-__device__ __forceinline__ void gemm4x4(const float* inT, const float* Ws, int a0, int f0, float acc[4][4]) {
+__device__ __forceinline__ void stage_rows(float* X, const float* __restrict__ src, int base, int n_atoms) {
+    using T = AtomTile<F>;
+    for (int t = threadIdx.x; t < T::A * F / 4; t += T::NT) {
+        const int a = t / (F / 4), c = (t % (F / 4)) * 4;
+        if (base + a < n_atoms) cp_async16(X + a * T::XS + c, src + (size_t)(base + a) * F + c);
+        else *reinterpret_cast<float4*>(X + a * T::XS + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// acc[a][f] = sum_k X[a0 + a][k] * Ws[k][f0 + f], k ascending.
+template <int F>
+__device__ __forceinline__ void gemm4x4(const float* X, const float* Ws, int a0, int f0, float acc[4][4]) {
     using T = AtomTile<F>;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int f = 0; f < 4; ++f) acc[a][f] = 0.f;
-#pragma unroll 8
-    for (int k = 0; k < F; ++k) {
-        float4 x = *reinterpret_cast<const float4*>(inT + k * T::IS + a0);
-        float4 w = *reinterpret_cast<const float4*>(Ws + k * T::WS + f0);
-        float xa[4] = {x.x, x.y, x.z, x.w}, wf[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll 4
+    for (int k = 0; k < F; k += 4) {
+        float xv[4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a) {
+            const float4 x = *reinterpret_cast<const float4*>(X + (a0 + a) * T::XS + k);
+            xv[a][0] = x.x; xv[a][1] = x.y; xv[a][2] = x.z; xv[a][3] = x.w;
+        }
 #pragma unroll
-            for (int f = 0; f < 4; ++f) acc[a][f] += xa[a] * wf[f];
+        for (int kk = 0; kk < 4; ++kk) {
+            const float4 w = *reinterpret_cast<const float4*>(Ws + (k + kk) * T::WS + f0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                acc[a][0] += xv[a][kk] * w.x;
+                acc[a][1] += xv[a][kk] * w.y;
+                acc[a][2] += xv[a][kk] * w.z;
+                acc[a][3] += xv[a][kk] * w.w;
+            }
+        }
     }
 }
 
-// Store v[a][f] transposed into outT[k = f][a].
 template <int F>
-__device__ __forceinline__ void store_t(float* outT, int a0, int f0, const float v[4][4]) {
+__device__ __forceinline__ void put_rows(float* X, int a0, int f0, const float v[4][4]) {
     using T = AtomTile<F>;
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
-        *reinterpret_cast<float4*>(outT + (f0 + f) * T::IS + a0) = make_float4(v[0][f], v[1][f], v[2][f], v[3][f]);
-}
-
-// Load rows [atom][F] of a global [N][F] array into inT (transposed), zero past N.
-template <int F>
-__device__ __forceinline__ void load_rows_t(float* inT, const float* __restrict__ src, int base, int n_atoms) {
-    using T = AtomTile<F>;
-    for (int t = threadIdx.x; t < T::A * F; t += kAT) {
-        int a = t / F, f = t % F;
-        int i = base + a;
-        inT[f * T::IS + a] = i < n_atoms ? src[(size_t)i * F + f] : 0.f;
-    }
+    for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4*>(X + (a0 + a) * T::XS + f0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
 }
 
 template <int F>
@@ -90,7 +107,7 @@ __device__ __forceinline__ void store_rows(float* __restrict__ dst, int base, in
                                            const float v[4][4]) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        int i = base + a0 + a;
+        const int i = base + a0 + a;
         if (i < n_atoms)
             *reinterpret_cast<float4*>(dst + (size_t)i * F + f0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
     }
@@ -101,19 +118,29 @@ __device__ __forceinline__ void load_rows4(float v[4][4], const float* __restric
                                            int a0, int f0) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        int i = base + a0 + a;
-        float4 x = i < n_atoms ? *reinterpret_cast<const float4*>(src + (size_t)i * F + f0) : make_float4(0, 0, 0, 0);
+        const int i = base + a0 + a;
+        const float4 x = i < n_atoms ? *reinterpret_cast<const float4*>(src + (size_t)i * F + f0)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         v[a][0] = x.x; v[a][1] = x.y; v[a][2] = x.z; v[a][3] = x.w;
     }
 }
 
+// Transposed F x F copies: W_in^T, U1^T, U2^T of every layer, then R1^T.
+__device__ __forceinline__ const float* wt_of(const PotArgs& p, int F, int l, int which) {
+    return p.PT + ((size_t)3 * l + which) * F * F;
+}
+__device__ __forceinline__ const float* r1t_of(const PotArgs& p, int F) {
+    return p.PT + (size_t)3 * p.n_layers * F * F;
+}
+
 template <int F>
-__global__ void __launch_bounds__(kAT) k_atom_fwd(PotArgs p, const float* __restrict__ msg) {
+__global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const float* __restrict__ msg) {
     using T = AtomTile<F>;
     extern __shared__ float4 smem4[];
-    float* X = reinterpret_cast<float*>(smem4);      // [F][IS]
-    float* Y = X + F * T::IS;                        // [F][IS]
-    float* Ws = Y + F * T::IS;                       // [F][WS]
+    float* X = reinterpret_cast<float*>(smem4);      // [A][XS]
+    float* Y = X + T::A * T::XS;                     // [A][XS]
+    float* W0 = Y + T::A * T::XS;                    // [F][WS]
+    float* W1 = W0 + F * T::WS;                      // [F][WS]
     __shared__ float sE[T::A];
     const int l = p.layer;
     const int base = blockIdx.x * T::A;
@@ -123,12 +150,16 @@ __global__ void __launch_bounds__(kAT) k_atom_fwd(PotArgs p, const float* __rest
     const bool last = (l == p.n_layers - 1);
     float z[4][4], v[4][4], h[4][4];
 
-    load_rows_t<F>(X, msg, base, p.n_atoms);
-    load_w<F>(Ws, P + p.off.U1[l], false);
-    gemm4x4<F>(X, Ws, a0, f0, z);
+    stage_rows<F>(X, msg, base, p.n_atoms);
+    stage_w<F>(W0, P + p.off.U1[l]);                                     // group: message rows + U1
+    stage_w<F>(W1, P + p.off.U2[l]);                                     // group: U2
+    load_rows4<F>(h, p.h_in, base, p.n_atoms, a0, f0);
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(X, W0, a0, f0, z);                                        // z = m U1 + c1
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        float c1 = __ldg(P + p.off.c1[l] + f0 + f);
+        const float c1 = __ldg(P + p.off.c1[l] + f0 + f);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             z[a][f] += c1;
@@ -136,136 +167,151 @@ __global__ void __launch_bounds__(kAT) k_atom_fwd(PotArgs p, const float* __rest
         }
     }
     store_rows<F>(p.z, base, p.n_atoms, a0, f0, z);
-    store_t<F>(Y, a0, f0, v);
-    load_w<F>(Ws, P + p.off.U2[l], false);
-    gemm4x4<F>(Y, Ws, a0, f0, v);
-    load_rows4<F>(h, p.h, base, p.n_atoms, a0, f0);
+    put_rows<F>(Y, a0, f0, v);
+    __syncthreads();                                                     // W0 read, Y complete
+    stage_w<F>(W0, last ? P + p.off.R1 : P + p.off.W_in[l + 1]);
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(Y, W1, a0, f0, v);                                        // h += SiLU(z) U2 + c2
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        float c2 = __ldg(P + p.off.c2[l] + f0 + f);
+        const float c2 = __ldg(P + p.off.c2[l] + f0 + f);
 #pragma unroll
         for (int a = 0; a < 4; ++a) h[a][f] += v[a][f] + c2;
     }
     store_rows<F>(p.h, base, p.n_atoms, a0, f0, h);
-    store_t<F>(X, a0, f0, h);
+    put_rows<F>(X, a0, f0, h);
+    __syncthreads();                                                     // W1 read, X complete
     if (!last) {
-        load_w<F>(Ws, P + p.off.W_in[l + 1], false);
-        gemm4x4<F>(X, Ws, a0, f0, v);
+        cp_wait<0>();
+        __syncthreads();
+        gemm4x4<F>(X, W0, a0, f0, v);                                    // u^{l+1} = h W_in^{l+1}
         store_rows<F>(p.u_next, base, p.n_atoms, a0, f0, v);
         return;
     }
-    // readout and its adjoint
-    load_w<F>(Ws, P + p.off.R1, false);
-    gemm4x4<F>(X, Ws, a0, f0, v);
+    stage_w<F>(W1, r1t_of(p, F));
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(X, W0, a0, f0, v);                                        // q = h R1 + d1
     float e_part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        float d1 = __ldg(P + p.off.d1 + f0 + f), r2 = __ldg(P + p.off.R2 + f0 + f);
+        const float d1 = __ldg(P + p.off.d1 + f0 + f), r2 = __ldg(P + p.off.R2 + f0 + f);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            float q = v[a][f] + d1;
-            float s = sig(q);
+            const float q = v[a][f] + d1;
+            const float s = sig(q);
             e_part[a] += q * s * r2;
-            v[a][f] = s * (1.f + q * (1.f - s)) * r2;     // dE/dq
+            v[a][f] = s * (1.f + q * (1.f - s)) * r2;                  // dE/dq
         }
     }
     // sum the energy terms over the FG threads of this atom group (consecutive lanes)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
+#pragma unroll
         for (int o = T::FG / 2; o > 0; o >>= 1) e_part[a] += __shfl_xor_sync(0xffffffffu, e_part[a], o);
     if (fg == 0)
+#pragma unroll
         for (int a = 0; a < 4; ++a) sE[a0 + a] = e_part[a];
-    store_t<F>(Y, a0, f0, v);
-    load_w<F>(Ws, P + p.off.R1, true);
-    gemm4x4<F>(Y, Ws, a0, f0, v);                    // gh = gq R1^T
-    store_rows<F>(p.gh, base, p.n_atoms, a0, f0, v);
-    store_t<F>(X, a0, f0, v);
-    for (int a = tid; a < T::A; a += kAT) {
-        int i = base + a;
+    put_rows<F>(Y, a0, f0, v);
+    __syncthreads();                                                     // W0 read, Y and sE complete
+    stage_w<F>(W0, wt_of(p, F, l, 2));                                   // U2^T
+    for (int a = tid; a < T::A; a += T::NT) {
+        const int i = base + a;
         if (i < p.n_atoms)
             p.Ei[i] = (double)sE[a] + (double)__ldg(P + p.off.d2) + (double)__ldg(P + p.off.e0 + p.species[i]) +
                       (double)p.erep[i];
     }
-    load_w<F>(Ws, P + p.off.U2[l], true);
-    gemm4x4<F>(X, Ws, a0, f0, v);                    // gy = gh U2^T
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(Y, W1, a0, f0, v);                                        // gh = gq R1^T
+    store_rows<F>(p.gh, base, p.n_atoms, a0, f0, v);
+    put_rows<F>(X, a0, f0, v);
+    __syncthreads();                                                     // W1 read, X complete
+    stage_w<F>(W1, wt_of(p, F, l, 1));                                   // U1^T
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(X, W0, a0, f0, v);                                        // gy = gh U2^T
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            float s = sig(z[a][f]);
+            const float s = sig(z[a][f]);
             v[a][f] *= s * (1.f + z[a][f] * (1.f - s));
         }
-    store_t<F>(Y, a0, f0, v);
-    load_w<F>(Ws, P + p.off.U1[l], true);
-    gemm4x4<F>(Y, Ws, a0, f0, v);                    // mbar = gz U1^T
+    put_rows<F>(Y, a0, f0, v);
+    cp_wait<0>();
+    __syncthreads();
+    gemm4x4<F>(Y, W1, a0, f0, v);                                        // mbar = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
 }
 
 template <int F>
-__global__ void __launch_bounds__(kAT) k_atom_bwd(PotArgs p, const float* __restrict__ ubar) {
+__global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_bwd(PotArgs p, const float* __restrict__ ubar) {
     using T = AtomTile<F>;
     extern __shared__ float4 smem4[];
     float* X = reinterpret_cast<float*>(smem4);
-    float* Y = X + F * T::IS;
-    float* Ws = Y + F * T::IS;
+    float* Y = X + T::A * T::XS;
+    float* W0 = Y + T::A * T::XS;
+    float* W1 = W0 + F * T::WS;
     const int l = p.layer;   // >= 1
     const int base = blockIdx.x * T::A;
     const int tid = threadIdx.x, fg = tid % T::FG, ag = tid / T::FG;
     const int f0 = 4 * fg, a0 = 4 * ag;
-    const float* P = p.P;
     float v[4][4], g[4][4], z[4][4];
-    load_rows_t<F>(X, ubar, base, p.n_atoms);
-    load_w<F>(Ws, P + p.off.W_in[l], true);
-    gemm4x4<F>(X, Ws, a0, f0, v);                    // ubar W_in^T
+    stage_rows<F>(X, ubar, base, p.n_atoms);
+    stage_w<F>(W0, wt_of(p, F, l, 0));                                   // group: ubar rows + W_in^{l T}
+    stage_w<F>(W1, wt_of(p, F, l - 1, 2));                               // group: U2^{l-1 T}
     load_rows4<F>(g, p.gh, base, p.n_atoms, a0, f0);
+    load_rows4<F>(z, p.z_prev, base, p.n_atoms, a0, f0);
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(X, W0, a0, f0, v);                                        // ubar W_in^T
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int f = 0; f < 4; ++f) g[a][f] += v[a][f];
     store_rows<F>(p.gh, base, p.n_atoms, a0, f0, g);
-    store_t<F>(Y, a0, f0, g);
-    load_w<F>(Ws, P + p.off.U2[l - 1], true);
-    gemm4x4<F>(Y, Ws, a0, f0, v);                    // gy = gh U2^T
-    load_rows4<F>(z, p.z_prev, base, p.n_atoms, a0, f0);
+    put_rows<F>(Y, a0, f0, g);
+    __syncthreads();                                                     // W0 read, Y complete
+    stage_w<F>(W0, wt_of(p, F, l - 1, 1));                               // U1^{l-1 T}
+    cp_wait<1>();
+    __syncthreads();
+    gemm4x4<F>(Y, W1, a0, f0, v);                                        // gy = gh U2^T
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            float s = sig(z[a][f]);
+            const float s = sig(z[a][f]);
             v[a][f] *= s * (1.f + z[a][f] * (1.f - s));
         }
-    store_t<F>(X, a0, f0, v);
-    load_w<F>(Ws, P + p.off.U1[l - 1], true);
-    gemm4x4<F>(X, Ws, a0, f0, v);                    // mbar^{l-1} = gz U1^T
+    put_rows<F>(X, a0, f0, v);
+    cp_wait<0>();
+    __syncthreads();
+    gemm4x4<F>(X, W0, a0, f0, v);                                        // mbar^{l-1} = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
 }
 
 template <int F>
-size_t atom_smem() {
-    using T = AtomTile<F>;
-    return sizeof(float) * (2 * F * T::IS + F * T::WS);
-}
-
-template <int F>
 void atom_fwd_go(const PotArgs& p, const float* msg, cudaStream_t s) {
+    using T = AtomTile<F>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_atom_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)atom_smem<F>());
+        cudaFuncSetAttribute(k_atom_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
         attr = true;
     }
-    int grid = (p.n_atoms + AtomTile<F>::A - 1) / AtomTile<F>::A;
-    k_atom_fwd<F><<<grid, kAT, atom_smem<F>(), s>>>(p, msg);
+    k_atom_fwd<F><<<(p.n_atoms + T::A - 1) / T::A, T::NT, T::SMEM, s>>>(p, msg);
 }
 
 template <int F>
 void atom_bwd_go(const PotArgs& p, const float* ubar, cudaStream_t s) {
+    using T = AtomTile<F>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_atom_bwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)atom_smem<F>());
+        cudaFuncSetAttribute(k_atom_bwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
         attr = true;
     }
-    int grid = (p.n_atoms + AtomTile<F>::A - 1) / AtomTile<F>::A;
-    k_atom_bwd<F><<<grid, kAT, atom_smem<F>(), s>>>(p, ubar);
+    k_atom_bwd<F><<<(p.n_atoms + T::A - 1) / T::A, T::NT, T::SMEM, s>>>(p, ubar);
 }
 
 }  // namespace

@@ -80,7 +80,11 @@ struct Model {
     int row_cap = 0;
     long long e_cap = 0;
     int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
+    int vl_cap = 0;                    // Verlet-skin candidate rows [N][vl_cap] (ascending j)
+    int *vl_rows = nullptr, *vl_cnt = nullptr;
     float *h = nullptr, *gh = nullptr, *force = nullptr, *vir6 = nullptr;
+    float* h0 = nullptr;               // [N][F] h^0 = A[Z_i] (constant between parameter uploads)
+    float* PT = nullptr;               // transposed weight copies for the per-atom MLPs
     float* u[kMaxLayers] = {};
     float* z[kMaxLayers] = {};
     float* mbar[2] = {};
@@ -115,6 +119,14 @@ struct dmts_ctx {
     float *d_bfs = nullptr, *d_bfb = nullptr;
     Model m[2];
     double rc_max = 0;
+    // Verlet-skin lists shared by the two models: the model with the larger
+    // cutoff (vl_src) builds candidate rows from its cell list at rc + skin,
+    // the other filters its own from them; skin 0 rebuilds every evaluation.
+    double skin = 0;
+    double vl_thr2 = 0;                 // rebuild once max |x - x_ref|^2 exceeds this
+    int vl_src = 1;
+    double* d_xref = nullptr;           // FP64 SoA [3][N], positions of the last rebuild
+    VerletState* d_vl = nullptr;
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
     bool broken = false;
@@ -180,8 +192,8 @@ int check_model(const dmts_model_desc* d, const char* name) {
 }
 
 void free_model_nbr(Model& m) {
-    dfree(m.nbr_tmp); dfree(m.col); dfree(m.recv);
-    m.nbr_tmp = m.col = m.recv = nullptr;
+    dfree(m.nbr_tmp); dfree(m.col); dfree(m.recv); dfree(m.vl_rows);
+    m.nbr_tmp = m.col = m.recv = m.vl_rows = nullptr;
 }
 
 cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
@@ -189,6 +201,7 @@ cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
     if ((e = dalloc(&m.nbr_tmp, (size_t)c->N * m.row_cap)) != cudaSuccess) return e;
     if ((e = dalloc(&m.col, (size_t)m.e_cap)) != cudaSuccess) return e;
     if ((e = dalloc(&m.recv, (size_t)m.e_cap)) != cudaSuccess) return e;
+    if (c->skin > 0 && (e = dalloc(&m.vl_rows, (size_t)c->N * m.vl_cap)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -196,8 +209,8 @@ void free_model(Model& m) {
     dfree(m.P);
     dfree(m.cell_count); dfree(m.cell_start); dfree(m.cell_atoms); dfree(m.atom_cell); dfree(m.atom_slot);
     free_model_nbr(m);
-    dfree(m.nbr_cnt); dfree(m.row_ptr);
-    dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6);
+    dfree(m.nbr_cnt); dfree(m.row_ptr); dfree(m.vl_cnt);
+    dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
     for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); }
     dfree(m.mbar[0]); dfree(m.mbar[1]);
     dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt);
@@ -238,17 +251,38 @@ std::vector<uint16_t> build_weight_tiles(const Model& m, const std::vector<float
     return t;
 }
 
+// Transposed copies of the per-atom MLP matrices: W_in^T, U1^T, U2^T of each
+// layer, then R1^T (each F x F, row-major).
+std::vector<float> build_transposed(const Model& m, const std::vector<float>& pf) {
+    const int F = m.F;
+    const size_t FF = (size_t)F * F;
+    std::vector<float> t((3 * (size_t)m.L + 1) * FF);
+    auto put = [&](size_t slot, int off) {
+        for (int r = 0; r < F; ++r)
+            for (int k = 0; k < F; ++k) t[slot * FF + (size_t)k * F + r] = pf[off + (size_t)r * F + k];
+    };
+    for (int l = 0; l < m.L; ++l) {
+        put(3 * l + 0, m.off.W_in[l]);
+        put(3 * l + 1, m.off.U1[l]);
+        put(3 * l + 2, m.off.U2[l]);
+    }
+    put(3 * (size_t)m.L, m.off.R1);
+    return t;
+}
+
 int upload_params(dmts_ctx* c, Model& m, const double* params) {
     std::vector<float> pf(m.n_params);
     for (size_t k = 0; k < m.n_params; ++k) pf[k] = (float)params[k];
     CUDA_TRY(cudaMemcpyAsync(m.P, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     std::vector<uint16_t> tiles = build_weight_tiles(m, pf);
     CUDA_TRY(cudaMemcpyAsync(m.wt, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice, c->stream));
+    std::vector<float> tr = build_transposed(m, pf);
+    CUDA_TRY(cudaMemcpyAsync(m.PT, tr.data(), tr.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return DMTS_OK;
 }
 
-int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
+int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     m.present = true;
     m.F = d->n_feat; m.K = d->n_radial; m.L = d->n_layers; m.S = d->n_species;
     m.precision = d->precision;
@@ -262,18 +296,23 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     CUDA_TRY(dalloc(&m.P, m.n_params));
     m.wt_layer_bytes = bf16_weight_tile_bytes(m.F);
     CUDA_TRY(dalloc(&m.wt, m.wt_layer_bytes * m.L));
+    CUDA_TRY(dalloc(&m.PT, (3 * (size_t)m.L + 1) * m.F * m.F));
     int rc = upload_params(c, m, d->params);
     if (rc) return rc;
-    // cells (periodic) and capacity estimates
+    // cells (periodic) and capacity estimates; with a skin the cells and the
+    // candidate rows use rc + skin
     double expected;
+    const double rv = m.rc + c->skin;
     if (c->periodic) {
         double L = c->h_box[0];
-        int nc = (int)floor(L / (m.rc * (1.0 + 1e-9) + 1e-6));
-        m.nc = nc >= 3 ? nc : 0;
+        int nc = (int)floor(L / (rv * (1.0 + 1e-9) + 1e-6));
+        m.nc = (nc >= 3 && cells) ? nc : 0;
         double rho = N / (L * L * L);
         expected = 4.0 / 3.0 * M_PI * m.rc * m.rc * m.rc * rho;
         m.row_cap = std::min(N, (int)(ceil(expected * 1.5 / 32.0) * 32) + 32);
         m.e_cap = (long long)(N * expected * c->cap_factor) + 1024;
+        const double expected_v = 4.0 / 3.0 * M_PI * rv * rv * rv * rho;
+        m.vl_cap = std::min(N, (int)(ceil(expected_v * 1.5 / 32.0) * 32) + 32);
     } else {
         int mx = 0;
         long long sq = 0;
@@ -284,6 +323,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
         }
         m.nc = 0;
         m.row_cap = std::max(32, ((mx + 31) / 32) * 32);
+        m.vl_cap = m.row_cap;
         m.e_cap = std::max<long long>(1024, std::min<long long>(sq, (long long)(N * std::min(mx, 64) * c->cap_factor)) + 1024);
     }
     if (m.nc > 0) {
@@ -296,9 +336,11 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d) {
     }
     CUDA_TRY(alloc_model_nbr(c, m));
     CUDA_TRY(dalloc(&m.nbr_cnt, N));
+    CUDA_TRY(dalloc(&m.vl_cnt, N));
     CUDA_TRY(dalloc(&m.row_ptr, N + 1));
     size_t nf = (size_t)N * m.F;
     CUDA_TRY(dalloc(&m.h, nf));
+    CUDA_TRY(dalloc(&m.h0, nf));
     CUDA_TRY(dalloc(&m.gh, nf));
     for (int l = 0; l < m.L; ++l) {
         CUDA_TRY(dalloc(&m.u[l], nf));
@@ -350,6 +392,8 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
     a.recv = m.recv;
     a.flags = c->d_flags;
     a.which = which;
+    a.exact = 1;
+    a.flag_row = kFlagMaxRow0 + which;
     return a;
 }
 
@@ -377,7 +421,9 @@ PotArgs pot_args(dmts_ctx* c, Model& m) {
     a.msg_out = m.msg;
     a.wt = m.wt;
     a.wt_layer_bytes = m.wt_layer_bytes;
+    a.PT = m.PT;
     a.h = m.h;
+    a.h_in = m.h;
     a.gh = m.gh;
     a.Ei = m.Ei;
     a.force = m.force;
@@ -385,18 +431,81 @@ PotArgs pot_args(dmts_ctx* c, Model& m) {
     return a;
 }
 
-// Quantise (optionally), build the neighbour list and evaluate energy and
-// forces of one model. Stream-ordered, no host synchronisation.
-void enqueue_neighbors(dmts_ctx* c, int which, bool quantize) {
+// Position-independent per-atom inputs of one model: h^0 = A[Z_i] and
+// u^0 = h^0 W_in^0. Run after every parameter upload.
+int prepare_embedding(dmts_ctx* c, Model& m) {
+    if (!m.present || c->N == 0) return DMTS_OK;
+    PotArgs a = pot_args(c, m);
+    a.h = m.h0;
+    a.u_next = m.u[0];
+    launch_embed(a, m.F, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    return DMTS_OK;
+}
+
+// Candidate-row arguments of model w at rc + skin (FP32 bound, no exact test).
+NbrArgs candidate_args(dmts_ctx* c, int w) {
+    Model& m = c->m[w];
+    NbrArgs a = nbr_args(c, m, w);
+    const double rv = m.rc + c->skin;
+    a.rc = rv;
+    a.exact = 0;
+    a.rc2_lo = a.rc2_hi = (float)(rv * rv * (1.0 + 1e-5));
+    a.row_cap = m.vl_cap;
+    a.nbr_tmp = m.vl_rows;
+    a.nbr_cnt = m.vl_cnt;
+    a.flag_row = kFlagMaxVl0 + w;
+    a.gate = &c->d_vl->rebuild;
+    return a;
+}
+
+// Quantise (optionally) and build the neighbour list of one model.
+// Stream-ordered, no host synchronisation. With a skin, check = true means the
+// positions may have moved since the last check: the displacement check runs
+// and, when it trips, both models' candidate rows are rebuilt; the exact
+// filter of the candidate rows always runs.
+void enqueue_neighbors(dmts_ctx* c, int which, bool quantize, bool check = true) {
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
     if (quantize) {
         if (!c->periodic) launch_frames(c->n_sys, c->d_off, c->d_x, c->N, c->d_box, c->rc_max, c->d_frame, s);
         launch_quantize(c->N, c->d_x, c->d_sys, c->d_frame, c->d_q, s);
     }
-    if (m.nc > 0)
-        launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot, s);
-    launch_neighbors(nbr_args(c, m, which), s);
+    if (c->skin <= 0) {
+        if (m.nc > 0)
+            launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot, s);
+        launch_neighbors(nbr_args(c, m, which), s);
+        return;
+    }
+    if (check) {
+        launch_vl_check(c->N, c->d_x, c->d_xref, c->d_sys, c->d_box, c->vl_thr2, c->d_vl, s);
+        const int w0 = c->vl_src;
+        Model& src = c->m[w0];
+        NbrArgs b = candidate_args(c, w0);
+        if (src.nc > 0)
+            launch_cells_gated(c->N, c->d_q, src.nc, src.cell_count, src.cell_start, src.cell_atoms, src.atom_cell,
+                               src.atom_slot, b.gate, s);
+        b.xref = c->d_xref;
+        launch_vl_build(b, s);
+        if (c->m[1 - w0].present) {
+            NbrArgs d = candidate_args(c, 1 - w0);
+            d.src_rows = src.vl_rows;
+            d.src_cnt = src.vl_cnt;
+            d.src_cap = src.vl_cap;
+            launch_row_filter(d, s);
+        }
+    }
+    NbrArgs f = nbr_args(c, m, which);
+    f.src_rows = m.vl_rows;
+    f.src_cnt = m.vl_cnt;
+    f.src_cap = m.vl_cap;
+    launch_vl_filter(f, s);
+}
+
+int force_rebuild(dmts_ctx* c) {
+    if (c->skin <= 0) return DMTS_OK;
+    CUDA_TRY(cudaMemsetAsync(&c->d_vl->force, 1, sizeof(int), c->stream));
+    return DMTS_OK;
 }
 
 void launch_edge_fwd(dmts_ctx* c, Model& m, const PotArgs& a) {
@@ -409,16 +518,17 @@ void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
     else launch_edge_bwd_f32(a, m.F, m.K, c->stream);
 }
 
-void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true) {
+void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, bool check = true,
+                  bool virial = false) {
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
-    enqueue_neighbors(c, which, quantize);
+    enqueue_neighbors(c, which, quantize, check);
     PotArgs a = pot_args(c, m);
-    a.u_next = m.u[0];
-    launch_embed(a, m.F, s);
+    a.virial = virial ? 1 : 0;
     for (int l = 0; l < m.L; ++l) {
         PotArgs f = a;
         f.layer = l;
+        f.h_in = l == 0 ? m.h0 : m.h;
         f.atoms_per_cta = m.apc_fwd;
         f.u = m.u[l];
         f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
@@ -465,10 +575,13 @@ int grow_capacity(dmts_ctx* c) {
         int max_row = c->h_flags[kFlagMaxRow0 + w];
         long long max_e = (long long)(unsigned int)c->h_flags[kFlagMaxE0 + w];
         bool grow = false;
+        int max_vl = c->h_flags[kFlagMaxVl0 + w];
         if (max_row > m.row_cap) { m.row_cap = std::min(c->N, ((int)(max_row * 1.25) + 63) / 32 * 32); grow = true; }
         if (max_e > m.e_cap) { m.e_cap = (long long)(max_e * 1.25) + 1024; grow = true; }
+        if (c->skin > 0 && max_vl > m.vl_cap) { m.vl_cap = std::min(c->N, ((int)(max_vl * 1.25) + 63) / 32 * 32); grow = true; }
         if (grow) {
-            if (m.row_cap > 6000) return fail(DMTS_ERR_CAPACITY, "neighbour row capacity %d too large", m.row_cap);
+            if (m.row_cap > 6000 || m.vl_cap > 6000)
+                return fail(DMTS_ERR_CAPACITY, "neighbour row capacity %d too large", std::max(m.row_cap, m.vl_cap));
             CUDA_TRY(cudaStreamSynchronize(c->stream));
             free_model_nbr(m);
             cudaError_t e = alloc_model_nbr(c, m);
@@ -476,7 +589,7 @@ int grow_capacity(dmts_ctx* c) {
         }
     }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-    return DMTS_OK;
+    return force_rebuild(c);                // rows reallocated, or truncated by the overflow
 }
 
 int reset_flags(dmts_ctx* c) {
@@ -510,7 +623,7 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, s);
             enqueue_eval(c, 0, nonper, false);       // the small model's energy is not reported
         }
-        enqueue_eval(c, 1, false);
+        enqueue_eval(c, 1, false, true, false);     // same positions as the last small evaluation
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
                           c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, s);
     } else {
@@ -649,6 +762,7 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
+    dfree(c->d_xref); dfree(c->d_vl);
     dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
     dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -707,6 +821,13 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     c->cap_factor = json_number(options, "edge_capacity_factor", 1.5);
     if (!(c->cap_factor > 0.0)) c->cap_factor = 1.5;
     const double opt_row_cap = json_number(options, "row_capacity", 0.0);
+    c->skin = json_number(options, "skin", 1.0);
+    if (!(c->skin >= 0.0) || c->skin > 10.0) {
+        delete c;
+        return fail(DMTS_ERR_ARG, "skin must be in [0, 10] A");
+    }
+    c->vl_thr2 = 0.25 * c->skin * c->skin * (1.0 - 2e-3);
+    c->vl_src = (small && small->cutoff > big->cutoff) ? 0 : 1;
 #define CREATE_TRY(expr)                                                          \
     do {                                                                          \
         cudaError_t e_ = (expr);                                                  \
@@ -744,6 +865,12 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(dalloc(&c->d_bfs, (size_t)3 * N));
     CREATE_TRY(dalloc(&c->d_bfb, (size_t)3 * N));
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
+    if (c->skin > 0) {
+        CREATE_TRY(dalloc(&c->d_xref, (size_t)3 * N));
+        CREATE_TRY(dalloc(&c->d_vl, 1));
+        CREATE_TRY(cudaMemset(c->d_vl, 0, sizeof(VerletState)));
+        CREATE_TRY(cudaMemset(&c->d_vl->force, 1, sizeof(int)));
+    }
     CREATE_TRY(cudaMemcpy(c->d_off, sys->atom_offset, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
     CREATE_TRY(cudaMemcpy(c->d_species, sys->species, sizeof(int) * std::max(N, 0), cudaMemcpyHostToDevice));
     CREATE_TRY(cudaMemcpy(c->d_sys, sys_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
@@ -754,12 +881,12 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(cudaMemset(c->d_v, 0, sizeof(double) * 3 * std::max(N, 1)));
     CREATE_TRY(cudaMemset(c->d_flags, 0, sizeof(int) * kFlagCount));
     if (small) {
-        rc = init_model(c, c->m[0], small);
+        rc = init_model(c, c->m[0], small, c->skin <= 0 || c->vl_src == 0);
         if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
         c->m[0].apc_fwd = std::min(c->m[0].apc_fwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_fwd));
         c->m[0].apc_bwd = std::min(c->m[0].apc_bwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_bwd));
     }
-    rc = init_model(c, c->m[1], big);
+    rc = init_model(c, c->m[1], big, c->skin <= 0 || c->vl_src == 1);
     if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
     c->m[1].apc_fwd = std::min(c->m[1].apc_fwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_fwd));
     c->m[1].apc_bwd = std::min(c->m[1].apc_bwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_bwd));
@@ -767,11 +894,15 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
         if (c->m[w].present && opt_row_cap >= 1.0) {
             // smaller initial row capacity (exercises the overflow-and-retry path)
             c->m[w].row_cap = std::min(c->m[w].row_cap, (int)opt_row_cap);
+            c->m[w].vl_cap = std::min(c->m[w].vl_cap, (int)opt_row_cap);
             free_model_nbr(c->m[w]);
             CREATE_TRY(alloc_model_nbr(c, c->m[w]));
         }
         c->m[w].apc_fwd = std::max(8, c->m[w].apc_fwd);
         c->m[w].apc_bwd = std::max(8, c->m[w].apc_bwd);
+    }
+    for (int w = 0; w < 2; ++w) {
+        if ((rc = prepare_embedding(c, c->m[w]))) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
     }
     if (c->periodic) {
         // constant frame; computed once on the device
@@ -822,7 +953,7 @@ int dmts_forces(dmts_ctx* c, int which, double* f_out, double* energy_out, doubl
     if ((rc = autotune_models(c))) return rc;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = reset_flags(c))) return rc;
-        enqueue_eval(c, which, true);
+        enqueue_eval(c, which, true, true, true, virial_out != nullptr);
         if (virial_out) launch_virial_sum(c->n_sys, c->d_off, m.vir6, m.W, c->stream);
         if ((rc = sync_check(c))) return rc;
         if (!c->h_flags[kFlagOverflow]) break;
@@ -879,6 +1010,7 @@ int dmts_set_params(dmts_ctx* c, int which, const double* params, size_t n_param
         if (!isfinite(params[k])) return fail(DMTS_ERR_ARG, "parameter %zu is not finite", k);
     int rc = upload_params(c, m, params);
     if (rc) return rc;
+    if ((rc = prepare_embedding(c, m))) return rc;
     c->forces_valid = false;
     return DMTS_OK;
 }
@@ -1055,13 +1187,12 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
         enqueue_neighbors(c, which, true);
         end(0);
         PotArgs a = pot_args(c, m);
-        a.u_next = m.u[0];
-        begin(1);
-        launch_embed(a, m.F, s);
+        begin(1);                                  // the embedding is built once per parameter upload
         end(1);
         for (int l = 0; l < L; ++l) {
             PotArgs f = a;
             f.layer = l;
+            f.h_in = l == 0 ? m.h0 : m.h;
             f.atoms_per_cta = m.apc_fwd;
             f.u = m.u[l];
             f.u_next = (l + 1 < L) ? m.u[l + 1] : nullptr;
@@ -1107,6 +1238,18 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
 }
 
 long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
+
+int dmts_neighbor_stats(dmts_ctx* c, long long* n_checks, long long* n_rebuilds) {
+    CTX_GUARD(c);
+    VerletState st{};
+    if (c->skin > 0) {
+        CUDA_TRY(cudaMemcpyAsync(&st, c->d_vl, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    if (n_checks) *n_checks = st.n_checks;
+    if (n_rebuilds) *n_rebuilds = st.n_rebuilds;
+    return DMTS_OK;
+}
 
 int dmts_get_tuning(dmts_ctx* c, int which, int* atoms_fwd, int* atoms_bwd) {
     if (!c) return fail(DMTS_ERR_ARG, "context is NULL");

@@ -50,7 +50,22 @@ enum Flag {
     kFlagMaxE1 = 5,        // (big)
     kFlagStep = 6,         // energies ring index
     kFlagTimeout = 7,      // a bounded device-side wait gave up
-    kFlagCount = 8
+    kFlagMaxVl0 = 8,       // max candidate (Verlet) row length seen (small model)
+    kFlagMaxVl1 = 9,       // (big)
+    kFlagCount = 10
+};
+
+// Verlet-skin bookkeeping (device memory, one per context). The candidate
+// rows of both models were built at the positions x_ref; k_vl_check reduces
+// max |x - x_ref|^2 into max_d2, and the last CTA to finish sets rebuild
+// (read by the rebuild kernels as their gate) and clears max_d2 and done.
+struct VerletState {
+    unsigned long long max_d2;   // FP64 bits of the largest squared displacement
+    unsigned int done;           // CTAs of the current check that have finished
+    int rebuild;                 // gate of the rebuild kernels
+    int force;                   // set by the host: rebuild at the next check
+    int pad;
+    long long n_checks, n_rebuilds;
 };
 
 // Everything the neighbour builder needs for one model.
@@ -76,6 +91,14 @@ struct NbrArgs {
     int* recv;               // [e_cap]
     int* flags;
     int which;
+    // Verlet-skin mode
+    const int* gate;         // non-null: the kernel runs only if *gate != 0
+    int exact;               // 1: exact FP64 decision in the band; 0: keep every candidate with d^2 <= rc2_hi
+    int flag_row;            // flags index receiving the longest row
+    double* xref;            // non-null: the builder records x here (positions of the rebuild)
+    const int* src_rows;     // row filter input: candidate rows [N][src_cap], sorted by j
+    const int* src_cnt;      // [N]
+    int src_cap;
 };
 
 // Arguments of the potential's kernels (one model, one layer).
@@ -104,7 +127,9 @@ struct PotArgs {
     float* msg_out;          // [N][F] per-atom sums: messages m^l (forward) or ubar^l (backward)
     const unsigned char* wt; // BF16 operand tiles of the filter weights, per layer
     size_t wt_layer_bytes;
+    const float* PT;         // FP32 transposed copies: W_in^T, U1^T, U2^T per layer, then R1^T
     // features
+    const float* h_in;       // h entering the per-atom MLP of this layer (h^0 table for layer 0)
     float* h;
     const float* u;          // u^l (gathered)
     float* u_next;           // u^{l+1}
@@ -117,6 +142,7 @@ struct PotArgs {
     float* force;            // SoA [3][N]
     float* vir6;             // [N][6]
     int accumulate;          // backward: add to force/vir6 instead of overwrite
+    int virial;              // backward: also the per-atom virial vir6 (tensor-core path; FP32 always)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -128,6 +154,17 @@ void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const
 void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
                   int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s);
 void launch_neighbors(const NbrArgs& a, cudaStream_t s);
+// Verlet-skin lists: displacement check (sets st->rebuild), gated cell list,
+// gated candidate build (a.nbr_tmp / a.nbr_cnt / a.row_cap = candidate rows),
+// gated candidate-from-candidate filter, and the per-evaluation exact filter
+// of candidate rows into the CSR.
+void launch_vl_check(int n_atoms, const double* x, const double* xref, const int* sys_of_atom,
+                     const double* box, double thr2, VerletState* st, cudaStream_t s);
+void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
+                        int* cell_atoms, int* atom_cell, int* atom_slot, const int* gate, cudaStream_t s);
+void launch_vl_build(const NbrArgs& a, cudaStream_t s);
+void launch_row_filter(const NbrArgs& a, cudaStream_t s);
+void launch_vl_filter(const NbrArgs& a, cudaStream_t s);
 
 // potential_f32.cu
 void launch_embed(const PotArgs& a, int F, cudaStream_t s);

@@ -7,6 +7,17 @@
 // (the wrapped integer difference is the minimum image); only candidates in
 // a thin band around rc^2, where FP32 rounding could flip the decision, are
 // decided by the exact FP64 expression.
+//
+// Verlet-skin mode keeps, per model, candidate rows of every j within
+// rc + skin at the positions x_ref of the last rebuild. While no atom has
+// moved by skin / 2 or more since then, every pair now inside rc was inside
+// rc + skin at the rebuild (|r_now| >= |r_ref| - |dx_i| - |dx_j|), so the
+// exact test applied to the candidate rows yields the same pair set as a
+// fresh build. The rebuild decision is taken on the device: the rebuild
+// kernels stay in the stream (and in captured graphs) and return at once
+// when their gate is clear.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace dmts {
@@ -110,8 +121,16 @@ __device__ __forceinline__ int cell_coord(unsigned int qc, int nc) {
     return (int)(((unsigned long long)qc * (unsigned long long)nc) >> 32);
 }
 
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate && *gate == 0; }
+
+__global__ void k_cell_clear(int n, int* __restrict__ count, const int* gate) {
+    if (gated_off(gate)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) count[i] = 0;
+}
+
 __global__ void k_cell_count(int n, const uint4* __restrict__ q, int nc, int* __restrict__ count,
-                             int* __restrict__ atom_cell, int* __restrict__ slot) {
+                             int* __restrict__ atom_cell, int* __restrict__ slot, const int* gate) {
+    if (gated_off(gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint4 p = q[i];
@@ -120,65 +139,101 @@ __global__ void k_cell_count(int n, const uint4* __restrict__ q, int nc, int* __
     slot[i] = atomicAdd(&count[c], 1);
 }
 
-// Exclusive scan of count[0..n) into start[0..n], one CTA of 1024 threads.
-__global__ void k_scan_1cta(int n, const int* __restrict__ count, int* __restrict__ start,
-                            long long cap, int* __restrict__ flags, int flag_max) {
+// Exclusive scan of count[0..n) into start[0..n] by one CTA of 1024 threads,
+// in tiles of 8 consecutive values per thread (two 16-byte loads and stores);
+// start[n] is the total. With flags: overflow if the total exceeds cap, and
+// flags[flag_max] = max(total).
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_1cta(int n, const int* __restrict__ count,
+                                                            int* __restrict__ start, long long cap,
+                                                            int* __restrict__ flags, int flag_max, const int* gate) {
+    if (gated_off(gate)) return;
     __shared__ int warp_sums[32];
-    int t = threadIdx.x;
-    int per = (n + blockDim.x - 1) / blockDim.x;
-    int b = t * per, e = min(n, b + per);
-    int local = 0;
-    for (int k = b; k < e; ++k) local += count[k];
-    // block exclusive scan of local
-    int lane = t & 31, w = t >> 5;
-    int v = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_sums[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        int s = lane < nw ? warp_sums[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    constexpr int nw = kScanThreads / 32;
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanThreads * kScanPer) {
+        const int i0 = base + t * kScanPer;
+        int v[kScanPer];
+        if (i0 + kScanPer <= n) {
+            const int4 a = *reinterpret_cast<const int4*>(count + i0);
+            const int4 b = *reinterpret_cast<const int4*>(count + i0 + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < n ? count[i0 + k] : 0;
         }
-        warp_sums[lane] = s;
+        int local = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) local += v[k];
+        int incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int sum = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, sum, o);
+                if (lane >= o) sum += y;
+            }
+            warp_sums[lane] = sum;
+        }
+        __syncthreads();
+        int e = carry + incl - local + (w > 0 ? warp_sums[w - 1] : 0);
+        int o[kScanPer];
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) { o[k] = e; e += v[k]; }
+        if (i0 + kScanPer <= n) {
+            *reinterpret_cast<int4*>(start + i0) = make_int4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<int4*>(start + i0 + 4) = make_int4(o[4], o[5], o[6], o[7]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanPer; ++k)
+                if (i0 + k < n) start[i0 + k] = o[k];
+        }
+        carry += warp_sums[nw - 1];
+        __syncthreads();                                   // warp_sums is rewritten by the next tile
     }
-    __syncthreads();
-    int excl = v - local + (w > 0 ? warp_sums[w - 1] : 0);
-    for (int k = b; k < e; ++k) {
-        start[k] = excl;
-        excl += count[k];
-    }
-    if (t == blockDim.x - 1) {
-        start[n] = excl;
+    if (t == 0) {
+        start[n] = carry;
         if (flags) {
-            if ((long long)excl > cap) atomicOr(&flags[kFlagOverflow], 1);
-            atomicMax(&flags[flag_max], excl);
+            if ((long long)carry > cap) atomicOr(&flags[kFlagOverflow], 1);
+            atomicMax(&flags[flag_max], carry);
         }
     }
 }
 
 __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell, const int* __restrict__ slot,
-                            const int* __restrict__ start, int* __restrict__ cell_atoms) {
+                            const int* __restrict__ start, int* __restrict__ cell_atoms, const int* gate) {
+    if (gated_off(gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     cell_atoms[start[atom_cell[i]] + slot[i]] = i;
 }
 
-void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s) {
+void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
+                        int* cell_atoms, int* atom_cell, int* atom_slot, const int* gate, cudaStream_t s) {
     int n_cells = nc * nc * nc;
     if (n_atoms == 0) return;
-    cudaMemsetAsync(cell_count, 0, sizeof(int) * n_cells, s);
+    k_cell_clear<<<std::min(152, (n_cells + 255) / 256), 256, 0, s>>>(n_cells, cell_count, gate);
     int g = (n_atoms + 255) / 256;
-    k_cell_count<<<g, 256, 0, s>>>(n_atoms, q, nc, cell_count, atom_cell, atom_slot);
-    k_scan_1cta<<<1, 1024, 0, s>>>(n_cells, cell_count, cell_start, 0, nullptr, 0);
-    k_cell_fill<<<g, 256, 0, s>>>(n_atoms, atom_cell, atom_slot, cell_start, cell_atoms);
-    count_launch(3);
+    k_cell_count<<<g, 256, 0, s>>>(n_atoms, q, nc, cell_count, atom_cell, atom_slot, gate);
+    k_scan_1cta<<<1, kScanThreads, 0, s>>>(n_cells, cell_count, cell_start, 0, nullptr, 0, gate);
+    k_cell_fill<<<g, 256, 0, s>>>(n_atoms, atom_cell, atom_slot, cell_start, cell_atoms, gate);
+    count_launch(4);
+}
+
+void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
+                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s) {
+    launch_cells_gated(n_atoms, q, nc, cell_count, cell_start, cell_atoms, atom_cell, atom_slot, nullptr, s);
 }
 
 // ------------------------------------------------------------ neighbours
@@ -204,6 +259,7 @@ constexpr int kNbrWarps = 8;
 // system), keep those inside the cutoff, sort the row by j (rank sort) and
 // store it in the fixed-capacity staging array.
 __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
+    if (gated_off(a.gate)) return;
     extern __shared__ int smem_i[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* row = smem_i + w * (a.row_cap + 64);
@@ -215,6 +271,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
     int s = (int)qi.w;
     float qscale = a.frame[s].qscale;
     double L = a.box[s];
+    if (a.xref && lane < 3) a.xref[(size_t)lane * a.n_atoms + i] = a.x[(size_t)lane * a.n_atoms + i];
     int total;
     int base = 0;
     if (a.nc > 0) {
@@ -259,7 +316,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
                 float3 r = edge_vec(qi, a.q[j], qscale);
                 float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                 if (d2 < rc2_lo) keep = true;
-                else if (d2 <= rc2_hi) keep = exact_inside(a.x, a.n_atoms, i, j, L, a.rc);
+                else if (d2 <= rc2_hi) keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
             }
         }
         unsigned int m = __ballot_sync(0xffffffffu, keep);
@@ -271,7 +328,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
     }
     __syncwarp();
     if (lane == 0) {
-        atomicMax(&a.flags[kFlagMaxRow0 + a.which], n_row);
+        atomicMax(&a.flags[a.flag_row], n_row);
         if (n_row > a.row_cap) atomicOr(&a.flags[kFlagOverflow], 1);
     }
     int n_keep = min(n_row, a.row_cap);
@@ -300,6 +357,133 @@ __global__ void k_nbr_compact(NbrArgs a) {
     }
 }
 
+// One warp per atom: keep the candidates of row i (ascending j) that pass the
+// test, in order, so the output row is ascending as well. a.exact selects the
+// exact cutoff test of the final pair set or the plain FP32 bound used to
+// derive one model's candidate rows from the other's.
+__global__ void __launch_bounds__(256) k_row_filter(NbrArgs a) {
+    if (gated_off(a.gate)) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= a.n_atoms) return;
+    const uint4 qi = a.q[i];
+    const int s = (int)qi.w;
+    const float qscale = a.frame[s].qscale;
+    const double L = a.box[s];
+    const int cnt = a.src_cnt[i];
+    const int* src = a.src_rows + (size_t)i * a.src_cap;
+    int* dst = a.nbr_tmp + (size_t)i * a.row_cap;
+    const float rc2_lo = a.rc2_lo, rc2_hi = a.rc2_hi;
+    int n_row = 0;
+    for (int v0 = 0; v0 < cnt; v0 += 32) {
+        const int v = v0 + lane;
+        bool keep = false;
+        int j = -1;
+        if (v < cnt) {
+            j = src[v];
+            float3 r = edge_vec(qi, a.q[j], qscale);
+            float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+            if (d2 < rc2_lo) keep = true;
+            else if (d2 <= rc2_hi) keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
+        }
+        const unsigned int m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = n_row + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.row_cap) dst[pos] = j;
+        }
+        n_row += __popc(m);
+    }
+    if (lane == 0) {
+        atomicMax(&a.flags[a.flag_row], n_row);
+        if (n_row > a.row_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+        a.nbr_cnt[i] = min(n_row, a.row_cap);
+    }
+}
+
+// Largest squared displacement since the rebuild (minimum image in periodic
+// boxes), reduced over CTAs; the last CTA to finish takes the decision.
+__global__ void __launch_bounds__(256) k_vl_check(int n, const double* __restrict__ x, const double* __restrict__ xref,
+                                                  const int* __restrict__ sys, const double* __restrict__ box,
+                                                  double thr2, VerletState* st) {
+    __shared__ double wmax[8];
+    __shared__ bool last;
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double L = box[sys[i]];
+        double d2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double d = x[(size_t)c * n + i] - xref[(size_t)c * n + i];
+            if (L > 0.0) d -= L * rint(d / L);
+            d2 += d * d;
+        }
+        if (!(d2 <= thr2)) d2 = fmax(d2, 2.0 * thr2 + 1.0);   // NaN counts as a large move
+        m = fmax(m, d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wmax[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, wmax[k]);
+        atomicMax(&st->max_d2, (unsigned long long)__double_as_longlong(m));
+        __threadfence();
+        last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicAdd(&st->max_d2, 0ull));
+        const int force = *(volatile int*)&st->force;
+        const int rb = (force || mx > thr2) ? 1 : 0;
+        st->rebuild = rb;
+        st->force = 0;
+        st->max_d2 = 0ull;
+        st->done = 0u;
+        st->n_checks += 1;
+        st->n_rebuilds += rb;
+    }
+}
+
+void launch_vl_check(int n_atoms, const double* x, const double* xref, const int* sys_of_atom,
+                     const double* box, double thr2, VerletState* st, cudaStream_t s) {
+    const int g = std::max(1, std::min(4 * 152, (n_atoms + 255) / 256));
+    k_vl_check<<<g, 256, 0, s>>>(n_atoms, x, xref, sys_of_atom, box, thr2, st);
+    count_launch();
+}
+
+void launch_row_filter(const NbrArgs& a, cudaStream_t s) {
+    if (a.n_atoms == 0) return;
+    k_row_filter<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);
+    count_launch();
+}
+
+void launch_vl_build(const NbrArgs& a, cudaStream_t s) {
+    if (a.n_atoms == 0) return;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_nbr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_done = true;
+    }
+    int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
+    size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
+    k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
+    count_launch();
+}
+
+void launch_vl_filter(const NbrArgs& a, cudaStream_t s) {
+    if (a.n_atoms == 0) {
+        cudaMemsetAsync(a.row_ptr, 0, sizeof(int), s);
+        return;
+    }
+    k_row_filter<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);
+    k_scan_1cta<<<1, kScanThreads, 0, s>>>(a.n_atoms, a.nbr_cnt, a.row_ptr, a.e_cap, a.flags,
+                                          kFlagMaxE0 + a.which, nullptr);
+    k_nbr_compact<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);
+    count_launch(3);
+}
+
 void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
     if (a.n_atoms == 0) {
         cudaMemsetAsync(a.row_ptr, 0, sizeof(int), s);
@@ -313,8 +497,8 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
     int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
-    k_scan_1cta<<<1, 1024, 0, s>>>(a.n_atoms, a.nbr_cnt, a.row_ptr, a.e_cap, a.flags,
-                                  kFlagMaxE0 + a.which);
+    k_scan_1cta<<<1, kScanThreads, 0, s>>>(a.n_atoms, a.nbr_cnt, a.row_ptr, a.e_cap, a.flags,
+                                          kFlagMaxE0 + a.which, nullptr);
     k_nbr_compact<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);
     count_launch(3);
 }

@@ -159,9 +159,10 @@ struct VecSlots {
 };
 
 template <int F>
-__device__ __forceinline__ void warp_vec_segments(const float* sP, const int* srow, VecSlots<F>* vs,
-                                                  float* __restrict__ out, int a0) {
+__device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, const int* __restrict__ srow,
+                                                  VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0) {
     constexpr int NF = F / 32;
+    constexpr int B = 8;                           // edges whose values are loaded together
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // row of every edge of the warp, segment starts and ends as warp-uniform bit masks
     const int myrow = srow[32 * w + lane];
@@ -181,28 +182,36 @@ __device__ __forceinline__ void warp_vec_segments(const float* sP, const int* sr
 #pragma unroll
     for (int c = 0; c < NF; ++c) acc[c] = 0.f;
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        if (e < n_valid) {
-            const bool st = (starts >> e) & 1u;
+    for (int e0 = 0; e0 < 32; e0 += B) {
+        if (e0 >= n_valid) break;
+        // issue the batch's loads before any store of the batch
+        float v[B][NF];
 #pragma unroll
-            for (int c = 0; c < NF; ++c) {
-                const float v = base[prow<F>(e, lane + 32 * c)];
-                acc[c] = st ? v : acc[c] + v;
-            }
-            if ((ends >> e) & 1u) {
-                const int r = __shfl_sync(0xffffffffu, myrow, e);
-                const bool first = (starts & ((2u << e) - 1u)) == (starts & 1u) && (starts & 1u);  // segment 0
-                if (first) {
+        for (int k = 0; k < B; ++k)
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) vs->v[w][0][lane + 32 * c] = acc[c];
-                    if (lane == 0) vs->row[w][0] = r;
-                } else if (e == last_end) {
+            for (int c = 0; c < NF; ++c) v[k][c] = base[prow<F>(e0 + k, lane + 32 * c)];
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) vs->v[w][1][lane + 32 * c] = acc[c];
-                    if (lane == 0) vs->row[w][1] = r;
-                } else {
+        for (int k = 0; k < B; ++k) {
+            const int e = e0 + k;
+            if (e < n_valid) {
+                const bool st = (starts >> e) & 1u;
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) out[(size_t)(a0 + r) * F + lane + 32 * c] = acc[c];
+                for (int c = 0; c < NF; ++c) acc[c] = st ? v[k][c] : acc[c] + v[k][c];
+                if ((ends >> e) & 1u) {
+                    const int r = __shfl_sync(0xffffffffu, myrow, e);
+                    const bool first = (starts & ((2u << e) - 1u)) == (starts & 1u) && (starts & 1u);  // segment 0
+                    if (first) {
+#pragma unroll
+                        for (int c = 0; c < NF; ++c) vs->v[w][0][lane + 32 * c] = acc[c];
+                        if (lane == 0) vs->row[w][0] = r;
+                    } else if (e == last_end) {
+#pragma unroll
+                        for (int c = 0; c < NF; ++c) vs->v[w][1][lane + 32 * c] = acc[c];
+                        if (lane == 0) vs->row[w][1] = r;
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NF; ++c) out[(size_t)(a0 + r) * F + lane + 32 * c] = acc[c];
+                    }
                 }
             }
         }
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
 }
 
 // ------------------------------------------------------------ backward
-template <int F>
+template <int F, int NV>
 struct BwdSmem {
     unsigned char w1t[F * kKP * 2];     // B[n][k] = W1[k][n]
     unsigned char w2t[F * F * 2];       // B[n][k] = W2[k][n]
@@ -457,15 +466,16 @@ struct BwdSmem {
     float P[kT * F];                    // mbar_j rows, then ubar messages (swizzled rows)
     float U[kT * F];                    // u_j rows (swizzled)
     int row[kT];
-    ScalSlots<9> ss;                    // the vector slots live in a1 (free once D1 is complete)
+    ScalSlots<NV> ss;                   // the vector slots live in a1 (free once D1 is complete)
     uint64_t mbar;
     uint32_t taddr;
 };
 
-template <int F>
+// NV = 9: forces and the per-atom virial; NV = 3: forces only.
+template <int F, int NV>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    BwdSmem<F>& S = *reinterpret_cast<BwdSmem<F>*>(smraw);
+    BwdSmem<F, NV>& S = *reinterpret_cast<BwdSmem<F, NV>*>(smraw);
     static_assert(sizeof(VecSlots<F>) <= sizeof(S.a1), "vector slots must fit the basis tile");
     VecSlots<F>* vs = reinterpret_cast<VecSlots<F>*>(S.a1);
     constexpr int TCOLS = 4 * F;   // D1 | D4 | D2 | D3
@@ -513,12 +523,12 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             for (int t = tid; t < nA * F; t += kT) a.msg_out[(size_t)a0 * F + t] = 0.f;
         const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
         const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
-        int cur = -1;      // threads < F: ubar row; threads F..F+8: force / virial row
+        int cur = -1;      // threads < F: ubar row; threads F..F+NV-1: force / virial row
         float run = 0.f;
         // per-atom force and virial start at zero (or keep the later layer's value)
         if (!a.accumulate)
-            for (int t = tid; t < nA * 9; t += kT) {
-                int r = t / 9, c = t % 9;
+            for (int t = tid; t < nA * NV; t += kT) {
+                int r = t / NV, c = t % NV;
                 if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + r] = 0.f;
                 else a.vir6[(size_t)(a0 + r) * 6 + c - 3] = 0.f;
             }
@@ -605,6 +615,13 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
                 for (int c = 0; c < F; c += 16) {
+                    // the receiving atom's rows (shared by most of the warp) before the TMEM load
+                    float4 ui16[4], mi16[4];
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        ui16[qq] = __ldg(reinterpret_cast<const float4*>(ui + c + 4 * qq));
+                        mi16[qq] = __ldg(reinterpret_cast<const float4*>(mi + c + 4 * qq));
+                    }
                     float v[16], g[16];
                     tmem_ld16(tD2 + lane_base + c, v);
 #pragma unroll
@@ -612,8 +629,8 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                         const int o = prow<F>(tid, c + q);
                         float4 u4 = *reinterpret_cast<const float4*>(S.U + o);
                         float4 m4 = *reinterpret_cast<const float4*>(S.P + o);
-                        float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
-                        float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
+                        const float4 ui4 = ui16[q / 4];
+                        const float4 mi4 = mi16[q / 4];
                         float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
                         float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
                         g[q] = mi4.x * u4.x + m4.x * ui4.x;
@@ -663,12 +680,14 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 se += dphi;
             }
             {
-                float val[9];
+                float val[NV];
                 val[0] = se * rx; val[1] = se * ry; val[2] = se * rz;
-                float hv = -0.5f * se * d;
-                val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
-                val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
-                warp_scal_segments<9>(val, row, &S.ss);
+                if constexpr (NV == 9) {
+                    float hv = -0.5f * se * d;
+                    val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
+                    val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
+                }
+                warp_scal_segments<NV>(val, row, &S.ss);
             }
             fence_before_sync();
             ok = __syncthreads_and(ok);
@@ -676,7 +695,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             __syncthreads();
             if (need_ubar && tid < F) {
                 merge_vec_slots<F>(vs, tid, cur, run, a.msg_out, a0);
-            } else if (tid >= F && tid < F + 9) {
+            } else if (tid >= F && tid < F + NV) {
                 const int c = tid - F;
                 for (int w = 0; w < 4; ++w)
                     for (int k = 0; k < S.ss.n[w]; ++k) {
@@ -697,7 +716,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
         }
         if (cur >= 0) {
             if (need_ubar && tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
-            else if (tid >= F && tid < F + 9) {
+            else if (tid >= F && tid < F + NV) {
                 const int c = tid - F;
                 if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + cur] += run;
                 else a.vir6[(size_t)(a0 + cur) * 6 + c - 3] += run;
@@ -711,40 +730,55 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     if (!ok && tid == 0) atomicOr(status, 1);
 }
 
-template <int F, bool Bwd>
-void go(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    auto kern = Bwd ? k_edge_bwd_bf16<F> : k_edge_fwd_bf16<F>;
-    const int smem = Bwd ? (int)sizeof(BwdSmem<F>) : (int)sizeof(FwdSmem<F>);
-    static int grid_cap = 0;
+// Persistent launch: one CTA per resident slot, bounded by shared memory
+// (1 KB reserved per CTA) and by the 512 tensor-memory columns of an SM.
+template <class Kern>
+void launch_persistent(Kern kern, int smem, int tmem_cols, int& grid_cap, const PotArgs& a, int K, int* status,
+                       cudaStream_t s) {
     if (!grid_cap) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int dev = 0, sms = 0, smem_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        // resident CTAs per SM: shared memory (1 KB reserved per CTA) and the
-        // 512 tensor-memory columns (each CTA holds 2F or 4F of them)
         const int by_smem = smem_sm / (smem + 1024);
-        const int by_tmem = 512 / (Bwd ? 4 * F : 2 * F);
+        const int by_tmem = 512 / tmem_cols;
         grid_cap = std::max(1, sms * std::max(1, std::min(by_smem, by_tmem)));
     }
     int n_chunks = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
     kern<<<std::min(n_chunks, grid_cap), kT, smem, s>>>(a, K, status);
 }
 
+template <int F>
+void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    static int cap = 0;
+    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, cap, a, K, status, s);
+}
+
+template <int F, int NV>
+void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    static int cap = 0;
+    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 4 * F, cap, a, K, status, s);
+}
+
 }  // namespace
 
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    if (F == 64) go<64, false>(a, K, status, s);
-    else go<32, false>(a, K, status, s);
+    if (F == 64) go_fwd<64>(a, K, status, s);
+    else go_fwd<32>(a, K, status, s);
     count_launch();
 }
 
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    if (F == 64) go<64, true>(a, K, status, s);
-    else go<32, true>(a, K, status, s);
+    if (a.virial) {
+        if (F == 64) go_bwd<64, 9>(a, K, status, s);
+        else go_bwd<32, 9>(a, K, status, s);
+    } else {
+        if (F == 64) go_bwd<64, 3>(a, K, status, s);
+        else go_bwd<32, 3>(a, K, status, s);
+    }
     count_launch();
 }
 

@@ -118,7 +118,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
 // Each thread of the warp reads 16 consecutive 32-bit columns of its own TMEM
 // lane (warp w of the CTA may access lanes 32 (w % 4) .. 32 (w % 4) + 31).
 // The load and its completion wait are one asm statement, so the compiler
-// cannot consume the destination registers before they are written.
+// cannot consume the destination registers before they are written. Tensor
+// memory is not addressed by ordinary loads and stores, so the statement
+// does not clobber "memory": the compiler may move independent shared and
+// global accesses across it (its order relative to the other tcgen05 and
+// mbarrier statements, all volatile, is kept).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -127,7 +131,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr) : "memory");
+        : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }

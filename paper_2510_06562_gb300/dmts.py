@@ -29,7 +29,7 @@ SMALL, BIG = 0, 1
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
-            "dmts_force_matching_grad", "dmts_get_tuning")
+            "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats")
 
 
 class DmtsError(RuntimeError):
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_force_matching_grad.restype = C.c_int
     lib.dmts_get_tuning.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.dmts_get_tuning.restype = C.c_int
+    lib.dmts_neighbor_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.dmts_neighbor_stats.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -250,6 +252,12 @@ class Context:
     @property
     def launch_count(self) -> int:
         return load_library().dmts_launch_count(self._h)
+
+    def neighbor_stats(self) -> tuple[int, int]:
+        """(displacement checks, candidate-row rebuilds) of the Verlet-skin lists."""
+        a, b = C.c_longlong(), C.c_longlong()
+        _check(load_library().dmts_neighbor_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "_h", None):

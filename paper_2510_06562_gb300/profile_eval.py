@@ -21,11 +21,13 @@ def main():
     ap.add_argument("--system", default="water12288", choices=["water192", "water12288"])
     ap.add_argument("--evals", type=int, default=3)
     ap.add_argument("--respa", type=int, default=0, help="instead: this many 3 fs / 1 fs outer steps")
+    ap.add_argument("--options", default=None, help="context options (JSON)")
     args = ap.parse_args()
     s = I.water_12288(0) if args.system == "water12288" else I.water_192(0)
     prec = D.BF16_MLP if args.precision == "bf16" else D.FP32
     sa, ba = I.small_arch(s.n_species), I.big_arch(s.n_species)
-    with D.Context(s, ba, I.init_params(ba, 3), sa, I.init_params(sa, 2), precision=prec) as ctx:
+    with D.Context(s, ba, I.init_params(ba, 3), sa, I.init_params(sa, 2), precision=prec,
+                   options=args.options) as ctx:
         ctx.set_state(s.x)
         which = D.BIG if args.which == "big" else D.SMALL
         if args.respa:
