@@ -124,8 +124,9 @@ typedef struct {
  * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
  * "autotune" (default 1: pick the kernels' work granularity by timing),
  * "atoms_per_cta_big" / "atoms_per_cta_small" (atoms per thread block of the
- * force kernels), "skin" (default 1.0 Angstrom, in [0, 10]: Verlet-skin
- * neighbour lists; 0 builds the pair list from scratch at every evaluation).
+ * force kernels), "skin" (default 0, in [0, 10] Angstrom: Verlet-skin
+ * neighbour lists; 0 builds the pair list from scratch at every evaluation,
+ * which measured faster on liquid water at 3 fs outer steps).
  * With a skin, candidate rows of all j within rc + skin are kept from the
  * last rebuild and filtered with the exact cutoff test at every evaluation,
  * which yields the same pair set as a fresh build; both models' rows are

@@ -13,8 +13,10 @@ namespace dmts {
 constexpr double kAccel = 9.648533215665327e-3;
 constexpr double kKinetic = 103.64269652680505;
 
+// x - L floor(x / L) for periodic boxes; coordinates already inside [0, L)
+// are returned as they are (the common case needs no FP64 division).
 __device__ __forceinline__ double wrap_coord(double x, double L) {
-    return L > 0.0 ? x - L * floor(x / L) : x;
+    return (L > 0.0 && (x < 0.0 || x >= L)) ? x - L * floor(x / L) : x;
 }
 
 __device__ __forceinline__ unsigned int fixed_of(double v, double o, double inv) {
@@ -80,42 +82,46 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
                             const double* __restrict__ inv_m, const float* __restrict__ fs,
                             const float* __restrict__ fb, const int* __restrict__ sys,
                             const double* __restrict__ box, const Frame* __restrict__ frame,
-                            uint4* __restrict__ q, int* __restrict__ flags) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int s = sys[i];
-    double L = box[s];
-    Frame fr = frame[s];
-    double im = inv_m[i];
-    unsigned int qc[3];
-    bool ok = true;
-    for (int c = 0; c < 3; ++c) {
-        size_t o = (size_t)c * n + i;
-        double vv = v[o];
-        double Fs = (double)fs[o];
-        if (first) vv = vv + c_outer * im * ((double)fb[o] - Fs);
-        else vv = vv + c_inner * im * Fs;
-        vv = vv + c_inner * im * Fs;
-        double xx = wrap_coord(x[o] + half_h * vv, L);
-        xx = wrap_coord(xx + half_h * vv, L);
-        ok = ok && isfinite(vv) && isfinite(xx);
-        v[o] = vv;
-        x[o] = xx;
-        double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
-        qc[c] = fixed_of(xx, oc, fr.inv);
+                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    if (i < n) {
+        int s = sys[i];
+        double L = box[s];
+        Frame fr = frame[s];
+        double im = inv_m[i];
+        unsigned int qc[3];
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            size_t o = (size_t)c * n + i;
+            double vv = v[o];
+            double Fs = (double)fs[o];
+            if (first) vv = vv + c_outer * im * ((double)fb[o] - Fs);
+            else vv = vv + c_inner * im * Fs;
+            vv = vv + c_inner * im * Fs;
+            double xx = wrap_coord(x[o] + half_h * vv, L);
+            xx = wrap_coord(xx + half_h * vv, L);
+            ok = ok && isfinite(vv) && isfinite(xx);
+            v[o] = vv;
+            x[o] = xx;
+            double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
+            qc[c] = fixed_of(xx, oc, fr.inv);
+        }
+        q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+        if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+        if (vc.st) m = vl_disp2(x, vc.xref, (size_t)n, (size_t)i, L, vc.thr2);
     }
-    q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
-    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+    if (vc.st) vl_block_decide(m, vc);               // the neighbour-list check of the new positions
 }
 
 void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
-                      const Frame* frame, uint4* q, int* flags, cudaStream_t s) {
+                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
-                                                     frame, q, flags);
+                                                     frame, q, flags, vc);
     count_launch();
 }
 
@@ -158,35 +164,40 @@ __global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x
                          double* __restrict__ v, const double* __restrict__ inv_m,
                          const float* __restrict__ f, const int* __restrict__ sys,
                          const double* __restrict__ box, const Frame* __restrict__ frame,
-                         uint4* __restrict__ q, int* __restrict__ flags) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int s = sys[i];
-    double L = box[s];
-    Frame fr = frame[s];
-    double im = inv_m[i];
-    unsigned int qc[3];
-    bool ok = true;
-    for (int c = 0; c < 3; ++c) {
-        size_t o = (size_t)c * n + i;
-        double vv = v[o] + c_half * im * (double)f[o];
-        double xx = wrap_coord(x[o] + dt * vv, L);
-        ok = ok && isfinite(vv) && isfinite(xx);
-        v[o] = vv;
-        x[o] = xx;
-        double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
-        qc[c] = fixed_of(xx, oc, fr.inv);
+                         uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    if (i < n) {
+        int s = sys[i];
+        double L = box[s];
+        Frame fr = frame[s];
+        double im = inv_m[i];
+        unsigned int qc[3];
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            size_t o = (size_t)c * n + i;
+            double vv = v[o] + c_half * im * (double)f[o];
+            double xx = wrap_coord(x[o] + dt * vv, L);
+            ok = ok && isfinite(vv) && isfinite(xx);
+            v[o] = vv;
+            x[o] = xx;
+            double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
+            qc[c] = fixed_of(xx, oc, fr.inv);
+        }
+        q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+        if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+        if (vc.st) m = vl_disp2(x, vc.xref, (size_t)n, (size_t)i, L, vc.thr2);
     }
-    q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
-    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+    if (vc.st) vl_block_decide(m, vc);
 }
 
 void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const double* inv_mass, const float* f, const int* sys_of_atom,
-                   const double* box, const Frame* frame, uint4* q, int* flags, cudaStream_t s) {
+                   const double* box, const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
+                   cudaStream_t s) {
     if (n_atoms == 0) return;
     k_vv_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, dt, x, v, inv_mass, f, sys_of_atom,
-                                                  box, frame, q, flags);
+                                                  box, frame, q, flags, vc);
     count_launch();
 }
 

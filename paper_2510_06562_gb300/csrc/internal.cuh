@@ -68,6 +68,14 @@ struct VerletState {
     long long n_checks, n_rebuilds;
 };
 
+// A displacement check run inside a kernel that has just written x (the
+// integrator) or by k_vl_check. st == nullptr: no check.
+struct VerletCheck {
+    const double* xref;
+    VerletState* st;
+    double thr2;
+};
+
 // Everything the neighbour builder needs for one model.
 struct NbrArgs {
     int n_atoms;
@@ -158,8 +166,8 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s);
 // gated candidate build (a.nbr_tmp / a.nbr_cnt / a.row_cap = candidate rows),
 // gated candidate-from-candidate filter, and the per-evaluation exact filter
 // of candidate rows into the CSR.
-void launch_vl_check(int n_atoms, const double* x, const double* xref, const int* sys_of_atom,
-                     const double* box, double thr2, VerletState* st, cudaStream_t s);
+void launch_vl_check(int n_atoms, const double* x, const int* sys_of_atom, const double* box,
+                     const VerletCheck& vc, cudaStream_t s);
 void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
                         int* cell_atoms, int* atom_cell, int* atom_slot, const int* gate, cudaStream_t s);
 void launch_vl_build(const NbrArgs& a, cudaStream_t s);
@@ -205,7 +213,7 @@ void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t 
 void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
-                      const Frame* frame, uint4* q, int* flags, cudaStream_t s);
+                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc, cudaStream_t s);
 // after the big force: last inner post-kick and the outer half-kick.
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, const float* f_small, const float* f_big,
@@ -213,7 +221,8 @@ void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
 // velocity Verlet: half-kick + drift + wrap + quantise; half-kick + kinetic energy.
 void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const double* inv_mass, const float* f, const int* sys_of_atom,
-                   const double* box, const Frame* frame, uint4* q, int* flags, cudaStream_t s);
+                   const double* box, const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
+                   cudaStream_t s);
 void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
                     cudaStream_t s);
@@ -253,6 +262,56 @@ __device__ __forceinline__ float rep_phi(float d, float a, float inv_rho, float 
 __device__ __forceinline__ float silu_f(float a, float& sig) {
     sig = 1.0f / (1.0f + __expf(-a));
     return a * sig;
+}
+
+// Squared displacement of one atom since the rebuild; periodic boxes take
+// the nearest image (a move of L/2 or more trips the check either way).
+// NaN counts as a large move.
+__device__ __forceinline__ double vl_disp2(const double* __restrict__ x, const double* __restrict__ xref,
+                                           size_t n, size_t i, double L, double thr2) {
+    double d2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d = x[c * n + i] - xref[c * n + i];
+        if (L > 0.0) {
+            if (d > 0.5 * L) d -= L;
+            else if (d < -0.5 * L) d += L;
+        }
+        d2 += d * d;
+    }
+    return (d2 <= thr2) ? d2 : fmax(d2, 2.0 * thr2 + 1.0);
+}
+
+// Reduce the block's largest squared displacement m into vc.st; the last
+// block to finish sets the rebuild gate, clears the accumulator and counts.
+// Every thread of every block must call it.
+__device__ __forceinline__ void vl_block_decide(double m, const VerletCheck& vc) {
+    __shared__ double vl_wmax[32];
+    __shared__ bool vl_last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) vl_wmax[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)((blockDim.x + 31) >> 5); ++k) m = fmax(m, vl_wmax[k]);
+        atomicMax(&vc.st->max_d2, (unsigned long long)__double_as_longlong(m));
+        __threadfence();
+        vl_last = atomicAdd(&vc.st->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (vl_last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicAdd(&vc.st->max_d2, 0ull));
+        const int force = *(volatile int*)&vc.st->force;
+        const int rb = (force || mx > vc.thr2) ? 1 : 0;
+        vc.st->rebuild = rb;
+        vc.st->force = 0;
+        vc.st->max_d2 = 0ull;
+        vc.st->done = 0u;
+        vc.st->n_checks += 1;
+        vc.st->n_rebuilds += rb;
+    }
 }
 
 // Edge vector r_ij = x_j - x_i from fixed-point coordinates: the wrapped

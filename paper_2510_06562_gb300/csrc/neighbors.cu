@@ -306,8 +306,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
         int j = -1;
         if (v < total) {
             if (a.nc > 0) {
-                int c = 0;
-                while (c < 26 && cpre[c + 1] <= v) ++c;
+                int c = 0;                                   // last of the 27 cells with cpre[c] <= v
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (c + step < 27 && cpre[c + step] <= v) c += step;
                 j = a.cell_atoms[cstart[c] + (v - cpre[c])];
             } else {
                 j = base + v;
@@ -400,56 +402,20 @@ __global__ void __launch_bounds__(256) k_row_filter(NbrArgs a) {
     }
 }
 
-// Largest squared displacement since the rebuild (minimum image in periodic
-// boxes), reduced over CTAs; the last CTA to finish takes the decision.
-__global__ void __launch_bounds__(256) k_vl_check(int n, const double* __restrict__ x, const double* __restrict__ xref,
-                                                  const int* __restrict__ sys, const double* __restrict__ box,
-                                                  double thr2, VerletState* st) {
-    __shared__ double wmax[8];
-    __shared__ bool last;
+// Largest squared displacement since the rebuild, reduced over CTAs; the
+// last CTA to finish takes the decision (vl_block_decide).
+__global__ void __launch_bounds__(256) k_vl_check(int n, const double* __restrict__ x, const int* __restrict__ sys,
+                                                  const double* __restrict__ box, VerletCheck vc) {
     double m = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double L = box[sys[i]];
-        double d2 = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double d = x[(size_t)c * n + i] - xref[(size_t)c * n + i];
-            if (L > 0.0) d -= L * rint(d / L);
-            d2 += d * d;
-        }
-        if (!(d2 <= thr2)) d2 = fmax(d2, 2.0 * thr2 + 1.0);   // NaN counts as a large move
-        m = fmax(m, d2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) wmax[w] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, wmax[k]);
-        atomicMax(&st->max_d2, (unsigned long long)__double_as_longlong(m));
-        __threadfence();
-        last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const double mx = __longlong_as_double((long long)atomicAdd(&st->max_d2, 0ull));
-        const int force = *(volatile int*)&st->force;
-        const int rb = (force || mx > thr2) ? 1 : 0;
-        st->rebuild = rb;
-        st->force = 0;
-        st->max_d2 = 0ull;
-        st->done = 0u;
-        st->n_checks += 1;
-        st->n_rebuilds += rb;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = fmax(m, vl_disp2(x, vc.xref, (size_t)n, (size_t)i, box[sys[i]], vc.thr2));
+    vl_block_decide(m, vc);
 }
 
-void launch_vl_check(int n_atoms, const double* x, const double* xref, const int* sys_of_atom,
-                     const double* box, double thr2, VerletState* st, cudaStream_t s) {
+void launch_vl_check(int n_atoms, const double* x, const int* sys_of_atom, const double* box,
+                     const VerletCheck& vc, cudaStream_t s) {
     const int g = std::max(1, std::min(4 * 152, (n_atoms + 255) / 256));
-    k_vl_check<<<g, 256, 0, s>>>(n_atoms, x, xref, sys_of_atom, box, thr2, st);
+    k_vl_check<<<g, 256, 0, s>>>(n_atoms, x, sys_of_atom, box, vc);
     count_launch();
 }
 

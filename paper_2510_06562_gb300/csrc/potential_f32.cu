@@ -655,22 +655,25 @@ int max_atoms_per_cta_f32(int F, int K, bool bwd) {
 
 // ------------------------------------------------------------ reductions
 // Per-system FP64 sums in a fixed order (deterministic): one CTA per system,
-// strided partial sums, then a fixed-shape tree.
+// strided partial sums, then fixed-shape shuffle trees (deterministic).
 template <int NT>
 __global__ void __launch_bounds__(NT) k_system_sum(int n_sys, const int* __restrict__ off,
                                                   const double* __restrict__ v, double* __restrict__ out,
                                                   int stride) {
-    __shared__ double sh[NT];
-    int s = blockIdx.x;
+    __shared__ double wsum[NT / 32];
+    const int s = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double acc = 0.0;
     for (int i = off[s] + threadIdx.x; i < off[s + 1]; i += NT) acc += v[i];
-    sh[threadIdx.x] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsum[w] = acc;
     __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    if (w == 0) {
+        double t = lane < NT / 32 ? wsum[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) out[(size_t)s * stride] = t;
     }
-    if (threadIdx.x == 0) out[(size_t)s * stride] = sh[0];
 }
 
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
