@@ -19,6 +19,7 @@ same step) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -193,6 +194,37 @@ def measure(D, I, torch, s, models_, prec, args, flush, dt, n_inner, seed):
     return out
 
 
+KERNEL_OF_STAGE = {
+    # (precision is BF16, stage prefix) -> (kernel name in the ncu capture, source file)
+    (True, "edge_bwd"): ("k_edge_bwd_bf16<64,3>", "potential_bf16.cu"),
+    (True, "edge_fwd"): ("k_edge_fwd_bf16<64>", "potential_bf16.cu"),
+    (False, "edge_bwd"): ("k_edge_bwd<64,16>", "potential_f32.cu"),
+    (False, "edge_fwd"): ("k_edge_fwd<64,16>", "potential_f32.cu"),
+}
+
+
+def captured_traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` (template arguments without spaces)
+    from a committed ncu summary under profiles/ (a line `counters:
+    kernel=... source_sha256=... dram_bytes_per_launch=...`), or None when
+    there is none or the kernel's source changed since the capture."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "paper_2510_06562_gb300", "csrc", source)
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    pdir = os.path.join(here, "profiles")
+    for name in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        for line in open(os.path.join(pdir, name), errors="replace"):
+            if "counters:" not in line:
+                continue
+            fields = dict(kv.split("=", 1) for kv in line.split("counters:", 1)[1].split() if "=" in kv)
+            if fields.get("kernel") == kernel and fields.get("source_sha256") == sha and "dram_bytes_per_launch" in fields:
+                return float(fields["dram_bytes_per_launch"])
+    return None
+
+
 def roofline_of(D, prec, stages_big, E_big, ba):
     dom = max((k for k in stages_big if k.startswith("edge_")), key=lambda k: stages_big[k])
     K, F = ba.n_radial, ba.n_feat
@@ -204,8 +236,9 @@ def roofline_of(D, prec, stages_big, E_big, ba):
         flop_edge = 2 * (2 * 16 * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (16 * F + F * F)
         peak, bound, src, kind = measured_peak("bf16_tflops"), "tensor", "MEASURED_PEAKS.json bf16_tflops (burst)", "BF16 tcgen05"
     achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
+    kname, ksrc = KERNEL_OF_STAGE[(prec != D.FP32, dom[:8])]
     return {"kernel": f"{dom} (big model, {kind})", "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic(kname, ksrc),
             "algorithmic_flop_per_launch": flop_edge * E_big, "launch_ms": stages_big[dom], "peak_source": src}
 
 

@@ -686,50 +686,37 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
 // do not change; the tensor-core kernels group a row's partial sums by tile,
 // so theirs can change at the rounding level. Runs once per context, at the
 // first evaluation.
+int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc);
+
 int autotune_models(dmts_ctx* c) {
     if (!c->autotune || c->tuned) return DMTS_OK;
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
     int rc = DMTS_OK;
     for (int w = 0; w < 2 && rc == DMTS_OK; ++w) {
         Model& m = c->m[w];
         if (!m.present) continue;
         const bool tc = m.precision == DMTS_BF16_MLP;
-        std::vector<int> cand = tc ? std::vector<int>{4, 8, 16, 32}
+        std::vector<int> cand = tc ? std::vector<int>{4, 8, 12, 16, 24, 32}
                                    : (m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48});
         const int lim_f = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, false);
         const int lim_b = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, true);
-        float best = 1e30f;
+        double best_tf = 1e30, best_tb = 1e30;
         int best_f = m.apc_fwd, best_b = m.apc_bwd;
         for (int A : cand) {
             m.apc_fwd = std::min(A, lim_f);
             m.apc_bwd = std::min(A, lim_b);
-            if ((rc = reset_flags(c))) break;
-            enqueue_eval(c, w, true);                    // warm-up (sizes capacities)
-            if ((rc = sync_check(c))) break;
-            if (c->h_flags[kFlagOverflow]) {
-                if ((rc = grow_capacity(c))) break;
-                continue;
+            std::vector<double> st;
+            if ((rc = time_stages_impl(c, w, 3, st))) break;   // sizes capacities, then times the stages
+            double tf = 0.0, tb = 0.0;                          // forward and backward edge passes
+            for (int l = 0; l < m.L; ++l) {
+                tf += st[2 + l];
+                tb += st[2 + 2 * m.L + l];
             }
-            float total = 0.f;
-            for (int r = 0; r < 3; ++r) {
-                CUDA_TRY(cudaEventRecord(e0, c->stream));
-                enqueue_eval(c, w, true);
-                CUDA_TRY(cudaEventRecord(e1, c->stream));
-                CUDA_TRY(cudaEventSynchronize(e1));
-                float t = 0.f;
-                CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-                total += t;
-            }
-            if ((rc = sync_check(c))) break;
-            if (total < best) { best = total; best_f = m.apc_fwd; best_b = m.apc_bwd; }
+            if (tf < best_tf) { best_tf = tf; best_f = m.apc_fwd; }
+            if (tb < best_tb) { best_tb = tb; best_b = m.apc_bwd; }
         }
         m.apc_fwd = best_f;
         m.apc_bwd = best_b;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     c->tuned = true;
     return rc;
@@ -1186,10 +1173,25 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
     if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
     if (reps < 1 || !ms_out) return fail(DMTS_ERR_ARG, "reps must be >= 1 and ms_out non-NULL");
     LaunchScope ls(c);
+    const int n_st = 3 + 4 * c->m[which].L;
+    if (n_out < n_st) return fail(DMTS_ERR_ARG, "ms_out needs %d entries", n_st);
+    std::vector<double> acc;
+    int rc = time_stages_impl(c, which, reps, acc);
+    if (rc) return rc;
+    for (int k = 0; k < n_st; ++k) ms_out[k] = acc[k];
+    return n_st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Per-stage milliseconds of one evaluation of model `which` (CUDA events on
+// the context's stream, mean over reps), in the order of dmts_time_stages.
+int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc) {
     Model& m = c->m[which];
     const int L = m.L;
     const int n_st = 3 + 4 * L;
-    if (n_out < n_st) return fail(DMTS_ERR_ARG, "ms_out needs %d entries", n_st);
     int rc;
     // one untimed evaluation sizes the capacities
     if ((rc = reset_flags(c))) return rc;
@@ -1204,7 +1206,7 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
     cudaStream_t s = c->stream;
     std::vector<cudaEvent_t> ev(2 * n_st);
     for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
-    std::vector<double> acc(n_st, 0.0);
+    acc.assign(n_st, 0.0);
     for (int r = 0; r < reps; ++r) {
         auto begin = [&](int slot) { cudaEventRecord(ev[2 * slot], s); };
         auto end = [&](int slot) { cudaEventRecord(ev[2 * slot + 1], s); };
@@ -1257,10 +1259,13 @@ int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < n_st; ++k) ms_out[k] = acc[k] / reps;
-    if ((rc = sync_check(c))) return rc;
-    return n_st;
+    for (int k = 0; k < n_st; ++k) acc[k] /= reps;
+    return sync_check(c);
 }
+
+}  // namespace
+
+extern "C" {
 
 long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
 

@@ -276,8 +276,7 @@ template <int F>
 struct FwdSmem {
     unsigned char w1t[F * kKP * 2];
     unsigned char w2t[F * F * 2];
-    unsigned char a1[kT * kKP * 2];
-    unsigned char a2[kT * F * 2];
+    unsigned char a1[kT * kKP * 2];     // (the second MMA's A operand lives in tensor memory)
     float b1[F], b2[F];
     float P[kT * F];                    // u_j rows, then messages (swizzled rows)
     int row[kT];
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
     const uint32_t tmem = S.taddr;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const uint32_t idesc = idesc_bf16_f32(128, F);
-    const uint32_t sA1 = smem_u32(S.a1), sA2 = smem_u32(S.a2);
+    const uint32_t sA1 = smem_u32(S.a1);
     const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t);
     uint32_t phase = 0;
     bool ok = true;
@@ -376,27 +375,29 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             ok = mbar_wait(&S.mbar, phase, kWaitIter);
             phase ^= 1;
             fence_after_sync();
+            // SiLU(a) as BF16 pairs written back over the first F/2 columns of
+            // D1 (each block of 16 columns is read before its 8 packed columns
+            // are written): the second MMA reads its A operand from there
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + lane_base + c, v);
+                uint32_t pk[8];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    float x = v[q] + S.b1[c + q];
-                    v[q] = x * sigmoid_fast(x);
+                for (int q = 0; q < 16; q += 2) {
+                    const float x0 = v[q] + S.b1[c + q], x1 = v[q + 1] + S.b1[c + q + 1];
+                    pk[q / 2] = pack_bf16(x0 * sigmoid_fast(x0), x1 * sigmoid_fast(x1));
                 }
-                st_row8(S.a2, tid, c, F, v);
-                st_row8(S.a2, tid, c + 8, F, v + 8);
+                tmem_st8(tmem + lane_base + c / 2, pk);
             }
-            fence_proxy_async();
+            tmem_st_wait();
             fence_before_sync();
             ok = __syncthreads_and(ok);
             fence_after_sync();
             if (tid == 0 && ok) {
 #pragma unroll
                 for (int kk = 0; kk < F / 16; ++kk)
-                    mma_bf16(tmem + F, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
-                             idesc, kk > 0);
+                    mma_bf16_ta(tmem + F, tmem + kk * 8, make_desc(sW2T + kk * 256, 128, F * 16), idesc, kk > 0);
                 mma_commit(&S.mbar);
             }
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
@@ -580,18 +581,25 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             ok = mbar_wait(&S.mbar, phase, kWaitIter);
             phase ^= 1;
             fence_after_sync();
+            // SiLU(a) -> BF16 operand of the next MMA; p = SiLU'(a) (e' W1), the
+            // factor the basis-derivative term needs, replaces D1 in tensor memory
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
-                float v[16];
+                float v[16], tv[16];
                 tmem_ld16(tD1 + lane_base + c, v);
+                tmem_ld16(tD4 + lane_base + c, tv);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    float x = v[q] + S.b1[c + q];
-                    v[q] = x * sigmoid_fast(x);
+                    const float x = v[q] + S.b1[c + q];
+                    const float sg = sigmoid_fast(x);
+                    v[q] = x * sg;
+                    tv[q] *= sg * (1.f + x * (1.f - sg));
                 }
                 st_row8(S.a2, tid, c, F, v);
                 st_row8(S.a2, tid, c + 8, F, v + 8);
+                tmem_st16(tD1 + lane_base + c, tv);
             }
+            tmem_st_wait();
             fence_proxy_async();
             fence_before_sync();
             ok = __syncthreads_and(ok);
@@ -662,16 +670,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             float s2 = 0.f;
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
-                float ab[16], av[16], tv[16];
+                float ab[16], pv[16];
                 tmem_ld16(tD3 + lane_base + c, ab);
-                tmem_ld16(tD1 + lane_base + c, av);
-                tmem_ld16(tD4 + lane_base + c, tv);
+                tmem_ld16(tD1 + lane_base + c, pv);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    float x = av[q] + S.b1[c + q];
-                    float sg = sigmoid_fast(x);
-                    s2 += ab[q] * (sg * (1.f + x * (1.f - sg))) * tv[q];
-                }
+                for (int q = 0; q < 16; ++q) s2 += ab[q] * pv[q];
             }
             float se = dfc * gphi + fc * s2;
             if (l == 0 && valid) {
