@@ -12,7 +12,8 @@ with plain PyTorch CPU float64 operations:
                 virial, and the force-matching loss gradient (double
                 backward) of the distillation step;
 * ``integrate`` velocity Verlet and the RESPA multiple-time-step step of
-                Algorithm 1 (thermostat = identity, NVE).
+                Algorithm 1, NVE or with the Langevin O-step (BAOAB) and its
+                counter-based noise; hydrogen mass repartitioning.
 
 Pins (tests marked ``not gpu``) tie it to the mathematics: finite
 differences, invariances, closed-form degenerate cases, textbook special cases

@@ -7,6 +7,14 @@
   large force and a second half-kick with F - F_small.
 * ``velocity_verlet`` is the textbook single-time-step scheme: half-kick,
   full drift, force, half-kick.
+* With ``thermo`` given, both become Langevin schemes: Algorithm 1's
+  thermostat step (between the two half-drifts of each inner step) is the
+  exact Ornstein-Uhlenbeck update of the velocities (the "O" of BAOAB), and
+  velocity Verlet becomes BAOAB (half-kick, half-drift, O, half-drift,
+  force, half-kick), the paper's single-time-step reference. The friction
+  is 1 ps^-1 in the paper (section "Simulation details").
+* ``hmr_masses`` is hydrogen mass repartitioning: each hydrogen's mass is
+  raised to a target and the excess is taken from its bonded heavy atom.
 
 Positions of periodic systems are wrapped into [0, L) after every drift
 (x - L floor(x / L)); the paper does not say where its engines wrap.
@@ -26,7 +34,81 @@ ACCEL = (1.602176634e-19 / 1e-10) / 1.66053906660e-27 / 1e20
 # 1 amu (A/fs)^2 in eV: the inverse of ACCEL.
 KE_EV = 1.0 / ACCEL
 
+# Boltzmann constant in eV/K (CODATA 2018, exact by the SI definitions).
+KB_EV = 8.617333262e-5
+
 Force = Callable[[np.ndarray], np.ndarray]
+
+_M32 = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, "Parallel
+    random numbers: as easy as 1, 2, 3", SC 2011): a counter-based generator
+    whose output for a 128-bit counter and a 64-bit key is a fixed bijection
+    of the counter. ``ctr`` [n, 4] and ``key`` [2] hold 32-bit words; returns
+    [n, 4] uint32. Each round multiplies words 0 and 2 by the two Philox
+    multipliers, crosses the high halves with words 1 and 3 and the key, and
+    the key advances by the two Weyl constants between rounds."""
+    c = np.asarray(ctr, dtype=np.uint64).reshape(-1, 4) & _M32
+    k0, k1 = int(key[0]) & _M32, int(key[1]) & _M32
+    m0, m1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + 0x9E3779B9) & _M32
+            k1 = (k1 + 0xBB67AE85) & _M32
+        p0 = c[:, 0] * m0
+        p1 = c[:, 2] * m1
+        c = np.stack([(p1 >> np.uint64(32)) ^ c[:, 1] ^ np.uint64(k0), p1 & np.uint64(_M32),
+                      (p0 >> np.uint64(32)) ^ c[:, 3] ^ np.uint64(k1), p0 & np.uint64(_M32)], axis=1)
+    return c.astype(np.uint32)
+
+
+def langevin_normals(n_atoms: int, step: int, seed: int) -> np.ndarray:
+    """Three standard normal deviates per atom for inner step ``step``: one
+    Philox call per atom with counter (atom, step low word, step high word, 0)
+    and key (seed low word, seed high word); the four words become uniforms
+    u = (w + 1/2) / 2^32 and the Box-Muller pairs (u0, u1) -> two normals,
+    (u2, u3) -> one."""
+    i = np.arange(n_atoms, dtype=np.uint64)
+    ctr = np.stack([i, np.full_like(i, step & _M32), np.full_like(i, (step >> 32) & _M32),
+                    np.zeros_like(i)], axis=1)
+    w = philox4x32_10(ctr, (seed & _M32, (seed >> 32) & _M32)).astype(np.float64)
+    u = (w + 0.5) / 4294967296.0
+    r01 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r23 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    return np.stack([r01 * np.cos(2.0 * np.pi * u[:, 1]), r01 * np.sin(2.0 * np.pi * u[:, 1]),
+                     r23 * np.cos(2.0 * np.pi * u[:, 3])], axis=1)
+
+
+def o_step(v, mass, h: float, thermo: dict, step: int):
+    """Exact Ornstein-Uhlenbeck update over time h (fs) at friction
+    thermo["gamma"] (1/fs) and temperature thermo["temperature"] (K):
+    v <- c1 v + sqrt((1 - c1^2) k_B T / m) xi, c1 = exp(-gamma h)."""
+    c1 = np.exp(-thermo["gamma"] * h)
+    c2 = np.sqrt(1.0 - c1 * c1)
+    sigma = np.sqrt(KB_EV * thermo["temperature"] * ACCEL / np.asarray(mass, dtype=np.float64))
+    xi = langevin_normals(len(v), step, thermo["seed"])
+    return c1 * v + (c2 * sigma)[:, None] * xi
+
+
+def hmr_masses(mass, bonds, h_mass: float = 3.024, h_max: float = 1.5):
+    """Hydrogen mass repartitioning: every atom lighter than ``h_max`` amu
+    that is bonded to a heavier atom gets mass ``h_mass``; the difference is
+    subtracted from that bonded heavy atom, so each molecule keeps its total
+    mass. ``bonds`` [n_bonds, 2]; a hydrogen uses its first heavy partner."""
+    m = np.array(mass, dtype=np.float64)
+    m0 = np.asarray(mass, dtype=np.float64)
+    done = np.zeros(len(m), dtype=bool)
+    for a, b in np.asarray(bonds, dtype=np.int64).reshape(-1, 2):
+        for h, heavy in ((a, b), (b, a)):
+            if m0[h] < h_max and m0[heavy] >= h_max and not done[h]:
+                m[heavy] -= h_mass - m0[h]
+                m[h] = h_mass
+                done[h] = True
+    if np.any(m <= 0):
+        raise ValueError("repartitioning leaves a non-positive mass")
+    return m
 
 
 def _wrap(x, box_per_atom):
@@ -48,16 +130,22 @@ def kinetic_energy(v, mass, atom_offset=None):
 
 
 def velocity_verlet(x, v, mass, f: Force, dt: float, n_steps: int,
-                    box_per_atom=None, F=None):
-    """n_steps of velocity Verlet with time step dt; returns (x, v, F)."""
+                    box_per_atom=None, F=None, thermo: dict | None = None, step0: int = 0):
+    """n_steps of velocity Verlet with time step dt; returns (x, v, F).
+    With ``thermo``: BAOAB, step k drawing its noise at counter step0 + k."""
     x = np.array(x, dtype=np.float64)
     v = np.array(v, dtype=np.float64)
     a = ACCEL / np.asarray(mass, dtype=np.float64)[:, None]
     if F is None:
         F = f(x)
-    for _ in range(n_steps):
+    for k in range(n_steps):
         v = v + 0.5 * dt * a * F
-        x = _wrap(x + dt * v, box_per_atom)
+        if thermo is None:
+            x = _wrap(x + dt * v, box_per_atom)
+        else:
+            x = _wrap(x + (0.5 * dt) * v, box_per_atom)
+            v = o_step(v, mass, dt, thermo, step0 + k)
+            x = _wrap(x + (0.5 * dt) * v, box_per_atom)
         F = f(x)
         v = v + 0.5 * dt * a * F
     return x, v, F
@@ -66,9 +154,11 @@ def velocity_verlet(x, v, mass, f: Force, dt: float, n_steps: int,
 def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int,
           n_outer: int, box_per_atom=None, F_small=None, F=None,
           energy_big: Callable[[np.ndarray], float] | None = None,
-          atom_offset=None):
-    """n_outer steps of Algorithm 1 (thermo = identity) with outer step dt and
-    n_slow inner steps of dt / n_slow.
+          atom_offset=None, thermo: dict | None = None, step0: int = 0):
+    """n_outer steps of Algorithm 1 with outer step dt and n_slow inner steps
+    of dt / n_slow. thermo = None: the identity (NVE); else the O-step
+    (``o_step``) with inner step j of outer step s drawing its noise at
+    counter step0 + s n_slow + j.
 
     ``F_small`` and ``F`` carry the forces at ``x`` between calls; when either
     is None this is the algorithm's first step and both are evaluated.
@@ -85,12 +175,13 @@ def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int,
         F = f_big(x)
     h = dt / n_slow
     out = []
-    for _ in range(n_outer):
+    for s in range(n_outer):
         v = v + (0.5 * dt) * a * (F - F_small)
-        for _ in range(n_slow):
+        for j in range(n_slow):
             v = v + (0.5 * h) * a * F_small
             x = _wrap(x + (0.5 * h) * v, box_per_atom)
-            # thermo(v, h) = v  (NVE)
+            if thermo is not None:                          # v <- thermo(v, h)
+                v = o_step(v, mass, h, thermo, step0 + s * n_slow + j)
             x = _wrap(x + (0.5 * h) * v, box_per_atom)
             F_small = f_small(x)
             v = v + (0.5 * h) * a * F_small
