@@ -135,6 +135,16 @@ typedef struct {
  * The paper does not describe its neighbour search; this is an
  * implementation choice that leaves every result unchanged up to the order
  * of floating-point additions.
+ * "langevin_friction" (default 0 = NVE, in ps^-1; the paper uses 1),
+ * "temperature" (K, default 300), "seed" (default 0): Algorithm 1's
+ * thermostat step thermo(v, h) becomes the exact Ornstein-Uhlenbeck update
+ * v <- c1 v + sqrt((1 - c1^2) k_B T / m) xi, c1 = exp(-gamma h), between the
+ * two half-drifts of every inner step, and velocity Verlet (no small model)
+ * becomes BAOAB. xi are standard normals from Philox-4x32-10 with counter
+ * (atom index, inner-step counter low/high words, 0) and key (seed low/high
+ * words), Box-Muller on the four uniforms (w + 1/2) 2^-32: (u0, u1) give the
+ * x and y components, (u2, u3) the z component. The inner-step counter
+ * starts at 0 at dmts_set_state and advances by n_inner per outer step.
  * On success *out holds the new context; on failure *out is NULL. */
 DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big,
                 const dmts_system_desc* sys, const char* options, dmts_ctx** out);
@@ -190,6 +200,17 @@ DMTS_API void* dmts_stream(dmts_ctx* ctx);
 /* Number of the library's kernel launches since the context was created
  * (including launches inside CUDA graph replays). */
 DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
+
+/* Hydrogen mass repartitioning (the paper's HMR; the target mass is the
+ * caller's choice, commonly 3.024 amu). Every atom lighter than 1.5 amu that
+ * is bonded to an atom of at least 1.5 amu gets mass h_mass, and the
+ * difference is taken from that bonded heavy atom (the first such partner in
+ * bond order), so every molecule keeps its total mass. mass [n_atoms] in,
+ * mass_out [n_atoms] out (may alias mass), bonds [n_bonds][2] atom indices.
+ * Host-only; needs no context or GPU. DMTS_ERR_ARG if a bond index is out of
+ * range or a mass would become <= 0 (mass_out is then not written). */
+DMTS_API int dmts_hmr_masses(int n_atoms, const double* mass, int n_bonds, const int* bonds, double h_mass,
+                             double* mass_out);
 
 /* Verlet-skin statistics since the context was created: displacement checks
  * run (one per evaluation at new positions) and candidate-row rebuilds among

@@ -127,6 +127,10 @@ struct dmts_ctx {
     int vl_src = 1;
     double* d_xref = nullptr;           // FP64 SoA [3][N], positions of the last rebuild
     VerletState* d_vl = nullptr;
+    // Langevin thermostat of Algorithm 1 (friction 0: NVE)
+    double friction_ps = 0.0, temperature = 300.0;
+    unsigned long long seed = 0;
+    unsigned long long* d_rng = nullptr;   // [0] inner-step counter of the noise, [1] copy at call entry
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
     bool broken = false;
@@ -459,6 +463,21 @@ NbrArgs candidate_args(dmts_ctx* c, int w) {
     return a;
 }
 
+// Thermostat parameters for inner steps of length h (fs).
+Langevin langevin(dmts_ctx* c, double h) {
+    Langevin lg{};
+    lg.step = c->d_rng;
+    if (!(c->friction_ps > 0.0)) return lg;
+    const double gamma = c->friction_ps * 1e-3;             // 1/fs
+    lg.on = 1;
+    lg.c1 = exp(-gamma * h);
+    lg.c2 = sqrt(1.0 - lg.c1 * lg.c1);
+    lg.kT_accel = 8.617333262e-5 * c->temperature * accel_constant();
+    lg.key0 = (uint32_t)(c->seed & 0xffffffffull);
+    lg.key1 = (uint32_t)(c->seed >> 32);
+    return lg;
+}
+
 VerletCheck verlet_check(dmts_ctx* c) {
     VerletCheck vc{};
     if (c->skin <= 0) return vc;
@@ -642,21 +661,22 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     const VerletCheck vc = verlet_check(c);
     if (c->m[0].present) {
         double h = dt / n_inner;
+        const Langevin lg = langevin(c, h);
         for (int k = 0; k < n_inner; ++k) {
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, vc,
-                             s);
+                             lg, k, s);
             enqueue_eval(c, 0, nonper, false, Check::Done);   // the small model's energy is not reported
         }
         enqueue_eval(c, 1, false, true, Check::None);          // same positions as the last small evaluation
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
-                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, s);
+                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, s);
     } else {
         launch_vv_pre(c->N, 0.5 * dt * acc, dt, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,
-                      c->d_frame, c->d_q, c->d_flags, vc, s);
+                      c->d_frame, c->d_q, c->d_flags, vc, langevin(c, dt), s);
         enqueue_eval(c, 1, nonper, true, Check::Done);
         launch_vv_post(c->N, 0.5 * dt * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
-                       c->d_flags, s);
+                       c->d_flags, c->d_rng, s);
     }
     launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, s);
     launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
@@ -774,7 +794,7 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
-    dfree(c->d_xref); dfree(c->d_vl);
+    dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng);
     dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
     dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -839,6 +859,15 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
         return fail(DMTS_ERR_ARG, "skin must be in [0, 10] A");
     }
     c->vl_thr2 = 0.25 * c->skin * c->skin * (1.0 - 2e-3);
+    c->friction_ps = json_number(options, "langevin_friction", 0.0);
+    c->temperature = json_number(options, "temperature", 300.0);
+    const double seed_d = json_number(options, "seed", 0.0);
+    if (!(c->friction_ps >= 0.0) || !(c->temperature >= 0.0) || !(seed_d >= 0.0) || seed_d > 9.0e15 ||
+        !isfinite(c->friction_ps) || !isfinite(c->temperature)) {
+        delete c;
+        return fail(DMTS_ERR_ARG, "langevin_friction and temperature must be >= 0, seed in [0, 9e15]");
+    }
+    c->seed = (unsigned long long)seed_d;
     c->vl_src = (small && small->cutoff > big->cutoff) ? 0 : 1;
 #define CREATE_TRY(expr)                                                          \
     do {                                                                          \
@@ -877,6 +906,8 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(dalloc(&c->d_bfs, (size_t)3 * N));
     CREATE_TRY(dalloc(&c->d_bfb, (size_t)3 * N));
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
+    CREATE_TRY(dalloc(&c->d_rng, 2));
+    CREATE_TRY(cudaMemset(c->d_rng, 0, 2 * sizeof(unsigned long long)));
     if (c->skin > 0) {
         CREATE_TRY(dalloc(&c->d_xref, (size_t)3 * N));
         CREATE_TRY(dalloc(&c->d_vl, 1));
@@ -937,6 +968,7 @@ int dmts_set_state(dmts_ctx* c, const double* x, const double* v, int n_atoms) {
     if (v && (rc = copy_in(c, c->d_stage + n3, v, n3))) return rc;
     launch_set_state(c->N, c->d_stage, v ? c->d_stage + n3 : nullptr, c->d_sys, c->d_box, c->d_x, c->d_v,
                      c->stream);
+    CUDA_TRY(cudaMemsetAsync(c->d_rng, 0, sizeof(unsigned long long), c->stream));   // noise restarts at step 0
     if ((rc = sync_check(c))) return rc;
     c->state_set = true;
     c->forces_valid = false;
@@ -1052,6 +1084,8 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
     const bool valid0 = c->forces_valid;
     CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_rng + 1, c->d_rng, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                             c->stream));
     if (valid0) {
         if (c->m[0].present)
             CUDA_TRY(cudaMemcpyAsync(c->d_bfs, c->m[0].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -1077,6 +1111,8 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         // restore and retry with grown capacity
         CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_rng, c->d_rng + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                 c->stream));
         if (valid0) {
             if (c->m[0].present)
                 CUDA_TRY(cudaMemcpyAsync(c->m[0].force, c->d_bfs, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -1268,6 +1304,33 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
 extern "C" {
 
 long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
+
+int dmts_hmr_masses(int n_atoms, const double* mass, int n_bonds, const int* bonds, double h_mass,
+                    double* mass_out) {
+    g_err.clear();
+    if (n_atoms < 0 || n_bonds < 0) return fail(DMTS_ERR_ARG, "negative count");
+    if ((n_atoms > 0 && (!mass || !mass_out)) || (n_bonds > 0 && !bonds)) return fail(DMTS_ERR_ARG, "NULL array");
+    if (!(h_mass > 0.0) || !isfinite(h_mass)) return fail(DMTS_ERR_ARG, "h_mass must be > 0");
+    const double h_max = 1.5;                      // hydrogens: atoms lighter than 1.5 amu
+    std::vector<double> m(mass, mass + n_atoms);
+    std::vector<char> moved(n_atoms, 0);
+    for (int b = 0; b < n_bonds; ++b) {
+        const int a0 = bonds[2 * b], a1 = bonds[2 * b + 1];
+        if (a0 < 0 || a0 >= n_atoms || a1 < 0 || a1 >= n_atoms) return fail(DMTS_ERR_ARG, "bond %d out of range", b);
+        for (int side = 0; side < 2; ++side) {
+            const int h = side ? a1 : a0, heavy = side ? a0 : a1;
+            if (mass[h] < h_max && mass[heavy] >= h_max && !moved[h]) {
+                m[heavy] -= h_mass - mass[h];
+                m[h] = h_mass;
+                moved[h] = 1;
+            }
+        }
+    }
+    for (int i = 0; i < n_atoms; ++i)
+        if (!(m[i] > 0.0)) return fail(DMTS_ERR_ARG, "repartitioning leaves atom %d with mass %g", i, m[i]);
+    std::copy(m.begin(), m.end(), mass_out);
+    return DMTS_OK;
+}
 
 int dmts_neighbor_stats(dmts_ctx* c, long long* n_checks, long long* n_rebuilds) {
     CTX_GUARD(c);

@@ -1,7 +1,7 @@
-// Integrator kernels: the kicks and drifts of Algorithm 1 (thermostat = the
-// identity, NVE) and of velocity Verlet, on the FP64 SoA state, fused with
-// periodic wrapping and the fixed-point quantisation that the next force
-// evaluation reads. One thread per atom; every kernel streams x, v, 1/m and
+// Integrator kernels: the kicks and drifts of Algorithm 1 (thermostat: the
+// identity, NVE, or the Langevin O-step) and of velocity Verlet (or BAOAB),
+// on the FP64 SoA state, fused with periodic wrapping and the fixed-point
+// quantisation that the next force evaluation reads. One thread per atom; every kernel streams x, v, 1/m and
 // the FP32 forces once.
 #include "internal.cuh"
 
@@ -17,6 +17,41 @@ constexpr double kKinetic = 103.64269652680505;
 // are returned as they are (the common case needs no FP64 division).
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     return (L > 0.0 && (x < 0.0 || x >= L)) ? x - L * floor(x / L) : x;
+}
+
+// Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC 2011): per
+// round, words 0 and 2 are multiplied by the two Philox multipliers, their
+// high halves are crossed with words 1 and 3 and the key; the key advances by
+// the two Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Three standard normals for atom i at inner step t: uniforms (w + 1/2) 2^-32
+// of the four Philox words, Box-Muller on (u0, u1) for two and on (u2, u3)
+// for the third.
+__device__ __forceinline__ void langevin_normals(unsigned int i, unsigned long long t, uint32_t k0, uint32_t k1,
+                                                 double* n) {
+    const uint4 w = philox4x32_10(make_uint4(i, (unsigned int)t, (unsigned int)(t >> 32), 0u), k0, k1);
+    const double s32 = 2.3283064365386963e-10;          // 2^-32
+    const double u0 = ((double)w.x + 0.5) * s32, u1 = ((double)w.y + 0.5) * s32;
+    const double u2 = ((double)w.z + 0.5) * s32, u3 = ((double)w.w + 0.5) * s32;
+    const double r01 = sqrt(-2.0 * log(u0)), r23 = sqrt(-2.0 * log(u2));
+    double sn, cs;
+    sincospi(2.0 * u1, &sn, &cs);
+    n[0] = r01 * cs;
+    n[1] = r01 * sn;
+    n[2] = r23 * cospi(2.0 * u3);
 }
 
 __device__ __forceinline__ unsigned int fixed_of(double v, double o, double inv) {
@@ -82,7 +117,7 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
                             const double* __restrict__ inv_m, const float* __restrict__ fs,
                             const float* __restrict__ fb, const int* __restrict__ sys,
                             const double* __restrict__ box, const Frame* __restrict__ frame,
-                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc) {
+                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg, int k) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (i < n) {
@@ -92,6 +127,11 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
         double im = inv_m[i];
         unsigned int qc[3];
         bool ok = true;
+        double xi[3] = {0.0, 0.0, 0.0}, sig = 0.0;
+        if (lg.on) {
+            langevin_normals((unsigned int)i, *lg.step + (unsigned long long)k, lg.key0, lg.key1, xi);
+            sig = lg.c2 * sqrt(lg.kT_accel * im);
+        }
         for (int c = 0; c < 3; ++c) {
             size_t o = (size_t)c * n + i;
             double vv = v[o];
@@ -100,6 +140,7 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
             else vv = vv + c_inner * im * Fs;
             vv = vv + c_inner * im * Fs;
             double xx = wrap_coord(x[o] + half_h * vv, L);
+            if (lg.on) vv = lg.c1 * vv + sig * xi[c];            // v <- thermo(v, h)
             xx = wrap_coord(xx + half_h * vv, L);
             ok = ok && isfinite(vv) && isfinite(xx);
             v[o] = vv;
@@ -117,11 +158,12 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
 void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
-                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc, cudaStream_t s) {
+                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
+                      const Langevin& lg, int k, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
-                                                     frame, q, flags, vc);
+                                                     frame, q, flags, vc, lg, k);
     count_launch();
 }
 
@@ -131,9 +173,10 @@ __global__ void k_respa_post(int n, double c_outer, double c_inner, double* __re
                              const double* __restrict__ inv_m, const float* __restrict__ fs,
                              const float* __restrict__ fb, const double* __restrict__ x,
                              double* __restrict__ ke, const double* __restrict__ mass,
-                             int* __restrict__ flags) {
+                             int* __restrict__ flags, unsigned long long* __restrict__ step, int advance) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (step && i == 0) *step += (unsigned long long)advance;   // every reader of it ran in earlier kernels
     double im = inv_m[i];
     double v2 = 0.0;
     bool ok = true;
@@ -152,10 +195,11 @@ __global__ void k_respa_post(int n, double c_outer, double c_inner, double* __re
 
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, const float* f_small, const float* f_big,
-                       const double* x, double* ke, const double* mass, int* flags, cudaStream_t s) {
+                       const double* x, double* ke, const double* mass, int* flags,
+                       unsigned long long* step, int advance, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
-                                                      f_big, x, ke, mass, flags);
+                                                      f_big, x, ke, mass, flags, step, advance);
     count_launch();
 }
 
@@ -164,7 +208,7 @@ __global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x
                          double* __restrict__ v, const double* __restrict__ inv_m,
                          const float* __restrict__ f, const int* __restrict__ sys,
                          const double* __restrict__ box, const Frame* __restrict__ frame,
-                         uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc) {
+                         uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (i < n) {
@@ -174,10 +218,22 @@ __global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x
         double im = inv_m[i];
         unsigned int qc[3];
         bool ok = true;
+        double xi[3] = {0.0, 0.0, 0.0}, sig = 0.0;
+        if (lg.on) {
+            langevin_normals((unsigned int)i, *lg.step, lg.key0, lg.key1, xi);
+            sig = lg.c2 * sqrt(lg.kT_accel * im);
+        }
         for (int c = 0; c < 3; ++c) {
             size_t o = (size_t)c * n + i;
             double vv = v[o] + c_half * im * (double)f[o];
-            double xx = wrap_coord(x[o] + dt * vv, L);
+            double xx;
+            if (lg.on) {                                            // BAOAB: A, O, A
+                xx = wrap_coord(x[o] + (0.5 * dt) * vv, L);
+                vv = lg.c1 * vv + sig * xi[c];
+                xx = wrap_coord(xx + (0.5 * dt) * vv, L);
+            } else {
+                xx = wrap_coord(x[o] + dt * vv, L);
+            }
             ok = ok && isfinite(vv) && isfinite(xx);
             v[o] = vv;
             x[o] = xx;
@@ -194,19 +250,21 @@ __global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x
 void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const double* inv_mass, const float* f, const int* sys_of_atom,
                    const double* box, const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                   cudaStream_t s) {
+                   const Langevin& lg, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_vv_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, dt, x, v, inv_mass, f, sys_of_atom,
-                                                  box, frame, q, flags, vc);
+                                                  box, frame, q, flags, vc, lg);
     count_launch();
 }
 
 __global__ void k_vv_post(int n, double c_half, double* __restrict__ v,
                           const double* __restrict__ inv_m, const float* __restrict__ f,
                           const double* __restrict__ x, double* __restrict__ ke,
-                          const double* __restrict__ mass, int* __restrict__ flags) {
+                          const double* __restrict__ mass, int* __restrict__ flags,
+                          unsigned long long* __restrict__ step) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (step && i == 0) *step += 1ull;
     double im = inv_m[i];
     double v2 = 0.0;
     bool ok = true;
@@ -223,9 +281,9 @@ __global__ void k_vv_post(int n, double c_half, double* __restrict__ v,
 
 void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
-                    cudaStream_t s) {
+                    unsigned long long* step, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_vv_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags);
+    k_vv_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags, step);
     count_launch();
 }
 

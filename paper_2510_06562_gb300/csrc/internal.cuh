@@ -68,6 +68,19 @@ struct VerletState {
     long long n_checks, n_rebuilds;
 };
 
+// Algorithm 1's thermostat step as the exact Ornstein-Uhlenbeck update
+// v <- c1 v + c2 sqrt(k_B T / m) xi (on = 0: the identity, NVE). The
+// normals xi come from Philox-4x32-10 with counter (atom, t low, t high, 0)
+// and key (seed low, seed high); t = *step + k for inner step k of a
+// captured outer step, and the step's closing kernel advances *step.
+struct Langevin {
+    int on;
+    double c1, c2;
+    double kT_accel;              // k_B T in eV times the eV/(A amu) -> A/fs^2 factor
+    uint32_t key0, key1;
+    unsigned long long* step;
+};
+
 // A displacement check run inside a kernel that has just written x (the
 // integrator) or by k_vl_check. st == nullptr: no check.
 struct VerletCheck {
@@ -213,19 +226,23 @@ void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t 
 void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, double half_h,
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
-                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc, cudaStream_t s);
+                      const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
+                      const Langevin& lg, int k, cudaStream_t s);
 // after the big force: last inner post-kick and the outer half-kick.
+// With a step counter: advances it by `advance` (the inner steps taken).
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, const float* f_small, const float* f_big,
-                       const double* x, double* ke, const double* mass, int* flags, cudaStream_t s);
-// velocity Verlet: half-kick + drift + wrap + quantise; half-kick + kinetic energy.
+                       const double* x, double* ke, const double* mass, int* flags,
+                       unsigned long long* step, int advance, cudaStream_t s);
+// velocity Verlet: half-kick + drift (with Langevin: half-drift, O-step,
+// half-drift, i.e. BAOAB) + wrap + quantise; half-kick + kinetic energy.
 void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const double* inv_mass, const float* f, const int* sys_of_atom,
                    const double* box, const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                   cudaStream_t s);
+                   const Langevin& lg, cudaStream_t s);
 void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
-                    cudaStream_t s);
+                    unsigned long long* step, cudaStream_t s);
 // energies ring: ring[step][sys] = {Epot, Ekin, Epot + Ekin}; step = flags[kFlagStep]++.
 void launch_energy_record(int n_sys, const double* epot, const double* ekin, double* ring,
                           int ring_len, int* flags, cudaStream_t s);

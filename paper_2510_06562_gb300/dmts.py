@@ -29,7 +29,7 @@ SMALL, BIG = 0, 1
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
-            "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats")
+            "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses")
 
 
 class DmtsError(RuntimeError):
@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_get_tuning.restype = C.c_int
     lib.dmts_neighbor_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     lib.dmts_neighbor_stats.restype = C.c_int
+    lib.dmts_hmr_masses.argtypes = [C.c_int, P, C.c_int, P, C.c_double, P]
+    lib.dmts_hmr_masses.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -127,6 +129,18 @@ def _f64(a):
     if a.dtype != torch.float64:
         raise TypeError("tensors must be float64")
     return a.contiguous()
+
+
+def hmr_masses(mass, bonds, h_mass: float = 3.024) -> np.ndarray:
+    """Hydrogen mass repartitioning (``dmts_hmr_masses``): hydrogens (< 1.5
+    amu) bonded to a heavy atom get ``h_mass``; the heavy partner loses the
+    difference. ``bonds`` [n_bonds, 2] atom indices."""
+    m = np.ascontiguousarray(mass, dtype=np.float64)
+    b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    out = np.empty_like(m)
+    _check(load_library().dmts_hmr_masses(len(m), _ptr(m), len(b), _ptr(b) if len(b) else None, float(h_mass),
+                                          _ptr(out)))
+    return out
 
 
 class Context:

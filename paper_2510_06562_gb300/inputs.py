@@ -201,7 +201,9 @@ class System:
 
     ``x`` [N, 3] float64; ``species`` [N] int32; ``mass`` [N] float64;
     ``atom_offset`` [n_systems + 1] int32; ``box`` [n_systems] float64 cubic
-    edge length (<= 0 means non-periodic).
+    edge length (<= 0 means non-periodic); ``bonds`` [n_bonds, 2] int32 atom
+    indices of the generator's covalent bonds (used for hydrogen mass
+    repartitioning only; the potentials do not use bonds).
     """
 
     x: np.ndarray
@@ -211,6 +213,7 @@ class System:
     box: np.ndarray
     n_species: int
     name: str = ""
+    bonds: np.ndarray | None = None
 
     @property
     def n_atoms(self) -> int:
@@ -245,10 +248,13 @@ def make_water(n_side: int, box: float, seed: int = 0) -> System:
     x = x - box * np.floor(x / box)
     species = np.tile(np.array([1, 0, 0], dtype=np.int32), n_mol)
     mass = np.where(species == 1, MASS_O, MASS_H).astype(np.float64)
+    o_idx = 3 * np.arange(n_mol)
+    bonds = np.stack([np.repeat(o_idx, 2), np.stack([o_idx + 1, o_idx + 2], axis=1).reshape(-1)],
+                     axis=1).astype(np.int32)
     return System(x=x, species=species, mass=mass,
                   atom_offset=np.array([0, 3 * n_mol], dtype=np.int32),
                   box=np.array([box], dtype=np.float64), n_species=2,
-                  name=f"water{3 * n_mol}")
+                  name=f"water{3 * n_mol}", bonds=bonds)
 
 
 def water_192(seed: int = 0) -> System:
@@ -281,9 +287,11 @@ def make_vacuum_batch(n_mol: int = 512, n_min: int = 10, n_max: int = 60,
     masses = np.array([MASS_H, MASS_C, MASS_N, MASS_O])
     species = np.concatenate(zs).astype(np.int32)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    bonds = np.concatenate([np.stack([np.arange(off[k], off[k + 1] - 1), np.arange(off[k] + 1, off[k + 1])],
+                                     axis=1) for k in range(n_mol)]).astype(np.int32)
     return System(x=np.concatenate(xs), species=species, mass=masses[species],
                   atom_offset=off, box=np.zeros(n_mol), n_species=4,
-                  name=f"vacuum{n_mol}")
+                  name=f"vacuum{n_mol}", bonds=bonds)
 
 
 def make_solvated_polymer(n_heavy: int = 3000, n_total: int = 100_000, density: float = 1.0,
@@ -373,8 +381,15 @@ def make_solvated_polymer(n_heavy: int = 3000, n_total: int = 100_000, density: 
     x = np.concatenate([poly, wat])
     species = np.concatenate([poly_species, np.tile(np.array([3, 0, 0]), n_water)]).astype(np.int32)
     mass = heavy_mass[species]
+    n_p = len(poly)
+    o_idx = n_p + 3 * np.arange(n_water)
+    bonds = np.concatenate([
+        np.stack([np.arange(n_heavy - 1), np.arange(1, n_heavy)], axis=1),              # chain
+        np.stack([np.asarray(h_parent, dtype=np.int64), n_heavy + np.arange(len(hs))], axis=1),
+        np.stack([np.repeat(o_idx, 2), np.stack([o_idx + 1, o_idx + 2], axis=1).reshape(-1)], axis=1),
+    ]).astype(np.int32)
     return System(x=x, species=species, mass=mass, atom_offset=np.array([0, len(x)], dtype=np.int32),
-                  box=np.array([L]), n_species=4, name=f"polymer{len(x)}")
+                  box=np.array([L]), n_species=4, name=f"polymer{len(x)}", bonds=bonds)
 
 
 def maxwell_boltzmann(mass: np.ndarray, temperature: float, seed: int = 1,

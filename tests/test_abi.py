@@ -89,3 +89,28 @@ def test_system_validation(lib):
                           bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         out = ctypes.c_void_p()
         assert lib.dmts_create(None, ctypes.byref(big), ctypes.byref(sd), None, ctypes.byref(out)) == code
+
+
+# ------------------------------------------------------------------ host-only entry points
+
+@pytest.mark.parametrize("make", [lambda: I.water_192(0), lambda: I.make_vacuum_batch(64, 10, 60, seed=0)])
+def test_hmr_masses_equal_the_oracle(lib, make):
+    """dmts_hmr_masses (host code, no GPU) against the oracle's definition,
+    bit for bit, on the generators' bond lists."""
+    from oracle import integrate as G
+    s = make()
+    got = D.hmr_masses(s.mass, s.bonds, 3.024)
+    np.testing.assert_array_equal(got, G.hmr_masses(s.mass, s.bonds, 3.024))
+    off = s.atom_offset
+    for k in range(len(off) - 1):
+        assert abs(got[off[k]:off[k + 1]].sum() - s.mass[off[k]:off[k + 1]].sum()) < 1e-9
+    if s.box[0] > 0:                                   # water: O 15.999 - 2 (3.024 - 1.008)
+        np.testing.assert_allclose(got[0::3], 11.967)
+        np.testing.assert_allclose(got[1::3], 3.024)
+
+
+def test_hmr_masses_rejects_bad_input(lib):
+    with pytest.raises(D.DmtsError):
+        D.hmr_masses(np.array([16.0, 1.0]), np.array([[0, 2]]))
+    with pytest.raises(D.DmtsError):
+        D.hmr_masses(np.array([2.0, 1.0]), np.array([[0, 1]]), h_mass=3.5)
