@@ -15,6 +15,12 @@
   is 1 ps^-1 in the paper (section "Simulation details").
 * ``hmr_masses`` is hydrogen mass repartitioning: each hydrogen's mass is
   raised to a target and the excess is taken from its bonded heavy atom.
+* ``respa_monitored`` adds the force-difference monitor of the paper's
+  active-learning section: after each outer step, if some atom's
+  |F - F_small| exceeds the threshold (150 kcal/mol/A in the paper), the step
+  is redone from its starting state with the single-time-step integrator
+  (n_slow velocity-Verlet or BAOAB steps of dt / n_slow with the large model),
+  and the small model is evaluated at the end for the next step's kicks.
 
 Positions of periodic systems are wrapped into [0, L) after every drift
 (x - L floor(x / L)); the paper does not say where its engines wrap.
@@ -193,3 +199,36 @@ def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int,
             out.append(np.stack([ep, ek, ep + ek], axis=-1))
     energies = np.asarray(out) if energy_big is not None else None
     return x, v, F_small, F, energies
+
+
+def force_difference_norms(F, F_small):
+    """Per-atom |F - F_small| (eV/A)."""
+    d = np.asarray(F, dtype=np.float64) - np.asarray(F_small, dtype=np.float64)
+    return np.sqrt((d * d).sum(axis=1))
+
+
+def respa_monitored(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int, n_outer: int,
+                    threshold: float, box_per_atom=None, thermo: dict | None = None, step0: int = 0):
+    """n_outer outer steps of Algorithm 1 with the force-difference monitor
+    and single-time-step fallback. Returns (x, v, F_small, F, n_fallback,
+    max_df) with max_df the largest |F - F_small| seen at the end of an
+    outer step (before any fallback)."""
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    F_small = f_small(x)
+    F = f_big(x)
+    h = dt / n_slow
+    n_fallback, max_df = 0, 0.0
+    for s_ in range(n_outer):
+        t0 = step0 + s_ * n_slow
+        x1, v1, Fs1, F1, _ = respa(x, v, mass, f_small, f_big, dt, n_slow, 1, box_per_atom=box_per_atom,
+                                   F_small=F_small, F=F, thermo=thermo, step0=t0)
+        df = force_difference_norms(F1, Fs1).max()
+        max_df = max(max_df, df)
+        if df > threshold:
+            n_fallback += 1
+            x1, v1, F1 = velocity_verlet(x, v, mass, f_big, h, n_slow, box_per_atom=box_per_atom, F=F,
+                                         thermo=thermo, step0=t0)
+            Fs1 = f_small(x1)
+        x, v, F_small, F = x1, v1, Fs1, F1
+    return x, v, F_small, F, n_fallback, max_df

@@ -1,7 +1,8 @@
 """Pins of the oracle's Langevin pieces (CPU only): the counter-based
 generator, the Box-Muller normals, the exact Ornstein-Uhlenbeck O-step,
 Algorithm 1 with the thermostat (BAOAB-RESPA) and velocity Verlet as BAOAB,
-and hydrogen mass repartitioning.
+hydrogen mass repartitioning, and the force-difference monitor with its
+single-time-step fallback.
 
 The generator is pinned by properties a mistake in a multiplier, a shift, a
 word order or the key schedule destroys (injectivity on a sample, avalanche,
@@ -177,3 +178,57 @@ def test_hmr_masses_water_and_conservation():
     np.testing.assert_allclose(out2, [12.011 - 2.016, 3.024, 14.007])
     with pytest.raises(ValueError):
         G.hmr_masses(np.array([2.0, 1.0]), np.array([[0, 1]]), h_mass=3.5)
+
+
+# ------------------------------------------------------------------ force-difference monitor
+
+def _harmonic_pair(k_small, k_big):
+    return (lambda y: -k_small * y), (lambda y: -k_big * y)
+
+
+def test_monitor_never_tripping_is_plain_respa():
+    rng = np.random.default_rng(5)
+    x, v = rng.normal(size=(20, 3)), rng.normal(size=(20, 3)) * 0.02
+    m = rng.uniform(1, 16, size=20)
+    fs, fb = _harmonic_pair(0.4, 0.5)
+    a = G.respa(x, v, m, fs, fb, 3.0, 3, 5)
+    b = G.respa_monitored(x, v, m, fs, fb, 3.0, 3, 5, threshold=np.inf)
+    for p, q in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(p, q)
+    assert b[4] == 0
+    # the reported maximum is the largest end-of-step force difference
+    assert abs(b[5] - max(G.force_difference_norms(fb(x_), fs(x_)).max()
+                          for x_ in [G.respa(x, v, m, fs, fb, 3.0, 3, s)[0] for s in range(1, 6)])) < 1e-12
+
+
+@pytest.mark.parametrize("thermo", [None, {"gamma": 0.05, "temperature": 300.0, "seed": 4}])
+def test_monitor_always_tripping_is_single_time_step(thermo):
+    """With a zero threshold every outer step falls back: the trajectory is
+    n_slow x n_outer steps of the single-time-step integrator at dt / n_slow
+    with the large model, drawing the same noise counters."""
+    rng = np.random.default_rng(6)
+    x, v = rng.normal(size=(20, 3)), rng.normal(size=(20, 3)) * 0.02
+    m = rng.uniform(1, 16, size=20)
+    fs, fb = _harmonic_pair(0.4, 0.9)
+    xr, vr, Fr = G.velocity_verlet(x, v, m, fb, 1.0, 12, thermo=thermo, step0=0)
+    xm, vm, Fsm, Fm, nf, _ = G.respa_monitored(x, v, m, fs, fb, 3.0, 3, 4, threshold=0.0, thermo=thermo)
+    np.testing.assert_allclose(xm, xr, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(vm, vr, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(Fsm, fs(xm))
+    assert nf == 4
+
+
+def test_monitor_trips_only_on_large_differences():
+    """A small model that is wrong only far from the origin: steps whose end
+    state has an atom there fall back, the others do not."""
+    rng = np.random.default_rng(7)
+    n = 10
+    x = rng.normal(size=(n, 3)) * 0.2
+    x[0] = [2.0, 0.0, 0.0]                              # starts in the bad region, moving out of it
+    v = np.zeros((n, 3))
+    v[0] = [-0.2, 0.0, 0.0]
+    m = np.full(n, 12.0)
+    fb = lambda y: -0.5 * y
+    fs = lambda y: -0.5 * y + np.where(np.linalg.norm(y, axis=1, keepdims=True) > 1.5, 3.0, 0.0)
+    out = G.respa_monitored(x, v, m, fs, fb, 2.0, 2, 6, threshold=1.0)
+    assert 1 <= out[4] < 6
