@@ -145,6 +145,14 @@ typedef struct {
  * words), Box-Muller on the four uniforms (w + 1/2) 2^-32: (u0, u1) give the
  * x and y components, (u2, u3) the z component. The inner-step counter
  * starts at 0 at dmts_set_state and advances by n_inner per outer step.
+ * "fallback_threshold" (eV/A, default 0 = off; the paper uses 150
+ * kcal/mol/A = 6.505 eV/A): after each outer step of Algorithm 1, if some
+ * atom's |F_big - F_small| exceeds it, the step is redone from its starting
+ * state with n_inner single-time-step steps of dt / n_inner with the big
+ * model (velocity Verlet, or BAOAB with the thermostat, drawing the noise of
+ * the inner steps they replace), and the small model is evaluated at the end
+ * (the paper's temporary reversion to the single-time-step integrator). The
+ * monitor statistics (dmts_monitor) are gathered with or without it.
  * On success *out holds the new context; on failure *out is NULL. */
 DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big,
                 const dmts_system_desc* sys, const char* options, dmts_ctx** out);
@@ -200,6 +208,19 @@ DMTS_API void* dmts_stream(dmts_ctx* ctx);
 /* Number of the library's kernel launches since the context was created
  * (including launches inside CUDA graph replays). */
 DMTS_API long long dmts_launch_count(dmts_ctx* ctx);
+
+/* Force-difference monitor of dmts_respa_step (with a small model), since
+ * the context was created or dmts_monitor_reset: the largest per-atom
+ * |F_big - F_small| (eV/A) seen at the end of an outer step, the number of
+ * outer steps redone by the fallback, the atom count above the threshold
+ * summed over steps, and a histogram of log10 |dF| in bins of 1/8 decade
+ * from 1e-3 eV/A (bin b: [10^(b/8 - 3), 10^((b+1)/8 - 3)); the first and the
+ * last bins are open). hist receives min(n_bins, bin count) entries; any
+ * output may be NULL. Returns the number of bins (48) or a negative status.
+ * Synchronises the context's stream. */
+DMTS_API int dmts_monitor(dmts_ctx* ctx, double* max_df, long long* n_fallback, long long* n_flagged,
+                          long long* hist, int n_bins);
+DMTS_API int dmts_monitor_reset(dmts_ctx* ctx);
 
 /* Hydrogen mass repartitioning (the paper's HMR; the target mass is the
  * caller's choice, commonly 3.024 amu). Every atom lighter than 1.5 amu that

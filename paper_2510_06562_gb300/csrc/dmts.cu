@@ -131,6 +131,13 @@ struct dmts_ctx {
     double friction_ps = 0.0, temperature = 300.0;
     unsigned long long seed = 0;
     unsigned long long* d_rng = nullptr;   // [0] inner-step counter of the noise, [1] copy at call entry
+    // force-difference monitor and single-time-step fallback (threshold 0: statistics only)
+    double fb_threshold = 0.0;             // eV/A
+    ForceMonitor* d_mon = nullptr;
+    double *d_sx = nullptr, *d_sv = nullptr;   // state at the start of the outer step
+    float* d_sf = nullptr;
+    cudaStream_t aux = nullptr;            // captures the fallback body of the step graph
+    long long body_launches = 0, fallback_seen = 0;
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
     bool broken = false;
@@ -649,6 +656,60 @@ int copy_out(dmts_ctx* c, double* dst, const double* src, size_t n) {
     return DMTS_OK;
 }
 
+// The single-time-step fallback of one outer step (body of the IF node):
+// restore x, v and the large-model force saved at the start of the step, take
+// n_inner velocity-Verlet (BAOAB) steps of dt / n_inner with the large model,
+// drawing the noise of the inner steps they replace, then evaluate the small
+// model at the final positions for the next step's kicks.
+void enqueue_fallback(dmts_ctx* c, int n_inner, double dt) {
+    const double acc = accel_constant();
+    const double h = dt / n_inner;
+    const bool nonper = !c->periodic;
+    launch_copy_state(c->N, c->d_sx, c->d_sv, c->d_sf, c->d_x, c->d_v, c->m[1].force, c->stream);
+    Langevin lg = langevin(c, h);
+    for (int k = 0; k < n_inner; ++k) {
+        lg.offset = (long long)k - n_inner;              // the counter was advanced by the step's closing kernel
+        launch_vv_pre(c->N, 0.5 * h * acc, h, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,
+                      c->d_frame, c->d_q, c->d_flags, verlet_check(c), lg, c->stream);
+        enqueue_eval(c, 1, nonper, true, Check::Done);
+        launch_vv_post(c->N, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
+                       c->d_flags, nullptr, c->stream);
+    }
+    enqueue_eval(c, 0, false, false, Check::None);
+}
+
+// During stream capture: an IF node on `h` whose body is the fallback,
+// captured on the auxiliary stream; the capture continues after the node.
+cudaError_t capture_fallback_node(dmts_ctx* c, cudaGraphConditionalHandle h, int n_inner, double dt) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &p)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCaptureToGraph(c->aux, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+    const cudaStream_t main = c->stream;
+    const long long before = c->launches;
+    c->stream = c->aux;                        // every launcher enqueues on c->stream
+    enqueue_fallback(c, n_inner, dt);
+    c->stream = main;
+    c->body_launches = c->launches - before;
+    c->launches = before;                      // counted when a body runs
+    cudaGraph_t body = nullptr;
+    if ((e = cudaStreamEndCapture(c->aux, &body)) != cudaSuccess) return e;
+    return cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     cudaStream_t s = c->stream;
@@ -656,21 +717,34 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     long long before = c->launches;
     CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const bool nonper = !c->periodic;
+    cudaError_t ce = cudaSuccess;
     // the integrator kernels that move the atoms also run the neighbour-list
     // displacement check (with a skin)
     const VerletCheck vc = verlet_check(c);
     if (c->m[0].present) {
         double h = dt / n_inner;
-        const Langevin lg = langevin(c, h);
+        Langevin lg = langevin(c, h);
+        const bool fallback = c->fb_threshold > 0.0;
+        MonitorArgs mon{c->d_mon, c->fb_threshold, 0, 0};
+        if (fallback) {
+            cudaGraph_t g = nullptr;
+            cudaStreamCaptureStatus st;
+            ce = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+            if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&mon.cond, g, 0, cudaGraphCondAssignDefault);
+            mon.use_cond = 1;
+            launch_copy_state(c->N, c->d_x, c->d_v, c->m[1].force, c->d_sx, c->d_sv, c->d_sf, s);
+        }
         for (int k = 0; k < n_inner; ++k) {
+            lg.offset = k;
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, vc,
-                             lg, k, s);
+                             lg, s);
             enqueue_eval(c, 0, nonper, false, Check::Done);   // the small model's energy is not reported
         }
         enqueue_eval(c, 1, false, true, Check::None);          // same positions as the last small evaluation
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
-                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, s);
+                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, s);
+        if (fallback && ce == cudaSuccess) ce = capture_fallback_node(c, mon.cond, n_inner, dt);
     } else {
         launch_vv_pre(c->N, 0.5 * dt * acc, dt, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,
                       c->d_frame, c->d_q, c->d_flags, vc, langevin(c, dt), s);
@@ -682,7 +756,9 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = ce;
     if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
         c->broken = true;
         return fail(DMTS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
     }
@@ -795,6 +871,8 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
     dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng);
+    dfree(c->d_mon); dfree(c->d_sx); dfree(c->d_sv); dfree(c->d_sf);
+    if (c->aux) cudaStreamDestroy(c->aux);
     dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
     dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -868,6 +946,11 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
         return fail(DMTS_ERR_ARG, "langevin_friction and temperature must be >= 0, seed in [0, 9e15]");
     }
     c->seed = (unsigned long long)seed_d;
+    c->fb_threshold = json_number(options, "fallback_threshold", 0.0);
+    if (!(c->fb_threshold >= 0.0)) {
+        delete c;
+        return fail(DMTS_ERR_ARG, "fallback_threshold must be >= 0 (eV/A)");
+    }
     c->vl_src = (small && small->cutoff > big->cutoff) ? 0 : 1;
 #define CREATE_TRY(expr)                                                          \
     do {                                                                          \
@@ -908,6 +991,14 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
     CREATE_TRY(dalloc(&c->d_rng, 2));
     CREATE_TRY(cudaMemset(c->d_rng, 0, 2 * sizeof(unsigned long long)));
+    CREATE_TRY(dalloc(&c->d_mon, 1));
+    CREATE_TRY(cudaMemset(c->d_mon, 0, sizeof(ForceMonitor)));
+    if (c->fb_threshold > 0.0) {
+        CREATE_TRY(dalloc(&c->d_sx, (size_t)3 * N));
+        CREATE_TRY(dalloc(&c->d_sv, (size_t)3 * N));
+        CREATE_TRY(dalloc(&c->d_sf, (size_t)3 * N));
+        CREATE_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    }
     if (c->skin > 0) {
         CREATE_TRY(dalloc(&c->d_xref, (size_t)3 * N));
         CREATE_TRY(dalloc(&c->d_vl, 1));
@@ -1106,6 +1197,13 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
             c->launches += c->g_nodes;
         }
         if ((rc = sync_check(c))) return rc;
+        if (c->fb_threshold > 0.0 && c->m[0].present) {
+            // kernels of the fallback bodies that ran
+            unsigned long long nf = 0;
+            CUDA_TRY(cudaMemcpy(&nf, &c->d_mon->n_fallback, sizeof(nf), cudaMemcpyDeviceToHost));
+            c->launches += ((long long)nf - c->fallback_seen) * c->body_launches;
+            c->fallback_seen = (long long)nf;
+        }
         if (!c->h_flags[kFlagOverflow]) break;
         if (attempt >= 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
         // restore and retry with grown capacity
@@ -1304,6 +1402,28 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
 extern "C" {
 
 long long dmts_launch_count(dmts_ctx* c) { return c ? c->launches : -1; }
+
+int dmts_monitor(dmts_ctx* c, double* max_df, long long* n_fallback, long long* n_flagged, long long* hist,
+                 int n_bins) {
+    CTX_GUARD(c);
+    ForceMonitor m{};
+    CUDA_TRY(cudaMemcpyAsync(&m, c->d_mon, sizeof(m), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (max_df) memcpy(max_df, &m.max_bits, sizeof(double));
+    if (n_fallback) *n_fallback = (long long)m.n_fallback;
+    if (n_flagged) *n_flagged = (long long)m.n_flagged;
+    if (hist)
+        for (int b = 0; b < n_bins && b < kMonitorBins; ++b) hist[b] = (long long)m.hist[b];
+    return kMonitorBins;
+}
+
+int dmts_monitor_reset(dmts_ctx* c) {
+    CTX_GUARD(c);
+    CUDA_TRY(cudaMemsetAsync(c->d_mon, 0, sizeof(ForceMonitor), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->fallback_seen = 0;
+    return DMTS_OK;
+}
 
 int dmts_hmr_masses(int n_atoms, const double* mass, int n_bonds, const int* bonds, double h_mass,
                     double* mass_out) {

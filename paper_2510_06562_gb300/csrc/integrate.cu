@@ -3,6 +3,8 @@
 // on the FP64 SoA state, fused with periodic wrapping and the fixed-point
 // quantisation that the next force evaluation reads. One thread per atom; every kernel streams x, v, 1/m and
 // the FP32 forces once.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace dmts {
@@ -117,7 +119,7 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
                             const double* __restrict__ inv_m, const float* __restrict__ fs,
                             const float* __restrict__ fb, const int* __restrict__ sys,
                             const double* __restrict__ box, const Frame* __restrict__ frame,
-                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg, int k) {
+                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (i < n) {
@@ -129,7 +131,7 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
         bool ok = true;
         double xi[3] = {0.0, 0.0, 0.0}, sig = 0.0;
         if (lg.on) {
-            langevin_normals((unsigned int)i, *lg.step + (unsigned long long)k, lg.key0, lg.key1, xi);
+            langevin_normals((unsigned int)i, *lg.step + (unsigned long long)lg.offset, lg.key0, lg.key1, xi);
             sig = lg.c2 * sqrt(lg.kT_accel * im);
         }
         for (int c = 0; c < 3; ++c) {
@@ -159,47 +161,120 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                      const Langevin& lg, int k, cudaStream_t s) {
+                      const Langevin& lg, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
-                                                     frame, q, flags, vc, lg, k);
+                                                     frame, q, flags, vc, lg);
     count_launch();
 }
 
 // After the big force: v += (h/2m) F_small (last inner post-kick), then
 // v += (dt/2m) (F - F_small) (outer half-kick); per-atom kinetic energy.
-__global__ void k_respa_post(int n, double c_outer, double c_inner, double* __restrict__ v,
-                             const double* __restrict__ inv_m, const float* __restrict__ fs,
-                             const float* __restrict__ fb, const double* __restrict__ x,
-                             double* __restrict__ ke, const double* __restrict__ mass,
-                             int* __restrict__ flags, unsigned long long* __restrict__ step, int advance) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (step && i == 0) *step += (unsigned long long)advance;   // every reader of it ran in earlier kernels
-    double im = inv_m[i];
-    double v2 = 0.0;
-    bool ok = true;
-    for (int c = 0; c < 3; ++c) {
-        size_t o = (size_t)c * n + i;
-        double Fs = (double)fs[o];
-        double vv = v[o] + c_inner * im * Fs;
-        vv = vv + c_outer * im * ((double)fb[o] - Fs);
-        v[o] = vv;
-        v2 += vv * vv;
-        ok = ok && isfinite(vv) && isfinite(x[o]);
+// With a monitor: per-atom |F - F_small| (the forces of the step's end),
+// reduced per block (maximum, atoms above the threshold, histogram) and
+// over blocks; the last block to finish decides whether the step falls back
+// (some atom above the threshold) and sets the graph conditional.
+__global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, double c_inner, double* __restrict__ v,
+                                                    const double* __restrict__ inv_m, const float* __restrict__ fs,
+                                                    const float* __restrict__ fb, const double* __restrict__ x,
+                                                    double* __restrict__ ke, const double* __restrict__ mass,
+                                                    int* __restrict__ flags, unsigned long long* __restrict__ step,
+                                                    int advance, MonitorArgs mon) {
+    __shared__ unsigned int s_hist[kMonitorBins];
+    __shared__ double s_max[8];
+    __shared__ unsigned int s_flag;
+    __shared__ bool s_last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mon.mon) {
+        for (int b = threadIdx.x; b < kMonitorBins; b += blockDim.x) s_hist[b] = 0u;
+        if (threadIdx.x == 0) s_flag = 0u;
+        __syncthreads();
     }
-    ke[i] = 0.5 * mass[i] * v2 * kKinetic;
-    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+    double df = 0.0;
+    if (i < n) {
+        if (step && i == 0) *step += (unsigned long long)advance;   // every reader of it ran in earlier kernels
+        double im = inv_m[i];
+        double v2 = 0.0, d2 = 0.0;
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            size_t o = (size_t)c * n + i;
+            double Fs = (double)fs[o];
+            const double dF = (double)fb[o] - Fs;
+            d2 += dF * dF;
+            double vv = v[o] + c_inner * im * Fs;
+            vv = vv + c_outer * im * dF;
+            v[o] = vv;
+            v2 += vv * vv;
+            ok = ok && isfinite(vv) && isfinite(x[o]);
+        }
+        ke[i] = 0.5 * mass[i] * v2 * kKinetic;
+        if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+        df = sqrt(d2);
+        if (mon.mon) {
+            int b = 0;
+            if (df > 0.0) b = (int)floor((log10(df) + 3.0) * 8.0);
+            b = b < 0 ? 0 : (b >= kMonitorBins ? kMonitorBins - 1 : b);
+            if (!(df == df)) b = kMonitorBins - 1;                  // NaN: the top bin
+            atomicAdd(&s_hist[b], 1u);
+            if (mon.threshold > 0.0 && !(df <= mon.threshold)) atomicAdd(&s_flag, 1u);
+        }
+    }
+    if (!mon.mon) return;
+    if (!(df == df)) df = 1e300;
+    double m = df;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_max[k]);
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+        atomicMax(&mon.mon->max_bits, bits);
+        atomicMax(&mon.mon->step_max_bits, bits);
+        if (s_flag) atomicAdd(&mon.mon->n_flagged, (unsigned long long)s_flag);
+    }
+    for (int b = threadIdx.x; b < kMonitorBins; b += blockDim.x)
+        if (s_hist[b]) atomicAdd(&mon.mon->hist[b], (unsigned long long)s_hist[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&mon.mon->done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicAdd(&mon.mon->step_max_bits, 0ull));
+        const int fall = (mon.threshold > 0.0 && !(mx <= mon.threshold)) ? 1 : 0;
+        mon.mon->n_fallback += (unsigned long long)fall;
+        mon.mon->step_max_bits = 0ull;
+        mon.mon->done = 0u;
+        if (mon.use_cond) cudaGraphSetConditional(mon.cond, (unsigned int)fall);
+    }
 }
 
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, const float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
-                       unsigned long long* step, int advance, cudaStream_t s) {
+                       unsigned long long* step, int advance, const MonitorArgs& mon, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
-                                                      f_big, x, ke, mass, flags, step, advance);
+                                                      f_big, x, ke, mass, flags, step, advance, mon);
+    count_launch();
+}
+
+__global__ void k_copy_state(int n, const double* __restrict__ x, const double* __restrict__ v,
+                             const float* __restrict__ f, double* __restrict__ xo, double* __restrict__ vo,
+                             float* __restrict__ fo) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * n; t += gridDim.x * blockDim.x) {
+        xo[t] = x[t];
+        vo[t] = v[t];
+        fo[t] = f[t];
+    }
+}
+
+void launch_copy_state(int n_atoms, const double* x, const double* v, const float* f, double* x_out,
+                       double* v_out, float* f_out, cudaStream_t s) {
+    if (n_atoms == 0) return;
+    k_copy_state<<<std::min(4 * 152, (3 * n_atoms + 255) / 256), 256, 0, s>>>(n_atoms, x, v, f, x_out, v_out, f_out);
     count_launch();
 }
 
@@ -220,7 +295,7 @@ __global__ void k_vv_pre(int n, double c_half, double dt, double* __restrict__ x
         bool ok = true;
         double xi[3] = {0.0, 0.0, 0.0}, sig = 0.0;
         if (lg.on) {
-            langevin_normals((unsigned int)i, *lg.step, lg.key0, lg.key1, xi);
+            langevin_normals((unsigned int)i, *lg.step + (unsigned long long)lg.offset, lg.key0, lg.key1, xi);
             sig = lg.c2 * sqrt(lg.kT_accel * im);
         }
         for (int c = 0; c < 3; ++c) {

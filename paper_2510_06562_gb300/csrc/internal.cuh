@@ -71,14 +71,37 @@ struct VerletState {
 // Algorithm 1's thermostat step as the exact Ornstein-Uhlenbeck update
 // v <- c1 v + c2 sqrt(k_B T / m) xi (on = 0: the identity, NVE). The
 // normals xi come from Philox-4x32-10 with counter (atom, t low, t high, 0)
-// and key (seed low, seed high); t = *step + k for inner step k of a
-// captured outer step, and the step's closing kernel advances *step.
+// and key (seed low, seed high); t = *step + offset (offset k for inner step
+// k of a captured outer step), and the step's closing kernel advances *step.
 struct Langevin {
     int on;
     double c1, c2;
     double kT_accel;              // k_B T in eV times the eV/(A amu) -> A/fs^2 factor
     uint32_t key0, key1;
     unsigned long long* step;
+    long long offset;
+};
+
+// Force-difference monitor (device memory, one per context), filled by the
+// closing kernel of every outer step: per-atom |F_big - F_small| against the
+// threshold, histogram of log10 |dF| in kMonitorBins bins of 1/8 decade from
+// 1e-3 eV/A (first and last bins open), and the fallback decision of the step.
+constexpr int kMonitorBins = 48;
+struct ForceMonitor {
+    unsigned long long max_bits;          // FP64 bits of the largest |dF| since the last reset
+    unsigned long long step_max_bits;     // ... of the current outer step (cleared by the decision)
+    unsigned long long n_flagged;         // atoms above the threshold, summed over steps
+    unsigned long long n_fallback;        // outer steps redone with the single-time-step integrator
+    unsigned long long hist[kMonitorBins];
+    unsigned int done;                    // CTAs of the current step that have finished
+    int pad;
+};
+
+struct MonitorArgs {
+    ForceMonitor* mon;                    // nullptr: no monitoring
+    double threshold;                     // eV/A; <= 0: no fallback decision
+    cudaGraphConditionalHandle cond;      // set to 1 when the step falls back
+    int use_cond;
 };
 
 // A displacement check run inside a kernel that has just written x (the
@@ -227,13 +250,17 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                      const Langevin& lg, int k, cudaStream_t s);
+                      const Langevin& lg, cudaStream_t s);
 // after the big force: last inner post-kick and the outer half-kick.
 // With a step counter: advances it by `advance` (the inner steps taken).
+// With a monitor: the force-difference statistics and fallback decision.
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, const float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
-                       unsigned long long* step, int advance, cudaStream_t s);
+                       unsigned long long* step, int advance, const MonitorArgs& mon, cudaStream_t s);
+// dst = src for the integrator state: x, v (FP64 [3][N]) and one force (FP32 [3][N]).
+void launch_copy_state(int n_atoms, const double* x, const double* v, const float* f, double* x_out,
+                       double* v_out, float* f_out, cudaStream_t s);
 // velocity Verlet: half-kick + drift (with Langevin: half-drift, O-step,
 // half-drift, i.e. BAOAB) + wrap + quantise; half-kick + kinetic energy.
 void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,

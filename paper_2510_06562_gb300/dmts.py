@@ -29,7 +29,8 @@ SMALL, BIG = 0, 1
 EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
-            "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses")
+            "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses",
+            "dmts_monitor", "dmts_monitor_reset")
 
 
 class DmtsError(RuntimeError):
@@ -93,6 +94,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_neighbor_stats.restype = C.c_int
     lib.dmts_hmr_masses.argtypes = [C.c_int, P, C.c_int, P, C.c_double, P]
     lib.dmts_hmr_masses.restype = C.c_int
+    lib.dmts_monitor.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), P,
+                                 C.c_int]
+    lib.dmts_monitor.restype = C.c_int
+    lib.dmts_monitor_reset.argtypes = [P]
+    lib.dmts_monitor_reset.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -266,6 +272,20 @@ class Context:
     @property
     def launch_count(self) -> int:
         return load_library().dmts_launch_count(self._h)
+
+    def monitor(self) -> dict:
+        """Force-difference monitor: max |F_big - F_small| (eV/A), outer steps
+        redone by the fallback, flagged atoms, log10 histogram (48 bins of 1/8
+        decade from 1e-3 eV/A)."""
+        mx, nf, na = C.c_double(), C.c_longlong(), C.c_longlong()
+        hist = np.zeros(48, dtype=np.int64)
+        n = load_library().dmts_monitor(self._h, C.byref(mx), C.byref(nf), C.byref(na), _ptr(hist), hist.size)
+        if n < 0:
+            _check(n)
+        return {"max_df": mx.value, "n_fallback": nf.value, "n_flagged": na.value, "hist": hist[:n]}
+
+    def monitor_reset(self):
+        _check(load_library().dmts_monitor_reset(self._h))
 
     def neighbor_stats(self) -> tuple[int, int]:
         """(displacement checks, candidate-row rebuilds) of the Verlet-skin lists."""

@@ -1,0 +1,89 @@
+"""Force-difference monitor and single-time-step fallback on the GPU (needs a
+GB300). The fallback redoes an outer step with n_inner velocity-Verlet (or
+BAOAB) steps of the large model; when every step falls back the trajectory
+must therefore be, bit for bit, the one a large-model-only context integrates
+with dt / n_inner (FP32 path: results do not depend on the tuner's choices),
+including the thermostat noise, whose counters line up."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2510_06562_gb300 import dmts as D
+from paper_2510_06562_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(s, small=True, **opts):
+    sa, ba = I.small_arch(s.n_species), I.big_arch(s.n_species)
+    o = json.dumps(opts) if opts else None
+    if small:
+        return D.Context(s, ba, I.init_params(ba, 3), sa, I.init_params(sa, 2), options=o)
+    return D.Context(s, ba, I.init_params(ba, 3), options=o)
+
+
+SYSTEMS = {
+    "water192": lambda: I.water_192(0),
+    "vacuum16": lambda: I.make_vacuum_batch(16, 10, 30, seed=1),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("friction", [0.0, 20.0])
+def test_always_falling_back_is_the_single_time_step_run(name, friction):
+    s = SYSTEMS[name]()
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1, s.atom_offset)
+    lang = {"langevin_friction": friction, "seed": 5}
+    with _ctx(s, fallback_threshold=1e-9, **lang) as a, _ctx(s, small=False, **lang) as b:
+        a.set_state(s.x, v0)
+        ea = a.respa_step(4, 3.0, 3)
+        b.set_state(s.x, v0)
+        eb = b.respa_step(12, 1.0, 1)
+        xa, va = a.get_state()
+        xb, vb = b.get_state()
+        np.testing.assert_array_equal(xa, xb)
+        np.testing.assert_array_equal(va, vb)
+        np.testing.assert_array_equal(ea[:, :, 0], eb[2::3, :, 0])   # E_pot after every outer step
+        mon = a.monitor()
+        assert mon["n_fallback"] == 4
+        assert mon["n_flagged"] == 4 * s.n_atoms
+        # the small model was re-evaluated at the end of the step: the next
+        # call continues exactly like the single-time-step run
+        a.respa_step(1, 3.0, 3)
+        b.respa_step(3, 1.0, 1)
+        np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+
+
+def test_never_falling_back_changes_nothing():
+    s = I.water_192(0)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s, fallback_threshold=1e6) as a, _ctx(s) as b:
+        a.set_state(s.x, v0)
+        a.respa_step(12, 3.0, 3)
+        b.set_state(s.x, v0)
+        b.respa_step(12, 3.0, 3)
+        np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+        np.testing.assert_array_equal(a.get_state()[1], b.get_state()[1])
+        mon = a.monitor()
+        assert mon["n_fallback"] == 0 and mon["n_flagged"] == 0
+        assert mon["hist"].sum() == 12 * s.n_atoms
+        assert b.monitor()["hist"].sum() == 12 * s.n_atoms      # statistics are gathered without a threshold too
+
+
+def test_monitor_maximum_is_the_end_of_step_force_difference():
+    s = I.water_192(0)
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    with _ctx(s) as ctx:
+        ctx.set_state(s.x, v0)
+        ctx.respa_step(2, 3.0, 3)
+        ctx.monitor_reset()
+        ctx.respa_step(1, 3.0, 3)
+        mon = ctx.monitor()
+        _, fb = ctx.forces(D.BIG)
+        _, fs = ctx.forces(D.SMALL)
+        df = np.sqrt(((fb - fs) ** 2).sum(axis=1))
+        assert abs(mon["max_df"] - df.max()) <= 1e-12 * df.max()
+        edges = 10.0 ** (np.arange(49) / 8.0 - 3.0)
+        ref = np.histogram(np.clip(df, edges[0], edges[-1] * 0.999), bins=edges)[0]
+        assert np.abs(mon["hist"] - ref).sum() <= 2               # bin edges: log10 in FP64 on both sides
