@@ -145,6 +145,10 @@ typedef struct {
  * words), Box-Muller on the four uniforms (w + 1/2) 2^-32: (u0, u1) give the
  * x and y components, (u2, u3) the z component. The inner-step counter
  * starts at 0 at dmts_set_state and advances by n_inner per outer step.
+ * "concurrent_models" (default 1): with fresh neighbour lists, the outer
+ * step's large-model evaluation and the last inner step's small-model
+ * evaluation (same positions, independent) run on two streams of the step
+ * graph; results are identical either way.
  * "fallback_threshold" (eV/A, default 0 = off; the paper uses 150
  * kcal/mol/A = 6.505 eV/A): after each outer step of Algorithm 1, if some
  * atom's |F_big - F_small| exceeds it, the step is redone from its starting

@@ -137,6 +137,11 @@ struct dmts_ctx {
     double *d_sx = nullptr, *d_sv = nullptr;   // state at the start of the outer step
     float* d_sf = nullptr;
     cudaStream_t aux = nullptr;            // captures the fallback body of the step graph
+    // second stream of the step graph: the large-model evaluation at the end of
+    // the outer step runs beside the last small-model evaluation (same positions)
+    cudaStream_t s_big = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool concurrent = true;
     long long body_launches = 0, fallback_seen = 0;
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
@@ -734,14 +739,32 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
             mon.use_cond = 1;
             launch_copy_state(c->N, c->d_x, c->d_v, c->m[1].force, c->d_sx, c->d_sv, c->d_sf, s);
         }
+        // with fresh neighbour lists the two evaluations at the final positions
+        // share nothing but the read-only positions: fork the large one
+        const bool fork = c->concurrent && c->skin <= 0;
         for (int k = 0; k < n_inner; ++k) {
             lg.offset = k;
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, vc,
                              lg, s);
-            enqueue_eval(c, 0, nonper, false, Check::Done);   // the small model's energy is not reported
+            if (fork && k == n_inner - 1) {
+                if (nonper) {                                  // frames and fixed-point positions for both
+                    launch_frames(c->n_sys, c->d_off, c->d_x, c->N, c->d_box, c->rc_max, c->d_frame, s);
+                    launch_quantize(c->N, c->d_x, c->d_sys, c->d_frame, c->d_q, s);
+                }
+                CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+                CUDA_TRY(cudaStreamWaitEvent(c->s_big, c->ev_fork, 0));
+                c->stream = c->s_big;                          // every launcher enqueues on c->stream
+                enqueue_eval(c, 1, false, true, Check::None);
+                c->stream = s;
+                CUDA_TRY(cudaEventRecord(c->ev_join, c->s_big));
+                enqueue_eval(c, 0, false, false, Check::None);
+                CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+            } else {
+                enqueue_eval(c, 0, nonper, false, Check::Done);   // the small model's energy is not reported
+            }
         }
-        enqueue_eval(c, 1, false, true, Check::None);          // same positions as the last small evaluation
+        if (!fork) enqueue_eval(c, 1, false, true, Check::None);   // same positions as the last small evaluation
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
                           c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, s);
         if (fallback && ce == cudaSuccess) ce = capture_fallback_node(c, mon.cond, n_inner, dt);
@@ -873,6 +896,9 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng);
     dfree(c->d_mon); dfree(c->d_sx); dfree(c->d_sv); dfree(c->d_sf);
     if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->s_big) cudaStreamDestroy(c->s_big);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
     dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -991,6 +1017,10 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
     CREATE_TRY(dalloc(&c->d_rng, 2));
     CREATE_TRY(cudaMemset(c->d_rng, 0, 2 * sizeof(unsigned long long)));
+    CREATE_TRY(cudaStreamCreateWithFlags(&c->s_big, cudaStreamNonBlocking));
+    CREATE_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CREATE_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    c->concurrent = json_number(options, "concurrent_models", 1.0) != 0.0;
     CREATE_TRY(dalloc(&c->d_mon, 1));
     CREATE_TRY(cudaMemset(c->d_mon, 0, sizeof(ForceMonitor)));
     if (c->fb_threshold > 0.0) {
