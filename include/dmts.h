@@ -242,12 +242,13 @@ DMTS_API int dmts_hmr_masses(int n_atoms, const double* mass, int n_bonds, const
  * them. Both 0 when the skin is 0. Synchronises the context's stream. */
 DMTS_API int dmts_neighbor_stats(dmts_ctx* ctx, long long* n_checks, long long* n_rebuilds);
 
-/* Work granularity of one model's force kernels: atoms per thread block
- * (FP32) or atoms per work chunk (BF16), forward and backward. The tuner
- * (option "autotune", default 1) times a few candidates at the context's
- * first force evaluation and keeps the fastest. FP32 results do not depend on
- * the choice; BF16 results can differ at the rounding level (partial sums are
- * grouped by tile). Returns 1 if tuned, 0 if not yet, or a negative status. */
+/* Work granularity of one model's force kernels, forward and backward:
+ * atoms per thread block (FP32), or persistent thread blocks per SM (BF16,
+ * 0 = as many as fit; the tensor-core kernels cut the pair list into
+ * 128-pair tiles). The tuner (option "autotune", default 1) times the
+ * candidates at the context's first force evaluation and keeps the fastest
+ * for each pass. Results do not depend on the choice. Returns 1 if tuned, 0
+ * if not yet, or a negative status. */
 DMTS_API int dmts_get_tuning(dmts_ctx* ctx, int which, int* atoms_fwd, int* atoms_bwd);
 
 /* Time one model's force evaluation at the current positions, stage by stage,

@@ -92,7 +92,9 @@ struct Model {
     unsigned char* wt = nullptr;       // BF16 filter-weight operand tiles, per layer
     size_t wt_layer_bytes = 0;
     double *Ei = nullptr, *E = nullptr, *W = nullptr;
-    int apc_fwd = 16, apc_bwd = 16;
+    int apc_fwd = 16, apc_bwd = 16;    // FP32 kernels: atoms per CTA
+    int cps_fwd = 0, cps_bwd = 0;      // tensor-core kernels: persistent CTAs per SM (0: as many as fit)
+    float* carry = nullptr;            // tensor-core path: per-tile partial sums of split rows
 };
 
 }  // namespace
@@ -208,8 +210,9 @@ int check_model(const dmts_model_desc* d, const char* name) {
 }
 
 void free_model_nbr(Model& m) {
-    dfree(m.nbr_tmp); dfree(m.col); dfree(m.recv); dfree(m.vl_rows);
+    dfree(m.nbr_tmp); dfree(m.col); dfree(m.recv); dfree(m.vl_rows); dfree(m.carry);
     m.nbr_tmp = m.col = m.recv = m.vl_rows = nullptr;
+    m.carry = nullptr;
 }
 
 cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
@@ -218,6 +221,8 @@ cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
     if ((e = dalloc(&m.col, (size_t)m.e_cap)) != cudaSuccess) return e;
     if ((e = dalloc(&m.recv, (size_t)m.e_cap)) != cudaSuccess) return e;
     if (c->skin > 0 && (e = dalloc(&m.vl_rows, (size_t)c->N * m.vl_cap)) != cudaSuccess) return e;
+    const size_t tiles = (size_t)((m.e_cap + 127) / 128);
+    if ((e = dalloc(&m.carry, tiles * 2 * (size_t)(m.F + 16))) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -375,9 +380,9 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     const bool tc = m.precision == DMTS_BF16_MLP;
     // FP32: atoms per CTA (bounded by shared memory); BF16: atoms per chunk of
     // the persistent kernels
-    int mf = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, false);
-    int mb = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, true);
-    int want = tc ? 8 : (m.F == 64 ? 16 : 32);
+    int mf = max_atoms_per_cta_f32(m.F, m.K, false);
+    int mb = max_atoms_per_cta_f32(m.F, m.K, true);
+    int want = m.F == 64 ? 16 : 32;
     m.apc_fwd = std::max(8, std::min(want, mf));
     m.apc_bwd = std::max(8, std::min(want, mb));
     return DMTS_OK;
@@ -438,6 +443,8 @@ PotArgs pot_args(dmts_ctx* c, Model& m) {
     a.wt = m.wt;
     a.wt_layer_bytes = m.wt_layer_bytes;
     a.PT = m.PT;
+    a.carry = m.carry;
+    a.carry_w = m.F + 16;
     a.h = m.h;
     a.h_in = m.h;
     a.gh = m.gh;
@@ -582,6 +589,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
         f.layer = l;
         f.h_in = l == 0 ? m.h0 : m.h;
         f.atoms_per_cta = m.apc_fwd;
+        f.ctas_per_sm = m.cps_fwd;
         f.u = m.u[l];
         f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
         f.z = m.z[l];
@@ -593,6 +601,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
         PotArgs b = a;
         b.layer = l;
         b.atoms_per_cta = m.apc_bwd;
+        b.ctas_per_sm = m.cps_bwd;
         b.u = m.u[l];
         b.mbar = m.mbar[l & 1];
         b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
@@ -814,15 +823,20 @@ int autotune_models(dmts_ctx* c) {
         Model& m = c->m[w];
         if (!m.present) continue;
         const bool tc = m.precision == DMTS_BF16_MLP;
-        std::vector<int> cand = tc ? std::vector<int>{4, 8, 12, 16, 24, 32}
-                                   : (m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48});
-        const int lim_f = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, false);
-        const int lim_b = tc ? 256 : max_atoms_per_cta_f32(m.F, m.K, true);
+        // tensor-core kernels: persistent CTAs per SM; FP32 kernels: atoms per CTA
+        const int mx = tc ? std::max(bf16_max_ctas_per_sm(m.F, false), bf16_max_ctas_per_sm(m.F, true)) : 0;
+        std::vector<int> cand;
+        if (tc) for (int k = 1; k <= mx; ++k) cand.push_back(k);
+        else cand = m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48};
+        const int lim_f = tc ? bf16_max_ctas_per_sm(m.F, false) : max_atoms_per_cta_f32(m.F, m.K, false);
+        const int lim_b = tc ? bf16_max_ctas_per_sm(m.F, true) : max_atoms_per_cta_f32(m.F, m.K, true);
+        int& gf = tc ? m.cps_fwd : m.apc_fwd;
+        int& gb = tc ? m.cps_bwd : m.apc_bwd;
         double best_tf = 1e30, best_tb = 1e30;
-        int best_f = m.apc_fwd, best_b = m.apc_bwd;
+        int best_f = gf, best_b = gb;
         for (int A : cand) {
-            m.apc_fwd = std::min(A, lim_f);
-            m.apc_bwd = std::min(A, lim_b);
+            gf = std::min(A, lim_f);
+            gb = std::min(A, lim_b);
             std::vector<double> st;
             if ((rc = time_stages_impl(c, w, 3, st))) break;   // sizes capacities, then times the stages
             double tf = 0.0, tb = 0.0;                          // forward and backward edge passes
@@ -830,11 +844,11 @@ int autotune_models(dmts_ctx* c) {
                 tf += st[2 + l];
                 tb += st[2 + 2 * m.L + l];
             }
-            if (tf < best_tf) { best_tf = tf; best_f = m.apc_fwd; }
-            if (tb < best_tb) { best_tb = tb; best_b = m.apc_bwd; }
+            if (tf < best_tf) { best_tf = tf; best_f = gf; }
+            if (tb < best_tb) { best_tb = tb; best_b = gb; }
         }
-        m.apc_fwd = best_f;
-        m.apc_bwd = best_b;
+        gf = best_f;
+        gb = best_b;
     }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     c->tuned = true;
@@ -1385,6 +1399,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             f.layer = l;
             f.h_in = l == 0 ? m.h0 : m.h;
             f.atoms_per_cta = m.apc_fwd;
+            f.ctas_per_sm = m.cps_fwd;
             f.u = m.u[l];
             f.u_next = (l + 1 < L) ? m.u[l + 1] : nullptr;
             f.z = m.z[l];
@@ -1400,6 +1415,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             PotArgs b = a;
             b.layer = l;
             b.atoms_per_cta = m.apc_bwd;
+            b.ctas_per_sm = m.cps_bwd;
             b.u = m.u[l];
             b.mbar = m.mbar[l & 1];
             b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
@@ -1498,8 +1514,9 @@ int dmts_get_tuning(dmts_ctx* c, int which, int* atoms_fwd, int* atoms_bwd) {
     if (!c) return fail(DMTS_ERR_ARG, "context is NULL");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
-    if (atoms_fwd) *atoms_fwd = c->m[which].apc_fwd;
-    if (atoms_bwd) *atoms_bwd = c->m[which].apc_bwd;
+    const bool tc = c->m[which].precision == DMTS_BF16_MLP;
+    if (atoms_fwd) *atoms_fwd = tc ? c->m[which].cps_fwd : c->m[which].apc_fwd;
+    if (atoms_bwd) *atoms_bwd = tc ? c->m[which].cps_bwd : c->m[which].apc_bwd;
     return c->tuned ? 1 : 0;
 }
 

@@ -187,6 +187,10 @@ struct PotArgs {
     float* vir6;             // [N][6]
     int accumulate;          // backward: add to force/vir6 instead of overwrite
     int virial;              // backward: also the per-atom virial vir6 (tensor-core path; FP32 always)
+    // tensor-core path: 128-pair tiles
+    float* carry;            // [tiles][2][carry_w] partial sums of rows split across tiles
+    int carry_w;             // F + 16
+    int ctas_per_sm;         // persistent CTAs per SM (0: as many as fit)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -220,6 +224,7 @@ int max_atoms_per_cta_f32(int F, int K, bool bwd);
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
 size_t bf16_weight_tile_bytes(int F);
+int bf16_max_ctas_per_sm(int F, bool bwd);
 
 // distill_f32.cu: force-matching gradient of a single-layer model
 bool fm_supported(int F, int K, int L);

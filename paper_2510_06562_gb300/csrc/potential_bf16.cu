@@ -218,25 +218,64 @@ __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, 
     }
 }
 
-// Merge the slots of one tile (thread f of the first F threads).
+// Pair tiles. Tile t holds pairs [tb, te) = [128 t, min(128 t + 128, E)).
+// A row's segment in the tile is complete when the row starts and ends
+// inside it; otherwise the tile's first segment (a row begun in an earlier
+// tile) goes to the tile's "first" carry slot and its last segment (a row
+// that continues into later tiles) to its "last" slot. k_tile_fixup then
+// gives each split row the sum of its head tile's last slot and the later
+// tiles' first slots, in tile order. Carry slots hold F vector values then
+// the scalar values of the pass. prev_row / next_row are the rows of pairs
+// tb - 1 and te (-1 if none): the first segment continues an earlier tile
+// iff its row is prev_row, the last continues into a later one iff its row
+// is next_row.
+struct TileCtx {
+    int prev_row, next_row;
+    float* cf;                 // this tile's first carry slot
+    float* cl;                 // this tile's last carry slot
+};
+
+// 0: complete in the tile; 1: continues a row of earlier tiles; 2: a row
+// that starts here and continues into later tiles.
+__device__ __forceinline__ int seg_route(const TileCtx& t, int r, bool first, bool last) {
+    const bool start_in = !first || r != t.prev_row;
+    const bool end_in = !last || r != t.next_row;
+    return (start_in && end_in) ? 0 : (start_in ? 2 : 1);
+}
+
+// Merge the warp slots of one tile in edge order (thread f of the first F
+// threads) and route each segment.
 template <int F>
-__device__ __forceinline__ void merge_vec_slots(const VecSlots<F>* vs, int f, int& cur, float& run,
-                                                float* __restrict__ out, int a0) {
+__device__ __forceinline__ void merge_tile_vec(const VecSlots<F>* vs, int f, const TileCtx& t,
+                                               float* __restrict__ out) {
+    int cur = -1;
+    float run = 0.f;
+    bool first = true;
+    auto put = [&](int r, float v, bool fst, bool lst) {
+        const int rt = seg_route(t, r, fst, lst);
+        if (rt == 0) out[(size_t)r * F + f] = v;
+        else if (rt == 1) t.cf[f] = v;
+        else t.cl[f] = v;
+    };
 #pragma unroll
     for (int w = 0; w < 4; ++w)
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            int r = vs->row[w][k];
+            const int r = vs->row[w][k];
             if (r < 0) continue;
-            float v = vs->v[w][k][f];
+            const float v = vs->v[w][k][f];
             if (r == cur) {
                 run += v;
             } else {
-                if (cur >= 0) out[(size_t)(a0 + cur) * F + f] = run;
+                if (cur >= 0) {
+                    put(cur, run, first, false);
+                    first = false;
+                }
                 cur = r;
                 run = v;
             }
         }
+    if (cur >= 0) put(cur, run, first, true);
 }
 
 template <int NV>
@@ -271,6 +310,83 @@ __device__ __forceinline__ void warp_scal_segments(float* val, int row, ScalSlot
     if (lane == 0) ss->n[w] = __popc(ends);
 }
 
+// Scalar counterpart of merge_tile_vec (thread c of NV threads): the
+// segment ends of the four warps in edge order. store(r, c, v) writes a
+// complete row; carries go to slot index F + c.
+template <int NV, int F, class Store>
+__device__ __forceinline__ void merge_tile_scal(const ScalSlots<NV>* ss, int c, const TileCtx& t, Store store) {
+    int cur = -1;
+    float run = 0.f;
+    bool first = true;
+    auto put = [&](int r, float v, bool fst, bool lst) {
+        const int rt = seg_route(t, r, fst, lst);
+        if (rt == 0) store(r, c, v);
+        else if (rt == 1) t.cf[F + c] = v;
+        else t.cl[F + c] = v;
+    };
+    for (int w = 0; w < 4; ++w)
+        for (int k = 0; k < ss->n[w]; ++k) {
+            const int r = ss->row[w][k];
+            const float v = ss->v[w][k][c];
+            if (r == cur) {
+                run += v;
+            } else {
+                if (cur >= 0) {
+                    put(cur, run, first, false);
+                    first = false;
+                }
+                cur = r;
+                run = v;
+            }
+        }
+    if (cur >= 0) put(cur, run, first, true);
+}
+
+// Split rows and rows without pairs after a tiled pass (one warp per atom):
+// rows inside one tile were written by the pass. vec_out (F values per atom)
+// may be null; n_scal scalars go to erep (kind 0) or to the force and the
+// per-atom virial (kind 1, added when accumulate).
+template <int F>
+__global__ void __launch_bounds__(256) k_tile_fixup(int n, const int* __restrict__ row_ptr, long long e_cap,
+                                                    const float* __restrict__ carry, int cw, float* __restrict__ vec_out,
+                                                    int n_scal, int kind, float* __restrict__ erep,
+                                                    float* __restrict__ force, float* __restrict__ vir6,
+                                                    int accumulate) {
+    constexpr int NF = F / 32;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const long long r0 = min((long long)row_ptr[i], e_cap), r1 = min((long long)row_ptr[i + 1], e_cap);
+    float v[NF], sc = 0.f;
+#pragma unroll
+    for (int c = 0; c < NF; ++c) v[c] = 0.f;
+    if (r1 > r0) {
+        const long long t0 = r0 >> 7, t1 = (r1 - 1) >> 7;
+        if (t0 == t1) return;                              // written by the tile
+        const float* cl = carry + (2 * t0 + 1) * (long long)cw;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) v[c] = cl[lane + 32 * c];
+        if (lane < n_scal) sc = cl[F + lane];
+        for (long long u = t0 + 1; u <= t1; ++u) {
+            const float* cf = carry + 2 * u * (long long)cw;
+#pragma unroll
+            for (int c = 0; c < NF; ++c) v[c] += cf[lane + 32 * c];
+            if (lane < n_scal) sc += cf[F + lane];
+        }
+    }
+    if (vec_out)
+#pragma unroll
+        for (int c = 0; c < NF; ++c) vec_out[(size_t)i * F + lane + 32 * c] = v[c];
+    if (lane < n_scal) {
+        if (kind == 0) {
+            erep[i] = sc;
+        } else {
+            float* dst = lane < 3 ? force + (size_t)lane * n + i : vir6 + (size_t)i * 6 + lane - 3;
+            *dst = accumulate ? *dst + sc : sc;
+        }
+    }
+}
+
 // ------------------------------------------------------------ forward
 template <int F>
 struct FwdSmem {
@@ -292,9 +408,9 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
     FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
-    const int A = a.atoms_per_cta;
-    const int n_chunks = (a.n_atoms + A - 1) / A;
-    if ((int)blockIdx.x >= n_chunks) return;
+    const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
+    const long long n_tiles = (E + kT - 1) / kT;
+    if ((long long)blockIdx.x >= n_tiles) return;
 
     // weights: pre-converted BF16 operand tiles (16-byte copies)
     {
@@ -322,26 +438,23 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int chunk = blockIdx.x; chunk < n_chunks && ok; chunk += gridDim.x) {
-        const int a0 = chunk * A;
-        const int a1 = min(a.n_atoms, a0 + A);
-        // rows without edges must read as zero
-        for (int t = tid; t < (a1 - a0) * F; t += kT) a.msg_out[(size_t)a0 * F + t] = 0.f;
-        if (l == 0)
-            for (int t = tid; t < a1 - a0; t += kT) a.erep[a0 + t] = 0.f;
-        const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
-        const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
-        int cur = -1;          // open row of the merged sums (threads < F: messages, thread F: repulsion)
-        float run = 0.f;
-        EdgeIn nx;
-        load_idx(a, e_beg + tid, e_end, nx);
-        load_pos(a, nx);
-        for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
+    const int cw = a.carry_w;
+    EdgeIn nx;
+    load_idx(a, (long long)blockIdx.x * kT + tid, E, nx);
+    load_pos(a, nx);
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        {
+            const long long tb = tile * kT, te = min(tb + kT, E);
+            int prev_row = -1, next_row = -1;              // read by the merges at the end of the tile
+            if (tid <= F) {
+                if (tb > 0) prev_row = __ldg(a.recv + tb - 1);
+                if (te < E) next_row = __ldg(a.recv + te);
+            }
             const EdgeIn ex = nx;
             const bool valid = ex.j >= 0;
-            const int j = valid ? ex.j : a0;
-            const int row = valid ? ex.i - a0 : -1;
-            load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
+            const int j = valid ? ex.j : 0;
+            const int row = valid ? ex.i : -1;
+            load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // the message needs u_j: start copying the warp's rows into P now
             gather_rows<F>(S.P, a.u, j);
             cp_async_commit();
@@ -423,30 +536,17 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss);
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, a0);
+            warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, 0);
             __syncthreads();
+            const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (tid < F) {
-                merge_vec_slots<F>(&S.vs, tid, cur, run, a.msg_out, a0);
+                merge_tile_vec<F>(&S.vs, tid, tc, a.msg_out);
             } else if (tid == F && l == 0) {
-                for (int w = 0; w < 4; ++w)
-                    for (int k = 0; k < S.ss.n[w]; ++k) {
-                        int r = S.ss.row[w][k];
-                        float v = S.ss.v[w][k][0];
-                        if (r == cur) run += v;
-                        else {
-                            if (cur >= 0) a.erep[a0 + cur] = run;
-                            cur = r;
-                            run = v;
-                        }
-                    }
+                float* erep = a.erep;
+                merge_tile_scal<1, F>(&S.ss, 0, tc, [erep](int r, int, float v) { erep[r] = v; });
             }
             // the slots are rewritten only after two more barriers (next tile)
         }
-        if (cur >= 0) {
-            if (tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
-            else if (tid == F && l == 0) a.erep[a0 + cur] = run;
-        }
-        __syncthreads();
     }
     fence_before_sync();
     __syncthreads();
@@ -482,9 +582,9 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     constexpr int TCOLS = 4 * F;   // D1 | D4 | D2 | D3
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
-    const int A = a.atoms_per_cta;
-    const int n_chunks = (a.n_atoms + A - 1) / A;
-    if ((int)blockIdx.x >= n_chunks) return;
+    const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
+    const long long n_tiles = (E + kT - 1) / kT;
+    if ((long long)blockIdx.x >= n_tiles) return;
     const bool need_ubar = (l > 0);
 
     {
@@ -516,33 +616,23 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int chunk = blockIdx.x; chunk < n_chunks && ok; chunk += gridDim.x) {
-        const int a0 = chunk * A;
-        const int a1 = min(a.n_atoms, a0 + A);
-        const int nA = a1 - a0;
-        if (need_ubar)
-            for (int t = tid; t < nA * F; t += kT) a.msg_out[(size_t)a0 * F + t] = 0.f;
-        const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap);
-        const long long e_end = min((long long)a.row_ptr[a1], a.e_cap);
-        int cur = -1;      // threads < F: ubar row; threads F..F+NV-1: force / virial row
-        float run = 0.f;
-        // per-atom force and virial start at zero (or keep the later layer's value)
-        if (!a.accumulate)
-            for (int t = tid; t < nA * NV; t += kT) {
-                int r = t / NV, c = t % NV;
-                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + r] = 0.f;
-                else a.vir6[(size_t)(a0 + r) * 6 + c - 3] = 0.f;
+    const int cw = a.carry_w;
+    EdgeIn nx;
+    load_idx(a, (long long)blockIdx.x * kT + tid, E, nx);
+    load_pos(a, nx);
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        {
+            const long long tb = tile * kT, te = min(tb + kT, E);
+            int prev_row = -1, next_row = -1;              // read by the merges at the end of the tile
+            if (tid < F + NV) {
+                if (tb > 0) prev_row = __ldg(a.recv + tb - 1);
+                if (te < E) next_row = __ldg(a.recv + te);
             }
-        __syncthreads();
-        EdgeIn nx;
-        load_idx(a, e_beg + tid, e_end, nx);
-        load_pos(a, nx);
-        for (long long t0 = e_beg; t0 < e_end && ok; t0 += kT) {
             const EdgeIn ex = nx;
             const bool valid = ex.j >= 0;
-            const int j = valid ? ex.j : a0;
-            const int row = valid ? ex.i - a0 : -1;
-            load_idx(a, t0 + kT + tid, e_end, nx);        // next tile's indices
+            const int j = valid ? ex.j : 0;
+            const int row = valid ? ex.i : -1;
+            load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // g needs mbar_j and u_j, the ubar message mbar_j: start the warp's row copies now
             gather_rows<F>(S.P, a.mbar, j);
             gather_rows<F>(S.U, a.u, j);
@@ -618,7 +708,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             __syncwarp();
             float gphi = 0.f;
             {
-                const int i = row < 0 ? a0 : a0 + row;
+                const int i = valid ? row : 0;
                 const float* ui = a.u + (size_t)i * F;
                 const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
@@ -694,38 +784,22 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             }
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            if (need_ubar) warp_vec_segments<F>(S.P, S.row, vs, a.msg_out, a0);
+            if (need_ubar) warp_vec_segments<F>(S.P, S.row, vs, a.msg_out, 0);
             __syncthreads();
+            const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (need_ubar && tid < F) {
-                merge_vec_slots<F>(vs, tid, cur, run, a.msg_out, a0);
+                merge_tile_vec<F>(vs, tid, tc, a.msg_out);
             } else if (tid >= F && tid < F + NV) {
-                const int c = tid - F;
-                for (int w = 0; w < 4; ++w)
-                    for (int k = 0; k < S.ss.n[w]; ++k) {
-                        int r = S.ss.row[w][k];
-                        float v = S.ss.v[w][k][c];
-                        if (r == cur) run += v;
-                        else {
-                            if (cur >= 0) {
-                                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + cur] += run;
-                                else a.vir6[(size_t)(a0 + cur) * 6 + c - 3] += run;
-                            }
-                            cur = r;
-                            run = v;
-                        }
-                    }
+                float* force = a.force;
+                float* vir6 = a.vir6;
+                const int n = a.n_atoms, acc = a.accumulate;
+                merge_tile_scal<NV, F>(&S.ss, tid - F, tc, [=](int r, int c, float v) {
+                    float* dst = c < 3 ? force + (size_t)c * n + r : vir6 + (size_t)r * 6 + c - 3;
+                    *dst = acc ? *dst + v : v;
+                });
             }
             __syncthreads();                               // slots read before the next basis overwrites a1
         }
-        if (cur >= 0) {
-            if (need_ubar && tid < F) a.msg_out[(size_t)(a0 + cur) * F + tid] = run;
-            else if (tid >= F && tid < F + NV) {
-                const int c = tid - F;
-                if (c < 3) a.force[(size_t)c * a.n_atoms + a0 + cur] += run;
-                else a.vir6[(size_t)(a0 + cur) * 6 + c - 3] += run;
-            }
-        }
-        __syncthreads();
     }
     fence_before_sync();
     __syncthreads();
@@ -733,35 +807,42 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     if (!ok && tid == 0) atomicOr(status, 1);
 }
 
-// Persistent launch: one CTA per resident slot, bounded by shared memory
-// (1 KB reserved per CTA) and by the 512 tensor-memory columns of an SM.
+// Persistent launch: SMs x CTAs per SM, bounded by shared memory (1 KB
+// reserved per CTA), the 512 tensor-memory columns of an SM and the tuner's
+// choice; never more CTAs than tiles the pair capacity can hold.
 template <class Kern>
-void launch_persistent(Kern kern, int smem, int tmem_cols, int& grid_cap, const PotArgs& a, int K, int* status,
-                       cudaStream_t s) {
-    if (!grid_cap) {
+void launch_persistent(Kern kern, int smem, int tmem_cols, int& max_per_sm, int& sms, const PotArgs& a, int K,
+                       int* status, cudaStream_t s) {
+    if (!max_per_sm) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int dev = 0, sms = 0, smem_sm = 0;
+        int dev = 0, smem_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        const int by_smem = smem_sm / (smem + 1024);
-        const int by_tmem = 512 / tmem_cols;
-        grid_cap = std::max(1, sms * std::max(1, std::min(by_smem, by_tmem)));
+        max_per_sm = std::max(1, std::min(smem_sm / (smem + 1024), 512 / tmem_cols));
     }
-    int n_chunks = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
-    kern<<<std::min(n_chunks, grid_cap), kT, smem, s>>>(a, K, status);
+    const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, max_per_sm) : max_per_sm;
+    const long long tiles = (a.e_cap + kT - 1) / kT;
+    const long long grid = std::min<long long>(tiles, (long long)sms * per_sm);
+    if (grid > 0) kern<<<(int)grid, kT, smem, s>>>(a, K, status);
 }
 
 template <int F>
 void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static int cap = 0;
-    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, cap, a, K, status, s);
+    static int cap = 0, sms = 0;
+    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, cap, sms, a, K, status, s);
+    k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
+                                                                 a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
+                                                                 nullptr, nullptr, 0);
 }
 
 template <int F, int NV>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static int cap = 0;
-    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 4 * F, cap, a, K, status, s);
+    static int cap = 0, sms = 0;
+    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 4 * F, cap, sms, a, K, status, s);
+    k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
+                                                                 a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
+                                                                 a.force, a.vir6, a.accumulate);
 }
 
 }  // namespace
@@ -770,7 +851,7 @@ void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
     if (a.n_atoms == 0) return;
     if (F == 64) go_fwd<64>(a, K, status, s);
     else go_fwd<32>(a, K, status, s);
-    count_launch();
+    count_launch(2);
 }
 
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
@@ -782,7 +863,19 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
         if (F == 64) go_bwd<64, 3>(a, K, status, s);
         else go_bwd<32, 3>(a, K, status, s);
     }
-    count_launch();
+    count_launch(2);
+}
+
+int bf16_max_ctas_per_sm(int F, bool bwd) {
+    const int smem = bwd ? (int)(F == 64 ? sizeof(BwdSmem<64, 3>) : sizeof(BwdSmem<32, 3>))
+                         : (int)(F == 64 ? sizeof(FwdSmem<64>) : sizeof(FwdSmem<32>));
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        smem_sm = 233472;
+    }
+    return std::max(1, std::min(smem_sm / (smem + 1024), 512 / ((bwd ? 4 : 2) * F)));
 }
 
 size_t bf16_weight_tile_bytes(int F) {
