@@ -285,9 +285,8 @@ DMTS_API int dmts_force_matching_grad(dmts_ctx* ctx, int n_frames, const double*
  * Allocation-free neighbour list. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- an MD engine
  * that owns all device memory through its own pool and hands plug-ins
- * pre-allocated buffers, or code running under a fixed memory budget or
- * inside a stream capture, where cudaMalloc would synchronise the device or
- * invalidate the capture.
+ * pre-allocated buffers, or code running under a fixed memory budget, where
+ * a cudaMalloc would synchronise the device or fail.
  *
  * Computes the same pair set and row order as dmts_neighbors for one system
  * without a context: directed pairs (i, j), j != i, |r_ij|^2 < cutoff^2 in

@@ -3,9 +3,9 @@
 //
 // Some callers cannot call cudaMalloc: an MD engine that owns every byte of
 // device memory through its own pool and hands plug-ins pre-allocated
-// buffers, or code running under a fixed memory budget or inside a stream
-// capture where an allocation would synchronise the device or break the
-// capture. For them this entry point keeps its scratch (fixed-point
+// buffers, or code running under a fixed memory budget where an allocation
+// would synchronise the device or fail. For them this entry point keeps its
+// scratch (fixed-point
 // positions, cell list, per-atom counts) in one file-scope static device
 // array of fixed size, reserved once per device when the library is loaded
 // and held until the process exits. The caller passes device buffers for the

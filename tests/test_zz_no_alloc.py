@@ -2,7 +2,7 @@
 
 It serves callers that cannot allocate device memory themselves or let a
 library do so: an MD engine that owns all device memory through its own pool,
-or code under a fixed memory budget or inside a stream capture. Its scratch
+or code under a fixed memory budget. Its scratch
 is a static device array, so these checks call it twice in a row on different
 systems (the second call sees the first call's leftovers) and compare each
 result, through the C ABI, with the context-based dmts_neighbors: the pair
