@@ -76,7 +76,8 @@ struct Model {
     float* P = nullptr;
     int nc = 0, n_cells = 0;
     int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr, *atom_cell = nullptr,
-        *atom_slot = nullptr;
+        *atom_slot = nullptr, *atom_pos = nullptr;
+    uint4* cell_q = nullptr;
     int row_cap = 0;
     long long e_cap = 0;
     int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
@@ -229,6 +230,7 @@ cudaError_t alloc_model_nbr(dmts_ctx* c, Model& m) {
 void free_model(Model& m) {
     dfree(m.P);
     dfree(m.cell_count); dfree(m.cell_start); dfree(m.cell_atoms); dfree(m.atom_cell); dfree(m.atom_slot);
+    dfree(m.atom_pos); dfree(m.cell_q);
     free_model_nbr(m);
     dfree(m.nbr_cnt); dfree(m.row_ptr); dfree(m.vl_cnt);
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
@@ -354,6 +356,8 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
         CUDA_TRY(dalloc(&m.cell_atoms, N));
         CUDA_TRY(dalloc(&m.atom_cell, N));
         CUDA_TRY(dalloc(&m.atom_slot, N));
+        CUDA_TRY(dalloc(&m.atom_pos, N));
+        CUDA_TRY(dalloc(&m.cell_q, N));
     }
     CUDA_TRY(alloc_model_nbr(c, m));
     CUDA_TRY(dalloc(&m.nbr_cnt, N));
@@ -404,6 +408,8 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
     a.nc = m.nc;
     a.cell_start = m.cell_start;
     a.cell_atoms = m.cell_atoms;
+    a.cell_q = m.cell_q;
+    a.atom_pos = m.atom_pos;
     a.row_cap = m.row_cap;
     a.e_cap = m.e_cap;
     a.nbr_tmp = m.nbr_tmp;
@@ -514,7 +520,7 @@ void enqueue_rebuild(dmts_ctx* c, cudaStream_t s) {
     NbrArgs b = candidate_args(c, w0);
     if (src.nc > 0)
         launch_cells_gated(c->N, c->d_q, src.nc, src.cell_count, src.cell_start, src.cell_atoms, src.atom_cell,
-                           src.atom_slot, b.gate, s);
+                           src.atom_slot, src.cell_q, src.atom_pos, b.gate, s);
     b.xref = c->d_xref;
     launch_vl_build(b, s);
     if (c->m[1 - w0].present) {
@@ -548,7 +554,8 @@ void enqueue_neighbors(dmts_ctx* c, int which, bool quantize, Check check = Chec
     }
     if (c->skin <= 0) {
         if (m.nc > 0)
-            launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot, s);
+            launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot,
+                         m.cell_q, m.atom_pos, s);
         launch_neighbors(nbr_args(c, m, which), s);
         return;
     }

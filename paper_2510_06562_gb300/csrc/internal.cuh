@@ -125,7 +125,9 @@ struct NbrArgs {
     float rc2_lo, rc2_hi;    // FP32 band around rc^2
     int nc;                  // cells per dimension (0: all pairs within system)
     const int* cell_start;   // [nc^3 + 1]
-    const int* cell_atoms;   // [N]
+    const int* cell_atoms;   // [N] atoms in cell order
+    const uint4* cell_q;     // [N] their fixed-point positions, in cell order
+    const int* atom_pos;     // [N] each atom's place in cell order
     int row_cap;
     long long e_cap;
     int* nbr_tmp;            // [N][row_cap]
@@ -200,7 +202,7 @@ void launch_frames(int n_sys, const int* atom_offset, const double* x, int n_ato
 void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const Frame* frame,
                      uint4* q, cudaStream_t s);
 void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s);
+                  int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos, cudaStream_t s);
 void launch_neighbors(const NbrArgs& a, cudaStream_t s);
 // Verlet-skin lists: displacement check (sets st->rebuild), gated cell list,
 // gated candidate build (a.nbr_tmp / a.nbr_cnt / a.row_cap = candidate rows),
@@ -209,7 +211,8 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s);
 void launch_vl_check(int n_atoms, const double* x, const int* sys_of_atom, const double* box,
                      const VerletCheck& vc, cudaStream_t s);
 void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                        int* cell_atoms, int* atom_cell, int* atom_slot, const int* gate, cudaStream_t s);
+                        int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos,
+                        const int* gate, cudaStream_t s);
 void launch_vl_build(const NbrArgs& a, cudaStream_t s);
 void launch_row_filter(const NbrArgs& a, cudaStream_t s);
 void launch_vl_filter(const NbrArgs& a, cudaStream_t s);

@@ -211,29 +211,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_1cta(int n, const int* __
     }
 }
 
+// Atoms in cell order, with their fixed-point positions beside them (the
+// builder then reads each cell's candidates contiguously) and each atom's own
+// place in that order.
 __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell, const int* __restrict__ slot,
-                            const int* __restrict__ start, int* __restrict__ cell_atoms, const int* gate) {
+                            const int* __restrict__ start, int* __restrict__ cell_atoms, const uint4* __restrict__ q,
+                            uint4* __restrict__ cell_q, int* __restrict__ atom_pos, const int* gate) {
     if (gated_off(gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cell_atoms[start[atom_cell[i]] + slot[i]] = i;
+    const int pos = start[atom_cell[i]] + slot[i];
+    cell_atoms[pos] = i;
+    cell_q[pos] = q[i];
+    atom_pos[i] = pos;
 }
 
 void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                        int* cell_atoms, int* atom_cell, int* atom_slot, const int* gate, cudaStream_t s) {
+                        int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos,
+                        const int* gate, cudaStream_t s) {
     int n_cells = nc * nc * nc;
     if (n_atoms == 0) return;
     k_cell_clear<<<std::min(152, (n_cells + 255) / 256), 256, 0, s>>>(n_cells, cell_count, gate);
     int g = (n_atoms + 255) / 256;
     k_cell_count<<<g, 256, 0, s>>>(n_atoms, q, nc, cell_count, atom_cell, atom_slot, gate);
     k_scan_1cta<<<1, kScanThreads, 0, s>>>(n_cells, cell_count, cell_start, 0, nullptr, 0, gate);
-    k_cell_fill<<<g, 256, 0, s>>>(n_atoms, atom_cell, atom_slot, cell_start, cell_atoms, gate);
+    k_cell_fill<<<g, 256, 0, s>>>(n_atoms, atom_cell, atom_slot, cell_start, cell_atoms, q, cell_q, atom_pos, gate);
     count_launch(4);
 }
 
 void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                  int* cell_atoms, int* atom_cell, int* atom_slot, cudaStream_t s) {
-    launch_cells_gated(n_atoms, q, nc, cell_count, cell_start, cell_atoms, atom_cell, atom_slot, nullptr, s);
+                  int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos, cudaStream_t s) {
+    launch_cells_gated(n_atoms, q, nc, cell_count, cell_start, cell_atoms, atom_cell, atom_slot, cell_q, atom_pos,
+                       nullptr, s);
 }
 
 // ------------------------------------------------------------ neighbours
@@ -300,6 +309,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
     }
     int n_row = 0;
     const float rc2_lo = a.rc2_lo, rc2_hi = a.rc2_hi;
+    const int my_pos = a.nc > 0 ? a.atom_pos[i] : -1;
     for (int v0 = 0; v0 < total; v0 += 32) {
         int v = v0 + lane;
         bool keep = false;
@@ -310,15 +320,27 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
                     if (c + step < 27 && cpre[c + step] <= v) c += step;
-                j = a.cell_atoms[cstart[c] + (v - cpre[c])];
+                // candidates in cell order: consecutive lanes read consecutive positions
+                const int pos = cstart[c] + (v - cpre[c]);
+                if (pos != my_pos) {
+                    float3 r = edge_vec(qi, a.cell_q[pos], qscale);
+                    float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    if (d2 < rc2_lo) {
+                        keep = true;
+                        j = a.cell_atoms[pos];
+                    } else if (d2 <= rc2_hi) {
+                        j = a.cell_atoms[pos];
+                        keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
+                    }
+                }
             } else {
                 j = base + v;
-            }
-            if (j != i) {
-                float3 r = edge_vec(qi, a.q[j], qscale);
-                float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                if (d2 < rc2_lo) keep = true;
-                else if (d2 <= rc2_hi) keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
+                if (j != i) {
+                    float3 r = edge_vec(qi, a.q[j], qscale);
+                    float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    if (d2 < rc2_lo) keep = true;
+                    else if (d2 <= rc2_hi) keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
+                }
             }
         }
         unsigned int m = __ballot_sync(0xffffffffu, keep);
