@@ -15,6 +15,8 @@
 // natural [atom][k] layout in shared memory; the weight matrix of the next
 // stage (row-major; the transposed ones are copies prepared on the host)
 // streams in with cp.async while the current stage computes.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace dmts {
@@ -113,6 +115,26 @@ __device__ __forceinline__ void store_rows(float* __restrict__ dst, int base, in
     }
 }
 
+// BF16 copy of the same 4 x 4 block into interleaved rows (F * 4 bytes per
+// atom; per 16 features 16 u values then 16 mbar values, half 0 or 1).
+template <int F>
+__device__ __forceinline__ void store_rows_bf16(unsigned char* __restrict__ dst, int half, int base, int n_atoms,
+                                                int a0, int f0, const float v[4][4]) {
+    if (!dst) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = base + a0 + a;
+        if (i < n_atoms) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[a][0], v[a][1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(v[a][2], v[a][3]);
+            uint2 w;
+            w.x = *reinterpret_cast<uint32_t*>(&lo);
+            w.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(dst + (size_t)i * F * 4 + (f0 >> 4) * 64 + half * 32 + (f0 & 15) * 2) = w;
+        }
+    }
+}
+
 template <int F>
 __device__ __forceinline__ void load_rows4(float v[4][4], const float* __restrict__ src, int base, int n_atoms,
                                            int a0, int f0) {
@@ -187,6 +209,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
         __syncthreads();
         gemm4x4<F>(X, W0, a0, f0, v);                                    // u^{l+1} = h W_in^{l+1}
         store_rows<F>(p.u_next, base, p.n_atoms, a0, f0, v);
+        store_rows_bf16<F>(p.um_u_out, 0, base, p.n_atoms, a0, f0, v);
         return;
     }
     stage_w<F>(W1, r1t_of(p, F));
@@ -244,6 +267,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     __syncthreads();
     gemm4x4<F>(Y, W1, a0, f0, v);                                        // mbar = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
+    store_rows_bf16<F>(p.um_mbar_out, 1, base, p.n_atoms, a0, f0, v);
 }
 
 template <int F>
@@ -290,6 +314,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_bwd(PotArgs p, const f
     __syncthreads();
     gemm4x4<F>(X, W0, a0, f0, v);                                        // mbar^{l-1} = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
+    store_rows_bf16<F>(p.um_mbar_out, 1, base, p.n_atoms, a0, f0, v);
 }
 
 template <int F>

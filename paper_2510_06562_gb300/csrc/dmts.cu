@@ -89,6 +89,7 @@ struct Model {
     float* u[kMaxLayers] = {};
     float* z[kMaxLayers] = {};
     float* mbar[2] = {};
+    unsigned char* um[kMaxLayers] = {};   // BF16 u^l | mbar^l rows for the tensor-core backward
     float* msg = nullptr;              // [N][F] per-atom sums between edge and atom kernels
     unsigned char* wt = nullptr;       // BF16 filter-weight operand tiles, per layer
     size_t wt_layer_bytes = 0;
@@ -234,7 +235,7 @@ void free_model(Model& m) {
     free_model_nbr(m);
     dfree(m.nbr_cnt); dfree(m.row_ptr); dfree(m.vl_cnt);
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
-    for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); }
+    for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); dfree(m.um[l]); }
     dfree(m.mbar[0]); dfree(m.mbar[1]);
     dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt);
     m = Model();
@@ -370,6 +371,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     for (int l = 0; l < m.L; ++l) {
         CUDA_TRY(dalloc(&m.u[l], nf));
         CUDA_TRY(dalloc(&m.z[l], nf));
+        CUDA_TRY(dalloc(&m.um[l], nf * 4));
     }
     CUDA_TRY(dalloc(&m.mbar[0], nf));
     CUDA_TRY(dalloc(&m.mbar[1], nf));
@@ -467,6 +469,7 @@ int prepare_embedding(dmts_ctx* c, Model& m) {
     PotArgs a = pot_args(c, m);
     a.h = m.h0;
     a.u_next = m.u[0];
+    a.um_u_out = m.um[0];
     launch_embed(a, m.F, c->stream);
     CUDA_TRY(cudaGetLastError());
     return DMTS_OK;
@@ -584,6 +587,40 @@ void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
     else launch_edge_bwd_f32(a, m.F, m.K, c->stream);
 }
 
+// Arguments of layer l's forward pass (edge kernel, then atom MLP) and
+// backward pass (edge kernel, then atom MLP for l > 0).
+PotArgs fwd_args(const PotArgs& a, Model& m, int l) {
+    PotArgs f = a;
+    f.layer = l;
+    f.h_in = l == 0 ? m.h0 : m.h;
+    f.atoms_per_cta = m.apc_fwd;
+    f.ctas_per_sm = m.cps_fwd;
+    f.u = m.u[l];
+    f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
+    f.z = m.z[l];
+    f.mbar_out = m.mbar[(m.L - 1) & 1];
+    if (m.precision == DMTS_BF16_MLP) {
+        f.um_u_out = (l + 1 < m.L) ? m.um[l + 1] : nullptr;
+        f.um_mbar_out = m.um[m.L - 1];
+    }
+    return f;
+}
+
+PotArgs bwd_args(const PotArgs& a, Model& m, int l) {
+    PotArgs b = a;
+    b.layer = l;
+    b.atoms_per_cta = m.apc_bwd;
+    b.ctas_per_sm = m.cps_bwd;
+    b.u = m.u[l];
+    b.mbar = m.mbar[l & 1];
+    b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
+    b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
+    b.accumulate = (l < m.L - 1) ? 1 : 0;
+    b.um = m.um[l];
+    if (m.precision == DMTS_BF16_MLP) b.um_mbar_out = (l > 0) ? m.um[l - 1] : nullptr;
+    return b;
+}
+
 void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Check check = Check::Kernel,
                   bool virial = false) {
     Model& m = c->m[which];
@@ -592,28 +629,12 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     PotArgs a = pot_args(c, m);
     a.virial = virial ? 1 : 0;
     for (int l = 0; l < m.L; ++l) {
-        PotArgs f = a;
-        f.layer = l;
-        f.h_in = l == 0 ? m.h0 : m.h;
-        f.atoms_per_cta = m.apc_fwd;
-        f.ctas_per_sm = m.cps_fwd;
-        f.u = m.u[l];
-        f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
-        f.z = m.z[l];
-        f.mbar_out = m.mbar[(m.L - 1) & 1];
+        PotArgs f = fwd_args(a, m, l);
         launch_edge_fwd(c, m, f);
         launch_atom_fwd(f, m.F, m.msg, s);
     }
     for (int l = m.L - 1; l >= 0; --l) {
-        PotArgs b = a;
-        b.layer = l;
-        b.atoms_per_cta = m.apc_bwd;
-        b.ctas_per_sm = m.cps_bwd;
-        b.u = m.u[l];
-        b.mbar = m.mbar[l & 1];
-        b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
-        b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
-        b.accumulate = (l < m.L - 1) ? 1 : 0;
+        PotArgs b = bwd_args(a, m, l);
         launch_edge_bwd(c, m, b);
         if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
     }
@@ -1402,15 +1423,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
         begin(1);                                  // the embedding is built once per parameter upload
         end(1);
         for (int l = 0; l < L; ++l) {
-            PotArgs f = a;
-            f.layer = l;
-            f.h_in = l == 0 ? m.h0 : m.h;
-            f.atoms_per_cta = m.apc_fwd;
-            f.ctas_per_sm = m.cps_fwd;
-            f.u = m.u[l];
-            f.u_next = (l + 1 < L) ? m.u[l + 1] : nullptr;
-            f.z = m.z[l];
-            f.mbar_out = m.mbar[(L - 1) & 1];
+            PotArgs f = fwd_args(a, m, l);
             begin(2 + l);
             launch_edge_fwd(c, m, f);
             end(2 + l);
@@ -1419,15 +1432,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             end(2 + L + l);
         }
         for (int l = L - 1; l >= 0; --l) {
-            PotArgs b = a;
-            b.layer = l;
-            b.atoms_per_cta = m.apc_bwd;
-            b.ctas_per_sm = m.cps_bwd;
-            b.u = m.u[l];
-            b.mbar = m.mbar[l & 1];
-            b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
-            b.z_prev = (l > 0) ? m.z[l - 1] : nullptr;
-            b.accumulate = (l < L - 1) ? 1 : 0;
+            PotArgs b = bwd_args(a, m, l);
             begin(2 + 2 * L + l);
             launch_edge_bwd(c, m, b);
             end(2 + 2 * L + l);

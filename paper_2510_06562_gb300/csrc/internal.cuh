@@ -184,6 +184,11 @@ struct PotArgs {
     float* gh;               // dE/dh
     const float* mbar;       // mbar^l (gathered)
     float* mbar_out;         // mbar^l (forward tail) or mbar^{l-1} (backward tail)
+    // tensor-core backward: BF16 copies of u^l and mbar^l, interleaved per 16
+    // features ([N][F/16][16 u | 16 mbar], F * 4 bytes per atom), gathered per pair
+    const unsigned char* um; // layer l's rows (backward edge pass)
+    unsigned char* um_u_out; // u half, written beside u_next (or u^0 by the embedding); may be null
+    unsigned char* um_mbar_out;  // mbar half, written beside mbar_out; may be null
     double* Ei;              // [N]
     float* force;            // SoA [3][N]
     float* vir6;             // [N][6]

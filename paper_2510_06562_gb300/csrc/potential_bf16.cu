@@ -159,13 +159,12 @@ struct VecSlots {
 };
 
 template <int F>
-__device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, const int* __restrict__ srow,
+__device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, int myrow,
                                                   VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0) {
     constexpr int NF = F / 32;
     constexpr int B = 8;                           // edges whose values are loaded together
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // row of every edge of the warp, segment starts and ends as warp-uniform bit masks
-    const int myrow = srow[32 * w + lane];
+    // row of every edge of the warp (myrow: this lane's), segment starts and ends as warp-uniform bit masks
     const int prev = __shfl_up_sync(0xffffffffu, myrow, 1);
     const int next = __shfl_down_sync(0xffffffffu, myrow, 1);
     const unsigned int valid = __ballot_sync(0xffffffffu, myrow >= 0);
@@ -395,7 +394,6 @@ struct FwdSmem {
     unsigned char a1[kT * kKP * 2];     // (the second MMA's A operand lives in tensor memory)
     float b1[F], b2[F];
     float P[kT * F];                    // u_j rows, then messages (swizzled rows)
-    int row[kT];
     VecSlots<F> vs;
     ScalSlots<1> ss;
     uint64_t mbar;
@@ -472,7 +470,6 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
 #pragma unroll
                     for (int k = 0; k < kKP; ++k) eb[k] = 0.f;
                 }
-                S.row[tid] = row;
                 st_row8(S.a1, tid, 0, kKP, eb);
                 st_row8(S.a1, tid, 8, kKP, eb + 8);
             }
@@ -536,7 +533,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss);
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            warp_vec_segments<F>(S.P, S.row, &S.vs, a.msg_out, 0);
+            warp_vec_segments<F>(S.P, row, &S.vs, a.msg_out, 0);
             __syncthreads();
             const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (tid < F) {
@@ -560,26 +557,43 @@ struct BwdSmem {
     unsigned char w1t[F * kKP * 2];     // B[n][k] = W1[k][n]
     unsigned char w2t[F * F * 2];       // B[n][k] = W2[k][n]
     unsigned char w2n[F * F * 2];       // B[n][k] = W2[n][k]
-    unsigned char a1[kT * kKP * 2];     // basis
-    unsigned char a4[kT * kKP * 2];     // basis derivative
+    unsigned char a14[2 * kT * kKP * 2];  // basis | basis derivative; then the tile's vector and scalar slots
     unsigned char a2[kT * F * 2];       // SiLU hidden, then g
     float b1[F], b2[F];
-    float P[kT * F];                    // mbar_j rows, then ubar messages (swizzled rows)
-    float U[kT * F];                    // u_j rows (swizzled)
-    int row[kT];
-    ScalSlots<NV> ss;                   // the vector slots live in a1 (free once D1 is complete)
+    // per pair F * 4 bytes: the gathered BF16 row of atom j (per 16 features
+    // 16 u_j then 16 mbar_j), overwritten in place by the FP32 ubar message
+    // (swizzled 16-byte chunks)
+    float G[kT * F];
     uint64_t mbar;
     uint32_t taddr;
 };
+
+template <int F>
+__host__ __device__ constexpr int scal_slot_offset() { return (int)((sizeof(VecSlots<F>) + 15) / 16 * 16); }
+
+// Eight BF16 values of a 16-byte chunk as FP32 (exact).
+__device__ __forceinline__ void unpack_bf16x8(uint4 w, float* v) {
+    const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(x[k] << 16);
+        v[2 * k + 1] = __uint_as_float(x[k] & 0xffff0000u);
+    }
+}
 
 // NV = 9: forces and the per-atom virial; NV = 3: forces only.
 template <int F, int NV>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdSmem<F, NV>& S = *reinterpret_cast<BwdSmem<F, NV>*>(smraw);
-    static_assert(sizeof(VecSlots<F>) <= sizeof(S.a1), "vector slots must fit the basis tile");
-    VecSlots<F>* vs = reinterpret_cast<VecSlots<F>*>(S.a1);
-    constexpr int TCOLS = 4 * F;   // D1 | D4 | D2 | D3
+    static_assert(scal_slot_offset<F>() + sizeof(ScalSlots<NV>) <= sizeof(S.a14), "slots must fit the basis tiles");
+    // the slots are written once the tile's first MMA (the only reader of the basis tiles) has completed
+    VecSlots<F>* vs = reinterpret_cast<VecSlots<F>*>(S.a14);
+    ScalSlots<NV>* ss = reinterpret_cast<ScalSlots<NV>*>(S.a14 + scal_slot_offset<F>());
+    unsigned char* const a1 = S.a14;
+    unsigned char* const a4 = S.a14 + kT * kKP * 2;
+    // tensor memory: D1 (then p) | D4, then D2, then D3 (each read before the next MMA overwrites it)
+    constexpr int TCOLS = 2 * F;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
     const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
@@ -609,9 +623,9 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     fence_after_sync();
     const uint32_t tmem = S.taddr;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    const uint32_t tD1 = tmem, tD4 = tmem + F, tD2 = tmem + 2 * F, tD3 = tmem + 3 * F;
+    const uint32_t tD1 = tmem, tD4 = tmem + F, tD2 = tmem + F, tD3 = tmem + F;
     const uint32_t idesc = idesc_bf16_f32(128, F);
-    const uint32_t sA1 = smem_u32(S.a1), sA4 = smem_u32(S.a4), sA2 = smem_u32(S.a2);
+    const uint32_t sA1 = smem_u32(a1), sA4 = smem_u32(a4), sA2 = smem_u32(S.a2);
     const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t), sW2N = smem_u32(S.w2n);
     uint32_t phase = 0;
     bool ok = true;
@@ -633,9 +647,8 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             const int j = valid ? ex.j : 0;
             const int row = valid ? ex.i : -1;
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
-            // g needs mbar_j and u_j, the ubar message mbar_j: start the warp's row copies now
-            gather_rows<F>(S.P, a.mbar, j);
-            gather_rows<F>(S.U, a.u, j);
+            // g needs u_j and mbar_j, the ubar message mbar_j: start the warp's row copies now
+            gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j);
             cp_async_commit();
             float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
             {
@@ -652,11 +665,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
 #pragma unroll
                     for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
                 }
-                S.row[tid] = row;
-                st_row8(S.a1, tid, 0, kKP, eb);
-                st_row8(S.a1, tid, 8, kKP, eb + 8);
-                st_row8(S.a4, tid, 0, kKP, db);
-                st_row8(S.a4, tid, 8, kKP, db + 8);
+                st_row8(a1, tid, 0, kKP, eb);
+                st_row8(a1, tid, 8, kKP, eb + 8);
+                st_row8(a4, tid, 0, kKP, db);
+                st_row8(a4, tid, 8, kKP, db + 8);
             }
             fence_proxy_async();
             fence_before_sync();
@@ -704,7 +716,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
             phase ^= 1;
             fence_after_sync();
-            cp_async_wait();                               // the warp's mbar_j and u_j rows are in P, U
+            cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
             __syncwarp();
             float gphi = 0.f;
             {
@@ -720,24 +732,34 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                         ui16[qq] = __ldg(reinterpret_cast<const float4*>(ui + c + 4 * qq));
                         mi16[qq] = __ldg(reinterpret_cast<const float4*>(mi + c + 4 * qq));
                     }
-                    float v[16], g[16];
+                    float v[16], g[16], uj[16], mj[16];
                     tmem_ld16(tD2 + lane_base + c, v);
+                    {
+                        // the four 16-byte chunks of these 16 features: u_j (2), mbar_j (2)
+                        uint4 w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            w[k] = *reinterpret_cast<const uint4*>(S.G + prow<F>(tid, c + 4 * k));
+                        unpack_bf16x8(w[0], uj);
+                        unpack_bf16x8(w[1], uj + 8);
+                        unpack_bf16x8(w[2], mj);
+                        unpack_bf16x8(w[3], mj + 8);
+                    }
 #pragma unroll
                     for (int q = 0; q < 16; q += 4) {
-                        const int o = prow<F>(tid, c + q);
-                        float4 u4 = *reinterpret_cast<const float4*>(S.U + o);
-                        float4 m4 = *reinterpret_cast<const float4*>(S.P + o);
                         const float4 ui4 = ui16[q / 4];
                         const float4 mi4 = mi16[q / 4];
                         float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
                         float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
-                        g[q] = mi4.x * u4.x + m4.x * ui4.x;
-                        g[q + 1] = mi4.y * u4.y + m4.y * ui4.y;
-                        g[q + 2] = mi4.z * u4.z + m4.z * ui4.z;
-                        g[q + 3] = mi4.w * u4.w + m4.w * ui4.w;
+                        g[q] = mi4.x * uj[q] + mj[q] * ui4.x;
+                        g[q + 1] = mi4.y * uj[q + 1] + mj[q + 1] * ui4.y;
+                        g[q + 2] = mi4.z * uj[q + 2] + mj[q + 2] * ui4.z;
+                        g[q + 3] = mi4.w * uj[q + 3] + mj[q + 3] * ui4.w;
                         gphi += g[q] * ph0 + g[q + 1] * ph1 + g[q + 2] * ph2 + g[q + 3] * ph3;
-                        *reinterpret_cast<float4*>(S.P + o) =
-                            make_float4(fc * ph0 * m4.x, fc * ph1 * m4.y, fc * ph2 * m4.z, fc * ph3 * m4.w);
+                        // the message replaces the chunks just read (this thread's row only)
+                        *reinterpret_cast<float4*>(S.G + prow<F>(tid, c + q)) =
+                            make_float4(fc * ph0 * mj[q], fc * ph1 * mj[q + 1], fc * ph2 * mj[q + 2],
+                                        fc * ph3 * mj[q + 3]);
                     }
                     st_row8(S.a2, tid, c, F, g);
                     st_row8(S.a2, tid, c + 8, F, g + 8);
@@ -780,11 +802,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
                     val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
                 }
-                warp_scal_segments<NV>(val, row, &S.ss);
+                warp_scal_segments<NV>(val, row, ss);
             }
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            if (need_ubar) warp_vec_segments<F>(S.P, S.row, vs, a.msg_out, 0);
+            if (need_ubar) warp_vec_segments<F>(S.G, row, vs, a.msg_out, 0);
             __syncthreads();
             const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (need_ubar && tid < F) {
@@ -793,12 +815,12 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 float* force = a.force;
                 float* vir6 = a.vir6;
                 const int n = a.n_atoms, acc = a.accumulate;
-                merge_tile_scal<NV, F>(&S.ss, tid - F, tc, [=](int r, int c, float v) {
+                merge_tile_scal<NV, F>(ss, tid - F, tc, [=](int r, int c, float v) {
                     float* dst = c < 3 ? force + (size_t)c * n + r : vir6 + (size_t)r * 6 + c - 3;
                     *dst = acc ? *dst + v : v;
                 });
             }
-            __syncthreads();                               // slots read before the next basis overwrites a1
+            __syncthreads();                               // slots read before the next basis overwrites them
         }
     }
     fence_before_sync();
@@ -839,7 +861,7 @@ void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
 template <int F, int NV>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     static int cap = 0, sms = 0;
-    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 4 * F, cap, sms, a, K, status, s);
+    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 2 * F, cap, sms, a, K, status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
                                                                  a.force, a.vir6, a.accumulate);
@@ -875,7 +897,7 @@ int bf16_max_ctas_per_sm(int F, bool bwd) {
         cudaGetLastError();
         smem_sm = 233472;
     }
-    return std::max(1, std::min(smem_sm / (smem + 1024), 512 / ((bwd ? 4 : 2) * F)));
+    return std::max(1, std::min(smem_sm / (smem + 1024), 512 / (2 * F)));
 }
 
 size_t bf16_weight_tile_bytes(int F) {

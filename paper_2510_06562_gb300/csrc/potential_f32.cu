@@ -14,6 +14,8 @@
 // fc sum_k [(g W2^T)_k SiLU'(a_k)] (e' W1)_k, and F_i = sum_j dE/dd_ij rhat_ij
 // over row i; the adjoint of u is ubar_i = sum_j w_ij * mbar_j, again a sum
 // over row i. Both are gathers over the atom's own row.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace dmts {
@@ -105,6 +107,9 @@ __global__ void k_embed(PotArgs a) {
     for (int k = 0; k < F; ++k) acc += __ldg(A + k) * __ldg(W + k * F + f);
     a.h[(size_t)i * F + f] = __ldg(A + f);
     a.u_next[(size_t)i * F + f] = acc;
+    if (a.um_u_out)
+        *reinterpret_cast<__nv_bfloat16*>(a.um_u_out + (size_t)i * F * 4 + (f >> 4) * 64 + (f & 15) * 2) =
+            __float2bfloat16_rn(acc);
 }
 
 // ------------------------------------------------------------ forward edge pass
