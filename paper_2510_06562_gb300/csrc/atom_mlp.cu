@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     float* W0 = Y + T::A * T::XS;                    // [F][WS]
     float* W1 = W0 + F * T::WS;                      // [F][WS]
     __shared__ float sE[T::A];
+    __shared__ float sBias[4][F];                    // c1, c2 of this layer; d1, R2 (last layer)
     const int l = p.layer;
     const int base = blockIdx.x * T::A;
     const int tid = threadIdx.x, fg = tid % T::FG, ag = tid / T::FG;
@@ -176,12 +177,25 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     stage_w<F>(W0, P + p.off.U1[l]);                                     // group: message rows + U1
     stage_w<F>(W1, P + p.off.U2[l]);                                     // group: U2
     load_rows4<F>(h, p.h_in, base, p.n_atoms, a0, f0);
+    // the small per-layer vectors and the per-atom energy constants, loaded while the copies run
+    for (int t = tid; t < F; t += T::NT) {
+        sBias[0][t] = __ldg(P + p.off.c1[l] + t);
+        sBias[1][t] = __ldg(P + p.off.c2[l] + t);
+        if (last) {
+            sBias[2][t] = __ldg(P + p.off.d1 + t);
+            sBias[3][t] = __ldg(P + p.off.R2 + t);
+        }
+    }
+    double e_const = 0.0;                            // d2 + e0[Z_i] + E_rep,i of atom base + tid
+    if (last && tid < T::A && base + tid < p.n_atoms)
+        e_const = (double)__ldg(P + p.off.d2) + (double)__ldg(P + p.off.e0 + p.species[base + tid]) +
+                  (double)p.erep[base + tid];
     cp_wait<1>();
     __syncthreads();
     gemm4x4<F>(X, W0, a0, f0, z);                                        // z = m U1 + c1
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const float c1 = __ldg(P + p.off.c1[l] + f0 + f);
+        const float c1 = sBias[0][f0 + f];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             z[a][f] += c1;
@@ -197,7 +211,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     gemm4x4<F>(Y, W1, a0, f0, v);                                        // h += SiLU(z) U2 + c2
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const float c2 = __ldg(P + p.off.c2[l] + f0 + f);
+        const float c2 = sBias[1][f0 + f];
 #pragma unroll
         for (int a = 0; a < 4; ++a) h[a][f] += v[a][f] + c2;
     }
@@ -219,7 +233,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     float e_part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const float d1 = __ldg(P + p.off.d1 + f0 + f), r2 = __ldg(P + p.off.R2 + f0 + f);
+        const float d1 = sBias[2][f0 + f], r2 = sBias[3][f0 + f];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const float q = v[a][f] + d1;
@@ -239,12 +253,8 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     put_rows<F>(Y, a0, f0, v);
     __syncthreads();                                                     // W0 read, Y and sE complete
     stage_w<F>(W0, wt_of(p, F, l, 2));                                   // U2^T
-    for (int a = tid; a < T::A; a += T::NT) {
-        const int i = base + a;
-        if (i < p.n_atoms)
-            p.Ei[i] = (double)sE[a] + (double)__ldg(P + p.off.d2) + (double)__ldg(P + p.off.e0 + p.species[i]) +
-                      (double)p.erep[i];
-    }
+    static_assert(T::NT >= T::A, "one thread per atom of the tile");
+    if (tid < T::A && base + tid < p.n_atoms) p.Ei[base + tid] = (double)sE[tid] + e_const;
     cp_wait<1>();
     __syncthreads();
     gemm4x4<F>(Y, W1, a0, f0, v);                                        // gh = gq R1^T

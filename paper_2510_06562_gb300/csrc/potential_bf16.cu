@@ -146,14 +146,14 @@ __device__ void stage_b(unsigned char* tile, const float* __restrict__ W, int N,
 
 // ------------------------------------------------------------ segmented sums
 // Rows (receiving atoms) are contiguous runs of edges. Vector sums (F values
-// per edge, in sP[e][f]): every warp sums its 32 edges sequentially, one lane
-// per feature; rows that start and end inside the warp are complete and are
+// per edge, in sP[e][f]): every warp sums its 32 edges sequentially, each lane
+// F / 32 adjacent features; rows that start and end inside the warp are complete and are
 // written to global memory directly, the warp's first and last row segments
 // go to two slots. Scalar sums (NV values per edge): a segmented shuffle scan
 // per warp, every row segment to a slot. The slots are then merged in edge
 // order by one thread per value, carrying the open row across tiles.
 template <int F>
-struct VecSlots {
+struct alignas(16) VecSlots {
     float v[4][2][F];
     int row[4][2];
 };
@@ -161,9 +161,11 @@ struct VecSlots {
 template <int F>
 __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, int myrow,
                                                   VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0) {
-    constexpr int NF = F / 32;
+    constexpr int VW = F / 32;                     // consecutive features per lane (one 4- or 8-byte access)
+    static_assert(VW == 1 || VW == 2, "F must be 32 or 64");
     constexpr int B = 8;                           // edges whose values are loaded together
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f0 = VW * lane;
     // row of every edge of the warp (myrow: this lane's), segment starts and ends as warp-uniform bit masks
     const int prev = __shfl_up_sync(0xffffffffu, myrow, 1);
     const int next = __shfl_down_sync(0xffffffffu, myrow, 1);
@@ -177,39 +179,47 @@ __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, 
         vs->row[w][1] = -1;
     }
     const float* base = sP + (32 * w) * F;
-    float acc[NF];
+    auto put = [&](float* dst, const float* v) {
+        if constexpr (VW == 2) *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+        else *dst = v[0];
+    };
+    float acc[VW];
 #pragma unroll
-    for (int c = 0; c < NF; ++c) acc[c] = 0.f;
+    for (int c = 0; c < VW; ++c) acc[c] = 0.f;
 #pragma unroll
     for (int e0 = 0; e0 < 32; e0 += B) {
         if (e0 >= n_valid) break;
         // issue the batch's loads before any store of the batch
-        float v[B][NF];
+        float v[B][VW];
 #pragma unroll
-        for (int k = 0; k < B; ++k)
-#pragma unroll
-            for (int c = 0; c < NF; ++c) v[k][c] = base[prow<F>(e0 + k, lane + 32 * c)];
+        for (int k = 0; k < B; ++k) {
+            const float* src = base + prow<F>(e0 + k, f0);
+            if constexpr (VW == 2) {
+                const float2 x = *reinterpret_cast<const float2*>(src);
+                v[k][0] = x.x;
+                v[k][1] = x.y;
+            } else {
+                v[k][0] = *src;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int e = e0 + k;
             if (e < n_valid) {
                 const bool st = (starts >> e) & 1u;
 #pragma unroll
-                for (int c = 0; c < NF; ++c) acc[c] = st ? v[k][c] : acc[c] + v[k][c];
+                for (int c = 0; c < VW; ++c) acc[c] = st ? v[k][c] : acc[c] + v[k][c];
                 if ((ends >> e) & 1u) {
                     const int r = __shfl_sync(0xffffffffu, myrow, e);
                     const bool first = (starts & ((2u << e) - 1u)) == (starts & 1u) && (starts & 1u);  // segment 0
                     if (first) {
-#pragma unroll
-                        for (int c = 0; c < NF; ++c) vs->v[w][0][lane + 32 * c] = acc[c];
+                        put(&vs->v[w][0][f0], acc);
                         if (lane == 0) vs->row[w][0] = r;
                     } else if (e == last_end) {
-#pragma unroll
-                        for (int c = 0; c < NF; ++c) vs->v[w][1][lane + 32 * c] = acc[c];
+                        put(&vs->v[w][1][f0], acc);
                         if (lane == 0) vs->row[w][1] = r;
                     } else {
-#pragma unroll
-                        for (int c = 0; c < NF; ++c) out[(size_t)(a0 + r) * F + lane + 32 * c] = acc[c];
+                        put(out + (size_t)(a0 + r) * F + f0, acc);
                     }
                 }
             }
