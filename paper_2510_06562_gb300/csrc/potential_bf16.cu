@@ -37,10 +37,19 @@ __device__ __forceinline__ float sigmoid_fast(float x) {
     return fmaf(0.5f, t, 0.5f);
 }
 
-// Asynchronous 16-byte global -> shared copies (L1-cached); the issuing
-// thread waits for its own copies with cp_async_wait().
+// Asynchronous 16-byte global -> shared copies; the issuing thread waits for
+// its own copies with cp_async_wait(). They bypass L1 (a gathered row is
+// reused by other tiles much later, if at all), which leaves the few KB of
+// L1 beside the shared-memory carve-out to the receiving atoms' rows.
 __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst_smem)), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+
+// Pull the 128-byte lines of an F-float row into L1 ahead of its use.
+template <int F>
+__device__ __forceinline__ void prefetch_row_l1(const float* row) {
+#pragma unroll
+    for (int k = 0; k < F * 4; k += 128) asm volatile("prefetch.global.L1 [%0];" :: "l"(row + k / 4));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -660,6 +669,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             // g needs u_j and mbar_j, the ubar message mbar_j: start the warp's row copies now
             gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j);
             cp_async_commit();
+            if (valid) {                                   // the receiving atom's rows, read in the second epilogue
+                prefetch_row_l1<F>(a.u + (size_t)row * F);
+                prefetch_row_l1<F>(a.mbar + (size_t)row * F);
+            }
             float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
             {
                 float eb[kKP], db[kKP];
@@ -705,7 +718,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     const float x = v[q] + S.b1[c + q];
                     const float sg = sigmoid_fast(x);
                     v[q] = x * sg;
-                    tv[q] *= sg * (1.f + x * (1.f - sg));
+                    tv[q] *= fmaf(v[q], 1.f - sg, sg);     // SiLU'(x) = sg + x sg (1 - sg)
                 }
                 st_row8(S.a2, tid, c, F, v);
                 st_row8(S.a2, tid, c + 8, F, v + 8);
