@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmts.so")
-SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu", "atom_mlp.cu", "distill_f32.cu"]
+SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu", "atom_mlp.cu", "atom_tc.cu", "distill_f32.cu"]
 HEADERS = ["internal.cuh", "umma.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

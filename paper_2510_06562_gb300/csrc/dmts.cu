@@ -92,6 +92,7 @@ struct Model {
     unsigned char* um[kMaxLayers] = {};   // BF16 u^l | mbar^l rows for the tensor-core backward
     float* msg = nullptr;              // [N][F] per-atom sums between edge and atom kernels
     unsigned char* wt = nullptr;       // BF16 filter-weight operand tiles, per layer
+    unsigned char* at = nullptr;       // BF16 hi/lo tiles of the per-atom MLP matrices (tensor-core path)
     size_t wt_layer_bytes = 0;
     double *Ei = nullptr, *E = nullptr, *W = nullptr;
     int apc_fwd = 16, apc_bwd = 16;    // FP32 kernels: atoms per CTA
@@ -146,6 +147,7 @@ struct dmts_ctx {
     cudaStream_t s_big = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool concurrent = true;
+    bool atom_tc = true;                   // BF16 mode: per-atom MLPs on the tensor cores
     long long body_launches = 0, fallback_seen = 0;
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
@@ -237,7 +239,7 @@ void free_model(Model& m) {
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
     for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); dfree(m.um[l]); }
     dfree(m.mbar[0]); dfree(m.mbar[1]);
-    dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt);
+    dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt); dfree(m.at);
     m = Model();
 }
 
@@ -275,6 +277,46 @@ std::vector<uint16_t> build_weight_tiles(const Model& m, const std::vector<float
     return t;
 }
 
+float bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float x;
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+// Operand tiles of the per-atom MLP matrices for the tensor-core kernels
+// (atom_tc.cu): per layer W_in, U1, U2 as B operands of X W (B[n][k] =
+// W[k][n]) and of X W^T (B[n][k] = W[n][k]), then R1 both ways; each slot a
+// high BF16 tile then the BF16 rounding of the remainder, K-major.
+std::vector<uint16_t> build_atom_tiles(const Model& m, const std::vector<float>& pf) {
+    const int F = m.F;
+    const size_t FF = (size_t)F * F;
+    std::vector<uint16_t> t((6 * (size_t)m.L + 2) * 2 * FF, 0);
+    auto put = [&](size_t slot, int off, bool transpose) {
+        uint16_t* hi = t.data() + slot * 2 * FF;
+        uint16_t* lo = hi + FF;
+        for (int n = 0; n < F; ++n)
+            for (int k = 0; k < F; ++k) {
+                const float w = transpose ? pf[off + (size_t)n * F + k] : pf[off + (size_t)k * F + n];
+                const uint16_t h = bf16_bits(w);
+                const size_t o = umma::tile_offset(n, k, F) / 2;
+                hi[o] = h;
+                lo[o] = bf16_bits(w - bf16_value(h));
+            }
+    };
+    for (int l = 0; l < m.L; ++l) {
+        put(6 * (size_t)l + 0, m.off.W_in[l], false);
+        put(6 * (size_t)l + 1, m.off.U1[l], false);
+        put(6 * (size_t)l + 2, m.off.U2[l], false);
+        put(6 * (size_t)l + 3, m.off.W_in[l], true);
+        put(6 * (size_t)l + 4, m.off.U1[l], true);
+        put(6 * (size_t)l + 5, m.off.U2[l], true);
+    }
+    put(6 * (size_t)m.L, m.off.R1, false);
+    put(6 * (size_t)m.L + 1, m.off.R1, true);
+    return t;
+}
+
 // Transposed copies of the per-atom MLP matrices: W_in^T, U1^T, U2^T of each
 // layer, then R1^T (each F x F, row-major).
 std::vector<float> build_transposed(const Model& m, const std::vector<float>& pf) {
@@ -302,6 +344,8 @@ int upload_params(dmts_ctx* c, Model& m, const double* params) {
     CUDA_TRY(cudaMemcpyAsync(m.wt, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice, c->stream));
     std::vector<float> tr = build_transposed(m, pf);
     CUDA_TRY(cudaMemcpyAsync(m.PT, tr.data(), tr.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    std::vector<uint16_t> at = build_atom_tiles(m, pf);
+    CUDA_TRY(cudaMemcpyAsync(m.at, at.data(), at.size() * 2, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return DMTS_OK;
 }
@@ -321,6 +365,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     m.wt_layer_bytes = bf16_weight_tile_bytes(m.F);
     CUDA_TRY(dalloc(&m.wt, m.wt_layer_bytes * m.L));
     CUDA_TRY(dalloc(&m.PT, (3 * (size_t)m.L + 1) * m.F * m.F));
+    CUDA_TRY(dalloc(&m.at, atom_tile_bytes(m.F, m.L)));
     int rc = upload_params(c, m, d->params);
     if (rc) return rc;
     // cells (periodic) and capacity estimates; with a skin the cells and the
@@ -451,6 +496,7 @@ PotArgs pot_args(dmts_ctx* c, Model& m) {
     a.wt = m.wt;
     a.wt_layer_bytes = m.wt_layer_bytes;
     a.PT = m.PT;
+    a.at = m.at;
     a.carry = m.carry;
     a.carry_w = m.F + 16;
     a.h = m.h;
@@ -582,6 +628,24 @@ void launch_edge_fwd(dmts_ctx* c, Model& m, const PotArgs& a) {
     else launch_edge_fwd_f32(a, m.F, m.K, c->stream);
 }
 
+// Per-atom MLPs: tensor cores in the BF16 precision mode for F >= 64
+// (unless the option atom_tensor_cores is 0), FP32 SIMT otherwise. At F = 32
+// the SIMT kernels measured faster (16 vs 17 us for 12,288 atoms): the
+// tensor-core kernels' fixed cost is not repaid by their half-size products.
+bool atom_on_tc(const dmts_ctx* c, const Model& m) {
+    return m.precision == DMTS_BF16_MLP && c->atom_tc && m.F >= 64;
+}
+
+void launch_atom_fwd_m(dmts_ctx* c, Model& m, const PotArgs& a) {
+    if (atom_on_tc(c, m)) launch_atom_fwd_tc(a, m.F, m.msg, c->d_flags + kFlagTimeout, c->stream);
+    else launch_atom_fwd(a, m.F, m.msg, c->stream);
+}
+
+void launch_atom_bwd_m(dmts_ctx* c, Model& m, const PotArgs& a) {
+    if (atom_on_tc(c, m)) launch_atom_bwd_tc(a, m.F, m.msg, c->d_flags + kFlagTimeout, c->stream);
+    else launch_atom_bwd(a, m.F, m.msg, c->stream);
+}
+
 void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
     if (m.precision == DMTS_BF16_MLP) launch_edge_bwd_bf16(a, m.F, m.K, c->d_flags + kFlagTimeout, c->stream);
     else launch_edge_bwd_f32(a, m.F, m.K, c->stream);
@@ -631,12 +695,12 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     for (int l = 0; l < m.L; ++l) {
         PotArgs f = fwd_args(a, m, l);
         launch_edge_fwd(c, m, f);
-        launch_atom_fwd(f, m.F, m.msg, s);
+        launch_atom_fwd_m(c, m, f);
     }
     for (int l = m.L - 1; l >= 0; --l) {
         PotArgs b = bwd_args(a, m, l);
         launch_edge_bwd(c, m, b);
-        if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
+        if (l > 0) launch_atom_bwd_m(c, m, b);
     }
     if (energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
 }
@@ -1063,6 +1127,7 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CREATE_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     c->concurrent = json_number(options, "concurrent_models", 1.0) != 0.0;
+    c->atom_tc = json_number(options, "atom_tensor_cores", 1.0) != 0.0;
     CREATE_TRY(dalloc(&c->d_mon, 1));
     CREATE_TRY(cudaMemset(c->d_mon, 0, sizeof(ForceMonitor)));
     if (c->fb_threshold > 0.0) {
@@ -1428,7 +1493,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             launch_edge_fwd(c, m, f);
             end(2 + l);
             begin(2 + L + l);
-            launch_atom_fwd(f, m.F, m.msg, s);
+            launch_atom_fwd_m(c, m, f);
             end(2 + L + l);
         }
         for (int l = L - 1; l >= 0; --l) {
@@ -1437,7 +1502,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             launch_edge_bwd(c, m, b);
             end(2 + 2 * L + l);
             begin(2 + 3 * L + l);
-            if (l > 0) launch_atom_bwd(b, m.F, m.msg, s);
+            if (l > 0) launch_atom_bwd_m(c, m, b);
             end(2 + 3 * L + l);
         }
         begin(2 + 4 * L);

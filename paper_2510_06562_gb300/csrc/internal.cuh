@@ -189,6 +189,7 @@ struct PotArgs {
     const unsigned char* um; // layer l's rows (backward edge pass)
     unsigned char* um_u_out; // u half, written beside u_next (or u^0 by the embedding); may be null
     unsigned char* um_mbar_out;  // mbar half, written beside mbar_out; may be null
+    const unsigned char* at; // tensor-core per-atom MLPs: BF16 hi/lo weight tiles (atom_tc.cu)
     double* Ei;              // [N]
     float* force;            // SoA [3][N]
     float* vir6;             // [N][6]
@@ -245,6 +246,10 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
 // atom_mlp.cu: per-atom MLPs after the edge passes
 void launch_atom_fwd(const PotArgs& p, int F, const float* msg, cudaStream_t s);
 void launch_atom_bwd(const PotArgs& p, int F, const float* ubar, cudaStream_t s);
+// atom_tc.cu: the same passes on the tensor cores (BF16 precision mode)
+void launch_atom_fwd_tc(const PotArgs& p, int F, const float* msg, int* status, cudaStream_t s);
+void launch_atom_bwd_tc(const PotArgs& p, int F, const float* ubar, int* status, cudaStream_t s);
+size_t atom_tile_bytes(int F, int L);
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
                        int stride, cudaStream_t s);
 void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, double* out,
