@@ -98,6 +98,7 @@ struct Model {
     int apc_fwd = 16, apc_bwd = 16;    // FP32 kernels: atoms per CTA
     int cps_fwd = 0, cps_bwd = 0;      // tensor-core kernels: persistent CTAs per SM (0: as many as fit)
     float* carry = nullptr;            // tensor-core path: per-tile partial sums of split rows
+    SumScratch esum{};                 // scratch of the per-system energy sum
 };
 
 }  // namespace
@@ -147,6 +148,7 @@ struct dmts_ctx {
     cudaStream_t s_big = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool concurrent = true;
+    SumScratch kesum{};                    // scratch of the per-system kinetic-energy sum
     bool atom_tc = true;                   // BF16 mode: per-atom MLPs on the tensor cores
     long long body_launches = 0, fallback_seen = 0;
     double cap_factor = 1.5;
@@ -238,7 +240,7 @@ void free_model(Model& m) {
     dfree(m.nbr_cnt); dfree(m.row_ptr); dfree(m.vl_cnt);
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
     for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); dfree(m.um[l]); }
-    dfree(m.mbar[0]); dfree(m.mbar[1]);
+    dfree(m.mbar[0]); dfree(m.mbar[1]); dfree(m.esum.part); dfree(m.esum.ctr);
     dfree(m.Ei); dfree(m.E); dfree(m.W); dfree(m.erep); dfree(m.msg); dfree(m.wt); dfree(m.at);
     m = Model();
 }
@@ -427,6 +429,9 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     CUDA_TRY(dalloc(&m.Ei, N));
     CUDA_TRY(dalloc(&m.erep, N));
     CUDA_TRY(dalloc(&m.E, c->n_sys));
+    CUDA_TRY(dalloc(&m.esum.part, (size_t)kSumMaxSplit * kSumChunks));
+    CUDA_TRY(dalloc(&m.esum.ctr, kSumMaxSplit));
+    CUDA_TRY(cudaMemset(m.esum.ctr, 0, sizeof(unsigned int) * kSumMaxSplit));
     CUDA_TRY(dalloc(&m.W, (size_t)9 * c->n_sys));
     const bool tc = m.precision == DMTS_BF16_MLP;
     // FP32: atoms per CTA (bounded by shared memory); BF16: atoms per chunk of
@@ -702,7 +707,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
         launch_edge_bwd(c, m, b);
         if (l > 0) launch_atom_bwd_m(c, m, b);
     }
-    if (energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
+    if (energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, m.esum, s);
 }
 
 int sync_check(dmts_ctx* c) {
@@ -876,7 +881,7 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
         launch_vv_post(c->N, 0.5 * dt * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
                        c->d_flags, c->d_rng, s);
     }
-    launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, s);
+    launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, c->kesum, s);
     launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -999,7 +1004,7 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
-    dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng);
+    dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng); dfree(c->kesum.part); dfree(c->kesum.ctr);
     dfree(c->d_mon); dfree(c->d_sx); dfree(c->d_sv); dfree(c->d_sf);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->s_big) cudaStreamDestroy(c->s_big);
@@ -1121,6 +1126,9 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(dalloc(&c->d_bfs, (size_t)3 * N));
     CREATE_TRY(dalloc(&c->d_bfb, (size_t)3 * N));
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
+    CREATE_TRY(dalloc(&c->kesum.part, (size_t)kSumMaxSplit * kSumChunks));
+    CREATE_TRY(dalloc(&c->kesum.ctr, kSumMaxSplit));
+    CREATE_TRY(cudaMemset(c->kesum.ctr, 0, sizeof(unsigned int) * kSumMaxSplit));
     CREATE_TRY(dalloc(&c->d_rng, 2));
     CREATE_TRY(cudaMemset(c->d_rng, 0, 2 * sizeof(unsigned long long)));
     CREATE_TRY(cudaStreamCreateWithFlags(&c->s_big, cudaStreamNonBlocking));
@@ -1506,7 +1514,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             end(2 + 3 * L + l);
         }
         begin(2 + 4 * L);
-        launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, s);
+        launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, m.esum, s);
         end(2 + 4 * L);
         CUDA_TRY(cudaEventSynchronize(ev[2 * n_st - 1]));
         for (int q = 0; q < n_st; ++q) {

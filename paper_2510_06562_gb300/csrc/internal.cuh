@@ -250,8 +250,18 @@ void launch_atom_bwd(const PotArgs& p, int F, const float* ubar, cudaStream_t s)
 void launch_atom_fwd_tc(const PotArgs& p, int F, const float* msg, int* status, cudaStream_t s);
 void launch_atom_bwd_tc(const PotArgs& p, int F, const float* ubar, int* status, cudaStream_t s);
 size_t atom_tile_bytes(int F, int L);
+// Per-system FP64 sums (deterministic). With scratch (part: kSumMaxSplit x
+// kSumChunks doubles, ctr: kSumMaxSplit counters, zero on entry and exit) a
+// few large systems are split over many CTAs; calls that may run at the same
+// time need separate scratch.
+constexpr int kSumChunks = 48;
+constexpr int kSumMaxSplit = 8;
+struct SumScratch {
+    double* part;
+    unsigned int* ctr;
+};
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
-                       int stride, cudaStream_t s);
+                       int stride, const SumScratch& sc, cudaStream_t s);
 void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, double* out,
                        cudaStream_t s);
 

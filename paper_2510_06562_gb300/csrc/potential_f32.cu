@@ -681,11 +681,58 @@ __global__ void __launch_bounds__(NT) k_system_sum(int n_sys, const int* __restr
     }
 }
 
+// A few large systems: each system's values in kSumChunks consecutive
+// chunks, one CTA per chunk (fixed-order partial sums); the CTA of a system
+// that finishes last adds the partials in chunk order and clears the
+// system's counter. The FP64 additions spread over many SMs.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_system_sum_split(const int* __restrict__ off, const double* __restrict__ v,
+                                                        double* __restrict__ out, int stride,
+                                                        double* __restrict__ part, unsigned int* __restrict__ ctr) {
+    __shared__ double wsum[NT / 32];
+    __shared__ bool last;
+    const int s = blockIdx.y, b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int begin = off[s], end = off[s + 1];
+    const int per = (end - begin + kSumChunks - 1) / kSumChunks;
+    const int lo = begin + b * per, hi = min(end, lo + per);
+    double acc = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += NT) acc += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsum[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < NT / 32; ++k) t += wsum[k];
+        part[(size_t)s * kSumChunks + b] = t;
+        __threadfence();
+        last = atomicAdd(&ctr[s], 1u) == (unsigned int)kSumChunks - 1u;
+    }
+    __syncthreads();
+    if (last && w == 0) {
+        __threadfence();
+        double u = 0.0;
+        for (int k = lane; k < kSumChunks; k += 32) u += __ldcg(part + (size_t)s * kSumChunks + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            out[(size_t)s * stride] = u;
+            ctr[s] = 0u;
+        }
+    }
+}
+
 void launch_system_sum(int n_sys, const int* atom_offset, const double* per_atom, double* out,
-                       int stride, cudaStream_t s) {
-    // one CTA per system: wide for a single large system, narrow for many molecules
-    if (n_sys <= 8) k_system_sum<1024><<<n_sys, 1024, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
-    else k_system_sum<64><<<n_sys, 64, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
+                       int stride, const SumScratch& sc, cudaStream_t s) {
+    if (n_sys <= kSumMaxSplit && sc.part) {
+        k_system_sum_split<256><<<dim3(kSumChunks, n_sys), 256, 0, s>>>(atom_offset, per_atom, out, stride, sc.part,
+                                                                         sc.ctr);
+    } else if (n_sys <= 8) {
+        // one CTA per system: wide for a single large system, narrow for many molecules
+        k_system_sum<1024><<<n_sys, 1024, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
+    } else {
+        k_system_sum<64><<<n_sys, 64, 0, s>>>(n_sys, atom_offset, per_atom, out, stride);
+    }
     count_launch();
 }
 
