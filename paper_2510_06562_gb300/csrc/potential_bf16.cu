@@ -141,18 +141,6 @@ __device__ __forceinline__ void basis16(float d, float inv_d, int K, float pi_ov
     dfc = -0.5f * pi_over_rc * s1;
 }
 
-// Stage a weight matrix as a K-major BF16 operand tile: B[n][k] = W[k][n]
-// (transpose = true, W row-major [Kc][N]) or B[n][k] = W[n][k] (transpose =
-// false, W row-major [N][Kc]); columns k >= Kreal are zero.
-__device__ void stage_b(unsigned char* tile, const float* __restrict__ W, int N, int Kc, int Kreal, bool transpose) {
-    for (int t = threadIdx.x; t < N * Kc; t += blockDim.x) {
-        int n = t / Kc, k = t % Kc;
-        float v = 0.f;
-        if (k < Kreal) v = transpose ? __ldg(W + (size_t)k * N + n) : __ldg(W + (size_t)n * Kc + k);
-        *reinterpret_cast<__nv_bfloat16*>(tile + tile_offset(n, k, Kc)) = __float2bfloat16_rn(v);
-    }
-}
-
 // ------------------------------------------------------------ segmented sums
 // Rows (receiving atoms) are contiguous runs of edges. Vector sums (F values
 // per edge, in sP[e][f]): every warp sums its 32 edges sequentially, each lane
@@ -172,17 +160,13 @@ __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, 
                                                   VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0) {
     constexpr int VW = F / 32;                     // consecutive features per lane (one 4- or 8-byte access)
     static_assert(VW == 1 || VW == 2, "F must be 32 or 64");
-    constexpr int B = 8;                           // edges whose values are loaded together
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f0 = VW * lane;
-    // row of every edge of the warp (myrow: this lane's), segment starts and ends as warp-uniform bit masks
+    // row of every edge of the warp (myrow: this lane's); segment starts as a warp-uniform bit mask
     const int prev = __shfl_up_sync(0xffffffffu, myrow, 1);
-    const int next = __shfl_down_sync(0xffffffffu, myrow, 1);
     const unsigned int valid = __ballot_sync(0xffffffffu, myrow >= 0);
     const unsigned int starts = __ballot_sync(0xffffffffu, myrow >= 0 && (lane == 0 || prev != myrow));
-    const unsigned int ends = __ballot_sync(0xffffffffu, myrow >= 0 && (lane == 31 || next != myrow));
     const int n_valid = __popc(valid);             // valid edges form a prefix
-    const int last_end = n_valid - 1;
     if (lane == 0) {
         vs->row[w][0] = -1;
         vs->row[w][1] = -1;
@@ -192,46 +176,35 @@ __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, 
         if constexpr (VW == 2) *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
         else *dst = v[0];
     };
-    float acc[VW];
+    // one pass per segment (warp-uniform bounds), its edges summed in order
+    unsigned int rem = starts;
+    for (int seg = 0; rem; ++seg) {
+        const int e0 = __ffs(rem) - 1;
+        rem &= rem - 1u;
+        const int e1 = rem ? __ffs(rem) - 1 : n_valid;
+        float acc[VW];
 #pragma unroll
-    for (int c = 0; c < VW; ++c) acc[c] = 0.f;
-#pragma unroll
-    for (int e0 = 0; e0 < 32; e0 += B) {
-        if (e0 >= n_valid) break;
-        // issue the batch's loads before any store of the batch
-        float v[B][VW];
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const float* src = base + prow<F>(e0 + k, f0);
+        for (int c = 0; c < VW; ++c) acc[c] = 0.f;
+#pragma unroll 4
+        for (int e = e0; e < e1; ++e) {
+            const float* src = base + prow<F>(e, f0);
             if constexpr (VW == 2) {
                 const float2 x = *reinterpret_cast<const float2*>(src);
-                v[k][0] = x.x;
-                v[k][1] = x.y;
+                acc[0] = e == e0 ? x.x : acc[0] + x.x;
+                acc[1] = e == e0 ? x.y : acc[1] + x.y;
             } else {
-                v[k][0] = *src;
+                acc[0] = e == e0 ? *src : acc[0] + *src;
             }
         }
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const int e = e0 + k;
-            if (e < n_valid) {
-                const bool st = (starts >> e) & 1u;
-#pragma unroll
-                for (int c = 0; c < VW; ++c) acc[c] = st ? v[k][c] : acc[c] + v[k][c];
-                if ((ends >> e) & 1u) {
-                    const int r = __shfl_sync(0xffffffffu, myrow, e);
-                    const bool first = (starts & ((2u << e) - 1u)) == (starts & 1u) && (starts & 1u);  // segment 0
-                    if (first) {
-                        put(&vs->v[w][0][f0], acc);
-                        if (lane == 0) vs->row[w][0] = r;
-                    } else if (e == last_end) {
-                        put(&vs->v[w][1][f0], acc);
-                        if (lane == 0) vs->row[w][1] = r;
-                    } else {
-                        put(out + (size_t)(a0 + r) * F + f0, acc);
-                    }
-                }
-            }
+        const int r = __shfl_sync(0xffffffffu, myrow, e0);
+        if (seg == 0) {                            // may continue a row of the previous warp
+            put(&vs->v[w][0][f0], acc);
+            if (lane == 0) vs->row[w][0] = r;
+        } else if (e1 == n_valid) {                // may continue into the next warp
+            put(&vs->v[w][1][f0], acc);
+            if (lane == 0) vs->row[w][1] = r;
+        } else {
+            put(out + (size_t)(a0 + r) * F + f0, acc);
         }
     }
 }
