@@ -41,10 +41,25 @@ def _rmse(a, b):
     return float(np.sqrt(np.mean((np.asarray(a) - np.asarray(b)) ** 2)))
 
 
+def _with_isolated_atoms():
+    """Molecules of 1 to 12 atoms (single-atom molecules have no pairs), and
+    in one larger molecule the last atom moved 30 A away: an atom without
+    neighbours inside a system that has pairs. Exercises the empty rows of
+    every pass (pair lists, tiles and their fix-up, per-atom MLPs)."""
+    s = I.make_vacuum_batch(40, 1, 12, seed=5)
+    x = s.x.copy()
+    sizes = np.diff(s.atom_offset)
+    k = int(np.nonzero(sizes >= 4)[0][0])
+    x[s.atom_offset[k + 1] - 1] += np.array([30.0, 0.0, 0.0])
+    return I.System(x=x, species=s.species, mass=s.mass, atom_offset=s.atom_offset, box=s.box,
+                    n_species=s.n_species, name="isolated40", bonds=s.bonds)
+
+
 SYSTEMS = {
     "water192": lambda: I.water_192(0),
     "water12288": lambda: I.water_12288(0),
     "vacuum64": lambda: I.make_vacuum_batch(64, 10, 60, seed=0),
+    "isolated40": _with_isolated_atoms,
 }
 
 
