@@ -1,13 +1,16 @@
 // BF16 tensor-core path of the potential (DMTS_BF16_MLP): the per-edge filter
 // MLP runs on the 5th-generation tensor cores (tcgen05.mma, BF16 operands in
-// shared memory, FP32 accumulators in tensor memory); edge geometry, message
-// sums, forces and the per-atom MLPs stay FP32.
+// shared or tensor memory, FP32 accumulators in tensor memory); edge
+// geometry, message sums and forces stay FP32.
 //
-// A persistent CTA of 4 warps takes chunks of atoms (whole CSR rows) in turn
-// and walks each chunk's edges in tiles of 128: one edge per thread and per
-// TMEM lane, so after each MMA a thread loads its own edge's feature row from
-// TMEM. The per-atom sums (messages, or the adjoint ubar, forces and virial)
-// go to global memory; the per-atom MLPs run in their own kernels.
+// The pair list is cut into fixed tiles of 128 pairs, taken round-robin by
+// persistent CTAs: one pair per thread and per TMEM lane, so after each MMA a
+// thread loads its own pair's feature row from TMEM. A CTA of 4 warps has one
+// tile in flight; the F = 64 backward pass has two, in two groups of 4 warps
+// sharing the weight tiles. Per-atom sums (messages, or the adjoint ubar,
+// forces and virial) of rows that start and end in a tile go to global memory
+// directly; rows split across tiles are summed in tile order by a fix-up
+// pass. The per-atom MLPs run in their own kernels.
 //   forward, per tile:  A1 = basis (128 x 16)           D1 = A1 W1        (hidden pre-activation)
 //                       A2 = SiLU(D1 + b1) (128 x F)    D2 = A2 W2        (filter, w = fc (D2 + b2))
 //   backward, per tile: D1 = A1 W1, D4 = A1' W1 (basis derivative), D2 = SiLU(D1 + b1) W2,
@@ -68,10 +71,10 @@ __device__ __forceinline__ int prow(int e, int f) {
 // each, so one warp instruction reads 32 / (F/4) whole rows: the loads are
 // coalesced per row instead of one scattered row per lane.
 template <int F>
-__device__ __forceinline__ void gather_rows(float* buf, const float* __restrict__ src, int j) {
+__device__ __forceinline__ void gather_rows(float* buf, const float* __restrict__ src, int j, int tid) {
     constexpr int TPR = F / 4;
     constexpr int RPI = 32 / TPR;
-    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
+    const int lane = tid & 31, w0 = tid & ~31;       // tid: the thread's edge within the tile
     const int sub = lane / TPR, ch = lane % TPR;
 #pragma unroll
     for (int rr = 0; rr < 32; rr += RPI) {
@@ -157,10 +160,11 @@ struct alignas(16) VecSlots {
 
 template <int F>
 __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, int myrow,
-                                                  VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0) {
+                                                  VecSlots<F>* __restrict__ vs, float* __restrict__ out, int a0,
+                                                  int tid) {
     constexpr int VW = F / 32;                     // consecutive features per lane (one 4- or 8-byte access)
     static_assert(VW == 1 || VW == 2, "F must be 32 or 64");
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = tid >> 5, lane = tid & 31;       // tid: the thread's edge within the tile
     const int f0 = VW * lane;
     // row of every edge of the warp (myrow: this lane's); segment starts as a warp-uniform bit mask
     const int prev = __shfl_up_sync(0xffffffffu, myrow, 1);
@@ -277,8 +281,8 @@ struct ScalSlots {
 };
 
 template <int NV>
-__device__ __forceinline__ void warp_scal_segments(float* val, int row, ScalSlots<NV>* ss) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void warp_scal_segments(float* val, int row, ScalSlots<NV>* ss, int tid) {
+    const int w = tid >> 5, lane = tid & 31;       // tid: the thread's edge within the tile
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         int ro = __shfl_up_sync(0xffffffffu, row, off);
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const int row = valid ? ex.i : -1;
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // the message needs u_j: start copying the warp's rows into P now
-            gather_rows<F>(S.P, a.u, j);
+            gather_rows<F>(S.P, a.u, j, tid);
             cp_async_commit();
             float fc = 0.f, rep = 0.f;
             {
@@ -522,10 +526,10 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                     }
                 }
             }
-            if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss);
+            if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss, tid);
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            warp_vec_segments<F>(S.P, row, &S.vs, a.msg_out, 0);
+            warp_vec_segments<F>(S.P, row, &S.vs, a.msg_out, 0, tid);
             __syncthreads();
             const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (tid < F) {
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             const int row = valid ? ex.i : -1;
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // g needs u_j and mbar_j, the ubar message mbar_j: start the warp's row copies now
-            gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j);
+            gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j, tid);
             cp_async_commit();
             if (valid) {                                   // the receiving atom's rows, read in the second epilogue
                 prefetch_row_l1<F>(a.u + (size_t)row * F);
@@ -798,11 +802,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
                     val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
                 }
-                warp_scal_segments<NV>(val, row, ss);
+                warp_scal_segments<NV>(val, row, ss, tid);
             }
             fence_before_sync();
             ok = __syncthreads_and(ok);
-            if (need_ubar) warp_vec_segments<F>(S.G, row, vs, a.msg_out, 0);
+            if (need_ubar) warp_vec_segments<F>(S.G, row, vs, a.msg_out, 0, tid);
             __syncthreads();
             const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (need_ubar && tid < F) {
@@ -825,30 +829,356 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     if (!ok && tid == 0) atomicOr(status, 1);
 }
 
-// Persistent launch: SMs x CTAs per SM, bounded by shared memory (1 KB
-// reserved per CTA), the 512 tensor-memory columns of an SM and the tuner's
-// choice; never more CTAs than tiles the pair capacity can hold.
+// ------------------------------------------------------------ backward, NG tiles per CTA
+// The same pass with NG tiles in flight per CTA: NG groups of 4 warps, each
+// with its own tile buffers, tensor-memory columns, mbarrier and named
+// barrier, sharing one copy of the weight tiles. The second and third MMAs
+// take their A operand from tensor memory, which keeps one tile in 2F
+// columns: per group X = [0, F) and Y = [F, 2F),
+//   MMA1:  D1 -> X, D4 -> Y
+//   epi 1: p = SiLU'(a)(e'W1) as BF16 -> X[0, F/2); SiLU(a) as BF16 -> Y[0, F/2)
+//   MMA2:  D2 = SiLU W2 as two N = F/2 halves -> X[F/2, F), Y[F/2, F)
+//   epi 2: g as BF16 -> Y[0, F/2)
+//   MMA3:  D3 = g W2^T as two halves -> X[F/2, F), Y[F/2, F)
+//   epi 3: sum_k D3_k p_k
+// (each epilogue writes a BF16 chunk only into columns it has already read).
+template <int F>
+struct alignas(16) BwdGroup {
+    unsigned char a14[2 * kT * kKP * 2];  // basis | basis derivative; then the tile's vector and scalar slots
+    float G[kT * F];                       // gathered BF16 rows of u_j | mbar_j, then the FP32 ubar messages
+    uint64_t mbar;
+    uint64_t pad;
+};
+
+template <int F, int NG>
+struct BwdGSmem {
+    unsigned char w1t[F * kKP * 2];       // B[n][k] = W1[k][n]
+    unsigned char w2t[F * F * 2];         // B[n][k] = W2[k][n]
+    unsigned char w2n[F * F * 2];         // B[n][k] = W2[n][k]
+    float b1[F], b2[F];
+    BwdGroup<F> grp[NG];
+    uint32_t taddr;
+};
+
+// Named barrier of one 128-thread group (ids 1 .. NG; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "n"(kT) : "memory");
+}
+__device__ __forceinline__ bool group_sync_and(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t"
+        "}"
+        : "=r"(r) : "r"((uint32_t)v), "r"(id), "n"(kT) : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void unpack_bf16x16(const uint32_t* w, float* v) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+
+template <int F, int NV, int NG>
+__global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, int* status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    BwdGSmem<F, NG>& S = *reinterpret_cast<BwdGSmem<F, NG>*>(smraw);
+    constexpr int H = F / 2;
+    const int g = threadIdx.x / kT;                    // this thread's group
+    const int tid = threadIdx.x & (kT - 1), warp = tid >> 5;
+    const int bar = 1 + g;
+    BwdGroup<F>& T = S.grp[g];
+    static_assert(scal_slot_offset<F>() + sizeof(ScalSlots<NV>) <= sizeof(T.a14), "slots must fit the basis tiles");
+    static_assert(H % 16 == 0, "half the features must be whole 16-column chunks");
+    VecSlots<F>* vs = reinterpret_cast<VecSlots<F>*>(T.a14);
+    ScalSlots<NV>* ss = reinterpret_cast<ScalSlots<NV>*>(T.a14 + scal_slot_offset<F>());
+    unsigned char* const a1 = T.a14;
+    unsigned char* const a4 = T.a14 + kT * kKP * 2;
+    const int l = a.layer;
+    const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
+    const long long n_tiles = (E + kT - 1) / kT;
+    const bool need_ubar = (l > 0);
+
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wt + (size_t)l * a.wt_layer_bytes);
+        uint4* d1 = reinterpret_cast<uint4*>(S.w1t);
+        uint4* d2 = reinterpret_cast<uint4*>(S.w2t);
+        uint4* d3 = reinterpret_cast<uint4*>(S.w2n);
+        for (int t = threadIdx.x; t < F * kKP * 2 / 16; t += kT * NG) d1[t] = src[t];
+        src += F * kKP * 2 / 16;
+        for (int t = threadIdx.x; t < F * F * 2 / 16; t += kT * NG) d2[t] = src[t];
+        src += F * F * 2 / 16;
+        for (int t = threadIdx.x; t < F * F * 2 / 16; t += kT * NG) d3[t] = src[t];
+    }
+    for (int t = threadIdx.x; t < F; t += kT * NG) {
+        S.b1[t] = __ldg(a.P + a.off.b1[l] + t);
+        S.b2[t] = __ldg(a.P + a.off.b2[l] + t);
+    }
+    if (tid == 0) mbar_init(&T.mbar, 1);
+    if (threadIdx.x < 32) tmem_alloc(&S.taddr, NG * 2 * F);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tX = S.taddr + g * 2 * F, tY = tX + F;
+    const uint32_t idesc = idesc_bf16_f32(128, F), idesc_h = idesc_bf16_f32(128, H);
+    const uint32_t sA1 = smem_u32(a1), sA4 = smem_u32(a4);
+    const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t), sW2N = smem_u32(S.w2n);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    const int cw = a.carry_w;
+    const long long first = (long long)blockIdx.x * NG + g, step = (long long)gridDim.x * NG;
+    EdgeIn nx;
+    load_idx(a, first * kT + tid, E, nx);
+    load_pos(a, nx);
+    for (long long tile = first; tile < n_tiles && ok; tile += step) {
+        const long long tb = tile * kT, te = min(tb + kT, E);
+        int prev_row = -1, next_row = -1;                  // read by the merges at the end of the tile
+        if (tid < F + NV) {
+            if (tb > 0) prev_row = __ldg(a.recv + tb - 1);
+            if (te < E) next_row = __ldg(a.recv + te);
+        }
+        const EdgeIn ex = nx;
+        const bool valid = ex.j >= 0;
+        const int j = valid ? ex.j : 0;
+        const int row = valid ? ex.i : -1;
+        load_idx(a, (tile + step) * kT + tid, E, nx);      // this group's next tile's indices
+        gather_rows<F>(T.G, reinterpret_cast<const float*>(a.um), j, tid);
+        cp_async_commit();
+        if (valid) {                                       // the receiving atom's rows, read in the second epilogue
+            prefetch_row_l1<F>(a.u + (size_t)row * F);
+            prefetch_row_l1<F>(a.mbar + (size_t)row * F);
+        }
+        float fc = 0.f, dfc = 0.f, d = 1.f, rx = 0.f, ry = 0.f, rz = 0.f;
+        {
+            float eb[kKP], db[kKP];
+            if (valid) {
+                const uint4 qi = ex.qi, qj = ex.qj;
+                float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
+                float r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                float inv = rsqrtf(r2);
+                d = r2 * inv;
+                rx = r.x * inv; ry = r.y * inv; rz = r.z * inv;
+                basis16(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
+            }
+            st_row8(a1, tid, 0, kKP, eb);
+            st_row8(a1, tid, 8, kKP, eb + 8);
+            st_row8(a4, tid, 0, kKP, db);
+            st_row8(a4, tid, 8, kKP, db + 8);
+        }
+        fence_proxy_async();
+        fence_before_sync();
+        group_sync(bar);
+        fence_after_sync();
+        if (tid == 0) {
+            mma_bf16(tX, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
+            mma_bf16(tY, make_desc(sA4, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
+            mma_commit(&T.mbar);
+        }
+        load_pos(a, nx);                                   // next tile's positions
+        ok = mbar_wait(&T.mbar, phase, kWaitIter);
+        phase ^= 1;
+        fence_after_sync();
+        // epilogue 1: p = SiLU'(a)(e'W1) -> X[0, F/2), SiLU(a) -> Y[0, F/2), both BF16
+#pragma unroll
+        for (int c = 0; c < F; c += 16) {
+            float v[16], tv[16];
+            tmem_ld16(tX + lane_base + c, v);
+            tmem_ld16(tY + lane_base + c, tv);
+            uint32_t ps[8], pp[8];
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) {
+                const float x0 = v[q] + S.b1[c + q], x1 = v[q + 1] + S.b1[c + q + 1];
+                const float s0 = sigmoid_fast(x0), s1 = sigmoid_fast(x1);
+                const float y0 = x0 * s0, y1 = x1 * s1;
+                ps[q / 2] = pack_bf16(y0, y1);
+                pp[q / 2] = pack_bf16(tv[q] * fmaf(y0, 1.f - s0, s0), tv[q + 1] * fmaf(y1, 1.f - s1, s1));
+            }
+            tmem_st8(tY + lane_base + c / 2, ps);
+            tmem_st8(tX + lane_base + c / 2, pp);
+        }
+        tmem_st_wait();
+        fence_before_sync();
+        ok = group_sync_and(bar, ok);
+        fence_after_sync();
+        if (tid == 0 && ok) {
+#pragma unroll
+            for (int kk = 0; kk < F / 16; ++kk) {
+                mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2T + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2T + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+            }
+            mma_commit(&T.mbar);
+        }
+        ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+        phase ^= 1;
+        fence_after_sync();
+        cp_async_wait();                                   // the warp's u_j | mbar_j rows are in G
+        __syncwarp();
+        float gphi = 0.f;
+        {
+            const int i = valid ? row : 0;
+            const float* ui = a.u + (size_t)i * F;
+            const float* mi = a.mbar + (size_t)i * F;
+#pragma unroll
+            for (int c = 0; c < F; c += 16) {
+                float v[16];
+                tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, v);
+                uint4 w[4];                                // BF16 u_j (w[0], w[1]) and mbar_j (w[2], w[3])
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w[k] = *reinterpret_cast<const uint4*>(T.G + prow<F>(tid, c + 4 * k));
+                uint32_t pg[8];
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
+                    const float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
+                    const uint32_t u01 = q < 8 ? (q == 0 ? w[0].x : w[0].z) : (q == 8 ? w[1].x : w[1].z);
+                    const uint32_t u23 = q < 8 ? (q == 0 ? w[0].y : w[0].w) : (q == 8 ? w[1].y : w[1].w);
+                    const uint32_t m01 = q < 8 ? (q == 0 ? w[2].x : w[2].z) : (q == 8 ? w[3].x : w[3].z);
+                    const uint32_t m23 = q < 8 ? (q == 0 ? w[2].y : w[2].w) : (q == 8 ? w[3].y : w[3].w);
+                    float uj[4], mj[4];
+                    uj[0] = __uint_as_float(u01 << 16); uj[1] = __uint_as_float(u01 & 0xffff0000u);
+                    uj[2] = __uint_as_float(u23 << 16); uj[3] = __uint_as_float(u23 & 0xffff0000u);
+                    mj[0] = __uint_as_float(m01 << 16); mj[1] = __uint_as_float(m01 & 0xffff0000u);
+                    mj[2] = __uint_as_float(m23 << 16); mj[3] = __uint_as_float(m23 & 0xffff0000u);
+                    float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
+                    float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
+                    const float g0 = mi4.x * uj[0] + mj[0] * ui4.x;
+                    const float g1 = mi4.y * uj[1] + mj[1] * ui4.y;
+                    const float g2 = mi4.z * uj[2] + mj[2] * ui4.z;
+                    const float g3 = mi4.w * uj[3] + mj[3] * ui4.w;
+                    gphi += g0 * ph0 + g1 * ph1 + g2 * ph2 + g3 * ph3;
+                    pg[q / 2] = pack_bf16(g0, g1);
+                    pg[q / 2 + 1] = pack_bf16(g2, g3);
+                    // the message replaces the chunk (read above into w) of this thread's row
+                    *reinterpret_cast<float4*>(T.G + prow<F>(tid, c + q)) =
+                        make_float4(fc * ph0 * mj[0], fc * ph1 * mj[1], fc * ph2 * mj[2], fc * ph3 * mj[3]);
+                }
+                tmem_st8(tY + lane_base + c / 2, pg);     // over SiLU (read by the completed MMA2)
+            }
+        }
+        tmem_st_wait();
+        fence_before_sync();
+        ok = group_sync_and(bar, ok);
+        fence_after_sync();
+        if (tid == 0 && ok) {
+#pragma unroll
+            for (int kk = 0; kk < F / 16; ++kk) {
+                mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2N + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2N + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+            }
+            mma_commit(&T.mbar);
+        }
+        ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+        phase ^= 1;
+        fence_after_sync();
+        float s2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < F; c += 16) {
+            float ab[16], pv[16];
+            uint32_t pw[8];
+            tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, ab);
+            tmem_ld8(tX + lane_base + c / 2, pw);
+            unpack_bf16x16(pw, pv);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s2 += ab[q] * pv[q];
+        }
+        float se = dfc * gphi + fc * s2;
+        if (l == 0 && valid) {
+            float dphi;
+            (void)rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, &dphi);
+            se += dphi;
+        }
+        {
+            float val[NV];
+            val[0] = se * rx; val[1] = se * ry; val[2] = se * rz;
+            if constexpr (NV == 9) {
+                float hv = -0.5f * se * d;
+                val[3] = hv * rx * rx; val[4] = hv * ry * ry; val[5] = hv * rz * rz;
+                val[6] = hv * rx * ry; val[7] = hv * rx * rz; val[8] = hv * ry * rz;
+            }
+            warp_scal_segments<NV>(val, row, ss, tid);
+        }
+        fence_before_sync();
+        ok = group_sync_and(bar, ok);
+        if (need_ubar) warp_vec_segments<F>(T.G, row, vs, a.msg_out, 0, tid);
+        group_sync(bar);
+        const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
+        if (need_ubar && tid < F) {
+            merge_tile_vec<F>(vs, tid, tc, a.msg_out);
+        } else if (tid >= F && tid < F + NV) {
+            float* force = a.force;
+            float* vir6 = a.vir6;
+            const int n = a.n_atoms, acc = a.accumulate;
+            merge_tile_scal<NV, F>(ss, tid - F, tc, [=](int r, int c, float v) {
+                float* dst = c < 3 ? force + (size_t)c * n + r : vir6 + (size_t)r * 6 + c - 3;
+                *dst = acc ? *dst + v : v;
+            });
+        }
+        group_sync(bar);                                   // slots read before the next basis overwrites them
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(S.taddr, NG * 2 * F);
+    if (!ok && tid == 0) atomicOr(status, 1);
+}
+
+// CTAs of a kernel that fit on one SM: shared memory (1 KB reserved per
+// CTA), the 512 tensor-memory columns, registers (allocated per warp in
+// multiples of 8 per thread) and threads.
 template <class Kern>
-void launch_persistent(Kern kern, int smem, int tmem_cols, int& max_per_sm, int& sms, const PotArgs& a, int K,
-                       int* status, cudaStream_t s) {
+int ctas_per_sm_limit(Kern kern, int smem, int tmem_cols, int threads) {
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        smem_sm = 233472;
+    }
+    int regs = 0;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess) regs = fa.numRegs;
+    else cudaGetLastError();
+    const int by_regs = regs > 0 ? 65536 / (((regs + 7) / 8 * 8) * threads) : 64;
+    return std::max(1, std::min({smem_sm / (smem + 1024), 512 / tmem_cols, by_regs, 2048 / threads}));
+}
+
+// Persistent launch: SMs x CTAs per SM, bounded as above and by the tuner's
+// choice; never more CTAs than needed for the tiles the pair capacity can
+// hold (tiles_per_cta tiles in flight per CTA).
+template <class Kern>
+void launch_persistent(Kern kern, int smem, int tmem_cols, int threads, int tiles_per_cta, int& max_per_sm, int& sms,
+                       const PotArgs& a, int K, int* status, cudaStream_t s) {
     if (!max_per_sm) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int dev = 0, smem_sm = 0;
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        max_per_sm = std::max(1, std::min(smem_sm / (smem + 1024), 512 / tmem_cols));
+        max_per_sm = ctas_per_sm_limit(kern, smem, tmem_cols, threads);
     }
     const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, max_per_sm) : max_per_sm;
     const long long tiles = (a.e_cap + kT - 1) / kT;
-    const long long grid = std::min<long long>(tiles, (long long)sms * per_sm);
-    if (grid > 0) kern<<<(int)grid, kT, smem, s>>>(a, K, status);
+    const long long grid = std::min<long long>((tiles + tiles_per_cta - 1) / tiles_per_cta, (long long)sms * per_sm);
+    if (grid > 0) kern<<<(int)grid, threads, smem, s>>>(a, K, status);
 }
+
+// Tiles in flight per CTA of the F = 64 backward pass (k_edge_bwd_grp). At
+// F = 32 the one-tile kernel measured faster (28.6 vs 31.6 us): it fits 5 CTAs
+// of 4 warps per SM, the grouped one 2 of 8.
+constexpr int kBwdGroups = 2;
 
 template <int F>
 void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     static int cap = 0, sms = 0;
-    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, cap, sms, a, K, status, s);
+    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, cap, sms, a, K, status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
                                                                  nullptr, nullptr, 0);
@@ -857,7 +1187,12 @@ void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
 template <int F, int NV>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     static int cap = 0, sms = 0;
-    launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 2 * F, cap, sms, a, K, status, s);
+    if constexpr (F == 64)
+        launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
+                          kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, cap, sms, a, K, status, s);
+    else
+        launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, cap, sms, a, K, status,
+                          s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
                                                                  a.force, a.vir6, a.accumulate);
@@ -885,15 +1220,13 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
 }
 
 int bf16_max_ctas_per_sm(int F, bool bwd) {
-    const int smem = bwd ? (int)(F == 64 ? sizeof(BwdSmem<64, 3>) : sizeof(BwdSmem<32, 3>))
-                         : (int)(F == 64 ? sizeof(FwdSmem<64>) : sizeof(FwdSmem<32>));
-    int dev = 0, smem_sm = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
-        cudaGetLastError();
-        smem_sm = 233472;
+    if (bwd) {
+        constexpr int G = kBwdGroups;
+        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G>, (int)sizeof(BwdGSmem<64, G>), G * 128, kT * G)
+                       : ctas_per_sm_limit(k_edge_bwd_bf16<32, 3>, (int)sizeof(BwdSmem<32, 3>), 64, kT);
     }
-    return std::max(1, std::min(smem_sm / (smem + 1024), 512 / (2 * F)));
+    return F == 64 ? ctas_per_sm_limit(k_edge_fwd_bf16<64>, (int)sizeof(FwdSmem<64>), 128, kT)
+                   : ctas_per_sm_limit(k_edge_fwd_bf16<32>, (int)sizeof(FwdSmem<32>), 64, kT);
 }
 
 size_t bf16_weight_tile_bytes(int F) {
