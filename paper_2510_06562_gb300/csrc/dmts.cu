@@ -433,7 +433,6 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     CUDA_TRY(dalloc(&m.esum.ctr, kSumMaxSplit));
     CUDA_TRY(cudaMemset(m.esum.ctr, 0, sizeof(unsigned int) * kSumMaxSplit));
     CUDA_TRY(dalloc(&m.W, (size_t)9 * c->n_sys));
-    const bool tc = m.precision == DMTS_BF16_MLP;
     // FP32: atoms per CTA (bounded by shared memory); BF16: atoms per chunk of
     // the persistent kernels
     int mf = max_atoms_per_cta_f32(m.F, m.K, false);

@@ -126,6 +126,10 @@ __device__ __forceinline__ void st_row8(unsigned char* tile, int r, int k0, int 
 // from inv_d = 1/d. The angle pi d / rc lies in [0, pi], where the hardware
 // sine/cosine approximations are accurate to ~1e-6 absolute, far below the
 // BF16 rounding the basis undergoes next.
+// KC > 0: the number of functions as a compile-time constant (the terms
+// past it, and the recurrence steps that feed only them, compile away);
+// KC = 0: K at run time.
+template <int KC>
 __device__ __forceinline__ void basis16(float d, float inv_d, int K, float pi_over_rc, float pref, float* e,
                                         float* de, float& fc, float& dfc) {
     float s1, c1;
@@ -133,7 +137,7 @@ __device__ __forceinline__ void basis16(float d, float inv_d, int K, float pi_ov
     float sk = s1, skm1 = 0.f, ck = c1, ckm1 = 1.f;
 #pragma unroll
     for (int k = 0; k < kKP; ++k) {
-        bool on = k < K;
+        const bool on = KC > 0 ? k < KC : k < K;
         e[k] = on ? pref * sk * inv_d : 0.f;
         if (de) de[k] = on ? pref * ((float)(k + 1) * pi_over_rc * ck - sk * inv_d) * inv_d : 0.f;
         float sn = 2.f * c1 * sk - skm1, cn = 2.f * c1 * ck - ckm1;
@@ -396,7 +400,7 @@ struct FwdSmem {
     uint32_t taddr;
 };
 
-template <int F>
+template <int F, int KC>
 __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                     float r2 = r.x * r.x + r.y * r.y + r.z * r.z;
                     float inv_d = rsqrtf(r2);
                     float d = r2 * inv_d;
-                    basis16(d, inv_d, K, a.pi_over_rc, a.bessel_pref, eb, nullptr, fc, dfc);
+                    basis16<KC>(d, inv_d, K, a.pi_over_rc, a.bessel_pref, eb, nullptr, fc, dfc);
                     if (l == 0) rep = 0.5f * rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, nullptr);
                 } else {
 #pragma unroll
@@ -578,7 +582,7 @@ __device__ __forceinline__ void unpack_bf16x8(uint4 w, float* v) {
 }
 
 // NV = 9: forces and the per-atom virial; NV = 3: forces only.
-template <int F, int NV>
+template <int F, int NV, int KC>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdSmem<F, NV>& S = *reinterpret_cast<BwdSmem<F, NV>*>(smraw);
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     float inv = rsqrtf(r2);
                     d = r2 * inv;
                     rx = r.x * inv; ry = r.y * inv; rz = r.z * inv;
-                    basis16(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+                    basis16<KC>(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
                 } else {
 #pragma unroll
                     for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
@@ -885,7 +889,7 @@ __device__ __forceinline__ void unpack_bf16x16(const uint32_t* w, float* v) {
     }
 }
 
-template <int F, int NV, int NG>
+template <int F, int NV, int NG, int KC>
 __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdGSmem<F, NG>& S = *reinterpret_cast<BwdGSmem<F, NG>*>(smraw);
@@ -966,7 +970,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
                 float inv = rsqrtf(r2);
                 d = r2 * inv;
                 rx = r.x * inv; ry = r.y * inv; rz = r.z * inv;
-                basis16(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+                basis16<KC>(d, inv, K, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
             } else {
 #pragma unroll
                 for (int k = 0; k < kKP; ++k) { eb[k] = 0.f; db[k] = 0.f; }
@@ -1175,46 +1179,64 @@ void launch_persistent(Kern kern, int smem, int tmem_cols, int threads, int tile
 // of 4 warps per SM, the grouped one 2 of 8.
 constexpr int kBwdGroups = 2;
 
+// The radial-function count compiled into the kernels of each width (the
+// big model: F = 64, K = 16; the small one: F = 32, K = 8); other counts use
+// the kernels that take K at run time.
 template <int F>
+constexpr int kSpecK = F == 64 ? 16 : 8;
+
+template <int F, int KC>
 void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     static int cap = 0, sms = 0;
-    launch_persistent(k_edge_fwd_bf16<F>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, cap, sms, a, K, status, s);
+    launch_persistent(k_edge_fwd_bf16<F, KC>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, cap, sms, a, K, status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
                                                                  nullptr, nullptr, 0);
 }
 
-template <int F, int NV>
+template <int F, int NV, int KC>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     static int cap = 0, sms = 0;
     if constexpr (F == 64)
-        launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
+        launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups, KC>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
                           kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, cap, sms, a, K, status, s);
     else
-        launch_persistent(k_edge_bwd_bf16<F, NV>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, cap, sms, a, K, status,
-                          s);
+        launch_persistent(k_edge_bwd_bf16<F, NV, KC>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, cap, sms, a, K,
+                          status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
                                                                  a.force, a.vir6, a.accumulate);
+}
+
+template <int F>
+void fwd_k(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    if (K == kSpecK<F>) go_fwd<F, kSpecK<F>>(a, K, status, s);
+    else go_fwd<F, 0>(a, K, status, s);
+}
+
+template <int F, int NV>
+void bwd_k(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    if (K == kSpecK<F>) go_bwd<F, NV, kSpecK<F>>(a, K, status, s);
+    else go_bwd<F, NV, 0>(a, K, status, s);
 }
 
 }  // namespace
 
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    if (F == 64) go_fwd<64>(a, K, status, s);
-    else go_fwd<32>(a, K, status, s);
+    if (F == 64) fwd_k<64>(a, K, status, s);
+    else fwd_k<32>(a, K, status, s);
     count_launch(2);
 }
 
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;
     if (a.virial) {
-        if (F == 64) go_bwd<64, 9>(a, K, status, s);
-        else go_bwd<32, 9>(a, K, status, s);
+        if (F == 64) bwd_k<64, 9>(a, K, status, s);
+        else bwd_k<32, 9>(a, K, status, s);
     } else {
-        if (F == 64) go_bwd<64, 3>(a, K, status, s);
-        else go_bwd<32, 3>(a, K, status, s);
+        if (F == 64) bwd_k<64, 3>(a, K, status, s);
+        else bwd_k<32, 3>(a, K, status, s);
     }
     count_launch(2);
 }
@@ -1222,11 +1244,12 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
 int bf16_max_ctas_per_sm(int F, bool bwd) {
     if (bwd) {
         constexpr int G = kBwdGroups;
-        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G>, (int)sizeof(BwdGSmem<64, G>), G * 128, kT * G)
-                       : ctas_per_sm_limit(k_edge_bwd_bf16<32, 3>, (int)sizeof(BwdSmem<32, 3>), 64, kT);
+        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>>, (int)sizeof(BwdGSmem<64, G>), G * 128,
+                                           kT * G)
+                       : ctas_per_sm_limit(k_edge_bwd_bf16<32, 3, kSpecK<32>>, (int)sizeof(BwdSmem<32, 3>), 64, kT);
     }
-    return F == 64 ? ctas_per_sm_limit(k_edge_fwd_bf16<64>, (int)sizeof(FwdSmem<64>), 128, kT)
-                   : ctas_per_sm_limit(k_edge_fwd_bf16<32>, (int)sizeof(FwdSmem<32>), 64, kT);
+    return F == 64 ? ctas_per_sm_limit(k_edge_fwd_bf16<64, kSpecK<64>>, (int)sizeof(FwdSmem<64>), 128, kT)
+                   : ctas_per_sm_limit(k_edge_fwd_bf16<32, kSpecK<32>>, (int)sizeof(FwdSmem<32>), 64, kT);
 }
 
 size_t bf16_weight_tile_bytes(int F) {

@@ -363,6 +363,25 @@ def test_atom_mlp_tensor_cores_match_fp32_kernels(name):
     assert np.abs(W1 - W0).max() <= 1e-4 * max(1.0, np.abs(W0).max())
 
 
+def test_bf16_other_radial_counts():
+    """The BF16 kernels have the shipped radial-function counts (16 at F = 64,
+    8 at F = 32) compiled in and take any other count at run time: K = 10
+    and K = 12 against the oracle."""
+    s = I.water_192(0)
+    ba = I.Arch(cutoff=5.0, n_radial=10, n_layers=2, n_feat=64, n_species=2)
+    sa = I.Arch(cutoff=3.5, n_radial=12, n_layers=1, n_feat=32, n_species=2)
+    bp, sp = I.init_params(ba, 3), I.init_params(sa, 2)
+    with D.Context(s, ba, bp, sa, sp, precision=D.BF16_MLP) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            E, F = ctx.forces(which)
+            Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box)
+            de, err_f = float(np.abs(E - Er).sum() / s.n_atoms), _rmse(F, Fr)
+            print(json.dumps({"model": "small" if which == 0 else "big", "K": arch.n_radial,
+                              "dE_per_atom": de, "force_rmse": err_f}))
+            assert de <= 5e-3 and err_f <= F_TOL_BF16
+
+
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_energy_forces_bf16(name):
     """Filter MLPs on tensor cores with BF16 operands and FP32 accumulation."""
