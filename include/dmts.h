@@ -122,6 +122,8 @@ typedef struct {
  * JSON object; recognised keys: "edge_capacity_factor" (default 1.5, the
  * neighbour-pair capacity relative to the uniform-density estimate),
  * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
+ * "cell_capacity" (initial atoms per cell of the cell list with skin 0; it
+ * grows on demand),
  * "autotune" (default 1: pick the kernels' work granularity by timing),
  * "atoms_per_cta_big" / "atoms_per_cta_small" (atoms per thread block of the
  * force kernels), "skin" (default 0, in [0, 10] Angstrom: Verlet-skin

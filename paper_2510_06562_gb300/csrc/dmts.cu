@@ -78,6 +78,7 @@ struct Model {
     int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr, *atom_cell = nullptr,
         *atom_slot = nullptr, *atom_pos = nullptr;
     uint4* cell_q = nullptr;
+    int ccap = 0;                      // skin 0: slots per cell ([n_cells][ccap] cell_atoms / cell_q)
     int row_cap = 0;
     long long e_cap = 0;
     int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
@@ -400,12 +401,19 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     if (m.nc > 0) {
         m.n_cells = m.nc * m.nc * m.nc;
         CUDA_TRY(dalloc(&m.cell_count, m.n_cells));
-        CUDA_TRY(dalloc(&m.cell_start, m.n_cells + 1));
-        CUDA_TRY(dalloc(&m.cell_atoms, N));
-        CUDA_TRY(dalloc(&m.atom_cell, N));
-        CUDA_TRY(dalloc(&m.atom_slot, N));
+        CUDA_TRY(cudaMemset(m.cell_count, 0, sizeof(int) * m.n_cells));
         CUDA_TRY(dalloc(&m.atom_pos, N));
-        CUDA_TRY(dalloc(&m.cell_q, N));
+        if (c->skin > 0) {                 // compact cells rebuilt by count, scan and fill
+            CUDA_TRY(dalloc(&m.cell_start, m.n_cells + 1));
+            CUDA_TRY(dalloc(&m.atom_cell, N));
+            CUDA_TRY(dalloc(&m.atom_slot, N));
+            CUDA_TRY(dalloc(&m.cell_atoms, N));
+            CUDA_TRY(dalloc(&m.cell_q, N));
+        } else {                           // fixed-capacity cells: twice the mean occupancy plus 16, grown on overflow
+            m.ccap = ((int)(2.0 * N / m.n_cells) + 16 + 7) / 8 * 8;
+            CUDA_TRY(dalloc(&m.cell_atoms, (size_t)m.n_cells * m.ccap));
+            CUDA_TRY(dalloc(&m.cell_q, (size_t)m.n_cells * m.ccap));
+        }
     }
     CUDA_TRY(alloc_model_nbr(c, m));
     CUDA_TRY(dalloc(&m.nbr_cnt, N));
@@ -472,6 +480,9 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
     a.which = which;
     a.exact = 1;
     a.flag_row = kFlagMaxRow0 + which;
+    a.ccap = m.ccap;
+    a.n_cells = m.nc > 0 ? m.n_cells : 0;
+    a.cell_count = m.cell_count;
     return a;
 }
 
@@ -606,10 +617,7 @@ void enqueue_neighbors(dmts_ctx* c, int which, bool quantize, Check check = Chec
         launch_quantize(c->N, c->d_x, c->d_sys, c->d_frame, c->d_q, s);
     }
     if (c->skin <= 0) {
-        if (m.nc > 0)
-            launch_cells(c->N, c->d_q, m.nc, m.cell_count, m.cell_start, m.cell_atoms, m.atom_cell, m.atom_slot,
-                         m.cell_q, m.atom_pos, s);
-        launch_neighbors(nbr_args(c, m, which), s);
+        launch_neighbors(nbr_args(c, m, which), s);     // places the atoms into the cells first
         return;
     }
     if (check == Check::Kernel) launch_vl_check(c->N, c->d_x, c->d_sys, c->d_box, verlet_check(c), s);
@@ -736,6 +744,18 @@ int grow_capacity(dmts_ctx* c) {
         if (max_row > m.row_cap) { m.row_cap = std::min(c->N, ((int)(max_row * 1.25) + 63) / 32 * 32); grow = true; }
         if (max_e > m.e_cap) { m.e_cap = (long long)(max_e * 1.25) + 1024; grow = true; }
         if (c->skin > 0 && max_vl > m.vl_cap) { m.vl_cap = std::min(c->N, ((int)(max_vl * 1.25) + 63) / 32 * 32); grow = true; }
+        const int max_cell = c->h_flags[kFlagMaxCell0 + w];
+        if (m.ccap > 0 && max_cell > m.ccap) {
+            m.ccap = ((int)(max_cell * 1.25) + 8 + 7) / 8 * 8;
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            dfree(m.cell_atoms);
+            dfree(m.cell_q);
+            m.cell_atoms = nullptr;
+            m.cell_q = nullptr;
+            cudaError_t e = dalloc(&m.cell_atoms, (size_t)m.n_cells * m.ccap);
+            if (e == cudaSuccess) e = dalloc(&m.cell_q, (size_t)m.n_cells * m.ccap);
+            if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "growing cell capacity: %s", cudaGetErrorString(e));
+        }
         if (grow) {
             if (m.row_cap > 6000 || m.vl_cap > 6000)
                 return fail(DMTS_ERR_CAPACITY, "neighbour row capacity %d too large", std::max(m.row_cap, m.vl_cap));
@@ -1067,6 +1087,7 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     c->cap_factor = json_number(options, "edge_capacity_factor", 1.5);
     if (!(c->cap_factor > 0.0)) c->cap_factor = 1.5;
     const double opt_row_cap = json_number(options, "row_capacity", 0.0);
+    const double opt_cell_cap = json_number(options, "cell_capacity", 0.0);
     c->skin = json_number(options, "skin", 0.0);
     if (!(c->skin >= 0.0) || c->skin > 10.0) {
         delete c;
@@ -1175,6 +1196,17 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
             c->m[w].vl_cap = std::min(c->m[w].vl_cap, (int)opt_row_cap);
             free_model_nbr(c->m[w]);
             CREATE_TRY(alloc_model_nbr(c, c->m[w]));
+        }
+        if (c->m[w].present && c->m[w].ccap > 0 && opt_cell_cap >= 1.0) {
+            // smaller initial cell capacity (exercises the overflow-and-retry path)
+            Model& m = c->m[w];
+            m.ccap = std::min(m.ccap, (int)opt_cell_cap);
+            dfree(m.cell_atoms);
+            dfree(m.cell_q);
+            m.cell_atoms = nullptr;
+            m.cell_q = nullptr;
+            CREATE_TRY(dalloc(&m.cell_atoms, (size_t)m.n_cells * m.ccap));
+            CREATE_TRY(dalloc(&m.cell_q, (size_t)m.n_cells * m.ccap));
         }
         c->m[w].apc_fwd = std::max(8, c->m[w].apc_fwd);
         c->m[w].apc_bwd = std::max(8, c->m[w].apc_bwd);

@@ -52,7 +52,9 @@ enum Flag {
     kFlagTimeout = 7,      // a bounded device-side wait gave up
     kFlagMaxVl0 = 8,       // max candidate (Verlet) row length seen (small model)
     kFlagMaxVl1 = 9,       // (big)
-    kFlagCount = 10
+    kFlagMaxCell0 = 10,    // most atoms placed in one cell, when a cell overflowed (small model)
+    kFlagMaxCell1 = 11,    // (big)
+    kFlagCount = 12
 };
 
 // Verlet-skin bookkeeping (device memory, one per context). The candidate
@@ -145,6 +147,12 @@ struct NbrArgs {
     const int* src_rows;     // row filter input: candidate rows [N][src_cap], sorted by j
     const int* src_cnt;      // [N]
     int src_cap;
+    // fresh lists (skin 0): cells of fixed capacity ccap > 0, slots
+    // [n_cells][ccap] of cell_atoms / cell_q filled by atomic counters
+    // cell_count (zero between builds: the compaction clears them)
+    int ccap;
+    int n_cells;
+    int* cell_count;
 };
 
 // Arguments of the potential's kernels (one model, one layer).
@@ -207,9 +215,9 @@ void launch_frames(int n_sys, const int* atom_offset, const double* x, int n_ato
                    const double* box, double rc_max, Frame* frame, cudaStream_t s);
 void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const Frame* frame,
                      uint4* q, cudaStream_t s);
-void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                  int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos, cudaStream_t s);
 void launch_neighbors(const NbrArgs& a, cudaStream_t s);
+// Fresh pair list with fixed-capacity cells (a.ccap > 0; a.cell_count zero on
+// entry, and again on exit): placement, row build, row scan, compaction.
 // Verlet-skin lists: displacement check (sets st->rebuild), gated cell list,
 // gated candidate build (a.nbr_tmp / a.nbr_cnt / a.row_cap = candidate rows),
 // gated candidate-from-candidate filter, and the per-evaluation exact filter

@@ -211,6 +211,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_1cta(int n, const int* __
     }
 }
 
+// Fixed-capacity cells (fresh lists): every atom takes the next free slot of
+// its cell (atomic counter), with its fixed-point position beside it; an atom
+// beyond the capacity is not placed, and the overflow is flagged (the list is
+// rebuilt with larger cells). The slot order varies from run to run; the
+// builder sorts every row by j, so the list does not.
+__global__ void k_cell_place(int n, const uint4* __restrict__ q, int nc, int ccap, int* __restrict__ cell_count,
+                             int* __restrict__ cell_atoms, uint4* __restrict__ cell_q, int* __restrict__ atom_pos,
+                             int* __restrict__ flags, int flag_cell) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 p = q[i];
+    const int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
+    const int slot = atomicAdd(&cell_count[c], 1);
+    if (slot < ccap) {
+        const int pos = c * ccap + slot;
+        cell_atoms[pos] = i;
+        cell_q[pos] = p;
+        atom_pos[i] = pos;
+    } else {
+        atom_pos[i] = -1;
+        atomicMax(&flags[flag_cell], slot + 1);
+        atomicOr(&flags[kFlagOverflow], 1);
+    }
+}
+
 // Atoms in cell order, with their fixed-point positions beside them (the
 // builder then reads each cell's candidates contiguously) and each atom's own
 // place in that order.
@@ -239,11 +264,6 @@ void launch_cells_gated(int n_atoms, const uint4* q, int nc, int* cell_count, in
     count_launch(4);
 }
 
-void launch_cells(int n_atoms, const uint4* q, int nc, int* cell_count, int* cell_start,
-                  int* cell_atoms, int* atom_cell, int* atom_slot, uint4* cell_q, int* atom_pos, cudaStream_t s) {
-    launch_cells_gated(n_atoms, q, nc, cell_count, cell_start, cell_atoms, atom_cell, atom_slot, cell_q, atom_pos,
-                       nullptr, s);
-}
 
 // ------------------------------------------------------------ neighbours
 // Exact FP64 decision, operation by operation (no contraction).
@@ -291,8 +311,13 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
             int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
             int x2 = (cx + dx + nc) % nc, y2 = (cy + dy + nc) % nc, z2 = (cz + dz + nc) % nc;
             int c = (z2 * nc + y2) * nc + x2;
-            st = a.cell_start[c];
-            cnt = a.cell_start[c + 1] - st;
+            if (a.ccap > 0) {                        // fixed-capacity cells
+                st = c * a.ccap;
+                cnt = min(a.cell_count[c], a.ccap);
+            } else {
+                st = a.cell_start[c];
+                cnt = a.cell_start[c + 1] - st;
+            }
         }
         int v = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -367,6 +392,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
 }
 
 __global__ void k_nbr_compact(NbrArgs a) {
+    // fixed-capacity cells: the counters start the next build at zero
+    if (a.ccap > 0)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
+            a.cell_count[k] = 0;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= a.n_atoms) return;
     int i = w;
@@ -476,6 +505,14 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
     if (a.n_atoms == 0) {
         cudaMemsetAsync(a.row_ptr, 0, sizeof(int), s);
         return;
+    }
+    if (a.nc > 0 && a.ccap > 0) {
+        k_cell_place<<<(a.n_atoms + 255) / 256, 256, 0, s>>>(a.n_atoms, a.q, a.nc, a.ccap, a.cell_count,
+                                                             const_cast<int*>(a.cell_atoms),
+                                                             const_cast<uint4*>(a.cell_q),
+                                                             const_cast<int*>(a.atom_pos), a.flags,
+                                                             kFlagMaxCell0 + a.which);
+        count_launch();
     }
     static bool attr_done = false;
     if (!attr_done) {

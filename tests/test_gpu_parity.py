@@ -262,10 +262,15 @@ def test_checkpoint_resume_is_exact():
     np.testing.assert_array_equal(v1, v2)
 
 
-def test_capacity_overflow_retry_gives_identical_results():
-    s = I.water_192(0)
+@pytest.mark.parametrize("name", ["water192", "water12288"])
+def test_capacity_overflow_retry_gives_identical_results(name):
+    """Row, pair-list and cell capacities far too small at the start: every
+    overflow is detected on the device, the capacities grow and the work is
+    redone, with results identical to a context that never overflowed."""
+    s = SYSTEMS[name]()
     v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
-    with _ctx(s) as a, _ctx(s, options='{"row_capacity": 4, "edge_capacity_factor": 0.05}') as b:
+    opts = '{"row_capacity": 4, "edge_capacity_factor": 0.05, "cell_capacity": 2}'
+    with _ctx(s) as a, _ctx(s, options=opts) as b:
         a.set_state(s.x, v0)
         b.set_state(s.x, v0)
         Ea, Fa = a.forces(D.BIG)
