@@ -196,8 +196,8 @@ def measure(D, I, torch, s, models_, prec, args, flush, dt, n_inner, seed):
 
 KERNEL_OF_STAGE = {
     # (precision is BF16, stage prefix) -> (kernel name in the ncu capture, source file)
-    (True, "edge_bwd"): ("k_edge_bwd_grp<64,3,2>", "potential_bf16.cu"),
-    (True, "edge_fwd"): ("k_edge_fwd_bf16<64>", "potential_bf16.cu"),
+    (True, "edge_bwd"): ("k_edge_bwd_grp<64,3,2,16>", "potential_bf16.cu"),
+    (True, "edge_fwd"): ("k_edge_fwd_bf16<64,16>", "potential_bf16.cu"),
     (False, "edge_bwd"): ("k_edge_bwd<64,16>", "potential_f32.cu"),
     (False, "edge_fwd"): ("k_edge_fwd<64,16>", "potential_f32.cu"),
 }
