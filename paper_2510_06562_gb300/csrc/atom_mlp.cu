@@ -1,5 +1,7 @@
-// Per-atom MLPs of the potential (FP32, register-blocked SIMT), used by both
-// precisions after the edge passes have produced the per-atom sums:
+// Per-atom MLPs of the potential (FP32, register-blocked SIMT), run after the
+// edge passes have produced the per-atom sums: in the FP32 mode, and in the
+// BF16 mode for models narrower than F = 64 (wider ones use the tensor-core
+// kernels of atom_tc.cu):
 //
 //   forward, layer l:   z = m U1 + c1;  h <- h + SiLU(z) U2 + c2;
 //                       l < L-1:  u^{l+1} = h W_in^{l+1}

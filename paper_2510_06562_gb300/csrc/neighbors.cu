@@ -8,6 +8,13 @@
 // a thin band around rc^2, where FP32 rounding could flip the decision, are
 // decided by the exact FP64 expression.
 //
+// Fresh lists (skin 0) use cells of fixed capacity: one kernel puts every
+// atom into the next free slot of its cell (an atomic counter per cell), the
+// row build reads the 27 cells around each atom at fixed strides and sorts
+// each row by j (so the list does not depend on the slot order), a one-CTA
+// scan gives the row offsets, and the compaction writes the CSR arrays and
+// clears the cell counters for the next build.
+//
 // Verlet-skin mode keeps, per model, candidate rows of every j within
 // rc + skin at the positions x_ref of the last rebuild. While no atom has
 // moved by skin / 2 or more since then, every pair now inside rc was inside
