@@ -79,6 +79,7 @@ struct Model {
         *atom_slot = nullptr, *atom_pos = nullptr;
     uint4* cell_q = nullptr;
     int ccap = 0;                      // skin 0: slots per cell ([n_cells][ccap] cell_atoms / cell_q)
+    bool placed = false;               // while capturing: the integrator kernel fills the cells
     int row_cap = 0;
     long long e_cap = 0;
     int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
@@ -481,6 +482,7 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
     a.exact = 1;
     a.flag_row = kFlagMaxRow0 + which;
     a.ccap = m.ccap;
+    a.placed = m.placed ? 1 : 0;
     a.n_cells = m.nc > 0 ? m.n_cells : 0;
     a.cell_count = m.cell_count;
     return a;
@@ -840,7 +842,21 @@ cudaError_t capture_fallback_node(dmts_ctx* c, cudaGraphConditionalHandle h, int
     return cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
+// Cells of model w for the integrator kernel to fill (periodic systems with
+// fresh lists, whose fixed-point positions that kernel writes); nc = 0: none.
+CellPlace cell_place(dmts_ctx* c, int w) {
+    const Model& m = c->m[w];
+    CellPlace p{};
+    if (c->periodic && c->skin <= 0 && m.present && m.nc > 0 && m.ccap > 0)
+        p = CellPlace{m.nc, m.ccap, m.cell_count, m.cell_atoms, m.cell_q, m.atom_pos, kFlagMaxCell0 + w};
+    return p;
+}
+
 int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
+    struct PlacedReset {                       // no evaluation outside this capture skips its placement
+        dmts_ctx* c;
+        ~PlacedReset() { c->m[0].placed = c->m[1].placed = false; }
+    } placed_reset{c};
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     cudaStream_t s = c->stream;
     const double acc = accel_constant();
@@ -867,11 +883,19 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
         // with fresh neighbour lists the two evaluations at the final positions
         // share nothing but the read-only positions: fork the large one
         const bool fork = c->concurrent && c->skin <= 0;
+        // the small model's cells at every inner step, and the large model's
+        // at the last, are filled by the integrator kernel (each placement is
+        // followed by that model's build, whose compaction empties the cells)
+        const CellPlace none{};
+        const CellPlace cp0 = cell_place(c, 0), cp1 = cell_place(c, 1);
         for (int k = 0; k < n_inner; ++k) {
             lg.offset = k;
+            const bool last = k == n_inner - 1;
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, vc,
-                             lg, s);
+                             lg, cp0, last ? cp1 : none, s);
+            c->m[0].placed = cp0.nc > 0;
+            c->m[1].placed = last && cp1.nc > 0;
             if (fork && k == n_inner - 1) {
                 if (nonper) {                                  // frames and fixed-point positions for both
                     launch_frames(c->n_sys, c->d_off, c->d_x, c->N, c->d_box, c->rc_max, c->d_frame, s);
@@ -890,6 +914,7 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
             }
         }
         if (!fork) enqueue_eval(c, 1, false, true, Check::None);   // same positions as the last small evaluation
+        c->m[0].placed = c->m[1].placed = false;
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
                           c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, s);
         if (fallback && ce == cudaSuccess) ce = capture_fallback_node(c, mon.cond, n_inner, dt);

@@ -113,13 +113,16 @@ void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t 
 //   first:  v += (dt/2m) (F - F_small)        (outer half-kick)
 //   else:   v += (h/2m) F_small               (post-kick of the previous inner step)
 //   then    v += (h/2m) F_small; x += (h/2) v; [thermo = identity]; x += (h/2) v
-// with the position wrapped after each half-drift; then quantise x.
+// with the position wrapped after each half-drift; then quantise x, and put
+// the atom into the fixed-capacity cells of the models evaluated next (cp0,
+// cp1; nc = 0: none), as the pair-list build would.
 __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, double half_h,
                             double* __restrict__ x, double* __restrict__ v,
                             const double* __restrict__ inv_m, const float* __restrict__ fs,
                             const float* __restrict__ fb, const int* __restrict__ sys,
                             const double* __restrict__ box, const Frame* __restrict__ frame,
-                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg) {
+                            uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg,
+                            CellPlace cp0, CellPlace cp1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (i < n) {
@@ -150,7 +153,10 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
             double oc = c == 0 ? fr.ox : (c == 1 ? fr.oy : fr.oz);
             qc[c] = fixed_of(xx, oc, fr.inv);
         }
-        q[i] = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+        const uint4 qi = make_uint4(qc[0], qc[1], qc[2], (unsigned int)s);
+        q[i] = qi;
+        if (cp0.nc > 0) place_in_cell(cp0, i, qi, flags);
+        if (cp1.nc > 0) place_in_cell(cp1, i, qi, flags);
         if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
         if (vc.st) m = vl_disp2(x, vc.xref, (size_t)n, (size_t)i, L, vc.thr2);
     }
@@ -161,11 +167,11 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                      const Langevin& lg, cudaStream_t s) {
+                      const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
-                                                     frame, q, flags, vc, lg);
+                                                     frame, q, flags, vc, lg, cp0, cp1);
     count_launch();
 }
 

@@ -153,6 +153,18 @@ struct NbrArgs {
     int ccap;
     int n_cells;
     int* cell_count;
+    int placed;              // the atoms are already in the cells (placed by the integrator kernel)
+};
+
+// Fixed-capacity cells of one model, for the integrator kernel that moves the
+// atoms to fill while it writes their fixed-point positions (nc = 0: none).
+struct CellPlace {
+    int nc, ccap;
+    int* count;
+    int* atoms;
+    uint4* q;
+    int* pos;
+    int flag_cell;
 };
 
 // Arguments of the potential's kernels (one model, one layer).
@@ -286,7 +298,8 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                      const Langevin& lg, cudaStream_t s);
+                      const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1,
+                      cudaStream_t s);
 // after the big force: last inner post-kick and the outer half-kick.
 // With a step counter: advances it by `advance` (the inner steps taken).
 // With a monitor: the force-difference statistics and fallback decision.
@@ -402,6 +415,32 @@ __device__ __forceinline__ float3 edge_vec(uint4 qi, uint4 qj, float qscale) {
     r.y = (float)(int)(qj.y - qi.y) * qscale;
     r.z = (float)(int)(qj.z - qi.z) * qscale;
     return r;
+}
+
+// Cell index along one axis of nc cells from a 32-bit fixed-point coordinate.
+__device__ __forceinline__ int cell_coord(unsigned int qc, int nc) {
+    return (int)(((unsigned long long)qc * (unsigned long long)nc) >> 32);
+}
+
+// Fixed-capacity cells (fresh lists): atom i, at fixed-point position p, takes
+// the next free slot of its cell (atomic counter), with its position beside
+// it; an atom beyond the capacity is not placed, and the overflow is flagged
+// (the list is rebuilt with larger cells). The slot order varies from run to
+// run; the builder sorts every row by j, so the list does not.
+__device__ __forceinline__ void place_in_cell(const CellPlace& cp, int i, uint4 p, int* __restrict__ flags) {
+    const int nc = cp.nc;
+    const int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
+    const int slot = atomicAdd(&cp.count[c], 1);
+    if (slot < cp.ccap) {
+        const int pos = c * cp.ccap + slot;
+        cp.atoms[pos] = i;
+        cp.q[pos] = p;
+        cp.pos[i] = pos;
+    } else {
+        cp.pos[i] = -1;
+        atomicMax(&flags[cp.flag_cell], slot + 1);
+        atomicOr(&flags[kFlagOverflow], 1);
+    }
 }
 
 }  // namespace dmts

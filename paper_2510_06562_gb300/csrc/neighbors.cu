@@ -124,10 +124,6 @@ void launch_quantize(int n_atoms, const double* x, const int* sys_of_atom, const
 }
 
 // ------------------------------------------------------------ cell list
-__device__ __forceinline__ int cell_coord(unsigned int qc, int nc) {
-    return (int)(((unsigned long long)qc * (unsigned long long)nc) >> 32);
-}
-
 __device__ __forceinline__ bool gated_off(const int* gate) { return gate && *gate == 0; }
 
 __global__ void k_cell_clear(int n, int* __restrict__ count, const int* gate) {
@@ -218,29 +214,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_1cta(int n, const int* __
     }
 }
 
-// Fixed-capacity cells (fresh lists): every atom takes the next free slot of
-// its cell (atomic counter), with its fixed-point position beside it; an atom
-// beyond the capacity is not placed, and the overflow is flagged (the list is
-// rebuilt with larger cells). The slot order varies from run to run; the
-// builder sorts every row by j, so the list does not.
-__global__ void k_cell_place(int n, const uint4* __restrict__ q, int nc, int ccap, int* __restrict__ cell_count,
-                             int* __restrict__ cell_atoms, uint4* __restrict__ cell_q, int* __restrict__ atom_pos,
-                             int* __restrict__ flags, int flag_cell) {
+// Fixed-capacity cells (fresh lists): every atom into its cell.
+__global__ void k_cell_place(int n, const uint4* __restrict__ q, CellPlace cp, int* __restrict__ flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint4 p = q[i];
-    const int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
-    const int slot = atomicAdd(&cell_count[c], 1);
-    if (slot < ccap) {
-        const int pos = c * ccap + slot;
-        cell_atoms[pos] = i;
-        cell_q[pos] = p;
-        atom_pos[i] = pos;
-    } else {
-        atom_pos[i] = -1;
-        atomicMax(&flags[flag_cell], slot + 1);
-        atomicOr(&flags[kFlagOverflow], 1);
-    }
+    place_in_cell(cp, i, q[i], flags);
 }
 
 // Atoms in cell order, with their fixed-point positions beside them (the
@@ -513,12 +491,10 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
         cudaMemsetAsync(a.row_ptr, 0, sizeof(int), s);
         return;
     }
-    if (a.nc > 0 && a.ccap > 0) {
-        k_cell_place<<<(a.n_atoms + 255) / 256, 256, 0, s>>>(a.n_atoms, a.q, a.nc, a.ccap, a.cell_count,
-                                                             const_cast<int*>(a.cell_atoms),
-                                                             const_cast<uint4*>(a.cell_q),
-                                                             const_cast<int*>(a.atom_pos), a.flags,
-                                                             kFlagMaxCell0 + a.which);
+    if (a.nc > 0 && a.ccap > 0 && !a.placed) {
+        const CellPlace cp{a.nc, a.ccap, a.cell_count, const_cast<int*>(a.cell_atoms),
+                           const_cast<uint4*>(a.cell_q), const_cast<int*>(a.atom_pos), kFlagMaxCell0 + a.which};
+        k_cell_place<<<(a.n_atoms + 255) / 256, 256, 0, s>>>(a.n_atoms, a.q, cp, a.flags);
         count_launch();
     }
     static bool attr_done = false;
