@@ -203,11 +203,13 @@ KERNEL_OF_STAGE = {
 }
 
 
-def captured_traffic(kernel: str, source: str):
+def captured_traffic(kernel: str, source: str, pairs: int):
     """DRAM bytes per launch of `kernel` (template arguments without spaces)
     from a committed ncu summary under profiles/ (a line `counters:
-    kernel=... source_sha256=... dram_bytes_per_launch=...`), or None when
-    there is none or the kernel's source changed since the capture."""
+    kernel=... source_sha256=... dram_bytes_per_launch=... pairs=...`), or
+    None when there is none, the kernel's source changed since the capture,
+    or the capture was of another workload (pair count more than 1% away:
+    the count of one box drifts a little with the dynamics)."""
     here = os.path.dirname(os.path.abspath(__file__))
     src = os.path.join(here, "paper_2510_06562_gb300", "csrc", source)
     try:
@@ -220,7 +222,9 @@ def captured_traffic(kernel: str, source: str):
             if "counters:" not in line:
                 continue
             fields = dict(kv.split("=", 1) for kv in line.split("counters:", 1)[1].split() if "=" in kv)
-            if fields.get("kernel") == kernel and fields.get("source_sha256") == sha and "dram_bytes_per_launch" in fields:
+            if (fields.get("kernel") == kernel and fields.get("source_sha256") == sha
+                    and "dram_bytes_per_launch" in fields and "pairs" in fields
+                    and abs(int(fields["pairs"]) - pairs) <= 0.01 * pairs):
                 return float(fields["dram_bytes_per_launch"])
     return None
 
@@ -238,7 +242,7 @@ def roofline_of(D, prec, stages_big, E_big, ba):
     achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
     kname, ksrc = KERNEL_OF_STAGE[(prec != D.FP32, dom[:8])]
     return {"kernel": f"{dom} (big model, {kind})", "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic(kname, ksrc),
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic(kname, ksrc, E_big),
             "algorithmic_flop_per_launch": flop_edge * E_big, "launch_ms": stages_big[dom], "peak_source": src}
 
 
