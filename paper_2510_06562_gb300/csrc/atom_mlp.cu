@@ -332,22 +332,14 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_bwd(PotArgs p, const f
 template <int F>
 void atom_fwd_go(const PotArgs& p, const float* msg, cudaStream_t s) {
     using T = AtomTile<F>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_atom_fwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
-        attr = true;
-    }
+    smem_opt_in((const void*)k_atom_fwd<F>, T::SMEM);
     k_atom_fwd<F><<<(p.n_atoms + T::A - 1) / T::A, T::NT, T::SMEM, s>>>(p, msg);
 }
 
 template <int F>
 void atom_bwd_go(const PotArgs& p, const float* ubar, cudaStream_t s) {
     using T = AtomTile<F>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_atom_bwd<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
-        attr = true;
-    }
+    smem_opt_in((const void*)k_atom_bwd<F>, T::SMEM);
     k_atom_bwd<F><<<(p.n_atoms + T::A - 1) / T::A, T::NT, T::SMEM, s>>>(p, ubar);
 }
 

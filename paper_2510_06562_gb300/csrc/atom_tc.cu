@@ -419,12 +419,8 @@ __global__ void __launch_bounds__(kA * (F / 16)) k_atom_tc(PotArgs p, const floa
 
 template <int F>
 void atom_tc_go(const PotArgs& p, const float* msg, int bwd, int* status, cudaStream_t s) {
-    static bool attr = false;
     const int smem = (int)sizeof(AtcSmem<F>);
-    if (!attr) {
-        cudaFuncSetAttribute(k_atom_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    smem_opt_in((const void*)k_atom_tc<F>, smem);
     k_atom_tc<F><<<(p.n_atoms + kA - 1) / kA, kA * (F / 16), smem, s>>>(p, msg, bwd, status);
 }
 

@@ -599,11 +599,7 @@ size_t edge_smem() { return sizeof(EdgeSmem<F, K>); }
 
 template <int F, int K>
 void tangent_go(const PotArgs& a, const float* g, float* mdot, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fm_tangent<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_smem<F, K>());
-        attr = true;
-    }
+    smem_opt_in((const void*)k_fm_tangent<F, K>, (int)edge_smem<F, K>());
     int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
     k_fm_tangent<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mdot);
 }
@@ -611,11 +607,7 @@ void tangent_go(const PotArgs& a, const float* g, float* mdot, cudaStream_t s) {
 template <int F, int K>
 void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
                   int n_params, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fm_grad_edge<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)edge_smem<F, K>());
-        attr = true;
-    }
+    smem_opt_in((const void*)k_fm_grad_edge<F, K>, (int)edge_smem<F, K>());
     int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
     k_fm_grad_edge<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mb, mdb, ubar, partial, n_params);
 }

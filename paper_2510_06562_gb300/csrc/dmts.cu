@@ -17,7 +17,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/dmts.h"
@@ -26,6 +29,17 @@
 
 namespace dmts {
 thread_local long long* g_launch_counter = nullptr;
+
+void smem_opt_in(const void* kern, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.insert({kern, dev}).second) return;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        done.erase({kern, dev});             // the launch then reports the error
+}
 double accel_constant();
 }  // namespace dmts
 

@@ -332,6 +332,12 @@ inline void count_launch(long long n = 1) {
     if (g_launch_counter) *g_launch_counter += n;
 }
 
+// Raises kernel `kern`'s dynamic shared-memory limit to `bytes` on the calling
+// thread's current device, once per kernel and device: the attribute belongs
+// to the device, and the contexts of one process may use different devices.
+// Thread-safe.
+void smem_opt_in(const void* kern, int bytes);
+
 }  // namespace dmts
 
 // ------------------------------------------------------------ device helpers

@@ -463,11 +463,7 @@ void launch_row_filter(const NbrArgs& a, cudaStream_t s) {
 
 void launch_vl_build(const NbrArgs& a, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_nbr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_done = true;
-    }
+    smem_opt_in((const void*)k_nbr_build, 227 * 1024);
     int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
@@ -497,11 +493,7 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
         k_cell_place<<<(a.n_atoms + 255) / 256, 256, 0, s>>>(a.n_atoms, a.q, cp, a.flags);
         count_launch();
     }
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_nbr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_done = true;
-    }
+    smem_opt_in((const void*)k_nbr_build, 227 * 1024);
     int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);

@@ -20,6 +20,9 @@
 // mbarrier (bounded waits: a wait that gives up sets the timeout flag and the
 // kernel finishes without further MMAs, freeing its tensor memory).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.cuh"
 #include "umma.cuh"
@@ -1155,22 +1158,43 @@ int ctas_per_sm_limit(Kern kern, int smem, int tmem_cols, int threads) {
     return std::max(1, std::min({smem_sm / (smem + 1024), 512 / tmem_cols, by_regs, 2048 / threads}));
 }
 
+// SM count and CTAs per SM that fit, per kernel and device (computed at the
+// first launch on each device).
+struct PersistLimits {
+    int sms = 0, per_sm = 0;
+};
+std::mutex g_limits_mu;
+std::map<std::pair<const void*, int>, PersistLimits> g_limits;
+
+template <class Kern>
+PersistLimits persist_limits(Kern kern, int smem, int tmem_cols, int threads) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::pair<const void*, int> key{(const void*)kern, dev};
+    std::lock_guard<std::mutex> lock(g_limits_mu);
+    auto it = g_limits.find(key);
+    if (it != g_limits.end()) return it->second;
+    smem_opt_in((const void*)kern, smem);
+    PersistLimits lim;
+    if (cudaDeviceGetAttribute(&lim.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        lim.sms = 1;
+    }
+    lim.per_sm = ctas_per_sm_limit(kern, smem, tmem_cols, threads);
+    g_limits[key] = lim;
+    return lim;
+}
+
 // Persistent launch: SMs x CTAs per SM, bounded as above and by the tuner's
 // choice; never more CTAs than needed for the tiles the pair capacity can
 // hold (tiles_per_cta tiles in flight per CTA).
 template <class Kern>
-void launch_persistent(Kern kern, int smem, int tmem_cols, int threads, int tiles_per_cta, int& max_per_sm, int& sms,
-                       const PotArgs& a, int K, int* status, cudaStream_t s) {
-    if (!max_per_sm) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        max_per_sm = ctas_per_sm_limit(kern, smem, tmem_cols, threads);
-    }
-    const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, max_per_sm) : max_per_sm;
+void launch_persistent(Kern kern, int smem, int tmem_cols, int threads, int tiles_per_cta, const PotArgs& a, int K,
+                       int* status, cudaStream_t s) {
+    const PersistLimits lim = persist_limits(kern, smem, tmem_cols, threads);
+    const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, lim.per_sm) : lim.per_sm;
     const long long tiles = (a.e_cap + kT - 1) / kT;
-    const long long grid = std::min<long long>((tiles + tiles_per_cta - 1) / tiles_per_cta, (long long)sms * per_sm);
+    const long long grid = std::min<long long>((tiles + tiles_per_cta - 1) / tiles_per_cta, (long long)lim.sms * per_sm);
     if (grid > 0) kern<<<(int)grid, threads, smem, s>>>(a, K, status);
 }
 
@@ -1187,8 +1211,7 @@ constexpr int kSpecK = F == 64 ? 16 : 8;
 
 template <int F, int KC>
 void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static int cap = 0, sms = 0;
-    launch_persistent(k_edge_fwd_bf16<F, KC>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, cap, sms, a, K, status, s);
+    launch_persistent(k_edge_fwd_bf16<F, KC>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, a, K, status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
                                                                  nullptr, nullptr, 0);
@@ -1196,13 +1219,11 @@ void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
 
 template <int F, int NV, int KC>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    static int cap = 0, sms = 0;
     if constexpr (F == 64)
         launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups, KC>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
-                          kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, cap, sms, a, K, status, s);
+                          kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, a, K, status, s);
     else
-        launch_persistent(k_edge_bwd_bf16<F, NV, KC>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, cap, sms, a, K,
-                          status, s);
+        launch_persistent(k_edge_bwd_bf16<F, NV, KC>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, a, K, status, s);
     k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
                                                                  a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
                                                                  a.force, a.vir6, a.accumulate);

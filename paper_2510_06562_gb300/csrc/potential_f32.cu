@@ -538,11 +538,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd(PotArgs a) {
 
 template <int F, int K>
 void set_smem_attrs() {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(k_edge_fwd<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_edge_bwd<F, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    done = true;
+    smem_opt_in((const void*)k_edge_fwd<F, K>, 227 * 1024);
+    smem_opt_in((const void*)k_edge_bwd<F, K>, 227 * 1024);
 }
 
 template <int F, int K>
