@@ -203,20 +203,19 @@ KERNEL_OF_STAGE = {
 }
 
 
-def captured_traffic(kernel: str, source: str, pairs: int):
+def captured_traffic(kernel: str, source: str, pairs: int, root: str = ROOT):
     """DRAM bytes per launch of `kernel` (template arguments without spaces)
     from a committed ncu summary under profiles/ (a line `counters:
     kernel=... source_sha256=... dram_bytes_per_launch=... pairs=...`), or
     None when there is none, the kernel's source changed since the capture,
     or the capture was of another workload (pair count more than 1% away:
     the count of one box drifts a little with the dynamics)."""
-    here = os.path.dirname(os.path.abspath(__file__))
-    src = os.path.join(here, "paper_2510_06562_gb300", "csrc", source)
+    src = os.path.join(root, "paper_2510_06562_gb300", "csrc", source)
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    pdir = os.path.join(here, "profiles")
+    pdir = os.path.join(root, "profiles")
     for name in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
         for line in open(os.path.join(pdir, name), errors="replace"):
             if "counters:" not in line:
