@@ -137,6 +137,39 @@ def _f64(a):
     return a.contiguous()
 
 
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _in_f64(a, n: int, name: str):
+    """An input of n float64 values: NumPy data is converted, a torch tensor
+    must be float64 (made contiguous). The library reads exactly n values."""
+    a = _f64(a)
+    if a is not None and _numel(a) != n:
+        raise ValueError(f"{name} must hold {n} values, got {_numel(a)}")
+    return a
+
+
+def _out_f64(a, n: int, name: str):
+    """An output buffer the library writes n float64 values into: it must be
+    float64, contiguous and of exactly that size (no conversion: the caller
+    reads the buffer it passed)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable
+    elif hasattr(a, "data_ptr"):
+        import torch
+        ok = a.dtype == torch.float64 and a.is_contiguous()
+    else:
+        raise TypeError(f"{name}: unsupported array type {type(a)}")
+    if not ok:
+        raise TypeError(f"{name} must be a writable, contiguous float64 buffer")
+    if _numel(a) != n:
+        raise ValueError(f"{name} must hold {n} values, got {_numel(a)}")
+    return a
+
+
 def hmr_masses(mass, bonds, h_mass: float = 3.024) -> np.ndarray:
     """Hydrogen mass repartitioning (``dmts_hmr_masses``): hydrogens (< 1.5
     amu) bonded to a heavy atom get ``h_mass``; the heavy partner loses the
@@ -187,20 +220,22 @@ class Context:
 
     # ---------------------------------------------------------------- state
     def set_state(self, x, v=None):
-        x = _f64(x)
-        v = _f64(v)
+        if x is None:
+            raise ValueError("x is required")
+        x = _in_f64(x, 3 * self.n_atoms, "x")
+        v = _in_f64(v, 3 * self.n_atoms, "v")
         _check(load_library().dmts_set_state(self._h, _ptr(x), _ptr(v), self.n_atoms))
 
     def get_state(self, x_out=None, v_out=None):
-        x_out = np.empty((self.n_atoms, 3)) if x_out is None else x_out
-        v_out = np.empty((self.n_atoms, 3)) if v_out is None else v_out
+        x_out = np.empty((self.n_atoms, 3)) if x_out is None else _out_f64(x_out, 3 * self.n_atoms, "x_out")
+        v_out = np.empty((self.n_atoms, 3)) if v_out is None else _out_f64(v_out, 3 * self.n_atoms, "v_out")
         _check(load_library().dmts_get_state(self._h, _ptr(x_out), _ptr(v_out)))
         return x_out, v_out
 
     # ---------------------------------------------------------------- forces
     def forces(self, which: int = BIG, virial: bool = False, f_out=None, e_out=None):
-        f_out = np.empty((self.n_atoms, 3)) if f_out is None else f_out
-        e_out = np.empty(self.n_systems) if e_out is None else e_out
+        f_out = np.empty((self.n_atoms, 3)) if f_out is None else _out_f64(f_out, 3 * self.n_atoms, "f_out")
+        e_out = np.empty(self.n_systems) if e_out is None else _out_f64(e_out, self.n_systems, "e_out")
         w_out = np.empty((self.n_systems, 3, 3)) if virial else None
         _check(load_library().dmts_forces(self._h, which, _ptr(f_out), _ptr(e_out), _ptr(w_out)))
         return (e_out, f_out, w_out) if virial else (e_out, f_out)
@@ -226,6 +261,8 @@ class Context:
         (E_pot big, E_kin, E_tot) or None."""
         if energies and out is None and n_outer >= 0:
             out = np.empty((n_outer, self.n_systems, 3))
+        elif energies and out is not None and n_outer >= 0:
+            out = _out_f64(out, 3 * n_outer * self.n_systems, "out")
         _check(load_library().dmts_respa_step(self._h, n_outer, float(dt_outer), n_inner,
                                               _ptr(out) if energies else None))
         return out if energies else None
@@ -240,7 +277,8 @@ class Context:
         if tuple(f_ref.shape) != tuple(frames.shape) or frames.shape[1:] != (self.n_atoms, 3):
             raise ValueError("frames and f_ref must both be [M, N, 3]")
         loss = np.zeros(1)
-        grad = np.empty(self.small_n_params) if grad_out is None else grad_out
+        grad = np.empty(self.small_n_params) if grad_out is None else _out_f64(grad_out, self.small_n_params,
+                                                                               "grad_out")
         _check(load_library().dmts_force_matching_grad(self._h, m, _ptr(frames), _ptr(f_ref), _ptr(loss),
                                                        _ptr(grad)))
         return float(loss[0]), grad
