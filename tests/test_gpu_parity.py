@@ -462,7 +462,7 @@ def test_force_matching_autograd_function():
         loss.backward()
         _, g = ctx.force_matching_grad(frames, f_ref)
     np.testing.assert_allclose(theta.grad.numpy(), g, rtol=0, atol=0)
-    assert float(loss) > 0
+    assert float(loss.detach()) > 0
 
 
 # ------------------------------------------------------------ solvated polymer (4 species)
