@@ -41,6 +41,9 @@
  *  - All device work of a context runs on its own CUDA stream
  *    (dmts_stream); calls return after that work has completed.
  *  - A context is not thread-safe: one thread at a time per context.
+ *    Different contexts may be used from different threads at the same
+ *    time, also on one device; a context belongs to the device that is
+ *    current when dmts_create is called.
  */
 #ifndef DMTS_H
 #define DMTS_H
