@@ -150,6 +150,10 @@ typedef struct {
  * words), Box-Muller on the four uniforms (w + 1/2) 2^-32: (u0, u1) give the
  * x and y components, (u2, u3) the z component. The inner-step counter
  * starts at 0 at dmts_set_state and advances by n_inner per outer step.
+ * A thermostatted run resumed from dmts_get_state (in this or a new
+ * context) therefore needs a new seed: with the same seed the restarted
+ * counter would draw the first segment's noise again. NVE runs resume
+ * exactly.
  * "concurrent_models" (default 1): with fresh neighbour lists, the outer
  * step's large-model evaluation and the last inner step's small-model
  * evaluation (same positions, independent) run on two streams of the step
