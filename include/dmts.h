@@ -121,8 +121,11 @@ typedef struct {
 
 /* Create a context on the current CUDA device (Algorithm 1's two force
  * fields, masses and boxes). small may be NULL: then dmts_respa_step runs
- * single-time-step velocity Verlet with the big model. options: NULL or a
- * JSON object; recognised keys: "edge_capacity_factor" (default 1.5, the
+ * single-time-step velocity Verlet with the big model. options: NULL, "" or
+ * a flat JSON object of numbers and booleans (true = 1, false = 0); a key
+ * other than those below, a repeated key, another kind of value or
+ * malformed JSON is DMTS_ERR_ARG, checked before any device work.
+ * Keys: "edge_capacity_factor" (default 1.5, the
  * neighbour-pair capacity relative to the uniform-density estimate),
  * "row_capacity" (initial per-atom neighbour capacity; it grows on demand),
  * "cell_capacity" (initial atoms per cell of the cell list with skin 0; it
@@ -166,6 +169,9 @@ typedef struct {
  * the inner steps they replace), and the small model is evaluated at the end
  * (the paper's temporary reversion to the single-time-step integrator). The
  * monitor statistics (dmts_monitor) are gathered with or without it.
+ * "atom_tensor_cores" (default 1): in DMTS_BF16_MLP mode, the per-atom MLPs
+ * of models with F >= 64 run on the tensor cores with each operand split
+ * into two BF16 parts (near-FP32 results); 0 keeps them on the FP32 kernels.
  * On success *out holds the new context; on failure *out is NULL. */
 DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big,
                 const dmts_system_desc* sys, const char* options, dmts_ctx** out);

@@ -67,16 +67,83 @@ int fail(int code, const char* fmt, ...) {
                         "%s: %s", #expr, cudaGetErrorString(e_));                        \
     } while (0)
 
-double json_number(const char* js, const char* key, double dflt) {
-    if (!js) return dflt;
-    std::string k = std::string("\"") + key + "\"";
-    const char* p = strstr(js, k.c_str());
-    if (!p) return dflt;
-    p = strchr(p + k.size(), ':');
-    if (!p) return dflt;
-    char* end = nullptr;
-    double v = strtod(p + 1, &end);
-    return end == p + 1 ? dflt : v;
+// Context options: a flat JSON object whose values are numbers or booleans
+// (true = 1, false = 0), e.g. {"skin": 1.0, "autotune": false}. The whole
+// string is checked before any device work: malformed JSON, a key that is
+// not an option, a repeated key, or another kind of value is an argument
+// error, so a misspelt option cannot pass unnoticed.
+constexpr const char* kOptionKeys[] = {
+    "atom_tensor_cores", "atoms_per_cta_big", "atoms_per_cta_small", "autotune", "cell_capacity",
+    "concurrent_models", "edge_capacity_factor", "fallback_threshold", "langevin_friction", "row_capacity",
+    "seed", "skin", "temperature"};
+
+struct Options {
+    std::vector<std::pair<std::string, double>> kv;
+    double get(const char* key, double dflt) const {
+        for (const auto& e : kv)
+            if (e.first == key) return e.second;
+        return dflt;
+    }
+};
+
+int parse_options(const char* js, Options& out) {
+    out.kv.clear();
+    if (!js) return DMTS_OK;
+    const char* p = js;
+    auto ws = [&p] { while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') ++p; };
+    ws();
+    if (!*p) return DMTS_OK;                                   // empty string: no options
+    if (*p != '{') return fail(DMTS_ERR_ARG, "options: a JSON object was expected");
+    ++p;
+    ws();
+    if (*p == '}') {
+        ++p;
+        ws();
+        return *p ? fail(DMTS_ERR_ARG, "options: text after the closing brace") : DMTS_OK;
+    }
+    for (;;) {
+        if (*p != '"') return fail(DMTS_ERR_ARG, "options: a quoted key was expected at offset %d", (int)(p - js));
+        const char* k0 = ++p;
+        while (*p && *p != '"' && *p != '\\') ++p;
+        if (*p != '"') return fail(DMTS_ERR_ARG, "options: unterminated key or escape in a key");
+        const std::string key(k0, p - k0);
+        ++p;
+        bool known = false;
+        for (const char* k : kOptionKeys) known = known || key == k;
+        if (!known) return fail(DMTS_ERR_ARG, "options: unknown key \"%s\"", key.c_str());
+        for (const auto& e : out.kv)
+            if (e.first == key) return fail(DMTS_ERR_ARG, "options: key \"%s\" repeated", key.c_str());
+        ws();
+        if (*p != ':') return fail(DMTS_ERR_ARG, "options: ':' expected after \"%s\"", key.c_str());
+        ++p;
+        ws();
+        double v = 0.0;
+        if (strncmp(p, "true", 4) == 0) {
+            v = 1.0;
+            p += 4;
+        } else if (strncmp(p, "false", 5) == 0) {
+            v = 0.0;
+            p += 5;
+        } else if (*p == '-' || (*p >= '0' && *p <= '9')) {
+            char* end = nullptr;
+            v = strtod(p, &end);
+            if (end == p || !isfinite(v)) return fail(DMTS_ERR_ARG, "options: bad number for \"%s\"", key.c_str());
+            p = end;
+        } else {
+            return fail(DMTS_ERR_ARG, "options: \"%s\" must be a number or a boolean", key.c_str());
+        }
+        out.kv.emplace_back(key, v);
+        ws();
+        if (*p == ',') {
+            ++p;
+            ws();
+            continue;
+        }
+        if (*p != '}') return fail(DMTS_ERR_ARG, "options: ',' or '}' expected after \"%s\"", key.c_str());
+        ++p;
+        ws();
+        return *p ? fail(DMTS_ERR_ARG, "options: text after the closing brace") : DMTS_OK;
+    }
 }
 
 struct Model {
@@ -1108,6 +1175,8 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
         if (sys->species[i] < 0 || sys->species[i] >= S_min) return fail(DMTS_ERR_ARG, "species[%d] out of range", i);
         if (!(sys->mass[i] > 0) || !isfinite(sys->mass[i])) return fail(DMTS_ERR_ARG, "mass[%d] must be > 0", i);
     }
+    Options opt;
+    if ((rc = parse_options(options, opt))) return rc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -1122,27 +1191,27 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     c->h_off.assign(sys->atom_offset, sys->atom_offset + ns + 1);
     c->h_box.assign(sys->box, sys->box + ns);
     c->rc_max = rc_max;
-    c->autotune = json_number(options, "autotune", 1.0) != 0.0;
-    c->cap_factor = json_number(options, "edge_capacity_factor", 1.5);
+    c->autotune = opt.get("autotune", 1.0) != 0.0;
+    c->cap_factor = opt.get("edge_capacity_factor", 1.5);
     if (!(c->cap_factor > 0.0)) c->cap_factor = 1.5;
-    const double opt_row_cap = json_number(options, "row_capacity", 0.0);
-    const double opt_cell_cap = json_number(options, "cell_capacity", 0.0);
-    c->skin = json_number(options, "skin", 0.0);
+    const double opt_row_cap = opt.get("row_capacity", 0.0);
+    const double opt_cell_cap = opt.get("cell_capacity", 0.0);
+    c->skin = opt.get("skin", 0.0);
     if (!(c->skin >= 0.0) || c->skin > 10.0) {
         delete c;
         return fail(DMTS_ERR_ARG, "skin must be in [0, 10] A");
     }
     c->vl_thr2 = 0.25 * c->skin * c->skin * (1.0 - 2e-3);
-    c->friction_ps = json_number(options, "langevin_friction", 0.0);
-    c->temperature = json_number(options, "temperature", 300.0);
-    const double seed_d = json_number(options, "seed", 0.0);
+    c->friction_ps = opt.get("langevin_friction", 0.0);
+    c->temperature = opt.get("temperature", 300.0);
+    const double seed_d = opt.get("seed", 0.0);
     if (!(c->friction_ps >= 0.0) || !(c->temperature >= 0.0) || !(seed_d >= 0.0) || seed_d > 9.0e15 ||
         !isfinite(c->friction_ps) || !isfinite(c->temperature)) {
         delete c;
         return fail(DMTS_ERR_ARG, "langevin_friction and temperature must be >= 0, seed in [0, 9e15]");
     }
     c->seed = (unsigned long long)seed_d;
-    c->fb_threshold = json_number(options, "fallback_threshold", 0.0);
+    c->fb_threshold = opt.get("fallback_threshold", 0.0);
     if (!(c->fb_threshold >= 0.0)) {
         delete c;
         return fail(DMTS_ERR_ARG, "fallback_threshold must be >= 0 (eV/A)");
@@ -1193,8 +1262,8 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(cudaStreamCreateWithFlags(&c->s_big, cudaStreamNonBlocking));
     CREATE_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CREATE_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    c->concurrent = json_number(options, "concurrent_models", 1.0) != 0.0;
-    c->atom_tc = json_number(options, "atom_tensor_cores", 1.0) != 0.0;
+    c->concurrent = opt.get("concurrent_models", 1.0) != 0.0;
+    c->atom_tc = opt.get("atom_tensor_cores", 1.0) != 0.0;
     CREATE_TRY(dalloc(&c->d_mon, 1));
     CREATE_TRY(cudaMemset(c->d_mon, 0, sizeof(ForceMonitor)));
     if (c->fb_threshold > 0.0) {
@@ -1221,13 +1290,13 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     if (small) {
         rc = init_model(c, c->m[0], small, c->skin <= 0 || c->vl_src == 0);
         if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
-        c->m[0].apc_fwd = std::min(c->m[0].apc_fwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_fwd));
-        c->m[0].apc_bwd = std::min(c->m[0].apc_bwd, (int)json_number(options, "atoms_per_cta_small", c->m[0].apc_bwd));
+        c->m[0].apc_fwd = std::min(c->m[0].apc_fwd, (int)opt.get("atoms_per_cta_small", c->m[0].apc_fwd));
+        c->m[0].apc_bwd = std::min(c->m[0].apc_bwd, (int)opt.get("atoms_per_cta_small", c->m[0].apc_bwd));
     }
     rc = init_model(c, c->m[1], big, c->skin <= 0 || c->vl_src == 1);
     if (rc) { std::string k = g_err; dmts_destroy(c); g_err = k; return rc; }
-    c->m[1].apc_fwd = std::min(c->m[1].apc_fwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_fwd));
-    c->m[1].apc_bwd = std::min(c->m[1].apc_bwd, (int)json_number(options, "atoms_per_cta_big", c->m[1].apc_bwd));
+    c->m[1].apc_fwd = std::min(c->m[1].apc_fwd, (int)opt.get("atoms_per_cta_big", c->m[1].apc_fwd));
+    c->m[1].apc_bwd = std::min(c->m[1].apc_bwd, (int)opt.get("atoms_per_cta_big", c->m[1].apc_bwd));
     for (int w = 0; w < 2; ++w) {
         if (c->m[w].present && opt_row_cap >= 1.0) {
             // smaller initial row capacity (exercises the overflow-and-retry path)

@@ -1,6 +1,7 @@
 """The C ABI library builds, loads and exports every declared symbol; argument
 validation that needs no GPU (CPU only, no compute calls)."""
 import ctypes
+import json
 import os
 import re
 
@@ -114,3 +115,90 @@ def test_hmr_masses_rejects_bad_input(lib):
         D.hmr_masses(np.array([16.0, 1.0]), np.array([[0, 2]]))
     with pytest.raises(D.DmtsError):
         D.hmr_masses(np.array([2.0, 1.0]), np.array([[0, 1]]), h_mass=3.5)
+
+
+# ------------------------------------------------------------------ options
+
+def _create_rc(lib, options):
+    """dmts_create on 192 waters with `options`; returns its status (a
+    context created on a machine with a GPU is destroyed at once)."""
+    arch = I.big_arch()
+    p = I.init_params(arch, 3)
+    big = D.ModelDesc(arch.cutoff, arch.n_radial, arch.n_layers, arch.n_feat, arch.n_species,
+                      p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, 0)
+    s = I.water_192(0)
+    off = np.array([0, s.n_atoms], np.int32)
+    sp = s.species.astype(np.int32).copy()
+    ms = s.mass.copy()
+    bx = np.array(s.box, dtype=np.float64)
+    sd = D.SystemDesc(1, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      sp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    out = ctypes.c_void_p()
+    rc = lib.dmts_create(None, ctypes.byref(big), ctypes.byref(sd),
+                         options.encode() if options is not None else None, ctypes.byref(out))
+    if rc == 0:
+        lib.dmts_destroy(out)
+    return rc
+
+
+# every option set the tests and the benchmark pass, and the documented forms
+GOOD_OPTIONS = [
+    None, "", "  ", "{}", ' { } ',
+    '{"autotune": 0}', '{"autotune": false}', '{"autotune": true, "concurrent_models": false}',
+    json.dumps({"langevin_friction": 20.0, "temperature": 300.0, "seed": 12345, "autotune": 0}),
+    json.dumps({"langevin_friction": 1.0, "temperature": 300.0, "seed": 7, "fallback_threshold": 6.505}),
+    json.dumps({"fallback_threshold": 1e-9, "langevin_friction": 1.0, "seed": 5}),
+    '{"row_capacity": 4, "edge_capacity_factor": 0.05, "cell_capacity": 2}',
+    json.dumps({"skin": 1.0, "autotune": 0, "row_capacity": 8}),
+    json.dumps({"atom_tensor_cores": 0}), json.dumps({"atom_tensor_cores": True}),
+    '{"atoms_per_cta_big": 8, "atoms_per_cta_small": 16}',
+    '{\n  "skin": 2e0,\n  "seed": 0\n}',
+]
+
+BAD_OPTIONS = [
+    '{"autotun": 0}',                          # misspelt key
+    '{"Skin": 1.0}',                           # keys are case-sensitive
+    '{"skin": "1.0"}',                         # string value
+    '{"skin": null}',
+    '{"skin": [1]}',
+    '{"skin": 1.0, "skin": 2.0}',              # repeated key
+    '{"skin": 1.0',                            # unterminated object
+    '{"skin" 1.0}',
+    '{"skin": 1.0,}',                          # trailing comma
+    '{"skin": 1.0} x',                         # text after the object
+    '"skin": 1.0',
+    '{skin: 1.0}',
+    '{"skin": .5}',
+    '{"skin": nan}',
+    '{"skin": 1e999}',                         # not finite
+    '{"ski\\n": 1}',                           # escapes are not option keys
+]
+
+
+@pytest.mark.parametrize("opts", GOOD_OPTIONS)
+def test_options_accepted(lib, opts):
+    """Accepted options pass on to the device check: DMTS_ERR_CUDA without a
+    GPU, success with one."""
+    assert _create_rc(lib, opts) in (0, -3), lib.dmts_last_error()
+
+
+@pytest.mark.parametrize("opts", BAD_OPTIONS)
+def test_options_rejected_before_device_use(lib, opts):
+    assert _create_rc(lib, opts) == -1
+    assert b"options" in lib.dmts_last_error()
+
+
+def test_option_keys_match_the_header():
+    """Every option key the library accepts is documented in the header, and
+    every quoted key the header documents as an option is accepted."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "paper_2510_06562_gb300", "csrc", "dmts.cu")).read()
+    block = src[src.index("kOptionKeys[] = {"):]
+    keys = set(re.findall(r'"([a-z_]+)"', block[:block.index("};")]))
+    header = open(os.path.join(root, "include", "dmts.h")).read()
+    for k in keys:
+        assert f'"{k}"' in header, k
+    assert len(keys) == 13
