@@ -58,6 +58,18 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def step_config(args, s, precision: str, parallelism: str) -> dict:
+    """The timed workload: the water box by name and size, the RESPA split,
+    the two models and how the step is measured."""
+    return {"workload": f"{args.workload}: {s.n_atoms // 3:,} rigid waters, {s.n_atoms:,} atoms, "
+                        f"L={s.box[0]:.1f} A, periodic",
+            "outer_fs": args.outer_fs, "inner_fs": args.outer_fs / args.n_inner, "n_inner": args.n_inner,
+            "precision": precision,
+            "small_model": "3.5 A, K=8, 1 layer, F=32", "big_model": "5.0 A, K=16, 2 layers, F=64",
+            "state": "FP64 x, v",
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": parallelism}
+
+
 def models(n_species: int):
     from paper_2510_06562_gb300 import inputs as I
     return (I.small_arch(n_species), I.init_params(I.small_arch(n_species), 2),
@@ -332,12 +344,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_prec == D.BF16_MLP else "f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 4,096 rigid waters, 12,288 atoms, L=49.7 A, periodic",
-                   "outer_fs": dt, "inner_fs": dt / n_inner, "n_inner": n_inner,
-                   "precision": args.precision + (" (MLP operands; FP32 accumulation, geometry, sums)" if args.precision == "bf16" else ""),
-                   "small_model": "3.5 A, K=8, 1 layer, F=32", "big_model": "5.0 A, K=16, 2 layers, F=64",
-                   "state": "FP64 x, v",
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
+        "config": step_config(args, s, args.precision + (" (MLP operands; FP32 accumulation, geometry, sums)"
+                                                         if args.precision == "bf16" else ""), f"replicas{world}"),
         "atom_force_evals_per_s": m["atom_force_evals_per_s"], "sts_1fs_ns_per_day": m["sts_1fs_ns_per_day"],
         "speedup_vs_sts": m["dmts_ns_per_day"] / m["sts_1fs_ns_per_day"],
         "dmts_6fs_ns_per_day": m["dmts_6fs_ns_per_day"],
@@ -498,8 +506,8 @@ def run_reference(args):
     return {"metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": len(times),
             "warmup": 1, "ms_per_step": t * 1e3 / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.workload}: 4,096 rigid waters, 12,288 atoms, L=49.7 A, periodic",
-                       "outer_fs": dt, "inner_fs": dt / n_inner, "n_inner": n_inner, "precision": "fp64"},
+            "config": dict(step_config(args, s, "fp64 (the oracle on the host cores)", "host, one process"),
+                           l2="not applicable (host)"),
             "cpu_baseline": {"value": value, "unit": "ns/day", "cores": torch.get_num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

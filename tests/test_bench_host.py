@@ -73,3 +73,38 @@ def test_roofline_arithmetic():
     assert r["algorithmic_flop_per_launch"] == 2 * (8 * 64 + 64 * 64) * E
     assert r["bound"] == "alu"
     assert abs(r["peak"] - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def _run_bench(*argv, env=None):
+    import subprocess
+    import sys
+    e = dict(os.environ, **(env or {}))
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), *argv], capture_output=True,
+                       text=True, timeout=600, env=e)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stdout
+
+
+def test_reference_arm_line_on_the_small_box():
+    """The reference arm times the FP64 oracle on the host cores and prints
+    the same metric, unit and workload as the CUDA arm, with its own
+    cpu_baseline and an e2e that moves no bytes."""
+    import json
+    out = _run_bench("--impl", "reference", "--workload", "water192", "--steps", "1", "--warmup", "0")
+    lines = [ln for ln in out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "ns/day"
+    assert d["higher_is_better"] is True and d["dtype"] == "f64" and d["steps"] == 1
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 3.0 / d["value"] * 86.4) < 1e-6 * d["ms_per_step"]
+    assert d["config"]["workload"].startswith("water192: 64 rigid waters, 192 atoms, L=12.4 A")
+    assert d["config"]["n_inner"] == 3 and d["config"]["inner_fs"] == 1.0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "192-atom" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    out = _run_bench("--impl", "reference", "--workload", "water192", "--steps", "1",
+                     env={"RANK": "1", "WORLD_SIZE": "2"})
+    assert out.strip() == ""
