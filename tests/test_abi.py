@@ -202,3 +202,25 @@ def test_option_keys_match_the_header():
     for k in keys:
         assert f'"{k}"' in header, k
     assert len(keys) == 13
+
+
+def test_options_parser_survives_arbitrary_text(lib):
+    """Whatever the options string, dmts_create returns a status: an
+    argument error, or (valid options) the device check's result."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    keys = ["skin", "autotune", "seed", "temperature", "cell_capacity", "bogus", ""]
+    values = st.one_of(st.floats(allow_nan=True, allow_infinity=True).map(repr), st.integers().map(str),
+                       st.sampled_from(["true", "false", "null", '"x"', "[]", "{}", "-", "1e", ".5", "0x10"]))
+    pairs = st.lists(st.tuples(st.sampled_from(keys), values), max_size=4)
+    objects = pairs.map(lambda kv: "{" + ", ".join(f'"{k}": {v}' for k, v in kv) + "}")
+    texts = st.one_of(st.text(max_size=40), objects, objects.map(lambda s: s[:-1]), objects.map(lambda s: s + ","))
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(texts)
+    def check(opts):
+        if "\x00" in opts:
+            return                                   # a C string ends at the first NUL
+        assert _create_rc(lib, opts) in (-1, -3, 0)
+
+    check()
