@@ -1,10 +1,10 @@
 """FP64 oracle of the integrators (test infrastructure only).
 
-* ``respa`` is Algorithm 1 (the MTS integration step with force splitting)
-  step by step, with the thermostat ``thermo`` the identity (NVE): an outer
-  half-kick with the force difference F - F_small, n_slow inner steps of
-  kick / half-drift / (thermostat) / half-drift / small force / kick, then the
-  large force and a second half-kick with F - F_small.
+* ``respa`` is the multiple-time-step integrator of Algorithm 1, written
+  from its force splitting: the small model's force is the fast part, taken
+  by n_inner velocity-Verlet substeps per outer step, and the remainder
+  F - F_small is the slow part, applied as half-kicks at both ends of the
+  outer step (NVE when ``thermo`` is None).
 * ``velocity_verlet`` is the textbook single-time-step scheme: half-kick,
   full drift, force, half-kick.
 * With ``thermo`` given, both become Langevin schemes: Algorithm 1's
@@ -19,7 +19,7 @@
   active-learning section: after each outer step, if some atom's
   |F - F_small| exceeds the threshold (150 kcal/mol/A in the paper), the step
   is redone from its starting state with the single-time-step integrator
-  (n_slow velocity-Verlet or BAOAB steps of dt / n_slow with the large model),
+  (n_inner velocity-Verlet or BAOAB steps of dt / n_inner with the large model),
   and the small model is evaluated at the end for the next step's kicks.
 
 Positions of periodic systems are wrapped into [0, L) after every drift
@@ -157,17 +157,41 @@ def velocity_verlet(x, v, mass, f: Force, dt: float, n_steps: int,
     return x, v, F
 
 
-def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int,
+def _kick(v, a, tau: float, F):
+    """Velocity update by force F over time tau: v + tau F / m."""
+    return v + tau * a * F
+
+
+def _fast_substep(x, v, a, mass, h: float, F_fast, f_fast: Force, box_per_atom, thermo, step: int):
+    """One substep of length h under the fast force alone: half-kick, two
+    half-drifts (with the Ornstein-Uhlenbeck velocity update between them
+    when ``thermo`` is given, drawing its noise at counter ``step``), the
+    fast force at the new positions, half-kick. Returns (x, v, F_fast)."""
+    v = _kick(v, a, 0.5 * h, F_fast)
+    x = _wrap(x + (0.5 * h) * v, box_per_atom)
+    if thermo is not None:
+        v = o_step(v, mass, h, thermo, step)
+    x = _wrap(x + (0.5 * h) * v, box_per_atom)
+    F_fast = f_fast(x)
+    v = _kick(v, a, 0.5 * h, F_fast)
+    return x, v, F_fast
+
+
+def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_inner: int,
           n_outer: int, box_per_atom=None, F_small=None, F=None,
           energy_big: Callable[[np.ndarray], float] | None = None,
           atom_offset=None, thermo: dict | None = None, step0: int = 0):
-    """n_outer steps of Algorithm 1 with outer step dt and n_slow inner steps
-    of dt / n_slow. thermo = None: the identity (NVE); else the O-step
-    (``o_step``) with inner step j of outer step s drawing its noise at
-    counter step0 + s n_slow + j.
+    """n_outer outer steps of the multiple-time-step scheme of Algorithm 1.
+
+    The large model's force is split as F = F_small + (F - F_small): the
+    small model's force is the fast part, integrated by n_inner substeps of
+    h = dt / n_inner (``_fast_substep``); the remainder is the slow part,
+    applied as a half-kick of dt / 2 before and after them. thermo = None:
+    NVE; else substep j of outer step s draws its noise at counter
+    step0 + s n_inner + j.
 
     ``F_small`` and ``F`` carry the forces at ``x`` between calls; when either
-    is None this is the algorithm's first step and both are evaluated.
+    is None they are evaluated first (a start at new positions).
     Returns (x, v, F_small, F, energies) where energies is [n_outer, 3] with
     (E_pot of the big model, E_kin, E_pot + E_kin) after each outer step if
     ``energy_big`` is given, else None.
@@ -176,23 +200,18 @@ def respa(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int,
     v = np.array(v, dtype=np.float64)
     mass = np.asarray(mass, dtype=np.float64)
     a = ACCEL / mass[:, None]
-    if F_small is None or F is None:                        # first_step
+    if F_small is None or F is None:
         F_small = f_small(x)
         F = f_big(x)
-    h = dt / n_slow
+    h = dt / n_inner
     out = []
     for s in range(n_outer):
-        v = v + (0.5 * dt) * a * (F - F_small)
-        for j in range(n_slow):
-            v = v + (0.5 * h) * a * F_small
-            x = _wrap(x + (0.5 * h) * v, box_per_atom)
-            if thermo is not None:                          # v <- thermo(v, h)
-                v = o_step(v, mass, h, thermo, step0 + s * n_slow + j)
-            x = _wrap(x + (0.5 * h) * v, box_per_atom)
-            F_small = f_small(x)
-            v = v + (0.5 * h) * a * F_small
+        v = _kick(v, a, 0.5 * dt, F - F_small)                   # slow half-kick
+        for j in range(n_inner):
+            x, v, F_small = _fast_substep(x, v, a, mass, h, F_small, f_small, box_per_atom, thermo,
+                                          step0 + s * n_inner + j)
         F = f_big(x)
-        v = v + (0.5 * dt) * a * (F - F_small)
+        v = _kick(v, a, 0.5 * dt, F - F_small)                   # slow half-kick
         if energy_big is not None:
             ep = np.asarray(energy_big(x), dtype=np.float64).reshape(-1)
             ek = kinetic_energy(v, mass, atom_offset)
@@ -207,27 +226,31 @@ def force_difference_norms(F, F_small):
     return np.sqrt((d * d).sum(axis=1))
 
 
-def respa_monitored(x, v, mass, f_small: Force, f_big: Force, dt: float, n_slow: int, n_outer: int,
-                    threshold: float, box_per_atom=None, thermo: dict | None = None, step0: int = 0):
+def respa_monitored(x, v, mass, f_small: Force, f_big: Force, dt: float, n_inner: int, n_outer: int,
+                    threshold: float, box_per_atom=None, thermo: dict | None = None, step0: int = 0,
+                    df_out: list | None = None):
     """n_outer outer steps of Algorithm 1 with the force-difference monitor
     and single-time-step fallback. Returns (x, v, F_small, F, n_fallback,
     max_df) with max_df the largest |F - F_small| seen at the end of an
-    outer step (before any fallback)."""
+    outer step (before any fallback). If ``df_out`` is a list, each outer
+    step's largest |F - F_small| is appended to it."""
     x = np.array(x, dtype=np.float64)
     v = np.array(v, dtype=np.float64)
     F_small = f_small(x)
     F = f_big(x)
-    h = dt / n_slow
+    h = dt / n_inner
     n_fallback, max_df = 0, 0.0
     for s_ in range(n_outer):
-        t0 = step0 + s_ * n_slow
-        x1, v1, Fs1, F1, _ = respa(x, v, mass, f_small, f_big, dt, n_slow, 1, box_per_atom=box_per_atom,
+        t0 = step0 + s_ * n_inner
+        x1, v1, Fs1, F1, _ = respa(x, v, mass, f_small, f_big, dt, n_inner, 1, box_per_atom=box_per_atom,
                                    F_small=F_small, F=F, thermo=thermo, step0=t0)
         df = force_difference_norms(F1, Fs1).max()
+        if df_out is not None:
+            df_out.append(float(df))
         max_df = max(max_df, df)
         if df > threshold:
             n_fallback += 1
-            x1, v1, F1 = velocity_verlet(x, v, mass, f_big, h, n_slow, box_per_atom=box_per_atom, F=F,
+            x1, v1, F1 = velocity_verlet(x, v, mass, f_big, h, n_inner, box_per_atom=box_per_atom, F=F,
                                          thermo=thermo, step0=t0)
             Fs1 = f_small(x1)
         x, v, F_small, F = x1, v1, Fs1, F1
