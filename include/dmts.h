@@ -178,8 +178,15 @@ DMTS_API int dmts_create(const dmts_model_desc* small, const dmts_model_desc* bi
 
 /* Set positions x[N*3] and velocities v[N*3] (NULL: zero velocities).
  * Periodic positions are wrapped into [0, L) as x - L floor(x / L).
- * Invalidates the cached forces: the next dmts_respa_step evaluates both
- * models first (Algorithm 1's first_step). n_atoms must equal N. */
+ * If a wrapped position differs, bit for bit, from the context's current
+ * one, the cached forces become invalid and the next dmts_respa_step
+ * evaluates both models first (Algorithm 1's first_step). If every position
+ * is unchanged (e.g. a caller that reads the state back after each call and
+ * uploads it again, or changes only velocities), the forces cached at those
+ * positions are kept: they depend on positions only, and every evaluation
+ * is deterministic, so recomputing them would give the same bits. The
+ * thermostat's inner-step counter restarts at 0 either way. n_atoms must
+ * equal N. */
 DMTS_API int dmts_set_state(dmts_ctx* ctx, const double* x, const double* v, int n_atoms);
 
 /* Read back positions and velocities (either pointer may be NULL). */
@@ -205,7 +212,13 @@ DMTS_API int dmts_respa_step(dmts_ctx* ctx, int n_outer, double dt_outer_fs, int
 /* Destroy a context and free its device memory. NULL is a no-op. */
 DMTS_API void dmts_destroy(dmts_ctx* ctx);
 
-/* Message describing the calling thread's last error ("" if none). */
+/* Message describing the calling thread's last error ("" if none).
+ * DMTS_ERR_TIMEOUT: a bounded device-side wait (the tensor-core kernels'
+ * completion waits) gave up. The kernel stopped early, so that call's
+ * results are invalid; dmts_respa_step restores the state it started from.
+ * If the work the kernel had in flight finished, the context stays usable
+ * (the cached forces are invalidated); if that did not finish in time
+ * either, later calls return DMTS_ERR_STATE. */
 DMTS_API const char* dmts_last_error(void);
 
 /* Neighbour pairs of one model at the current positions, in CSR form:
@@ -266,6 +279,11 @@ DMTS_API int dmts_neighbor_stats(dmts_ctx* ctx, long long* n_checks, long long* 
  * if not yet, or a negative status. */
 DMTS_API int dmts_get_tuning(dmts_ctx* ctx, int which, int* atoms_fwd, int* atoms_bwd);
 
+/* Set one model's work granularity (as reported by dmts_get_tuning), clamped
+ * to what the kernels support, and keep it: the tuner then leaves the context
+ * alone. fwd, bwd >= 1. Results do not depend on the choice. */
+DMTS_API int dmts_set_tuning(dmts_ctx* ctx, int which, int fwd, int bwd);
+
 /* Time one model's force evaluation at the current positions, stage by stage,
  * with CUDA events on the context's stream, averaged over reps (>= 1)
  * evaluations. ms_out[n_out] receives milliseconds per evaluation for:
@@ -297,6 +315,27 @@ DMTS_API int dmts_force_matching_grad(dmts_ctx* ctx, int n_frames, const double*
                                       const double* f_ref, double* loss_out, double* grad_out);
 
 /* ------------------------------------------------------------------------
+ * Diagnostics (the paper has no counterpart).
+ *
+ * dmts_wait_selftest: one thread block on the context's stream allocates
+ * tensor memory, waits on an mbarrier through the same bounded wait as the
+ * tensor-core force kernels (at most max_polls polls, 1 <= max_polls <=
+ * 2^22), frees the tensor memory and reports through the same device flag.
+ * arrive = 1: a thread arrives first and the wait completes (DMTS_OK);
+ * arrive = 0: nothing arrives, the wait gives up and the call returns
+ * DMTS_ERR_TIMEOUT. No MMA is issued, so nothing is left in flight and the
+ * context stays usable. It touches no state or cached force.
+ *
+ * dmts_philox4x32_10: the thermostat's noise generator (Philox-4x32 with 10
+ * rounds; Salmon, Moraes, Dror and Shaw, SC 2011) run on the current device
+ * for n counters ctr[n][4] under key[2] (host arrays of 32-bit words);
+ * out[n][4] receives the raw output words, for comparison with the
+ * generator's published known-answer vectors. Needs no context; allocates
+ * and frees two small device buffers. */
+DMTS_API int dmts_wait_selftest(dmts_ctx* ctx, int arrive, int max_polls);
+DMTS_API int dmts_philox4x32_10(int n, const unsigned int* ctr, const unsigned int* key, unsigned int* out);
+
+/* ------------------------------------------------------------------------
  * Allocation-free neighbour list. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- an MD engine
  * that owns all device memory through its own pool and hands plug-ins
@@ -322,7 +361,10 @@ DMTS_API int dmts_force_matching_grad(dmts_ctx* ctx, int n_frames, const double*
  * pairs exceed capacity (row_ptr and *n_pairs are still written).
  * The first call on a device resolves the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the one array, so calls whose
+ * before any stream capture. The address is kept for the life of the
+ * process, so do not reset a device (cudaDeviceReset) on which this entry
+ * point has been called: the module would be loaded again, possibly at
+ * another address. All calls share the one array, so calls whose
  * work overlaps on the GPU (other streams, other host threads) race: issue
  * them one at a time per device. */
 #define DMTS_NOALLOC_MAX_ATOMS 16384

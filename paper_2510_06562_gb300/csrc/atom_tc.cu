@@ -404,17 +404,21 @@ __global__ void __launch_bounds__(kA * (F / 16)) k_atom_tc(PotArgs p, const floa
     fence_before_sync();
     __syncthreads();
     if (ok && out_dst) rows_out<F, NT>(out_dst + roff, S.io[out_buf], nrows);
+    bool drained = true;                               // status bit 1: something still in flight
     if (x == 0) {
         while (waited < issued) {
-            if (!mbar_wait(&S.mbar_b[waited & 1], (uint32_t)((waited >> 1) & 1), kWait)) break;
+            if (!mbar_wait(&S.mbar_b[waited & 1], (uint32_t)((waited >> 1) & 1), kWait)) {
+                drained = false;
+                break;
+            }
             ++waited;
         }
-        if (mma_out) (void)mbar_wait(&S.mbar_mma, ph ^ 1u, kWait);
+        if (mma_out && !mbar_wait(&S.mbar_mma, ph ^ 1u, kWait)) drained = false;
     }
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(S.taddr, 2 * F);
-    if (!ok && x == 0) atomicOr(status, 1);
+    if (!ok && x == 0) atomicOr(status, drained ? 1 : 3);
 }
 
 template <int F>

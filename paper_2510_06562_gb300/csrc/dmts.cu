@@ -808,9 +808,17 @@ int sync_check(dmts_ctx* c) {
         return fail(DMTS_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
     }
     CUDA_TRY(cudaMemcpy(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost));
-    if (c->h_flags[kFlagTimeout]) {
-        c->broken = true;
-        return fail(DMTS_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    if (const int t = c->h_flags[kFlagTimeout]) {
+        // bit 0: a bounded wait gave up and its kernel stopped early (results
+        // invalid); bit 1: work it had in flight did not finish in time either
+        if (t & 2) {
+            c->broken = true;
+            return fail(DMTS_ERR_TIMEOUT, "a completion wait gave up and in-flight work did not drain");
+        }
+        c->forces_valid = false;
+        CUDA_TRY(cudaMemsetAsync(c->d_flags + kFlagTimeout, 0, sizeof(int), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        return fail(DMTS_ERR_TIMEOUT, "a bounded completion wait gave up");
     }
     return DMTS_OK;
 }
@@ -1030,12 +1038,13 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
 }
 
 // Autotuner: times one force evaluation of each model for a few work
-// granularities (atoms per CTA for the FP32 kernels, atoms per chunk for the
-// persistent tensor-core kernels) and keeps the fastest. The FP32 kernels sum
-// every atom's row in edge order whatever the granularity, so their results
-// do not change; the tensor-core kernels group a row's partial sums by tile,
-// so theirs can change at the rounding level. Runs once per context, at the
-// first evaluation.
+// granularities (atoms per CTA for the FP32 kernels, persistent CTAs per SM
+// for the tensor-core kernels) and keeps the fastest forward and backward
+// edge pass. The FP32 kernels sum every atom's row in edge order whatever the
+// granularity; the tensor-core kernels cut the pair list into the same fixed
+// 128-pair tiles whatever the grid and sum split rows in tile order. So the
+// results are bit-identical for every candidate. Runs once per context, at
+// the first evaluation.
 int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc);
 
 int autotune_models(dmts_ctx* c) {
@@ -1341,12 +1350,16 @@ int dmts_set_state(dmts_ctx* c, const double* x, const double* v, int n_atoms) {
     int rc = copy_in(c, c->d_stage, x, n3);
     if (rc) return rc;
     if (v && (rc = copy_in(c, c->d_stage + n3, v, n3))) return rc;
+    CUDA_TRY(cudaMemsetAsync(c->d_flags + kFlagMoved, 0, sizeof(int), c->stream));
     launch_set_state(c->N, c->d_stage, v ? c->d_stage + n3 : nullptr, c->d_sys, c->d_box, c->d_x, c->d_v,
-                     c->stream);
+                     c->d_flags + kFlagMoved, c->stream);
     CUDA_TRY(cudaMemsetAsync(c->d_rng, 0, sizeof(unsigned long long), c->stream));   // noise restarts at step 0
     if ((rc = sync_check(c))) return rc;
+    // The forces depend on the positions only, and every evaluation of them is
+    // deterministic: forces cached at bit-identical positions stay valid, and
+    // only a change of position makes the next step Algorithm 1's first step.
+    c->forces_valid = c->forces_valid && c->state_set && c->h_flags[kFlagMoved] == 0;
     c->state_set = true;
-    c->forces_valid = false;
     return DMTS_OK;
 }
 
@@ -1466,6 +1479,21 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
             CUDA_TRY(cudaMemcpyAsync(c->d_bfs, c->m[0].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_bfb, c->m[1].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     }
+    // back to the state of the call's entry (after an overflow, or a bounded
+    // wait that gave up)
+    auto restore = [&]() -> int {
+        CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_rng, c->d_rng + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        if (valid0) {
+            if (c->m[0].present)
+                CUDA_TRY(cudaMemcpyAsync(c->m[0].force, c->d_bfs, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(c->m[1].force, c->d_bfb, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        }
+        c->forces_valid = valid0;
+        return DMTS_OK;
+    };
     for (int attempt = 0;; ++attempt) {
         if ((rc = reset_flags(c))) return rc;
         if (!c->forces_valid) {
@@ -1480,7 +1508,14 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             c->launches += c->g_nodes;
         }
-        if ((rc = sync_check(c))) return rc;
+        if ((rc = sync_check(c))) {
+            if (rc == DMTS_ERR_TIMEOUT && !c->broken && restore() == DMTS_OK) {
+                c->forces_valid = false;
+                (void)cudaStreamSynchronize(c->stream);
+                set_error_message("a bounded completion wait gave up; the state of the call's entry is restored");
+            }
+            return rc;
+        }
         if (c->fb_threshold > 0.0 && c->m[0].present) {
             // kernels of the fallback bodies that ran
             unsigned long long nf = 0;
@@ -1491,16 +1526,7 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         if (!c->h_flags[kFlagOverflow]) break;
         if (attempt >= 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
         // restore and retry with grown capacity
-        CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(c->d_rng, c->d_rng + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
-                                 c->stream));
-        if (valid0) {
-            if (c->m[0].present)
-                CUDA_TRY(cudaMemcpyAsync(c->m[0].force, c->d_bfs, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-            CUDA_TRY(cudaMemcpyAsync(c->m[1].force, c->d_bfb, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-        }
-        c->forces_valid = valid0;
+        if ((rc = restore())) return rc;
         if ((rc = grow_capacity(c))) return rc;
     }
     c->forces_valid = true;
@@ -1556,7 +1582,7 @@ int dmts_force_matching_grad(dmts_ctx* c, int n_frames, const double* frames, co
             if (!rc) rc = copy_in(c, c->fm_stage + n3, f_ref + (size_t)fr * n3, n3);
             if (rc) { m.precision = prec; return rc; }
             // frame positions into x (velocities, saved above, are zeroed meanwhile)
-            launch_set_state(N, c->fm_stage, nullptr, c->d_sys, c->d_box, c->d_x, c->d_v, c->stream);
+            launch_set_state(N, c->fm_stage, nullptr, c->d_sys, c->d_box, c->d_x, c->d_v, nullptr, c->stream);
             enqueue_eval(c, 0, true);
             if ((rc = sync_check(c))) { m.precision = prec; return rc; }
             if (!c->h_flags[kFlagOverflow]) break;
@@ -1742,6 +1768,55 @@ int dmts_get_tuning(dmts_ctx* c, int which, int* atoms_fwd, int* atoms_bwd) {
     if (atoms_fwd) *atoms_fwd = tc ? c->m[which].cps_fwd : c->m[which].apc_fwd;
     if (atoms_bwd) *atoms_bwd = tc ? c->m[which].cps_bwd : c->m[which].apc_bwd;
     return c->tuned ? 1 : 0;
+}
+
+int dmts_set_tuning(dmts_ctx* c, int which, int fwd, int bwd) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    Model& m = c->m[which];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (fwd < 1 || bwd < 1) return fail(DMTS_ERR_ARG, "granularity must be >= 1");
+    if (m.precision == DMTS_BF16_MLP) {
+        m.cps_fwd = std::min(fwd, bf16_max_ctas_per_sm(m.F, false));
+        m.cps_bwd = std::min(bwd, bf16_max_ctas_per_sm(m.F, true));
+    } else {
+        m.apc_fwd = std::min(fwd, max_atoms_per_cta_f32(m.F, m.K, false));
+        m.apc_bwd = std::min(bwd, max_atoms_per_cta_f32(m.F, m.K, true));
+    }
+    c->tuned = true;                          // the tuner keeps the caller's choice
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return DMTS_OK;
+}
+
+int dmts_wait_selftest(dmts_ctx* c, int arrive, int max_polls) {
+    CTX_GUARD(c);
+    if (max_polls < 1 || max_polls > (1 << 22)) return fail(DMTS_ERR_ARG, "max_polls must be in [1, 2^22]");
+    LaunchScope ls(c);
+    int rc = reset_flags(c);
+    if (rc) return rc;
+    launch_wait_selftest(arrive ? 1 : 0, (unsigned int)max_polls, c->d_flags + kFlagTimeout, c->stream);
+    const bool valid = c->forces_valid;       // the self-test touches no force or state
+    rc = sync_check(c);
+    if (!c->broken) c->forces_valid = valid;
+    return rc;
+}
+
+int dmts_philox4x32_10(int n, const unsigned int* ctr, const unsigned int* key, unsigned int* out) {
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(DMTS_ERR_ARG, "bad arguments");
+    if (n == 0) return DMTS_OK;
+    uint4 *d_in = nullptr, *d_out = nullptr;
+    CUDA_TRY(dalloc(&d_in, (size_t)n));
+    cudaError_t e = dalloc(&d_out, (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(d_in, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_philox_words(n, d_in, key[0], key[1], d_out, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
+    dfree(d_in);
+    dfree(d_out);
+    if (e != cudaSuccess) return fail(DMTS_ERR_CUDA, "philox: %s", cudaGetErrorString(e));
+    return DMTS_OK;
 }
 
 }  // extern "C"

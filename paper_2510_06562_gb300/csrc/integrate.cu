@@ -39,6 +39,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The generator's raw output for given counters and one key: the words the
+// thermostat's noise is made of, for comparison with published test vectors.
+__global__ void k_philox_words(int n, const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                               uint4* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
 // Three standard normals for atom i at inner step t: uniforms (w + 1/2) 2^-32
 // of the four Philox words, Box-Muller on (u0, u1) for two and on (u2, u3)
 // for the third.
@@ -63,20 +71,30 @@ __device__ __forceinline__ unsigned int fixed_of(double v, double o, double inv)
 
 __global__ void k_set_state(int n, const double* __restrict__ xa, const double* __restrict__ va,
                             const int* __restrict__ sys, const double* __restrict__ box,
-                            double* __restrict__ x, double* __restrict__ v) {
+                            double* __restrict__ x, double* __restrict__ v, int* __restrict__ moved) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double L = box[sys[i]];
+    bool diff = false;
     for (int c = 0; c < 3; ++c) {
-        x[(size_t)c * n + i] = wrap_coord(xa[3 * (size_t)i + c], L);
+        const double w = wrap_coord(xa[3 * (size_t)i + c], L);
+        if (moved) diff = diff || __double_as_longlong(w) != __double_as_longlong(x[(size_t)c * n + i]);
+        x[(size_t)c * n + i] = w;
         v[(size_t)c * n + i] = va ? va[3 * (size_t)i + c] : 0.0;
     }
+    if (diff) atomicOr(moved, 1);
+}
+
+void launch_philox_words(int n, const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, cudaStream_t s) {
+    if (n <= 0) return;
+    k_philox_words<<<(n + 255) / 256, 256, 0, s>>>(n, ctr, k0, k1, out);
+    count_launch();
 }
 
 void launch_set_state(int n_atoms, const double* x_aos, const double* v_aos, const int* sys_of_atom,
-                      const double* box, double* x, double* v, cudaStream_t s) {
+                      const double* box, double* x, double* v, int* moved, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_set_state<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, x_aos, v_aos, sys_of_atom, box, x, v);
+    k_set_state<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, x_aos, v_aos, sys_of_atom, box, x, v, moved);
     count_launch();
 }
 

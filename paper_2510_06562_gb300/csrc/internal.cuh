@@ -54,7 +54,8 @@ enum Flag {
     kFlagMaxVl1 = 9,       // (big)
     kFlagMaxCell0 = 10,    // most atoms placed in one cell, when a cell overflowed (small model)
     kFlagMaxCell1 = 11,    // (big)
-    kFlagCount = 12
+    kFlagMoved = 12,       // dmts_set_state: a position differs from the current one
+    kFlagCount = 13
 };
 
 // Verlet-skin bookkeeping (device memory, one per context). The candidate
@@ -252,6 +253,9 @@ int max_atoms_per_cta_f32(int F, int K, bool bwd);
 // potential_bf16.cu (tensor cores; status receives 1 if a bounded wait gave up)
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s);
+// Self-test of the bounded completion waits (no MMA): status bit 0 is set if
+// the wait of at most `polls` polls gives up; with arrive = 0 nothing arrives.
+void launch_wait_selftest(int arrive, unsigned int polls, int* status, cudaStream_t s);
 size_t bf16_weight_tile_bytes(int F);
 int bf16_max_ctas_per_sm(int F, bool bwd);
 
@@ -286,8 +290,12 @@ void launch_virial_sum(int n_sys, const int* atom_offset, const float* vir6, dou
                        cudaStream_t s);
 
 // integrate.cu
+// Philox-4x32-10 words of n counters under key (k0, k1), as the thermostat draws them.
+void launch_philox_words(int n, const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, cudaStream_t s);
+// moved (or null): set to 1 if some wrapped position differs, bit for bit,
+// from the position it replaces.
 void launch_set_state(int n_atoms, const double* x_aos, const double* v_aos, const int* sys_of_atom,
-                      const double* box, double* x, double* v, cudaStream_t s);
+                      const double* box, double* x, double* v, int* moved, cudaStream_t s);
 void launch_get_state(int n_atoms, const double* x, const double* v, double* x_aos, double* v_aos,
                       cudaStream_t s);
 void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t s);

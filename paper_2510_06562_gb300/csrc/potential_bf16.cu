@@ -37,6 +37,14 @@ constexpr int kT = 128;          // threads per CTA = edges per tile = TMEM lane
 constexpr int kKP = 16;          // radial functions padded to one MMA K step
 constexpr uint32_t kWaitIter = 1u << 22;
 
+// After a completion wait that gave up: the issuing thread waits, again with
+// a bound, for the MMA group it committed last (parity pend) if it has not
+// seen that group complete, so that the tensor memory those MMAs write is not
+// freed under them. Returns false if this wait gives up too.
+__device__ __forceinline__ bool drain_mma(bool mma_out, uint64_t* mbar, uint32_t pend) {
+    return !mma_out || mbar_wait(mbar, pend, kWaitIter);
+}
+
 __device__ __forceinline__ float sigmoid_fast(float x) {
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
@@ -438,6 +446,8 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
     const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t);
     uint32_t phase = 0;
     bool ok = true;
+    bool mma_out = false;                                  // thread 0: a commit not yet seen complete
+    uint32_t pend = 0;                                     // ... and the parity it completes
 
     const int cw = a.carry_w;
     EdgeIn nx;
@@ -483,9 +493,12 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             if (tid == 0) {
                 mma_bf16(tmem, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
                 mma_commit(&S.mbar);
+                mma_out = true;
+                pend = phase;
             }
             load_pos(a, nx);                               // next tile's positions
             ok = mbar_wait(&S.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
             // SiLU(a) as BF16 pairs written back over the first F/2 columns of
@@ -512,8 +525,11 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                 for (int kk = 0; kk < F / 16; ++kk)
                     mma_bf16_ta(tmem + F, tmem + kk * 8, make_desc(sW2T + kk * 256, 128, F * 16), idesc, kk > 0);
                 mma_commit(&S.mbar);
+                mma_out = true;
+                pend = phase;
             }
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
             cp_async_wait();                               // the warp's u_j rows are in P
@@ -548,10 +564,13 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             // the slots are rewritten only after two more barriers (next tile)
         }
     }
+    // after a wait that gave up, the MMAs in flight complete before their
+    // tensor memory is freed (status bit 2 if they do not, in time)
+    const bool drained = drain_mma(mma_out, &S.mbar, pend);
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 2 * F);
-    if (!ok && tid == 0) atomicOr(status, 1);
+    if (!ok && tid == 0) atomicOr(status, drained ? 1 : 3);
 }
 
 // ------------------------------------------------------------ backward
@@ -632,6 +651,8 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t), sW2N = smem_u32(S.w2n);
     uint32_t phase = 0;
     bool ok = true;
+    bool mma_out = false;                                  // thread 0: a commit not yet seen complete
+    uint32_t pend = 0;                                     // ... and the parity it completes
 
     const int cw = a.carry_w;
     EdgeIn nx;
@@ -685,9 +706,12 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 mma_bf16(tD1, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
                 mma_bf16(tD4, make_desc(sA4, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
                 mma_commit(&S.mbar);
+                mma_out = true;
+                pend = phase;
             }
             load_pos(a, nx);                               // next tile's positions
             ok = mbar_wait(&S.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
             // SiLU(a) -> BF16 operand of the next MMA; p = SiLU'(a) (e' W1), the
@@ -719,8 +743,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     mma_bf16(tD2, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
                              idesc, kk > 0);
                 mma_commit(&S.mbar);
+                mma_out = true;
+                pend = phase;
             }
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
             cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
@@ -782,8 +809,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
                              idesc, kk > 0);
                 mma_commit(&S.mbar);
+                mma_out = true;
+                pend = phase;
             }
             ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
             float s2 = 0.f;
@@ -830,10 +860,11 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             __syncthreads();                               // slots read before the next basis overwrites them
         }
     }
+    const bool drained = drain_mma(mma_out, &S.mbar, pend);   // as in the forward kernel
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TCOLS);
-    if (!ok && tid == 0) atomicOr(status, 1);
+    if (!ok && tid == 0) atomicOr(status, drained ? 1 : 3);
 }
 
 // ------------------------------------------------------------ backward, NG tiles per CTA
@@ -939,6 +970,8 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
     const uint32_t sW1T = smem_u32(S.w1t), sW2T = smem_u32(S.w2t), sW2N = smem_u32(S.w2n);
     uint32_t phase = 0;
     bool ok = true;
+    bool mma_out = false;                                  // thread 0: a commit not yet seen complete
+    uint32_t pend = 0;                                     // ... and the parity it completes
 
     const int cw = a.carry_w;
     const long long first = (long long)blockIdx.x * NG + g, step = (long long)gridDim.x * NG;
@@ -991,9 +1024,12 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
             mma_bf16(tX, make_desc(sA1, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
             mma_bf16(tY, make_desc(sA4, 128, kKP * 16), make_desc(sW1T, 128, kKP * 16), idesc, 0);
             mma_commit(&T.mbar);
+            mma_out = true;
+            pend = phase;
         }
         load_pos(a, nx);                                   // next tile's positions
         ok = mbar_wait(&T.mbar, phase, kWaitIter);
+        if (tid == 0 && ok) mma_out = false;
         phase ^= 1;
         fence_after_sync();
         // epilogue 1: p = SiLU'(a)(e'W1) -> X[0, F/2), SiLU(a) -> Y[0, F/2), both BF16
@@ -1025,8 +1061,11 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
                 mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2T + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
             }
             mma_commit(&T.mbar);
+            mma_out = true;
+            pend = phase;
         }
         ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+        if (tid == 0 && ok) mma_out = false;
         phase ^= 1;
         fence_after_sync();
         cp_async_wait();                                   // the warp's u_j | mbar_j rows are in G
@@ -1084,8 +1123,11 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
                 mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2N + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
             }
             mma_commit(&T.mbar);
+            mma_out = true;
+            pend = phase;
         }
         ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+        if (tid == 0 && ok) mma_out = false;
         phase ^= 1;
         fence_after_sync();
         float s2 = 0.f;
@@ -1133,10 +1175,11 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         }
         group_sync(bar);                                   // slots read before the next basis overwrites them
     }
+    const bool drained = drain_mma(mma_out, &T.mbar, pend);   // each group's issuing thread, as above
     fence_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) tmem_dealloc(S.taddr, NG * 2 * F);
-    if (!ok && tid == 0) atomicOr(status, 1);
+    if (!ok && tid == 0) atomicOr(status, drained ? 1 : 3);
 }
 
 // CTAs of a kernel that fit on one SM: shared memory (1 KB reserved per
@@ -1241,7 +1284,34 @@ void bwd_k(const PotArgs& a, int K, int* status, cudaStream_t s) {
     else go_bwd<F, NV, 0>(a, K, status, s);
 }
 
+// Self-test of the bounded completion waits, issuing no MMA: warp 0 takes 32
+// tensor-memory columns, the mbarrier expects one arrival, thread 0 arrives
+// only if `arrive` is set, and every thread waits through the same bounded
+// wait as the force kernels, at most `polls` polls. The columns are freed
+// either way, and a wait that gave up sets status bit 0, as in those kernels.
+__global__ void __launch_bounds__(kT) k_wait_selftest(int arrive, uint32_t polls, int* status) {
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t taddr;
+    const int tid = threadIdx.x;
+    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid < 32) tmem_alloc(&taddr, 32);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (arrive && tid == 0) mbar_arrive(&mbar);
+    const bool ok = mbar_wait(&mbar, 0, polls);
+    fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tmem_dealloc(taddr, 32);
+    if (!ok && (tid & 31) == 0) atomicOr(status, 1);
+}
+
 }  // namespace
+
+void launch_wait_selftest(int arrive, unsigned int polls, int* status, cudaStream_t s) {
+    k_wait_selftest<<<1, kT, 0, s>>>(arrive, polls, status);
+    count_launch();
+}
 
 void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
     if (a.n_atoms == 0) return;

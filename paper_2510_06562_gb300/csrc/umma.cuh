@@ -110,6 +110,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// One arrival of the calling thread (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile(
+        "{\n\t"
+        ".reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t"
+        "}\n"
+        :: "r"(smem_u32(mbar)) : "memory");
+}
+
 // Bounded wait for the phase with the given parity to complete. Returns
 // false if it gave up after max_iter polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {

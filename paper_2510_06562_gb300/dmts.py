@@ -30,7 +30,8 @@ EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "d
             "dmts_destroy", "dmts_last_error", "dmts_neighbors", "dmts_set_params", "dmts_stream",
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
             "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses",
-            "dmts_monitor", "dmts_monitor_reset")
+            "dmts_monitor", "dmts_monitor_reset", "dmts_set_tuning", "dmts_wait_selftest",
+            "dmts_philox4x32_10")
 
 
 class DmtsError(RuntimeError):
@@ -99,6 +100,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_monitor.restype = C.c_int
     lib.dmts_monitor_reset.argtypes = [P]
     lib.dmts_monitor_reset.restype = C.c_int
+    lib.dmts_set_tuning.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.dmts_set_tuning.restype = C.c_int
+    lib.dmts_wait_selftest.argtypes = [P, C.c_int, C.c_int]
+    lib.dmts_wait_selftest.restype = C.c_int
+    lib.dmts_philox4x32_10.argtypes = [C.c_int, P, P, P]
+    lib.dmts_philox4x32_10.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -168,6 +175,17 @@ def _out_f64(a, n: int, name: str):
     if _numel(a) != n:
         raise ValueError(f"{name} must hold {n} values, got {_numel(a)}")
     return a
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Raw Philox-4x32-10 words of the thermostat's generator, run on the
+    current GPU (``dmts_philox4x32_10``): ctr [n, 4] and key [2] 32-bit words;
+    returns [n, 4] uint32."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros_like(c)
+    _check(load_library().dmts_philox4x32_10(len(c), _ptr(c), _ptr(k), _ptr(out)))
+    return out
 
 
 def hmr_masses(mass, bonds, h_mass: float = 3.024) -> np.ndarray:
@@ -302,6 +320,15 @@ class Context:
         if code < 0:
             _check(code)
         return {"tuned": bool(code), "atoms_fwd": f.value, "atoms_bwd": b.value}
+
+    def set_tuning(self, which: int, fwd: int, bwd: int):
+        """Fix one model's work granularity (``dmts_set_tuning``)."""
+        _check(load_library().dmts_set_tuning(self._h, which, int(fwd), int(bwd)))
+
+    def wait_selftest(self, arrive: bool, max_polls: int = 1000) -> int:
+        """Run the bounded-wait self-test (``dmts_wait_selftest``); returns its
+        status code (0, or -6 when the wait gave up) without raising."""
+        return load_library().dmts_wait_selftest(self._h, 1 if arrive else 0, int(max_polls))
 
     @property
     def stream(self) -> int:

@@ -9,6 +9,8 @@ import json
 import numpy as np
 import pytest
 
+from oracle import integrate as G
+from oracle import model as M
 from paper_2510_06562_gb300 import dmts as D
 from paper_2510_06562_gb300 import inputs as I
 
@@ -87,3 +89,61 @@ def test_monitor_maximum_is_the_end_of_step_force_difference():
         edges = 10.0 ** (np.arange(49) / 8.0 - 3.0)
         ref = np.histogram(np.clip(df, edges[0], edges[-1] * 0.999), bins=edges)[0]
         assert np.abs(mon["hist"] - ref).sum() <= 2               # bin edges: log10 in FP64 on both sides
+
+
+def _pick_threshold(dfs, lo=0.2, hi=0.8):
+    """Thresholds inside the widest gaps of the sorted per-step maxima whose
+    rank lies between the lo and hi quantiles, widest first."""
+    d = np.sort(np.asarray(dfs))
+    n = len(d)
+    gaps = [(d[k + 1] - d[k], 0.5 * (d[k] + d[k + 1])) for k in range(int(lo * n), min(n - 1, int(np.ceil(hi * n))))]
+    return [t for _, t in sorted(gaps, reverse=True)]
+
+
+@pytest.mark.parametrize("friction", [0.0, 20.0])
+def test_partial_fallback_matches_oracle(friction):
+    """The paper's reversion rule on a threshold that some outer steps exceed
+    and others do not: the threshold lies in a gap of the per-step maxima of
+    |F_big - F_small| between their 20th and 80th percentiles, at least
+    1e-3 eV/A from every step's value in the oracle's own monitored run (the
+    FP32 forces differ from the oracle's by about 1e-5 eV/A, so both sides
+    take the same decision at every step). Positions, velocities, the number
+    of steps redone and the largest force difference are compared with the
+    oracle's respa_monitored, NVE and with the Langevin thermostat."""
+    s = I.water_192(0)
+    sa, ba = I.small_arch(2), I.big_arch(2)
+    sp, bp = I.init_params(sa, 2), I.init_params(ba, 3)
+    spec_s, spec_b = M.spec_of(sa), M.spec_of(ba)
+    fs = lambda x: M.energy_forces(spec_s, sp, x, s.species, s.atom_offset, s.box)[1]  # noqa: E731
+    fb = lambda x: M.energy_forces(spec_b, bp, x, s.species, s.atom_offset, s.box)[1]  # noqa: E731
+    v0 = I.maxwell_boltzmann(s.mass, 300.0, 1)
+    bpa = np.full(s.n_atoms, s.box[0])
+    n_outer = 10
+    thermo = {"gamma": friction * 1e-3, "temperature": 300.0, "seed": 5} if friction > 0 else None
+    free = []
+    G.respa_monitored(s.x, v0, s.mass, fs, fb, 3.0, 3, n_outer, np.inf, box_per_atom=bpa, thermo=thermo,
+                      df_out=free)
+    chosen = None
+    for thr in _pick_threshold(free):
+        dfs = []
+        ref = G.respa_monitored(s.x, v0, s.mass, fs, fb, 3.0, 3, n_outer, thr, box_per_atom=bpa, thermo=thermo,
+                                df_out=dfs)
+        if 0 < ref[4] < n_outer and np.abs(np.asarray(dfs) - thr).min() > 1e-3:
+            chosen = (thr, ref, dfs)
+            break
+    assert chosen is not None, free
+    thr, (xr, vr, _, _, n_fb, max_df), dfs = chosen
+    with _ctx(s, fallback_threshold=thr, langevin_friction=friction, seed=5, temperature=300.0) as ctx:
+        ctx.set_state(s.x, v0)
+        ctx.respa_step(n_outer, 3.0, 3)
+        xg, vg = ctx.get_state()
+        mon = ctx.monitor()
+    dx = xg - xr
+    dx -= s.box[0] * np.round(dx / s.box[0])
+    print(json.dumps({"friction": friction, "threshold": thr, "n_fallback": int(n_fb), "dfs": dfs,
+                      "max_dx": float(np.abs(dx).max()), "max_dv": float(np.abs(vg - vr).max()),
+                      "max_df_gpu": mon["max_df"], "max_df_ref": max_df}))
+    assert mon["n_fallback"] == n_fb
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vr).max() < 1e-4
+    assert abs(mon["max_df"] - max_df) <= 1e-4 * max_df

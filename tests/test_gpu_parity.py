@@ -407,6 +407,60 @@ def test_energy_forces_bf16(name):
             assert de <= 5e-3
 
 
+@pytest.mark.parametrize("name", ["water192", "water12288"])
+@pytest.mark.parametrize("prec", [D.FP32, D.BF16_MLP])
+def test_energy_forces_network_only(name, prec):
+    """The same comparisons with the pair repulsion switched off (rep_a = 0):
+    the forces are then the networks' alone (RMS about 0.17 eV/A on water,
+    against 0.84 with the repulsion), so the error of the MLP path is
+    measured undiluted. Absolute bounds as above, and relative to the
+    network force: FP32 1e-4, BF16 3e-2 of its RMS."""
+    import dataclasses
+    s = SYSTEMS[name]()
+    sa = dataclasses.replace(I.small_arch(s.n_species), rep_a=0.0)
+    ba = dataclasses.replace(I.big_arch(s.n_species), rep_a=0.0)
+    sp, bp = I.init_params(sa, 2), I.init_params(ba, 3)
+    with D.Context(s, ba, bp, sa, sp, precision=prec) as ctx:
+        ctx.set_state(s.x)
+        for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+            E, F = ctx.forces(which)
+            Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box)
+            de, err_f = float(np.abs(E - Er).sum() / s.n_atoms), _rmse(F, Fr)
+            rms = float(np.sqrt(np.mean(Fr ** 2)))
+            print(json.dumps({"system": name, "precision": int(prec), "model": int(which), "rep_a": 0.0,
+                              "dE_per_atom": de, "force_rmse": err_f, "force_rms": rms,
+                              "rel_force_rmse": err_f / rms}))
+            if prec == D.FP32:
+                assert de <= E_TOL and err_f <= F_TOL and err_f <= 1e-4 * rms
+            else:
+                assert de <= 5e-3 and err_f <= F_TOL_BF16 and err_f <= 3e-2 * rms
+
+
+@pytest.mark.parametrize("prec", [D.FP32, D.BF16_MLP])
+def test_every_tuning_candidate_gives_identical_forces(prec):
+    """The autotuner's candidates (persistent CTAs per SM for the tensor-core
+    kernels, atoms per CTA for the FP32 kernels) change only how the same
+    fixed work is spread over the GPU: forces and energies are bit-identical
+    for every choice, on a system large enough for every grid to differ."""
+    s = I.water_12288(0)
+    cands = [1, 2, 3, 4, 5, 6] if prec == D.BF16_MLP else [8, 16, 24, 32, 48]
+    ref = None
+    with _ctx_bf16(s) if prec == D.BF16_MLP else _ctx(s) as ctx:
+        ctx.set_state(s.x)
+        for k in cands:
+            out = []
+            for which in (D.SMALL, D.BIG):
+                ctx.set_tuning(which, k, k)
+                E, F = ctx.forces(which)
+                out.append((E, F))
+            if ref is None:
+                ref = out
+                continue
+            for (E, F), (E0, F0) in zip(out, ref):
+                np.testing.assert_array_equal(E, E0)
+                np.testing.assert_array_equal(F, F0)
+
+
 def test_bf16_virial_and_dynamics():
     s = I.water_192(0)
     sa, sp, ba, bp = _models(2)
@@ -424,45 +478,62 @@ def test_bf16_virial_and_dynamics():
 
 # ------------------------------------------------------------ distillation gradient (double backward)
 
-def test_force_matching_gradient_matches_oracle():
-    """dL/dtheta of the force-matching loss through the forces, by the
-    library's adjoint kernels, against the FP64 oracle (autograd double
-    backward), on two frames of the 192-atom box with reference forces from
-    the big model."""
-    s = I.water_192(0)
-    sa, sp, ba, bp = _models(2)
-    rng = np.random.default_rng(7)
-    frames = np.stack([s.x, s.x + rng.normal(scale=0.03, size=s.x.shape)])
+def _fm_frames(s, ba, bp, n_frames=2, seed=7):
+    """Frames: the structure and a copy displaced by 0.03 A per component;
+    reference forces from the big model (FP64 oracle)."""
+    rng = np.random.default_rng(seed)
+    frames = np.stack([s.x] + [s.x + rng.normal(scale=0.03, size=s.x.shape) for _ in range(n_frames - 1)])
     frames = frames - s.box[0] * np.floor(frames / s.box[0])
     f_ref = np.stack([M.energy_forces(M.spec_of(ba), bp, f, s.species, s.atom_offset, s.box)[1] for f in frames])
+    return frames, f_ref
+
+
+@pytest.mark.parametrize("name,rel", [("water192", 1e-6), ("water12288", 1e-5)])
+def test_force_matching_gradient_matches_oracle(name, rel):
+    """dL/dtheta of the force-matching loss through the forces, by the
+    library's FP32 adjoint kernels, against the FP64 oracle (autograd double
+    backward) on two frames, entry by entry:
+    |g - g_ref| <= rel * max|g_ref| + 1e-9. Each entry is a fixed-order FP32
+    sum over all pairs of all frames, so its rounding error grows like the
+    square root of the term count: measured 2.6e-7 of max|g_ref| on 192 atoms;
+    64 times the terms on 12,288 atoms allow 8 times that, hence 1e-5 there.
+    A wrong entry (a dropped term, a transposed weight gradient) is off by
+    the size of the entry itself, far above either bound."""
+    s = SYSTEMS[name]()
+    sa, sp, ba, bp = _models(2)
+    frames, f_ref = _fm_frames(s, ba, bp)
     L_ref, g_ref = M.force_matching_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref)
     with _ctx(s) as ctx:
         ctx.set_state(s.x)
         L, g = ctx.force_matching_grad(frames, f_ref)
     rel_L = abs(L - L_ref) / L_ref
     err = np.abs(g - g_ref)
-    rel_g = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
-    print(json.dumps({"loss": L, "loss_ref": L_ref, "rel_loss_err": rel_L, "grad_rel_l2_err": rel_g,
-                      "grad_max_abs_err": float(err.max()), "grad_max_abs": float(np.abs(g_ref).max())}))
+    bound = rel * np.abs(g_ref).max() + 1e-9
+    print(json.dumps({"system": name, "loss": L, "loss_ref": L_ref, "rel_loss_err": rel_L,
+                      "grad_max_abs_err": float(err.max()), "grad_max_abs": float(np.abs(g_ref).max()),
+                      "bound": float(bound), "worst_entry": int(err.argmax())}))
     assert rel_L < 1e-5
-    assert rel_g < 1e-3
-    assert np.all(g[-2:] == 0.0)          # d2 and e0 do not move forces
+    assert np.all(err <= bound), (int(err.argmax()), float(err.max()), float(bound))
+    assert np.all(g[-(1 + s.n_species):] == 0.0)          # d2 and e0 do not move forces
 
 
 def test_force_matching_autograd_function():
+    """ForceMatchingLoss (a torch.autograd.Function around the library call)
+    returns the oracle's loss and, through backward, the oracle's gradient
+    scaled by the incoming gradient."""
     torch = pytest.importorskip("torch")
     s = I.water_192(0)
     sa, sp, ba, bp = _models(2)
-    frames = s.x[None].copy()
-    f_ref = M.energy_forces(M.spec_of(ba), bp, s.x, s.species, s.atom_offset, s.box)[1][None]
+    frames, f_ref = _fm_frames(s, ba, bp, n_frames=1)
+    L_ref, g_ref = M.force_matching_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref)
     with _ctx(s) as ctx:
         ctx.set_state(s.x)
         theta = torch.tensor(sp, requires_grad=True)
         loss = D.ForceMatchingLoss.apply(theta, ctx, frames, f_ref)
-        loss.backward()
-        _, g = ctx.force_matching_grad(frames, f_ref)
-    np.testing.assert_allclose(theta.grad.numpy(), g, rtol=0, atol=0)
-    assert float(loss.detach()) > 0
+        (2.5 * loss).backward()
+    assert abs(float(loss.detach()) - L_ref) <= 1e-5 * L_ref
+    err = np.abs(theta.grad.numpy() - 2.5 * g_ref)
+    assert np.all(err <= 2.5 * (1e-6 * np.abs(g_ref).max() + 1e-9)), float(err.max())
 
 
 # ------------------------------------------------------------ solvated polymer (4 species)

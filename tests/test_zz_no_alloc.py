@@ -16,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import model as M
 from paper_2510_06562_gb300 import build as B
 from paper_2510_06562_gb300 import dmts as D
 from paper_2510_06562_gb300 import inputs as I
@@ -64,3 +65,51 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                       ctypes.c_void_p(16), 1, ctypes.byref(n), None)
     assert code == -1
     assert b"16384" in lib.dmts_last_error()
+
+
+def _pairs(rp, col):
+    return np.repeat(np.arange(len(rp) - 1), np.diff(rp)), col.astype(np.int64)
+
+
+def test_noalloc_open_boundaries_and_all_pairs_path():
+    """The branches the periodic cell-list case does not take: one molecule
+    without a box (its own fixed-point frame) and the 192-atom box at 5.0 A,
+    where fewer than three cells fit per edge and every pair is tested;
+    each against the oracle's brute-force pair list, twice in a row."""
+    torch = pytest.importorskip("torch")
+    lib = D.load_library()
+    mol = I.make_vacuum_batch(1, 60, 60, seed=4)
+    assert mol.box[0] <= 0
+    cases = [(mol, 5.0), (I.water_192(0), 5.0), (mol, 3.5), (I.water_192(0), 5.0)]
+    for s, rc in cases:
+        code, rp, col, n = _noalloc(lib, torch, s, rc, 64 * s.n_atoms + 1024)
+        assert code == 0, lib.dmts_last_error()
+        oi, oj = M.pair_list(s.x, s.atom_offset, s.box, rc)
+        gi, gj = _pairs(rp, col)
+        assert n == len(oi)
+        np.testing.assert_array_equal(gi, oi)
+        np.testing.assert_array_equal(gj, oj)
+
+
+def test_noalloc_capacity_errors_still_write_the_counts():
+    """Too small an output: DMTS_ERR_CAPACITY, with *n_pairs and row_ptr
+    written; a row longer than the 256 neighbours the fill pass sorts:
+    DMTS_ERR_CAPACITY with a message."""
+    torch = pytest.importorskip("torch")
+    lib = D.load_library()
+    s = I.water_192(0)
+    code, rp, _, n = _noalloc(lib, torch, s, 3.5, 100)
+    assert code == -4
+    oi, _ = M.pair_list(s.x, s.atom_offset, s.box, 3.5)
+    assert n == len(oi) > 100
+    np.testing.assert_array_equal(np.diff(rp), np.bincount(oi, minlength=s.n_atoms))
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0.0, 3.0, size=(300, 3))           # every atom within 5.2 A of every other
+    dense = I.System(x=x, species=np.zeros(300, np.int32), mass=np.ones(300),
+                     atom_offset=np.array([0, 300], np.int32), box=np.array([0.0]), n_species=1)
+    code, _, _, n = _noalloc(lib, torch, dense, 6.0, 300 * 300)
+    assert code == -4
+    assert b"256" in lib.dmts_last_error()
+    # and the entry point still works afterwards
+    code, rp, col, n = _noalloc(lib, torch, s, 3.5, 64 * s.n_atoms)
+    assert code == 0 and n == len(oi)
