@@ -58,16 +58,17 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def step_config(args, s, precision: str, parallelism: str) -> dict:
+def step_config(args, s, world: int) -> dict:
     """The timed workload: the water box by name and size, the RESPA split,
-    the two models and how the step is measured."""
+    the two models and how a step is measured. Both arms print this same
+    object; the arithmetic each arm computes in is its ``dtype``."""
     return {"workload": f"{args.workload}: {s.n_atoms // 3:,} rigid waters, {s.n_atoms:,} atoms, "
                         f"L={s.box[0]:.1f} A, periodic",
             "outer_fs": args.outer_fs, "inner_fs": args.outer_fs / args.n_inner, "n_inner": args.n_inner,
-            "precision": precision,
             "small_model": "3.5 A, K=8, 1 layer, F=32", "big_model": "5.0 A, K=16, 2 layers, F=64",
             "state": "FP64 x, v",
-            "l2": "flushed (256 MB write) before every timed step", "parallelism": parallelism}
+            "l2": "GPU: flushed (256 MB write) before every timed step; host: not applicable",
+            "parallelism": f"replicas{world}"}
 
 
 def models(n_species: int):
@@ -312,6 +313,11 @@ def run_ours(args):
     vh = torch.tensor(main["v0"]).pin_memory()
     eh = torch.empty((1, s.n_systems, 3), dtype=torch.float64).pin_memory()
     k_e2e = max(3, args.steps // 4)
+    # one untimed round trip: the first upload moves the atoms back to the
+    # start, so that step re-evaluates both models (Algorithm 1's first step)
+    r.set_state(xh, vh)
+    r.respa_step(1, dt, n_inner, out=eh)
+    r.get_state(xh, vh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
@@ -321,7 +327,9 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t0
     e2e = {"value": world * k_e2e * dt / FS_PER_NS / t_e2e * SEC_PER_DAY, "unit": "ns/day",
            "h2d_bytes_per_step": 2 * N * 3 * 8, "d2h_bytes_per_step": 2 * N * 3 * 8 + 3 * 8 * s.n_systems,
-           "note": "state uploaded and read back every step; each upload recomputes both models' first-step forces"}
+           "steps": k_e2e,
+           "note": ("every step: x and v uploaded from pinned host buffers (dmts_set_state), one outer step, "
+                    "energies and x, v read back; positions equal to the device's keep the cached forces")}
 
     extras = {}
     if not args.single_precision:
@@ -338,14 +346,15 @@ def run_ours(args):
 
     if rank != 0:
         return None
-    cpu = cpu_baseline(args, s, sa, sp, ba, bp, dt, n_inner) if world == 1 and not args.no_cpu else None
+    cpu = cpu_baseline(args, s, mdl, dt, n_inner) if world == 1 and not args.no_cpu else None
     line = {
         "metric": METRIC, "value": m["dmts_ns_per_day"], "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_prec == D.BF16_MLP else "f32",
         "data": "synthetic",
-        "config": step_config(args, s, args.precision + (" (MLP operands; FP32 accumulation, geometry, sums)"
-                                                         if args.precision == "bf16" else ""), f"replicas{world}"),
+        "config": step_config(args, s, world),
+        "precision": args.precision + (" MLP operands on tcgen05, FP32 accumulation, geometry and sums; "
+                                       "FP64 integrator state" if args.precision == "bf16" else ""),
         "atom_force_evals_per_s": m["atom_force_evals_per_s"], "sts_1fs_ns_per_day": m["sts_1fs_ns_per_day"],
         "speedup_vs_sts": m["dmts_ns_per_day"] / m["sts_1fs_ns_per_day"],
         "dmts_6fs_ns_per_day": m["dmts_6fs_ns_per_day"],
@@ -459,31 +468,69 @@ def distill_rate(D, I, torch, s, mdl, n_frames=4):
 
 
 # ------------------------------------------------------------------- oracle
-def _oracle_step_time(s, sa, sp, ba, bp, n_inner):
-    """Seconds of one outer step of Algorithm 1 by the FP64 oracle: n_inner
-    small-model and one big-model evaluation (pairs + energy + forces)."""
-    from oracle import model as M
-    t0 = time.perf_counter()
-    M.energy_forces(M.spec_of(sa), sp, s.x, s.species, s.atom_offset, s.box)
-    t_small = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    M.energy_forces(M.spec_of(ba), bp, s.x, s.species, s.atom_offset, s.box)
-    t_big = time.perf_counter() - t0
-    return n_inner * t_small + t_big, t_small, t_big
+class OracleStep:
+    """Outer steps of Algorithm 1 by the FP64 oracle (``oracle.integrate.respa``
+    with ``oracle.model`` forces, O(N^2) pair search), carrying the forces
+    between steps as the algorithm does."""
+
+    def __init__(self, s, sa, sp, ba, bp, v0):
+        from oracle import model as M
+        self.s = s
+        self.fs = lambda x: M.energy_forces(M.spec_of(sa), sp, x, s.species, s.atom_offset, s.box)[1]
+        self.fb = lambda x: M.energy_forces(M.spec_of(ba), bp, x, s.species, s.atom_offset, s.box)[1]
+        self.bpa = np.full(s.n_atoms, s.box[0])
+        self.x, self.v = np.array(s.x, dtype=np.float64), np.array(v0, dtype=np.float64)
+        self.F_small = self.F = None
+
+    def step(self, dt, n_inner):
+        """One outer step; returns its wall-clock seconds."""
+        from oracle import integrate as G
+        t0 = time.perf_counter()
+        self.x, self.v, self.F_small, self.F, _ = G.respa(self.x, self.v, self.s.mass, self.fs, self.fb, dt,
+                                                         n_inner, 1, box_per_atom=self.bpa,
+                                                         F_small=self.F_small, F=self.F)
+        return time.perf_counter() - t0
 
 
-def cpu_baseline(args, s, sa, sp, ba, bp, dt, n_inner):
+def _oracle_ns_per_day(s, mdl, dt, n_inner, n_steps=1):
+    """ns/day of the oracle on system s: one untimed step (it evaluates both
+    models at the start), then n_steps timed outer steps."""
+    from paper_2510_06562_gb300 import inputs as I
+    sa, sp, ba, bp = mdl
+    o = OracleStep(s, sa, sp, ba, bp, I.maxwell_boltzmann(s.mass, 300.0, 1, s.atom_offset))
+    o.step(dt, n_inner)
+    t = sum(o.step(dt, n_inner) for _ in range(n_steps))
+    return n_steps * dt / FS_PER_NS / t * SEC_PER_DAY, t / n_steps
+
+
+def cpu_baseline(args, s, mdl, dt, n_inner):
+    """The oracle as it stands on the host cores: one outer step of the timed
+    workload (after one untimed step), plus the 192-atom box on all cores and
+    on one thread."""
     import torch
-    t_step, t_small, t_big = _oracle_step_time(s, sa, sp, ba, bp, n_inner)
-    return {"value": dt / FS_PER_NS / t_step * SEC_PER_DAY, "unit": "ns/day",
-            "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": (f"one small ({t_small:.2f} s) and one big ({t_big:.2f} s) FP64 force evaluation of the "
-                       f"{s.n_atoms}-atom box with O(N^2) pairs, combined as {n_inner} small + 1 big per "
-                       f"{dt:g} fs outer step")}
+    from paper_2510_06562_gb300 import inputs as I
+    cores = torch.get_num_threads()
+    value, t_step = _oracle_ns_per_day(s, mdl, dt, n_inner)
+    small = I.water_192(0)
+    v192, t192 = _oracle_ns_per_day(small, models(small.n_species), dt, n_inner, n_steps=5)
+    torch.set_num_threads(1)
+    try:
+        v192_1, t192_1 = _oracle_ns_per_day(small, models(small.n_species), dt, n_inner, n_steps=5)
+    finally:
+        torch.set_num_threads(cores)
+    return {"value": value, "unit": "ns/day", "cores": cores, "kind": "oracle",
+            "sample": (f"one outer step of Algorithm 1 ({n_inner} small + 1 big FP64 force evaluations, O(N^2) "
+                       f"pair search; {t_step:.2f} s) on the {s.n_atoms}-atom box after one untimed step"),
+            "water192": {"ns_per_day": v192, "s_per_step": t192, "cores": cores, "steps": 5},
+            "water192_single_thread": {"ns_per_day": v192_1, "s_per_step": t192_1, "cores": 1, "steps": 5}}
 
 
 def run_reference(args):
+    """The oracle arm: every step is one outer step of Algorithm 1 by the FP64
+    oracle on the same workload, integrated (not extrapolated); W untimed
+    warm-up steps first (the first evaluates both models at the start)."""
     import torch
+    from paper_2510_06562_gb300 import inputs as I
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -491,23 +538,18 @@ def run_reference(args):
     s = workload(args.workload)
     sa, sp, ba, bp = models(s.n_species)
     dt, n_inner = args.outer_fs, args.n_inner
-    # bounded: every step is one full outer step of the oracle (~10-20 s);
-    # as many as fit in about two minutes after one warm-up step
-    _oracle_step_time(s, sa, sp, ba, bp, n_inner)
-    budget = 120.0
-    times = []
-    t_start = time.perf_counter()
-    while len(times) < args.steps and (time.perf_counter() - t_start) < budget:
-        times.append(_oracle_step_time(s, sa, sp, ba, bp, n_inner)[0])
-    t = sum(times)
-    value = len(times) * dt / FS_PER_NS / t * SEC_PER_DAY
-    sample = (f"{len(times)} outer step(s) of {dt:g} fs ({n_inner} small + 1 big FP64 force evaluation each, "
-              f"O(N^2) pairs) on the {s.n_atoms}-atom box, capped at ~{budget:.0f} s")
-    return {"metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": len(times),
-            "warmup": 1, "ms_per_step": t * 1e3 / len(times), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(step_config(args, s, "fp64 (the oracle on the host cores)", "host, one process"),
-                           l2="not applicable (host)"),
+    o = OracleStep(s, sa, sp, ba, bp, I.maxwell_boltzmann(s.mass, 300.0, 1, s.atom_offset))
+    for _ in range(args.warmup):
+        o.step(dt, n_inner)
+    t = sum(o.step(dt, n_inner) for _ in range(args.steps))
+    value = args.steps * dt / FS_PER_NS / t * SEC_PER_DAY
+    sample = (f"{args.steps} outer steps of {dt:g} fs ({n_inner} small + 1 big FP64 force evaluations each, "
+              f"O(N^2) pair search) on the {s.n_atoms}-atom box, integrated by the oracle after "
+              f"{args.warmup} untimed steps")
+    return {"metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": step_config(args, s, world), "precision": "fp64 (the oracle on the host cores)",
             "cpu_baseline": {"value": value, "unit": "ns/day", "cores": torch.get_num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -99,6 +99,11 @@ def test_reference_arm_line_on_the_small_box():
     assert d["value"] > 0 and abs(d["ms_per_step"] - 3.0 / d["value"] * 86.4) < 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"].startswith("water192: 64 rigid waters, 192 atoms, L=12.4 A")
     assert d["config"]["n_inner"] == 3 and d["config"]["inner_fs"] == 1.0
+    import argparse
+    from paper_2510_06562_gb300 import inputs as I
+    ns = argparse.Namespace(workload="water192", outer_fs=3.0, n_inner=3)
+    assert d["config"] == bench.step_config(ns, I.water_192(0), 1)     # the CUDA arm's config, key for key
+    assert d["warmup"] == 3                                              # at least 3 untimed steps
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "192-atom" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
