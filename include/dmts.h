@@ -314,6 +314,37 @@ DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out
 DMTS_API int dmts_force_matching_grad(dmts_ctx* ctx, int n_frames, const double* frames,
                                       const double* f_ref, double* loss_out, double* grad_out);
 
+/* Energy and force distillation loss of the small model and its parameter
+ * gradient (section "Training procedures": the distilled model is trained on
+ * the energies and forces the reference model gives for frames of a short
+ * reference MD run):
+ *   L(theta) = 1/M sum_{m<M} [ lambda_e ((E(theta; x_m) - E_ref,m) / N)^2
+ *                              + 1/(3 N) sum_i |F_i(theta; x_m) - F_ref,m,i|^2 ],
+ * E the frame's energy summed over the context's systems. The paper leaves
+ * the weights to its Supporting Information; lambda_e >= 0 is the caller's
+ * ((eV/atom)^-2 against (eV/A)^-2 for the force term; 0 gives
+ * dmts_force_matching_grad). Arguments as dmts_force_matching_grad, plus
+ * e_ref [M] reference energies (host or device); same support, FP32
+ * adjoints, restored state and invalidated forces. The frames are enqueued
+ * without host synchronisation between them; a neighbour overflow in any
+ * frame grows the capacities and redoes the batch. */
+DMTS_API int dmts_distill_grad(dmts_ctx* ctx, int n_frames, const double* frames, const double* f_ref,
+                               const double* e_ref, double lambda_e, double* loss_out, double* grad_out);
+
+/* One Adam step (Kingma and Ba, ICLR 2015) on one model's parameters:
+ * with g = grad (n_params doubles, host or device), the caller's moment
+ * estimates m1, m2 (n_params doubles each, host memory, zero before step 1)
+ * become beta1 m1 + (1 - beta1) g and beta2 m2 + (1 - beta2) g^2, and the
+ * parameters theta - lr (m1 / (1 - beta1^t)) / (sqrt(m2 / (1 - beta2^t)) + eps)
+ * are uploaded as by dmts_set_params (t >= 1 is the step number). The update
+ * of these few thousand numbers runs on the host inside the library. */
+DMTS_API int dmts_adam_step(dmts_ctx* ctx, int which, const double* grad, double* m1, double* m2, long long t,
+                            double lr, double beta1, double beta2, double eps);
+
+/* The parameters of one model as last set (n_params doubles in the flat
+ * order; host or device). */
+DMTS_API int dmts_get_params(dmts_ctx* ctx, int which, double* params_out, size_t n_params);
+
 /* ------------------------------------------------------------------------
  * Diagnostics (the paper has no counterpart).
  *

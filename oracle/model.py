@@ -26,8 +26,9 @@ N(i) is the set of j != i with |r_ij|^2 < rc^2 (strict, FP64), where r_ij is
 the minimum-image difference x_j - x_i - L rint((x_j - x_i) / L) in a periodic
 cubic box of edge L, or x_j - x_i without periodicity; atoms of different
 systems never interact. Forces are F = -dE/dx (the quantity Algorithm 1
-consumes); the distillation loss is the force-matching mean square error of
-the knowledge-distillation step (section "Training procedures").
+consumes); the distillation losses are the force-matching mean square error
+and its energy-and-force extension of the knowledge-distillation step
+(section "Training procedures"), optimised by Adam.
 
 The derivatives are taken by reverse-mode automatic differentiation of the
 energy written above (a library primitive computing the exact derivative);
@@ -326,3 +327,48 @@ def force_matching_grad(spec: Spec, params, frames, species, atom_offset, box, f
     L = force_matching_loss(spec, th, frames, species, atom_offset, box, f_ref, create_graph=True)
     (g,) = torch.autograd.grad(L, th)
     return float(L.detach()), g.numpy()
+
+
+def distill_loss(spec: Spec, params, frames, species, atom_offset, box, f_ref, e_ref, lambda_e: float,
+                 create_graph: bool = False):
+    """Energy and force distillation loss over M frames (the small model fit
+    to the large model's energies and forces of MD frames, section "Training
+    procedures"):
+        L = 1/M sum_m [ lambda_e ((E_m - E_ref,m) / N)^2
+                        + 1/(3 N) sum_i |F_i(x_m) - F_ref,m,i|^2 ],
+    E_m the frame's energy summed over its systems, N its atom count. With
+    lambda_e = 0 it is ``force_matching_loss``."""
+    frames = np.asarray(frames, dtype=np.float64)
+    f_ref = np.asarray(f_ref, dtype=np.float64)
+    e_ref = np.asarray(e_ref, dtype=np.float64).reshape(-1)
+    M, N = frames.shape[0], frames.shape[1]
+    total = torch.zeros((), dtype=DT)
+    for m in range(M):
+        xt = torch.tensor(frames[m], requires_grad=True)
+        E = energy(spec, params, xt, species, atom_offset, box).sum()
+        (g,) = torch.autograd.grad(E, xt, create_graph=create_graph)
+        total = total + ((-g - torch.as_tensor(f_ref[m])) ** 2).sum() / (3.0 * N)
+        total = total + lambda_e * ((E - float(e_ref[m])) / N) ** 2
+    return total / M
+
+
+def distill_grad(spec: Spec, params, frames, species, atom_offset, box, f_ref, e_ref, lambda_e: float):
+    """(L, dL/dtheta) of ``distill_loss`` as (float, numpy float64 [n_params])."""
+    th = torch.tensor(np.asarray(params, dtype=np.float64), requires_grad=True)
+    L = distill_loss(spec, th, frames, species, atom_offset, box, f_ref, e_ref, lambda_e, create_graph=True)
+    (g,) = torch.autograd.grad(L, th)
+    return float(L.detach()), g.numpy()
+
+
+def adam_step(theta, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """Step t (1-based) of Adam (Kingma and Ba, ICLR 2015, Algorithm 1):
+    biased first and second moment estimates, their bias corrections, and
+    the update theta - lr m_hat / (sqrt(v_hat) + eps). Returns (theta, m, v)."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return np.asarray(theta, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+

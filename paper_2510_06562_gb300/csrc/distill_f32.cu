@@ -1,7 +1,9 @@
-// Force-matching gradient of a single-layer model (FP32, hand-written
-// adjoints): the parameter gradient of the distillation loss
-//   L(theta) = 1/(3 N M) sum_frames sum_i |F_i(theta) - F_ref,i|^2
-// through the forces F = -dE/dx (a second derivative of the energy).
+// Distillation gradient of a single-layer model (FP32, hand-written
+// adjoints): the parameter gradient of the energy and force loss
+//   L(theta) = 1/M sum_frames [ lambda_E ((E(theta) - E_ref) / N)^2
+//                               + 1/(3 N) sum_i |F_i(theta) - F_ref,i|^2 ]
+// (lambda_E = 0: force matching), the forces F = -dE/dx making it a second
+// derivative of the energy.
 //
 // With g = dL/dF = 2 (F - F_ref) / (3 N M) per frame and
 //   Psi(theta) = sum_i g_i . dE/dx_i = d/d eps E(x + eps g) |_{eps=0},
@@ -16,6 +18,12 @@
 // dPsi/dm' and the per-atom weight gradients), and an edge pass for the
 // filter-weight gradients and dPsi/du. Every gradient is summed per CTA and
 // the CTA partials are added in a fixed order (deterministic).
+//
+// The energy term adds c_E dE/dtheta per frame, c_E = dL/dE = 2 lambda_E
+// (E - E_ref) / (M N^2): the same reverse pass seeded at the readout with
+// -c_E besides the tangent's seed (the passes accumulate -d(.)/dtheta), so
+// dPsi/dq gains -c_E SiLU'(q) R2, dPsi/dR2 gains -c_E SiLU(q), and d2 and
+// e0[Z_i] gain -c_E per atom.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -291,7 +299,8 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
                                                               const float* __restrict__ mdot,
                                                               float* __restrict__ mbar_psi,
                                                               float* __restrict__ mdotbar_psi,
-                                                              float* __restrict__ partial, int n_params) {
+                                                              float* __restrict__ partial, int n_params,
+                                                              const double* __restrict__ c_energy) {
     constexpr int F = 32;
     __shared__ float U1[F * F], U2[F * F], R1[F * F];          // W[k][f], for x W
     __shared__ float U1T[F * 33], U2T[F * 33], R1T[F * 33];    // W[k][f] padded, for x W^T
@@ -306,6 +315,8 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
     __syncthreads();
     const float c1 = P[a.off.c1[0] + lane], c2 = P[a.off.c2[0] + lane], d1 = P[a.off.d1 + lane],
                 r2 = P[a.off.R2 + lane];
+    const float ce = c_energy ? (float)*c_energy : 0.f;        // dL/dE of this frame (energy term)
+    float n_here = 0.f, n_sp_here = 0.f;                       // atoms of this warp; of species `lane`
     // per-lane gradient accumulators: column `lane` of dR1, dU2, dU1 (k = 0..31), and vectors
     float gR1[F], gU2[F], gU1[F];
 #pragma unroll
@@ -330,8 +341,8 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
         float sq, s1q, s2q;
         silu3(q, sq, s1q, s2q);
         const float qdb = s1q * r2;                // dPsi/dq'
-        const float qb = s2q * qd * r2;            // dPsi/dq
-        gR2 += s1q * qd;
+        const float qb = s2q * qd * r2 - ce * s1q * r2;   // dPsi/dq, with the energy term's seed
+        gR2 += s1q * qd - ce * sq;
         gd1 += qb;
 #pragma unroll
         for (int k = 0; k < F; ++k) gR1[k] += bcast(h1, k) * qb + bcast(h1d, k) * qdb;
@@ -353,6 +364,8 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
 #pragma unroll
         for (int zz = 0; zz < 16; ++zz)
             if (zz == sp) gA[zz] += hb;               // residual h1 = h0 + ... with h0 = A[Z]
+        n_here += 1.f;
+        if (lane == sp) n_sp_here += 1.f;
     }
     // write this warp's partials: partial[(blockIdx * warps + w) * n_params + param]
     float* out = partial + ((size_t)blockIdx.x * kAtomWarps + w) * n_params;
@@ -367,6 +380,9 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
     out[a.off.c2[0] + lane] = gc2;
     out[a.off.c1[0] + lane] = gc1;
     for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
+    // every atom adds d2 and e0[Z_i] to the energy once (exact counts in FP32)
+    if (lane == 0) out[a.off.d2] = -ce * n_here;
+    if (lane < n_sp) out[a.off.e0 + lane] = -ce * n_sp_here;
 }
 
 // ------------------------------------------------------------ filter-weight gradient edge pass
@@ -571,6 +587,19 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_input(PotArgs a, const f
     for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
 }
 
+// Energy term of one frame: E = sum over the systems of the model's energies,
+// r = (E - E_ref) / N; loss += lambda r^2 / M and c_E = dL/dE = 2 lambda r / (M N).
+__global__ void k_fm_energy_term(int n_sys, const double* __restrict__ E, const double* __restrict__ e_ref,
+                                 double lambda, int n_atoms, double inv_frames, double* __restrict__ c_energy,
+                                 double* __restrict__ loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double e = 0.0;
+    for (int k = 0; k < n_sys; ++k) e += E[k];
+    const double r = (e - *e_ref) / (double)n_atoms;
+    *loss += lambda * r * r * inv_frames;
+    *c_energy = 2.0 * lambda * r * inv_frames / (double)n_atoms;
+}
+
 // grad[p] (+)= -sum_c partial[c][p] for p in the listed range (fixed order).
 __global__ void k_fm_reduce(const float* __restrict__ partial, int n_rows, int n_params, int p0, int p1,
                             double* __restrict__ grad) {
@@ -623,21 +652,29 @@ int fm_edge_ctas(int n_atoms) { return (n_atoms + fm_atoms_per_cta() - 1) / fm_a
 int fm_atom_ctas(int n_atoms) { return std::max(1, std::min(152 * 2, (n_atoms + kAtomWarps - 1) / kAtomWarps)); }
 
 // One frame's contribution: g from the forces already in p.force, then the
-// three passes; grad_out accumulates -dPsi/dtheta, loss_out the loss.
+// three passes; grad_out accumulates -dPsi/dtheta (+ c_E dE/dtheta with the
+// energy term), loss_out the loss. e_ref: this frame's reference energy on
+// the device, or null for force matching alone.
 void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
                      const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
-                     float* partial_a, int n_params, double* grad, double* loss, cudaStream_t s) {
+                     float* partial_a, int n_params, double* grad, double* loss, const FmEnergy& en,
+                     cudaStream_t s) {
     const int n = p.n_atoms;
     if (n == 0) return;
     k_fm_residual<<<(n + 255) / 256, 256, 0, s>>>(n, p.force, f_ref, c_loss, g, sq);
     k_sum_all<<<1, 256, 0, s>>>(n, sq, 0.5 * c_loss, loss);
+    if (en.e_ref) {
+        k_fm_energy_term<<<1, 32, 0, s>>>(en.n_sys, en.E, en.e_ref, en.lambda, n, en.inv_frames, en.c_energy, loss);
+        count_launch();
+    }
     PotArgs a = p;
     a.atoms_per_cta = fm_atoms_per_cta();
     if (K == 8) tangent_go<32, 8>(a, g, mdot, s);
     else tangent_go<32, 16>(a, g, mdot, s);
     const int ga = fm_atom_ctas(n);
     cudaMemsetAsync(partial_a, 0, sizeof(float) * (size_t)ga * kAtomWarps * n_params, s);
-    k_fm_atom<<<ga, kAtomWarps * 32, 0, s>>>(a, m, mdot, mbar_psi, mdotbar_psi, partial_a, n_params);
+    k_fm_atom<<<ga, kAtomWarps * 32, 0, s>>>(a, m, mdot, mbar_psi, mdotbar_psi, partial_a, n_params,
+                                             en.e_ref ? en.c_energy : nullptr);
     k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_a, ga * kAtomWarps, n_params, 0, n_params, grad);
     const int ge = fm_edge_ctas(n);
     cudaMemsetAsync(partial_e, 0, sizeof(float) * (size_t)ge * n_params, s);

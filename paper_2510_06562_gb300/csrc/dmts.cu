@@ -153,6 +153,7 @@ struct Model {
     double rep_a = 0, rep_rho = 1, rep_rc = 0;
     float* erep = nullptr;
     size_t n_params = 0;
+    std::vector<double> hp;            // the parameters as last uploaded (FP64, flat order)
     ModelOffsets off{};
     float* P = nullptr;
     int nc = 0, n_cells = 0;
@@ -242,6 +243,8 @@ struct dmts_ctx {
     float *fm_g = nullptr, *fm_m = nullptr, *fm_mdot = nullptr, *fm_mb = nullptr, *fm_mdb = nullptr,
           *fm_ubar = nullptr, *fm_pe = nullptr, *fm_pa = nullptr;
     double *fm_sq = nullptr, *fm_grad = nullptr, *fm_loss = nullptr, *fm_stage = nullptr;
+    double *fm_eref = nullptr, *fm_ce = nullptr;   // reference energies [fm_eref_cap], dL/dE scratch
+    int fm_eref_cap = 0;
     cudaGraphExec_t graph = nullptr;
     int g_n_inner = 0;
     double g_dt = 0;
@@ -422,6 +425,7 @@ std::vector<float> build_transposed(const Model& m, const std::vector<float>& pf
 }
 
 int upload_params(dmts_ctx* c, Model& m, const double* params) {
+    if (m.hp.data() != params) m.hp.assign(params, params + m.n_params);
     std::vector<float> pf(m.n_params);
     for (size_t k = 0; k < m.n_params; ++k) pf[k] = (float)params[k];
     CUDA_TRY(cudaMemcpyAsync(m.P, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1146,6 +1150,7 @@ void dmts_destroy(dmts_ctx* c) {
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     dfree(c->fm_g); dfree(c->fm_m); dfree(c->fm_mdot); dfree(c->fm_mb); dfree(c->fm_mdb); dfree(c->fm_ubar);
     dfree(c->fm_pe); dfree(c->fm_pa); dfree(c->fm_sq); dfree(c->fm_grad); dfree(c->fm_loss); dfree(c->fm_stage);
+    dfree(c->fm_eref); dfree(c->fm_ce);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1538,14 +1543,23 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
 
 void* dmts_stream(dmts_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
-int dmts_force_matching_grad(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref,
-                             double* loss_out, double* grad_out) {
+}  // extern "C"
+
+namespace {
+
+// Distillation loss of the small model over n_frames frames and its
+// parameter gradient (e_ref null: force matching alone). Every frame is
+// enqueued without a host synchronisation; a neighbour overflow in any frame
+// grows the capacities and redoes the whole batch.
+int distill_impl(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref, const double* e_ref,
+                 double lambda_e, double* loss_out, double* grad_out) {
     CTX_GUARD(c);
     Model& m = c->m[0];
     if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (!fm_supported(m.F, m.K, m.L))
-        return fail(DMTS_ERR_ARG, "force matching needs a single-layer small model with n_feat 32, n_radial 8 or 16");
+        return fail(DMTS_ERR_ARG, "distillation needs a single-layer small model with n_feat 32, n_radial 8 or 16");
     if (n_frames < 1 || !frames || !f_ref || !loss_out || !grad_out) return fail(DMTS_ERR_ARG, "bad arguments");
+    if (e_ref && !(lambda_e >= 0.0 && isfinite(lambda_e))) return fail(DMTS_ERR_ARG, "lambda_e must be >= 0");
     LaunchScope ls(c);
     const int N = c->N;
     const size_t n3 = (size_t)3 * N, nf = (size_t)N * m.F;
@@ -1563,50 +1577,127 @@ int dmts_force_matching_grad(dmts_ctx* c, int n_frames, const double* frames, co
         if (e == cudaSuccess) e = dalloc(&c->fm_sq, N);
         if (e == cudaSuccess) e = dalloc(&c->fm_grad, np);
         if (e == cudaSuccess) e = dalloc(&c->fm_loss, 1);
+        if (e == cudaSuccess) e = dalloc(&c->fm_ce, 1);
         if (e == cudaSuccess) e = dalloc(&c->fm_stage, 2 * n3);
-        if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "force-matching buffers: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "distillation buffers: %s", cudaGetErrorString(e));
+    }
+    if (e_ref && n_frames > c->fm_eref_cap) {
+        dfree(c->fm_eref);
+        c->fm_eref = nullptr;
+        c->fm_eref_cap = 0;
+        CUDA_TRY(dalloc(&c->fm_eref, (size_t)n_frames));
+        c->fm_eref_cap = n_frames;
     }
     int rc;
+    if (e_ref && (rc = copy_in(c, c->fm_eref, e_ref, (size_t)n_frames))) return rc;
     // keep the dynamical state
     CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(cudaMemsetAsync(c->fm_grad, 0, sizeof(double) * np, c->stream));
-    CUDA_TRY(cudaMemsetAsync(c->fm_loss, 0, sizeof(double), c->stream));
     const int prec = m.precision;
-    m.precision = DMTS_FP32;                 // the adjoint passes are FP32; so is the force they differentiate
+    struct PrecisionRestore {                  // the adjoint passes are FP32; so is the force they differentiate
+        Model& m;
+        int p;
+        ~PrecisionRestore() { m.precision = p; }
+    } restore_prec{m, prec};
+    m.precision = DMTS_FP32;
     const double cl = 2.0 / (3.0 * (double)N * (double)n_frames);
-    for (int fr = 0; fr < n_frames && N > 0; ++fr) {
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            if ((rc = reset_flags(c))) { m.precision = prec; return rc; }
-            rc = copy_in(c, c->fm_stage, frames + (size_t)fr * n3, n3);
-            if (!rc) rc = copy_in(c, c->fm_stage + n3, f_ref + (size_t)fr * n3, n3);
-            if (rc) { m.precision = prec; return rc; }
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = reset_flags(c))) return rc;
+        CUDA_TRY(cudaMemsetAsync(c->fm_grad, 0, sizeof(double) * np, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->fm_loss, 0, sizeof(double), c->stream));
+        for (int fr = 0; fr < n_frames && N > 0; ++fr) {
+            if ((rc = copy_in(c, c->fm_stage, frames + (size_t)fr * n3, n3))) return rc;
+            if ((rc = copy_in(c, c->fm_stage + n3, f_ref + (size_t)fr * n3, n3))) return rc;
             // frame positions into x (velocities, saved above, are zeroed meanwhile)
             launch_set_state(N, c->fm_stage, nullptr, c->d_sys, c->d_box, c->d_x, c->d_v, nullptr, c->stream);
-            enqueue_eval(c, 0, true);
-            if ((rc = sync_check(c))) { m.precision = prec; return rc; }
-            if (!c->h_flags[kFlagOverflow]) break;
-            if ((rc = grow_capacity(c))) { m.precision = prec; return rc; }
-            if (attempt == 3) { m.precision = prec; return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists"); }
+            enqueue_eval(c, 0, true, e_ref != nullptr);
+            CUDA_TRY(cudaMemcpyAsync(c->fm_m, m.msg, nf * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            PotArgs a = pot_args(c, m);
+            a.layer = 0;
+            a.u = m.u[0];                      // u^0 = h0 W_in (gathered per edge)
+            if (!a.u || !a.h || !a.force || !a.P || !a.row_ptr || !a.col || !a.recv || !a.q)
+                return fail(DMTS_ERR_STATE, "distillation: buffers missing");
+            FmEnergy en;
+            if (e_ref) {
+                en.e_ref = c->fm_eref + fr;
+                en.E = m.E;
+                en.n_sys = c->n_sys;
+                en.lambda = lambda_e;
+                en.inv_frames = 1.0 / n_frames;
+                en.c_energy = c->fm_ce;
+            }
+            launch_fm_frame(a, m.K, c->fm_stage + n3, cl, c->fm_g, c->fm_sq, c->fm_m, c->fm_mdot, c->fm_mb,
+                            c->fm_mdb, c->fm_ubar, c->fm_pe, c->fm_pa, np, c->fm_grad, c->fm_loss, en, c->stream);
         }
-        CUDA_TRY(cudaMemcpyAsync(c->fm_m, m.msg, nf * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-        PotArgs a = pot_args(c, m);
-        a.layer = 0;
-        a.u = m.u[0];                         // u^0 = h0 W_in (gathered per edge)
-        if (!a.u || !a.h || !a.force || !a.P || !a.row_ptr || !a.col || !a.recv || !a.q) {
-            m.precision = prec;
-            return fail(DMTS_ERR_STATE, "force matching: buffers missing");
-        }
-        launch_fm_frame(a, m.K, c->fm_stage + n3, cl, c->fm_g, c->fm_sq, c->fm_m, c->fm_mdot, c->fm_mb, c->fm_mdb,
-                        c->fm_ubar, c->fm_pe, c->fm_pa, np, c->fm_grad, c->fm_loss, c->stream);
-        if ((rc = sync_check(c))) { m.precision = prec; return rc; }
+        if ((rc = sync_check(c))) return rc;
+        if (!c->h_flags[kFlagOverflow]) break;
+        if (attempt == 3) return fail(DMTS_ERR_CAPACITY, "neighbour capacity overflow persists");
+        if ((rc = grow_capacity(c))) return rc;
     }
-    m.precision = prec;
     CUDA_TRY(cudaMemcpyAsync(c->d_x, c->d_bx, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     c->forces_valid = false;
     if ((rc = copy_out(c, grad_out, c->fm_grad, np))) return rc;
     if ((rc = copy_out(c, loss_out, c->fm_loss, 1))) return rc;
+    return sync_check(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmts_force_matching_grad(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref,
+                             double* loss_out, double* grad_out) {
+    return distill_impl(c, n_frames, frames, f_ref, nullptr, 0.0, loss_out, grad_out);
+}
+
+int dmts_distill_grad(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref, const double* e_ref,
+                      double lambda_e, double* loss_out, double* grad_out) {
+    if (!e_ref) return fail(DMTS_ERR_ARG, "e_ref is NULL");
+    return distill_impl(c, n_frames, frames, f_ref, e_ref, lambda_e, loss_out, grad_out);
+}
+
+int dmts_get_params(dmts_ctx* c, int which, double* params_out, size_t n_params) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    const Model& m = c->m[which];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!params_out || n_params != m.n_params) return fail(DMTS_ERR_ARG, "expected %zu parameters", m.n_params);
+    if (is_device_ptr(params_out)) {
+        CUDA_TRY(cudaMemcpy(params_out, m.hp.data(), sizeof(double) * n_params, cudaMemcpyHostToDevice));
+    } else {
+        std::copy(m.hp.begin(), m.hp.end(), params_out);
+    }
+    return DMTS_OK;
+}
+
+int dmts_adam_step(dmts_ctx* c, int which, const double* grad, double* m1, double* m2, long long t, double lr,
+                   double beta1, double beta2, double eps) {
+    CTX_GUARD(c);
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    Model& m = c->m[which];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (!grad || !m1 || !m2) return fail(DMTS_ERR_ARG, "NULL argument");
+    if (is_device_ptr(m1) || is_device_ptr(m2)) return fail(DMTS_ERR_ARG, "the moment estimates must be host arrays");
+    if (t < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return fail(DMTS_ERR_ARG, "need t >= 1, lr > 0, 0 <= beta < 1, eps > 0");
+    const size_t n = m.n_params;
+    std::vector<double> g(n);
+    if (is_device_ptr(grad)) CUDA_TRY(cudaMemcpy(g.data(), grad, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    else std::copy(grad, grad + n, g.begin());
+    const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    std::vector<double> th = m.hp;
+    for (size_t k = 0; k < n; ++k) {
+        if (!isfinite(g[k])) return fail(DMTS_ERR_ARG, "gradient entry %zu is not finite", k);
+        m1[k] = beta1 * m1[k] + (1.0 - beta1) * g[k];
+        m2[k] = beta2 * m2[k] + (1.0 - beta2) * g[k] * g[k];
+        th[k] -= lr * (m1[k] / c1) / (sqrt(m2[k] / c2) + eps);
+    }
+    LaunchScope ls(c);
+    int rc = upload_params(c, m, th.data());
+    if (rc) return rc;
+    if ((rc = prepare_embedding(c, m))) return rc;
+    c->forces_valid = false;
     return sync_check(c);
 }
 

@@ -263,9 +263,18 @@ int bf16_max_ctas_per_sm(int F, bool bwd);
 bool fm_supported(int F, int K, int L);
 int fm_edge_ctas(int n_atoms);
 int fm_atom_ctas(int n_atoms);
+// Energy term of the distillation loss for one frame (e_ref null: none).
+struct FmEnergy {
+    const double* e_ref = nullptr;   // device scalar: the frame's reference energy
+    const double* E = nullptr;       // device [n_sys]: the model's energies at the frame
+    int n_sys = 0;
+    double lambda = 0.0, inv_frames = 0.0;
+    double* c_energy = nullptr;      // device scalar scratch: dL/dE of the frame
+};
 void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
                      const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
-                     float* partial_a, int n_params, double* grad, double* loss, cudaStream_t s);
+                     float* partial_a, int n_params, double* grad, double* loss, const FmEnergy& en,
+                     cudaStream_t s);
 
 // atom_mlp.cu: per-atom MLPs after the edge passes
 void launch_atom_fwd(const PotArgs& p, int F, const float* msg, cudaStream_t s);

@@ -31,7 +31,7 @@ EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "d
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
             "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses",
             "dmts_monitor", "dmts_monitor_reset", "dmts_set_tuning", "dmts_wait_selftest",
-            "dmts_philox4x32_10")
+            "dmts_philox4x32_10", "dmts_distill_grad", "dmts_adam_step", "dmts_get_params")
 
 
 class DmtsError(RuntimeError):
@@ -106,6 +106,13 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_wait_selftest.restype = C.c_int
     lib.dmts_philox4x32_10.argtypes = [C.c_int, P, P, P]
     lib.dmts_philox4x32_10.restype = C.c_int
+    lib.dmts_distill_grad.argtypes = [P, C.c_int, P, P, P, C.c_double, P, P]
+    lib.dmts_distill_grad.restype = C.c_int
+    lib.dmts_adam_step.argtypes = [P, C.c_int, P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double,
+                                   C.c_double]
+    lib.dmts_adam_step.restype = C.c_int
+    lib.dmts_get_params.argtypes = [P, C.c_int, P, C.c_size_t]
+    lib.dmts_get_params.restype = C.c_int
     for name in ("dmts_set_state", "dmts_get_state", "dmts_forces", "dmts_respa_step",
                  "dmts_neighbors", "dmts_set_params"):
         getattr(lib, name).restype = C.c_int
@@ -235,6 +242,7 @@ class Context:
         self._h = h
         self.has_small = small_arch is not None
         self.small_n_params = small_arch.param_count() if small_arch is not None else 0
+        self.big_n_params = big_arch.param_count()
 
     # ---------------------------------------------------------------- state
     def set_state(self, x, v=None):
@@ -300,6 +308,43 @@ class Context:
         _check(load_library().dmts_force_matching_grad(self._h, m, _ptr(frames), _ptr(f_ref), _ptr(loss),
                                                        _ptr(grad)))
         return float(loss[0]), grad
+
+    def distill_grad(self, frames, f_ref, e_ref, lambda_e: float, grad_out=None):
+        """Energy and force distillation loss of the small model and its
+        parameter gradient (``dmts_distill_grad``): (loss, grad [n_params]).
+        frames, f_ref: [M, N, 3]; e_ref: [M] float64 (host or device)."""
+        frames = _f64(frames)
+        f_ref = _f64(f_ref)
+        e_ref = _f64(e_ref)
+        m = frames.shape[0]
+        if tuple(f_ref.shape) != tuple(frames.shape) or frames.shape[1:] != (self.n_atoms, 3):
+            raise ValueError("frames and f_ref must both be [M, N, 3]")
+        if _numel(e_ref) != m:
+            raise ValueError("e_ref must hold one energy per frame")
+        loss = np.zeros(1)
+        grad = np.empty(self.small_n_params) if grad_out is None else _out_f64(grad_out, self.small_n_params,
+                                                                               "grad_out")
+        _check(load_library().dmts_distill_grad(self._h, m, _ptr(frames), _ptr(f_ref), _ptr(e_ref),
+                                                float(lambda_e), _ptr(loss), _ptr(grad)))
+        return float(loss[0]), grad
+
+    def adam_step(self, which: int, grad, m1: np.ndarray, m2: np.ndarray, t: int, lr: float,
+                  beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        """One Adam step on a model's parameters (``dmts_adam_step``); m1, m2
+        are the caller's float64 moment arrays, updated in place."""
+        n = self.small_n_params if which == SMALL else self.big_n_params
+        g = _f64(grad)
+        for a, name in ((m1, "m1"), (m2, "m2")):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == n and a.flags.c_contiguous):
+                raise TypeError(f"{name} must be a contiguous float64 NumPy array of {n} values")
+        _check(load_library().dmts_adam_step(self._h, which, _ptr(g), _ptr(m1), _ptr(m2), int(t), float(lr),
+                                             float(beta1), float(beta2), float(eps)))
+
+    def get_params(self, which: int = SMALL) -> np.ndarray:
+        n = self.small_n_params if which == SMALL else self.big_n_params
+        out = np.empty(n)
+        _check(load_library().dmts_get_params(self._h, which, _ptr(out), n))
+        return out
 
     def time_stages(self, which: int = BIG, reps: int = 10) -> dict:
         """Per-stage milliseconds of one force evaluation (CUDA events)."""

@@ -73,11 +73,11 @@ def test_set_state_with_unchanged_positions_keeps_cached_forces():
     with _ctx(s, D.BF16_MLP) as a, _ctx(s, D.BF16_MLP) as b:
         a.set_state(s.x, v0)
         b.set_state(s.x, v0)
-        a.respa_step(2, 3.0, 3)
+        a.respa_step(3, 3.0, 3)
         b.respa_step(2, 3.0, 3)
         n0 = b.launch_count
         b.respa_step(1, 3.0, 3)
-        per_step = b.launch_count - n0
+        per_step = b.launch_count - n0                    # both contexts have taken 3 steps
         for _ in range(3):
             x, v = a.get_state()
             a.set_state(x, v)

@@ -1,0 +1,118 @@
+"""GPU tests of the system-specific distillation (section "Training
+procedures"): the energy and force loss gradient through the forces against
+the FP64 oracle, Adam against the oracle's Adam, and the frame pipeline and
+training loop run through the library.
+
+Inputs of the parity tests come from the seeded generators and the oracle
+(frames are the structure plus seeded displacements, labels the oracle's big
+model), never from the CUDA path.
+"""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from paper_2510_06562_gb300 import distill as DS
+from paper_2510_06562_gb300 import dmts as D
+from paper_2510_06562_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _models():
+    sa, ba = I.small_arch(2), I.big_arch(2)
+    return sa, I.init_params(sa, 2), ba, I.init_params(ba, 3)
+
+
+def _labelled_frames(s, ba, bp, n_frames, seed):
+    rng = np.random.default_rng(seed)
+    frames = np.stack([s.x] + [s.x + rng.normal(scale=0.03, size=s.x.shape) for _ in range(n_frames - 1)])
+    frames = frames - s.box[0] * np.floor(frames / s.box[0])
+    f_ref, e_ref = [], []
+    for f in frames:
+        E, F = M.energy_forces(M.spec_of(ba), bp, f, s.species, s.atom_offset, s.box)
+        f_ref.append(F)
+        e_ref.append(float(E.sum()))
+    return frames, np.stack(f_ref), np.array(e_ref)
+
+
+@pytest.mark.parametrize("lambda_e", [1.0, 0.05])
+def test_distill_gradient_matches_oracle(lambda_e):
+    """Energy + force loss and its gradient on two frames of the 192-atom
+    box, entry by entry as the force-matching test: |g - g_ref| <= 1e-6
+    max|g_ref| + 1e-9 (FP32 sums over all pairs in a fixed order). The
+    energy term moves d2 and e0, which the force term leaves at zero."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models()
+    frames, f_ref, e_ref = _labelled_frames(s, ba, bp, 2, 7)
+    L_ref, g_ref = M.distill_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref, e_ref,
+                                  lambda_e)
+    with D.Context(s, ba, bp, sa, sp) as ctx:
+        ctx.set_state(s.x)
+        L, g = ctx.distill_grad(frames, f_ref, e_ref, lambda_e)
+    err = np.abs(g - g_ref)
+    bound = 1e-6 * np.abs(g_ref).max() + 1e-9
+    print(json.dumps({"lambda_e": lambda_e, "loss": L, "loss_ref": L_ref, "grad_max_abs_err": float(err.max()),
+                      "grad_max_abs": float(np.abs(g_ref).max()), "worst_entry": int(err.argmax())}))
+    assert abs(L - L_ref) <= 1e-5 * L_ref
+    assert np.all(err <= bound), (int(err.argmax()), float(err.max()), float(bound))
+    assert np.abs(g_ref[-3:]).min() > 0                  # d2 and e0 carry the energy term
+
+
+def test_distill_without_energy_term_is_force_matching():
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models()
+    frames, f_ref, e_ref = _labelled_frames(s, ba, bp, 2, 8)
+    with D.Context(s, ba, bp, sa, sp) as ctx:
+        ctx.set_state(s.x)
+        L0, g0 = ctx.distill_grad(frames, f_ref, e_ref, 0.0)
+        Lf, gf = ctx.force_matching_grad(frames, f_ref)
+    assert L0 == Lf
+    np.testing.assert_array_equal(g0, gf)
+
+
+def test_adam_step_matches_oracle():
+    """The library's Adam update of the small model's parameters, three
+    steps with an oracle gradient as input, against the oracle's Adam (both
+    FP64 on the host): equal to rounding (the library's compiler may fuse a
+    multiply and an add that NumPy rounds separately: a few units in the
+    last place)."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models()
+    rng = np.random.default_rng(1)
+    with D.Context(s, ba, bp, sa, sp) as ctx:
+        ctx.set_state(s.x)
+        m1, m2 = np.zeros(len(sp)), np.zeros(len(sp))
+        th, r1, r2 = sp.copy(), np.zeros(len(sp)), np.zeros(len(sp))
+        for t in (1, 2, 3):
+            g = rng.normal(size=len(sp)) * 1e-2
+            ctx.adam_step(D.SMALL, g, m1, m2, t, 1e-3)
+            th, r1, r2 = M.adam_step(th, g, r1, r2, t, 1e-3)
+        got = ctx.get_params(D.SMALL)
+    np.testing.assert_allclose(got, th, rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(m1, r1, rtol=1e-12, atol=1e-20)
+    np.testing.assert_allclose(m2, r2, rtol=1e-12, atol=1e-24)
+
+
+def test_frame_pipeline_labels_and_training_reduce_the_loss():
+    """Frames from big-model MD through the library, labelled with its
+    energies and forces: the labels equal the oracle's big model at those
+    frames (FP32 tolerances); then full-batch Adam on the energy and force
+    loss lowers it."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models()
+    frames, f_ref, e_ref = DS.sample_frames(s, ba, bp, n_frames=6, n_traj=2, stride_fs=10.0)
+    assert frames.shape == (6, s.n_atoms, 3) and e_ref.shape == (6,)
+    assert len({float(e) for e in e_ref}) == 6                 # distinct frames
+    for k in (0, 5):
+        Er, Fr = M.energy_forces(M.spec_of(ba), bp, frames[k], s.species, s.atom_offset, s.box)
+        assert abs(e_ref[k] - Er.sum()) / s.n_atoms <= 1e-6
+        assert np.sqrt(np.mean((f_ref[k] - Fr) ** 2)) <= 1e-5
+    with D.Context(s, ba, bp, sa, sp) as ctx:
+        ctx.set_state(s.x)
+        losses = DS.train(ctx, frames, f_ref, e_ref, n_steps=12, lr=2e-3, lambda_e=1.0)
+        final, _ = ctx.distill_grad(frames, f_ref, e_ref, 1.0)
+    print(json.dumps({"losses": losses, "final": final}))
+    assert final < 0.8 * losses[0]
+    assert all(np.isfinite(losses))

@@ -343,3 +343,80 @@ def test_pair_repulsion_closed_form(dist):
                                             - 0.5 * math.pi / r * math.sin(math.pi * dist / r))
     assert abs(F[1, 0] + dref) <= 1e-10 * max(1.0, abs(dref))
     assert abs(F[0, 0] - dref) <= 1e-10 * max(1.0, abs(dref))
+
+
+def test_distill_gradient_finite_differences():
+    """Energy + force loss: dL/dtheta against central differences of L in
+    theta, along random directions and for single parameters including d2
+    and e0 (which the energy term moves and the force term does not)."""
+    s = _small_water()
+    spec = M.spec_of(I.small_arch())
+    par = I.init_params(I.small_arch(), 2)
+    rng = np.random.default_rng(4)
+    frames = np.stack([s.x, s.x + rng.normal(scale=0.05, size=s.x.shape)])
+    f_ref = rng.normal(scale=0.5, size=frames.shape)
+    e_ref = np.array([1.5, -2.0]) * s.n_atoms
+    lam = 0.7
+    L, g = M.distill_grad(spec, par, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, lam)
+    h = 1e-5
+
+    def loss(p):
+        return float(M.distill_loss(spec, p, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, lam))
+
+    for _ in range(3):
+        dv = rng.normal(size=par.shape)
+        dv /= np.linalg.norm(dv)
+        assert abs((loss(par + h * dv) - loss(par - h * dv)) / (2 * h) - g @ dv) < 1e-7 * max(1.0, np.abs(g).max())
+    for k in [0, 70, len(par) - 1, len(par) - 2, len(par) - 3]:
+        dv = np.zeros_like(par)
+        dv[k] = 1
+        assert abs((loss(par + h * dv) - loss(par - h * dv)) / (2 * h) - g[k]) < 1e-7 * max(1.0, np.abs(g).max())
+    assert abs(L - loss(par)) <= 1e-12 * L
+
+
+def test_distill_energy_term_closed_forms():
+    """lambda_e = 0 is the force-matching loss; the gradient's d2 and e0
+    entries come from the energy term alone and have closed forms:
+    dL/dd2 = 2 lambda_e / M sum_m (E_m - E_ref,m) / N (every atom adds d2
+    once) and dL/de0[s] = 2 lambda_e / M sum_m (E_m - E_ref,m) n_s / N^2."""
+    s = _small_water(1)
+    spec = M.spec_of(I.small_arch())
+    par = I.init_params(I.small_arch(), 2)
+    rng = np.random.default_rng(5)
+    frames = np.stack([s.x, s.x + rng.normal(scale=0.05, size=s.x.shape)])
+    f_ref = rng.normal(scale=0.5, size=frames.shape)
+    e_ref = np.array([0.3, -0.4]) * s.n_atoms
+    L0, g0 = M.distill_grad(spec, par, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, 0.0)
+    Lf, gf = M.force_matching_grad(spec, par, frames, s.species, s.atom_offset, s.box, f_ref)
+    assert abs(L0 - Lf) <= 1e-12 * Lf
+    np.testing.assert_allclose(g0, gf, rtol=0, atol=1e-13 * np.abs(gf).max())
+    lam = 2.0
+    _, g = M.distill_grad(spec, par, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, lam)
+    E = np.array([M.energy(spec, par, f, s.species, s.atom_offset, s.box).sum().item() for f in frames])
+    N, Mf = s.n_atoms, len(frames)
+    r = (E - e_ref) / N
+    n_s = np.bincount(s.species, minlength=spec.n_species)
+    S = spec.n_species
+    assert abs(g[-1 - S] - 2 * lam / Mf * r.sum()) <= 1e-12 * max(1.0, abs(g[-1 - S]))
+    np.testing.assert_allclose(g[-S:], 2 * lam / Mf * r.sum() * n_s / N, rtol=1e-12, atol=0)
+
+
+def test_adam_first_step_and_constant_gradient():
+    """Adam's first step moves each parameter by lr g / (|g| + eps) against
+    its gradient (both bias corrections are exact at t = 1); under a constant
+    gradient every later step does the same, since m_hat = g and
+    v_hat = g^2 at every t."""
+    rng = np.random.default_rng(0)
+    th = rng.normal(size=50)
+    g = rng.normal(size=50)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    lr, eps = 1e-3, 1e-8
+    t1, m, v = M.adam_step(th, g, m, v, 1, lr, eps=eps)
+    np.testing.assert_allclose(t1, th - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    t = t1
+    for k in range(2, 6):
+        t_new, m, v = M.adam_step(t, g, m, v, k, lr, eps=eps)
+        np.testing.assert_allclose(t_new, t - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-14)
+        t = t_new
+
