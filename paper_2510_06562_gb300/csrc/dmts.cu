@@ -23,6 +23,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dmts.h"
 #include "internal.cuh"
 #include "umma.cuh"
@@ -257,6 +259,13 @@ namespace {
 struct LaunchScope {
     explicit LaunchScope(dmts_ctx* c) { g_launch_counter = &c->launches; }
     ~LaunchScope() { g_launch_counter = nullptr; }
+};
+
+// An NVTX range around a host-side call (named in profilers' timelines; NVTX
+// is header-only and costs nothing unless a profiler is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
 };
 
 bool is_device_ptr(const void* p) {
@@ -786,6 +795,7 @@ PotArgs bwd_args(const PotArgs& a, Model& m, int l) {
 
 void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Check check = Check::Kernel,
                   bool virial = false) {
+    Range nvtx_range(which == DMTS_BIG ? "evaluate big model" : "evaluate small model");
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
     enqueue_neighbors(c, which, quantize, check);
@@ -1158,6 +1168,7 @@ void dmts_destroy(dmts_ctx* c) {
 
 int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const dmts_system_desc* sys,
                 const char* options, dmts_ctx** out) {
+    Range nvtx_range("dmts_create");
     g_err.clear();
     if (!out) return fail(DMTS_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -1348,6 +1359,7 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
 
 int dmts_set_state(dmts_ctx* c, const double* x, const double* v, int n_atoms) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_set_state");
     if (!x) return fail(DMTS_ERR_ARG, "x is NULL");
     if (n_atoms != c->N) return fail(DMTS_ERR_ARG, "n_atoms %d != %d", n_atoms, c->N);
     LaunchScope ls(c);
@@ -1370,6 +1382,7 @@ int dmts_set_state(dmts_ctx* c, const double* x, const double* v, int n_atoms) {
 
 int dmts_get_state(dmts_ctx* c, double* x, double* v) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_get_state");
     LaunchScope ls(c);
     size_t n3 = (size_t)3 * c->N;
     launch_get_state(c->N, c->d_x, c->d_v, c->d_stage, c->d_stage + n3, c->stream);
@@ -1381,6 +1394,7 @@ int dmts_get_state(dmts_ctx* c, double* x, double* v) {
 
 int dmts_forces(dmts_ctx* c, int which, double* f_out, double* energy_out, double* virial_out) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_forces");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
@@ -1409,6 +1423,7 @@ int dmts_forces(dmts_ctx* c, int which, double* f_out, double* energy_out, doubl
 
 int dmts_neighbors(dmts_ctx* c, int which, int* row_ptr, int* col, long long capacity, long long* n_pairs) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_neighbors");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
@@ -1439,6 +1454,7 @@ int dmts_neighbors(dmts_ctx* c, int which, int* row_ptr, int* col, long long cap
 
 int dmts_set_params(dmts_ctx* c, int which, const double* params, size_t n_params) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_set_params");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     Model& m = c->m[which];
     if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
@@ -1454,6 +1470,7 @@ int dmts_set_params(dmts_ctx* c, int which, const double* params, size_t n_param
 
 int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* energies_out) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_respa_step");
     if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
     if (n_outer < 0) return fail(DMTS_ERR_ARG, "n_outer must be >= 0");
     if (!(dt > 0) || !isfinite(dt)) return fail(DMTS_ERR_ARG, "dt must be > 0");
@@ -1554,6 +1571,7 @@ namespace {
 int distill_impl(dmts_ctx* c, int n_frames, const double* frames, const double* f_ref, const double* e_ref,
                  double lambda_e, double* loss_out, double* grad_out) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_distill_grad");
     Model& m = c->m[0];
     if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (!fm_supported(m.F, m.K, m.L))
@@ -1674,6 +1692,7 @@ int dmts_get_params(dmts_ctx* c, int which, double* params_out, size_t n_params)
 int dmts_adam_step(dmts_ctx* c, int which, const double* grad, double* m1, double* m2, long long t, double lr,
                    double beta1, double beta2, double eps) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_adam_step");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     Model& m = c->m[which];
     if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
@@ -1703,6 +1722,7 @@ int dmts_adam_step(dmts_ctx* c, int which, const double* grad, double* m1, doubl
 
 int dmts_time_stages(dmts_ctx* c, int which, int reps, double* ms_out, int n_out) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_time_stages");
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     if (!c->m[which].present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (!c->state_set) return fail(DMTS_ERR_STATE, "no state set");
@@ -1881,6 +1901,7 @@ int dmts_set_tuning(dmts_ctx* c, int which, int fwd, int bwd) {
 
 int dmts_wait_selftest(dmts_ctx* c, int arrive, int max_polls) {
     CTX_GUARD(c);
+    Range nvtx_range("dmts_wait_selftest");
     if (max_polls < 1 || max_polls > (1 << 22)) return fail(DMTS_ERR_ARG, "max_polls must be in [1, 2^22]");
     LaunchScope ls(c);
     int rc = reset_flags(c);

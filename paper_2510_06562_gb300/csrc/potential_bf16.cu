@@ -24,6 +24,7 @@
 #include <mutex>
 #include <utility>
 
+#include "f32x2.cuh"
 #include "internal.cuh"
 #include "umma.cuh"
 
@@ -43,6 +44,18 @@ constexpr uint32_t kWaitIter = 1u << 22;
 // freed under them. Returns false if this wait gives up too.
 __device__ __forceinline__ bool drain_mma(bool mma_out, uint64_t* mbar, uint32_t pend) {
     return !mma_out || mbar_wait(mbar, pend, kWaitIter);
+}
+
+constexpr f2::f32x2 kHalf2 = 0x3F0000003F000000ull;        // (0.5f, 0.5f)
+constexpr f2::f32x2 kMinusHalf2 = 0xBF000000BF000000ull;   // (-0.5f, -0.5f)
+
+// tanh(x / 2) of both halves (the hardware approximation, one per half)
+__device__ __forceinline__ f2::f32x2 tanh_half(f2::f32x2 x) {
+    const f2::f32x2 h = f2::mul(x, kHalf2);
+    float t0, t1;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(f2::lo(h)));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(f2::hi(h)));
+    return f2::pack(t0, t1);
 }
 
 __device__ __forceinline__ float sigmoid_fast(float x) {
@@ -145,15 +158,33 @@ __device__ __forceinline__ void basis16(float d, float inv_d, int K, float pi_ov
                                         float* de, float& fc, float& dfc) {
     float s1, c1;
     __sincosf(d * pi_over_rc, &s1, &c1);
-    float sk = s1, skm1 = 0.f, ck = c1, ckm1 = 1.f;
+    // sin(k t) and cos(k t), t = pi d / rc, by the Chebyshev recurrence
+    float sk[kKP], ck[kKP];
+    sk[0] = s1;
+    ck[0] = c1;
+    const float c2 = 2.f * c1;
 #pragma unroll
-    for (int k = 0; k < kKP; ++k) {
-        const bool on = KC > 0 ? k < KC : k < K;
-        e[k] = on ? pref * sk * inv_d : 0.f;
-        if (de) de[k] = on ? pref * ((float)(k + 1) * pi_over_rc * ck - sk * inv_d) * inv_d : 0.f;
-        float sn = 2.f * c1 * sk - skm1, cn = 2.f * c1 * ck - ckm1;
-        skm1 = sk; sk = sn;
-        ckm1 = ck; ck = cn;
+    for (int k = 1; k < kKP; ++k) {
+        sk[k] = c2 * sk[k - 1] - (k > 1 ? sk[k - 2] : 0.f);
+        ck[k] = c2 * ck[k - 1] - (k > 1 ? ck[k - 2] : 1.f);
+    }
+    // e_k = A sin(k t), e'_k = A (k pi / rc) cos(k t) - (A / d) sin(k t), A = pref / d;
+    // two functions per packed FP32 operation
+    const float A = pref * inv_d;
+    const f2::f32x2 A2 = f2::splat(A), mB2 = f2::splat(-A * inv_d), W2 = f2::splat(A * pi_over_rc);
+#pragma unroll
+    for (int k = 0; k < kKP; k += 2) {
+        const bool on0 = KC > 0 ? k < KC : k < K, on1 = KC > 0 ? k + 1 < KC : k + 1 < K;
+        const f2::f32x2 S = f2::pack(sk[k], sk[k + 1]);
+        const f2::f32x2 E = f2::mul(A2, S);
+        e[k] = on0 ? f2::lo(E) : 0.f;
+        e[k + 1] = on1 ? f2::hi(E) : 0.f;
+        if (de) {
+            const f2::f32x2 DE = f2::fma(f2::mul(W2, f2::pack((float)(k + 1), (float)(k + 2))),
+                                         f2::pack(ck[k], ck[k + 1]), f2::mul(mB2, S));
+            de[k] = on0 ? f2::lo(DE) : 0.f;
+            de[k + 1] = on1 ? f2::hi(DE) : 0.f;
+        }
     }
     fc = 0.5f * (c1 + 1.0f);
     dfc = -0.5f * pi_over_rc * s1;
@@ -201,19 +232,17 @@ __device__ __forceinline__ void warp_vec_segments(const float* __restrict__ sP, 
         const int e0 = __ffs(rem) - 1;
         rem &= rem - 1u;
         const int e1 = rem ? __ffs(rem) - 1 : n_valid;
-        float acc[VW];
-#pragma unroll
-        for (int c = 0; c < VW; ++c) acc[c] = 0.f;
+        float acc[VW];                             // e0 < e1: the segment has an edge
+        if constexpr (VW == 2) {
+            f2::f32x2 a2 = *reinterpret_cast<const f2::f32x2*>(base + prow<F>(e0, f0));
 #pragma unroll 4
-        for (int e = e0; e < e1; ++e) {
-            const float* src = base + prow<F>(e, f0);
-            if constexpr (VW == 2) {
-                const float2 x = *reinterpret_cast<const float2*>(src);
-                acc[0] = e == e0 ? x.x : acc[0] + x.x;
-                acc[1] = e == e0 ? x.y : acc[1] + x.y;
-            } else {
-                acc[0] = e == e0 ? *src : acc[0] + *src;
-            }
+            for (int e = e0 + 1; e < e1; ++e) a2 = f2::add(a2, *reinterpret_cast<const f2::f32x2*>(base + prow<F>(e, f0)));
+            acc[0] = f2::lo(a2);
+            acc[1] = f2::hi(a2);
+        } else {
+            acc[0] = base[prow<F>(e0, f0)];
+#pragma unroll 4
+            for (int e = e0 + 1; e < e1; ++e) acc[0] += base[prow<F>(e, f0)];
         }
         const int r = __shfl_sync(0xffffffffu, myrow, e0);
         if (seg == 0) {                            // may continue a row of the previous warp
@@ -510,9 +539,10 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                 tmem_ld16(tmem + lane_base + c, v);
                 uint32_t pk[8];
 #pragma unroll
-                for (int q = 0; q < 16; q += 2) {
-                    const float x0 = v[q] + S.b1[c + q], x1 = v[q + 1] + S.b1[c + q + 1];
-                    pk[q / 2] = pack_bf16(x0 * sigmoid_fast(x0), x1 * sigmoid_fast(x1));
+                for (int q = 0; q < 16; q += 2) {          // two features per packed FP32 operation
+                    const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                    const f2::f32x2 y = f2::mul(x, f2::fma(kHalf2, tanh_half(x), kHalf2));   // SiLU
+                    pk[q / 2] = pack_bf16(f2::lo(y), f2::hi(y));
                 }
                 tmem_st8(tmem + lane_base + c / 2, pk);
             }
@@ -535,17 +565,21 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             cp_async_wait();                               // the warp's u_j rows are in P
             __syncwarp();
             {
+                const f2::f32x2 fc2 = f2::splat(fc);
 #pragma unroll
                 for (int c = 0; c < F; c += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + F + c, v);
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) {
+                    for (int q = 0; q < 16; q += 4) {      // message fc (D2 + b2) u_j, two features per operation
                         float* p4 = S.P + prow<F>(tid, c + q);
-                        float4 u4 = *reinterpret_cast<const float4*>(p4);
-                        *reinterpret_cast<float4*>(p4) = make_float4(
-                            fc * (v[q] + S.b2[c + q]) * u4.x, fc * (v[q + 1] + S.b2[c + q + 1]) * u4.y,
-                            fc * (v[q + 2] + S.b2[c + q + 2]) * u4.z, fc * (v[q + 3] + S.b2[c + q + 3]) * u4.w);
+                        const float4 u4 = *reinterpret_cast<const float4*>(p4);
+                        const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                        const f2::f32x2 o01 = f2::mul(f2::mul(fc2, f2::add(f2::pack(v[q], v[q + 1]), b2[0])),
+                                                      f2::pack(u4.x, u4.y));
+                        const f2::f32x2 o23 = f2::mul(f2::mul(fc2, f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1])),
+                                                      f2::pack(u4.z, u4.w));
+                        *reinterpret_cast<float4*>(p4) = make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
                     }
                 }
             }
@@ -722,11 +756,16 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 tmem_ld16(tD1 + lane_base + c, v);
                 tmem_ld16(tD4 + lane_base + c, tv);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float x = v[q] + S.b1[c + q];
-                    const float sg = sigmoid_fast(x);
-                    v[q] = x * sg;
-                    tv[q] *= fmaf(v[q], 1.f - sg, sg);     // SiLU'(x) = sg + x sg (1 - sg)
+                for (int q = 0; q < 16; q += 2) {          // two features per packed FP32 operation
+                    const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                    const f2::f32x2 t = tanh_half(x);        // sigmoid(x) = (1 + tanh(x / 2)) / 2
+                    const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                    const f2::f32x2 y = f2::mul(x, sg);
+                    const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU'(x) T
+                    v[q] = f2::lo(y);
+                    v[q + 1] = f2::hi(y);
+                    tv[q] = f2::lo(pd);
+                    tv[q + 1] = f2::hi(pd);
                 }
                 st_row8(S.a2, tid, c, F, v);
                 st_row8(S.a2, tid, c + 8, F, v + 8);
@@ -752,9 +791,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             fence_after_sync();
             cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
             __syncwarp();
-            float gphi = 0.f;
+            f2::f32x2 gphi2 = 0ull;
             {
                 const int i = valid ? row : 0;
+                const f2::f32x2 fc2 = f2::splat(fc);
                 const float* ui = a.u + (size_t)i * F;
                 const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
@@ -780,20 +820,26 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                         unpack_bf16x8(w[3], mj + 8);
                     }
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) {
+                    for (int q = 0; q < 16; q += 4) {      // two features per packed FP32 operation
                         const float4 ui4 = ui16[q / 4];
                         const float4 mi4 = mi16[q / 4];
-                        float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
-                        float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
-                        g[q] = mi4.x * uj[q] + mj[q] * ui4.x;
-                        g[q + 1] = mi4.y * uj[q + 1] + mj[q + 1] * ui4.y;
-                        g[q + 2] = mi4.z * uj[q + 2] + mj[q + 2] * ui4.z;
-                        g[q + 3] = mi4.w * uj[q + 3] + mj[q + 3] * ui4.w;
-                        gphi += g[q] * ph0 + g[q + 1] * ph1 + g[q + 2] * ph2 + g[q + 3] * ph3;
+                        const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                        const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
+                        const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
+                        const f2::f32x2 mj01 = f2::pack(mj[q], mj[q + 1]), mj23 = f2::pack(mj[q + 2], mj[q + 3]);
+                        // g = mbar_i u_j + mbar_j u_i
+                        const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), f2::pack(uj[q], uj[q + 1]),
+                                                      f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                        const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), f2::pack(uj[q + 2], uj[q + 3]),
+                                                      f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                        g[q] = f2::lo(g01); g[q + 1] = f2::hi(g01);
+                        g[q + 2] = f2::lo(g23); g[q + 3] = f2::hi(g23);
+                        gphi2 = f2::fma(g01, ph01, gphi2);
+                        gphi2 = f2::fma(g23, ph23, gphi2);
                         // the message replaces the chunks just read (this thread's row only)
+                        const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
                         *reinterpret_cast<float4*>(S.G + prow<F>(tid, c + q)) =
-                            make_float4(fc * ph0 * mj[q], fc * ph1 * mj[q + 1], fc * ph2 * mj[q + 2],
-                                        fc * ph3 * mj[q + 3]);
+                            make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
                     }
                     st_row8(S.a2, tid, c, F, g);
                     st_row8(S.a2, tid, c + 8, F, g + 8);
@@ -816,15 +862,16 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             if (tid == 0 && ok) mma_out = false;
             phase ^= 1;
             fence_after_sync();
-            float s2 = 0.f;
+            f2::f32x2 s22 = 0ull;
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
                 float ab[16], pv[16];
                 tmem_ld16(tD3 + lane_base + c, ab);
                 tmem_ld16(tD1 + lane_base + c, pv);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) s2 += ab[q] * pv[q];
+                for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::pack(pv[q], pv[q + 1]), s22);
             }
+            const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
             float se = dfc * gphi + fc * s2;
             if (l == 0 && valid) {
                 float dphi;
@@ -1040,12 +1087,14 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
             tmem_ld16(tY + lane_base + c, tv);
             uint32_t ps[8], pp[8];
 #pragma unroll
-            for (int q = 0; q < 16; q += 2) {
-                const float x0 = v[q] + S.b1[c + q], x1 = v[q + 1] + S.b1[c + q + 1];
-                const float s0 = sigmoid_fast(x0), s1 = sigmoid_fast(x1);
-                const float y0 = x0 * s0, y1 = x1 * s1;
-                ps[q / 2] = pack_bf16(y0, y1);
-                pp[q / 2] = pack_bf16(tv[q] * fmaf(y0, 1.f - s0, s0), tv[q + 1] * fmaf(y1, 1.f - s1, s1));
+            for (int q = 0; q < 16; q += 2) {              // two features per packed FP32 operation
+                const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                const f2::f32x2 t = tanh_half(x);            // sigmoid(x) = (1 + tanh(x / 2)) / 2
+                const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                const f2::f32x2 y = f2::mul(x, sg);          // SiLU
+                const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU' (e'W1)
+                ps[q / 2] = pack_bf16(f2::lo(y), f2::hi(y));
+                pp[q / 2] = pack_bf16(f2::lo(pd), f2::hi(pd));
             }
             tmem_st8(tY + lane_base + c / 2, ps);
             tmem_st8(tX + lane_base + c / 2, pp);
@@ -1070,7 +1119,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         fence_after_sync();
         cp_async_wait();                                   // the warp's u_j | mbar_j rows are in G
         __syncwarp();
-        float gphi = 0.f;
+        f2::f32x2 gphi2 = 0ull;                            // (+0, +0)
         {
             const int i = valid ? row : 0;
             const float* ui = a.u + (size_t)i * F;
@@ -1083,6 +1132,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
 #pragma unroll
                 for (int k = 0; k < 4; ++k) w[k] = *reinterpret_cast<const uint4*>(T.G + prow<F>(tid, c + 4 * k));
                 uint32_t pg[8];
+                const f2::f32x2 fc2 = f2::splat(fc);
 #pragma unroll
                 for (int q = 0; q < 16; q += 4) {
                     const float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
@@ -1091,23 +1141,22 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
                     const uint32_t u23 = q < 8 ? (q == 0 ? w[0].y : w[0].w) : (q == 8 ? w[1].y : w[1].w);
                     const uint32_t m01 = q < 8 ? (q == 0 ? w[2].x : w[2].z) : (q == 8 ? w[3].x : w[3].z);
                     const uint32_t m23 = q < 8 ? (q == 0 ? w[2].y : w[2].w) : (q == 8 ? w[3].y : w[3].w);
-                    float uj[4], mj[4];
-                    uj[0] = __uint_as_float(u01 << 16); uj[1] = __uint_as_float(u01 & 0xffff0000u);
-                    uj[2] = __uint_as_float(u23 << 16); uj[3] = __uint_as_float(u23 & 0xffff0000u);
-                    mj[0] = __uint_as_float(m01 << 16); mj[1] = __uint_as_float(m01 & 0xffff0000u);
-                    mj[2] = __uint_as_float(m23 << 16); mj[3] = __uint_as_float(m23 & 0xffff0000u);
-                    float ph0 = v[q] + S.b2[c + q], ph1 = v[q + 1] + S.b2[c + q + 1];
-                    float ph2 = v[q + 2] + S.b2[c + q + 2], ph3 = v[q + 3] + S.b2[c + q + 3];
-                    const float g0 = mi4.x * uj[0] + mj[0] * ui4.x;
-                    const float g1 = mi4.y * uj[1] + mj[1] * ui4.y;
-                    const float g2 = mi4.z * uj[2] + mj[2] * ui4.z;
-                    const float g3 = mi4.w * uj[3] + mj[3] * ui4.w;
-                    gphi += g0 * ph0 + g1 * ph1 + g2 * ph2 + g3 * ph3;
-                    pg[q / 2] = pack_bf16(g0, g1);
-                    pg[q / 2 + 1] = pack_bf16(g2, g3);
+                    const f2::f32x2 uj01 = f2::from_bf16x2(u01), uj23 = f2::from_bf16x2(u23);
+                    const f2::f32x2 mj01 = f2::from_bf16x2(m01), mj23 = f2::from_bf16x2(m23);
+                    const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                    const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
+                    const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
+                    // g = mbar_i u_j + mbar_j u_i
+                    const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), uj01, f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                    const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), uj23, f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                    gphi2 = f2::fma(g01, ph01, gphi2);
+                    gphi2 = f2::fma(g23, ph23, gphi2);
+                    pg[q / 2] = pack_bf16(f2::lo(g01), f2::hi(g01));
+                    pg[q / 2 + 1] = pack_bf16(f2::lo(g23), f2::hi(g23));
                     // the message replaces the chunk (read above into w) of this thread's row
+                    const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
                     *reinterpret_cast<float4*>(T.G + prow<F>(tid, c + q)) =
-                        make_float4(fc * ph0 * mj[0], fc * ph1 * mj[1], fc * ph2 * mj[2], fc * ph3 * mj[3]);
+                        make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
                 }
                 tmem_st8(tY + lane_base + c / 2, pg);     // over SiLU (read by the completed MMA2)
             }
@@ -1130,17 +1179,17 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         if (tid == 0 && ok) mma_out = false;
         phase ^= 1;
         fence_after_sync();
-        float s2 = 0.f;
+        f2::f32x2 s22 = 0ull;
 #pragma unroll
         for (int c = 0; c < F; c += 16) {
-            float ab[16], pv[16];
+            float ab[16];
             uint32_t pw[8];
             tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, ab);
             tmem_ld8(tX + lane_base + c / 2, pw);
-            unpack_bf16x16(pw, pv);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) s2 += ab[q] * pv[q];
+            for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::from_bf16x2(pw[q / 2]), s22);
         }
+        const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
         float se = dfc * gphi + fc * s2;
         if (l == 0 && valid) {
             float dphi;

@@ -55,7 +55,23 @@ def _with_isolated_atoms():
                     n_species=s.n_species, name="isolated40", bonds=s.bonds)
 
 
+def _tiny_molecules():
+    """Three non-periodic systems in one context: a dimer (1.2 A), a bent
+    triatomic (bonds 1.0 and 1.4 A, 2.1 A apart at the ends) and one rigid
+    water molecule; the smallest cases of every pass, with rows of one and
+    two pairs."""
+    dimer = np.array([[0.0, 0.0, 0.0], [1.2, 0.0, 0.0]])
+    tri = np.array([[10.0, 0.0, 0.0], [11.0, 0.0, 0.0], [11.3, 1.37, 0.0]])
+    w = I.water_192(0)
+    water = w.x[:3] - w.x[0] + np.array([20.0, 0.0, 0.0])
+    x = np.concatenate([dimer, tri, water])
+    return I.System(x=x, species=np.array([0, 1, 1, 0, 0, 1, 0, 0], np.int32),
+                    mass=np.array([1.008, 15.999, 15.999, 1.008, 1.008, 15.999, 1.008, 1.008]),
+                    atom_offset=np.array([0, 2, 5, 8], np.int32), box=np.zeros(3), n_species=2, name="tiny3")
+
+
 SYSTEMS = {
+    "tiny3": _tiny_molecules,
     "water192": lambda: I.water_192(0),
     "water12288": lambda: I.water_12288(0),
     "vacuum64": lambda: I.make_vacuum_batch(64, 10, 60, seed=0),
