@@ -341,6 +341,7 @@ def run_ours(args):
     if args.extras and world == 1:
         extras["langevin_hmr_5fs"] = langevin_hmr(D, I, torch, s, mdl, main_prec, args, flush)
         extras["vacuum512"] = vacuum_batch(D, I, torch, main_prec, args, flush)
+        extras["replicas8"] = replicas_batch(D, I, torch, main_prec, args, flush)
         extras["distill"] = distill_rate(D, I, torch, s, mdl, main_prec)
         extras["polymer100k"] = polymer(D, I, torch, main_prec, args, flush)
 
@@ -384,6 +385,32 @@ def vacuum_batch(D, I, torch, prec, args, flush):
             "sts_1fs_ns_per_day": k * 1.0 / FS_PER_NS / r["t_sts"] * SEC_PER_DAY,
             "ms_per_step": r["t_dmts"] * 1e3 / k, "ms_per_step_sts": r["t_sts"] * 1e3 / k,
             "pairs": {"small": r["pairs_small"], "big": r["pairs_big"]}}
+
+
+def replicas_batch(D, I, torch, prec, args, flush, n_rep=8):
+    """n_rep periodic replicas of the 1,536-atom water box (512 waters,
+    L = 24.85 A, different orientations and velocities) in one context, one
+    graph per outer step for all of them, against the same boxes each in its
+    own context run one after another; DMTS 3 fs / 1 fs."""
+    boxes = [I.make_water(8, 24.85, k) for k in range(n_rep)]
+    s = I.replicas(boxes)
+    mdl = models(2)
+    k = max(10, args.steps // 2)
+    r = measure(D, I, torch, s, mdl, prec, argparse.Namespace(steps=k, warmup=3), flush, 3.0, 3, 1)
+    t_sep = 0.0
+    for b in boxes[:2]:                                # two separate contexts, scaled to n_rep
+        rb = measure(D, I, torch, b, mdl, prec, argparse.Namespace(steps=k, warmup=3), flush, 3.0, 3, 1)
+        t_sep += rb["t_dmts"]
+        rb["ctx"].close()
+        rb["sts"].close()
+    t_sep *= n_rep / 2
+    r["ctx"].close()
+    r["sts"].close()
+    agg = n_rep * k * 3.0 / FS_PER_NS / r["t_dmts"] * SEC_PER_DAY
+    return {"workload": f"{n_rep} periodic replicas of 1,536-atom water (L = 24.85 A), {s.n_atoms} atoms", "steps": k,
+            "dmts_ns_per_day_sum_over_replicas": agg,
+            "separate_contexts_ns_per_day_sum": n_rep * k * 3.0 / FS_PER_NS / t_sep * SEC_PER_DAY,
+            "ms_per_step": r["t_dmts"] * 1e3 / k, "pairs": {"small": r["pairs_small"], "big": r["pairs_big"]}}
 
 
 def langevin_hmr(D, I, torch, s, mdl, prec, args, flush, seed=1):

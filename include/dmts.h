@@ -109,8 +109,10 @@ typedef struct {
  * [N] in [0, n_species), mass [N] > 0 (amu), box [n_systems]: edge length of
  * a periodic cubic box (Angstrom, at least twice the largest cutoff), or
  * <= 0 for a non-periodic system. Atoms of different systems never interact.
- * Supported: one periodic system, or any number of non-periodic systems of
- * at most 1024 atoms each. */
+ * Supported: any number of periodic systems sharing one box edge (replicas,
+ * each with its own cells, integrated together in one graph), or any number
+ * of non-periodic systems of at most 1024 atoms each; the two kinds are not
+ * mixed in one context. */
 typedef struct {
     int n_systems;
     const int* atom_offset;
@@ -273,16 +275,24 @@ DMTS_API int dmts_neighbor_stats(dmts_ctx* ctx, long long* n_checks, long long* 
 /* Work granularity of one model's force kernels, forward and backward:
  * atoms per thread block (FP32), or persistent thread blocks per SM (BF16,
  * 0 = as many as fit; the tensor-core kernels cut the pair list into
- * 128-pair tiles). The tuner (option "autotune", default 1) times the
- * candidates at the context's first force evaluation and keeps the fastest
- * for each pass. Results do not depend on the choice. Returns 1 if tuned, 0
+ * 128-pair tiles, and the backward kernel keeps one or two tiles in flight
+ * per CTA: dmts_get_bwd_tiles). The tuner (option "autotune", default 1)
+ * times the candidates at the context's first force evaluation and keeps the
+ * fastest for each pass. Results do not depend on the choice. Returns 1 if tuned, 0
  * if not yet, or a negative status. */
 DMTS_API int dmts_get_tuning(dmts_ctx* ctx, int which, int* atoms_fwd, int* atoms_bwd);
 
 /* Set one model's work granularity (as reported by dmts_get_tuning), clamped
  * to what the kernels support, and keep it: the tuner then leaves the context
- * alone. fwd, bwd >= 1. Results do not depend on the choice. */
-DMTS_API int dmts_set_tuning(dmts_ctx* ctx, int which, int fwd, int bwd);
+ * alone. fwd, bwd >= 1; bwd_tiles: 128-pair tiles the tensor-core backward
+ * kernel keeps in flight per CTA, 1 or 2 (two groups of 4 warps sharing one
+ * copy of the weights), 0 to keep the current choice; ignored in FP32 mode.
+ * Results do not depend on any of the choices. */
+DMTS_API int dmts_set_tuning(dmts_ctx* ctx, int which, int fwd, int bwd, int bwd_tiles);
+
+/* The tensor-core backward kernel's tiles in flight per CTA (1 or 2; the
+ * tuner picks it with the CTAs per SM; 1 in FP32 mode), or a negative status. */
+DMTS_API int dmts_get_bwd_tiles(dmts_ctx* ctx, int which);
 
 /* Time one model's force evaluation at the current positions, stage by stage,
  * with CUDA events on the context's stream, averaged over reps (>= 1)

@@ -2,7 +2,10 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library next to this file. ``build()`` is idempotent: it rebuilds only when
-a source or header is newer than the library.
+a source or header is newer than the library. ``build(check=True)`` makes
+``libdmts_check.so``, the same library compiled with -DDMTS_CHECK: the
+kernels test the pair, row and cell indices they gather with against their
+array bounds, and a call that met one outside fails naming the source line.
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmts.so")
+LIB_CHECK = os.path.join(HERE, "libdmts_check.so")
 SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu", "atom_mlp.cu", "atom_tc.cu", "distill_f32.cu"]
 HEADERS = ["internal.cuh", "umma.cuh"]
 
@@ -30,24 +34,27 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "dmts.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
     """Compile and link; returns the library path. Raises on failure."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    lib = LIB_CHECK if check else LIB
+    if not force and not _stale(lib):
+        return lib
+    bdir = BUILD + ("_check" if check else "")
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
+    flags = FLAGS + (["-DDMTS_CHECK"] if check else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+        cmd = [nvcc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -57,13 +64,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -188,12 +188,58 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
             sBias[3][t] = __ldg(P + p.off.R2 + t);
         }
     }
+    // After a tensor-core forward pass that left its split rows to this kernel
+    // (fused_fixup): a row split across 128-pair tiles gets the head tile's
+    // last carry slot plus the later tiles' first slots, in tile order, and a
+    // row without pairs zeros (the order and sums of the separate fix-up pass).
+    auto split_row = [&](int i, long long& t0, long long& t1) -> int {   // 0: in one tile, 1: split, 2: empty
+        const long long r0 = min((long long)p.row_ptr[i], p.e_cap), r1 = min((long long)p.row_ptr[i + 1], p.e_cap);
+        if (r1 <= r0) return 2;
+        t0 = r0 >> 7;
+        t1 = (r1 - 1) >> 7;
+        return t0 == t1 ? 0 : 1;
+    };
     double e_const = 0.0;                            // d2 + e0[Z_i] + E_rep,i of atom base + tid
-    if (last && tid < T::A && base + tid < p.n_atoms)
-        e_const = (double)__ldg(P + p.off.d2) + (double)__ldg(P + p.off.e0 + p.species[base + tid]) +
-                  (double)p.erep[base + tid];
+    if (tid < T::A && base + tid < p.n_atoms && (last || (p.fused_fixup && l == 0))) {
+        const int i = base + tid;
+        float erep = 0.f;
+        if (l == 0 && p.fused_fixup) {               // E_rep,i is a scalar slot of the layer-0 pass
+            long long t0 = 0, t1 = 0;
+            const int k = split_row(i, t0, t1);
+            if (k == 0) {
+                erep = p.erep[i];
+            } else if (k == 1) {
+                erep = p.carry[(2 * t0 + 1) * (long long)p.carry_w + F];
+                for (long long u = t0 + 1; u <= t1; ++u) erep += p.carry[2 * u * (long long)p.carry_w + F];
+            }
+            p.erep[i] = erep;                        // read again by the last layer of deeper models
+        } else {
+            erep = p.erep[i];
+        }
+        if (last) e_const = (double)__ldg(P + p.off.d2) + (double)__ldg(P + p.off.e0 + p.species[i]) + (double)erep;
+    }
     cp_wait<1>();
     __syncthreads();
+    if (p.fused_fixup) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = base + a0 + a;
+            if (i >= p.n_atoms) continue;
+            long long t0 = 0, t1 = 0;
+            const int k = split_row(i, t0, t1);
+            if (k == 0) continue;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k == 1) {
+                v = *reinterpret_cast<const float4*>(p.carry + (2 * t0 + 1) * (long long)p.carry_w + f0);
+                for (long long u = t0 + 1; u <= t1; ++u) {
+                    const float4 w = *reinterpret_cast<const float4*>(p.carry + 2 * u * (long long)p.carry_w + f0);
+                    v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+                }
+            }
+            *reinterpret_cast<float4*>(X + (a0 + a) * T::XS + f0) = v;
+        }
+        __syncthreads();
+    }
     gemm4x4<F>(X, W0, a0, f0, z);                                        // z = m U1 + c1
 #pragma unroll
     for (int f = 0; f < 4; ++f) {

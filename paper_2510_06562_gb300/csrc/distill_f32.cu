@@ -148,7 +148,7 @@ __device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, 
     long long e = t0 + tid;
     float eb[K], db[K];
     if (e < e_end) {
-        int j = a.col[e], i = a.recv[e];
+        int j = DMTS_IDX(a.col[e], a.n_atoms, a.check), i = DMTS_IDX(a.recv[e], a.n_atoms, a.check);
         uint4 qi = a.q[i], qj = a.q[j];
         float3 r = edge_vec(qi, qj, a.frame[qi.w].qscale);
         float d = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);

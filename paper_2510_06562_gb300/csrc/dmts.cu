@@ -39,8 +39,10 @@ void smem_opt_in(const void* kern, int bytes) {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (!done.insert({kern, dev}).second) return;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
-        done.erase({kern, dev});             // the launch then reports the error
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaGetLastError();                  // not sticky: a launch that needs more reports its own error
+        done.erase({kern, dev});
+    }
 }
 double accel_constant();
 }  // namespace dmts
@@ -167,6 +169,8 @@ struct Model {
     int row_cap = 0;
     long long e_cap = 0;
     int *nbr_tmp = nullptr, *nbr_cnt = nullptr, *row_ptr = nullptr, *col = nullptr, *recv = nullptr;
+    int *block_sum = nullptr, *chunk_sum = nullptr;   // folded row scan of fresh builds
+    unsigned int* ticket = nullptr;
     int vl_cap = 0;                    // Verlet-skin candidate rows [N][vl_cap] (ascending j)
     int *vl_rows = nullptr, *vl_cnt = nullptr;
     float *h = nullptr, *gh = nullptr, *force = nullptr, *vir6 = nullptr;
@@ -183,6 +187,7 @@ struct Model {
     double *Ei = nullptr, *E = nullptr, *W = nullptr;
     int apc_fwd = 16, apc_bwd = 16;    // FP32 kernels: atoms per CTA
     int cps_fwd = 0, cps_bwd = 0;      // tensor-core kernels: persistent CTAs per SM (0: as many as fit)
+    int bwd_tiles = 0;                 // tensor-core backward: 128-pair tiles in flight per CTA (0: default)
     float* carry = nullptr;            // tensor-core path: per-tile partial sums of split rows
     SumScratch esum{};                 // scratch of the per-system energy sum
 };
@@ -333,6 +338,7 @@ void free_model(Model& m) {
     dfree(m.atom_pos); dfree(m.cell_q);
     free_model_nbr(m);
     dfree(m.nbr_cnt); dfree(m.row_ptr); dfree(m.vl_cnt);
+    dfree(m.block_sum); dfree(m.chunk_sum); dfree(m.ticket);
     dfree(m.h); dfree(m.gh); dfree(m.force); dfree(m.vir6); dfree(m.h0); dfree(m.PT);
     for (int l = 0; l < kMaxLayers; ++l) { dfree(m.u[l]); dfree(m.z[l]); dfree(m.um[l]); }
     dfree(m.mbar[0]); dfree(m.mbar[1]); dfree(m.esum.part); dfree(m.esum.ctr);
@@ -474,7 +480,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
         double L = c->h_box[0];
         int nc = (int)floor(L / (rv * (1.0 + 1e-9) + 1e-6));
         m.nc = (nc >= 3 && cells) ? nc : 0;
-        double rho = N / (L * L * L);
+        double rho = (double)N / c->n_sys / (L * L * L);     // replicas of one box edge
         expected = 4.0 / 3.0 * M_PI * m.rc * m.rc * m.rc * rho;
         m.row_cap = std::min(N, (int)(ceil(expected * 1.5 / 32.0) * 32) + 32);
         m.e_cap = (long long)(N * expected * c->cap_factor) + 1024;
@@ -494,7 +500,7 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
         m.e_cap = std::max<long long>(1024, std::min<long long>(sq, (long long)(N * std::min(mx, 64) * c->cap_factor)) + 1024);
     }
     if (m.nc > 0) {
-        m.n_cells = m.nc * m.nc * m.nc;
+        m.n_cells = c->n_sys * m.nc * m.nc * m.nc;            // each system its own cells
         CUDA_TRY(dalloc(&m.cell_count, m.n_cells));
         CUDA_TRY(cudaMemset(m.cell_count, 0, sizeof(int) * m.n_cells));
         CUDA_TRY(dalloc(&m.atom_pos, N));
@@ -513,6 +519,14 @@ int init_model(dmts_ctx* c, Model& m, const dmts_model_desc* d, bool cells) {
     CUDA_TRY(alloc_model_nbr(c, m));
     CUDA_TRY(dalloc(&m.nbr_cnt, N));
     CUDA_TRY(dalloc(&m.vl_cnt, N));
+    {   // folded row scan: a pair count per build block of 8 atoms and per chunk of 32 blocks
+        const size_t nb = (size_t)(N + 7) / 8, nch = (nb + 31) / 32 + 1;
+        CUDA_TRY(dalloc(&m.block_sum, nb));
+        CUDA_TRY(dalloc(&m.chunk_sum, nch));
+        CUDA_TRY(dalloc(&m.ticket, 1));
+        CUDA_TRY(cudaMemset(m.chunk_sum, 0, sizeof(int) * nch));
+        CUDA_TRY(cudaMemset(m.ticket, 0, sizeof(unsigned int)));
+    }
     CUDA_TRY(dalloc(&m.row_ptr, N + 1));
     size_t nf = (size_t)N * m.F;
     CUDA_TRY(dalloc(&m.h, nf));
@@ -579,11 +593,17 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
     a.placed = m.placed ? 1 : 0;
     a.n_cells = m.nc > 0 ? m.n_cells : 0;
     a.cell_count = m.cell_count;
+    if (c->skin <= 0) {                    // fresh builds fold the row scan into the compaction
+        a.block_sum = m.block_sum;
+        a.chunk_sum = m.chunk_sum;
+        a.ticket = m.ticket;
+    }
     return a;
 }
 
 PotArgs pot_args(dmts_ctx* c, Model& m) {
     PotArgs a{};
+    a.check = c->d_flags;
     a.P = m.P;
     a.off = m.off;
     a.n_layers = m.L;
@@ -645,6 +665,9 @@ NbrArgs candidate_args(dmts_ctx* c, int w) {
     a.nbr_cnt = m.vl_cnt;
     a.flag_row = kFlagMaxVl0 + w;
     a.gate = &c->d_vl->rebuild;
+    a.block_sum = nullptr;
+    a.chunk_sum = nullptr;
+    a.ticket = nullptr;
     return a;
 }
 
@@ -761,7 +784,7 @@ void launch_edge_bwd(dmts_ctx* c, Model& m, const PotArgs& a) {
 
 // Arguments of layer l's forward pass (edge kernel, then atom MLP) and
 // backward pass (edge kernel, then atom MLP for l > 0).
-PotArgs fwd_args(const PotArgs& a, Model& m, int l) {
+PotArgs fwd_args(dmts_ctx* c, const PotArgs& a, Model& m, int l) {
     PotArgs f = a;
     f.layer = l;
     f.h_in = l == 0 ? m.h0 : m.h;
@@ -771,6 +794,9 @@ PotArgs fwd_args(const PotArgs& a, Model& m, int l) {
     f.u_next = (l + 1 < m.L) ? m.u[l + 1] : nullptr;
     f.z = m.z[l];
     f.mbar_out = m.mbar[(m.L - 1) & 1];
+    // the SIMT per-atom kernel after a tensor-core forward pass sums the split
+    // rows itself (one launch fewer); the tensor-core one reads finished rows
+    f.fused_fixup = (m.precision == DMTS_BF16_MLP && !atom_on_tc(c, m)) ? 1 : 0;
     if (m.precision == DMTS_BF16_MLP) {
         f.um_u_out = (l + 1 < m.L) ? m.um[l + 1] : nullptr;
         f.um_mbar_out = m.um[m.L - 1];
@@ -783,6 +809,7 @@ PotArgs bwd_args(const PotArgs& a, Model& m, int l) {
     b.layer = l;
     b.atoms_per_cta = m.apc_bwd;
     b.ctas_per_sm = m.cps_bwd;
+    b.bwd_tiles = m.bwd_tiles;
     b.u = m.u[l];
     b.mbar = m.mbar[l & 1];
     b.mbar_out = (l > 0) ? m.mbar[(l - 1) & 1] : nullptr;
@@ -802,7 +829,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     PotArgs a = pot_args(c, m);
     a.virial = virial ? 1 : 0;
     for (int l = 0; l < m.L; ++l) {
-        PotArgs f = fwd_args(a, m, l);
+        PotArgs f = fwd_args(c, a, m, l);
         launch_edge_fwd(c, m, f);
         launch_atom_fwd_m(c, m, f);
     }
@@ -822,6 +849,11 @@ int sync_check(dmts_ctx* c) {
         return fail(DMTS_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
     }
     CUDA_TRY(cudaMemcpy(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost));
+    if (c->h_flags[kFlagCheck]) {            // checked builds only
+        c->broken = true;
+        return fail(DMTS_ERR_CUDA, "index check failed (source line %d): an index outside its array",
+                    c->h_flags[kFlagCheck]);
+    }
     if (const int t = c->h_flags[kFlagTimeout]) {
         // bit 0: a bounded wait gave up and its kernel stopped early (results
         // invalid); bit 1: work it had in flight did not finish in time either
@@ -1068,32 +1100,39 @@ int autotune_models(dmts_ctx* c) {
         Model& m = c->m[w];
         if (!m.present) continue;
         const bool tc = m.precision == DMTS_BF16_MLP;
-        // tensor-core kernels: persistent CTAs per SM; FP32 kernels: atoms per CTA
-        const int mx = tc ? std::max(bf16_max_ctas_per_sm(m.F, false), bf16_max_ctas_per_sm(m.F, true)) : 0;
-        std::vector<int> cand;
-        if (tc) for (int k = 1; k <= mx; ++k) cand.push_back(k);
-        else cand = m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48};
-        const int lim_f = tc ? bf16_max_ctas_per_sm(m.F, false) : max_atoms_per_cta_f32(m.F, m.K, false);
-        const int lim_b = tc ? bf16_max_ctas_per_sm(m.F, true) : max_atoms_per_cta_f32(m.F, m.K, true);
+        // tensor-core kernels: persistent CTAs per SM, and the backward
+        // kernel's tiles in flight per CTA (one, or two sharing the weights);
+        // FP32 kernels: atoms per CTA
+        std::vector<int> tiles_c = tc ? std::vector<int>{1, 2} : std::vector<int>{0};
         int& gf = tc ? m.cps_fwd : m.apc_fwd;
         int& gb = tc ? m.cps_bwd : m.apc_bwd;
         double best_tf = 1e30, best_tb = 1e30;
-        int best_f = gf, best_b = gb;
-        for (int A : cand) {
-            gf = std::min(A, lim_f);
-            gb = std::min(A, lim_b);
-            std::vector<double> st;
-            if ((rc = time_stages_impl(c, w, 3, st))) break;   // sizes capacities, then times the stages
-            double tf = 0.0, tb = 0.0;                          // forward and backward edge passes
-            for (int l = 0; l < m.L; ++l) {
-                tf += st[2 + l];
-                tb += st[2 + 2 * m.L + l];
+        int best_f = gf, best_b = gb, best_t = m.bwd_tiles;
+        for (int tiles : tiles_c) {
+            const int lim_f = tc ? bf16_max_ctas_per_sm(m.F, false) : max_atoms_per_cta_f32(m.F, m.K, false);
+            const int lim_b = tc ? bf16_max_ctas_per_sm(m.F, true, tiles) : max_atoms_per_cta_f32(m.F, m.K, true);
+            std::vector<int> cand;
+            if (tc) for (int k = 1; k <= std::max(lim_f, lim_b); ++k) cand.push_back(k);
+            else cand = m.F == 64 ? std::vector<int>{8, 16, 24} : std::vector<int>{16, 32, 48};
+            m.bwd_tiles = tiles;
+            for (int A : cand) {
+                gf = std::min(A, lim_f);
+                gb = std::min(A, lim_b);
+                std::vector<double> st;
+                if ((rc = time_stages_impl(c, w, 3, st))) break;   // sizes capacities, then times the stages
+                double tf = 0.0, tb = 0.0;                          // forward and backward edge passes
+                for (int l = 0; l < m.L; ++l) {
+                    tf += st[2 + l];
+                    tb += st[2 + 2 * m.L + l];
+                }
+                if (tf < best_tf) { best_tf = tf; best_f = gf; }
+                if (tb < best_tb) { best_tb = tb; best_b = gb; best_t = tiles; }
             }
-            if (tf < best_tf) { best_tf = tf; best_f = gf; }
-            if (tb < best_tb) { best_tb = tb; best_b = gb; }
+            if (rc) break;
         }
         gf = best_f;
         gb = best_b;
+        m.bwd_tiles = best_t;
     }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     c->tuned = true;
@@ -1194,7 +1233,9 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
             return fail(DMTS_ERR_ARG, "non-periodic system %d has more than %d atoms", s, kMaxMolAtoms);
         }
     }
-    if (n_per > 0 && ns != 1) return fail(DMTS_ERR_ARG, "a periodic box must be the only system");
+    if (n_per > 0 && n_per != ns) return fail(DMTS_ERR_ARG, "periodic and non-periodic systems cannot be mixed");
+    for (int s = 1; s < n_per; ++s)
+        if (sys->box[s] != sys->box[0]) return fail(DMTS_ERR_ARG, "periodic systems must share one box edge");
     int S_min = std::min(big->n_species, small ? small->n_species : 1 << 30);
     for (int i = 0; i < N; ++i) {
         if (sys->species[i] < 0 || sys->species[i] >= S_min) return fail(DMTS_ERR_ARG, "species[%d] out of range", i);
@@ -1772,7 +1813,7 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
         begin(1);                                  // the embedding is built once per parameter upload
         end(1);
         for (int l = 0; l < L; ++l) {
-            PotArgs f = fwd_args(a, m, l);
+            PotArgs f = fwd_args(c, a, m, l);
             begin(2 + l);
             launch_edge_fwd(c, m, f);
             end(2 + l);
@@ -1881,15 +1922,17 @@ int dmts_get_tuning(dmts_ctx* c, int which, int* atoms_fwd, int* atoms_bwd) {
     return c->tuned ? 1 : 0;
 }
 
-int dmts_set_tuning(dmts_ctx* c, int which, int fwd, int bwd) {
+int dmts_set_tuning(dmts_ctx* c, int which, int fwd, int bwd, int bwd_tiles) {
     CTX_GUARD(c);
     if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
     Model& m = c->m[which];
     if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
     if (fwd < 1 || bwd < 1) return fail(DMTS_ERR_ARG, "granularity must be >= 1");
+    if (bwd_tiles < 0 || bwd_tiles > 2) return fail(DMTS_ERR_ARG, "bwd_tiles must be 0, 1 or 2");
     if (m.precision == DMTS_BF16_MLP) {
+        if (bwd_tiles > 0) m.bwd_tiles = bwd_tiles;
         m.cps_fwd = std::min(fwd, bf16_max_ctas_per_sm(m.F, false));
-        m.cps_bwd = std::min(bwd, bf16_max_ctas_per_sm(m.F, true));
+        m.cps_bwd = std::min(bwd, bf16_max_ctas_per_sm(m.F, true, m.bwd_tiles));
     } else {
         m.apc_fwd = std::min(fwd, max_atoms_per_cta_f32(m.F, m.K, false));
         m.apc_bwd = std::min(bwd, max_atoms_per_cta_f32(m.F, m.K, true));
@@ -1897,6 +1940,15 @@ int dmts_set_tuning(dmts_ctx* c, int which, int fwd, int bwd) {
     c->tuned = true;                          // the tuner keeps the caller's choice
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return DMTS_OK;
+}
+
+int dmts_get_bwd_tiles(dmts_ctx* c, int which) {
+    if (!c) return fail(DMTS_ERR_ARG, "context is NULL");
+    if (which != DMTS_SMALL && which != DMTS_BIG) return fail(DMTS_ERR_ARG, "which must be 0 or 1");
+    const Model& m = c->m[which];
+    if (!m.present) return fail(DMTS_ERR_ARG, "no small model in this context");
+    if (m.precision != DMTS_BF16_MLP) return 1;
+    return m.bwd_tiles > 0 ? m.bwd_tiles : bf16_default_bwd_tiles(m.F);
 }
 
 int dmts_wait_selftest(dmts_ctx* c, int arrive, int max_polls) {

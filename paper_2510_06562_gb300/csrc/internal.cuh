@@ -17,6 +17,28 @@
 
 namespace dmts {
 
+// Checked builds (compiled with -DDMTS_CHECK): the pair, row and cell indices
+// the kernels gather and scatter with are tested against their array bounds
+// before use. An index outside [0, n) records the source line in
+// flags[kFlagCheck] (the largest line wins) and is replaced by 0, so the
+// access stays inside the array; the call then fails with a message naming
+// the line. Ordinary builds compile the check away. This stands in for a
+// memory checker where none can be run.
+#ifdef DMTS_CHECK
+#define DMTS_IDX(i, n, flags) ::dmts::checked_index((i), (n), (flags), __LINE__)
+#else
+#define DMTS_IDX(i, n, flags) (i)
+#endif
+
+template <class I>
+__device__ __forceinline__ I checked_index(I i, long long n, int* flags, int line) {
+    if ((long long)i < 0 || (long long)i >= n) {
+        if (flags) atomicMax(flags + 13, line);          // flags[kFlagCheck]
+        return (I)0;
+    }
+    return i;
+}
+
 constexpr int kMaxLayers = 4;
 constexpr int kThreads = 256;          // threads per CTA of the edge kernels
 constexpr int kMaxMolAtoms = 1024;     // atoms per non-periodic system
@@ -55,8 +77,10 @@ enum Flag {
     kFlagMaxCell0 = 10,    // most atoms placed in one cell, when a cell overflowed (small model)
     kFlagMaxCell1 = 11,    // (big)
     kFlagMoved = 12,       // dmts_set_state: a position differs from the current one
-    kFlagCount = 13
+    kFlagCheck = 13,       // checked builds: source line of an index outside its array
+    kFlagCount = 14
 };
+static_assert(kFlagCheck == 13, "checked_index records into flags[13]");
 
 // Verlet-skin bookkeeping (device memory, one per context). The candidate
 // rows of both models were built at the positions x_ref; k_vl_check reduces
@@ -155,6 +179,13 @@ struct NbrArgs {
     int n_cells;
     int* cell_count;
     int placed;              // the atoms are already in the cells (placed by the integrator kernel)
+    // fresh lists: the row scan folded into the compaction. The build adds each
+    // block's pair count to block_sum [ceil(N / 8)] and chunk_sum
+    // [ceil(N / 256)] (zero between builds: the compaction's last block clears
+    // chunk_sum and its ticket)
+    int* block_sum;
+    int* chunk_sum;
+    unsigned int* ticket;
 };
 
 // Fixed-capacity cells of one model, for the integrator kernel that moves the
@@ -170,6 +201,7 @@ struct CellPlace {
 
 // Arguments of the potential's kernels (one model, one layer).
 struct PotArgs {
+    int* check;              // checked builds: flags array receiving index violations
     const float* P;          // FP32 parameters, flat order
     ModelOffsets off;
     int layer;
@@ -220,6 +252,8 @@ struct PotArgs {
     float* carry;            // [tiles][2][carry_w] partial sums of rows split across tiles
     int carry_w;             // F + 16
     int ctas_per_sm;         // persistent CTAs per SM (0: as many as fit)
+    int bwd_tiles;           // tensor-core backward: 128-pair tiles in flight per CTA (1 or 2; 0: 2 at F = 64, else 1)
+    int fused_fixup;         // tensor-core forward: the per-atom kernel after it sums the split rows itself
 };
 
 // ---------------------------------------------------------------- launchers
@@ -257,7 +291,10 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
 // the wait of at most `polls` polls gives up; with arrive = 0 nothing arrives.
 void launch_wait_selftest(int arrive, unsigned int polls, int* status, cudaStream_t s);
 size_t bf16_weight_tile_bytes(int F);
-int bf16_max_ctas_per_sm(int F, bool bwd);
+// CTAs per SM that fit for the forward (bwd = false) or backward kernel;
+// tiles: the backward kernel's tiles in flight per CTA (1 or 2).
+int bf16_max_ctas_per_sm(int F, bool bwd, int tiles = 0);
+int bf16_default_bwd_tiles(int F);
 
 // distill_f32.cu: force-matching gradient of a single-layer model
 bool fm_supported(int F, int K, int L);
@@ -450,9 +487,15 @@ __device__ __forceinline__ int cell_coord(unsigned int qc, int nc) {
 // it; an atom beyond the capacity is not placed, and the overflow is flagged
 // (the list is rebuilt with larger cells). The slot order varies from run to
 // run; the builder sorts every row by j, so the list does not.
+// Cell of a fixed-point position: periodic systems of one box edge, stored
+// back to back, each own nc^3 cells (system p.w first).
+__device__ __forceinline__ int cell_of(uint4 p, int nc) {
+    return ((int)p.w * nc + cell_coord(p.z, nc)) * nc * nc + cell_coord(p.y, nc) * nc + cell_coord(p.x, nc);
+}
+
 __device__ __forceinline__ void place_in_cell(const CellPlace& cp, int i, uint4 p, int* __restrict__ flags) {
     const int nc = cp.nc;
-    const int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
+    const int c = cell_of(p, nc);
     const int slot = atomicAdd(&cp.count[c], 1);
     if (slot < cp.ccap) {
         const int pos = c * cp.ccap + slot;

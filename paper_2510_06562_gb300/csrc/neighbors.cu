@@ -137,7 +137,7 @@ __global__ void k_cell_count(int n, const uint4* __restrict__ q, int nc, int* __
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint4 p = q[i];
-    int c = (cell_coord(p.z, nc) * nc + cell_coord(p.y, nc)) * nc + cell_coord(p.x, nc);
+    int c = cell_of(p, nc);
     atom_cell[i] = c;
     slot[i] = atomicAdd(&count[c], 1);
 }
@@ -268,19 +268,43 @@ __device__ __forceinline__ bool exact_inside(const double* __restrict__ x, int n
 }
 
 constexpr int kNbrWarps = 8;
+constexpr int kChunkBlocks = 32;      // build blocks per chunk of the folded row scan
+// dynamic shared memory the builder may use: the per-block maximum (227 KB)
+// less room for its static arrays
+constexpr int kNbrDynSmemMax = 226 * 1024;
 
 // One warp per atom i: enumerate candidates (27 cells, or every atom of the
 // system), keep those inside the cutoff, sort the row by j (rank sort) and
 // store it in the fixed-capacity staging array.
+__device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int& n_out);
+
+// With block_sum set, the block also publishes its pair count (the sum of its
+// kNbrWarps rows) for the compaction's folded scan.
 __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
     if (gated_off(a.gate)) return;
     extern __shared__ int smem_i[];
+    __shared__ int rows_n[kNbrWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int n_out = 0;
+    if (blockIdx.x * kNbrWarps + w < a.n_atoms) nbr_build_row(a, smem_i, n_out);
+    if (!a.block_sum) return;
+    if (lane == 0) rows_n[w] = n_out;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int k = 0; k < kNbrWarps; ++k) sum += rows_n[k];
+        a.block_sum[blockIdx.x] = sum;
+        atomicAdd(&a.chunk_sum[blockIdx.x / kChunkBlocks], sum);    // integer: exact in any order
+    }
+}
+
+// Row of atom i = blockIdx.x * kNbrWarps + warp; n_out receives its length.
+__device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int& n_out) {
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* row = smem_i + w * (a.row_cap + 64);
     int* cstart = row + a.row_cap;       // 27 cell starts
     int* cpre = cstart + 28;             // 28 prefix sums
     int i = blockIdx.x * kNbrWarps + w;
-    if (i >= a.n_atoms) return;
     uint4 qi = a.q[i];
     int s = (int)qi.w;
     float qscale = a.frame[s].qscale;
@@ -295,7 +319,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
         if (lane < 27) {
             int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
             int x2 = (cx + dx + nc) % nc, y2 = (cy + dy + nc) % nc, z2 = (cz + dz + nc) % nc;
-            int c = (z2 * nc + y2) * nc + x2;
+            int c = ((s * nc + z2) * nc + y2) * nc + x2;       // the system's own cells
+            c = DMTS_IDX(c, a.ccap > 0 ? (long long)a.n_cells : (long long)nc * nc * nc * a.n_sys, a.flags);
             if (a.ccap > 0) {                        // fixed-capacity cells
                 st = c * a.ccap;
                 cnt = min(a.cell_count[c], a.ccap);
@@ -331,15 +356,16 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
                 for (int step = 16; step > 0; step >>= 1)
                     if (c + step < 27 && cpre[c + step] <= v) c += step;
                 // candidates in cell order: consecutive lanes read consecutive positions
-                const int pos = cstart[c] + (v - cpre[c]);
+                const int pos = DMTS_IDX(cstart[c] + (v - cpre[c]),
+                                         a.ccap > 0 ? (long long)a.n_cells * a.ccap : (long long)a.n_atoms, a.flags);
                 if (pos != my_pos) {
                     float3 r = edge_vec(qi, a.cell_q[pos], qscale);
                     float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                     if (d2 < rc2_lo) {
                         keep = true;
-                        j = a.cell_atoms[pos];
+                        j = DMTS_IDX(a.cell_atoms[pos], a.n_atoms, a.flags);
                     } else if (d2 <= rc2_hi) {
-                        j = a.cell_atoms[pos];
+                        j = DMTS_IDX(a.cell_atoms[pos], a.n_atoms, a.flags);
                         keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
                     }
                 }
@@ -374,6 +400,71 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_build(NbrArgs a) {
         dst[rank] = jk;
     }
     if (lane == 0) a.nbr_cnt[i] = n_keep;
+    n_out = n_keep;
+}
+
+// Compaction with the row scan folded in (fresh lists, block_sum set): block
+// b holds atoms kNbrWarps b .. + kNbrWarps - 1, the build's block b. Warp 0
+// adds the pair counts of every earlier chunk of kChunkBlocks build blocks
+// and of the earlier blocks of this chunk; the block's rows follow in atom
+// order. row_ptr[n] and the capacity checks come from the block of the last
+// atom. The last block to finish clears the chunk sums and the ticket for
+// the next build.
+__global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_compact_scan(NbrArgs a) {
+    __shared__ int base_s, row_beg[kNbrWarps + 1];
+    if (a.ccap > 0)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
+            a.cell_count[k] = 0;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x, chunk = b / kChunkBlocks;
+    if (w == 0) {
+        long long sum = 0;
+        for (int c = lane; c < chunk; c += 32) sum += a.chunk_sum[c];
+        for (int c = chunk * kChunkBlocks + lane; c < b; c += 32) sum += a.block_sum[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        int cnt = 0;
+        const int i = b * kNbrWarps + lane;
+        if (lane < kNbrWarps && i < a.n_atoms) cnt = a.nbr_cnt[i];
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane <= kNbrWarps) row_beg[lane] = (int)sum + incl - cnt;
+        if (lane == 0) base_s = (int)sum;
+    }
+    __syncthreads();
+    const int i = b * kNbrWarps + w;
+    if (i < a.n_atoms) {
+        const int beg = row_beg[w], cnt = row_beg[w + 1] - beg;
+        if (lane == 0) a.row_ptr[i] = beg;
+        if (i == a.n_atoms - 1 && lane == 0) {
+            const int total = beg + cnt;
+            a.row_ptr[a.n_atoms] = total;
+            if ((long long)total > a.e_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+            atomicMax(&a.flags[kFlagMaxE0 + a.which], total);
+        }
+        const int* src = a.nbr_tmp + (size_t)i * a.row_cap;
+        for (int k = lane; k < cnt; k += 32) {
+            const long long e = (long long)beg + k;
+            if (e < a.e_cap) {
+                a.col[e] = src[k];
+                a.recv[e] = i;
+            }
+        }
+    }
+    // every block has read the chunk sums: the last one clears them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
+            const int n_chunks = (gridDim.x + kChunkBlocks - 1) / kChunkBlocks;
+            for (int c = 0; c < n_chunks; ++c) a.chunk_sum[c] = 0;
+            *a.ticket = 0u;
+        }
+    }
 }
 
 __global__ void k_nbr_compact(NbrArgs a) {
@@ -463,7 +554,7 @@ void launch_row_filter(const NbrArgs& a, cudaStream_t s) {
 
 void launch_vl_build(const NbrArgs& a, cudaStream_t s) {
     if (a.n_atoms == 0) return;
-    smem_opt_in((const void*)k_nbr_build, 227 * 1024);
+    smem_opt_in((const void*)k_nbr_build, kNbrDynSmemMax);
     int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
@@ -493,10 +584,15 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
         k_cell_place<<<(a.n_atoms + 255) / 256, 256, 0, s>>>(a.n_atoms, a.q, cp, a.flags);
         count_launch();
     }
-    smem_opt_in((const void*)k_nbr_build, 227 * 1024);
+    smem_opt_in((const void*)k_nbr_build, kNbrDynSmemMax);
     int blocks = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
+    if (a.block_sum) {                     // row scan folded into the compaction
+        k_nbr_compact_scan<<<blocks, kNbrWarps * 32, 0, s>>>(a);
+        count_launch(2);
+        return;
+    }
     k_scan_1cta<<<1, kScanThreads, 0, s>>>(a.n_atoms, a.nbr_cnt, a.row_ptr, a.e_cap, a.flags,
                                           kFlagMaxE0 + a.which, nullptr);
     k_nbr_compact<<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a);

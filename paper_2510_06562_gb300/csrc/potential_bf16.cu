@@ -116,8 +116,8 @@ struct EdgeIn {
 
 __device__ __forceinline__ void load_idx(const PotArgs& a, long long e, long long e_end, EdgeIn& x) {
     if (e < e_end) {
-        x.j = __ldg(a.col + e);
-        x.i = __ldg(a.recv + e);
+        x.j = DMTS_IDX(__ldg(a.col + e), a.n_atoms, a.check);
+        x.i = DMTS_IDX(__ldg(a.recv + e), a.n_atoms, a.check);
     } else {
         x.j = -1;
         x.i = -1;
@@ -381,49 +381,99 @@ __device__ __forceinline__ void merge_tile_scal(const ScalSlots<NV>* ss, int c, 
     if (cur >= 0) put(cur, run, first, true);
 }
 
-// Split rows and rows without pairs after a tiled pass (one warp per atom):
-// rows inside one tile were written by the pass. vec_out (F values per atom)
-// may be null; n_scal scalars go to erep (kind 0) or to the force and the
-// per-atom virial (kind 1, added when accumulate).
+// Rows without pairs: the thread of the first pair after such rows writes
+// their outputs (zeros), and the thread of the last pair writes those of the
+// rows after it, so a tiled pass writes every row that does not cross a tile
+// boundary. rp: the row of the previous pair (-1 for the first); vec: F
+// values per row (or null); zero(r) writes the row's scalar outputs.
+template <int F, class Zero>
+__device__ __forceinline__ void fill_empty_rows(int rp, int row, bool last_pair, int n_atoms, float* __restrict__ vec,
+                                                Zero zero) {
+    auto fill = [&](int r) {
+        if (vec) {
+            float4* p = reinterpret_cast<float4*>(vec + (size_t)r * F);
+#pragma unroll
+            for (int k = 0; k < F / 4; ++k) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        zero(r);
+    };
+    for (int r = rp + 1; r < row; ++r) fill(r);
+    if (last_pair)
+        for (int r = row + 1; r < n_atoms; ++r) fill(r);
+}
+
+// The row of the pair before this thread's (-1 for pair 0): from the lane
+// below, or for lane 0 from the pair list. Every lane of the warp calls it.
+__device__ __forceinline__ int prev_pair_row(const int* __restrict__ recv, long long e, int row) {
+    const int lane = threadIdx.x & 31;
+    const int up = __shfl_up_sync(0xffffffffu, row, 1);
+    return lane > 0 ? up : (e > 0 ? __ldg(recv + e - 1) : -1);
+}
+
+// Rows split across tiles, after a tiled pass: one warp per tile boundary t
+// (1 <= t < tiles). The warp of the first boundary a row crosses gives it the
+// sum of its head tile's last carry slot and the later tiles' first slots,
+// in tile order. vec_out (F values per atom) may be null; n_scal scalars go
+// to erep (kind 0) or to the force and the per-atom virial (kind 1, added
+// when accumulate). With no pairs at all, the warps write every row's zeros.
 template <int F>
-__global__ void __launch_bounds__(256) k_tile_fixup(int n, const int* __restrict__ row_ptr, long long e_cap,
+__global__ void __launch_bounds__(256) k_tile_fixup(int n, const int* __restrict__ row_ptr,
+                                                    const int* __restrict__ recv, long long e_cap,
                                                     const float* __restrict__ carry, int cw, float* __restrict__ vec_out,
                                                     int n_scal, int kind, float* __restrict__ erep,
                                                     float* __restrict__ force, float* __restrict__ vir6,
-                                                    int accumulate) {
+                                                    int accumulate, int* check) {
     constexpr int NF = F / 32;
     const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    const long long r0 = min((long long)row_ptr[i], e_cap), r1 = min((long long)row_ptr[i + 1], e_cap);
-    float v[NF], sc = 0.f;
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long E = min((long long)row_ptr[n], e_cap);
+    auto put = [&](long long i, const float* v, float sc) {
+        if (vec_out)
+#pragma unroll
+            for (int c = 0; c < NF; ++c) vec_out[(size_t)i * F + lane + 32 * c] = v[c];
+        if (lane < n_scal) {
+            if (kind == 0) {
+                erep[i] = sc;
+            } else {
+                float* dst = lane < 3 ? force + (size_t)lane * n + i : vir6 + (size_t)i * 6 + lane - 3;
+                *dst = accumulate ? *dst + sc : sc;
+            }
+        }
+    };
+    float v[NF];
 #pragma unroll
     for (int c = 0; c < NF; ++c) v[c] = 0.f;
-    if (r1 > r0) {
-        const long long t0 = r0 >> 7, t1 = (r1 - 1) >> 7;
-        if (t0 == t1) return;                              // written by the tile
-        const float* cl = carry + (2 * t0 + 1) * (long long)cw;
-#pragma unroll
-        for (int c = 0; c < NF; ++c) v[c] = cl[lane + 32 * c];
-        if (lane < n_scal) sc = cl[F + lane];
-        for (long long u = t0 + 1; u <= t1; ++u) {
-            const float* cf = carry + 2 * u * (long long)cw;
-#pragma unroll
-            for (int c = 0; c < NF; ++c) v[c] += cf[lane + 32 * c];
-            if (lane < n_scal) sc += cf[F + lane];
-        }
+    if (E == 0) {
+        const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+        for (long long i = w; i < n; i += nw) put(i, v, 0.f);
+        return;
     }
-    if (vec_out)
+    const long long t = w + 1, n_tiles = (E + 127) >> 7;
+    if (t >= n_tiles) return;
+    const int r = DMTS_IDX(recv[t << 7], n, check);
+    if (recv[(t << 7) - 1] != r) return;                // no row crosses boundary t
+    const long long r0 = min((long long)row_ptr[r], e_cap), r1 = min((long long)row_ptr[r + 1], e_cap);
+    const long long t0 = r0 >> 7, t1 = (r1 - 1) >> 7;
+    if (t0 != t - 1) return;                            // the warp of an earlier boundary sums it
+    const float* cl = carry + (2 * t0 + 1) * (long long)cw;
+    float sc = 0.f;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) vec_out[(size_t)i * F + lane + 32 * c] = v[c];
-    if (lane < n_scal) {
-        if (kind == 0) {
-            erep[i] = sc;
-        } else {
-            float* dst = lane < 3 ? force + (size_t)lane * n + i : vir6 + (size_t)i * 6 + lane - 3;
-            *dst = accumulate ? *dst + sc : sc;
-        }
+    for (int c = 0; c < NF; ++c) v[c] = cl[lane + 32 * c];
+    if (lane < n_scal) sc = cl[F + lane];
+    for (long long u = t0 + 1; u <= t1; ++u) {
+        const float* cf = carry + 2 * u * (long long)cw;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) v[c] += cf[lane + 32 * c];
+        if (lane < n_scal) sc += cf[F + lane];
     }
+    put(r, v, sc);
+}
+
+// Blocks of the fix-up for a pair capacity of e_cap (one warp per possible
+// tile boundary, at least one block).
+inline int fixup_blocks(long long e_cap) {
+    const long long warps = std::max(1LL, (e_cap + 127) / 128);
+    return (int)((warps * 32 + 255) / 256);
 }
 
 // ------------------------------------------------------------ forward
@@ -494,6 +544,13 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const bool valid = ex.j >= 0;
             const int j = valid ? ex.j : 0;
             const int row = valid ? ex.i : -1;
+            {
+                const int rp = prev_pair_row(a.recv, tb + tid, row);
+                if (valid)
+                    fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, a.msg_out, [&](int r) {
+                        if (l == 0) a.erep[r] = 0.f;
+                    });
+            }
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // the message needs u_j: start copying the warp's rows into P now
             gather_rows<F>(S.P, a.u, j, tid);
@@ -608,6 +665,18 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
 }
 
 // ------------------------------------------------------------ backward
+// The force (and per-atom virial) of a row without pairs: zero in the pass
+// that writes them (the others add).
+template <int NV>
+__device__ __forceinline__ void zero_force_row(const PotArgs& a, int r) {
+    if (a.accumulate) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.force[(size_t)c * a.n_atoms + r] = 0.f;
+    if constexpr (NV == 9)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.vir6[(size_t)r * 6 + c] = 0.f;
+}
+
 template <int F, int NV>
 struct BwdSmem {
     unsigned char w1t[F * kKP * 2];     // B[n][k] = W1[k][n]
@@ -704,6 +773,12 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             const bool valid = ex.j >= 0;
             const int j = valid ? ex.j : 0;
             const int row = valid ? ex.i : -1;
+            {
+                const int rp = prev_pair_row(a.recv, tb + tid, row);
+                if (valid)
+                    fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
+                                       [&](int r) { zero_force_row<NV>(a, r); });
+            }
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // g needs u_j and mbar_j, the ubar message mbar_j: start the warp's row copies now
             gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j, tid);
@@ -764,8 +839,10 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                     const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU'(x) T
                     v[q] = f2::lo(y);
                     v[q + 1] = f2::hi(y);
-                    tv[q] = f2::lo(pd);
-                    tv[q + 1] = f2::hi(pd);
+                    // rounded to BF16 as the two-tile kernel keeps it, so the
+                    // tuner's choice between the kernels changes no result
+                    tv[q] = __bfloat162float(__float2bfloat16_rn(f2::lo(pd)));
+                    tv[q + 1] = __bfloat162float(__float2bfloat16_rn(f2::hi(pd)));
                 }
                 st_row8(S.a2, tid, c, F, v);
                 st_row8(S.a2, tid, c + 8, F, v + 8);
@@ -1036,6 +1113,12 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         const bool valid = ex.j >= 0;
         const int j = valid ? ex.j : 0;
         const int row = valid ? ex.i : -1;
+        {
+            const int rp = prev_pair_row(a.recv, tb + tid, row);
+            if (valid)
+                fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
+                                   [&](int r) { zero_force_row<NV>(a, r); });
+        }
         load_idx(a, (tile + step) * kT + tid, E, nx);      // this group's next tile's indices
         gather_rows<F>(T.G, reinterpret_cast<const float*>(a.um), j, tid);
         cp_async_commit();
@@ -1290,9 +1373,7 @@ void launch_persistent(Kern kern, int smem, int tmem_cols, int threads, int tile
     if (grid > 0) kern<<<(int)grid, threads, smem, s>>>(a, K, status);
 }
 
-// Tiles in flight per CTA of the F = 64 backward pass (k_edge_bwd_grp). At
-// F = 32 the one-tile kernel measured faster (28.6 vs 31.6 us): it fits 5 CTAs
-// of 4 warps per SM, the grouped one 2 of 8.
+// Tiles in flight per CTA of the grouped backward kernel (k_edge_bwd_grp).
 constexpr int kBwdGroups = 2;
 
 // The radial-function count compiled into the kernels of each width (the
@@ -1304,21 +1385,23 @@ constexpr int kSpecK = F == 64 ? 16 : 8;
 template <int F, int KC>
 void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     launch_persistent(k_edge_fwd_bf16<F, KC>, (int)sizeof(FwdSmem<F>), 2 * F, kT, 1, a, K, status, s);
-    k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
-                                                                 a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
-                                                                 nullptr, nullptr, 0);
+    if (a.fused_fixup) return;                         // the per-atom kernel sums the split rows
+    k_tile_fixup<F><<<fixup_blocks(a.e_cap), 256, 0, s>>>(a.n_atoms, a.row_ptr, a.recv, a.e_cap, a.carry,
+                                                          a.carry_w, a.msg_out, a.layer == 0 ? 1 : 0, 0, a.erep,
+                                                          nullptr, nullptr, 0, a.check);
 }
 
 template <int F, int NV, int KC>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
-    if constexpr (F == 64)
+    const int tiles = a.bwd_tiles > 0 ? a.bwd_tiles : bf16_default_bwd_tiles(F);
+    if (tiles == 2)
         launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups, KC>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
                           kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, a, K, status, s);
     else
         launch_persistent(k_edge_bwd_bf16<F, NV, KC>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, a, K, status, s);
-    k_tile_fixup<F><<<(a.n_atoms * 32 + 255) / 256, 256, 0, s>>>(a.n_atoms, a.row_ptr, a.e_cap, a.carry, a.carry_w,
-                                                                 a.layer > 0 ? a.msg_out : nullptr, NV, 1, nullptr,
-                                                                 a.force, a.vir6, a.accumulate);
+    k_tile_fixup<F><<<fixup_blocks(a.e_cap), 256, 0, s>>>(a.n_atoms, a.row_ptr, a.recv, a.e_cap, a.carry,
+                                                          a.carry_w, a.layer > 0 ? a.msg_out : nullptr, NV, 1,
+                                                          nullptr, a.force, a.vir6, a.accumulate, a.check);
 }
 
 template <int F>
@@ -1366,7 +1449,7 @@ void launch_edge_fwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
     if (a.n_atoms == 0) return;
     if (F == 64) fwd_k<64>(a, K, status, s);
     else fwd_k<32>(a, K, status, s);
-    count_launch(2);
+    count_launch(a.fused_fixup ? 1 : 2);
 }
 
 void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStream_t s) {
@@ -1381,11 +1464,22 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
     count_launch(2);
 }
 
-int bf16_max_ctas_per_sm(int F, bool bwd) {
+// The backward kernel's tiles in flight per CTA unless the tuner chooses:
+// two at F = 64 (two groups of 4 warps share one copy of the weights), one
+// at F = 32, where the one-tile kernel fits 5 CTAs of 4 warps per SM
+// against 2 of 8 (28.6 vs 31.6 us measured on 12,288-atom water).
+int bf16_default_bwd_tiles(int F) { return F == 64 ? 2 : 1; }
+
+int bf16_max_ctas_per_sm(int F, bool bwd, int tiles) {
     if (bwd) {
         constexpr int G = kBwdGroups;
-        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>>, (int)sizeof(BwdGSmem<64, G>), G * 128,
-                                           kT * G)
+        if (tiles <= 0) tiles = bf16_default_bwd_tiles(F);
+        if (tiles == 2)
+            return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>>, (int)sizeof(BwdGSmem<64, G>),
+                                               G * 128, kT * G)
+                           : ctas_per_sm_limit(k_edge_bwd_grp<32, 3, G, kSpecK<32>>, (int)sizeof(BwdGSmem<32, G>),
+                                               G * 64, kT * G);
+        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_bf16<64, 3, kSpecK<64>>, (int)sizeof(BwdSmem<64, 3>), 128, kT)
                        : ctas_per_sm_limit(k_edge_bwd_bf16<32, 3, kSpecK<32>>, (int)sizeof(BwdSmem<32, 3>), 64, kT);
     }
     return F == 64 ? ctas_per_sm_limit(k_edge_fwd_bf16<64, kSpecK<64>>, (int)sizeof(FwdSmem<64>), 128, kT)

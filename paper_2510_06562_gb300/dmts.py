@@ -17,7 +17,9 @@ import numpy as np
 from . import inputs as _inputs
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdmts.so")
+# DMTS_LIBRARY selects another build of the library (e.g. the bounds-checked
+# libdmts_check.so) for this process.
+LIB_PATH = os.environ.get("DMTS_LIBRARY") or os.path.join(_HERE, "libdmts.so")
 
 DMTS_OK = 0
 STATUS = {0: "DMTS_OK", -1: "DMTS_ERR_ARG", -2: "DMTS_ERR_OOM", -3: "DMTS_ERR_CUDA",
@@ -31,7 +33,8 @@ EXPORTED = ("dmts_create", "dmts_set_state", "dmts_get_state", "dmts_forces", "d
             "dmts_launch_count", "dmts_time_stages", "dmts_neighbors_noalloc",
             "dmts_force_matching_grad", "dmts_get_tuning", "dmts_neighbor_stats", "dmts_hmr_masses",
             "dmts_monitor", "dmts_monitor_reset", "dmts_set_tuning", "dmts_wait_selftest",
-            "dmts_philox4x32_10", "dmts_distill_grad", "dmts_adam_step", "dmts_get_params")
+            "dmts_philox4x32_10", "dmts_distill_grad", "dmts_adam_step", "dmts_get_params",
+            "dmts_get_bwd_tiles")
 
 
 class DmtsError(RuntimeError):
@@ -100,7 +103,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.dmts_monitor.restype = C.c_int
     lib.dmts_monitor_reset.argtypes = [P]
     lib.dmts_monitor_reset.restype = C.c_int
-    lib.dmts_set_tuning.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.dmts_set_tuning.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.dmts_get_bwd_tiles.argtypes = [P, C.c_int]
+    lib.dmts_get_bwd_tiles.restype = C.c_int
     lib.dmts_set_tuning.restype = C.c_int
     lib.dmts_wait_selftest.argtypes = [P, C.c_int, C.c_int]
     lib.dmts_wait_selftest.restype = C.c_int
@@ -364,11 +369,14 @@ class Context:
         code = load_library().dmts_get_tuning(self._h, which, C.byref(f), C.byref(b))
         if code < 0:
             _check(code)
-        return {"tuned": bool(code), "atoms_fwd": f.value, "atoms_bwd": b.value}
+        t = load_library().dmts_get_bwd_tiles(self._h, which)
+        if t < 0:
+            _check(t)
+        return {"tuned": bool(code), "atoms_fwd": f.value, "atoms_bwd": b.value, "bwd_tiles": t}
 
-    def set_tuning(self, which: int, fwd: int, bwd: int):
+    def set_tuning(self, which: int, fwd: int, bwd: int, bwd_tiles: int = 0):
         """Fix one model's work granularity (``dmts_set_tuning``)."""
-        _check(load_library().dmts_set_tuning(self._h, which, int(fwd), int(bwd)))
+        _check(load_library().dmts_set_tuning(self._h, which, int(fwd), int(bwd), int(bwd_tiles)))
 
     def wait_selftest(self, arrive: bool, max_polls: int = 1000) -> int:
         """Run the bounded-wait self-test (``dmts_wait_selftest``); returns its

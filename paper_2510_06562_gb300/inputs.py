@@ -257,6 +257,25 @@ def make_water(n_side: int, box: float, seed: int = 0) -> System:
                   name=f"water{3 * n_mol}", bonds=bonds)
 
 
+def replicas(systems: list) -> System:
+    """Independent systems stored back to back in one batch (periodic
+    replicas must share one box edge); atom indices of the bonds shift with
+    each system's offset."""
+    xs, sp, ms, bonds, box, off = [], [], [], [], [], [0]
+    for s in systems:
+        if s.bonds is not None and len(s.bonds):
+            bonds.append(np.asarray(s.bonds) + off[-1])
+        xs.append(s.x)
+        sp.append(s.species)
+        ms.append(s.mass)
+        box.append(s.box)
+        off.extend(int(o) + off[-1] for o in np.asarray(s.atom_offset)[1:])
+    return System(x=np.concatenate(xs), species=np.concatenate(sp).astype(np.int32), mass=np.concatenate(ms),
+                  atom_offset=np.array(off, dtype=np.int32), box=np.concatenate(box).astype(np.float64),
+                  n_species=max(s.n_species for s in systems), name=f"{len(systems)}x{systems[0].name}",
+                  bonds=np.concatenate(bonds).astype(np.int32) if bonds else None)
+
+
 def water_192(seed: int = 0) -> System:
     return make_water(4, 12.42, seed)
 

