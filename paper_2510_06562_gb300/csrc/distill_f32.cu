@@ -313,8 +313,7 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
         U1T[r * 33 + c] = u1; U2T[r * 33 + c] = u2; R1T[r * 33 + c] = r1;
     }
     __syncthreads();
-    const float c1 = P[a.off.c1[0] + lane], c2 = P[a.off.c2[0] + lane], d1 = P[a.off.d1 + lane],
-                r2 = P[a.off.R2 + lane];
+    const float c1 = P[a.off.c1[0] + lane], d1 = P[a.off.d1 + lane], r2 = P[a.off.R2 + lane];
     const float ce = c_energy ? (float)*c_energy : 0.f;        // dL/dE of this frame (energy term)
     float n_here = 0.f, n_sp_here = 0.f;                       // atoms of this warp; of species `lane`
     // per-lane gradient accumulators: column `lane` of dR1, dU2, dU1 (k = 0..31), and vectors

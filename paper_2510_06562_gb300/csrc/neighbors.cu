@@ -411,7 +411,7 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
 // atom. The last block to finish clears the chunk sums and the ticket for
 // the next build.
 __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_compact_scan(NbrArgs a) {
-    __shared__ int base_s, row_beg[kNbrWarps + 1];
+    __shared__ int row_beg[kNbrWarps + 1];
     if (a.ccap > 0)
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
             a.cell_count[k] = 0;
@@ -433,7 +433,6 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_compact_scan(NbrArgs a) 
             if (lane >= o) incl += y;
         }
         if (lane <= kNbrWarps) row_beg[lane] = (int)sum + incl - cnt;
-        if (lane == 0) base_s = (int)sum;
     }
     __syncthreads();
     const int i = b * kNbrWarps + w;

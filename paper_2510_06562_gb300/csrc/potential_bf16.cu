@@ -108,9 +108,10 @@ __device__ __forceinline__ void gather_rows(float* buf, const float* __restrict_
     }
 }
 
-// Edge indices and fixed-point positions of one tile edge, loaded one tile ahead.
+// Edge indices and fixed-point positions of one tile edge, loaded one tile
+// ahead; rp is the row of the pair before it (-1 for the first pair).
 struct EdgeIn {
-    int j, i;
+    int j, i, rp;
     uint4 qj, qi;
 };
 
@@ -118,9 +119,11 @@ __device__ __forceinline__ void load_idx(const PotArgs& a, long long e, long lon
     if (e < e_end) {
         x.j = DMTS_IDX(__ldg(a.col + e), a.n_atoms, a.check);
         x.i = DMTS_IDX(__ldg(a.recv + e), a.n_atoms, a.check);
+        x.rp = e > 0 ? __ldg(a.recv + e - 1) : -1;
     } else {
         x.j = -1;
         x.i = -1;
+        x.rp = -1;
     }
 }
 
@@ -384,8 +387,9 @@ __device__ __forceinline__ void merge_tile_scal(const ScalSlots<NV>* ss, int c, 
 // Rows without pairs: the thread of the first pair after such rows writes
 // their outputs (zeros), and the thread of the last pair writes those of the
 // rows after it, so a tiled pass writes every row that does not cross a tile
-// boundary. rp: the row of the previous pair (-1 for the first); vec: F
-// values per row (or null); zero(r) writes the row's scalar outputs.
+// boundary. rp: the row of the previous pair (-1 for the first; loaded with
+// the pair's indices); vec: F values per row (or null); zero(r) writes the
+// row's scalar outputs.
 template <int F, class Zero>
 __device__ __forceinline__ void fill_empty_rows(int rp, int row, bool last_pair, int n_atoms, float* __restrict__ vec,
                                                 Zero zero) {
@@ -400,14 +404,6 @@ __device__ __forceinline__ void fill_empty_rows(int rp, int row, bool last_pair,
     for (int r = rp + 1; r < row; ++r) fill(r);
     if (last_pair)
         for (int r = row + 1; r < n_atoms; ++r) fill(r);
-}
-
-// The row of the pair before this thread's (-1 for pair 0): from the lane
-// below, or for lane 0 from the pair list. Every lane of the warp calls it.
-__device__ __forceinline__ int prev_pair_row(const int* __restrict__ recv, long long e, int row) {
-    const int lane = threadIdx.x & 31;
-    const int up = __shfl_up_sync(0xffffffffu, row, 1);
-    return lane > 0 ? up : (e > 0 ? __ldg(recv + e - 1) : -1);
 }
 
 // Rows split across tiles, after a tiled pass: one warp per tile boundary t
@@ -544,13 +540,10 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const bool valid = ex.j >= 0;
             const int j = valid ? ex.j : 0;
             const int row = valid ? ex.i : -1;
-            {
-                const int rp = prev_pair_row(a.recv, tb + tid, row);
-                if (valid)
-                    fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, a.msg_out, [&](int r) {
-                        if (l == 0) a.erep[r] = 0.f;
-                    });
-            }
+            if (valid)
+                fill_empty_rows<F>(ex.rp, row, tb + tid == E - 1, a.n_atoms, a.msg_out, [&](int r) {
+                    if (l == 0) a.erep[r] = 0.f;
+                });
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // the message needs u_j: start copying the warp's rows into P now
             gather_rows<F>(S.P, a.u, j, tid);
@@ -773,12 +766,9 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
             const bool valid = ex.j >= 0;
             const int j = valid ? ex.j : 0;
             const int row = valid ? ex.i : -1;
-            {
-                const int rp = prev_pair_row(a.recv, tb + tid, row);
-                if (valid)
-                    fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
-                                       [&](int r) { zero_force_row<NV>(a, r); });
-            }
+            if (valid)
+                fill_empty_rows<F>(ex.rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
+                                   [&](int r) { zero_force_row<NV>(a, r); });
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // g needs u_j and mbar_j, the ubar message mbar_j: start the warp's row copies now
             gather_rows<F>(S.G, reinterpret_cast<const float*>(a.um), j, tid);
@@ -828,8 +818,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
                 float v[16], tv[16];
-                tmem_ld16(tD1 + lane_base + c, v);
-                tmem_ld16(tD4 + lane_base + c, tv);
+                tmem_ld16x2(tD1 + lane_base + c, v, tD4 + lane_base + c, tv);
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {          // two features per packed FP32 operation
                     const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
@@ -943,8 +932,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
                 float ab[16], pv[16];
-                tmem_ld16(tD3 + lane_base + c, ab);
-                tmem_ld16(tD1 + lane_base + c, pv);
+                tmem_ld16x2(tD3 + lane_base + c, ab, tD1 + lane_base + c, pv);
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::pack(pv[q], pv[q + 1]), s22);
             }
@@ -1113,12 +1101,9 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         const bool valid = ex.j >= 0;
         const int j = valid ? ex.j : 0;
         const int row = valid ? ex.i : -1;
-        {
-            const int rp = prev_pair_row(a.recv, tb + tid, row);
-            if (valid)
-                fill_empty_rows<F>(rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
-                                   [&](int r) { zero_force_row<NV>(a, r); });
-        }
+        if (valid)
+            fill_empty_rows<F>(ex.rp, row, tb + tid == E - 1, a.n_atoms, need_ubar ? a.msg_out : nullptr,
+                               [&](int r) { zero_force_row<NV>(a, r); });
         load_idx(a, (tile + step) * kT + tid, E, nx);      // this group's next tile's indices
         gather_rows<F>(T.G, reinterpret_cast<const float*>(a.um), j, tid);
         cp_async_commit();
@@ -1166,8 +1151,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
 #pragma unroll
         for (int c = 0; c < F; c += 16) {
             float v[16], tv[16];
-            tmem_ld16(tX + lane_base + c, v);
-            tmem_ld16(tY + lane_base + c, tv);
+            tmem_ld16x2(tX + lane_base + c, v, tY + lane_base + c, tv);
             uint32_t ps[8], pp[8];
 #pragma unroll
             for (int q = 0; q < 16; q += 2) {              // two features per packed FP32 operation
@@ -1267,8 +1251,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         for (int c = 0; c < F; c += 16) {
             float ab[16];
             uint32_t pw[8];
-            tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, ab);
-            tmem_ld8(tX + lane_base + c / 2, pw);
+            tmem_ld16_8((c < H ? tX : tY) + H + (c % H) + lane_base, ab, tX + lane_base + c / 2, pw);
 #pragma unroll
             for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::from_bf16x2(pw[q / 2]), s22);
         }
