@@ -302,8 +302,15 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
                                                               float* __restrict__ partial, int n_params,
                                                               const double* __restrict__ c_energy) {
     constexpr int F = 32;
-    __shared__ float U1[F * F], U2[F * F], R1[F * F];          // W[k][f], for x W
-    __shared__ float U1T[F * 33], U2T[F * 33], R1T[F * 33];    // W[k][f] padded, for x W^T
+    // U1, U2, R1 as W[k][f] (for x W), then padded copies U1T, U2T, R1T (for
+    // x W^T); at the end the same array holds the block's gradient sums
+    __shared__ float smw[3 * F * F + 3 * F * 33];
+    float* const U1 = smw;
+    float* const U2 = U1 + F * F;
+    float* const R1 = U2 + F * F;
+    float* const U1T = R1 + F * F;
+    float* const U2T = U1T + F * 33;
+    float* const R1T = U2T + F * 33;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const float* P = a.P;
     for (int t = tid; t < F * F; t += blockDim.x) {
@@ -366,22 +373,47 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
         n_here += 1.f;
         if (lane == sp) n_sp_here += 1.f;
     }
-    // write this warp's partials: partial[(blockIdx * warps + w) * n_params + param]
-    float* out = partial + ((size_t)blockIdx.x * kAtomWarps + w) * n_params;
+    // the block's partials: the warps' sums added in warp order in shared
+    // memory, then one row partial[blockIdx * n_params + param]
+    __syncthreads();                                   // the weight copies are no longer read
+    float* sacc = smw;                                 // 3 F^2 + 4 F + 16 F + 17 floats fit in smw
+    float* sR1 = sacc, *sU2 = sR1 + F * F, *sU1 = sU2 + F * F, *sv = sU1 + F * F;   // sv: R2 d1 c2 c1
+    float* sA = sv + 4 * F, *sE = sA + 16 * F;                                          // sE: d2, e0[16]
+    for (int ww = 0; ww < kAtomWarps; ++ww) {
+        if (w == ww) {
+            auto put = [&](float* dst, float v) { *dst = ww == 0 ? v : *dst + v; };
 #pragma unroll
-    for (int k = 0; k < F; ++k) {
-        out[a.off.R1 + k * F + lane] = gR1[k];
-        out[a.off.U2[0] + k * F + lane] = gU2[k];
-        out[a.off.U1[0] + k * F + lane] = gU1[k];
+            for (int k = 0; k < F; ++k) {
+                put(sR1 + k * F + lane, gR1[k]);
+                put(sU2 + k * F + lane, gU2[k]);
+                put(sU1 + k * F + lane, gU1[k]);
+            }
+            put(sv + lane, gR2);
+            put(sv + F + lane, gd1);
+            put(sv + 2 * F + lane, gc2);
+            put(sv + 3 * F + lane, gc1);
+            for (int zz = 0; zz < n_sp && zz < 16; ++zz) put(sA + zz * F + lane, gA[zz]);
+            // every atom adds d2 and e0[Z_i] to the energy once (exact counts in FP32)
+            if (lane == 0) put(sE, -ce * n_here);
+            if (lane < n_sp) put(sE + 1 + lane, -ce * n_sp_here);
+        }
+        __syncthreads();
     }
-    out[a.off.R2 + lane] = gR2;
-    out[a.off.d1 + lane] = gd1;
-    out[a.off.c2[0] + lane] = gc2;
-    out[a.off.c1[0] + lane] = gc1;
-    for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
-    // every atom adds d2 and e0[Z_i] to the energy once (exact counts in FP32)
-    if (lane == 0) out[a.off.d2] = -ce * n_here;
-    if (lane < n_sp) out[a.off.e0 + lane] = -ce * n_sp_here;
+    float* out = partial + (size_t)blockIdx.x * n_params;
+    for (int t = tid; t < F * F; t += blockDim.x) {
+        out[a.off.R1 + t] = sR1[t];
+        out[a.off.U2[0] + t] = sU2[t];
+        out[a.off.U1[0] + t] = sU1[t];
+    }
+    for (int t = tid; t < F; t += blockDim.x) {
+        out[a.off.R2 + t] = sv[t];
+        out[a.off.d1 + t] = sv[F + t];
+        out[a.off.c2[0] + t] = sv[2 * F + t];
+        out[a.off.c1[0] + t] = sv[3 * F + t];
+    }
+    for (int t = tid; t < n_sp * F; t += blockDim.x) out[a.off.A + t] = sA[t];
+    if (tid == 0) out[a.off.d2] = sE[0];
+    if (tid < n_sp) out[a.off.e0 + tid] = sE[1 + tid];
 }
 
 // ------------------------------------------------------------ filter-weight gradient edge pass
@@ -580,10 +612,22 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_input(PotArgs a, const f
         for (int zz = 0; zz < 16; ++zz)
             if (zz == sp) gA[zz] += t;
     }
-    float* out = partial + ((size_t)blockIdx.x * kAtomWarps + w) * n_params;
+    // the warps' sums added in warp order in shared memory, one row per block
+    __syncthreads();
+    float* sW = WinT;                                  // the W_in gradient: F^2 of its F * 33 floats
+    __shared__ float sA[16 * F];
+    for (int ww = 0; ww < kAtomWarps; ++ww) {
+        if (w == ww) {
 #pragma unroll
-    for (int k = 0; k < F; ++k) out[a.off.W_in[0] + k * F + lane] = gW[k];
-    for (int zz = 0; zz < n_sp && zz < 16; ++zz) out[a.off.A + zz * F + lane] = gA[zz];
+            for (int k = 0; k < F; ++k) sW[k * F + lane] = ww == 0 ? gW[k] : sW[k * F + lane] + gW[k];
+            for (int zz = 0; zz < n_sp && zz < 16; ++zz)
+                sA[zz * F + lane] = ww == 0 ? gA[zz] : sA[zz * F + lane] + gA[zz];
+        }
+        __syncthreads();
+    }
+    float* out = partial + (size_t)blockIdx.x * n_params;
+    for (int t = tid; t < F * F; t += blockDim.x) out[a.off.W_in[0] + t] = sW[t];
+    for (int t = tid; t < n_sp * F; t += blockDim.x) out[a.off.A + t] = sA[t];
 }
 
 // Energy term of one frame: E = sum over the systems of the model's energies,
@@ -599,14 +643,42 @@ __global__ void k_fm_energy_term(int n_sys, const double* __restrict__ E, const 
     *c_energy = 2.0 * lambda * r * inv_frames / (double)n_atoms;
 }
 
-// grad[p] (+)= -sum_c partial[c][p] for p in the listed range (fixed order).
-__global__ void k_fm_reduce(const float* __restrict__ partial, int n_rows, int n_params, int p0, int p1,
-                            double* __restrict__ grad) {
-    int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= p1) return;
-    double s = 0.0;
-    for (int c = 0; c < n_rows; ++c) s += (double)partial[(size_t)c * n_params + p];
-    grad[p] -= s;
+// grad[p] -= sum_c partial[c][p] for p in [p0, p1): 32 parameters per block,
+// each summed by kRedG threads; thread g keeps four FP64 sums over rows
+// c = g + kRedG (4k + u), u = 0..3 (four loads in flight), adds them in u
+// order, and the kRedG thread sums are added in g order: one order for any
+// grid.
+constexpr int kRedP = 32, kRedG = 16;
+__global__ void __launch_bounds__(kRedP * kRedG) k_fm_reduce(const float* __restrict__ partial, int n_rows,
+                                                               int n_params, int p0, int p1,
+                                                               double* __restrict__ grad) {
+    __shared__ double part[kRedG][kRedP];
+    const int lp = threadIdx.x % kRedP, g = threadIdx.x / kRedP;
+    const int p = p0 + blockIdx.x * kRedP + lp;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (p < p1) {
+        const float* col = partial + p;
+        int c = g;
+        for (; c + 3 * kRedG < n_rows; c += 4 * kRedG) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += (double)col[(size_t)(c + u * kRedG) * n_params];
+        }
+        for (int u = 0; c < n_rows; c += kRedG, ++u) acc[u] += (double)col[(size_t)c * n_params];
+    }
+    part[g][lp] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    __syncthreads();
+    if (g == 0 && p < p1) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kRedG; ++k) t += part[k][lp];
+        grad[p] -= t;
+    }
+}
+
+// The reduction of the partial rows over the parameter range [p0, p1).
+void fm_reduce(const float* partial, int n_rows, int n_params, int p0, int p1, double* grad, cudaStream_t s) {
+    if (p1 <= p0) return;
+    k_fm_reduce<<<(p1 - p0 + kRedP - 1) / kRedP, kRedP * kRedG, 0, s>>>(partial, n_rows, n_params, p0, p1, grad);
 }
 
 __global__ void k_sum_all(int n, const double* __restrict__ v, double scale, double* __restrict__ out) {
@@ -670,20 +742,24 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     a.atoms_per_cta = fm_atoms_per_cta();
     if (K == 8) tangent_go<32, 8>(a, g, mdot, s);
     else tangent_go<32, 16>(a, g, mdot, s);
-    const int ga = fm_atom_ctas(n);
-    cudaMemsetAsync(partial_a, 0, sizeof(float) * (size_t)ga * kAtomWarps * n_params, s);
+    // every row of a pass's partials holds every entry of the parameter
+    // blocks that pass writes; only those blocks are reduced
+    const ModelOffsets& o = a.off;
+    const int F = 32, S = (o.W_in[0] - o.A) / F;
+    const int ga = fm_atom_ctas(n), ra = ga;             // one partial row per per-atom block
     k_fm_atom<<<ga, kAtomWarps * 32, 0, s>>>(a, m, mdot, mbar_psi, mdotbar_psi, partial_a, n_params,
                                              en.e_ref ? en.c_energy : nullptr);
-    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_a, ga * kAtomWarps, n_params, 0, n_params, grad);
+    fm_reduce(partial_a, ra, n_params, o.A, o.A + S * F, grad, s);               // A
+    fm_reduce(partial_a, ra, n_params, o.U1[0], o.c2[0] + F, grad, s);          // U1, c1, U2, c2
+    fm_reduce(partial_a, ra, n_params, o.R1, o.e0 + S, grad, s);                // R1, d1, R2, d2, e0
     const int ge = fm_edge_ctas(n);
-    cudaMemsetAsync(partial_e, 0, sizeof(float) * (size_t)ge * n_params, s);
     if (K == 8) grad_edge_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
     else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
-    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_e, ge, n_params, 0, n_params, grad);
-    cudaMemsetAsync(partial_a, 0, sizeof(float) * (size_t)ga * kAtomWarps * n_params, s);
+    fm_reduce(partial_e, ge, n_params, o.W1[0], o.b2[0] + F, grad, s);          // W1, b1, W2, b2
     k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
-    k_fm_reduce<<<(n_params + 255) / 256, 256, 0, s>>>(partial_a, ga * kAtomWarps, n_params, 0, n_params, grad);
-    count_launch(11);
+    fm_reduce(partial_a, ra, n_params, o.A, o.A + S * F, grad, s);               // A
+    fm_reduce(partial_a, ra, n_params, o.W_in[0], o.W_in[0] + F * F, grad, s);  // W_in
+    count_launch(12);
 }
 
 }  // namespace dmts
