@@ -482,7 +482,7 @@ def distill_rate(D, I, torch, s, mdl, prec, n_frames=64, n_traj=8):
     t0 = time.perf_counter()
     frames, f_ref, e_ref = DS.sample_frames(s, ba, bp, n_frames, n_traj, 10.0, precision=prec)
     t_sample = time.perf_counter() - t0
-    ctx = D.Context(s, ba, bp, sa, sp)
+    ctx = D.Context(s, ba, bp, sa, sp, precision=prec)
     ctx.set_state(s.x)
     fd = torch.tensor(frames, device="cuda")
     rd = torch.tensor(f_ref, device="cuda")
@@ -500,6 +500,9 @@ def distill_rate(D, I, torch, s, mdl, prec, n_frames=64, n_traj=8):
     ctx.close()
     return {"workload": f"{n_frames} frames of the {s.n_atoms}-atom box from big-model MD ({n_traj} trajectories, "
                         f"10 fs apart), energy + force loss (lambda_e = 1)",
+            "precision": ("frame forces and energies " + ("BF16 MLP operands on tcgen05, FP32 accumulation"
+                                                           if prec == D.BF16_MLP else "FP32")
+                          + "; second-order adjoint passes FP32"),
             "frames_per_s": n_frames / t_grad, "ms_per_frame": t_grad * 1e3 / n_frames,
             "ms_per_training_step": (t_grad + t_adam) * 1e3, "frame_sampling_s": t_sample,
             "loss": loss, "loss_after_one_step": loss1}

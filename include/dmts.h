@@ -314,8 +314,10 @@ DMTS_API int dmts_time_stages(dmts_ctx* ctx, int which, int reps, double* ms_out
  * data labelled by the reference model):
  *   L(theta) = 1/(3 N M) sum_{m<M} sum_i |F_i(theta; x_m) - F_ref,m,i|^2,
  * with F = -dE/dx, so dL/dtheta involves second derivatives of the energy;
- * it is computed by hand-written adjoint kernels (FP32, whatever the model's
- * precision setting). frames: [M][N*3] positions, f_ref: [M][N*3] reference
+ * it is computed by hand-written adjoint kernels. Each frame's force and
+ * energy come from the model in its precision setting (BF16 tensor-core
+ * MLPs in DMTS_BF16_MLP mode: the gradient then carries that rounding); the
+ * second-order adjoint passes are FP32. frames: [M][N*3] positions, f_ref: [M][N*3] reference
  * forces (host or device). loss_out: scalar; grad_out: n_params doubles in
  * the flat parameter order (gradients of d2 and e0 are exactly 0). Supported
  * for a single-layer small model with n_feat 32 and n_radial 8 or 16. The

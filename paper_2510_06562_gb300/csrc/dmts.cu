@@ -241,6 +241,7 @@ struct dmts_ctx {
     bool concurrent = true;
     SumScratch kesum{};                    // scratch of the per-system kinetic-energy sum
     bool atom_tc = true;                   // BF16 mode: per-atom MLPs on the tensor cores
+    bool keep_msg = false;                 // every message row stays in memory (the distillation reads them)
     long long body_launches = 0, fallback_seen = 0;
     double cap_factor = 1.5;
     bool state_set = false, forces_valid = false;
@@ -796,7 +797,7 @@ PotArgs fwd_args(dmts_ctx* c, const PotArgs& a, Model& m, int l) {
     f.mbar_out = m.mbar[(m.L - 1) & 1];
     // the SIMT per-atom kernel after a tensor-core forward pass sums the split
     // rows itself (one launch fewer); the tensor-core one reads finished rows
-    f.fused_fixup = (m.precision == DMTS_BF16_MLP && !atom_on_tc(c, m)) ? 1 : 0;
+    f.fused_fixup = (m.precision == DMTS_BF16_MLP && !atom_on_tc(c, m) && !c->keep_msg) ? 1 : 0;
     if (m.precision == DMTS_BF16_MLP) {
         f.um_u_out = (l + 1 < m.L) ? m.um[l + 1] : nullptr;
         f.um_mbar_out = m.um[m.L - 1];
@@ -1652,13 +1653,15 @@ int distill_impl(dmts_ctx* c, int n_frames, const double* frames, const double* 
     // keep the dynamical state
     CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    const int prec = m.precision;
-    struct PrecisionRestore {                  // the adjoint passes are FP32; so is the force they differentiate
-        Model& m;
-        int p;
-        ~PrecisionRestore() { m.precision = p; }
-    } restore_prec{m, prec};
-    m.precision = DMTS_FP32;
+    // each frame's force and energy come from the model in its own precision
+    // (BF16 MLP operands on the tensor cores in DMTS_BF16_MLP mode); the
+    // second-order adjoint passes around them are FP32 and read every
+    // message row, so the split rows are written back (no fused fix-up)
+    struct KeepMsg {
+        dmts_ctx* c;
+        ~KeepMsg() { c->keep_msg = false; }
+    } keep_msg{c};
+    c->keep_msg = true;
     const double cl = 2.0 / (3.0 * (double)N * (double)n_frames);
     for (int attempt = 0;; ++attempt) {
         if ((rc = reset_flags(c))) return rc;

@@ -60,6 +60,34 @@ def test_distill_gradient_matches_oracle(lambda_e):
     assert np.abs(g_ref[-3:]).min() > 0                  # d2 and e0 carry the energy term
 
 
+def test_distill_gradient_bf16_mode_matches_oracle():
+    """In the BF16 mode each frame's force and energy come from the
+    tensor-core MLPs (BF16 operands, FP32 accumulation; force RMSE about
+    2e-4 eV/A against forces of RMS 1 eV/A), so the residuals, and with them
+    the gradient, carry that rounding. Residuals of RMS about 0.24 eV/A move
+    the loss by up to 2 x 2e-4 / 0.24 ~ 2e-3 relative, the energy term
+    (7e-5 eV/atom against residuals near 0.2 eV/atom) by up to 1e-3: loss
+    within 5e-3 relative (measured 8e-4), gradient within 2e-2 of its norm
+    (measured 1.2e-3) and entry by entry within 2e-2 of its largest entry,
+    all far below what a wrong term gives (order one)."""
+    s = I.water_192(0)
+    sa, sp, ba, bp = _models()
+    frames, f_ref, e_ref = _labelled_frames(s, ba, bp, 2, 9)
+    L_ref, g_ref = M.distill_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, 1.0)
+    with D.Context(s, ba, bp, sa, sp, precision=D.BF16_MLP) as ctx:
+        ctx.set_state(s.x)
+        L, g = ctx.distill_grad(frames, f_ref, e_ref, 1.0)
+        E, F = ctx.forces(D.SMALL)                      # the context still evaluates normally afterwards
+    rel = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    print(json.dumps({"bf16_loss": L, "loss_ref": L_ref, "grad_rel_l2": rel,
+                      "grad_max_abs_err": float(np.abs(g - g_ref).max()), "grad_max_abs": float(np.abs(g_ref).max())}))
+    assert abs(L - L_ref) <= 5e-3 * L_ref
+    assert rel <= 2e-2
+    assert np.abs(g - g_ref).max() <= 2e-2 * np.abs(g_ref).max()
+    Er, Fr = M.energy_forces(M.spec_of(sa), sp, s.x, s.species, s.atom_offset, s.box)
+    assert np.sqrt(np.mean((F - Fr) ** 2)) <= 5e-3
+
+
 def test_distill_without_energy_term_is_force_matching():
     s = I.water_192(0)
     sa, sp, ba, bp = _models()
