@@ -13,7 +13,8 @@
 //
 // Layer 0 reads h^0 = A[Z_i] from the per-atom copy built once per parameter
 // upload. A CTA takes A = 32 atoms; each stage is an [A x F] x [F x F]
-// product, each thread owning 4 atoms x 4 features. Inputs stay in their
+// product, each thread owning RA atoms x RF features (4 x 4 at F = 64; 2 x 2
+// at F = 32, so that the narrow model still has 8 warps per CTA). Inputs stay in their
 // natural [atom][k] layout in shared memory; the weight matrix of the next
 // stage (row-major; the transposed ones are copies prepared on the host)
 // streams in with cp.async while the current stage computes.
@@ -28,11 +29,14 @@ namespace {
 template <int F>
 struct AtomTile {
     static constexpr int A = 32;            // atoms per CTA
-    static constexpr int FG = F / 4;        // feature groups
-    static constexpr int NT = (A / 4) * FG; // threads per CTA: 128 (F = 64) or 64 (F = 32)
+    static constexpr int RA = F >= 64 ? 4 : 2;  // atoms per thread
+    static constexpr int RF = F >= 64 ? 4 : 2;  // features per thread
+    static constexpr int FG = F / RF;       // feature groups
+    static constexpr int NT = (A / RA) * FG; // threads per CTA: 128 (F = 64) or 256 (F = 32)
     static constexpr int XS = F + 4;        // row stride of per-atom rows [a][k]
     static constexpr int WS = F + 4;        // row stride of staged weights [k][f]
     static constexpr int SMEM = (2 * A * XS + 2 * F * WS) * 4;
+    static_assert(FG <= 32 && 32 % FG == 0, "an atom's feature groups are lanes of one warp");
 };
 
 __device__ __forceinline__ float sig(float x) { return 1.0f / (1.0f + __expf(-x)); }
@@ -44,6 +48,23 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// RF consecutive floats (RF = 2 or 4, aligned to RF floats) to and from registers.
+template <int RF>
+__device__ __forceinline__ void ld_vec(float (&d)[RF], const float* s) {
+    if constexpr (RF == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(s);
+        d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+    } else {
+        const float2 x = *reinterpret_cast<const float2*>(s);
+        d[0] = x.x; d[1] = x.y;
+    }
+}
+template <int RF>
+__device__ __forceinline__ void st_vec(float* d, const float (&v)[RF]) {
+    if constexpr (RF == 4) *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2*>(d) = make_float2(v[0], v[1]);
+}
 
 // Start copying the row-major F x F matrix W into Ws [F][WS] (closes a commit group).
 template <int F>
@@ -70,82 +91,87 @@ __device__ __forceinline__ void stage_rows(float* X, const float* __restrict__ s
 
 // acc[a][f] = sum_k X[a0 + a][k] * Ws[k][f0 + f], k ascending.
 template <int F>
-__device__ __forceinline__ void gemm4x4(const float* X, const float* Ws, int a0, int f0, float acc[4][4]) {
+__device__ __forceinline__ void gemm_blk(const float* X, const float* Ws, int a0, int f0,
+                                         float (&acc)[AtomTile<F>::RA][AtomTile<F>::RF]) {
     using T = AtomTile<F>;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < T::RA; ++a)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) acc[a][f] = 0.f;
+        for (int f = 0; f < T::RF; ++f) acc[a][f] = 0.f;
 #pragma unroll 4
     for (int k = 0; k < F; k += 4) {
-        float xv[4][4];
+        float xv[T::RA][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const float4 x = *reinterpret_cast<const float4*>(X + (a0 + a) * T::XS + k);
-            xv[a][0] = x.x; xv[a][1] = x.y; xv[a][2] = x.z; xv[a][3] = x.w;
-        }
+        for (int a = 0; a < T::RA; ++a) ld_vec<4>(xv[a], X + (a0 + a) * T::XS + k);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-            const float4 w = *reinterpret_cast<const float4*>(Ws + (k + kk) * T::WS + f0);
+            float w[T::RF];
+            ld_vec<T::RF>(w, Ws + (k + kk) * T::WS + f0);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                acc[a][0] += xv[a][kk] * w.x;
-                acc[a][1] += xv[a][kk] * w.y;
-                acc[a][2] += xv[a][kk] * w.z;
-                acc[a][3] += xv[a][kk] * w.w;
-            }
+            for (int a = 0; a < T::RA; ++a)
+#pragma unroll
+                for (int f = 0; f < T::RF; ++f) acc[a][f] += xv[a][kk] * w[f];
         }
     }
 }
 
 template <int F>
-__device__ __forceinline__ void put_rows(float* X, int a0, int f0, const float v[4][4]) {
+__device__ __forceinline__ void put_rows(float* X, int a0, int f0,
+                                         const float (&v)[AtomTile<F>::RA][AtomTile<F>::RF]) {
     using T = AtomTile<F>;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-        *reinterpret_cast<float4*>(X + (a0 + a) * T::XS + f0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+    for (int a = 0; a < T::RA; ++a) st_vec<T::RF>(X + (a0 + a) * T::XS + f0, v[a]);
 }
 
 template <int F>
 __device__ __forceinline__ void store_rows(float* __restrict__ dst, int base, int n_atoms, int a0, int f0,
-                                           const float v[4][4]) {
+                                           const float (&v)[AtomTile<F>::RA][AtomTile<F>::RF]) {
+    using T = AtomTile<F>;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < T::RA; ++a) {
         const int i = base + a0 + a;
-        if (i < n_atoms)
-            *reinterpret_cast<float4*>(dst + (size_t)i * F + f0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+        if (i < n_atoms) st_vec<T::RF>(dst + (size_t)i * F + f0, v[a]);
     }
 }
 
-// BF16 copy of the same 4 x 4 block into interleaved rows (F * 4 bytes per
-// atom; per 16 features 16 u values then 16 mbar values, half 0 or 1).
+// BF16 copy of the same block into interleaved rows (F * 4 bytes per atom;
+// per 16 features 16 u values then 16 mbar values, half 0 or 1).
 template <int F>
 __device__ __forceinline__ void store_rows_bf16(unsigned char* __restrict__ dst, int half, int base, int n_atoms,
-                                                int a0, int f0, const float v[4][4]) {
+                                                int a0, int f0, const float (&v)[AtomTile<F>::RA][AtomTile<F>::RF]) {
+    using T = AtomTile<F>;
     if (!dst) return;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < T::RA; ++a) {
         const int i = base + a0 + a;
-        if (i < n_atoms) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v[a][0], v[a][1]);
+        if (i >= n_atoms) continue;
+        unsigned char* row = dst + (size_t)i * F * 4 + (f0 >> 4) * 64 + half * 32 + (f0 & 15) * 2;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[a][0], v[a][1]);
+        if constexpr (T::RF == 4) {
             __nv_bfloat162 hi = __floats2bfloat162_rn(v[a][2], v[a][3]);
             uint2 w;
             w.x = *reinterpret_cast<uint32_t*>(&lo);
             w.y = *reinterpret_cast<uint32_t*>(&hi);
-            *reinterpret_cast<uint2*>(dst + (size_t)i * F * 4 + (f0 >> 4) * 64 + half * 32 + (f0 & 15) * 2) = w;
+            *reinterpret_cast<uint2*>(row) = w;
+        } else {
+            *reinterpret_cast<uint32_t*>(row) = *reinterpret_cast<uint32_t*>(&lo);
         }
     }
 }
 
 template <int F>
-__device__ __forceinline__ void load_rows4(float v[4][4], const float* __restrict__ src, int base, int n_atoms,
-                                           int a0, int f0) {
+__device__ __forceinline__ void load_rows(float (&v)[AtomTile<F>::RA][AtomTile<F>::RF], const float* __restrict__ src,
+                                          int base, int n_atoms, int a0, int f0) {
+    using T = AtomTile<F>;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < T::RA; ++a) {
         const int i = base + a0 + a;
-        const float4 x = i < n_atoms ? *reinterpret_cast<const float4*>(src + (size_t)i * F + f0)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[a][0] = x.x; v[a][1] = x.y; v[a][2] = x.z; v[a][3] = x.w;
+        if (i < n_atoms) {
+            ld_vec<T::RF>(v[a], src + (size_t)i * F + f0);
+        } else {
+#pragma unroll
+            for (int f = 0; f < T::RF; ++f) v[a][f] = 0.f;
+        }
     }
 }
 
@@ -170,15 +196,15 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     const int l = p.layer;
     const int base = blockIdx.x * T::A;
     const int tid = threadIdx.x, fg = tid % T::FG, ag = tid / T::FG;
-    const int f0 = 4 * fg, a0 = 4 * ag;
+    const int f0 = T::RF * fg, a0 = T::RA * ag;
     const float* P = p.P;
     const bool last = (l == p.n_layers - 1);
-    float z[4][4], v[4][4], h[4][4];
+    float z[T::RA][T::RF], v[T::RA][T::RF], h[T::RA][T::RF];
 
     stage_rows<F>(X, msg, base, p.n_atoms);
     stage_w<F>(W0, P + p.off.U1[l]);                                     // group: message rows + U1
     stage_w<F>(W1, P + p.off.U2[l]);                                     // group: U2
-    load_rows4<F>(h, p.h_in, base, p.n_atoms, a0, f0);
+    load_rows<F>(h, p.h_in, base, p.n_atoms, a0, f0);
     // the small per-layer vectors and the per-atom energy constants, loaded while the copies run
     for (int t = tid; t < F; t += T::NT) {
         sBias[0][t] = __ldg(P + p.off.c1[l] + t);
@@ -222,30 +248,34 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     __syncthreads();
     if (p.fused_fixup) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < T::RA; ++a) {
             const int i = base + a0 + a;
             if (i >= p.n_atoms) continue;
             long long t0 = 0, t1 = 0;
             const int k = split_row(i, t0, t1);
             if (k == 0) continue;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float v[T::RF];
+#pragma unroll
+            for (int f = 0; f < T::RF; ++f) v[f] = 0.f;
             if (k == 1) {
-                v = *reinterpret_cast<const float4*>(p.carry + (2 * t0 + 1) * (long long)p.carry_w + f0);
+                ld_vec<T::RF>(v, p.carry + (2 * t0 + 1) * (long long)p.carry_w + f0);
                 for (long long u = t0 + 1; u <= t1; ++u) {
-                    const float4 w = *reinterpret_cast<const float4*>(p.carry + 2 * u * (long long)p.carry_w + f0);
-                    v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+                    float w[T::RF];
+                    ld_vec<T::RF>(w, p.carry + 2 * u * (long long)p.carry_w + f0);
+#pragma unroll
+                    for (int f = 0; f < T::RF; ++f) v[f] += w[f];
                 }
             }
-            *reinterpret_cast<float4*>(X + (a0 + a) * T::XS + f0) = v;
+            st_vec<T::RF>(X + (a0 + a) * T::XS + f0, v);
         }
         __syncthreads();
     }
-    gemm4x4<F>(X, W0, a0, f0, z);                                        // z = m U1 + c1
+    gemm_blk<F>(X, W0, a0, f0, z);                                       // z = m U1 + c1
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < T::RF; ++f) {
         const float c1 = sBias[0][f0 + f];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < T::RA; ++a) {
             z[a][f] += c1;
             v[a][f] = z[a][f] * sig(z[a][f]);
         }
@@ -256,12 +286,12 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     stage_w<F>(W0, last ? P + p.off.R1 : P + p.off.W_in[l + 1]);
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(Y, W1, a0, f0, v);                                        // h += SiLU(z) U2 + c2
+    gemm_blk<F>(Y, W1, a0, f0, v);                                       // h += SiLU(z) U2 + c2
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < T::RF; ++f) {
         const float c2 = sBias[1][f0 + f];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) h[a][f] += v[a][f] + c2;
+        for (int a = 0; a < T::RA; ++a) h[a][f] += v[a][f] + c2;
     }
     store_rows<F>(p.h, base, p.n_atoms, a0, f0, h);
     put_rows<F>(X, a0, f0, h);
@@ -269,7 +299,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     if (!last) {
         cp_wait<0>();
         __syncthreads();
-        gemm4x4<F>(X, W0, a0, f0, v);                                    // u^{l+1} = h W_in^{l+1}
+        gemm_blk<F>(X, W0, a0, f0, v);                                   // u^{l+1} = h W_in^{l+1}
         store_rows<F>(p.u_next, base, p.n_atoms, a0, f0, v);
         store_rows_bf16<F>(p.um_u_out, 0, base, p.n_atoms, a0, f0, v);
         return;
@@ -277,13 +307,15 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     stage_w<F>(W1, r1t_of(p, F));
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(X, W0, a0, f0, v);                                        // q = h R1 + d1
-    float e_part[4] = {0.f, 0.f, 0.f, 0.f};
+    gemm_blk<F>(X, W0, a0, f0, v);                                       // q = h R1 + d1
+    float e_part[T::RA];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
+    for (int a = 0; a < T::RA; ++a) e_part[a] = 0.f;
+#pragma unroll
+    for (int f = 0; f < T::RF; ++f) {
         const float d1 = sBias[2][f0 + f], r2 = sBias[3][f0 + f];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < T::RA; ++a) {
             const float q = v[a][f] + d1;
             const float s = sig(q);
             e_part[a] += q * s * r2;
@@ -292,12 +324,12 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     }
     // sum the energy terms over the FG threads of this atom group (consecutive lanes)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < T::RA; ++a)
 #pragma unroll
         for (int o = T::FG / 2; o > 0; o >>= 1) e_part[a] += __shfl_xor_sync(0xffffffffu, e_part[a], o);
     if (fg == 0)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) sE[a0 + a] = e_part[a];
+        for (int a = 0; a < T::RA; ++a) sE[a0 + a] = e_part[a];
     put_rows<F>(Y, a0, f0, v);
     __syncthreads();                                                     // W0 read, Y and sE complete
     stage_w<F>(W0, wt_of(p, F, l, 2));                                   // U2^T
@@ -305,25 +337,25 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     if (tid < T::A && base + tid < p.n_atoms) p.Ei[base + tid] = (double)sE[tid] + e_const;
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(Y, W1, a0, f0, v);                                        // gh = gq R1^T
+    gemm_blk<F>(Y, W1, a0, f0, v);                                       // gh = gq R1^T
     store_rows<F>(p.gh, base, p.n_atoms, a0, f0, v);
     put_rows<F>(X, a0, f0, v);
     __syncthreads();                                                     // W1 read, X complete
     stage_w<F>(W1, wt_of(p, F, l, 1));                                   // U1^T
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(X, W0, a0, f0, v);                                        // gy = gh U2^T
+    gemm_blk<F>(X, W0, a0, f0, v);                                       // gy = gh U2^T
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < T::RA; ++a)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < T::RF; ++f) {
             const float s = sig(z[a][f]);
             v[a][f] *= s * (1.f + z[a][f] * (1.f - s));
         }
     put_rows<F>(Y, a0, f0, v);
     cp_wait<0>();
     __syncthreads();
-    gemm4x4<F>(Y, W1, a0, f0, v);                                        // mbar = gz U1^T
+    gemm_blk<F>(Y, W1, a0, f0, v);                                       // mbar = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
     store_rows_bf16<F>(p.um_mbar_out, 1, base, p.n_atoms, a0, f0, v);
 }
@@ -339,38 +371,38 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_bwd(PotArgs p, const f
     const int l = p.layer;   // >= 1
     const int base = blockIdx.x * T::A;
     const int tid = threadIdx.x, fg = tid % T::FG, ag = tid / T::FG;
-    const int f0 = 4 * fg, a0 = 4 * ag;
-    float v[4][4], g[4][4], z[4][4];
+    const int f0 = T::RF * fg, a0 = T::RA * ag;
+    float v[T::RA][T::RF], g[T::RA][T::RF], z[T::RA][T::RF];
     stage_rows<F>(X, ubar, base, p.n_atoms);
     stage_w<F>(W0, wt_of(p, F, l, 0));                                   // group: ubar rows + W_in^{l T}
     stage_w<F>(W1, wt_of(p, F, l - 1, 2));                               // group: U2^{l-1 T}
-    load_rows4<F>(g, p.gh, base, p.n_atoms, a0, f0);
-    load_rows4<F>(z, p.z_prev, base, p.n_atoms, a0, f0);
+    load_rows<F>(g, p.gh, base, p.n_atoms, a0, f0);
+    load_rows<F>(z, p.z_prev, base, p.n_atoms, a0, f0);
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(X, W0, a0, f0, v);                                        // ubar W_in^T
+    gemm_blk<F>(X, W0, a0, f0, v);                                       // ubar W_in^T
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < T::RA; ++a)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) g[a][f] += v[a][f];
+        for (int f = 0; f < T::RF; ++f) g[a][f] += v[a][f];
     store_rows<F>(p.gh, base, p.n_atoms, a0, f0, g);
     put_rows<F>(Y, a0, f0, g);
     __syncthreads();                                                     // W0 read, Y complete
     stage_w<F>(W0, wt_of(p, F, l - 1, 1));                               // U1^{l-1 T}
     cp_wait<1>();
     __syncthreads();
-    gemm4x4<F>(Y, W1, a0, f0, v);                                        // gy = gh U2^T
+    gemm_blk<F>(Y, W1, a0, f0, v);                                       // gy = gh U2^T
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < T::RA; ++a)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < T::RF; ++f) {
             const float s = sig(z[a][f]);
             v[a][f] *= s * (1.f + z[a][f] * (1.f - s));
         }
     put_rows<F>(X, a0, f0, v);
     cp_wait<0>();
     __syncthreads();
-    gemm4x4<F>(X, W0, a0, f0, v);                                        // mbar^{l-1} = gz U1^T
+    gemm_blk<F>(X, W0, a0, f0, v);                                       // mbar^{l-1} = gz U1^T
     store_rows<F>(p.mbar_out, base, p.n_atoms, a0, f0, v);
     store_rows_bf16<F>(p.um_mbar_out, 1, base, p.n_atoms, a0, f0, v);
 }

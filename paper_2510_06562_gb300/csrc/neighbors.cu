@@ -11,9 +11,10 @@
 // Fresh lists (skin 0) use cells of fixed capacity: one kernel puts every
 // atom into the next free slot of its cell (an atomic counter per cell), the
 // row build reads the 27 cells around each atom at fixed strides and sorts
-// each row by j (so the list does not depend on the slot order), a one-CTA
-// scan gives the row offsets, and the compaction writes the CSR arrays and
-// clears the cell counters for the next build.
+// each row by j (so the list does not depend on the slot order) and adds
+// its pair count to per-block and per-chunk sums, and the compaction finds
+// each row's offset from those sums, writes the CSR arrays and clears the
+// cell counters for the next build.
 //
 // Verlet-skin mode keeps, per model, candidate rows of every j within
 // rc + skin at the positions x_ref of the last rebuild. While no atom has
@@ -404,52 +405,64 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
 }
 
 // Compaction with the row scan folded in (fresh lists, block_sum set): block
-// b holds atoms kNbrWarps b .. + kNbrWarps - 1, the build's block b. Warp 0
-// adds the pair counts of every earlier chunk of kChunkBlocks build blocks
-// and of the earlier blocks of this chunk; the block's rows follow in atom
-// order. row_ptr[n] and the capacity checks come from the block of the last
-// atom. The last block to finish clears the chunk sums and the ticket for
-// the next build.
+// b holds the kCompactAtoms atoms of build blocks kCompactBlocks b ..
+// + kCompactBlocks - 1 (one chunk of the scan holds whole compaction
+// blocks). Warp 0 adds the pair counts of every earlier chunk of
+// kChunkBlocks build blocks and of the earlier build blocks of this chunk,
+// then scans the block's own rows; each warp copies four consecutive rows
+// as one range of pairs (the rows follow each other in the pair list).
+// row_ptr[n] and the capacity checks come from the warp of the last atom.
+// The last block to finish clears the chunk sums and the ticket for the
+// next build.
+constexpr int kCompactAtoms = 32;
+constexpr int kCompactBlocks = kCompactAtoms / kNbrWarps;
+constexpr int kCompactRows = kCompactAtoms / kNbrWarps;   // rows per warp
+static_assert(kCompactAtoms == 32, "warp 0 scans one row per lane");
+static_assert(kChunkBlocks % kCompactBlocks == 0, "a compaction block lies in one chunk");
+
 __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_compact_scan(NbrArgs a) {
-    __shared__ int row_beg[kNbrWarps + 1];
+    __shared__ int row_beg[kCompactAtoms + 1];
     if (a.ccap > 0)
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
             a.cell_count[k] = 0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x, chunk = b / kChunkBlocks;
+    const int b0 = blockIdx.x * kCompactBlocks, chunk = b0 / kChunkBlocks;
+    const int atom0 = blockIdx.x * kCompactAtoms;
     if (w == 0) {
         long long sum = 0;
         for (int c = lane; c < chunk; c += 32) sum += a.chunk_sum[c];
-        for (int c = chunk * kChunkBlocks + lane; c < b; c += 32) sum += a.block_sum[c];
+        for (int c = chunk * kChunkBlocks + lane; c < b0; c += 32) sum += a.block_sum[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        int cnt = 0;
-        const int i = b * kNbrWarps + lane;
-        if (lane < kNbrWarps && i < a.n_atoms) cnt = a.nbr_cnt[i];
+        const int cnt = atom0 + lane < a.n_atoms ? a.nbr_cnt[atom0 + lane] : 0;
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        if (lane <= kNbrWarps) row_beg[lane] = (int)sum + incl - cnt;
+        row_beg[lane] = (int)sum + incl - cnt;
+        if (lane == 31) row_beg[32] = (int)sum + incl;
     }
     __syncthreads();
-    const int i = b * kNbrWarps + w;
-    if (i < a.n_atoms) {
-        const int beg = row_beg[w], cnt = row_beg[w + 1] - beg;
-        if (lane == 0) a.row_ptr[i] = beg;
-        if (i == a.n_atoms - 1 && lane == 0) {
-            const int total = beg + cnt;
-            a.row_ptr[a.n_atoms] = total;
-            if ((long long)total > a.e_cap) atomicOr(&a.flags[kFlagOverflow], 1);
-            atomicMax(&a.flags[kFlagMaxE0 + a.which], total);
+    const int r0 = kCompactRows * w, i0 = atom0 + r0;
+    if (i0 < a.n_atoms) {
+        const int nr = min(kCompactRows, a.n_atoms - i0);
+        const int beg = row_beg[r0], end = row_beg[r0 + nr];
+        if (lane < nr) a.row_ptr[i0 + lane] = row_beg[r0 + lane];
+        if (i0 + nr == a.n_atoms && lane == 0) {
+            a.row_ptr[a.n_atoms] = end;
+            if ((long long)end > a.e_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+            atomicMax(&a.flags[kFlagMaxE0 + a.which], end);
         }
-        const int* src = a.nbr_tmp + (size_t)i * a.row_cap;
-        for (int k = lane; k < cnt; k += 32) {
-            const long long e = (long long)beg + k;
-            if (e < a.e_cap) {
-                a.col[e] = src[k];
+        for (int e = beg + lane; e < end; e += 32) {
+            int r = 0;                                   // the last of the warp's rows starting at or before e
+#pragma unroll
+            for (int q = 1; q < kCompactRows; ++q)
+                if (q < nr && row_beg[r0 + q] <= e) r = q;
+            if ((long long)e < a.e_cap) {
+                const int i = i0 + r;
+                a.col[e] = a.nbr_tmp[(size_t)i * a.row_cap + (e - row_beg[r0 + r])];
                 a.recv[e] = i;
             }
         }
@@ -459,7 +472,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr_compact_scan(NbrArgs a) 
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
-            const int n_chunks = (gridDim.x + kChunkBlocks - 1) / kChunkBlocks;
+            const int n_build = (a.n_atoms + kNbrWarps - 1) / kNbrWarps;
+            const int n_chunks = (n_build + kChunkBlocks - 1) / kChunkBlocks;
             for (int c = 0; c < n_chunks; ++c) a.chunk_sum[c] = 0;
             *a.ticket = 0u;
         }
@@ -588,7 +602,7 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t s) {
     size_t smem = sizeof(int) * (size_t)kNbrWarps * (a.row_cap + 64);
     k_nbr_build<<<blocks, kNbrWarps * 32, smem, s>>>(a);
     if (a.block_sum) {                     // row scan folded into the compaction
-        k_nbr_compact_scan<<<blocks, kNbrWarps * 32, 0, s>>>(a);
+        k_nbr_compact_scan<<<(a.n_atoms + kCompactAtoms - 1) / kCompactAtoms, kNbrWarps * 32, 0, s>>>(a);
         count_launch(2);
         return;
     }

@@ -700,7 +700,8 @@ __device__ __forceinline__ void unpack_bf16x8(uint4 w, float* v) {
 }
 
 // NV = 9: forces and the per-atom virial; NV = 3: forces only.
-template <int F, int NV, int KC>
+// L0: the layer-0 pass (a.layer == 0), whose u does not depend on the positions.
+template <int F, int NV, int KC, bool L0>
 __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdSmem<F, NV>& S = *reinterpret_cast<BwdSmem<F, NV>*>(smraw);
@@ -717,7 +718,7 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
     const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
     const long long n_tiles = (E + kT - 1) / kT;
     if ((long long)blockIdx.x >= n_tiles) return;
-    const bool need_ubar = (l > 0);
+    constexpr bool need_ubar = !L0;
 
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.wt + (size_t)l * a.wt_layer_bytes);
@@ -809,136 +810,241 @@ __global__ void __launch_bounds__(kT) k_edge_bwd_bf16(PotArgs a, int K, int* sta
                 pend = phase;
             }
             load_pos(a, nx);                               // next tile's positions
-            ok = mbar_wait(&S.mbar, phase, kWaitIter);
-            if (tid == 0 && ok) mma_out = false;
-            phase ^= 1;
-            fence_after_sync();
-            // SiLU(a) -> BF16 operand of the next MMA; p = SiLU'(a) (e' W1), the
-            // factor the basis-derivative term needs, replaces D1 in tensor memory
+            float se;
+            if constexpr (!need_ubar) {
+                // Layer 0: u does not depend on the positions, so the pass needs
+                // only g . dw/dd. With y = g W2^T, g . phi = SiLU(a) . y + g . b2,
+                // and dfc (g . phi) + fc (g . dphi/dd) = sum_k y_k q_k + dfc (g . b2)
+                // with q = dfc SiLU(a) + fc SiLU'(a)(e'W1): two dependent MMA
+                // groups (D1 | D4, then D3) instead of three. g goes to the MMA
+                // operand tile while the first MMAs run.
+                cp_async_wait();                           // the warp's u_j | mbar_j rows are in G
+                __syncwarp();
+                f2::f32x2 gb22 = 0ull;
+                {
+                    const int i = valid ? row : 0;
+                    const float* ui = a.u + (size_t)i * F;
+                    const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
-            for (int c = 0; c < F; c += 16) {
-                float v[16], tv[16];
-                tmem_ld16x2(tD1 + lane_base + c, v, tD4 + lane_base + c, tv);
+                    for (int c = 0; c < F; c += 16) {
+                        float4 ui16[4], mi16[4];
 #pragma unroll
-                for (int q = 0; q < 16; q += 2) {          // two features per packed FP32 operation
-                    const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
-                    const f2::f32x2 t = tanh_half(x);        // sigmoid(x) = (1 + tanh(x / 2)) / 2
-                    const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
-                    const f2::f32x2 y = f2::mul(x, sg);
-                    const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU'(x) T
-                    v[q] = f2::lo(y);
-                    v[q + 1] = f2::hi(y);
-                    // rounded to BF16 as the two-tile kernel keeps it, so the
-                    // tuner's choice between the kernels changes no result
-                    tv[q] = __bfloat162float(__float2bfloat16_rn(f2::lo(pd)));
-                    tv[q + 1] = __bfloat162float(__float2bfloat16_rn(f2::hi(pd)));
+                        for (int qq = 0; qq < 4; ++qq) {
+                            ui16[qq] = __ldg(reinterpret_cast<const float4*>(ui + c + 4 * qq));
+                            mi16[qq] = __ldg(reinterpret_cast<const float4*>(mi + c + 4 * qq));
+                        }
+                        float g[16], uj[16], mj[16];
+                        {
+                            uint4 w[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                w[k] = *reinterpret_cast<const uint4*>(S.G + prow<F>(tid, c + 4 * k));
+                            unpack_bf16x8(w[0], uj);
+                            unpack_bf16x8(w[1], uj + 8);
+                            unpack_bf16x8(w[2], mj);
+                            unpack_bf16x8(w[3], mj + 8);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4) {
+                            const float4 ui4 = ui16[q / 4];
+                            const float4 mi4 = mi16[q / 4];
+                            const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                            const f2::f32x2 mj01 = f2::pack(mj[q], mj[q + 1]), mj23 = f2::pack(mj[q + 2], mj[q + 3]);
+                            const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), f2::pack(uj[q], uj[q + 1]),
+                                                          f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                            const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), f2::pack(uj[q + 2], uj[q + 3]),
+                                                          f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                            gb22 = f2::fma(g01, b2[0], gb22);
+                            gb22 = f2::fma(g23, b2[1], gb22);
+                            g[q] = f2::lo(g01); g[q + 1] = f2::hi(g01);
+                            g[q + 2] = f2::lo(g23); g[q + 3] = f2::hi(g23);
+                        }
+                        st_row8(S.a2, tid, c, F, g);
+                        st_row8(S.a2, tid, c + 8, F, g + 8);
+                    }
                 }
-                st_row8(S.a2, tid, c, F, v);
-                st_row8(S.a2, tid, c + 8, F, v + 8);
-                tmem_st16(tD1 + lane_base + c, tv);
-            }
-            tmem_st_wait();
-            fence_proxy_async();
-            fence_before_sync();
-            ok = __syncthreads_and(ok);
-            fence_after_sync();
-            if (tid == 0 && ok) {
-#pragma unroll
-                for (int kk = 0; kk < F / 16; ++kk)
-                    mma_bf16(tD2, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
-                             idesc, kk > 0);
-                mma_commit(&S.mbar);
-                mma_out = true;
-                pend = phase;
-            }
-            ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
-            if (tid == 0 && ok) mma_out = false;
-            phase ^= 1;
-            fence_after_sync();
-            cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
-            __syncwarp();
-            f2::f32x2 gphi2 = 0ull;
-            {
-                const int i = valid ? row : 0;
-                const f2::f32x2 fc2 = f2::splat(fc);
-                const float* ui = a.u + (size_t)i * F;
-                const float* mi = a.mbar + (size_t)i * F;
+                ok = mbar_wait(&S.mbar, phase, kWaitIter);
+                if (tid == 0 && ok) mma_out = false;
+                phase ^= 1;
+                fence_after_sync();
+                const f2::f32x2 fc2 = f2::splat(fc), dfc2 = f2::splat(dfc);
 #pragma unroll
                 for (int c = 0; c < F; c += 16) {
-                    // the receiving atom's rows (shared by most of the warp) before the TMEM load
-                    float4 ui16[4], mi16[4];
+                    float v[16], tv[16];
+                    tmem_ld16x2(tD1 + lane_base + c, v, tD4 + lane_base + c, tv);
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        ui16[qq] = __ldg(reinterpret_cast<const float4*>(ui + c + 4 * qq));
-                        mi16[qq] = __ldg(reinterpret_cast<const float4*>(mi + c + 4 * qq));
+                    for (int q = 0; q < 16; q += 2) {
+                        const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                        const f2::f32x2 t = tanh_half(x);
+                        const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                        const f2::f32x2 y = f2::mul(x, sg);
+                        const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));
+                        const f2::f32x2 qv = f2::fma(dfc2, y, f2::mul(fc2, pd));
+                        // q rounded to BF16, as the two-tile kernel keeps it
+                        tv[q] = __bfloat162float(__float2bfloat16_rn(f2::lo(qv)));
+                        tv[q + 1] = __bfloat162float(__float2bfloat16_rn(f2::hi(qv)));
                     }
-                    float v[16], g[16], uj[16], mj[16];
-                    tmem_ld16(tD2 + lane_base + c, v);
-                    {
-                        // the four 16-byte chunks of these 16 features: u_j (2), mbar_j (2)
-                        uint4 w[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            w[k] = *reinterpret_cast<const uint4*>(S.G + prow<F>(tid, c + 4 * k));
-                        unpack_bf16x8(w[0], uj);
-                        unpack_bf16x8(w[1], uj + 8);
-                        unpack_bf16x8(w[2], mj);
-                        unpack_bf16x8(w[3], mj + 8);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 16; q += 4) {      // two features per packed FP32 operation
-                        const float4 ui4 = ui16[q / 4];
-                        const float4 mi4 = mi16[q / 4];
-                        const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
-                        const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
-                        const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
-                        const f2::f32x2 mj01 = f2::pack(mj[q], mj[q + 1]), mj23 = f2::pack(mj[q + 2], mj[q + 3]);
-                        // g = mbar_i u_j + mbar_j u_i
-                        const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), f2::pack(uj[q], uj[q + 1]),
-                                                      f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
-                        const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), f2::pack(uj[q + 2], uj[q + 3]),
-                                                      f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
-                        g[q] = f2::lo(g01); g[q + 1] = f2::hi(g01);
-                        g[q + 2] = f2::lo(g23); g[q + 3] = f2::hi(g23);
-                        gphi2 = f2::fma(g01, ph01, gphi2);
-                        gphi2 = f2::fma(g23, ph23, gphi2);
-                        // the message replaces the chunks just read (this thread's row only)
-                        const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
-                        *reinterpret_cast<float4*>(S.G + prow<F>(tid, c + q)) =
-                            make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
-                    }
-                    st_row8(S.a2, tid, c, F, g);
-                    st_row8(S.a2, tid, c + 8, F, g + 8);
+                    tmem_st16(tD1 + lane_base + c, tv);
                 }
-            }
-            fence_proxy_async();
-            fence_before_sync();
-            ok = __syncthreads_and(ok);
-            fence_after_sync();
-            if (tid == 0 && ok) {
+                tmem_st_wait();
+                fence_proxy_async();
+                fence_before_sync();
+                ok = __syncthreads_and(ok);
+                fence_after_sync();
+                if (tid == 0 && ok) {
 #pragma unroll
-                for (int kk = 0; kk < F / 16; ++kk)
-                    mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
-                             idesc, kk > 0);
-                mma_commit(&S.mbar);
-                mma_out = true;
-                pend = phase;
-            }
-            ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
-            if (tid == 0 && ok) mma_out = false;
-            phase ^= 1;
-            fence_after_sync();
-            f2::f32x2 s22 = 0ull;
+                    for (int kk = 0; kk < F / 16; ++kk)
+                        mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
+                                 idesc, kk > 0);
+                    mma_commit(&S.mbar);
+                    mma_out = true;
+                    pend = phase;
+                }
+                ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+                if (tid == 0 && ok) mma_out = false;
+                phase ^= 1;
+                fence_after_sync();
+                f2::f32x2 s22 = 0ull;
 #pragma unroll
-            for (int c = 0; c < F; c += 16) {
-                float ab[16], pv[16];
-                tmem_ld16x2(tD3 + lane_base + c, ab, tD1 + lane_base + c, pv);
+                for (int c = 0; c < F; c += 16) {
+                    float ab[16], pv[16];
+                    tmem_ld16x2(tD3 + lane_base + c, ab, tD1 + lane_base + c, pv);
 #pragma unroll
-                for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::pack(pv[q], pv[q + 1]), s22);
+                    for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::pack(pv[q], pv[q + 1]), s22);
+                }
+                se = __fmaf_rn(dfc, f2::lo(gb22) + f2::hi(gb22), f2::lo(s22) + f2::hi(s22));
+            } else {
+                ok = mbar_wait(&S.mbar, phase, kWaitIter);
+                if (tid == 0 && ok) mma_out = false;
+                phase ^= 1;
+                fence_after_sync();
+                // SiLU(a) -> BF16 operand of the next MMA; p = SiLU'(a) (e' W1), the
+                // factor the basis-derivative term needs, replaces D1 in tensor memory
+#pragma unroll
+                for (int c = 0; c < F; c += 16) {
+                    float v[16], tv[16];
+                    tmem_ld16x2(tD1 + lane_base + c, v, tD4 + lane_base + c, tv);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) {          // two features per packed FP32 operation
+                        const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                        const f2::f32x2 t = tanh_half(x);        // sigmoid(x) = (1 + tanh(x / 2)) / 2
+                        const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                        const f2::f32x2 y = f2::mul(x, sg);
+                        const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU'(x) T
+                        v[q] = f2::lo(y);
+                        v[q + 1] = f2::hi(y);
+                        // rounded to BF16 as the two-tile kernel keeps it, so the
+                        // tuner's choice between the kernels changes no result
+                        tv[q] = __bfloat162float(__float2bfloat16_rn(f2::lo(pd)));
+                        tv[q + 1] = __bfloat162float(__float2bfloat16_rn(f2::hi(pd)));
+                    }
+                    st_row8(S.a2, tid, c, F, v);
+                    st_row8(S.a2, tid, c + 8, F, v + 8);
+                    tmem_st16(tD1 + lane_base + c, tv);
+                }
+                tmem_st_wait();
+                fence_proxy_async();
+                fence_before_sync();
+                ok = __syncthreads_and(ok);
+                fence_after_sync();
+                if (tid == 0 && ok) {
+#pragma unroll
+                    for (int kk = 0; kk < F / 16; ++kk)
+                        mma_bf16(tD2, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
+                                 idesc, kk > 0);
+                    mma_commit(&S.mbar);
+                    mma_out = true;
+                    pend = phase;
+                }
+                ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+                if (tid == 0 && ok) mma_out = false;
+                phase ^= 1;
+                fence_after_sync();
+                cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
+                __syncwarp();
+                f2::f32x2 gphi2 = 0ull;
+                {
+                    const int i = valid ? row : 0;
+                    const f2::f32x2 fc2 = f2::splat(fc);
+                    const float* ui = a.u + (size_t)i * F;
+                    const float* mi = a.mbar + (size_t)i * F;
+#pragma unroll
+                    for (int c = 0; c < F; c += 16) {
+                        // the receiving atom's rows (shared by most of the warp) before the TMEM load
+                        float4 ui16[4], mi16[4];
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            ui16[qq] = __ldg(reinterpret_cast<const float4*>(ui + c + 4 * qq));
+                            mi16[qq] = __ldg(reinterpret_cast<const float4*>(mi + c + 4 * qq));
+                        }
+                        float v[16], g[16], uj[16], mj[16];
+                        tmem_ld16(tD2 + lane_base + c, v);
+                        {
+                            // the four 16-byte chunks of these 16 features: u_j (2), mbar_j (2)
+                            uint4 w[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                w[k] = *reinterpret_cast<const uint4*>(S.G + prow<F>(tid, c + 4 * k));
+                            unpack_bf16x8(w[0], uj);
+                            unpack_bf16x8(w[1], uj + 8);
+                            unpack_bf16x8(w[2], mj);
+                            unpack_bf16x8(w[3], mj + 8);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4) {      // two features per packed FP32 operation
+                            const float4 ui4 = ui16[q / 4];
+                            const float4 mi4 = mi16[q / 4];
+                            const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                            const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
+                            const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
+                            const f2::f32x2 mj01 = f2::pack(mj[q], mj[q + 1]), mj23 = f2::pack(mj[q + 2], mj[q + 3]);
+                            // g = mbar_i u_j + mbar_j u_i
+                            const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), f2::pack(uj[q], uj[q + 1]),
+                                                          f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                            const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), f2::pack(uj[q + 2], uj[q + 3]),
+                                                          f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                            g[q] = f2::lo(g01); g[q + 1] = f2::hi(g01);
+                            g[q + 2] = f2::lo(g23); g[q + 3] = f2::hi(g23);
+                            gphi2 = f2::fma(g01, ph01, gphi2);
+                            gphi2 = f2::fma(g23, ph23, gphi2);
+                            // the message replaces the chunks just read (this thread's row only)
+                            const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
+                            *reinterpret_cast<float4*>(S.G + prow<F>(tid, c + q)) =
+                                make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
+                        }
+                        st_row8(S.a2, tid, c, F, g);
+                        st_row8(S.a2, tid, c + 8, F, g + 8);
+                    }
+                }
+                fence_proxy_async();
+                fence_before_sync();
+                ok = __syncthreads_and(ok);
+                fence_after_sync();
+                if (tid == 0 && ok) {
+#pragma unroll
+                    for (int kk = 0; kk < F / 16; ++kk)
+                        mma_bf16(tD3, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
+                                 idesc, kk > 0);
+                    mma_commit(&S.mbar);
+                    mma_out = true;
+                    pend = phase;
+                }
+                ok = ok && mbar_wait(&S.mbar, phase, kWaitIter);
+                if (tid == 0 && ok) mma_out = false;
+                phase ^= 1;
+                fence_after_sync();
+                f2::f32x2 s22 = 0ull;
+#pragma unroll
+                for (int c = 0; c < F; c += 16) {
+                    float ab[16], pv[16];
+                    tmem_ld16x2(tD3 + lane_base + c, ab, tD1 + lane_base + c, pv);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::pack(pv[q], pv[q + 1]), s22);
+                }
+                const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
+                se = dfc * gphi + fc * s2;
             }
-            const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
-            float se = dfc * gphi + fc * s2;
-            if (l == 0 && valid) {
+            if (L0 && valid) {
                 float dphi;
                 (void)rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, &dphi);
                 se += dphi;
@@ -1035,7 +1141,7 @@ __device__ __forceinline__ void unpack_bf16x16(const uint32_t* w, float* v) {
     }
 }
 
-template <int F, int NV, int NG, int KC>
+template <int F, int NV, int NG, int KC, bool L0>
 __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     BwdGSmem<F, NG>& S = *reinterpret_cast<BwdGSmem<F, NG>*>(smraw);
@@ -1053,7 +1159,7 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
     const int l = a.layer;
     const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
     const long long n_tiles = (E + kT - 1) / kT;
-    const bool need_ubar = (l > 0);
+    constexpr bool need_ubar = !L0;
 
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.wt + (size_t)l * a.wt_layer_bytes);
@@ -1147,117 +1253,206 @@ __global__ void __launch_bounds__(kT * NG, 2) k_edge_bwd_grp(PotArgs a, int K, i
         if (tid == 0 && ok) mma_out = false;
         phase ^= 1;
         fence_after_sync();
-        // epilogue 1: p = SiLU'(a)(e'W1) -> X[0, F/2), SiLU(a) -> Y[0, F/2), both BF16
-#pragma unroll
-        for (int c = 0; c < F; c += 16) {
-            float v[16], tv[16];
-            tmem_ld16x2(tX + lane_base + c, v, tY + lane_base + c, tv);
-            uint32_t ps[8], pp[8];
-#pragma unroll
-            for (int q = 0; q < 16; q += 2) {              // two features per packed FP32 operation
-                const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
-                const f2::f32x2 t = tanh_half(x);            // sigmoid(x) = (1 + tanh(x / 2)) / 2
-                const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
-                const f2::f32x2 y = f2::mul(x, sg);          // SiLU
-                const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU' (e'W1)
-                ps[q / 2] = pack_bf16(f2::lo(y), f2::hi(y));
-                pp[q / 2] = pack_bf16(f2::lo(pd), f2::hi(pd));
-            }
-            tmem_st8(tY + lane_base + c / 2, ps);
-            tmem_st8(tX + lane_base + c / 2, pp);
-        }
-        tmem_st_wait();
-        fence_before_sync();
-        ok = group_sync_and(bar, ok);
-        fence_after_sync();
-        if (tid == 0 && ok) {
-#pragma unroll
-            for (int kk = 0; kk < F / 16; ++kk) {
-                mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2T + kk * 256, 128, F * 16), idesc_h, kk > 0);
-                mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2T + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
-            }
-            mma_commit(&T.mbar);
-            mma_out = true;
-            pend = phase;
-        }
-        ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
-        if (tid == 0 && ok) mma_out = false;
-        phase ^= 1;
-        fence_after_sync();
-        cp_async_wait();                                   // the warp's u_j | mbar_j rows are in G
-        __syncwarp();
-        f2::f32x2 gphi2 = 0ull;                            // (+0, +0)
-        {
-            const int i = valid ? row : 0;
-            const float* ui = a.u + (size_t)i * F;
-            const float* mi = a.mbar + (size_t)i * F;
+        float se;
+        if constexpr (!need_ubar) {
+            // Layer 0 (u independent of the positions), as in the one-tile kernel:
+            //   epi 1: q = dfc SiLU(a) + fc SiLU'(a)(e'W1) as BF16 -> X[0, F/2)
+            //   epi 2: g as BF16 -> Y[0, F/2)
+            //   MMA3:  D3 = g W2^T as two halves -> X[F/2, F), Y[F/2, F)
+            //   epi 3: sum_k D3_k q_k + dfc (g . b2)
+            const f2::f32x2 fc2 = f2::splat(fc), dfc2 = f2::splat(dfc);
 #pragma unroll
             for (int c = 0; c < F; c += 16) {
-                float v[16];
-                tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, v);
-                uint4 w[4];                                // BF16 u_j (w[0], w[1]) and mbar_j (w[2], w[3])
+                float v[16], tv[16];
+                tmem_ld16x2(tX + lane_base + c, v, tY + lane_base + c, tv);
+                uint32_t pq[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) w[k] = *reinterpret_cast<const uint4*>(T.G + prow<F>(tid, c + 4 * k));
-                uint32_t pg[8];
-                const f2::f32x2 fc2 = f2::splat(fc);
-#pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    const float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
-                    const float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
-                    const uint32_t u01 = q < 8 ? (q == 0 ? w[0].x : w[0].z) : (q == 8 ? w[1].x : w[1].z);
-                    const uint32_t u23 = q < 8 ? (q == 0 ? w[0].y : w[0].w) : (q == 8 ? w[1].y : w[1].w);
-                    const uint32_t m01 = q < 8 ? (q == 0 ? w[2].x : w[2].z) : (q == 8 ? w[3].x : w[3].z);
-                    const uint32_t m23 = q < 8 ? (q == 0 ? w[2].y : w[2].w) : (q == 8 ? w[3].y : w[3].w);
-                    const f2::f32x2 uj01 = f2::from_bf16x2(u01), uj23 = f2::from_bf16x2(u23);
-                    const f2::f32x2 mj01 = f2::from_bf16x2(m01), mj23 = f2::from_bf16x2(m23);
-                    const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
-                    const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
-                    const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
-                    // g = mbar_i u_j + mbar_j u_i
-                    const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), uj01, f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
-                    const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), uj23, f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
-                    gphi2 = f2::fma(g01, ph01, gphi2);
-                    gphi2 = f2::fma(g23, ph23, gphi2);
-                    pg[q / 2] = pack_bf16(f2::lo(g01), f2::hi(g01));
-                    pg[q / 2 + 1] = pack_bf16(f2::lo(g23), f2::hi(g23));
-                    // the message replaces the chunk (read above into w) of this thread's row
-                    const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
-                    *reinterpret_cast<float4*>(T.G + prow<F>(tid, c + q)) =
-                        make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
+                for (int q = 0; q < 16; q += 2) {
+                    const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                    const f2::f32x2 t = tanh_half(x);
+                    const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                    const f2::f32x2 y = f2::mul(x, sg);
+                    const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));
+                    const f2::f32x2 qv = f2::fma(dfc2, y, f2::mul(fc2, pd));
+                    pq[q / 2] = pack_bf16(f2::lo(qv), f2::hi(qv));
                 }
-                tmem_st8(tY + lane_base + c / 2, pg);     // over SiLU (read by the completed MMA2)
+                tmem_st8(tX + lane_base + c / 2, pq);
             }
-        }
-        tmem_st_wait();
-        fence_before_sync();
-        ok = group_sync_and(bar, ok);
-        fence_after_sync();
-        if (tid == 0 && ok) {
+            cp_async_wait();                               // the warp's u_j | mbar_j rows are in G
+            __syncwarp();
+            f2::f32x2 gb22 = 0ull;
+            {
+                const int i = valid ? row : 0;
+                const float* ui = a.u + (size_t)i * F;
+                const float* mi = a.mbar + (size_t)i * F;
 #pragma unroll
-            for (int kk = 0; kk < F / 16; ++kk) {
-                mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2N + kk * 256, 128, F * 16), idesc_h, kk > 0);
-                mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2N + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                for (int c = 0; c < F; c += 16) {
+                    uint4 w[4];                            // BF16 u_j (w[0], w[1]) and mbar_j (w[2], w[3])
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) w[k] = *reinterpret_cast<const uint4*>(T.G + prow<F>(tid, c + 4 * k));
+                    uint32_t pg[8];
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) {
+                        const float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
+                        const float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
+                        const uint32_t u01 = q < 8 ? (q == 0 ? w[0].x : w[0].z) : (q == 8 ? w[1].x : w[1].z);
+                        const uint32_t u23 = q < 8 ? (q == 0 ? w[0].y : w[0].w) : (q == 8 ? w[1].y : w[1].w);
+                        const uint32_t m01 = q < 8 ? (q == 0 ? w[2].x : w[2].z) : (q == 8 ? w[3].x : w[3].z);
+                        const uint32_t m23 = q < 8 ? (q == 0 ? w[2].y : w[2].w) : (q == 8 ? w[3].y : w[3].w);
+                        const f2::f32x2 uj01 = f2::from_bf16x2(u01), uj23 = f2::from_bf16x2(u23);
+                        const f2::f32x2 mj01 = f2::from_bf16x2(m01), mj23 = f2::from_bf16x2(m23);
+                        const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                        const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), uj01, f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                        const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), uj23, f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                        gb22 = f2::fma(g01, b2[0], gb22);
+                        gb22 = f2::fma(g23, b2[1], gb22);
+                        pg[q / 2] = pack_bf16(f2::lo(g01), f2::hi(g01));
+                        pg[q / 2 + 1] = pack_bf16(f2::lo(g23), f2::hi(g23));
+                    }
+                    tmem_st8(tY + lane_base + c / 2, pg);  // over e'W1 (read by epilogue 1)
+                }
             }
-            mma_commit(&T.mbar);
-            mma_out = true;
-            pend = phase;
-        }
-        ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
-        if (tid == 0 && ok) mma_out = false;
-        phase ^= 1;
-        fence_after_sync();
-        f2::f32x2 s22 = 0ull;
+            tmem_st_wait();
+            fence_before_sync();
+            ok = group_sync_and(bar, ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
 #pragma unroll
-        for (int c = 0; c < F; c += 16) {
-            float ab[16];
-            uint32_t pw[8];
-            tmem_ld16_8((c < H ? tX : tY) + H + (c % H) + lane_base, ab, tX + lane_base + c / 2, pw);
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2N + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                    mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2N + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                }
+                mma_commit(&T.mbar);
+                mma_out = true;
+                pend = phase;
+            }
+            ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
+            phase ^= 1;
+            fence_after_sync();
+            f2::f32x2 s22 = 0ull;
 #pragma unroll
-            for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::from_bf16x2(pw[q / 2]), s22);
+            for (int c = 0; c < F; c += 16) {
+                float ab[16];
+                uint32_t pw[8];
+                tmem_ld16_8((c < H ? tX : tY) + H + (c % H) + lane_base, ab, tX + lane_base + c / 2, pw);
+#pragma unroll
+                for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::from_bf16x2(pw[q / 2]), s22);
+            }
+            se = __fmaf_rn(dfc, f2::lo(gb22) + f2::hi(gb22), f2::lo(s22) + f2::hi(s22));
+        } else {
+            // epilogue 1: p = SiLU'(a)(e'W1) -> X[0, F/2), SiLU(a) -> Y[0, F/2), both BF16
+#pragma unroll
+            for (int c = 0; c < F; c += 16) {
+                float v[16], tv[16];
+                tmem_ld16x2(tX + lane_base + c, v, tY + lane_base + c, tv);
+                uint32_t ps[8], pp[8];
+#pragma unroll
+                for (int q = 0; q < 16; q += 2) {              // two features per packed FP32 operation
+                    const f2::f32x2 x = f2::add(f2::pack(v[q], v[q + 1]), *reinterpret_cast<const f2::f32x2*>(S.b1 + c + q));
+                    const f2::f32x2 t = tanh_half(x);            // sigmoid(x) = (1 + tanh(x / 2)) / 2
+                    const f2::f32x2 sg = f2::fma(kHalf2, t, kHalf2), sgc = f2::fma(kMinusHalf2, t, kHalf2);
+                    const f2::f32x2 y = f2::mul(x, sg);          // SiLU
+                    const f2::f32x2 pd = f2::mul(f2::pack(tv[q], tv[q + 1]), f2::fma(y, sgc, sg));   // SiLU' (e'W1)
+                    ps[q / 2] = pack_bf16(f2::lo(y), f2::hi(y));
+                    pp[q / 2] = pack_bf16(f2::lo(pd), f2::hi(pd));
+                }
+                tmem_st8(tY + lane_base + c / 2, ps);
+                tmem_st8(tX + lane_base + c / 2, pp);
+            }
+            tmem_st_wait();
+            fence_before_sync();
+            ok = group_sync_and(bar, ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2T + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                    mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2T + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                }
+                mma_commit(&T.mbar);
+                mma_out = true;
+                pend = phase;
+            }
+            ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
+            phase ^= 1;
+            fence_after_sync();
+            cp_async_wait();                                   // the warp's u_j | mbar_j rows are in G
+            __syncwarp();
+            f2::f32x2 gphi2 = 0ull;                            // (+0, +0)
+            {
+                const int i = valid ? row : 0;
+                const float* ui = a.u + (size_t)i * F;
+                const float* mi = a.mbar + (size_t)i * F;
+#pragma unroll
+                for (int c = 0; c < F; c += 16) {
+                    float v[16];
+                    tmem_ld16((c < H ? tX : tY) + H + (c % H) + lane_base, v);
+                    uint4 w[4];                                // BF16 u_j (w[0], w[1]) and mbar_j (w[2], w[3])
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) w[k] = *reinterpret_cast<const uint4*>(T.G + prow<F>(tid, c + 4 * k));
+                    uint32_t pg[8];
+                    const f2::f32x2 fc2 = f2::splat(fc);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) {
+                        const float4 ui4 = __ldg(reinterpret_cast<const float4*>(ui + c + q));
+                        const float4 mi4 = __ldg(reinterpret_cast<const float4*>(mi + c + q));
+                        const uint32_t u01 = q < 8 ? (q == 0 ? w[0].x : w[0].z) : (q == 8 ? w[1].x : w[1].z);
+                        const uint32_t u23 = q < 8 ? (q == 0 ? w[0].y : w[0].w) : (q == 8 ? w[1].y : w[1].w);
+                        const uint32_t m01 = q < 8 ? (q == 0 ? w[2].x : w[2].z) : (q == 8 ? w[3].x : w[3].z);
+                        const uint32_t m23 = q < 8 ? (q == 0 ? w[2].y : w[2].w) : (q == 8 ? w[3].y : w[3].w);
+                        const f2::f32x2 uj01 = f2::from_bf16x2(u01), uj23 = f2::from_bf16x2(u23);
+                        const f2::f32x2 mj01 = f2::from_bf16x2(m01), mj23 = f2::from_bf16x2(m23);
+                        const f2::f32x2* b2 = reinterpret_cast<const f2::f32x2*>(S.b2 + c + q);
+                        const f2::f32x2 ph01 = f2::add(f2::pack(v[q], v[q + 1]), b2[0]);
+                        const f2::f32x2 ph23 = f2::add(f2::pack(v[q + 2], v[q + 3]), b2[1]);
+                        // g = mbar_i u_j + mbar_j u_i
+                        const f2::f32x2 g01 = f2::fma(f2::pack(mi4.x, mi4.y), uj01, f2::mul(mj01, f2::pack(ui4.x, ui4.y)));
+                        const f2::f32x2 g23 = f2::fma(f2::pack(mi4.z, mi4.w), uj23, f2::mul(mj23, f2::pack(ui4.z, ui4.w)));
+                        gphi2 = f2::fma(g01, ph01, gphi2);
+                        gphi2 = f2::fma(g23, ph23, gphi2);
+                        pg[q / 2] = pack_bf16(f2::lo(g01), f2::hi(g01));
+                        pg[q / 2 + 1] = pack_bf16(f2::lo(g23), f2::hi(g23));
+                        // the message replaces the chunk (read above into w) of this thread's row
+                        const f2::f32x2 o01 = f2::mul(f2::mul(fc2, ph01), mj01), o23 = f2::mul(f2::mul(fc2, ph23), mj23);
+                        *reinterpret_cast<float4*>(T.G + prow<F>(tid, c + q)) =
+                            make_float4(f2::lo(o01), f2::hi(o01), f2::lo(o23), f2::hi(o23));
+                    }
+                    tmem_st8(tY + lane_base + c / 2, pg);     // over SiLU (read by the completed MMA2)
+                }
+            }
+            tmem_st_wait();
+            fence_before_sync();
+            ok = group_sync_and(bar, ok);
+            fence_after_sync();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16_ta(tX + H, tY + kk * 8, make_desc(sW2N + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                    mma_bf16_ta(tY + H, tY + kk * 8, make_desc(sW2N + F * F + kk * 256, 128, F * 16), idesc_h, kk > 0);
+                }
+                mma_commit(&T.mbar);
+                mma_out = true;
+                pend = phase;
+            }
+            ok = ok && mbar_wait(&T.mbar, phase, kWaitIter);
+            if (tid == 0 && ok) mma_out = false;
+            phase ^= 1;
+            fence_after_sync();
+            f2::f32x2 s22 = 0ull;
+#pragma unroll
+            for (int c = 0; c < F; c += 16) {
+                float ab[16];
+                uint32_t pw[8];
+                tmem_ld16_8((c < H ? tX : tY) + H + (c % H) + lane_base, ab, tX + lane_base + c / 2, pw);
+#pragma unroll
+                for (int q = 0; q < 16; q += 2) s22 = f2::fma(f2::pack(ab[q], ab[q + 1]), f2::from_bf16x2(pw[q / 2]), s22);
+            }
+            const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
+            se = dfc * gphi + fc * s2;
         }
-        const float gphi = f2::lo(gphi2) + f2::hi(gphi2), s2 = f2::lo(s22) + f2::hi(s22);
-        float se = dfc * gphi + fc * s2;
-        if (l == 0 && valid) {
+        if (L0 && valid) {
             float dphi;
             (void)rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, &dphi);
             se += dphi;
@@ -1374,14 +1569,20 @@ void go_fwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
                                                           nullptr, nullptr, 0, a.check);
 }
 
-template <int F, int NV, int KC>
-void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
+template <int F, int NV, int KC, bool L0>
+void go_bwd_layer(const PotArgs& a, int K, int* status, cudaStream_t s) {
     const int tiles = a.bwd_tiles > 0 ? a.bwd_tiles : bf16_default_bwd_tiles(F);
     if (tiles == 2)
-        launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups, KC>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
+        launch_persistent(k_edge_bwd_grp<F, NV, kBwdGroups, KC, L0>, (int)sizeof(BwdGSmem<F, kBwdGroups>),
                           kBwdGroups * 2 * F, kT * kBwdGroups, kBwdGroups, a, K, status, s);
     else
-        launch_persistent(k_edge_bwd_bf16<F, NV, KC>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, a, K, status, s);
+        launch_persistent(k_edge_bwd_bf16<F, NV, KC, L0>, (int)sizeof(BwdSmem<F, NV>), 2 * F, kT, 1, a, K, status, s);
+}
+
+template <int F, int NV, int KC>
+void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
+    if (a.layer == 0) go_bwd_layer<F, NV, KC, true>(a, K, status, s);
+    else go_bwd_layer<F, NV, KC, false>(a, K, status, s);
     k_tile_fixup<F><<<fixup_blocks(a.e_cap), 256, 0, s>>>(a.n_atoms, a.row_ptr, a.recv, a.e_cap, a.carry,
                                                           a.carry_w, a.layer > 0 ? a.msg_out : nullptr, NV, 1,
                                                           nullptr, a.force, a.vir6, a.accumulate, a.check);
@@ -1457,13 +1658,24 @@ int bf16_max_ctas_per_sm(int F, bool bwd, int tiles) {
     if (bwd) {
         constexpr int G = kBwdGroups;
         if (tiles <= 0) tiles = bf16_default_bwd_tiles(F);
+        // the fewer of the two layer variants
         if (tiles == 2)
-            return F == 64 ? ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>>, (int)sizeof(BwdGSmem<64, G>),
-                                               G * 128, kT * G)
-                           : ctas_per_sm_limit(k_edge_bwd_grp<32, 3, G, kSpecK<32>>, (int)sizeof(BwdGSmem<32, G>),
-                                               G * 64, kT * G);
-        return F == 64 ? ctas_per_sm_limit(k_edge_bwd_bf16<64, 3, kSpecK<64>>, (int)sizeof(BwdSmem<64, 3>), 128, kT)
-                       : ctas_per_sm_limit(k_edge_bwd_bf16<32, 3, kSpecK<32>>, (int)sizeof(BwdSmem<32, 3>), 64, kT);
+            return F == 64 ? std::min(ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>, false>,
+                                                        (int)sizeof(BwdGSmem<64, G>), G * 128, kT * G),
+                                      ctas_per_sm_limit(k_edge_bwd_grp<64, 3, G, kSpecK<64>, true>,
+                                                        (int)sizeof(BwdGSmem<64, G>), G * 128, kT * G))
+                           : std::min(ctas_per_sm_limit(k_edge_bwd_grp<32, 3, G, kSpecK<32>, false>,
+                                                        (int)sizeof(BwdGSmem<32, G>), G * 64, kT * G),
+                                      ctas_per_sm_limit(k_edge_bwd_grp<32, 3, G, kSpecK<32>, true>,
+                                                        (int)sizeof(BwdGSmem<32, G>), G * 64, kT * G));
+        return F == 64 ? std::min(ctas_per_sm_limit(k_edge_bwd_bf16<64, 3, kSpecK<64>, false>,
+                                                    (int)sizeof(BwdSmem<64, 3>), 128, kT),
+                                  ctas_per_sm_limit(k_edge_bwd_bf16<64, 3, kSpecK<64>, true>,
+                                                    (int)sizeof(BwdSmem<64, 3>), 128, kT))
+                       : std::min(ctas_per_sm_limit(k_edge_bwd_bf16<32, 3, kSpecK<32>, false>,
+                                                    (int)sizeof(BwdSmem<32, 3>), 64, kT),
+                                  ctas_per_sm_limit(k_edge_bwd_bf16<32, 3, kSpecK<32>, true>,
+                                                    (int)sizeof(BwdSmem<32, 3>), 64, kT));
     }
     return F == 64 ? ctas_per_sm_limit(k_edge_fwd_bf16<64, kSpecK<64>>, (int)sizeof(FwdSmem<64>), 128, kT)
                    : ctas_per_sm_limit(k_edge_fwd_bf16<32, kSpecK<32>>, (int)sizeof(FwdSmem<32>), 64, kT);
