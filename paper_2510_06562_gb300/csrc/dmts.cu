@@ -237,6 +237,7 @@ struct dmts_ctx {
     // second stream of the step graph: the large-model evaluation at the end of
     // the outer step runs beside the last small-model evaluation (same positions)
     cudaStream_t s_big = nullptr;
+    bool fold_small = false;           // while capturing a step: the integrator sums F_small's split rows
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool concurrent = true;
     SumScratch kesum{};                    // scratch of the per-system kinetic-energy sum
@@ -836,6 +837,10 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     }
     for (int l = m.L - 1; l >= 0; --l) {
         PotArgs b = bwd_args(a, m, l);
+        // inside a captured step the integrator kernels that read F_small sum
+        // its rows split across tiles (no separate fix-up pass)
+        b.fold_fixup = (which == DMTS_SMALL && c->fold_small && l == 0 && !b.accumulate && !virial &&
+                        m.precision == DMTS_BF16_MLP) ? 1 : 0;
         launch_edge_bwd(c, m, b);
         if (l > 0) launch_atom_bwd_m(c, m, b);
     }
@@ -988,10 +993,17 @@ CellPlace cell_place(dmts_ctx* c, int w) {
     return p;
 }
 
+// F_small as the integrator kernels of a captured step read it (ForceFold).
+ForceFold small_fold(dmts_ctx* c) {
+    const Model& m = c->m[0];
+    if (!c->fold_small) return ForceFold{};
+    return ForceFold{m.row_ptr, m.e_cap, m.carry, m.F + 16, m.F};
+}
+
 int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     struct PlacedReset {                       // no evaluation outside this capture skips its placement
-        dmts_ctx* c;
-        ~PlacedReset() { c->m[0].placed = c->m[1].placed = false; }
+        dmts_ctx* c;                           // or its force fix-up
+        ~PlacedReset() { c->m[0].placed = c->m[1].placed = false; c->fold_small = false; }
     } placed_reset{c};
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     cudaStream_t s = c->stream;
@@ -1024,12 +1036,14 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
         // followed by that model's build, whose compaction empties the cells)
         const CellPlace none{};
         const CellPlace cp0 = cell_place(c, 0), cp1 = cell_place(c, 1);
+        c->fold_small = c->m[0].precision == DMTS_BF16_MLP;
+        const ForceFold fold = small_fold(c);
         for (int k = 0; k < n_inner; ++k) {
             lg.offset = k;
             const bool last = k == n_inner - 1;
             launch_respa_pre(c->N, k == 0, 0.5 * dt * acc, 0.5 * h * acc, 0.5 * h, c->d_x, c->d_v, c->d_inv_m,
                              c->m[0].force, c->m[1].force, c->d_sys, c->d_box, c->d_frame, c->d_q, c->d_flags, vc,
-                             lg, cp0, last ? cp1 : none, s);
+                             lg, cp0, last ? cp1 : none, fold, s);
             c->m[0].placed = cp0.nc > 0;
             c->m[1].placed = last && cp1.nc > 0;
             if (fork && k == n_inner - 1) {
@@ -1052,7 +1066,8 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
         if (!fork) enqueue_eval(c, 1, false, true, Check::None);   // same positions as the last small evaluation
         c->m[0].placed = c->m[1].placed = false;
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
-                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, s);
+                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, fold, s);
+        c->fold_small = false;                 // the fallback body completes its own forces
         if (fallback && ce == cudaSuccess) ce = capture_fallback_node(c, mon.cond, n_inner, dt);
     } else {
         launch_vv_pre(c->N, 0.5 * dt * acc, dt, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,

@@ -134,13 +134,42 @@ void launch_forces_out(int n_atoms, const float* f, double* f_aos, cudaStream_t 
 // with the position wrapped after each half-drift; then quantise x, and put
 // the atom into the fixed-capacity cells of the models evaluated next (cp0,
 // cp1; nc = 0: none), as the pair-list build would.
+// Atom i's small-model force (see ForceFold): split rows summed from the
+// tiles' carry slots (head tile's last slot, then the later tiles' first
+// slots, in tile order, in FP32), rows without pairs zero, other rows read
+// from fs. Returns true if the value did not come from fs.
+__device__ __forceinline__ bool folded_force(const ForceFold& ff, const float* fs, int n, int i, float f[3]) {
+    if (ff.row_ptr) {
+        const long long r0 = min((long long)ff.row_ptr[i], ff.e_cap), r1 = min((long long)ff.row_ptr[i + 1], ff.e_cap);
+        if (r1 <= r0) {
+            f[0] = f[1] = f[2] = 0.f;
+            return true;
+        }
+        const long long t0 = r0 >> 7, t1 = (r1 - 1) >> 7;
+        if (t0 != t1) {
+            const float* cl = ff.carry + (2 * t0 + 1) * (long long)ff.carry_w + ff.F;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = cl[c];
+            for (long long u = t0 + 1; u <= t1; ++u) {
+                const float* cf = ff.carry + 2 * u * (long long)ff.carry_w + ff.F;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f[c] += cf[c];
+            }
+            return true;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] = fs[(size_t)c * n + i];
+    return false;
+}
+
 __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, double half_h,
                             double* __restrict__ x, double* __restrict__ v,
                             const double* __restrict__ inv_m, const float* __restrict__ fs,
                             const float* __restrict__ fb, const int* __restrict__ sys,
                             const double* __restrict__ box, const Frame* __restrict__ frame,
                             uint4* __restrict__ q, int* __restrict__ flags, VerletCheck vc, Langevin lg,
-                            CellPlace cp0, CellPlace cp1) {
+                            CellPlace cp0, CellPlace cp1, ForceFold fold) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double m = 0.0;
     if (i < n) {
@@ -155,10 +184,12 @@ __global__ void k_respa_pre(int n, int first, double c_outer, double c_inner, do
             langevin_normals((unsigned int)i, *lg.step + (unsigned long long)lg.offset, lg.key0, lg.key1, xi);
             sig = lg.c2 * sqrt(lg.kT_accel * im);
         }
+        float fsi[3];
+        (void)folded_force(fold, fs, n, i, fsi);
         for (int c = 0; c < 3; ++c) {
             size_t o = (size_t)c * n + i;
             double vv = v[o];
-            double Fs = (double)fs[o];
+            double Fs = (double)fsi[c];
             if (first) vv = vv + c_outer * im * ((double)fb[o] - Fs);
             else vv = vv + c_inner * im * Fs;
             vv = vv + c_inner * im * Fs;
@@ -185,11 +216,12 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       double* x, double* v, const double* inv_mass, const float* f_small,
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
-                      const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1, cudaStream_t s) {
+                      const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1,
+                      const ForceFold& fold, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
-                                                     frame, q, flags, vc, lg, cp0, cp1);
+                                                     frame, q, flags, vc, lg, cp0, cp1, fold);
     count_launch();
 }
 
@@ -200,11 +232,11 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
 // over blocks; the last block to finish decides whether the step falls back
 // (some atom above the threshold) and sets the graph conditional.
 __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, double c_inner, double* __restrict__ v,
-                                                    const double* __restrict__ inv_m, const float* __restrict__ fs,
+                                                    const double* __restrict__ inv_m, float* fs,
                                                     const float* __restrict__ fb, const double* __restrict__ x,
                                                     double* __restrict__ ke, const double* __restrict__ mass,
                                                     int* __restrict__ flags, unsigned long long* __restrict__ step,
-                                                    int advance, MonitorArgs mon) {
+                                                    int advance, MonitorArgs mon, ForceFold fold) {
     __shared__ unsigned int s_hist[kMonitorBins];
     __shared__ double s_max[8];
     __shared__ unsigned int s_flag;
@@ -221,9 +253,12 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
         double im = inv_m[i];
         double v2 = 0.0, d2 = 0.0;
         bool ok = true;
+        float fsi[3];
+        if (folded_force(fold, fs, n, i, fsi))                  // complete the array for later readers
+            for (int c = 0; c < 3; ++c) fs[(size_t)c * n + i] = fsi[c];
         for (int c = 0; c < 3; ++c) {
             size_t o = (size_t)c * n + i;
-            double Fs = (double)fs[o];
+            double Fs = (double)fsi[c];
             const double dF = (double)fb[o] - Fs;
             d2 += dF * dF;
             double vv = v[o] + c_inner * im * Fs;
@@ -276,12 +311,13 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
 }
 
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
-                       const double* inv_mass, const float* f_small, const float* f_big,
+                       const double* inv_mass, float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
-                       unsigned long long* step, int advance, const MonitorArgs& mon, cudaStream_t s) {
+                       unsigned long long* step, int advance, const MonitorArgs& mon,
+                       const ForceFold& fold, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
-                                                      f_big, x, ke, mass, flags, step, advance, mon);
+                                                      f_big, x, ke, mass, flags, step, advance, mon, fold);
     count_launch();
 }
 

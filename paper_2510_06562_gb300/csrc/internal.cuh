@@ -131,6 +131,20 @@ struct MonitorArgs {
     int use_cond;
 };
 
+// The small model's forces as the integrator kernels of a captured step
+// read them: rows split across 128-pair tiles are summed from the tiles'
+// carry slots (the order and sums of the separate fix-up pass, which the
+// step then skips), rows without pairs read zero, other rows the force
+// array. k_respa_post also writes the summed rows back, so the array is
+// complete after the step. row_ptr == nullptr: the array is complete.
+struct ForceFold {
+    const int* row_ptr;
+    long long e_cap;
+    const float* carry;   // [tiles][2][carry_w]: slot 2t "first", 2t + 1 "last"
+    int carry_w;
+    int F;                // the force scalars follow the F vector values of a slot
+};
+
 // A displacement check run inside a kernel that has just written x (the
 // integrator) or by k_vl_check. st == nullptr: no check.
 struct VerletCheck {
@@ -254,6 +268,7 @@ struct PotArgs {
     int ctas_per_sm;         // persistent CTAs per SM (0: as many as fit)
     int bwd_tiles;           // tensor-core backward: 128-pair tiles in flight per CTA (1 or 2; 0: 2 at F = 64, else 1)
     int fused_fixup;         // tensor-core forward: the per-atom kernel after it sums the split rows itself
+    int fold_fixup;          // tensor-core backward at layer 0: the integrator sums the split force rows
 };
 
 // ---------------------------------------------------------------- launchers
@@ -353,14 +368,16 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       const float* f_big, const int* sys_of_atom, const double* box,
                       const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
                       const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1,
-                      cudaStream_t s);
+                      const ForceFold& fold, cudaStream_t s);
 // after the big force: last inner post-kick and the outer half-kick.
 // With a step counter: advances it by `advance` (the inner steps taken).
 // With a monitor: the force-difference statistics and fallback decision.
+// With fold.row_ptr: F_small's split rows are summed here and written back.
 void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
-                       const double* inv_mass, const float* f_small, const float* f_big,
+                       const double* inv_mass, float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
-                       unsigned long long* step, int advance, const MonitorArgs& mon, cudaStream_t s);
+                       unsigned long long* step, int advance, const MonitorArgs& mon,
+                       const ForceFold& fold, cudaStream_t s);
 // dst = src for the integrator state: x, v (FP64 [3][N]) and one force (FP32 [3][N]).
 void launch_copy_state(int n_atoms, const double* x, const double* v, const float* f, double* x_out,
                        double* v_out, float* f_out, cudaStream_t s);

@@ -1583,6 +1583,7 @@ template <int F, int NV, int KC>
 void go_bwd(const PotArgs& a, int K, int* status, cudaStream_t s) {
     if (a.layer == 0) go_bwd_layer<F, NV, KC, true>(a, K, status, s);
     else go_bwd_layer<F, NV, KC, false>(a, K, status, s);
+    if (a.fold_fixup && a.layer == 0 && !a.accumulate && NV == 3) return;   // the integrator sums the split rows
     k_tile_fixup<F><<<fixup_blocks(a.e_cap), 256, 0, s>>>(a.n_atoms, a.row_ptr, a.recv, a.e_cap, a.carry,
                                                           a.carry_w, a.layer > 0 ? a.msg_out : nullptr, NV, 1,
                                                           nullptr, a.force, a.vir6, a.accumulate, a.check);
@@ -1645,7 +1646,7 @@ void launch_edge_bwd_bf16(const PotArgs& a, int F, int K, int* status, cudaStrea
         if (F == 64) bwd_k<64, 3>(a, K, status, s);
         else bwd_k<32, 3>(a, K, status, s);
     }
-    count_launch(2);
+    count_launch(a.fold_fixup && a.layer == 0 && !a.accumulate && !a.virial ? 1 : 2);
 }
 
 // The backward kernel's tiles in flight per CTA unless the tuner chooses:
