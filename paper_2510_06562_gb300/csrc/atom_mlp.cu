@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
         return t0 == t1 ? 0 : 1;
     };
     double e_const = 0.0;                            // d2 + e0[Z_i] + E_rep,i of atom base + tid
-    if (tid < T::A && base + tid < p.n_atoms && (last || (p.fused_fixup && l == 0))) {
+    if (tid < T::A && base + tid < p.n_atoms && p.energy && (last || (p.fused_fixup && l == 0))) {
         const int i = base + tid;
         float erep = 0.f;
         if (l == 0 && p.fused_fixup) {               // E_rep,i is a scalar slot of the layer-0 pass

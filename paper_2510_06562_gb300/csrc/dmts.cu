@@ -606,6 +606,7 @@ NbrArgs nbr_args(dmts_ctx* c, Model& m, int which) {
 PotArgs pot_args(dmts_ctx* c, Model& m) {
     PotArgs a{};
     a.check = c->d_flags;
+    a.energy = 1;
     a.P = m.P;
     a.off = m.off;
     a.n_layers = m.L;
@@ -830,6 +831,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     enqueue_neighbors(c, which, quantize, check);
     PotArgs a = pot_args(c, m);
     a.virial = virial ? 1 : 0;
+    a.energy = energy ? 1 : 0;
     for (int l = 0; l < m.L; ++l) {
         PotArgs f = fwd_args(c, a, m, l);
         launch_edge_fwd(c, m, f);

@@ -269,6 +269,7 @@ struct PotArgs {
     int bwd_tiles;           // tensor-core backward: 128-pair tiles in flight per CTA (1 or 2; 0: 2 at F = 64, else 1)
     int fused_fixup;         // tensor-core forward: the per-atom kernel after it sums the split rows itself
     int fold_fixup;          // tensor-core backward at layer 0: the integrator sums the split force rows
+    int energy;              // 0: no per-atom energy is read (the forward pass skips the repulsion energy)
 };
 
 // ---------------------------------------------------------------- launchers

@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
     FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l = a.layer;
+    const bool rep_on = l == 0 && a.energy;                // the repulsion energy of layer 0, when read
     const long long E = min((long long)a.row_ptr[a.n_atoms], a.e_cap);
     const long long n_tiles = (E + kT - 1) / kT;
     if ((long long)blockIdx.x >= n_tiles) return;
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const int row = valid ? ex.i : -1;
             if (valid)
                 fill_empty_rows<F>(ex.rp, row, tb + tid == E - 1, a.n_atoms, a.msg_out, [&](int r) {
-                    if (l == 0) a.erep[r] = 0.f;
+                    if (rep_on) a.erep[r] = 0.f;
                 });
             load_idx(a, (tile + gridDim.x) * kT + tid, E, nx);   // next tile's indices
             // the message needs u_j: start copying the warp's rows into P now
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                     float inv_d = rsqrtf(r2);
                     float d = r2 * inv_d;
                     basis16<KC>(d, inv_d, K, a.pi_over_rc, a.bessel_pref, eb, nullptr, fc, dfc);
-                    if (l == 0) rep = 0.5f * rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, nullptr);
+                    if (rep_on) rep = 0.5f * rep_phi(d, a.rep_a, a.rep_inv_rho, a.rep_rc, a.rep_pi_over_rc, nullptr);
                 } else {
 #pragma unroll
                     for (int k = 0; k < kKP; ++k) eb[k] = 0.f;
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
                     }
                 }
             }
-            if (l == 0) warp_scal_segments<1>(&rep, row, &S.ss, tid);
+            if (rep_on) warp_scal_segments<1>(&rep, row, &S.ss, tid);
             fence_before_sync();
             ok = __syncthreads_and(ok);
             warp_vec_segments<F>(S.P, row, &S.vs, a.msg_out, 0, tid);
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* sta
             const TileCtx tc{prev_row, next_row, a.carry + 2 * tile * cw, a.carry + (2 * tile + 1) * cw};
             if (tid < F) {
                 merge_tile_vec<F>(&S.vs, tid, tc, a.msg_out);
-            } else if (tid == F && l == 0) {
+            } else if (tid == F && rep_on) {
                 float* erep = a.erep;
                 merge_tile_scal<1, F>(&S.ss, 0, tc, [erep](int r, int, float v) { erep[r] = v; });
             }
