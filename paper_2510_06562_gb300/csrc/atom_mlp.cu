@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
             v[a][f] = z[a][f] * sig(z[a][f]);
         }
     }
-    store_rows<F>(p.z, base, p.n_atoms, a0, f0, z);
+    // a one-layer model read only for its force needs z, h, dE/dh and E_i of no later kernel
+    const bool keep = !(p.lean && p.n_layers == 1);
+    if (keep) store_rows<F>(p.z, base, p.n_atoms, a0, f0, z);
     put_rows<F>(Y, a0, f0, v);
     __syncthreads();                                                     // W0 read, Y complete
     stage_w<F>(W0, last ? P + p.off.R1 : P + p.off.W_in[l + 1]);
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
 #pragma unroll
         for (int a = 0; a < T::RA; ++a) h[a][f] += v[a][f] + c2;
     }
-    store_rows<F>(p.h, base, p.n_atoms, a0, f0, h);
+    if (keep) store_rows<F>(p.h, base, p.n_atoms, a0, f0, h);
     put_rows<F>(X, a0, f0, h);
     __syncthreads();                                                     // W1 read, X complete
     if (!last) {
@@ -334,11 +336,11 @@ __global__ void __launch_bounds__(AtomTile<F>::NT) k_atom_fwd(PotArgs p, const f
     __syncthreads();                                                     // W0 read, Y and sE complete
     stage_w<F>(W0, wt_of(p, F, l, 2));                                   // U2^T
     static_assert(T::NT >= T::A, "one thread per atom of the tile");
-    if (tid < T::A && base + tid < p.n_atoms) p.Ei[base + tid] = (double)sE[tid] + e_const;
+    if (keep && tid < T::A && base + tid < p.n_atoms) p.Ei[base + tid] = (double)sE[tid] + e_const;
     cp_wait<1>();
     __syncthreads();
     gemm_blk<F>(Y, W1, a0, f0, v);                                       // gh = gq R1^T
-    store_rows<F>(p.gh, base, p.n_atoms, a0, f0, v);
+    if (keep) store_rows<F>(p.gh, base, p.n_atoms, a0, f0, v);
     put_rows<F>(X, a0, f0, v);
     __syncthreads();                                                     // W1 read, X complete
     stage_w<F>(W1, wt_of(p, F, l, 1));                                   // U1^T

@@ -832,6 +832,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
     PotArgs a = pot_args(c, m);
     a.virial = virial ? 1 : 0;
     a.energy = energy ? 1 : 0;
+    a.lean = (which == DMTS_SMALL && c->fold_small && !energy && !virial) ? 1 : 0;   // inside a captured step
     for (int l = 0; l < m.L; ++l) {
         PotArgs f = fwd_args(c, a, m, l);
         launch_edge_fwd(c, m, f);

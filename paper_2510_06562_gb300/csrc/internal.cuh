@@ -181,7 +181,7 @@ struct NbrArgs {
     // Verlet-skin mode
     const int* gate;         // non-null: the kernel runs only if *gate != 0
     int exact;               // 1: exact FP64 decision in the band; 0: keep every candidate with d^2 <= rc2_hi
-    int flag_row;            // flags index receiving the longest row
+    int flag_row;            // flags index receiving the longest row that exceeded row_cap
     double* xref;            // non-null: the builder records x here (positions of the rebuild)
     const int* src_rows;     // row filter input: candidate rows [N][src_cap], sorted by j
     const int* src_cnt;      // [N]
@@ -270,6 +270,8 @@ struct PotArgs {
     int fused_fixup;         // tensor-core forward: the per-atom kernel after it sums the split rows itself
     int fold_fixup;          // tensor-core backward at layer 0: the integrator sums the split force rows
     int energy;              // 0: no per-atom energy is read (the forward pass skips the repulsion energy)
+    int lean;                // 1: only the force is read afterwards (the per-atom kernel of a one-layer
+                             // model stores neither z, h, dE/dh nor E_i)
 };
 
 // ---------------------------------------------------------------- launchers

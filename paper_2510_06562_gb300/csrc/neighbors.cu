@@ -389,8 +389,10 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
     }
     __syncwarp();
     if (lane == 0) {
-        atomicMax(&a.flags[a.flag_row], n_row);
-        if (n_row > a.row_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+        if (n_row > a.row_cap) {                     // the capacity grows from the longest overflowing row
+            atomicMax(&a.flags[a.flag_row], n_row);
+            atomicOr(&a.flags[kFlagOverflow], 1);
+        }
     }
     int n_keep = min(n_row, a.row_cap);
     int* dst = a.nbr_tmp + (size_t)i * a.row_cap;
@@ -536,8 +538,10 @@ __global__ void __launch_bounds__(256) k_row_filter(NbrArgs a) {
         n_row += __popc(m);
     }
     if (lane == 0) {
-        atomicMax(&a.flags[a.flag_row], n_row);
-        if (n_row > a.row_cap) atomicOr(&a.flags[kFlagOverflow], 1);
+        if (n_row > a.row_cap) {                     // the capacity grows from the longest overflowing row
+            atomicMax(&a.flags[a.flag_row], n_row);
+            atomicOr(&a.flags[kFlagOverflow], 1);
+        }
         a.nbr_cnt[i] = min(n_row, a.row_cap);
     }
 }
