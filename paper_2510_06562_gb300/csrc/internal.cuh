@@ -167,7 +167,7 @@ struct NbrArgs {
     int nc;                  // cells per dimension (0: all pairs within system)
     const int* cell_start;   // [nc^3 + 1]
     const int* cell_atoms;   // [N] atoms in cell order
-    const uint4* cell_q;     // [N] their fixed-point positions, in cell order
+    const uint4* cell_q;     // [N] their fixed-point positions {qx, qy, qz, atom index}, in cell order
     const int* atom_pos;     // [N] each atom's place in cell order
     int row_cap;
     long long e_cap;
@@ -520,7 +520,7 @@ __device__ __forceinline__ void place_in_cell(const CellPlace& cp, int i, uint4 
     if (slot < cp.ccap) {
         const int pos = c * cp.ccap + slot;
         cp.atoms[pos] = i;
-        cp.q[pos] = p;
+        cp.q[pos] = make_uint4(p.x, p.y, p.z, (unsigned int)i);   // the atom index beside its position
         cp.pos[i] = pos;
     } else {
         cp.pos[i] = -1;

@@ -223,8 +223,9 @@ __global__ void k_cell_place(int n, const uint4* __restrict__ q, CellPlace cp, i
 }
 
 // Atoms in cell order, with their fixed-point positions beside them (the
-// builder then reads each cell's candidates contiguously) and each atom's own
-// place in that order.
+// builder then reads each cell's candidates contiguously; the fourth word
+// holds the atom index instead of the system) and each atom's own place in
+// that order.
 __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell, const int* __restrict__ slot,
                             const int* __restrict__ start, int* __restrict__ cell_atoms, const uint4* __restrict__ q,
                             uint4* __restrict__ cell_q, int* __restrict__ atom_pos, const int* gate) {
@@ -232,8 +233,9 @@ __global__ void k_cell_fill(int n, const int* __restrict__ atom_cell, const int*
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int pos = start[atom_cell[i]] + slot[i];
+    const uint4 qi = q[i];
     cell_atoms[pos] = i;
-    cell_q[pos] = q[i];
+    cell_q[pos] = make_uint4(qi.x, qi.y, qi.z, (unsigned int)i);
     atom_pos[i] = pos;
 }
 
@@ -319,7 +321,9 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
         int cnt = 0, st = 0;
         if (lane < 27) {
             int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-            int x2 = (cx + dx + nc) % nc, y2 = (cy + dy + nc) % nc, z2 = (cz + dz + nc) % nc;
+            // periodic neighbour cells (the offsets are -1, 0 or 1: one wrap at most)
+            auto wrap = [nc](int t) { return t < 0 ? t + nc : (t >= nc ? t - nc : t); };
+            int x2 = wrap(cx + dx), y2 = wrap(cy + dy), z2 = wrap(cz + dz);
             int c = ((s * nc + z2) * nc + y2) * nc + x2;       // the system's own cells
             c = DMTS_IDX(c, a.ccap > 0 ? (long long)a.n_cells : (long long)nc * nc * nc * a.n_sys, a.flags);
             if (a.ccap > 0) {                        // fixed-capacity cells
@@ -360,13 +364,14 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
                 const int pos = DMTS_IDX(cstart[c] + (v - cpre[c]),
                                          a.ccap > 0 ? (long long)a.n_cells * a.ccap : (long long)a.n_atoms, a.flags);
                 if (pos != my_pos) {
-                    float3 r = edge_vec(qi, a.cell_q[pos], qscale);
+                    const uint4 qc = a.cell_q[pos];          // position and atom index in one load
+                    float3 r = edge_vec(qi, qc, qscale);
                     float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                     if (d2 < rc2_lo) {
                         keep = true;
-                        j = DMTS_IDX(a.cell_atoms[pos], a.n_atoms, a.flags);
+                        j = DMTS_IDX((int)qc.w, a.n_atoms, a.flags);
                     } else if (d2 <= rc2_hi) {
-                        j = DMTS_IDX(a.cell_atoms[pos], a.n_atoms, a.flags);
+                        j = DMTS_IDX((int)qc.w, a.n_atoms, a.flags);
                         keep = a.exact ? exact_inside(a.x, a.n_atoms, i, j, L, a.rc) : true;
                     }
                 }
