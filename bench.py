@@ -208,8 +208,10 @@ def measure(D, I, torch, s, models_, prec, args, flush, dt, n_inner, seed):
 
 
 KERNEL_OF_STAGE = {
-    # (precision is BF16, stage prefix) -> (kernel name in the ncu capture, source file)
-    (True, "edge_bwd"): ("k_edge_bwd_grp<64,3,2,16>", "potential_bf16.cu"),
+    # (precision is BF16, stage name or prefix) -> (kernel name in the ncu capture, source file);
+    # the tensor-core backward pass has a layer-0 variant (two MMA groups per tile)
+    (True, "edge_bwd_l0"): ("k_edge_bwd_grp<64,3,2,16,1>", "potential_bf16.cu"),
+    (True, "edge_bwd"): ("k_edge_bwd_grp<64,3,2,16,0>", "potential_bf16.cu"),
     (True, "edge_fwd"): ("k_edge_fwd_bf16<64,16>", "potential_bf16.cu"),
     (False, "edge_bwd"): ("k_edge_bwd<64,16>", "potential_f32.cu"),
     (False, "edge_fwd"): ("k_edge_fwd<64,16>", "potential_f32.cu"),
@@ -248,11 +250,18 @@ def roofline_of(D, prec, stages_big, E_big, ba):
         flop_edge = 2 * (2 * K * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (K * F + F * F)
         peak, bound, src, kind = FP32_SIMT_TFLOPS, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "FP32 SIMT"
     else:
-        # tensor-core MMAs issued (K padded to 16): forward 16F + F^2, backward 2 (16F) + 2 F^2 MACs per pair
-        flop_edge = 2 * (2 * 16 * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (16 * F + F * F)
+        # tensor-core MMAs issued (K padded to 16): forward 16F + F^2, backward 2 (16F) + 2 F^2 MACs per
+        # pair, and 2 (16F) + F^2 at layer 0, where the filter is not recomputed
+        if dom == "edge_bwd_l0":
+            flop_edge = 2 * (2 * 16 * F + F * F)
+        elif dom.startswith("edge_bwd"):
+            flop_edge = 2 * (2 * 16 * F + 2 * F * F)
+        else:
+            flop_edge = 2 * (16 * F + F * F)
         peak, bound, src, kind = measured_peak("bf16_tflops"), "tensor", "MEASURED_PEAKS.json bf16_tflops (burst)", "BF16 tcgen05"
     achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
-    kname, ksrc = KERNEL_OF_STAGE[(prec != D.FP32, dom[:8])]
+    bf16 = prec != D.FP32
+    kname, ksrc = KERNEL_OF_STAGE.get((bf16, dom)) or KERNEL_OF_STAGE[(bf16, dom[:8])]
     return {"kernel": f"{dom} (big model, {kind})", "bound": bound, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic(kname, ksrc, E_big),
             "algorithmic_flop_per_launch": flop_edge * E_big, "launch_ms": stages_big[dom], "peak_source": src}
