@@ -250,14 +250,10 @@ def roofline_of(D, prec, stages_big, E_big, ba):
         flop_edge = 2 * (2 * K * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (K * F + F * F)
         peak, bound, src, kind = FP32_SIMT_TFLOPS, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "FP32 SIMT"
     else:
-        # tensor-core MMAs issued (K padded to 16): forward 16F + F^2, backward 2 (16F) + 2 F^2 MACs per
-        # pair, and 2 (16F) + F^2 at layer 0, where the filter is not recomputed
-        if dom == "edge_bwd_l0":
-            flop_edge = 2 * (2 * 16 * F + F * F)
-        elif dom.startswith("edge_bwd"):
-            flop_edge = 2 * (2 * 16 * F + 2 * F * F)
-        else:
-            flop_edge = 2 * (16 * F + F * F)
+        # the algorithmic edge-GEMM work per pair and layer, K padded to 16: one pass 2F(16 + F) forward,
+        # two backward (the adjoint and the recomputed filter). The layer-0 backward kernel skips the
+        # recomputation and issues 2 (2 * 16 F + F^2); the figure stays the algorithm's.
+        flop_edge = 2 * (2 * 16 * F + 2 * F * F) if dom.startswith("edge_bwd") else 2 * (16 * F + F * F)
         peak, bound, src, kind = measured_peak("bf16_tflops"), "tensor", "MEASURED_PEAKS.json bf16_tflops (burst)", "BF16 tcgen05"
     achieved = flop_edge * E_big / (stages_big[dom] * 1e-3) / 1e12
     bf16 = prec != D.FP32
