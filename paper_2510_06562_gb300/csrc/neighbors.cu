@@ -333,6 +333,19 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
                 st = a.cell_start[c];
                 cnt = a.cell_start[c + 1] - st;
             }
+            // A neighbour cell whose box lies entirely beyond the cutoff has no
+            // pair: its distance from atom i is at least that of the faces of
+            // i's own cell it lies behind (fixed-point units, then A). The cells
+            // are wider than the cutoff, so a farther periodic image of the cell
+            // is out of range too; the 0.1 % margin covers the FP32 rounding of
+            // the bound. About a third of the candidates of a 27-cell scan are
+            // skipped when the cells are barely wider than the cutoff.
+            const float W = 4294967296.0f / (float)nc;
+            auto face = [W](int d, int cc, unsigned int q) {
+                return d == 0 ? 0.f : (d < 0 ? (float)q - (float)cc * W : (float)(cc + 1) * W - (float)q);
+            };
+            const float fx = face(dx, cx, qi.x), fy = face(dy, cy, qi.y), fz = face(dz, cz, qi.z);
+            if ((fx * fx + fy * fy + fz * fz) * (qscale * qscale) > a.rc2_hi * 1.001f) cnt = 0;
         }
         int v = cnt;
         for (int o = 1; o < 32; o <<= 1) {
