@@ -13,8 +13,8 @@
 //
 // Layer 0 reads h^0 = A[Z_i] from the per-atom copy built once per parameter
 // upload. A CTA takes A = 32 atoms; each stage is an [A x F] x [F x F]
-// product, each thread owning RA atoms x RF features (4 x 4 at F = 64; 2 x 2
-// at F = 32, so that the narrow model still has 8 warps per CTA). Inputs stay in their
+// product, each thread owning RA atoms x RF features (4 x 4 at F = 64; 4 x 2
+// at F = 32, so that the narrow model still has 4 warps per CTA). Inputs stay in their
 // natural [atom][k] layout in shared memory; the weight matrix of the next
 // stage (row-major; the transposed ones are copies prepared on the host)
 // streams in with cp.async while the current stage computes.
@@ -29,10 +29,10 @@ namespace {
 template <int F>
 struct AtomTile {
     static constexpr int A = 32;            // atoms per CTA
-    static constexpr int RA = F >= 64 ? 4 : 2;  // atoms per thread
+    static constexpr int RA = 4;            // atoms per thread
     static constexpr int RF = F >= 64 ? 4 : 2;  // features per thread
     static constexpr int FG = F / RF;       // feature groups
-    static constexpr int NT = (A / RA) * FG; // threads per CTA: 128 (F = 64) or 256 (F = 32)
+    static constexpr int NT = (A / RA) * FG; // threads per CTA: 128
     static constexpr int XS = F + 4;        // row stride of per-atom rows [a][k]
     static constexpr int WS = F + 4;        // row stride of staged weights [k][f]
     static constexpr int SMEM = (2 * A * XS + 2 * F * WS) * 4;
