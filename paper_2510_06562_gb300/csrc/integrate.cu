@@ -17,6 +17,11 @@ constexpr double kKinetic = 103.64269652680505;
 
 // x - L floor(x / L) for periodic boxes; coordinates already inside [0, L)
 // are returned as they are (the common case needs no FP64 division).
+// Threads per CTA of the integrator kernels: their FP64 arithmetic (GB300
+// issues FP64 at a small fraction of its FP32 rate) spreads over every SM
+// only with small CTAs (192 of them for 12,288 atoms instead of 48).
+constexpr int kIntThreads = 64;
+
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     return (L > 0.0 && (x < 0.0 || x >= L)) ? x - L * floor(x / L) : x;
 }
@@ -219,7 +224,7 @@ void launch_respa_pre(int n_atoms, int first, double c_outer, double c_inner, do
                       const Langevin& lg, const CellPlace& cp0, const CellPlace& cp1,
                       const ForceFold& fold, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_respa_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
+    k_respa_pre<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, first, c_outer, c_inner, half_h, x, v,
                                                      inv_mass, f_small, f_big, sys_of_atom, box,
                                                      frame, q, flags, vc, lg, cp0, cp1, fold);
     count_launch();
@@ -316,7 +321,7 @@ void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        unsigned long long* step, int advance, const MonitorArgs& mon,
                        const ForceFold& fold, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_respa_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
+    k_respa_post<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
                                                       f_big, x, ke, mass, flags, step, advance, mon, fold);
     count_launch();
 }
@@ -387,7 +392,7 @@ void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const double* box, const Frame* frame, uint4* q, int* flags, const VerletCheck& vc,
                    const Langevin& lg, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_vv_pre<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, dt, x, v, inv_mass, f, sys_of_atom,
+    k_vv_pre<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_half, dt, x, v, inv_mass, f, sys_of_atom,
                                                   box, frame, q, flags, vc, lg);
     count_launch();
 }
@@ -418,7 +423,7 @@ void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mas
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
                     unsigned long long* step, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_vv_post<<<(n_atoms + 255) / 256, 256, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags, step);
+    k_vv_post<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags, step);
     count_launch();
 }
 
