@@ -210,6 +210,8 @@ struct dmts_ctx {
     double *d_ke = nullptr, *d_ekin = nullptr;
     double* d_ring = nullptr;
     int ring_len = 0;
+    double* d_epart = nullptr;             // fused energy epilogue: block partials
+    unsigned int* d_eticket = nullptr;
     int* d_flags = nullptr;
     int* h_flags = nullptr;      // pinned
     double *d_bx = nullptr, *d_bv = nullptr;
@@ -823,8 +825,10 @@ PotArgs bwd_args(const PotArgs& a, Model& m, int l) {
     return b;
 }
 
+// sum_energy false: the per-atom energies are computed but summed elsewhere
+// (the closing kernel's fused energy epilogue).
 void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Check check = Check::Kernel,
-                  bool virial = false) {
+                  bool virial = false, bool sum_energy = true) {
     Range nvtx_range(which == DMTS_BIG ? "evaluate big model" : "evaluate small model");
     Model& m = c->m[which];
     cudaStream_t s = c->stream;
@@ -847,7 +851,7 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
         launch_edge_bwd(c, m, b);
         if (l > 0) launch_atom_bwd_m(c, m, b);
     }
-    if (energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, m.esum, s);
+    if (energy && sum_energy) launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, m.esum, s);
 }
 
 int sync_check(dmts_ctx* c) {
@@ -949,7 +953,7 @@ void enqueue_fallback(dmts_ctx* c, int n_inner, double dt) {
                       c->d_frame, c->d_q, c->d_flags, verlet_check(c), lg, c->stream);
         enqueue_eval(c, 1, nonper, true, Check::Done);
         launch_vv_post(c->N, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
-                       c->d_flags, nullptr, c->stream);
+                       c->d_flags, nullptr, EnergyFuse{}, c->stream);
     }
     enqueue_eval(c, 0, false, false, Check::None);
 }
@@ -1018,6 +1022,11 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
     // the integrator kernels that move the atoms also run the neighbour-list
     // displacement check (with a skin)
     const VerletCheck vc = verlet_check(c);
+    // one system, no fallback: the closing kernel sums the energies and writes the record
+    const bool fuse_e = c->n_sys == 1 && c->fb_threshold <= 0.0;
+    EnergyFuse ef{};
+    if (fuse_e)
+        ef = EnergyFuse{1, c->m[1].Ei, c->m[1].E, c->d_ekin, c->d_epart, c->d_eticket, c->d_ring, c->ring_len};
     if (c->m[0].present) {
         double h = dt / n_inner;
         Langevin lg = langevin(c, h);
@@ -1057,7 +1066,7 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
                 CUDA_TRY(cudaEventRecord(c->ev_fork, s));
                 CUDA_TRY(cudaStreamWaitEvent(c->s_big, c->ev_fork, 0));
                 c->stream = c->s_big;                          // every launcher enqueues on c->stream
-                enqueue_eval(c, 1, false, true, Check::None);
+                enqueue_eval(c, 1, false, true, Check::None, false, !fuse_e);
                 c->stream = s;
                 CUDA_TRY(cudaEventRecord(c->ev_join, c->s_big));
                 enqueue_eval(c, 0, false, false, Check::None);
@@ -1066,21 +1075,23 @@ int capture_step_graph(dmts_ctx* c, int n_inner, double dt) {
                 enqueue_eval(c, 0, nonper, false, Check::Done);   // the small model's energy is not reported
             }
         }
-        if (!fork) enqueue_eval(c, 1, false, true, Check::None);   // same positions as the last small evaluation
+        if (!fork) enqueue_eval(c, 1, false, true, Check::None, false, !fuse_e);   // same positions as the last small evaluation
         c->m[0].placed = c->m[1].placed = false;
         launch_respa_post(c->N, 0.5 * dt * acc, 0.5 * h * acc, c->d_v, c->d_inv_m, c->m[0].force,
-                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, fold, s);
+                          c->m[1].force, c->d_x, c->d_ke, c->d_mass, c->d_flags, c->d_rng, n_inner, mon, fold, ef, s);
         c->fold_small = false;                 // the fallback body completes its own forces
         if (fallback && ce == cudaSuccess) ce = capture_fallback_node(c, mon.cond, n_inner, dt);
     } else {
         launch_vv_pre(c->N, 0.5 * dt * acc, dt, c->d_x, c->d_v, c->d_inv_m, c->m[1].force, c->d_sys, c->d_box,
                       c->d_frame, c->d_q, c->d_flags, vc, langevin(c, dt), s);
-        enqueue_eval(c, 1, nonper, true, Check::Done);
+        enqueue_eval(c, 1, nonper, true, Check::Done, false, !fuse_e);
         launch_vv_post(c->N, 0.5 * dt * acc, c->d_v, c->d_inv_m, c->m[1].force, c->d_x, c->d_ke, c->d_mass,
-                       c->d_flags, c->d_rng, s);
+                       c->d_flags, c->d_rng, ef, s);
     }
-    launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, c->kesum, s);
-    launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
+    if (!fuse_e) {
+        launch_system_sum(c->n_sys, c->d_off, c->d_ke, c->d_ekin, 1, c->kesum, s);
+        launch_energy_record(c->n_sys, c->m[1].E, c->d_ekin, c->d_ring, c->ring_len, c->d_flags, s);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess) e = ce;
@@ -1208,7 +1219,7 @@ void dmts_destroy(dmts_ctx* c) {
     free_model(c->m[1]);
     dfree(c->d_off); dfree(c->d_species); dfree(c->d_sys); dfree(c->d_box); dfree(c->d_mass);
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
-    dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags);
+    dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags); dfree(c->d_epart); dfree(c->d_eticket);
     dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
     dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng); dfree(c->kesum.part); dfree(c->kesum.ctr);
     dfree(c->d_mon); dfree(c->d_sx); dfree(c->d_sv); dfree(c->d_sf);
@@ -1333,6 +1344,9 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(dalloc(&c->d_stage, (size_t)6 * N));
     CREATE_TRY(dalloc(&c->d_ke, N));
     CREATE_TRY(dalloc(&c->d_ekin, ns));
+    CREATE_TRY(dalloc(&c->d_epart, (size_t)2 * std::max(1, integrator_blocks(N))));
+    CREATE_TRY(dalloc(&c->d_eticket, 1));
+    CREATE_TRY(cudaMemset(c->d_eticket, 0, sizeof(unsigned int)));
     CREATE_TRY(dalloc(&c->d_flags, kFlagCount));
     CREATE_TRY(dalloc(&c->d_bx, (size_t)3 * N));
     CREATE_TRY(dalloc(&c->d_bv, (size_t)3 * N));

@@ -22,6 +22,62 @@ constexpr double kKinetic = 103.64269652680505;
 // only with small CTAs (192 of them for 12,288 atoms instead of 48).
 constexpr int kIntThreads = 64;
 
+int integrator_blocks(int n_atoms) { return (n_atoms + kIntThreads - 1) / kIntThreads; }
+
+// The fused energy epilogue of a closing kernel (see EnergyFuse); every
+// thread of every block calls it (ke_i = 0 past the last atom). Sums are
+// FP64: within a block in warp order, then over the blocks in block order.
+__device__ __forceinline__ void energy_epilogue(const EnergyFuse& ef, int n, int i, double ke_i, int* flags) {
+    __shared__ double s_part[2][kIntThreads / 32];
+    __shared__ bool s_last_e;
+    double a = i < n ? ke_i : 0.0;
+    double b = (i < n && ef.ei) ? ef.ei[i] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { s_part[0][w] = a; s_part[1][w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { ta += s_part[0][k]; tb += s_part[1][k]; }
+        ef.part[2 * blockIdx.x] = ta;
+        ef.part[2 * blockIdx.x + 1] = tb;
+        __threadfence();
+        s_last_e = atomicAdd(ef.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last_e && w == 0) {
+        __threadfence();
+        double ua = 0.0, ub = 0.0;
+        for (int k = lane; k < (int)gridDim.x; k += 32) {
+            ua += __ldcg(ef.part + 2 * k);
+            ub += __ldcg(ef.part + 2 * k + 1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ua += __shfl_down_sync(0xffffffffu, ua, o);
+            ub += __shfl_down_sync(0xffffffffu, ub, o);
+        }
+        if (lane == 0) {
+            *ef.ekin = ua;
+            if (ef.ei) *ef.epot = ub;
+            const double ep = *ef.epot;
+            const int step = flags[kFlagStep];
+            if (step < ef.ring_len) {
+                double* o = ef.ring + (size_t)step * 3;
+                o[0] = ep;
+                o[1] = ua;
+                o[2] = ep + ua;
+            }
+            flags[kFlagStep] = step + 1;
+            *ef.ticket = 0u;
+        }
+    }
+}
+
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     return (L > 0.0 && (x < 0.0 || x >= L)) ? x - L * floor(x / L) : x;
 }
@@ -241,7 +297,7 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
                                                     const float* __restrict__ fb, const double* __restrict__ x,
                                                     double* __restrict__ ke, const double* __restrict__ mass,
                                                     int* __restrict__ flags, unsigned long long* __restrict__ step,
-                                                    int advance, MonitorArgs mon, ForceFold fold) {
+                                                    int advance, MonitorArgs mon, ForceFold fold, EnergyFuse ef) {
     __shared__ unsigned int s_hist[kMonitorBins];
     __shared__ double s_max[8];
     __shared__ unsigned int s_flag;
@@ -252,7 +308,7 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
         if (threadIdx.x == 0) s_flag = 0u;
         __syncthreads();
     }
-    double df = 0.0;
+    double df = 0.0, ke_i = 0.0;
     if (i < n) {
         if (step && i == 0) *step += (unsigned long long)advance;   // every reader of it ran in earlier kernels
         double im = inv_m[i];
@@ -272,7 +328,8 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
             v2 += vv * vv;
             ok = ok && isfinite(vv) && isfinite(x[o]);
         }
-        ke[i] = 0.5 * mass[i] * v2 * kKinetic;
+        ke_i = 0.5 * mass[i] * v2 * kKinetic;
+        ke[i] = ke_i;
         if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
         df = sqrt(d2);
         if (mon.mon) {
@@ -284,6 +341,7 @@ __global__ void __launch_bounds__(256) k_respa_post(int n, double c_outer, doubl
             if (mon.threshold > 0.0 && !(df <= mon.threshold)) atomicAdd(&s_flag, 1u);
         }
     }
+    if (ef.on) energy_epilogue(ef, n, i, ke_i, flags);
     if (!mon.mon) return;
     if (!(df == df)) df = 1e300;
     double m = df;
@@ -319,10 +377,10 @@ void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
                        unsigned long long* step, int advance, const MonitorArgs& mon,
-                       const ForceFold& fold, cudaStream_t s) {
+                       const ForceFold& fold, const EnergyFuse& ef, cudaStream_t s) {
     if (n_atoms == 0) return;
     k_respa_post<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_outer, c_inner, v, inv_mass, f_small,
-                                                      f_big, x, ke, mass, flags, step, advance, mon, fold);
+                                                      f_big, x, ke, mass, flags, step, advance, mon, fold, ef);
     count_launch();
 }
 
@@ -401,29 +459,34 @@ __global__ void k_vv_post(int n, double c_half, double* __restrict__ v,
                           const double* __restrict__ inv_m, const float* __restrict__ f,
                           const double* __restrict__ x, double* __restrict__ ke,
                           const double* __restrict__ mass, int* __restrict__ flags,
-                          unsigned long long* __restrict__ step) {
+                          unsigned long long* __restrict__ step, EnergyFuse ef) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (step && i == 0) *step += 1ull;
-    double im = inv_m[i];
-    double v2 = 0.0;
-    bool ok = true;
-    for (int c = 0; c < 3; ++c) {
-        size_t o = (size_t)c * n + i;
-        double vv = v[o] + c_half * im * (double)f[o];
-        v[o] = vv;
-        v2 += vv * vv;
-        ok = ok && isfinite(vv) && isfinite(x[o]);
+    double ke_i = 0.0;
+    if (i < n) {
+        if (step && i == 0) *step += 1ull;
+        double im = inv_m[i];
+        double v2 = 0.0;
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            size_t o = (size_t)c * n + i;
+            double vv = v[o] + c_half * im * (double)f[o];
+            v[o] = vv;
+            v2 += vv * vv;
+            ok = ok && isfinite(vv) && isfinite(x[o]);
+        }
+        ke_i = 0.5 * mass[i] * v2 * kKinetic;
+        ke[i] = ke_i;
+        if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
     }
-    ke[i] = 0.5 * mass[i] * v2 * kKinetic;
-    if (!ok) atomicOr(&flags[kFlagNonfinite], 1);
+    if (ef.on) energy_epilogue(ef, n, i, ke_i, flags);
 }
 
 void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
-                    unsigned long long* step, cudaStream_t s) {
+                    unsigned long long* step, const EnergyFuse& ef, cudaStream_t s) {
     if (n_atoms == 0) return;
-    k_vv_post<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke, mass, flags, step);
+    k_vv_post<<<(n_atoms + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(n_atoms, c_half, v, inv_mass, f, x, ke,
+                                                                               mass, flags, step, ef);
     count_launch();
 }
 

@@ -145,6 +145,22 @@ struct ForceFold {
     int F;                // the force scalars follow the F vector values of a slot
 };
 
+// One system and no fallback: the closing kernel of a captured step also
+// sums the kinetic energy and the large model's per-atom energies (each
+// block's partial sums, then the last block adds the partials in block
+// order) and writes the step's energy record, in place of two sum kernels
+// and the record kernel. on == 0: those kernels run.
+struct EnergyFuse {
+    int on;
+    const double* ei;        // the large model's per-atom energies E_i
+    double* epot;            // [1] their sum
+    double* ekin;            // [1] the kinetic energy
+    double* part;            // [2 * blocks] block partials (kinetic, potential)
+    unsigned int* ticket;    // zero between steps (the last block resets it)
+    double* ring;            // energy record [ring_len][3] at flags[kFlagStep]
+    int ring_len;
+};
+
 // A displacement check run inside a kernel that has just written x (the
 // integrator) or by k_vl_check. st == nullptr: no check.
 struct VerletCheck {
@@ -380,7 +396,9 @@ void launch_respa_post(int n_atoms, double c_outer, double c_inner, double* v,
                        const double* inv_mass, float* f_small, const float* f_big,
                        const double* x, double* ke, const double* mass, int* flags,
                        unsigned long long* step, int advance, const MonitorArgs& mon,
-                       const ForceFold& fold, cudaStream_t s);
+                       const ForceFold& fold, const EnergyFuse& ef, cudaStream_t s);
+// Blocks of the closing kernels for n atoms (sizes EnergyFuse::part).
+int integrator_blocks(int n_atoms);
 // dst = src for the integrator state: x, v (FP64 [3][N]) and one force (FP32 [3][N]).
 void launch_copy_state(int n_atoms, const double* x, const double* v, const float* f, double* x_out,
                        double* v_out, float* f_out, cudaStream_t s);
@@ -392,7 +410,7 @@ void launch_vv_pre(int n_atoms, double c_half, double dt, double* x, double* v,
                    const Langevin& lg, cudaStream_t s);
 void launch_vv_post(int n_atoms, double c_half, double* v, const double* inv_mass,
                     const float* f, const double* x, double* ke, const double* mass, int* flags,
-                    unsigned long long* step, cudaStream_t s);
+                    unsigned long long* step, const EnergyFuse& ef, cudaStream_t s);
 // energies ring: ring[step][sys] = {Epot, Ekin, Epot + Ekin}; step = flags[kFlagStep]++.
 void launch_energy_record(int n_sys, const double* epot, const double* ekin, double* ring,
                           int ring_len, int* flags, cudaStream_t s);
