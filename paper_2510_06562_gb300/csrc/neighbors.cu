@@ -414,11 +414,40 @@ __device__ __forceinline__ void nbr_build_row(const NbrArgs& a, int* smem_i, int
     }
     int n_keep = min(n_row, a.row_cap);
     int* dst = a.nbr_tmp + (size_t)i * a.row_cap;
-    for (int k = lane; k < n_keep; k += 32) {
-        int jk = row[k];
-        int rank = 0;
-        for (int m2 = 0; m2 < n_keep; ++m2) rank += (row[m2] < jk);
-        dst[rank] = jk;
+    if (n_keep > 32 && n_keep <= 64) {
+        // 33 to 64 kept pairs: a bitonic sort of 64 keys, two per lane (key
+        // e = lane + 32 h in register h), padded with INT_MAX; the rank sort
+        // below would take n_keep shared-memory reads per key
+        int v[2];
+        v[0] = row[lane];
+        v[1] = lane + 32 < n_keep ? row[lane + 32] : 0x7fffffff;
+        for (int k = 2; k <= 64; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                if (jj == 32) {                              // partner: the other register of this lane
+                    const int lo = min(v[0], v[1]), hi = max(v[0], v[1]);
+                    v[0] = lo;                                // k = 64: ascending over the whole row
+                    v[1] = hi;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = lane + 32 * h;
+                        const int o = __shfl_xor_sync(0xffffffffu, v[h], jj);
+                        const bool up = (e & k) == 0;         // this k-block sorts ascending
+                        const bool low = (e & jj) == 0;       // this key is the lower of its pair
+                        v[h] = (low == up) ? min(v[h], o) : max(v[h], o);
+                    }
+                }
+            }
+        }
+        dst[lane] = v[0];
+        if (lane + 32 < n_keep) dst[lane + 32] = v[1];
+    } else {
+        for (int k = lane; k < n_keep; k += 32) {
+            int jk = row[k];
+            int rank = 0;
+            for (int m2 = 0; m2 < n_keep; ++m2) rank += (row[m2] < jk);
+            dst[rank] = jk;
+        }
     }
     if (lane == 0) a.nbr_cnt[i] = n_keep;
     n_out = n_keep;
