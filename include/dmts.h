@@ -296,7 +296,9 @@ DMTS_API int dmts_get_bwd_tiles(dmts_ctx* ctx, int which);
 
 /* Time one model's force evaluation at the current positions, stage by stage,
  * with CUDA events on the context's stream, averaged over reps (>= 1)
- * evaluations. ms_out[n_out] receives milliseconds per evaluation for:
+ * evaluations; each timed stage is bracketed by its own pair of events, whose
+ * own cost (about 2 us on GB300) it includes, and stages without work read 0.
+ * ms_out[n_out] receives milliseconds per evaluation for:
  *   [0] quantisation, cell list and neighbour list,
  *   [1] species embedding (no work: h^0 and u^0 depend only on species and
  *       parameters and are built once per parameter upload),

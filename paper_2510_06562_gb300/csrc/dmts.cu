@@ -1838,6 +1838,11 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
     std::vector<cudaEvent_t> ev(2 * n_st);
     for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
     acc.assign(n_st, 0.0);
+    // stages without work (the embedding, built once per parameter upload, and
+    // the layer-0 per-atom adjoint) are not timed: they read 0
+    std::vector<char> timed(n_st, 1);
+    timed[1] = 0;
+    timed[2 + 3 * L] = 0;
     for (int r = 0; r < reps; ++r) {
         auto begin = [&](int slot) { cudaEventRecord(ev[2 * slot], s); };
         auto end = [&](int slot) { cudaEventRecord(ev[2 * slot + 1], s); };
@@ -1845,8 +1850,6 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
         enqueue_neighbors(c, which, true);
         end(0);
         PotArgs a = pot_args(c, m);
-        begin(1);                                  // the embedding is built once per parameter upload
-        end(1);
         for (int l = 0; l < L; ++l) {
             PotArgs f = fwd_args(c, a, m, l);
             begin(2 + l);
@@ -1861,15 +1864,18 @@ int time_stages_impl(dmts_ctx* c, int which, int reps, std::vector<double>& acc)
             begin(2 + 2 * L + l);
             launch_edge_bwd(c, m, b);
             end(2 + 2 * L + l);
-            begin(2 + 3 * L + l);
-            if (l > 0) launch_atom_bwd_m(c, m, b);
-            end(2 + 3 * L + l);
+            if (l > 0) {
+                begin(2 + 3 * L + l);
+                launch_atom_bwd_m(c, m, b);
+                end(2 + 3 * L + l);
+            }
         }
         begin(2 + 4 * L);
         launch_system_sum(c->n_sys, c->d_off, m.Ei, m.E, 1, m.esum, s);
         end(2 + 4 * L);
         CUDA_TRY(cudaEventSynchronize(ev[2 * n_st - 1]));
         for (int q = 0; q < n_st; ++q) {
+            if (!timed[q]) continue;
             float t = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]));
             acc[q] += t;

@@ -9,6 +9,7 @@
 * dmts_set_state keeps the cached forces when the positions are unchanged
   (Algorithm 1's first step is a restart at new positions only), and
   recomputes them when a position changed.
+* dmts_time_stages reads 0 for the stages that launch nothing.
 """
 import os
 import sys
@@ -101,3 +102,18 @@ def test_set_state_with_unchanged_positions_keeps_cached_forces():
         n0 = a.launch_count
         a.respa_step(1, 3.0, 3)
         assert a.launch_count - n0 > per_step
+
+
+@pytest.mark.parametrize("precision", [D.FP32, D.BF16_MLP])
+def test_stage_timing_reads_zero_for_stages_without_work(precision):
+    """dmts_time_stages: the species embedding (built at parameter upload)
+    and the layer-0 per-atom adjoint launch nothing and read 0; every other
+    stage of both models is timed (> 0)."""
+    s = I.water_192(0)
+    with _ctx(s, precision) as ctx:
+        ctx.set_state(s.x)
+        for which in (D.SMALL, D.BIG):
+            st = ctx.time_stages(which, reps=2)
+            assert st["embed"] == 0.0 and st["atom_bwd_l0"] == 0.0
+            others = {k: v for k, v in st.items() if k not in ("embed", "atom_bwd_l0")}
+            assert all(v > 0.0 for v in others.values()), others
