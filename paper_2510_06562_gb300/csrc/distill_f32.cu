@@ -17,7 +17,10 @@
 // theta: a tangent edge pass (m'), a per-atom adjoint pass (dPsi/dm,
 // dPsi/dm' and the per-atom weight gradients), and an edge pass for the
 // filter-weight gradients and dPsi/du. Every gradient is summed per CTA and
-// the CTA partials are added in a fixed order (deterministic).
+// the CTA partials are added in a fixed order (deterministic). In the BF16
+// mode the filter-weight gradient sums over pairs run on the tensor cores
+// (BF16 operands, FP32 accumulation in tensor memory); every other step, and
+// every step of the FP32 mode, is FP32 on the SIMT pipes.
 //
 // The energy term adds c_E dE/dtheta per frame, c_E = dL/dE = 2 lambda_E
 // (E - E_ref) / (M N^2): the same reverse pass seeded at the readout with
@@ -26,13 +29,20 @@
 // e0[Z_i] gain -c_E per atom.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
+#include "umma.cuh"
 
 namespace dmts {
 
 namespace {
 
+using namespace umma;
+
 constexpr int kT = 256;
+constexpr int kFmAtoms = 32;                 // atoms per CTA of the edge passes
+constexpr uint32_t kFmWait = 1u << 22;       // bounded mbarrier polls (tensor-core weight gradients)
 
 __device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + expf(-x)); }
 // SiLU, its first and second derivatives at a
@@ -121,8 +131,40 @@ struct EdgeSmem {
     float X[TE * (F + 4)], Y[TE * (F + 4)];   // per-edge rows (msg, phibar, gbar, abar, tbar)
     float fc[TE], dfc[TE], delta[TE];
     int j[TE], row[TE];
-    float acc[64 * F];                   // per-atom row sums of the CTA (A <= 64)
+    float acc[kFmAtoms * F];             // per-atom row sums of the CTA
 };
+
+// Tensor-core weight gradients of the filter MLP (BF16 mode). Per pair tile
+// the FP32 tiles SiLU(a)^T and (SiLU'(a) T)^T (the ST and PT region, 32 KB)
+// are rewritten in place as one BF16 A operand of 128 rows by TE = 128 pairs:
+// rows 0-31 SiLU(a)^T, 32-63 (SiLU'(a) T)^T, then e^T and e'^T (K rows each),
+// zero rows after. B holds [phibar | gbar], later [abar | tbar], as 64 rows
+// by the tile's pairs. Two accumulators in tensor memory sum over the CTA's
+// tiles, D1 += A B1^T and D2 += A B2^T (64 FP32 columns each), and
+//   dW2[k][f] = D1[k][f] + D1[32 + k][32 + f],
+//   dW1[k][f] = D2[64 + k][f] + D2[64 + K + k][32 + f];
+// the other blocks of D1 and D2 are products nobody reads. Operands are
+// K-major without swizzle (umma.cuh), the pairs being the reduction (K)
+// dimension.
+template <int F, int K>
+struct GradTc {
+    EdgeSmem<F, K> e;
+    alignas(128) unsigned char b[64 * Geo<F, K>::TE * 2];   // the B operand
+    uint64_t mbar;
+    uint32_t taddr;
+};
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Four consecutive pairs (k = e0 .. e0 + 3, e0 a multiple of 4) of operand
+// row r as BF16 (one 8-byte store).
+__device__ __forceinline__ void st_k4(unsigned char* tile, int r, int e0, int Kc, float v0, float v1, float v2,
+                                      float v3) {
+    *reinterpret_cast<uint2*>(tile + tile_offset(r, e0, Kc)) = make_uint2(bf16x2(v0, v1), bf16x2(v2, v3));
+}
 
 template <int F, int K>
 __device__ __forceinline__ void load_weights(EdgeSmem<F, K>& S, const PotArgs& a) {
@@ -424,15 +466,36 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
 //   abar = (phibar W2^T) SiLU'(a) + (gbar W2^T) T SiLU''(a),  tbar = (gbar W2^T) SiLU'(a),
 //   dW1 += e^T abar + e'^T tbar,  db1 += abar;
 // and ubar_i = sum_j w_ij * Mbar_j + w'_ij * Mdbar_j (row gather, w symmetric).
-template <int F, int K>
+// TC: the dW2 and dW1 contractions on the tensor cores (GradTc), BF16 operands
+// with FP32 accumulation; a bounded wait that gives up sets status bit 0.
+template <int F, int K, bool TC>
 __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __restrict__ g,
                                                       const float* __restrict__ mb, const float* __restrict__ mdb,
                                                       float* __restrict__ ubar, float* __restrict__ partial,
-                                                      int n_params) {
+                                                      int n_params, int* status) {
     using G = Geo<F, K>;
     constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
+    static_assert(!TC || (TE == 128 && F == 32 && 2 * K <= 64), "tensor-core operand shapes");
     extern __shared__ float4 sm4[];
-    EdgeSmem<F, K>& S = *reinterpret_cast<EdgeSmem<F, K>*>(sm4);
+    GradTc<F, K>& T = *reinterpret_cast<GradTc<F, K>*>(sm4);   // (FP32 path: only T.e exists)
+    EdgeSmem<F, K>& S = T.e;
+    unsigned char* const opA = reinterpret_cast<unsigned char*>(S.ST);   // the A operand over ST and PT
+    uint32_t phase = 0;
+    bool ok = true, any = false, pending = false;      // any: an MMA was issued; pending: one may run
+    const uint32_t idesc = idesc_bf16_f32(128, 64);
+    bool failed = false;                                // a wait gave up (its parity in fail_phase)
+    uint32_t fail_phase = 0;
+    auto wait_mma = [&]() {                             // all threads: the oldest commit not yet waited for
+        const bool done = mbar_wait(&T.mbar, phase, kFmWait);
+        if (!done && !failed) {
+            failed = true;
+            fail_phase = phase;
+        }
+        ok = ok && done;
+        phase ^= 1;
+        pending = false;
+        fence_after_sync();
+    };
     const int tid = threadIdx.x, A = a.atoms_per_cta;
     const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
     float* out = partial + (size_t)blockIdx.x * n_params;
@@ -450,6 +513,14 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
         load_weights(S, a);
         for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
     }
+    if constexpr (TC) {
+        if (tid == 0) mbar_init(&T.mbar, 1);
+        if (tid < 32) tmem_alloc(&T.taddr, 128);
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    }
+    const uint32_t tD1 = TC ? T.taddr : 0u, tD2 = tD1 + 64;
     const long long e_beg = nA > 0 ? min((long long)a.row_ptr[a0], a.e_cap) : 0;
     const long long e_end = nA > 0 ? min((long long)a.row_ptr[a1], a.e_cap) : 0;
     const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
@@ -458,6 +529,11 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
     __syncthreads();
     for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
         edge_setup(S, a, g, t0, e_end, a0);
+        if constexpr (TC) {                    // the previous tile's second MMA reads A and B
+            if (pending) {
+                wait_mma();
+            }
+        }
         __syncthreads();
         float sp[4][4], spp[4][4], tt[4][4];
         filter_hidden(S, e0, f0, sp, spp, tt);
@@ -490,6 +566,58 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(gb4[r][0], gb4[r][1], gb4[r][2], gb4[r][3]);
         }
         __syncthreads();
+        if constexpr (TC) {
+            // this thread's four 8-pair chunks of SiLU(a)^T | (SiLU'(a) T)^T, read
+            // before the region is rewritten as the A operand
+            float4 cv[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = tid + kT * i, r = c >> 4, k8 = (c & 15) * 8;
+                const float* src = (r < F ? S.ST + r * TE : S.PT + (r - F) * TE) + k8;
+                cv[i][0] = *reinterpret_cast<const float4*>(src);
+                cv[i][1] = *reinterpret_cast<const float4*>(src + 4);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = tid + kT * i, r = c >> 4, k8 = (c & 15) * 8;
+                *reinterpret_cast<uint4*>(opA + tile_offset(r, k8, TE)) =
+                    make_uint4(bf16x2(cv[i][0].x, cv[i][0].y), bf16x2(cv[i][0].z, cv[i][0].w),
+                               bf16x2(cv[i][1].x, cv[i][1].y), bf16x2(cv[i][1].z, cv[i][1].w));
+            }
+            // rows 64 ..: e^T, e'^T (K rows each), then zero rows
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = tid + kT * i, r = 64 + (c >> 4), k8 = (c & 15) * 8;
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (r < 64 + 2 * K) {
+                    const float* src = (r < 64 + K ? S.BT + (r - 64) * TE : S.DT + (r - 64 - K) * TE) + k8;
+                    const float4 x0 = *reinterpret_cast<const float4*>(src), x1 = *reinterpret_cast<const float4*>(src + 4);
+                    w = make_uint4(bf16x2(x0.x, x0.y), bf16x2(x0.z, x0.w), bf16x2(x1.x, x1.y), bf16x2(x1.z, x1.w));
+                }
+                *reinterpret_cast<uint4*>(opA + tile_offset(r, k8, TE)) = w;
+            }
+            // B1 = [phibar | gbar]: rows f and F + f, this thread's four pairs
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                st_k4(T.b, f0 + c, e0, TE, phb[0][c], phb[1][c], phb[2][c], phb[3][c]);
+                st_k4(T.b, F + f0 + c, e0, TE, gb4[0][c], gb4[1][c], gb4[2][c], gb4[3][c]);
+            }
+            fence_proxy_async();
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            fence_after_sync();
+            if (ok) {
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < TE / 16; ++kk)
+                        mma_bf16(tD1, make_desc(smem_u32(opA) + kk * 256, 128, TE * 16),
+                                 make_desc(smem_u32(T.b) + kk * 256, 128, TE * 16), idesc, any || kk > 0);
+                    mma_commit(&T.mbar);
+                }
+                pending = true;
+            }
+        }
         // abar, tbar: need phibar W2^T and gbar W2^T (rows of X, Y as A operand, transposed access)
         float sb[4][4], pb[4][4];
 #pragma unroll
@@ -516,7 +644,7 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             }
         // weight gradients of this tile: dW2 (ST, PT against X, Y), db2; then dW1 (BT, DT against abar, tbar), db1
 #pragma unroll
-        for (int qq = 0; qq < NW2; ++qq) {
+        for (int qq = 0; qq < (TC ? 0 : NW2); ++qq) {
             int idx = tid + qq * kT;
             int k = idx / F, f = idx % F;
             float s = 0.f;
@@ -536,9 +664,36 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(ab[r][0], ab[r][1], ab[r][2], ab[r][3]);
             *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(tb[r][0], tb[r][1], tb[r][2], tb[r][3]);
         }
-        __syncthreads();
+        if constexpr (TC) {
+            // B2 = [abar | tbar] over B1, once the first MMA has read it
+            if (pending) {
+                wait_mma();
+            }
 #pragma unroll
-        for (int qq = 0; qq < NW1; ++qq) {
+            for (int c = 0; c < 4; ++c) {
+                st_k4(T.b, f0 + c, e0, TE, ab[0][c], ab[1][c], ab[2][c], ab[3][c]);
+                st_k4(T.b, F + f0 + c, e0, TE, tb[0][c], tb[1][c], tb[2][c], tb[3][c]);
+            }
+            fence_proxy_async();
+            fence_before_sync();
+            ok = __syncthreads_and(ok);
+            fence_after_sync();
+            if (ok) {
+                if (tid == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < TE / 16; ++kk)
+                        mma_bf16(tD2, make_desc(smem_u32(opA) + kk * 256, 128, TE * 16),
+                                 make_desc(smem_u32(T.b) + kk * 256, 128, TE * 16), idesc, any || kk > 0);
+                    mma_commit(&T.mbar);
+                }
+                pending = true;
+                any = true;
+            }
+        } else {
+            __syncthreads();
+        }
+#pragma unroll
+        for (int qq = 0; qq < (TC ? 0 : NW1); ++qq) {
             int idx = tid + qq * kT;
             if (idx < K * F) {
                 int k = idx / F, f = idx % F;
@@ -577,11 +732,49 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
         for (int t = tid; t < nA * F; t += kT) ubar[(size_t)a0 * F + t] = S.acc[t];
     }
     // CTA partials of the filter weights
+    if constexpr (TC) {
+        if (pending) {                          // the last MMA
+            wait_mma();
+        }
+        ok = __syncthreads_and(ok);
+        float* st = S.X;                        // staging: D1 blocks, then D2 blocks
+        const int w = tid >> 5, lane = tid & 31;
+        if (ok && any && w < 3) {
+            float v[32];
+            if (w < 2) {                        // lanes 32 w + lane: rows k of SiLU(a)^T (w 0), of (SiLU'(a) T)^T (w 1)
+                const uint32_t col = w == 0 ? 0u : 32u;
+                tmem_ld16x2(tD1 + ((uint32_t)(32 * w) << 16) + col, v, tD1 + ((uint32_t)(32 * w) << 16) + col + 16,
+                            v + 16);
+                for (int f = 0; f < 32; ++f) st[(w * 32 + lane) * 32 + f] = v[f];
+            } else {                            // rows 64 + lane: e^T (lane < K, columns 0-31), e'^T (K <= lane < 2K, 32-63)
+                const uint32_t row = tD2 + (64u << 16);   // the address is warp-uniform: both column halves
+                tmem_ld16x2(row, v, row + 16, v + 16);
+                if (lane < K)
+                    for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
+                tmem_ld16x2(row + 32, v, row + 48, v + 16);
+                if (lane >= K && lane < 2 * K)
+                    for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < F * F; idx += kT)
+            out[a.off.W2[0] + idx] = (ok && any) ? st[idx] + st[1024 + idx] : 0.f;
+        for (int idx = tid; idx < K * F; idx += kT)
+            out[a.off.W1[0] + idx] = (ok && any) ? st[2048 + idx] + st[2048 + K * F + idx] : 0.f;
+        // after a wait that gave up, the MMAs in flight complete before their
+        // tensor memory is freed (status bit 1 if they do not, in time)
+        const bool drained = !failed || mbar_wait(&T.mbar, fail_phase, kFmWait);
+        fence_before_sync();
+        __syncthreads();
+        if (tid < 32) tmem_dealloc(T.taddr, 128);
+        if (!ok && tid == 0) atomicOr(status, drained ? 1 : 3);
+    } else {
 #pragma unroll
-    for (int qq = 0; qq < NW2; ++qq) out[a.off.W2[0] + tid + qq * kT] = gW2[qq];
+        for (int qq = 0; qq < NW2; ++qq) out[a.off.W2[0] + tid + qq * kT] = gW2[qq];
 #pragma unroll
-    for (int qq = 0; qq < NW1; ++qq)
-        if (tid + qq * kT < K * F) out[a.off.W1[0] + tid + qq * kT] = gW1[qq];
+        for (int qq = 0; qq < NW1; ++qq)
+            if (tid + qq * kT < K * F) out[a.off.W1[0] + tid + qq * kT] = gW1[qq];
+    }
     if (tid < F) out[a.off.b2[0] + tid] = gb;
     if (tid >= kT - F) out[a.off.b1[0] + tid - (kT - F)] = gb;
 }
@@ -704,19 +897,20 @@ void tangent_go(const PotArgs& a, const float* g, float* mdot, cudaStream_t s) {
     k_fm_tangent<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mdot);
 }
 
-template <int F, int K>
+template <int F, int K, bool TC>
 void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
-                  int n_params, cudaStream_t s) {
-    smem_opt_in((const void*)k_fm_grad_edge<F, K>, (int)edge_smem<F, K>());
+                  int n_params, int* status, cudaStream_t s) {
+    const size_t smem = TC ? sizeof(GradTc<F, K>) : edge_smem<F, K>();
+    smem_opt_in((const void*)k_fm_grad_edge<F, K, TC>, (int)smem);
     int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
-    k_fm_grad_edge<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mb, mdb, ubar, partial, n_params);
+    k_fm_grad_edge<F, K, TC><<<grid, kT, smem, s>>>(a, g, mb, mdb, ubar, partial, n_params, status);
 }
 
 }  // namespace
 
 bool fm_supported(int F, int K, int L) { return F == 32 && (K == 8 || K == 16) && L == 1; }
 
-int fm_atoms_per_cta() { return 32; }
+int fm_atoms_per_cta() { return kFmAtoms; }
 
 int fm_edge_ctas(int n_atoms) { return (n_atoms + fm_atoms_per_cta() - 1) / fm_atoms_per_cta(); }
 
@@ -729,7 +923,7 @@ int fm_atom_ctas(int n_atoms) { return std::max(1, std::min(152 * 2, (n_atoms + 
 void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
                      const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
                      float* partial_a, int n_params, double* grad, double* loss, const FmEnergy& en,
-                     cudaStream_t s) {
+                     bool tensor_cores, int* status, cudaStream_t s) {
     const int n = p.n_atoms;
     if (n == 0) return;
     k_fm_residual<<<(n + 255) / 256, 256, 0, s>>>(n, p.force, f_ref, c_loss, g, sq);
@@ -753,8 +947,13 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     fm_reduce(partial_a, ra, n_params, o.U1[0], o.c2[0] + F, grad, s);          // U1, c1, U2, c2
     fm_reduce(partial_a, ra, n_params, o.R1, o.e0 + S, grad, s);                // R1, d1, R2, d2, e0
     const int ge = fm_edge_ctas(n);
-    if (K == 8) grad_edge_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
-    else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
+    if (tensor_cores) {
+        if (K == 8) grad_edge_go<32, 8, true>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+        else grad_edge_go<32, 16, true>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+    } else {
+        if (K == 8) grad_edge_go<32, 8, false>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+        else grad_edge_go<32, 16, false>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+    }
     fm_reduce(partial_e, ge, n_params, o.W1[0], o.b2[0] + F, grad, s);          // W1, b1, W2, b2
     k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
     fm_reduce(partial_a, ra, n_params, o.A, o.A + S * F, grad, s);               // A

@@ -1721,7 +1721,8 @@ int distill_impl(dmts_ctx* c, int n_frames, const double* frames, const double* 
                 en.c_energy = c->fm_ce;
             }
             launch_fm_frame(a, m.K, c->fm_stage + n3, cl, c->fm_g, c->fm_sq, c->fm_m, c->fm_mdot, c->fm_mb,
-                            c->fm_mdb, c->fm_ubar, c->fm_pe, c->fm_pa, np, c->fm_grad, c->fm_loss, en, c->stream);
+                            c->fm_mdb, c->fm_ubar, c->fm_pe, c->fm_pa, np, c->fm_grad, c->fm_loss, en,
+                            m.precision == DMTS_BF16_MLP, c->d_flags + kFlagTimeout, c->stream);
         }
         if ((rc = sync_check(c))) return rc;
         if (!c->h_flags[kFlagOverflow]) break;

@@ -345,7 +345,10 @@ struct FmEnergy {
 void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss, float* g, double* sq,
                      const float* m, float* mdot, float* mbar_psi, float* mdotbar_psi, float* ubar, float* partial_e,
                      float* partial_a, int n_params, double* grad, double* loss, const FmEnergy& en,
-                     cudaStream_t s);
+                     bool tensor_cores, int* status, cudaStream_t s);
+// (tensor_cores: the filter-weight gradient sums over pairs on tcgen05 with
+// BF16 operands; a bounded wait that gives up sets bit 0 of *status, bit 1
+// as well if the tensor-core work in flight did not drain)
 
 // atom_mlp.cu: per-atom MLPs after the edge passes
 void launch_atom_fwd(const PotArgs& p, int F, const float* msg, cudaStream_t s);
