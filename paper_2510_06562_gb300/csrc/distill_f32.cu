@@ -132,6 +132,8 @@ struct EdgeSmem {
     float fc[TE], dfc[TE], delta[TE];
     int j[TE], row[TE];
     float acc[kFmAtoms * F];             // per-atom row sums of the CTA
+    float slot[kT / 32][2][F];           // per-warp open row segments of a tile (row_sums)
+    int slot_row[kT / 32][2];
 };
 
 // Tensor-core weight gradients of the filter MLP (BF16 mode). Per pair tile
@@ -245,21 +247,72 @@ __device__ __forceinline__ void filter_hidden(EdgeSmem<F, K>& S, int e0, int f0,
     store_tT<TE>(S.PT, f0, e0, p);
 }
 
-// Segmented row sums of X[e][f] into acc[row][f] (threads < F, edge order,
-// the open row carried across tiles in cur/run).
-template <int F, int TE>
-__device__ __forceinline__ void row_sums(const float* X, const int* srow, float* acc, int& cur, float& run) {
-    const int f = threadIdx.x;
-    if (f >= F) return;
-    for (int e = 0; e < TE; ++e) {
-        int r = srow[e];
+// Segmented row sums of X[e][f] into acc[row][f] (rows are contiguous runs
+// of the tile's pairs; pairs past the end have row -1). Warp w sums pairs
+// [w TE/8, (w + 1) TE/8) segment by segment, lane f feature f; a segment that
+// starts and ends inside the warp's range is a whole row and is stored
+// directly, the range's first and last segments go to two slots. Threads < F
+// then merge the slots in pair order, the open row carried across tiles in
+// cur/run. Every row's sum is fixed by the tile boundaries (deterministic).
+// All threads take part (one barrier inside); a barrier after the call must
+// come before the slots, X or the rows are written again.
+template <int F, int TE, int K>
+__device__ __forceinline__ void row_sums(EdgeSmem<F, K>& S, const float* X, int& cur, float& run) {
+    static_assert(F == 32, "lane = feature");
+    constexpr int NW = kT / 32, EW = TE / NW;
+    const int w = threadIdx.x >> 5, f = threadIdx.x & 31;
+    int r0 = -1, nseg = 0;
+    float sum = 0.f;
+    int row_first = -1, row_last = -1;
+    float v_first = 0.f, v_last = 0.f;
+    for (int e = w * EW; e < (w + 1) * EW; ++e) {
+        const int r = S.row[e];
         if (r < 0) break;
-        if (r != cur) {
-            if (cur >= 0) acc[cur * F + f] = run;
-            cur = r;
-            run = 0.f;
+        if (r != r0) {
+            if (r0 >= 0) {
+                if (nseg == 0) {
+                    row_first = r0;
+                    v_first = sum;
+                } else {
+                    S.acc[r0 * F + f] = sum;
+                }
+                ++nseg;
+            }
+            r0 = r;
+            sum = 0.f;
         }
-        run += X[e * (F + 4) + f];
+        sum += X[e * (F + 4) + f];
+    }
+    if (r0 >= 0) {
+        if (nseg == 0) {
+            row_first = r0;
+            v_first = sum;
+        } else {
+            row_last = r0;
+            v_last = sum;
+        }
+    }
+    S.slot[w][0][f] = v_first;
+    S.slot[w][1][f] = v_last;
+    if (f == 0) {
+        S.slot_row[w][0] = row_first;
+        S.slot_row[w][1] = row_last;
+    }
+    __syncthreads();
+    if (threadIdx.x < F) {
+#pragma unroll
+        for (int k = 0; k < 2 * NW; ++k) {
+            const int r = S.slot_row[k >> 1][k & 1];
+            if (r < 0) continue;
+            const float v = S.slot[k >> 1][k & 1][f];
+            if (r == cur) {
+                run += v;
+            } else {
+                if (cur >= 0) S.acc[cur * F + f] = run;
+                cur = r;
+                run = v;
+            }
+        }
     }
 }
 
@@ -306,7 +359,7 @@ __global__ void __launch_bounds__(kT) k_fm_tangent(PotArgs a, const float* __res
             *reinterpret_cast<float4*>(S.X + e * PS + f0) = o;
         }
         __syncthreads();
-        row_sums<F, TE>(S.X, S.row, S.acc, cur, run);
+        row_sums<F, TE, K>(S, S.X, cur, run);
         __syncthreads();
     }
     if (tid < F && cur >= 0) S.acc[cur * F + tid] = run;
@@ -723,7 +776,7 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(o[0], o[1], o[2], o[3]);
         }
         __syncthreads();
-        row_sums<F, TE>(S.X, S.row, S.acc, cur, run);
+        row_sums<F, TE, K>(S, S.X, cur, run);
         __syncthreads();
     }
     if (nA > 0) {

@@ -90,6 +90,35 @@ def test_distill_gradient_bf16_mode_matches_oracle():
     assert np.sqrt(np.mean((F - Fr) ** 2)) <= 5e-3
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_distill_gradient_with_sixteen_radial_functions(precision):
+    """The distillation kernels built for 16 radial functions (the other
+    size they take; 8 above), with the bounds of the tests above: FP32 entry
+    by entry, BF16 through the loss, the norm and the largest entry."""
+    s = I.water_192(0)
+    sa = I.Arch(cutoff=3.5, n_radial=16, n_layers=1, n_feat=32, n_species=2)
+    sp = I.init_params(sa, 4)
+    ba = I.big_arch(2)
+    bp = I.init_params(ba, 3)
+    frames, f_ref, e_ref = _labelled_frames(s, ba, bp, 2, 11)
+    L_ref, g_ref = M.distill_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, 1.0)
+    prec = D.FP32 if precision == "fp32" else D.BF16_MLP
+    with D.Context(s, ba, bp, sa, sp, precision=prec) as ctx:
+        ctx.set_state(s.x)
+        L, g = ctx.distill_grad(frames, f_ref, e_ref, 1.0)
+    err = np.abs(g - g_ref)
+    rel = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    print(json.dumps({"precision": precision, "loss": L, "loss_ref": L_ref, "grad_rel_l2": rel,
+                      "grad_max_abs_err": float(err.max()), "grad_max_abs": float(np.abs(g_ref).max())}))
+    if precision == "fp32":
+        assert abs(L - L_ref) <= 1e-5 * L_ref
+        assert np.all(err <= 1e-6 * np.abs(g_ref).max() + 1e-9), (int(err.argmax()), float(err.max()))
+    else:
+        assert abs(L - L_ref) <= 5e-3 * L_ref
+        assert rel <= 2e-2
+        assert err.max() <= 2e-2 * np.abs(g_ref).max()
+
+
 def test_distill_without_energy_term_is_force_matching():
     s = I.water_192(0)
     sa, sp, ba, bp = _models()
