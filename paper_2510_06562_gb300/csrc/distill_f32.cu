@@ -136,22 +136,54 @@ struct EdgeSmem {
     int slot_row[kT / 32][2];
 };
 
-// Tensor-core weight gradients of the filter MLP (BF16 mode). Per pair tile
-// the FP32 tiles SiLU(a)^T and (SiLU'(a) T)^T (the ST and PT region, 32 KB)
-// are rewritten in place as one BF16 A operand of 128 rows by TE = 128 pairs:
-// rows 0-31 SiLU(a)^T, 32-63 (SiLU'(a) T)^T, then e^T and e'^T (K rows each),
-// zero rows after. B holds [phibar | gbar], later [abar | tbar], as 64 rows
-// by the tile's pairs. Two accumulators in tensor memory sum over the CTA's
-// tiles, D1 += A B1^T and D2 += A B2^T (64 FP32 columns each), and
+// ---------------------------------------------------------------- tensor-core operands (BF16 mode)
+// In the BF16 mode the per-pair MLP products of both edge passes and the
+// filter-weight gradient sums over pairs run on tcgen05: BF16 operands
+// (K-major, no swizzle, umma.cuh), FP32 accumulators in tensor memory, the
+// rest FP32 as in the passes above. A tile's TE = 128 pairs are the 128
+// lanes of tensor memory (pair e in lane e). Per tile:
+//   MMA1  [a - b1 | T]   = [e | e'] W1                    (N = F each, K = 16: e padded)
+//   MMA2  [phi - b2 | q] = [SiLU(a) | SiLU'(a) T] W2      (K = F)
+//   MMA3  [sb | pb]      = [phibar | gbar] W2^T            (gradient pass)
+// and the weight gradients, summed over the CTA's tiles: an A operand of 128
+// rows by the tile's pairs (the ST and PT region, 32 KB) holds SiLU(a)^T
+// (rows 0-31), (SiLU'(a) T)^T (32-63), e^T and e'^T (K rows each) and zero
+// rows; B holds [phibar | gbar], later [abar | tbar], as 64 rows by the
+// pairs; D1 += A B1^T, D2 += A B2^T (64 FP32 columns each), and
 //   dW2[k][f] = D1[k][f] + D1[32 + k][32 + f],
-//   dW1[k][f] = D2[64 + k][f] + D2[64 + K + k][32 + f];
-// the other blocks of D1 and D2 are products nobody reads. Operands are
-// K-major without swizzle (umma.cuh), the pairs being the reduction (K)
-// dimension.
+//   dW1[k][f] = D2[64 + k][f] + D2[64 + K + k][32 + f]
+// (the other blocks of D1 and D2 are products nobody reads). Accumulator
+// pairs are read back by all eight warps into FP32 rows [TE][F + 4], which
+// the 4 x 4 thread blocks of the passes read as before.
+constexpr int kKb = 16;                      // basis columns of the MMA1 operands (one K step)
+
+template <int F>
+struct TcWeights {
+    unsigned char w1t[F * kKb * 2];          // B[n][k] = W1[k][n] (zero for k >= K)
+    unsigned char w2t[F * F * 2];            // B[n][k] = W2[k][n]
+    unsigned char w2n[F * F * 2];            // B[n][k] = W2[n][k]
+};
+
+// Tangent pass: the MMA1 and MMA2 operands sit in the ST and PT region,
+// which this pass does not otherwise use.
+template <int F, int K>
+struct TangTc {
+    EdgeSmem<F, K> e;
+    TcWeights<F> w;
+    uint64_t mbar;
+    uint32_t taddr;
+};
+
 template <int F, int K>
 struct GradTc {
-    EdgeSmem<F, K> e;
-    alignas(128) unsigned char b[64 * Geo<F, K>::TE * 2];   // the B operand
+    static constexpr int TE = Geo<F, K>::TE;
+    EdgeSmem<F, K> e;                        // ST and PT: the weight-gradient A operand
+    TcWeights<F> w;
+    unsigned char a1[2][TE * kKb * 2];       // e | e' (pair rows)
+    unsigned char a2[2][TE * F * 2];         // SiLU(a) | SiLU'(a) T
+    unsigned char a3[2][TE * F * 2];         // phibar | gbar
+    unsigned char b[64 * TE * 2];            // weight-gradient B operand
+    float Z[2][TE * (F + 4)];                // MMA2 and MMA3 results as FP32 rows
     uint64_t mbar;
     uint32_t taddr;
 };
@@ -182,10 +214,12 @@ __device__ __forceinline__ void load_weights(EdgeSmem<F, K>& S, const PotArgs& a
     }
 }
 
-// Per-edge setup (threads < TE): geometry, basis, delta = rhat . (g_j - g_i).
+// Per-edge setup (threads < TE): geometry, basis, delta = rhat . (g_j - g_i);
+// a1 (tensor-core passes, else null): e and e' also as the BF16 pair rows of
+// the MMA1 operands (16 columns, zero past K).
 template <int F, int K>
 __device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, const float* __restrict__ g,
-                                           long long t0, long long e_end, int a0) {
+                                           long long t0, long long e_end, int a0, unsigned char* a1 = nullptr) {
     constexpr int TE = Geo<F, K>::TE;
     const int tid = threadIdx.x;
     if (tid >= TE) return;
@@ -219,6 +253,23 @@ __device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, 
     for (int k = 0; k < K; ++k) {
         S.BT[k * TE + tid] = eb[k];
         S.DT[k * TE + tid] = db[k];
+    }
+    if (a1) {
+        static_assert(K <= kKb && K % 8 == 0, "whole 8-column chunks of the basis");
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) =
+                make_uint4(bf16x2(eb[k0], eb[k0 + 1]), bf16x2(eb[k0 + 2], eb[k0 + 3]),
+                           bf16x2(eb[k0 + 4], eb[k0 + 5]), bf16x2(eb[k0 + 6], eb[k0 + 7]));
+            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) =
+                make_uint4(bf16x2(db[k0], db[k0 + 1]), bf16x2(db[k0 + 2], db[k0 + 3]),
+                           bf16x2(db[k0 + 4], db[k0 + 5]), bf16x2(db[k0 + 6], db[k0 + 7]));
+        }
+#pragma unroll
+        for (int k0 = K; k0 < kKb; k0 += 8) {
+            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
@@ -519,36 +570,15 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
 //   abar = (phibar W2^T) SiLU'(a) + (gbar W2^T) T SiLU''(a),  tbar = (gbar W2^T) SiLU'(a),
 //   dW1 += e^T abar + e'^T tbar,  db1 += abar;
 // and ubar_i = sum_j w_ij * Mbar_j + w'_ij * Mdbar_j (row gather, w symmetric).
-// TC: the dW2 and dW1 contractions on the tensor cores (GradTc), BF16 operands
-// with FP32 accumulation; a bounded wait that gives up sets status bit 0.
-template <int F, int K, bool TC>
+template <int F, int K>
 __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __restrict__ g,
                                                       const float* __restrict__ mb, const float* __restrict__ mdb,
                                                       float* __restrict__ ubar, float* __restrict__ partial,
-                                                      int n_params, int* status) {
+                                                      int n_params) {
     using G = Geo<F, K>;
     constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
-    static_assert(!TC || (TE == 128 && F == 32 && 2 * K <= 64), "tensor-core operand shapes");
     extern __shared__ float4 sm4[];
-    GradTc<F, K>& T = *reinterpret_cast<GradTc<F, K>*>(sm4);   // (FP32 path: only T.e exists)
-    EdgeSmem<F, K>& S = T.e;
-    unsigned char* const opA = reinterpret_cast<unsigned char*>(S.ST);   // the A operand over ST and PT
-    uint32_t phase = 0;
-    bool ok = true, any = false, pending = false;      // any: an MMA was issued; pending: one may run
-    const uint32_t idesc = idesc_bf16_f32(128, 64);
-    bool failed = false;                                // a wait gave up (its parity in fail_phase)
-    uint32_t fail_phase = 0;
-    auto wait_mma = [&]() {                             // all threads: the oldest commit not yet waited for
-        const bool done = mbar_wait(&T.mbar, phase, kFmWait);
-        if (!done && !failed) {
-            failed = true;
-            fail_phase = phase;
-        }
-        ok = ok && done;
-        phase ^= 1;
-        pending = false;
-        fence_after_sync();
-    };
+    EdgeSmem<F, K>& S = *reinterpret_cast<EdgeSmem<F, K>*>(sm4);
     const int tid = threadIdx.x, A = a.atoms_per_cta;
     const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
     float* out = partial + (size_t)blockIdx.x * n_params;
@@ -566,14 +596,6 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
         load_weights(S, a);
         for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
     }
-    if constexpr (TC) {
-        if (tid == 0) mbar_init(&T.mbar, 1);
-        if (tid < 32) tmem_alloc(&T.taddr, 128);
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-    }
-    const uint32_t tD1 = TC ? T.taddr : 0u, tD2 = tD1 + 64;
     const long long e_beg = nA > 0 ? min((long long)a.row_ptr[a0], a.e_cap) : 0;
     const long long e_end = nA > 0 ? min((long long)a.row_ptr[a1], a.e_cap) : 0;
     const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
@@ -582,11 +604,6 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
     __syncthreads();
     for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
         edge_setup(S, a, g, t0, e_end, a0);
-        if constexpr (TC) {                    // the previous tile's second MMA reads A and B
-            if (pending) {
-                wait_mma();
-            }
-        }
         __syncthreads();
         float sp[4][4], spp[4][4], tt[4][4];
         filter_hidden(S, e0, f0, sp, spp, tt);
@@ -619,58 +636,6 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(gb4[r][0], gb4[r][1], gb4[r][2], gb4[r][3]);
         }
         __syncthreads();
-        if constexpr (TC) {
-            // this thread's four 8-pair chunks of SiLU(a)^T | (SiLU'(a) T)^T, read
-            // before the region is rewritten as the A operand
-            float4 cv[4][2];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = tid + kT * i, r = c >> 4, k8 = (c & 15) * 8;
-                const float* src = (r < F ? S.ST + r * TE : S.PT + (r - F) * TE) + k8;
-                cv[i][0] = *reinterpret_cast<const float4*>(src);
-                cv[i][1] = *reinterpret_cast<const float4*>(src + 4);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = tid + kT * i, r = c >> 4, k8 = (c & 15) * 8;
-                *reinterpret_cast<uint4*>(opA + tile_offset(r, k8, TE)) =
-                    make_uint4(bf16x2(cv[i][0].x, cv[i][0].y), bf16x2(cv[i][0].z, cv[i][0].w),
-                               bf16x2(cv[i][1].x, cv[i][1].y), bf16x2(cv[i][1].z, cv[i][1].w));
-            }
-            // rows 64 ..: e^T, e'^T (K rows each), then zero rows
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = tid + kT * i, r = 64 + (c >> 4), k8 = (c & 15) * 8;
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if (r < 64 + 2 * K) {
-                    const float* src = (r < 64 + K ? S.BT + (r - 64) * TE : S.DT + (r - 64 - K) * TE) + k8;
-                    const float4 x0 = *reinterpret_cast<const float4*>(src), x1 = *reinterpret_cast<const float4*>(src + 4);
-                    w = make_uint4(bf16x2(x0.x, x0.y), bf16x2(x0.z, x0.w), bf16x2(x1.x, x1.y), bf16x2(x1.z, x1.w));
-                }
-                *reinterpret_cast<uint4*>(opA + tile_offset(r, k8, TE)) = w;
-            }
-            // B1 = [phibar | gbar]: rows f and F + f, this thread's four pairs
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                st_k4(T.b, f0 + c, e0, TE, phb[0][c], phb[1][c], phb[2][c], phb[3][c]);
-                st_k4(T.b, F + f0 + c, e0, TE, gb4[0][c], gb4[1][c], gb4[2][c], gb4[3][c]);
-            }
-            fence_proxy_async();
-            fence_before_sync();
-            ok = __syncthreads_and(ok);
-            fence_after_sync();
-            if (ok) {
-                if (tid == 0) {
-#pragma unroll
-                    for (int kk = 0; kk < TE / 16; ++kk)
-                        mma_bf16(tD1, make_desc(smem_u32(opA) + kk * 256, 128, TE * 16),
-                                 make_desc(smem_u32(T.b) + kk * 256, 128, TE * 16), idesc, any || kk > 0);
-                    mma_commit(&T.mbar);
-                }
-                pending = true;
-            }
-        }
         // abar, tbar: need phibar W2^T and gbar W2^T (rows of X, Y as A operand, transposed access)
         float sb[4][4], pb[4][4];
 #pragma unroll
@@ -697,7 +662,7 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             }
         // weight gradients of this tile: dW2 (ST, PT against X, Y), db2; then dW1 (BT, DT against abar, tbar), db1
 #pragma unroll
-        for (int qq = 0; qq < (TC ? 0 : NW2); ++qq) {
+        for (int qq = 0; qq < NW2; ++qq) {
             int idx = tid + qq * kT;
             int k = idx / F, f = idx % F;
             float s = 0.f;
@@ -717,36 +682,9 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
             *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(ab[r][0], ab[r][1], ab[r][2], ab[r][3]);
             *reinterpret_cast<float4*>(S.Y + e * PS + f0) = make_float4(tb[r][0], tb[r][1], tb[r][2], tb[r][3]);
         }
-        if constexpr (TC) {
-            // B2 = [abar | tbar] over B1, once the first MMA has read it
-            if (pending) {
-                wait_mma();
-            }
+        __syncthreads();
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                st_k4(T.b, f0 + c, e0, TE, ab[0][c], ab[1][c], ab[2][c], ab[3][c]);
-                st_k4(T.b, F + f0 + c, e0, TE, tb[0][c], tb[1][c], tb[2][c], tb[3][c]);
-            }
-            fence_proxy_async();
-            fence_before_sync();
-            ok = __syncthreads_and(ok);
-            fence_after_sync();
-            if (ok) {
-                if (tid == 0) {
-#pragma unroll
-                    for (int kk = 0; kk < TE / 16; ++kk)
-                        mma_bf16(tD2, make_desc(smem_u32(opA) + kk * 256, 128, TE * 16),
-                                 make_desc(smem_u32(T.b) + kk * 256, 128, TE * 16), idesc, any || kk > 0);
-                    mma_commit(&T.mbar);
-                }
-                pending = true;
-                any = true;
-            }
-        } else {
-            __syncthreads();
-        }
-#pragma unroll
-        for (int qq = 0; qq < (TC ? 0 : NW1); ++qq) {
+        for (int qq = 0; qq < NW1; ++qq) {
             int idx = tid + qq * kT;
             if (idx < K * F) {
                 int k = idx / F, f = idx % F;
@@ -785,51 +723,433 @@ __global__ void __launch_bounds__(kT) k_fm_grad_edge(PotArgs a, const float* __r
         for (int t = tid; t < nA * F; t += kT) ubar[(size_t)a0 * F + t] = S.acc[t];
     }
     // CTA partials of the filter weights
-    if constexpr (TC) {
-        if (pending) {                          // the last MMA
-            wait_mma();
-        }
-        ok = __syncthreads_and(ok);
-        float* st = S.X;                        // staging: D1 blocks, then D2 blocks
-        const int w = tid >> 5, lane = tid & 31;
-        if (ok && any && w < 3) {
-            float v[32];
-            if (w < 2) {                        // lanes 32 w + lane: rows k of SiLU(a)^T (w 0), of (SiLU'(a) T)^T (w 1)
-                const uint32_t col = w == 0 ? 0u : 32u;
-                tmem_ld16x2(tD1 + ((uint32_t)(32 * w) << 16) + col, v, tD1 + ((uint32_t)(32 * w) << 16) + col + 16,
-                            v + 16);
-                for (int f = 0; f < 32; ++f) st[(w * 32 + lane) * 32 + f] = v[f];
-            } else {                            // rows 64 + lane: e^T (lane < K, columns 0-31), e'^T (K <= lane < 2K, 32-63)
-                const uint32_t row = tD2 + (64u << 16);   // the address is warp-uniform: both column halves
-                tmem_ld16x2(row, v, row + 16, v + 16);
-                if (lane < K)
-                    for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
-                tmem_ld16x2(row + 32, v, row + 48, v + 16);
-                if (lane >= K && lane < 2 * K)
-                    for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
-            }
-        }
-        __syncthreads();
-        for (int idx = tid; idx < F * F; idx += kT)
-            out[a.off.W2[0] + idx] = (ok && any) ? st[idx] + st[1024 + idx] : 0.f;
-        for (int idx = tid; idx < K * F; idx += kT)
-            out[a.off.W1[0] + idx] = (ok && any) ? st[2048 + idx] + st[2048 + K * F + idx] : 0.f;
-        // after a wait that gave up, the MMAs in flight complete before their
-        // tensor memory is freed (status bit 1 if they do not, in time)
-        const bool drained = !failed || mbar_wait(&T.mbar, fail_phase, kFmWait);
-        fence_before_sync();
-        __syncthreads();
-        if (tid < 32) tmem_dealloc(T.taddr, 128);
-        if (!ok && tid == 0) atomicOr(status, drained ? 1 : 3);
-    } else {
 #pragma unroll
-        for (int qq = 0; qq < NW2; ++qq) out[a.off.W2[0] + tid + qq * kT] = gW2[qq];
+    for (int qq = 0; qq < NW2; ++qq) out[a.off.W2[0] + tid + qq * kT] = gW2[qq];
 #pragma unroll
-        for (int qq = 0; qq < NW1; ++qq)
-            if (tid + qq * kT < K * F) out[a.off.W1[0] + tid + qq * kT] = gW1[qq];
-    }
+    for (int qq = 0; qq < NW1; ++qq)
+        if (tid + qq * kT < K * F) out[a.off.W1[0] + tid + qq * kT] = gW1[qq];
     if (tid < F) out[a.off.b2[0] + tid] = gb;
     if (tid >= kT - F) out[a.off.b1[0] + tid - (kT - F)] = gb;
+}
+
+// ------------------------------------------------------------ tensor-core edge passes (BF16 mode)
+// The BF16 weight operands from the FP32 weights in shared memory.
+template <int F, int K>
+__device__ __forceinline__ void build_tc_weights(const EdgeSmem<F, K>& S, TcWeights<F>& W) {
+    for (int t = threadIdx.x; t < F * kKb; t += kT) {
+        const int n = t / kKb, k = t % kKb;
+        *reinterpret_cast<__nv_bfloat16*>(W.w1t + tile_offset(n, k, kKb)) =
+            __float2bfloat16_rn(k < K ? S.W1[k * F + n] : 0.f);
+    }
+    for (int t = threadIdx.x; t < F * F; t += kT) {
+        const int n = t / F, k = t % F;
+        *reinterpret_cast<__nv_bfloat16*>(W.w2t + tile_offset(n, k, F)) = __float2bfloat16_rn(S.W2[k * F + n]);
+        *reinterpret_cast<__nv_bfloat16*>(W.w2n + tile_offset(n, k, F)) = __float2bfloat16_rn(S.W2[n * F + k]);
+    }
+}
+
+// Two 32-column FP32 accumulators of the tile (tensor-memory columns t ..
+// t + 31 and t + 32 .. t + 63, lane = pair) into rows d0[e][.], d1[e][.]
+// (stride F + 4): warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31 of the
+// accumulator w / 4.
+template <int F>
+__device__ __forceinline__ void tmem_rows(uint32_t t, float* d0, float* d1) {
+    static_assert(F == 32 && kT == 256, "eight warps, one 32-column half each");
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, qd = w & 3, h = w >> 2;
+    const uint32_t ta = t + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * h);
+    float v[32];
+    tmem_ld16x2(ta, v, ta + 16, v + 16);
+    float* dst = (h ? d1 : d0) + (32 * qd + lane) * (F + 4);
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+}
+
+// Bounded completion waits on the CTA's MMA barrier (all threads): the
+// parity of the oldest commit not yet waited for; a wait that gives up clears
+// ok and records its parity, so that the MMAs in flight can be drained
+// before the tensor memory is freed.
+struct MmaWaits {
+    uint32_t phase = 0, fail_phase = 0;
+    bool ok = true, failed = false;
+    __device__ __forceinline__ void wait(uint64_t* mbar) {
+        const bool done = mbar_wait(mbar, phase, kFmWait);
+        if (!done && !failed) {
+            failed = true;
+            fail_phase = phase;
+        }
+        ok = ok && done;
+        phase ^= 1;
+        fence_after_sync();
+    }
+    // end of the kernel: drain, then bit 0 (a wait gave up) and bit 1 (its MMAs did not drain) of *status
+    __device__ __forceinline__ void finish(uint64_t* mbar, uint32_t taddr, uint32_t ncols, int* status) {
+        const bool drained = !failed || mbar_wait(mbar, fail_phase, kFmWait);
+        fence_before_sync();
+        ok = __syncthreads_and(ok);
+        if (threadIdx.x < 32) tmem_dealloc(taddr, ncols);
+        if (!ok && threadIdx.x == 0) atomicOr(status, drained ? 1 : 3);
+    }
+};
+
+// Barrier that also makes the operands written by this CTA's threads visible
+// to the tensor cores; returns the AND of ok over the CTA.
+__device__ __forceinline__ bool operands_ready(bool ok) {
+    fence_proxy_async();
+    fence_before_sync();
+    ok = __syncthreads_and(ok);
+    fence_after_sync();
+    return ok;
+}
+
+// m' by the tensor cores (k_fm_tangent with MMA1 and MMA2; see above).
+template <int F, int K>
+__global__ void __launch_bounds__(kT) k_fm_tangent_tc(PotArgs a, const float* __restrict__ g, float* __restrict__ mdot,
+                                                       int* status) {
+    using G = Geo<F, K>;
+    constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
+    static_assert(TE == 128 && F == 32, "one pair per tensor-memory lane");
+    extern __shared__ float4 sm4[];
+    TangTc<F, K>& T = *reinterpret_cast<TangTc<F, K>*>(sm4);
+    EdgeSmem<F, K>& S = T.e;
+    unsigned char* const a2 = reinterpret_cast<unsigned char*>(S.ST);   // SiLU(a) | SiLU'(a) T, 16 KB
+    unsigned char* const a1 = reinterpret_cast<unsigned char*>(S.PT);   // e | e', 8 KB
+    const int tid = threadIdx.x, A = a.atoms_per_cta;
+    const int a0 = blockIdx.x * A, a1_ = min(a.n_atoms, a0 + A), nA = a1_ - a0;
+    if (nA <= 0) return;
+    load_weights(S, a);
+    for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
+    __syncthreads();
+    build_tc_weights(S, T.w);
+    if (tid == 0) mbar_init(&T.mbar, 1);
+    if (tid < 32) tmem_alloc(&T.taddr, 64);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tXY = T.taddr, idesc = idesc_bf16_f32(128, F);
+    const uint32_t sA1 = smem_u32(a1), sA2 = smem_u32(a2);
+    const uint32_t sW1 = smem_u32(T.w.w1t), sW2 = smem_u32(T.w.w2t);
+    MmaWaits mw;
+    const long long e_beg = min((long long)a.row_ptr[a0], a.e_cap), e_end = min((long long)a.row_ptr[a1_], a.e_cap);
+    const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
+    int cur = -1;
+    float run = 0.f;
+    for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
+        edge_setup(S, a, g, t0, e_end, a0, a1);
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {
+            if (tid == 0) {
+                mma_bf16(tXY, make_desc(sA1, 128, kKb * 16), make_desc(sW1, 128, kKb * 16), idesc, 0);
+                mma_bf16(tXY + F, make_desc(sA1 + TE * kKb * 2, 128, kKb * 16), make_desc(sW1, 128, kKb * 16), idesc, 0);
+                mma_commit(&T.mbar);
+            }
+            mw.wait(&T.mbar);
+        }
+        tmem_rows<F>(tXY, S.X, S.Y);                     // a - b1 | T
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float sv[4], pv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float sp, spp;
+                silu3(S.X[(e0 + r) * PS + f0 + c] + S.b1[f0 + c], sv[c], sp, spp);
+                pv[c] = sp * S.Y[(e0 + r) * PS + f0 + c];
+            }
+            st_k4(a2, e0 + r, f0, F, sv[0], sv[1], sv[2], sv[3]);
+            st_k4(a2 + TE * F * 2, e0 + r, f0, F, pv[0], pv[1], pv[2], pv[3]);
+        }
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {
+            if (tid == 0) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16(tXY, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2 + kk * 256, 128, F * 16), idesc,
+                             kk > 0);
+                    mma_bf16(tXY + F, make_desc(sA2 + TE * F * 2 + kk * 256, 128, F * 16),
+                             make_desc(sW2 + kk * 256, 128, F * 16), idesc, kk > 0);
+                }
+                mma_commit(&T.mbar);
+            }
+            mw.wait(&T.mbar);
+        }
+        tmem_rows<F>(tXY, S.X, S.Y);                     // phi - b2 | q
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {                     // the message over this thread's own block of X
+            const int e = e0 + r;
+            const float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+            const float* uj = a.u + (size_t)S.j[e] * F + f0;
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float phi = S.X[e * PS + f0 + c] + S.b2[f0 + c], q = S.Y[e * PS + f0 + c];
+                o[c] = dl * (dfc * phi + fc * q) * uj[c];
+            }
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncthreads();
+        row_sums<F, TE, K>(S, S.X, cur, run);
+        __syncthreads();
+    }
+    if (tid < F && cur >= 0) S.acc[cur * F + tid] = run;
+    __syncthreads();
+    for (int t = tid; t < nA * F; t += kT) mdot[(size_t)a0 * F + t] = S.acc[t];
+    mw.finish(&T.mbar, T.taddr, 64, status);
+}
+
+// Filter-weight gradients and ubar by the tensor cores (k_fm_grad_edge with
+// MMA1-3 and the weight-gradient products; see above).
+template <int F, int K>
+__global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const float* __restrict__ g,
+                                                         const float* __restrict__ mb, const float* __restrict__ mdb,
+                                                         float* __restrict__ ubar, float* __restrict__ partial,
+                                                         int n_params, int* status) {
+    using G = Geo<F, K>;
+    constexpr int TE = G::TE, FG = G::FG, PS = F + 4;
+    static_assert(TE == 128 && F == 32 && 2 * K <= 64, "tensor-core operand shapes");
+    extern __shared__ float4 sm4[];
+    GradTc<F, K>& T = *reinterpret_cast<GradTc<F, K>*>(sm4);
+    EdgeSmem<F, K>& S = T.e;
+    unsigned char* const opA = reinterpret_cast<unsigned char*>(S.ST);   // weight-gradient A operand (ST and PT)
+    const int tid = threadIdx.x, A = a.atoms_per_cta;
+    const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
+    float* out = partial + (size_t)blockIdx.x * n_params;
+    float gb = 0.f;                      // one bias entry (db2: tid < F, db1: the last F threads)
+    if (nA > 0) {
+        load_weights(S, a);
+        for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
+    }
+    __syncthreads();
+    if (nA > 0) build_tc_weights(S, T.w);
+    if (tid == 0) mbar_init(&T.mbar, 1);
+    if (tid < 32) tmem_alloc(&T.taddr, 256);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    // tensor memory: MMA1-3 results in columns [0, 64), D1 in [64, 128), D2 in [128, 192)
+    const uint32_t tXY = T.taddr, tD1 = tXY + 64, tD2 = tXY + 128;
+    const uint32_t idesc = idesc_bf16_f32(128, F), idesc_w = idesc_bf16_f32(128, 64);
+    const uint32_t sA1 = smem_u32(T.a1), sA2 = smem_u32(T.a2), sA3 = smem_u32(T.a3), sB = smem_u32(T.b);
+    const uint32_t sOA = smem_u32(opA);
+    const uint32_t sW1 = smem_u32(T.w.w1t), sW2T = smem_u32(T.w.w2t), sW2N = smem_u32(T.w.w2n);
+    MmaWaits mw;
+    bool any = false, pending = false;   // a weight-gradient MMA was issued; the last commit is not yet waited for
+    const long long e_beg = nA > 0 ? min((long long)a.row_ptr[a0], a.e_cap) : 0;
+    const long long e_end = nA > 0 ? min((long long)a.row_ptr[a1], a.e_cap) : 0;
+    const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
+    int cur = -1;
+    float run = 0.f;
+    for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
+        edge_setup(S, a, g, t0, e_end, a0, &T.a1[0][0]);
+        if (pending) {                                   // the previous tile's D2 product reads A and B
+            mw.wait(&T.mbar);
+            pending = false;
+        }
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {                                     // MMA1: a - b1 | T
+            if (tid == 0) {
+                mma_bf16(tXY, make_desc(sA1, 128, kKb * 16), make_desc(sW1, 128, kKb * 16), idesc, 0);
+                mma_bf16(tXY + F, make_desc(sA1 + TE * kKb * 2, 128, kKb * 16), make_desc(sW1, 128, kKb * 16), idesc, 0);
+                mma_commit(&T.mbar);
+            }
+            mw.wait(&T.mbar);
+        }
+        tmem_rows<F>(tXY, S.X, S.Y);
+        __syncthreads();
+        float sp[4][4], spp[4][4], tt[4][4];
+        {
+            float sv[4][4], pv[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    tt[r][c] = S.Y[(e0 + r) * PS + f0 + c];
+                    silu3(S.X[(e0 + r) * PS + f0 + c] + S.b1[f0 + c], sv[r][c], sp[r][c], spp[r][c]);
+                    pv[r][c] = sp[r][c] * tt[r][c];
+                }
+                st_k4(&T.a2[0][0], e0 + r, f0, F, sv[r][0], sv[r][1], sv[r][2], sv[r][3]);
+                st_k4(&T.a2[1][0], e0 + r, f0, F, pv[r][0], pv[r][1], pv[r][2], pv[r][3]);
+            }
+            // weight-gradient A rows 0-63: SiLU(a)^T, (SiLU'(a) T)^T (feature rows, pair columns)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                st_k4(opA, f0 + c, e0, TE, sv[0][c], sv[1][c], sv[2][c], sv[3][c]);
+                st_k4(opA, F + f0 + c, e0, TE, pv[0][c], pv[1][c], pv[2][c], pv[3][c]);
+            }
+        }
+        // rows 64 ..: e^T, e'^T (K rows each), then zero rows
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = tid + kT * i, r = 64 + (c >> 4), k8 = (c & 15) * 8;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (r < 64 + 2 * K) {
+                const float* src = (r < 64 + K ? S.BT + (r - 64) * TE : S.DT + (r - 64 - K) * TE) + k8;
+                const float4 x0 = *reinterpret_cast<const float4*>(src), x1 = *reinterpret_cast<const float4*>(src + 4);
+                w = make_uint4(bf16x2(x0.x, x0.y), bf16x2(x0.z, x0.w), bf16x2(x1.x, x1.y), bf16x2(x1.z, x1.w));
+            }
+            *reinterpret_cast<uint4*>(opA + tile_offset(r, k8, TE)) = w;
+        }
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {                                     // MMA2: phi - b2 | q
+            if (tid == 0) {
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16(tXY, make_desc(sA2 + kk * 256, 128, F * 16), make_desc(sW2T + kk * 256, 128, F * 16),
+                             idesc, kk > 0);
+                    mma_bf16(tXY + F, make_desc(sA2 + TE * F * 2 + kk * 256, 128, F * 16),
+                             make_desc(sW2T + kk * 256, 128, F * 16), idesc, kk > 0);
+                }
+                mma_commit(&T.mbar);
+            }
+            mw.wait(&T.mbar);
+        }
+        tmem_rows<F>(tXY, T.Z[0], T.Z[1]);
+        __syncthreads();
+        float phi[4][4], q[4][4];
+        {
+            // edge adjoints phibar, gbar: X rows (db2), MMA3 A rows, weight-gradient B rows
+            float phb[4][4], gb4[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = e0 + r;
+                const int row = S.row[e];
+                const int i = row < 0 ? a0 : a0 + row;
+                const float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+                const float* uj = a.u + (size_t)S.j[e] * F + f0;
+                const float* mbi = mb + (size_t)i * F + f0;
+                const float* mdbi = mdb + (size_t)i * F + f0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    phi[r][c] = T.Z[0][e * PS + f0 + c] + S.b2[f0 + c];
+                    q[r][c] = T.Z[1][e * PS + f0 + c];
+                    const float wb = mbi[c] * uj[c], wdb = mdbi[c] * uj[c];
+                    phb[r][c] = fc * wb + dl * dfc * wdb;
+                    gb4[r][c] = dl * fc * wdb;
+                }
+                *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(phb[r][0], phb[r][1], phb[r][2], phb[r][3]);
+                st_k4(&T.a3[0][0], e, f0, F, phb[r][0], phb[r][1], phb[r][2], phb[r][3]);
+                st_k4(&T.a3[1][0], e, f0, F, gb4[r][0], gb4[r][1], gb4[r][2], gb4[r][3]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {                // B1 rows f (phibar) and F + f (gbar), pair columns e0 ..
+                st_k4(T.b, f0 + c, e0, TE, phb[0][c], phb[1][c], phb[2][c], phb[3][c]);
+                st_k4(T.b, F + f0 + c, e0, TE, gb4[0][c], gb4[1][c], gb4[2][c], gb4[3][c]);
+            }
+        }
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {                                     // D1 += A B1^T; MMA3: sb | pb
+            if (tid == 0) {
+#pragma unroll
+                for (int kk = 0; kk < TE / 16; ++kk)
+                    mma_bf16(tD1, make_desc(sOA + kk * 256, 128, TE * 16), make_desc(sB + kk * 256, 128, TE * 16),
+                             idesc_w, any || kk > 0);
+#pragma unroll
+                for (int kk = 0; kk < F / 16; ++kk) {
+                    mma_bf16(tXY, make_desc(sA3 + kk * 256, 128, F * 16), make_desc(sW2N + kk * 256, 128, F * 16),
+                             idesc, kk > 0);
+                    mma_bf16(tXY + F, make_desc(sA3 + TE * F * 2 + kk * 256, 128, F * 16),
+                             make_desc(sW2N + kk * 256, 128, F * 16), idesc, kk > 0);
+                }
+                mma_commit(&T.mbar);
+            }
+        }
+        if (tid < F) {
+            float s = 0.f;
+            for (int e = 0; e < TE; ++e) s += S.X[e * PS + tid];
+            gb += s;                                          // db2
+        }
+        if (mw.ok) mw.wait(&T.mbar);
+        tmem_rows<F>(tXY, T.Z[0], T.Z[1]);
+        __syncthreads();
+        float ab[4][4], tb[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float sb = T.Z[0][(e0 + r) * PS + f0 + c], pb = T.Z[1][(e0 + r) * PS + f0 + c];
+                ab[r][c] = sb * sp[r][c] + pb * tt[r][c] * spp[r][c];
+                tb[r][c] = pb * sp[r][c];
+            }
+        // abar -> X rows (db1); B2 = [abar | tbar] over B1, which the completed D1 product read
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            *reinterpret_cast<float4*>(S.X + (e0 + r) * PS + f0) = make_float4(ab[r][0], ab[r][1], ab[r][2], ab[r][3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            st_k4(T.b, f0 + c, e0, TE, ab[0][c], ab[1][c], ab[2][c], ab[3][c]);
+            st_k4(T.b, F + f0 + c, e0, TE, tb[0][c], tb[1][c], tb[2][c], tb[3][c]);
+        }
+        mw.ok = operands_ready(mw.ok);
+        if (mw.ok) {                                     // D2 += A B2^T
+            if (tid == 0) {
+#pragma unroll
+                for (int kk = 0; kk < TE / 16; ++kk)
+                    mma_bf16(tD2, make_desc(sOA + kk * 256, 128, TE * 16), make_desc(sB + kk * 256, 128, TE * 16),
+                             idesc_w, any || kk > 0);
+                mma_commit(&T.mbar);
+            }
+            pending = true;
+            any = true;
+        }
+        if (tid >= kT - F) {
+            const int f = tid - (kT - F);
+            float s = 0.f;
+            for (int e = 0; e < TE; ++e) s += S.X[e * PS + f];
+            gb += s;                                          // db1 (threads kT-F .. kT-1)
+        }
+        __syncthreads();
+        // ubar message: w * Mbar_j + w' * Mdbar_j with w = fc phi, w' = delta (fc' phi + fc q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = e0 + r;
+            const float dl = S.delta[e], fc = S.fc[e], dfc = S.dfc[e];
+            const float* mbj = mb + (size_t)S.j[e] * F + f0;
+            const float* mdbj = mdb + (size_t)S.j[e] * F + f0;
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) o[c] = fc * phi[r][c] * mbj[c] + dl * (dfc * phi[r][c] + fc * q[r][c]) * mdbj[c];
+            *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncthreads();
+        row_sums<F, TE, K>(S, S.X, cur, run);
+        __syncthreads();
+    }
+    if (nA > 0) {
+        if (tid < F && cur >= 0) S.acc[cur * F + tid] = run;
+        __syncthreads();
+        for (int t = tid; t < nA * F; t += kT) ubar[(size_t)a0 * F + t] = S.acc[t];
+    }
+    // CTA partials of the filter weights from D1 and D2
+    if (pending) mw.wait(&T.mbar);
+    const bool ok = __syncthreads_and(mw.ok);
+    float* st = S.X;                                     // staging: D1 blocks, then D2 blocks
+    const int w = tid >> 5, lane = tid & 31;
+    if (ok && any && w < 3) {
+        float v[32];
+        if (w < 2) {                                     // lanes 32 w + lane: SiLU(a)^T rows (w 0), (SiLU'(a) T)^T rows (w 1)
+            const uint32_t ta = tD1 + ((uint32_t)(32 * w) << 16) + (w == 0 ? 0u : 32u);
+            tmem_ld16x2(ta, v, ta + 16, v + 16);
+#pragma unroll
+            for (int f = 0; f < 32; ++f) st[(w * 32 + lane) * 32 + f] = v[f];
+        } else {                                         // lanes 64 + lane: e^T (lane < K), e'^T (K <= lane < 2K)
+            const uint32_t ta = tD2 + (64u << 16);       // both column halves (the address is warp-uniform)
+            tmem_ld16x2(ta, v, ta + 16, v + 16);
+            if (lane < K)
+#pragma unroll
+                for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
+            tmem_ld16x2(ta + 32, v, ta + 48, v + 16);
+            if (lane >= K && lane < 2 * K)
+#pragma unroll
+                for (int f = 0; f < 32; ++f) st[2048 + lane * 32 + f] = v[f];
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < F * F; idx += kT) out[a.off.W2[0] + idx] = (ok && any) ? st[idx] + st[1024 + idx] : 0.f;
+    for (int idx = tid; idx < K * F; idx += kT)
+        out[a.off.W1[0] + idx] = (ok && any) ? st[2048 + idx] + st[2048 + K * F + idx] : 0.f;
+    if (tid < F) out[a.off.b2[0] + tid] = gb;
+    if (tid >= kT - F) out[a.off.b1[0] + tid - (kT - F)] = gb;
+    mw.finish(&T.mbar, T.taddr, 256, status);
 }
 
 // dW_in += h0_i^T ubar_i, dA[Z_i] += ubar_i W_in^T (warp per atom, F = 32)
@@ -950,13 +1270,28 @@ void tangent_go(const PotArgs& a, const float* g, float* mdot, cudaStream_t s) {
     k_fm_tangent<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mdot);
 }
 
-template <int F, int K, bool TC>
-void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
-                  int n_params, int* status, cudaStream_t s) {
-    const size_t smem = TC ? sizeof(GradTc<F, K>) : edge_smem<F, K>();
-    smem_opt_in((const void*)k_fm_grad_edge<F, K, TC>, (int)smem);
+template <int F, int K>
+void tangent_tc_go(const PotArgs& a, const float* g, float* mdot, int* status, cudaStream_t s) {
+    smem_opt_in((const void*)k_fm_tangent_tc<F, K>, (int)sizeof(TangTc<F, K>));
     int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
-    k_fm_grad_edge<F, K, TC><<<grid, kT, smem, s>>>(a, g, mb, mdb, ubar, partial, n_params, status);
+    k_fm_tangent_tc<F, K><<<grid, kT, sizeof(TangTc<F, K>), s>>>(a, g, mdot, status);
+}
+
+template <int F, int K>
+void grad_edge_tc_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
+                     int n_params, int* status, cudaStream_t s) {
+    static_assert(sizeof(GradTc<F, K>) <= 227 * 1024, "shared memory of one CTA");
+    smem_opt_in((const void*)k_fm_grad_edge_tc<F, K>, (int)sizeof(GradTc<F, K>));
+    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
+    k_fm_grad_edge_tc<F, K><<<grid, kT, sizeof(GradTc<F, K>), s>>>(a, g, mb, mdb, ubar, partial, n_params, status);
+}
+
+template <int F, int K>
+void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float* mdb, float* ubar, float* partial,
+                  int n_params, cudaStream_t s) {
+    smem_opt_in((const void*)k_fm_grad_edge<F, K>, (int)edge_smem<F, K>());
+    int grid = (a.n_atoms + a.atoms_per_cta - 1) / a.atoms_per_cta;
+    k_fm_grad_edge<F, K><<<grid, kT, edge_smem<F, K>(), s>>>(a, g, mb, mdb, ubar, partial, n_params);
 }
 
 }  // namespace
@@ -987,8 +1322,13 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     }
     PotArgs a = p;
     a.atoms_per_cta = fm_atoms_per_cta();
-    if (K == 8) tangent_go<32, 8>(a, g, mdot, s);
-    else tangent_go<32, 16>(a, g, mdot, s);
+    if (tensor_cores) {
+        if (K == 8) tangent_tc_go<32, 8>(a, g, mdot, status, s);
+        else tangent_tc_go<32, 16>(a, g, mdot, status, s);
+    } else {
+        if (K == 8) tangent_go<32, 8>(a, g, mdot, s);
+        else tangent_go<32, 16>(a, g, mdot, s);
+    }
     // every row of a pass's partials holds every entry of the parameter
     // blocks that pass writes; only those blocks are reduced
     const ModelOffsets& o = a.off;
@@ -1001,11 +1341,11 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     fm_reduce(partial_a, ra, n_params, o.R1, o.e0 + S, grad, s);                // R1, d1, R2, d2, e0
     const int ge = fm_edge_ctas(n);
     if (tensor_cores) {
-        if (K == 8) grad_edge_go<32, 8, true>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
-        else grad_edge_go<32, 16, true>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+        if (K == 8) grad_edge_tc_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+        else grad_edge_tc_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
     } else {
-        if (K == 8) grad_edge_go<32, 8, false>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
-        else grad_edge_go<32, 16, false>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
+        if (K == 8) grad_edge_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
+        else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
     }
     fm_reduce(partial_e, ge, n_params, o.W1[0], o.b2[0] + F, grad, s);          // W1, b1, W2, b2
     k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
