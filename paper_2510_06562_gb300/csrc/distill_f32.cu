@@ -147,15 +147,17 @@ struct EdgeSmem {
 //   MMA3  [sb | pb]      = [phibar | gbar] W2^T            (gradient pass)
 // and the weight gradients, summed over the CTA's tiles: an A operand of 128
 // rows by the tile's pairs (the ST and PT region, 32 KB) holds SiLU(a)^T
-// (rows 0-31), (SiLU'(a) T)^T (32-63), e^T and e'^T (K rows each) and zero
-// rows; B holds [phibar | gbar], later [abar | tbar], as 64 rows by the
-// pairs; D1 += A B1^T, D2 += A B2^T (64 FP32 columns each), and
-//   dW2[k][f] = D1[k][f] + D1[32 + k][32 + f],
-//   dW1[k][f] = D2[64 + k][f] + D2[64 + K + k][32 + f]
+// (rows 0-31), (SiLU'(a) T)^T (32-63), e^T and e'^T (K rows each), zero
+// rows and a row of ones (127); B holds [phibar | gbar], later
+// [abar | tbar], as 64 rows by the pairs; D1 += A B1^T, D2 += A B2^T (64
+// FP32 columns each), and
+//   dW2[k][f] = D1[k][f] + D1[32 + k][32 + f],   db2[f] = D1[127][f],
+//   dW1[k][f] = D2[64 + k][f] + D2[64 + K + k][32 + f],   db1[f] = D2[127][f]
 // (the other blocks of D1 and D2 are products nobody reads). Accumulator
 // pairs are read back by all eight warps into FP32 rows [TE][F + 4], which
 // the 4 x 4 thread blocks of the passes read as before.
 constexpr int kKb = 16;                      // basis columns of the MMA1 operands (one K step)
+constexpr uint32_t kBf16Ones = 0x3F803F80u;  // two BF16 ones
 
 template <int F>
 struct TcWeights {
@@ -914,7 +916,6 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
     const int tid = threadIdx.x, A = a.atoms_per_cta;
     const int a0 = blockIdx.x * A, a1 = min(a.n_atoms, a0 + A), nA = a1 - a0;
     float* out = partial + (size_t)blockIdx.x * n_params;
-    float gb = 0.f;                      // one bias entry (db2: tid < F, db1: the last F threads)
     if (nA > 0) {
         load_weights(S, a);
         for (int t = tid; t < A * F; t += kT) S.acc[t] = 0.f;
@@ -977,11 +978,11 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
                 st_k4(opA, F + f0 + c, e0, TE, pv[0][c], pv[1][c], pv[2][c], pv[3][c]);
             }
         }
-        // rows 64 ..: e^T, e'^T (K rows each), then zero rows
+        // rows 64 ..: e^T, e'^T (K rows each), zero rows, and a row of ones (127: the bias sums)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int c = tid + kT * i, r = 64 + (c >> 4), k8 = (c & 15) * 8;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            uint4 w = r == 127 ? make_uint4(kBf16Ones, kBf16Ones, kBf16Ones, kBf16Ones) : make_uint4(0u, 0u, 0u, 0u);
             if (r < 64 + 2 * K) {
                 const float* src = (r < 64 + K ? S.BT + (r - 64) * TE : S.DT + (r - 64 - K) * TE) + k8;
                 const float4 x0 = *reinterpret_cast<const float4*>(src), x1 = *reinterpret_cast<const float4*>(src + 4);
@@ -1007,7 +1008,7 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
         __syncthreads();
         float phi[4][4], q[4][4];
         {
-            // edge adjoints phibar, gbar: X rows (db2), MMA3 A rows, weight-gradient B rows
+            // edge adjoints phibar, gbar: MMA3 A rows, weight-gradient B rows
             float phb[4][4], gb4[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -1026,7 +1027,6 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
                     phb[r][c] = fc * wb + dl * dfc * wdb;
                     gb4[r][c] = dl * fc * wdb;
                 }
-                *reinterpret_cast<float4*>(S.X + e * PS + f0) = make_float4(phb[r][0], phb[r][1], phb[r][2], phb[r][3]);
                 st_k4(&T.a3[0][0], e, f0, F, phb[r][0], phb[r][1], phb[r][2], phb[r][3]);
                 st_k4(&T.a3[1][0], e, f0, F, gb4[r][0], gb4[r][1], gb4[r][2], gb4[r][3]);
             }
@@ -1053,11 +1053,6 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
                 mma_commit(&T.mbar);
             }
         }
-        if (tid < F) {
-            float s = 0.f;
-            for (int e = 0; e < TE; ++e) s += S.X[e * PS + tid];
-            gb += s;                                          // db2
-        }
         if (mw.ok) mw.wait(&T.mbar);
         tmem_rows<F>(tXY, T.Z[0], T.Z[1]);
         __syncthreads();
@@ -1070,10 +1065,7 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
                 ab[r][c] = sb * sp[r][c] + pb * tt[r][c] * spp[r][c];
                 tb[r][c] = pb * sp[r][c];
             }
-        // abar -> X rows (db1); B2 = [abar | tbar] over B1, which the completed D1 product read
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            *reinterpret_cast<float4*>(S.X + (e0 + r) * PS + f0) = make_float4(ab[r][0], ab[r][1], ab[r][2], ab[r][3]);
+        // B2 = [abar | tbar] over B1, which the completed D1 product read
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             st_k4(T.b, f0 + c, e0, TE, ab[0][c], ab[1][c], ab[2][c], ab[3][c]);
@@ -1091,13 +1083,6 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
             pending = true;
             any = true;
         }
-        if (tid >= kT - F) {
-            const int f = tid - (kT - F);
-            float s = 0.f;
-            for (int e = 0; e < TE; ++e) s += S.X[e * PS + f];
-            gb += s;                                          // db1 (threads kT-F .. kT-1)
-        }
-        __syncthreads();
         // ubar message: w * Mbar_j + w' * Mdbar_j with w = fc phi, w' = delta (fc' phi + fc q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -1122,8 +1107,20 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
     // CTA partials of the filter weights from D1 and D2
     if (pending) mw.wait(&T.mbar);
     const bool ok = __syncthreads_and(mw.ok);
-    float* st = S.X;                                     // staging: D1 blocks, then D2 blocks
+    float* st = S.X;                                     // staging: D1 blocks, D2 blocks, the bias sums
     const int w = tid >> 5, lane = tid & 31;
+    if (ok && any && w == 3) {                           // row 127 (lane 31 of warp 3): sum over pairs of phibar, abar
+        float v[32];
+        const uint32_t ta = tD1 + (96u << 16), tb = tD2 + (96u << 16);
+        tmem_ld16x2(ta, v, ta + 16, v + 16);
+        if (lane == 31)
+#pragma unroll
+            for (int f = 0; f < 32; ++f) st[3072 + f] = v[f];
+        tmem_ld16x2(tb, v, tb + 16, v + 16);
+        if (lane == 31)
+#pragma unroll
+            for (int f = 0; f < 32; ++f) st[3104 + f] = v[f];
+    }
     if (ok && any && w < 3) {
         float v[32];
         if (w < 2) {                                     // lanes 32 w + lane: SiLU(a)^T rows (w 0), (SiLU'(a) T)^T rows (w 1)
@@ -1147,8 +1144,8 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
     for (int idx = tid; idx < F * F; idx += kT) out[a.off.W2[0] + idx] = (ok && any) ? st[idx] + st[1024 + idx] : 0.f;
     for (int idx = tid; idx < K * F; idx += kT)
         out[a.off.W1[0] + idx] = (ok && any) ? st[2048 + idx] + st[2048 + K * F + idx] : 0.f;
-    if (tid < F) out[a.off.b2[0] + tid] = gb;
-    if (tid >= kT - F) out[a.off.b1[0] + tid - (kT - F)] = gb;
+    if (tid < F) out[a.off.b2[0] + tid] = (ok && any) ? st[3072 + tid] : 0.f;
+    if (tid < F) out[a.off.b1[0] + tid] = (ok && any) ? st[3104 + tid] : 0.f;
     mw.finish(&T.mbar, T.taddr, 256, status);
 }
 
