@@ -479,8 +479,9 @@ def distill_rate(D, I, torch, s, mdl, prec, n_frames=64, n_traj=8):
     """System-specific distillation on the water box: n_frames frames from
     big-model MD (n_traj trajectories, one frame every 10 fs), labelled with
     the big model's energies and forces, then the energy and force loss
-    gradient of the small model over all frames (FP32 adjoints through the
-    forces) and a full training step (gradient + Adam update)."""
+    gradient of the small model over all frames (hand-written second-order
+    adjoints through the forces, in the context's precision) and a full
+    training step (gradient + Adam update)."""
     from paper_2510_06562_gb300 import distill as DS
     sa, sp, ba, bp = mdl
     torch.cuda.synchronize()
@@ -505,9 +506,10 @@ def distill_rate(D, I, torch, s, mdl, prec, n_frames=64, n_traj=8):
     ctx.close()
     return {"workload": f"{n_frames} frames of the {s.n_atoms}-atom box from big-model MD ({n_traj} trajectories, "
                         f"10 fs apart), energy + force loss (lambda_e = 1)",
-            "precision": ("frame forces and energies " + ("BF16 MLP operands on tcgen05, FP32 accumulation"
-                                                           if prec == D.BF16_MLP else "FP32")
-                          + "; second-order adjoint passes FP32"),
+            "precision": ("frame forces and energies, and the per-pair MLP products and filter-weight "
+                          "gradient sums of the second-order edge passes, BF16 operands on tcgen05 with FP32 "
+                          "accumulation; geometry, per-atom pass and sums FP32" if prec == D.BF16_MLP
+                          else "FP32 throughout"),
             "frames_per_s": n_frames / t_grad, "ms_per_frame": t_grad * 1e3 / n_frames,
             "ms_per_training_step": (t_grad + t_adam) * 1e3, "frame_sampling_s": t_sample,
             "loss": loss, "loss_after_one_step": loss1}

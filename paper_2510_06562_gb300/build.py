@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmts.so")
 LIB_CHECK = os.path.join(HERE, "libdmts_check.so")
-SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu", "atom_mlp.cu", "atom_tc.cu", "distill_f32.cu"]
+SOURCES = ["dmts.cu", "neighbors.cu", "potential_f32.cu", "integrate.cu", "noalloc.cu", "potential_bf16.cu", "atom_mlp.cu", "atom_tc.cu", "distill.cu"]
 HEADERS = ["internal.cuh", "umma.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,5 +1,5 @@
-// Distillation gradient of a single-layer model (FP32, hand-written
-// adjoints): the parameter gradient of the energy and force loss
+// Distillation gradient of a single-layer model (hand-written adjoints): the
+// parameter gradient of the energy and force loss
 //   L(theta) = 1/M sum_frames [ lambda_E ((E(theta) - E_ref) / N)^2
 //                               + 1/(3 N) sum_i |F_i(theta) - F_ref,i|^2 ]
 // (lambda_E = 0: force matching), the forces F = -dE/dx making it a second
@@ -17,10 +17,11 @@
 // theta: a tangent edge pass (m'), a per-atom adjoint pass (dPsi/dm,
 // dPsi/dm' and the per-atom weight gradients), and an edge pass for the
 // filter-weight gradients and dPsi/du. Every gradient is summed per CTA and
-// the CTA partials are added in a fixed order (deterministic). In the BF16
-// mode the filter-weight gradient sums over pairs run on the tensor cores
-// (BF16 operands, FP32 accumulation in tensor memory); every other step, and
-// every step of the FP32 mode, is FP32 on the SIMT pipes.
+// the CTA partials are added in a fixed order (deterministic). The FP32 mode
+// runs every step in FP32 on the SIMT pipes; in the BF16 mode the two edge
+// passes run their per-pair MLP products and their weight-gradient sums over
+// pairs on the tensor cores (BF16 operands, FP32 accumulation in tensor
+// memory), the per-atom pass stays FP32.
 //
 // The energy term adds c_E dE/dtheta per frame, c_E = dL/dE = 2 lambda_E
 // (E - E_ref) / (M N^2): the same reverse pass seeded at the readout with

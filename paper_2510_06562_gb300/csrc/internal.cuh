@@ -330,7 +330,7 @@ size_t bf16_weight_tile_bytes(int F);
 int bf16_max_ctas_per_sm(int F, bool bwd, int tiles = 0);
 int bf16_default_bwd_tiles(int F);
 
-// distill_f32.cu: force-matching gradient of a single-layer model
+// distill.cu: distillation (energy and force matching) gradient of a single-layer model
 bool fm_supported(int F, int K, int L);
 int fm_edge_ctas(int n_atoms);
 int fm_atom_ctas(int n_atoms);
