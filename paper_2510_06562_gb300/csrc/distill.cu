@@ -29,6 +29,8 @@
 // dPsi/dq gains -c_E SiLU'(q) R2, dPsi/dR2 gains -c_E SiLU(q), and d2 and
 // e0[Z_i] gain -c_E per atom.
 #include <algorithm>
+#include <initializer_list>
+#include <utility>
 
 #include <cuda_bf16.h>
 
@@ -427,19 +429,53 @@ __global__ void __launch_bounds__(kT) k_fm_tangent(PotArgs a, const float* __res
 // pass touches are written).
 __device__ __forceinline__ float bcast(float v, int k) { return __shfl_sync(0xffffffffu, v, k); }
 
-// out[lane] = sum_k in_k W[k][lane] with in_k held by lane k
-__device__ __forceinline__ float gemv(float in, const float* W) {
-    float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc += bcast(in, k) * W[k * 32 + (threadIdx.x & 31)];
-    return acc;
-}
 // out[lane] = sum_k in_k W[lane][k], W row-major with row stride 33 (x W^T)
 __device__ __forceinline__ float gemv_t(float in, const float* W) {
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc += bcast(in, k) * W[(threadIdx.x & 31) * 33 + k];
     return acc;
+}
+
+// out[lane] = sum_k v[k] W[k][lane] (gemv_s) and sum_k v[k] W[lane][k]
+// (gemv_t_s, W with row stride 33), the vector in shared memory (one copy
+// per warp) read four entries per broadcast load, the sums over k in order.
+__device__ __forceinline__ float gemv_s(const float* v, const float* W) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(v + k);
+        acc += x.x * W[k * 32 + lane];
+        acc += x.y * W[(k + 1) * 32 + lane];
+        acc += x.z * W[(k + 2) * 32 + lane];
+        acc += x.w * W[(k + 3) * 32 + lane];
+    }
+    return acc;
+}
+__device__ __forceinline__ float gemv_t_s(const float* v, const float* W) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(v + k);
+        acc += x.x * W[lane * 33 + k];
+        acc += x.y * W[lane * 33 + k + 1];
+        acc += x.z * W[lane * 33 + k + 2];
+        acc += x.w * W[lane * 33 + k + 3];
+    }
+    return acc;
+}
+// g[k] += a[k] sa + b[k] sb (a, b in shared memory, one copy per warp)
+__device__ __forceinline__ void outer(float* g, const float* a, float sa, const float* b, float sb) {
+#pragma unroll
+    for (int k = 0; k < 32; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(a + k), y = *reinterpret_cast<const float4*>(b + k);
+        g[k] += x.x * sa + y.x * sb;
+        g[k + 1] += x.y * sa + y.y * sb;
+        g[k + 2] += x.z * sa + y.z * sb;
+        g[k + 3] += x.w * sa + y.w * sb;
+    }
 }
 
 constexpr int kAtomWarps = 8;
@@ -454,6 +490,7 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
     // U1, U2, R1 as W[k][f] (for x W), then padded copies U1T, U2T, R1T (for
     // x W^T); at the end the same array holds the block's gradient sums
     __shared__ float smw[3 * F * F + 3 * F * 33];
+    __shared__ __align__(16) float vbuf[kAtomWarps][12][F];
     float* const U1 = smw;
     float* const U2 = U1 + F * F;
     float* const R1 = U2 + F * F;
@@ -482,39 +519,60 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_atom(PotArgs a, const fl
 #pragma unroll
     for (int z = 0; z < 16; ++z) gA[z] = 0.f;
     const int n_sp = S_species / F;
+    // per-warp vectors (one feature per lane) that the matrix-vector products
+    // read as broadcasts, four features per load; each slot is written once
+    // per atom
+    float* const vs = vbuf[w][0];
+    auto slot = [&](int k) { return vs + k * F; };
     for (int i = blockIdx.x * kAtomWarps + w; i < a.n_atoms; i += gridDim.x * kAtomWarps) {
         const size_t o = (size_t)i * F + lane;
         const float mv = m[o], md = mdot[o], h1 = a.h[o];
-        const float z = gemv(mv, U1) + c1;
-        const float zd = gemv(md, U1);
+        __syncwarp();                              // the previous atom's slots have been read
+        slot(0)[lane] = mv;
+        slot(1)[lane] = md;
+        slot(2)[lane] = h1;
+        __syncwarp();
+        const float z = gemv_s(slot(0), U1) + c1;
+        const float zd = gemv_s(slot(1), U1);
+        const float q = gemv_s(slot(2), R1) + d1;
         float sz, s1z, s2z;
         silu3(z, sz, s1z, s2z);
         const float yd = s1z * zd;                 // tangent of SiLU(z)
-        const float h1d = gemv(yd, U2);            // tangent of h1
-        const float q = gemv(h1, R1) + d1;
-        const float qd = gemv(h1d, R1);
+        slot(3)[lane] = yd;
+        slot(4)[lane] = sz;
+        __syncwarp();
+        const float h1d = gemv_s(slot(3), U2);     // tangent of h1
+        slot(5)[lane] = h1d;
+        __syncwarp();
+        const float qd = gemv_s(slot(5), R1);
         float sq, s1q, s2q;
         silu3(q, sq, s1q, s2q);
         const float qdb = s1q * r2;                // dPsi/dq'
         const float qb = s2q * qd * r2 - ce * s1q * r2;   // dPsi/dq, with the energy term's seed
         gR2 += s1q * qd - ce * sq;
         gd1 += qb;
-#pragma unroll
-        for (int k = 0; k < F; ++k) gR1[k] += bcast(h1, k) * qb + bcast(h1d, k) * qdb;
-        const float hb = gemv_t(qb, R1T);          // dPsi/dh1
-        const float hdb = gemv_t(qdb, R1T);        // dPsi/dh1'
+        outer(gR1, slot(2), qb, slot(5), qdb);
+        slot(6)[lane] = qb;
+        slot(7)[lane] = qdb;
+        __syncwarp();
+        const float hb = gemv_t_s(slot(6), R1T);   // dPsi/dh1
+        const float hdb = gemv_t_s(slot(7), R1T);  // dPsi/dh1'
         gc2 += hb;
-#pragma unroll
-        for (int k = 0; k < F; ++k) gU2[k] += bcast(sz, k) * hb + bcast(yd, k) * hdb;
-        const float yb = gemv_t(hb, U2T);
-        const float ydb = gemv_t(hdb, U2T);
+        outer(gU2, slot(4), hb, slot(3), hdb);
+        slot(8)[lane] = hb;
+        slot(9)[lane] = hdb;
+        __syncwarp();
+        const float yb = gemv_t_s(slot(8), U2T);
+        const float ydb = gemv_t_s(slot(9), U2T);
         const float zb = yb * s1z + ydb * s2z * zd;
         const float zdb = ydb * s1z;
         gc1 += zb;
-#pragma unroll
-        for (int k = 0; k < F; ++k) gU1[k] += bcast(mv, k) * zb + bcast(md, k) * zdb;
-        mbar_psi[o] = gemv_t(zb, U1T);
-        mdotbar_psi[o] = gemv_t(zdb, U1T);
+        outer(gU1, slot(0), zb, slot(1), zdb);
+        slot(10)[lane] = zb;
+        slot(11)[lane] = zdb;
+        __syncwarp();
+        mbar_psi[o] = gemv_t_s(slot(10), U1T);
+        mdotbar_psi[o] = gemv_t_s(slot(11), U1T);
         const int sp = a.species[i];
 #pragma unroll
         for (int zz = 0; zz < 16; ++zz)
@@ -1207,31 +1265,44 @@ __global__ void k_fm_energy_term(int n_sys, const double* __restrict__ E, const 
     *c_energy = 2.0 * lambda * r * inv_frames / (double)n_atoms;
 }
 
-// grad[p] -= sum_c partial[c][p] for p in [p0, p1): 32 parameters per block,
-// each summed by kRedG threads; thread g keeps four FP64 sums over rows
-// c = g + kRedG (4k + u), u = 0..3 (four loads in flight), adds them in u
-// order, and the kRedG thread sums are added in g order: one order for any
-// grid.
-constexpr int kRedP = 32, kRedG = 16;
+// grad[p] -= sum_c partial[c][p] for p in up to four ranges [p0, p1) of
+// the parameter vector (one launch): 32 parameters per block, each summed by
+// kRedG threads; thread g keeps eight FP64 sums over rows
+// c = g + kRedG (8k + u), u = 0..7 (eight loads in flight), adds them
+// pairwise in u order, and the kRedG thread sums are added in g order: one
+// order for any grid.
+constexpr int kRedP = 32, kRedG = 16, kRedU = 8, kRedMax = 4;
+struct RedRanges {
+    int n = 0;
+    int p0[kRedMax] = {}, p1[kRedMax] = {};
+    int blk0[kRedMax + 1] = {};          // first block of each range; blk0[n] = the grid
+};
+
 __global__ void __launch_bounds__(kRedP * kRedG) k_fm_reduce(const float* __restrict__ partial, int n_rows,
-                                                               int n_params, int p0, int p1,
+                                                               int n_params, RedRanges rr,
                                                                double* __restrict__ grad) {
     __shared__ double part[kRedG][kRedP];
+    int r = 0;
+    while (r + 1 < rr.n && (int)blockIdx.x >= rr.blk0[r + 1]) ++r;
     const int lp = threadIdx.x % kRedP, g = threadIdx.x / kRedP;
-    const int p = p0 + blockIdx.x * kRedP + lp;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (p < p1) {
+    const int p = rr.p0[r] + ((int)blockIdx.x - rr.blk0[r]) * kRedP + lp;
+    double acc[kRedU];
+#pragma unroll
+    for (int u = 0; u < kRedU; ++u) acc[u] = 0.0;
+    if (p < rr.p1[r]) {
         const float* col = partial + p;
         int c = g;
-        for (; c + 3 * kRedG < n_rows; c += 4 * kRedG) {
+        for (; c + (kRedU - 1) * kRedG < n_rows; c += kRedU * kRedG) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] += (double)col[(size_t)(c + u * kRedG) * n_params];
+            for (int u = 0; u < kRedU; ++u) acc[u] += (double)col[(size_t)(c + u * kRedG) * n_params];
         }
-        for (int u = 0; c < n_rows; c += kRedG, ++u) acc[u] += (double)col[(size_t)c * n_params];
+#pragma unroll
+        for (int u = 0; u < kRedU - 1; ++u)             // the rest: fewer than kRedU rows
+            if (c + u * kRedG < n_rows) acc[u] += (double)col[(size_t)(c + u * kRedG) * n_params];
     }
-    part[g][lp] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    part[g][lp] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     __syncthreads();
-    if (g == 0 && p < p1) {
+    if (g == 0 && p < rr.p1[r]) {
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < kRedG; ++k) t += part[k][lp];
@@ -1239,20 +1310,43 @@ __global__ void __launch_bounds__(kRedP * kRedG) k_fm_reduce(const float* __rest
     }
 }
 
-// The reduction of the partial rows over the parameter range [p0, p1).
-void fm_reduce(const float* partial, int n_rows, int n_params, int p0, int p1, double* grad, cudaStream_t s) {
-    if (p1 <= p0) return;
-    k_fm_reduce<<<(p1 - p0 + kRedP - 1) / kRedP, kRedP * kRedG, 0, s>>>(partial, n_rows, n_params, p0, p1, grad);
+// The reduction of the partial rows over the given parameter ranges (one launch).
+void fm_reduce(const float* partial, int n_rows, int n_params, std::initializer_list<std::pair<int, int>> ranges,
+               double* grad, cudaStream_t s) {
+    RedRanges rr;
+    int blocks = 0;
+    for (const auto& pr : ranges) {
+        if (pr.second <= pr.first || rr.n == kRedMax) continue;
+        rr.p0[rr.n] = pr.first;
+        rr.p1[rr.n] = pr.second;
+        rr.blk0[rr.n] = blocks;
+        blocks += (pr.second - pr.first + kRedP - 1) / kRedP;
+        ++rr.n;
+    }
+    rr.blk0[rr.n] = blocks;
+    if (blocks == 0) return;
+    k_fm_reduce<<<blocks, kRedP * kRedG, 0, s>>>(partial, n_rows, n_params, rr, grad);
 }
 
-__global__ void k_sum_all(int n, const double* __restrict__ v, double scale, double* __restrict__ out) {
-    __shared__ double sh[256];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
-    sh[threadIdx.x] = acc;
+// out += scale * sum v (one block; each thread four interleaved FP64 sums,
+// so four loads are in flight, then a fixed-order tree).
+constexpr int kSumT = 1024;
+__global__ void __launch_bounds__(kSumT) k_sum_all(int n, const double* __restrict__ v, double scale,
+                                                   double* __restrict__ out) {
+    __shared__ double sh[kSumT];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = threadIdx.x;
+    for (; i + 3 * kSumT < n; i += 4 * kSumT) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += v[i + u * kSumT];
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (i + u * kSumT < n) acc[u] += v[i + u * kSumT];
+    sh[threadIdx.x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    for (int w = kSumT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) *out += scale * sh[0];
@@ -1313,7 +1407,7 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     const int n = p.n_atoms;
     if (n == 0) return;
     k_fm_residual<<<(n + 255) / 256, 256, 0, s>>>(n, p.force, f_ref, c_loss, g, sq);
-    k_sum_all<<<1, 256, 0, s>>>(n, sq, 0.5 * c_loss, loss);
+    k_sum_all<<<1, kSumT, 0, s>>>(n, sq, 0.5 * c_loss, loss);
     if (en.e_ref) {
         k_fm_energy_term<<<1, 32, 0, s>>>(en.n_sys, en.E, en.e_ref, en.lambda, n, en.inv_frames, en.c_energy, loss);
         count_launch();
@@ -1334,9 +1428,9 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
     const int ga = fm_atom_ctas(n), ra = ga;             // one partial row per per-atom block
     k_fm_atom<<<ga, kAtomWarps * 32, 0, s>>>(a, m, mdot, mbar_psi, mdotbar_psi, partial_a, n_params,
                                              en.e_ref ? en.c_energy : nullptr);
-    fm_reduce(partial_a, ra, n_params, o.A, o.A + S * F, grad, s);               // A
-    fm_reduce(partial_a, ra, n_params, o.U1[0], o.c2[0] + F, grad, s);          // U1, c1, U2, c2
-    fm_reduce(partial_a, ra, n_params, o.R1, o.e0 + S, grad, s);                // R1, d1, R2, d2, e0
+    fm_reduce(partial_a, ra, n_params, {{o.A, o.A + S * F},                      // A
+                                        {o.U1[0], o.c2[0] + F},                 // U1, c1, U2, c2
+                                        {o.R1, o.e0 + S}}, grad, s);            // R1, d1, R2, d2, e0
     const int ge = fm_edge_ctas(n);
     if (tensor_cores) {
         if (K == 8) grad_edge_tc_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
@@ -1345,11 +1439,11 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
         if (K == 8) grad_edge_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
         else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
     }
-    fm_reduce(partial_e, ge, n_params, o.W1[0], o.b2[0] + F, grad, s);          // W1, b1, W2, b2
+    fm_reduce(partial_e, ge, n_params, {{o.W1[0], o.b2[0] + F}}, grad, s);       // W1, b1, W2, b2
     k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
-    fm_reduce(partial_a, ra, n_params, o.A, o.A + S * F, grad, s);               // A
-    fm_reduce(partial_a, ra, n_params, o.W_in[0], o.W_in[0] + F * F, grad, s);  // W_in
-    count_launch(12);
+    fm_reduce(partial_a, ra, n_params, {{o.A, o.A + S * F},                      // A
+                                        {o.W_in[0], o.W_in[0] + F * F}}, grad, s);   // W_in
+    count_launch(9);
 }
 
 }  // namespace dmts
