@@ -44,7 +44,7 @@ namespace {
 using namespace umma;
 
 constexpr int kT = 256;
-constexpr int kFmAtoms = 32;                 // atoms per CTA of the edge passes
+constexpr int kFmAtomsMax = 96;              // atoms per CTA of the edge passes, at most
 constexpr uint32_t kFmWait = 1u << 22;       // bounded mbarrier polls (tensor-core weight gradients)
 
 __device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + expf(-x)); }
@@ -134,7 +134,7 @@ struct EdgeSmem {
     float X[TE * (F + 4)], Y[TE * (F + 4)];   // per-edge rows (msg, phibar, gbar, abar, tbar)
     float fc[TE], dfc[TE], delta[TE];
     int j[TE], row[TE];
-    float acc[kFmAtoms * F];             // per-atom row sums of the CTA
+    float acc[kFmAtomsMax * F];          // per-atom row sums of the CTA
     float slot[kT / 32][2][F];           // per-warp open row segments of a tile (row_sums)
     int slot_row[kT / 32][2];
 };
@@ -427,15 +427,7 @@ __global__ void __launch_bounds__(kT) k_fm_tangent(PotArgs a, const float* __res
 // Warp per atom, lane = feature (F = 32). Gradient slots (floats) of the
 // per-CTA partial vector: the flat parameter layout (only the blocks this
 // pass touches are written).
-__device__ __forceinline__ float bcast(float v, int k) { return __shfl_sync(0xffffffffu, v, k); }
 
-// out[lane] = sum_k in_k W[lane][k], W row-major with row stride 33 (x W^T)
-__device__ __forceinline__ float gemv_t(float in, const float* W) {
-    float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc += bcast(in, k) * W[(threadIdx.x & 31) * 33 + k];
-    return acc;
-}
 
 // out[lane] = sum_k v[k] W[k][lane] (gemv_s) and sum_k v[k] W[lane][k]
 // (gemv_t_s, W with row stride 33), the vector in shared memory (one copy
@@ -1213,6 +1205,7 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_input(PotArgs a, const f
                                                                float* __restrict__ partial, int n_params) {
     constexpr int F = 32;
     __shared__ float WinT[F * 33];     // W_in[k][f] padded, for x W_in^T
+    __shared__ __align__(16) float vbuf[kAtomWarps][2][F];   // per-warp h0 and ubar of the atom
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int t = tid; t < F * F; t += blockDim.x) WinT[(t / F) * 33 + t % F] = a.P[a.off.W_in[0] + t];
     __syncthreads();
@@ -1227,9 +1220,19 @@ __global__ void __launch_bounds__(kAtomWarps * 32) k_fm_input(PotArgs a, const f
         const int sp = a.species[i];
         const float ub = ubar[(size_t)i * F + lane];
         const float h0 = a.P[a.off.A + sp * F + lane];
+        __syncwarp();                              // the previous atom's vectors have been read
+        vbuf[w][0][lane] = h0;
+        vbuf[w][1][lane] = ub;
+        __syncwarp();
 #pragma unroll
-        for (int k = 0; k < F; ++k) gW[k] += bcast(h0, k) * ub;
-        float t = gemv_t(ub, WinT);
+        for (int k = 0; k < F; k += 4) {
+            const float4 h = *reinterpret_cast<const float4*>(&vbuf[w][0][k]);
+            gW[k] += h.x * ub;
+            gW[k + 1] += h.y * ub;
+            gW[k + 2] += h.z * ub;
+            gW[k + 3] += h.w * ub;
+        }
+        float t = gemv_t_s(vbuf[w][1], WinT);
 #pragma unroll
         for (int zz = 0; zz < 16; ++zz)
             if (zz == sp) gA[zz] += t;
@@ -1390,11 +1393,44 @@ void grad_edge_go(const PotArgs& a, const float* g, const float* mb, const float
 
 bool fm_supported(int F, int K, int L) { return F == 32 && (K == 8 || K == 16) && L == 1; }
 
-int fm_atoms_per_cta() { return kFmAtoms; }
+namespace {
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    return sms;
+}
 
-int fm_edge_ctas(int n_atoms) { return (n_atoms + fm_atoms_per_cta() - 1) / fm_atoms_per_cta(); }
+// Atoms per CTA of an edge pass that runs `per_sm` CTAs per SM: the atoms
+// shared by one wave of CTAs (no partial last wave, fewer ragged tiles), at
+// most kFmAtomsMax.
+int fm_edge_atoms(int n_atoms, int per_sm) {
+    const int ctas = device_sms() * per_sm;
+    return std::max(1, std::min(kFmAtomsMax, (n_atoms + ctas - 1) / ctas));
+}
+}  // namespace
 
-int fm_atom_ctas(int n_atoms) { return std::max(1, std::min(152 * 2, (n_atoms + kAtomWarps - 1) / kAtomWarps)); }
+// The gradient edge pass (one CTA per SM, one partial row per CTA).
+int fm_edge_ctas(int n_atoms) {
+    const int apc = fm_edge_atoms(n_atoms, 1);
+    return (n_atoms + apc - 1) / apc;
+}
+
+// The per-atom adjoint pass: one block per SM (its registers allow one), one partial row per block.
+int fm_atom_ctas(int n_atoms) { return std::max(1, std::min(device_sms(), (n_atoms + kAtomWarps - 1) / kAtomWarps)); }
+
+namespace {
+// The input-gradient pass: three blocks per SM, one partial row per block.
+int fm_input_ctas(int n_atoms) {
+    return std::max(1, std::min(3 * device_sms(), (n_atoms + kAtomWarps - 1) / kAtomWarps));
+}
+}  // namespace
+
+// Rows of the per-atom passes' partial buffer.
+int fm_atom_rows(int n_atoms) { return std::max(fm_atom_ctas(n_atoms), fm_input_ctas(n_atoms)); }
 
 // One frame's contribution: g from the forces already in p.force, then the
 // three passes; grad_out accumulates -dPsi/dtheta (+ c_E dE/dtheta with the
@@ -1413,7 +1449,7 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
         count_launch();
     }
     PotArgs a = p;
-    a.atoms_per_cta = fm_atoms_per_cta();
+    a.atoms_per_cta = fm_edge_atoms(n, 2);               // the tangent pass: two CTAs per SM
     if (tensor_cores) {
         if (K == 8) tangent_tc_go<32, 8>(a, g, mdot, status, s);
         else tangent_tc_go<32, 16>(a, g, mdot, status, s);
@@ -1432,6 +1468,7 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
                                         {o.U1[0], o.c2[0] + F},                 // U1, c1, U2, c2
                                         {o.R1, o.e0 + S}}, grad, s);            // R1, d1, R2, d2, e0
     const int ge = fm_edge_ctas(n);
+    a.atoms_per_cta = fm_edge_atoms(n, 1);               // the gradient pass: one CTA per SM
     if (tensor_cores) {
         if (K == 8) grad_edge_tc_go<32, 8>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
         else grad_edge_tc_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, status, s);
@@ -1440,8 +1477,9 @@ void launch_fm_frame(const PotArgs& p, int K, const double* f_ref, double c_loss
         else grad_edge_go<32, 16>(a, g, mbar_psi, mdotbar_psi, ubar, partial_e, n_params, s);
     }
     fm_reduce(partial_e, ge, n_params, {{o.W1[0], o.b2[0] + F}}, grad, s);       // W1, b1, W2, b2
-    k_fm_input<<<ga, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
-    fm_reduce(partial_a, ra, n_params, {{o.A, o.A + S * F},                      // A
+    const int gi = fm_input_ctas(n);
+    k_fm_input<<<gi, kAtomWarps * 32, 0, s>>>(a, ubar, partial_a, n_params);
+    fm_reduce(partial_a, gi, n_params, {{o.A, o.A + S * F},                      // A
                                         {o.W_in[0], o.W_in[0] + F * F}}, grad, s);   // W_in
     count_launch(9);
 }

@@ -1665,7 +1665,7 @@ int distill_impl(dmts_ctx* c, int n_frames, const double* frames, const double* 
         if (e == cudaSuccess) e = dalloc(&c->fm_mdb, nf);
         if (e == cudaSuccess) e = dalloc(&c->fm_ubar, nf);
         if (e == cudaSuccess) e = dalloc(&c->fm_pe, (size_t)fm_edge_ctas(N) * np);
-        if (e == cudaSuccess) e = dalloc(&c->fm_pa, (size_t)fm_atom_ctas(N) * 8 * np);
+        if (e == cudaSuccess) e = dalloc(&c->fm_pa, (size_t)fm_atom_rows(N) * np);
         if (e == cudaSuccess) e = dalloc(&c->fm_sq, N);
         if (e == cudaSuccess) e = dalloc(&c->fm_grad, np);
         if (e == cudaSuccess) e = dalloc(&c->fm_loss, 1);

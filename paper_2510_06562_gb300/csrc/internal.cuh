@@ -334,6 +334,7 @@ int bf16_default_bwd_tiles(int F);
 bool fm_supported(int F, int K, int L);
 int fm_edge_ctas(int n_atoms);
 int fm_atom_ctas(int n_atoms);
+int fm_atom_rows(int n_atoms);
 // Energy term of the distillation loss for one frame (e_ref null: none).
 struct FmEnergy {
     const double* e_ref = nullptr;   // device scalar: the frame's reference energy
