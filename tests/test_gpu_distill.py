@@ -91,6 +91,28 @@ def test_distill_gradient_bf16_mode_matches_oracle():
     assert np.sqrt(np.mean((F - Fr) ** 2)) <= 5e-3
 
 
+def test_distill_gradient_bf16_mode_water12288():
+    """The BF16-mode passes on two frames of the 12,288-atom box: there each
+    CTA of the edge passes covers about 80 atoms, so its pairs span about
+    ten 128-pair tiles and the tensor-memory sums, the open row between
+    tiles and the rows split across CTAs are all exercised (on 192 atoms a
+    CTA holds one or two atoms and a single tile). Bounds as on 192 atoms."""
+    s = I.water_12288(0)
+    sa, sp, ba, bp = _models()
+    frames, f_ref, e_ref = _labelled_frames(s, ba, bp, 2, 13)
+    L_ref, g_ref = M.distill_grad(M.spec_of(sa), sp, frames, s.species, s.atom_offset, s.box, f_ref, e_ref, 1.0)
+    with D.Context(s, ba, bp, sa, sp, precision=D.BF16_MLP) as ctx:
+        ctx.set_state(s.x)
+        L, g = ctx.distill_grad(frames, f_ref, e_ref, 1.0)
+    err = np.abs(g - g_ref)
+    rel = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    print(json.dumps({"system": "water12288", "bf16_loss": L, "loss_ref": L_ref, "grad_rel_l2": rel,
+                      "grad_max_abs_err": float(err.max()), "grad_max_abs": float(np.abs(g_ref).max())}))
+    assert abs(L - L_ref) <= 5e-3 * L_ref
+    assert rel <= 2e-2
+    assert err.max() <= 2e-2 * np.abs(g_ref).max()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_distill_gradient_with_sixteen_radial_functions(precision):
     """The distillation kernels built for 16 radial functions (the other
