@@ -219,12 +219,95 @@ __device__ __forceinline__ void load_weights(EdgeSmem<F, K>& S, const PotArgs& a
     }
 }
 
-// Per-edge setup (threads < TE): geometry, basis, delta = rhat . (g_j - g_i);
-// a1 (tensor-core passes, else null): e and e' also as the BF16 pair rows of
-// the MMA1 operands (16 columns, zero past K).
+// One pair's inputs: its atoms, their fixed-point positions and residual
+// rows g (threads < TE; loaded a tile ahead by the tensor-core passes).
+struct PairIn {
+    int j = 0, i = 0;
+    bool valid = false;
+    uint4 qi, qj;
+    float gi[3], gj[3];
+};
+
+__device__ __forceinline__ void pair_idx(const PotArgs& a, long long e, long long e_end, PairIn& p) {
+    p.valid = e < e_end;
+    if (p.valid) {
+        p.j = DMTS_IDX(a.col[e], a.n_atoms, a.check);
+        p.i = DMTS_IDX(a.recv[e], a.n_atoms, a.check);
+    }
+}
+
+__device__ __forceinline__ void pair_pos(const PotArgs& a, const float* __restrict__ g, PairIn& p) {
+    if (p.valid) {
+        const int n = a.n_atoms;
+        p.qi = a.q[p.i];
+        p.qj = a.q[p.j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            p.gi[c] = g[c * n + p.i];
+            p.gj[c] = g[c * n + p.j];
+        }
+    }
+}
+
+// Per-edge setup of pair tid (threads < TE) from its inputs: geometry, basis,
+// delta = rhat . (g_j - g_i); a1 (tensor-core passes, else null): e and e'
+// also as the BF16 pair rows of the MMA1 operands (16 columns, zero past K).
+template <int F, int K>
+__device__ __forceinline__ void edge_setup_in(EdgeSmem<F, K>& S, const PotArgs& a, const PairIn& p, int a0,
+                                              unsigned char* a1) {
+    constexpr int TE = Geo<F, K>::TE;
+    const int tid = threadIdx.x;
+    float eb[K], db[K];
+    if (p.valid) {
+        float3 r = edge_vec(p.qi, p.qj, a.frame[p.qi.w].qscale);
+        float d = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+        float inv = 1.0f / d;
+        float fc, dfc;
+        basis_pair<K>(d, a.pi_over_rc, a.bessel_pref, eb, db, fc, dfc);
+        float dl = (r.x * (p.gj[0] - p.gi[0]) + r.y * (p.gj[1] - p.gi[1]) + r.z * (p.gj[2] - p.gi[2])) * inv;
+        S.fc[tid] = fc;
+        S.dfc[tid] = dfc;
+        S.delta[tid] = dl;
+        S.j[tid] = p.j;
+        S.row[tid] = p.i - a0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) { eb[k] = 0.f; db[k] = 0.f; }
+        S.fc[tid] = 0.f;
+        S.dfc[tid] = 0.f;
+        S.delta[tid] = 0.f;
+        S.j[tid] = a0;
+        S.row[tid] = -1;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        S.BT[k * TE + tid] = eb[k];
+        S.DT[k * TE + tid] = db[k];
+    }
+    if (a1) {
+        static_assert(K <= kKb && K % 8 == 0, "whole 8-column chunks of the basis");
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) =
+                make_uint4(bf16x2(eb[k0], eb[k0 + 1]), bf16x2(eb[k0 + 2], eb[k0 + 3]),
+                           bf16x2(eb[k0 + 4], eb[k0 + 5]), bf16x2(eb[k0 + 6], eb[k0 + 7]));
+            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) =
+                make_uint4(bf16x2(db[k0], db[k0 + 1]), bf16x2(db[k0 + 2], db[k0 + 3]),
+                           bf16x2(db[k0 + 4], db[k0 + 5]), bf16x2(db[k0 + 6], db[k0 + 7]));
+        }
+#pragma unroll
+        for (int k0 = K; k0 < kKb; k0 += 8) {
+            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// The same with the pair's inputs loaded here (the FP32 passes; written out
+// so that their register allocation stays that of a single load-and-compute).
 template <int F, int K>
 __device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, const float* __restrict__ g,
-                                           long long t0, long long e_end, int a0, unsigned char* a1 = nullptr) {
+                                           long long t0, long long e_end, int a0) {
     constexpr int TE = Geo<F, K>::TE;
     const int tid = threadIdx.x;
     if (tid >= TE) return;
@@ -258,23 +341,6 @@ __device__ __forceinline__ void edge_setup(EdgeSmem<F, K>& S, const PotArgs& a, 
     for (int k = 0; k < K; ++k) {
         S.BT[k * TE + tid] = eb[k];
         S.DT[k * TE + tid] = db[k];
-    }
-    if (a1) {
-        static_assert(K <= kKb && K % 8 == 0, "whole 8-column chunks of the basis");
-#pragma unroll
-        for (int k0 = 0; k0 < K; k0 += 8) {
-            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) =
-                make_uint4(bf16x2(eb[k0], eb[k0 + 1]), bf16x2(eb[k0 + 2], eb[k0 + 3]),
-                           bf16x2(eb[k0 + 4], eb[k0 + 5]), bf16x2(eb[k0 + 6], eb[k0 + 7]));
-            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) =
-                make_uint4(bf16x2(db[k0], db[k0 + 1]), bf16x2(db[k0 + 2], db[k0 + 3]),
-                           bf16x2(db[k0 + 4], db[k0 + 5]), bf16x2(db[k0 + 6], db[k0 + 7]));
-        }
-#pragma unroll
-        for (int k0 = K; k0 < kKb; k0 += 8) {
-            *reinterpret_cast<uint4*>(a1 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(a1 + TE * kKb * 2 + tile_offset(tid, k0, kKb)) = make_uint4(0u, 0u, 0u, 0u);
-        }
     }
 }
 
@@ -886,8 +952,16 @@ __global__ void __launch_bounds__(kT) k_fm_tangent_tc(PotArgs a, const float* __
     const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
     int cur = -1;
     float run = 0.f;
+    PairIn nx;                                           // the next tile's pair inputs (threads < TE)
+    if (tid < TE) {
+        pair_idx(a, e_beg + tid, e_end, nx);
+        pair_pos(a, g, nx);
+    }
     for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
-        edge_setup(S, a, g, t0, e_end, a0, a1);
+        if (tid < TE) {
+            edge_setup_in(S, a, nx, a0, a1);
+            pair_idx(a, t0 + TE + tid, e_end, nx);       // in flight during this tile
+        }
         mw.ok = operands_ready(mw.ok);
         if (mw.ok) {
             if (tid == 0) {
@@ -898,6 +972,7 @@ __global__ void __launch_bounds__(kT) k_fm_tangent_tc(PotArgs a, const float* __
             mw.wait(&T.mbar);
         }
         tmem_rows<F>(tXY, S.X, S.Y);                     // a - b1 | T
+        if (tid < TE) pair_pos(a, g, nx);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -991,8 +1066,16 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
     const int fg = tid % FG, eg = tid / FG, f0 = 4 * fg, e0 = 4 * eg;
     int cur = -1;
     float run = 0.f;
+    PairIn nx;                                           // the next tile's pair inputs (threads < TE)
+    if (tid < TE) {
+        pair_idx(a, e_beg + tid, e_end, nx);
+        pair_pos(a, g, nx);
+    }
     for (long long t0 = e_beg; t0 < e_end; t0 += TE) {
-        edge_setup(S, a, g, t0, e_end, a0, &T.a1[0][0]);
+        if (tid < TE) {
+            edge_setup_in(S, a, nx, a0, &T.a1[0][0]);
+            pair_idx(a, t0 + TE + tid, e_end, nx);       // in flight during this tile
+        }
         if (pending) {                                   // the previous tile's D2 product reads A and B
             mw.wait(&T.mbar);
             pending = false;
@@ -1007,6 +1090,7 @@ __global__ void __launch_bounds__(kT, 1) k_fm_grad_edge_tc(PotArgs a, const floa
             mw.wait(&T.mbar);
         }
         tmem_rows<F>(tXY, S.X, S.Y);
+        if (tid < TE) pair_pos(a, g, nx);
         __syncthreads();
         float sp[4][4], spp[4][4], tt[4][4];
         {
