@@ -207,7 +207,8 @@ DMTS_API int dmts_forces(dmts_ctx* ctx, int which, double* f_out, double* energy
  * wrapped after every drift. energies_out: NULL or [n_outer][n_systems][3]
  * holding, after each outer step, the big model's potential energy, the
  * kinetic energy and their sum. On neighbour overflow the call restores the
- * state it started from, grows the capacity and runs again. */
+ * state it started from, grows the capacity and runs again. If the call
+ * fails, the contents of energies_out are unspecified. */
 DMTS_API int dmts_respa_step(dmts_ctx* ctx, int n_outer, double dt_outer_fs, int n_inner,
                     double* energies_out);
 

@@ -855,13 +855,15 @@ void enqueue_eval(dmts_ctx* c, int which, bool quantize, bool energy = true, Che
 }
 
 int sync_check(dmts_ctx* c) {
+    // the flags follow the stream's work into pinned host memory: one wait
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         c->broken = true;
         return fail(DMTS_ERR_CUDA, "CUDA error: %s", cudaGetErrorString(e));
     }
-    CUDA_TRY(cudaMemcpy(c->h_flags, c->d_flags, sizeof(int) * kFlagCount, cudaMemcpyDeviceToHost));
     if (c->h_flags[kFlagCheck]) {            // checked builds only
         c->broken = true;
         return fail(DMTS_ERR_CUDA, "index check failed (source line %d): an index outside its array",
@@ -1604,6 +1606,8 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             c->launches += c->g_nodes;
         }
+        // this attempt's energies travel with its flags (one wait)
+        if (energies_out && (rc = copy_out(c, energies_out, c->d_ring, (size_t)n_outer * c->n_sys * 3))) return rc;
         if ((rc = sync_check(c))) {
             if (rc == DMTS_ERR_TIMEOUT && !c->broken && restore() == DMTS_OK) {
                 c->forces_valid = false;
@@ -1626,8 +1630,6 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         if ((rc = grow_capacity(c))) return rc;
     }
     c->forces_valid = true;
-    if (energies_out && (rc = copy_out(c, energies_out, c->d_ring, (size_t)n_outer * c->n_sys * 3))) return rc;
-    if ((rc = sync_check(c))) return rc;
     if (c->h_flags[kFlagNonfinite]) return fail(DMTS_ERR_NONFINITE, "non-finite position or velocity");
     return DMTS_OK;
 }
