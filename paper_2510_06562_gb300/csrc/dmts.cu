@@ -215,7 +215,6 @@ struct dmts_ctx {
     int* d_flags = nullptr;
     int* h_flags = nullptr;      // pinned
     double *d_bx = nullptr, *d_bv = nullptr;
-    float *d_bfs = nullptr, *d_bfb = nullptr;
     Model m[2];
     double rc_max = 0;
     // Verlet-skin lists shared by the two models: the model with the larger
@@ -1222,7 +1221,7 @@ void dmts_destroy(dmts_ctx* c) {
     dfree(c->d_off); dfree(c->d_species); dfree(c->d_sys); dfree(c->d_box); dfree(c->d_mass);
     dfree(c->d_inv_m); dfree(c->d_x); dfree(c->d_v); dfree(c->d_q); dfree(c->d_frame); dfree(c->d_stage);
     dfree(c->d_ke); dfree(c->d_ekin); dfree(c->d_ring); dfree(c->d_flags); dfree(c->d_epart); dfree(c->d_eticket);
-    dfree(c->d_bx); dfree(c->d_bv); dfree(c->d_bfs); dfree(c->d_bfb);
+    dfree(c->d_bx); dfree(c->d_bv);
     dfree(c->d_xref); dfree(c->d_vl); dfree(c->d_rng); dfree(c->kesum.part); dfree(c->kesum.ctr);
     dfree(c->d_mon); dfree(c->d_sx); dfree(c->d_sv); dfree(c->d_sf);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -1352,8 +1351,6 @@ int dmts_create(const dmts_model_desc* small, const dmts_model_desc* big, const 
     CREATE_TRY(dalloc(&c->d_flags, kFlagCount));
     CREATE_TRY(dalloc(&c->d_bx, (size_t)3 * N));
     CREATE_TRY(dalloc(&c->d_bv, (size_t)3 * N));
-    CREATE_TRY(dalloc(&c->d_bfs, (size_t)3 * N));
-    CREATE_TRY(dalloc(&c->d_bfb, (size_t)3 * N));
     CREATE_TRY(cudaMallocHost((void**)&c->h_flags, sizeof(int) * kFlagCount));
     CREATE_TRY(dalloc(&c->kesum.part, (size_t)kSumMaxSplit * kSumChunks));
     CREATE_TRY(dalloc(&c->kesum.ctr, kSumMaxSplit));
@@ -1566,17 +1563,13 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         if (e != cudaSuccess) return fail(DMTS_ERR_OOM, "energies ring: %s", cudaGetErrorString(e));
         c->ring_len = n_outer;
     }
-    // state at entry, for the retry after a capacity overflow
-    const bool valid0 = c->forces_valid;
+    // state at entry, for the retry after a capacity overflow (the cached
+    // forces are not saved: the retry evaluates them again at the restored
+    // positions, which gives the same bits, as every evaluation is deterministic)
     CUDA_TRY(cudaMemcpyAsync(c->d_bx, c->d_x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_bv, c->d_v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_rng + 1, c->d_rng, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                              c->stream));
-    if (valid0) {
-        if (c->m[0].present)
-            CUDA_TRY(cudaMemcpyAsync(c->d_bfs, c->m[0].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(c->d_bfb, c->m[1].force, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-    }
     // back to the state of the call's entry (after an overflow, or a bounded
     // wait that gave up)
     auto restore = [&]() -> int {
@@ -1584,12 +1577,7 @@ int dmts_respa_step(dmts_ctx* c, int n_outer, double dt, int n_inner, double* en
         CUDA_TRY(cudaMemcpyAsync(c->d_v, c->d_bv, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_rng, c->d_rng + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                                  c->stream));
-        if (valid0) {
-            if (c->m[0].present)
-                CUDA_TRY(cudaMemcpyAsync(c->m[0].force, c->d_bfs, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-            CUDA_TRY(cudaMemcpyAsync(c->m[1].force, c->d_bfb, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-        }
-        c->forces_valid = valid0;
+        c->forces_valid = false;
         return DMTS_OK;
     };
     for (int attempt = 0;; ++attempt) {
