@@ -405,10 +405,10 @@ DMTS_API int dmts_philox4x32_10(int n, const unsigned int* ctr, const unsigned i
  * at most 256 neighbours per atom (else DMTS_ERR_ARG / DMTS_ERR_CAPACITY with
  * a message in dmts_last_error). DMTS_ERR_CAPACITY is also returned when the
  * pairs exceed capacity (row_ptr and *n_pairs are still written).
- * The call is synchronous (it waits for its stream and reads counts back to
- * the host), so it cannot be captured in a CUDA graph. The first call on a
- * device resolves the scratch array's device address (cudaGetSymbolAddress)
- * with that device current. The address is kept for the life of the
+ * The call is synchronous: it waits for its stream and reads counts back to
+ * the host. The first call on a device resolves the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current. The address is
+ * kept for the life of the
  * process, so do not reset a device (cudaDeviceReset) on which this entry
  * point has been called: the module would be loaded again, possibly at
  * another address. All calls share the one array, so calls whose
