@@ -408,12 +408,11 @@ DMTS_API int dmts_philox4x32_10(int n, const unsigned int* ctr, const unsigned i
  * The call is synchronous: it waits for its stream and reads counts back to
  * the host. The first call on a device resolves the scratch array's device
  * address (cudaGetSymbolAddress) with that device current. The address is
- * kept for the life of the
- * process, so do not reset a device (cudaDeviceReset) on which this entry
- * point has been called: the module would be loaded again, possibly at
- * another address. All calls share the one array, so calls whose
- * work overlaps on the GPU (other streams, other host threads) race: issue
- * them one at a time per device. */
+ * kept for the life of the process, so do not reset a device
+ * (cudaDeviceReset) on which this entry point has been called: the module
+ * would be loaded again, possibly at another address. All calls share the
+ * one array, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race: issue them one at a time per device. */
 #define DMTS_NOALLOC_MAX_ATOMS 16384
 
 DMTS_API int dmts_neighbors_noalloc(const double* x, int n_atoms, double box, double cutoff,
