@@ -487,7 +487,7 @@ struct FwdSmem {
 };
 
 template <int F, int KC>
-__global__ void __launch_bounds__(kT) k_edge_fwd_bf16(PotArgs a, int K, int* status) {
+__global__ void __launch_bounds__(kT, F == 32 ? 8 : 1) k_edge_fwd_bf16(PotArgs a, int K, int* status) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     FwdSmem<F>& S = *reinterpret_cast<FwdSmem<F>*>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5;
