@@ -332,9 +332,9 @@ int bf16_default_bwd_tiles(int F);
 
 // distill.cu: distillation (energy and force matching) gradient of a single-layer model
 bool fm_supported(int F, int K, int L);
-int fm_edge_ctas(int n_atoms);
-int fm_atom_ctas(int n_atoms);
-int fm_atom_rows(int n_atoms);
+int fm_edge_ctas(int n_atoms);    // CTAs (= partial rows) of the gradient edge pass on the current device
+int fm_atom_ctas(int n_atoms);    // blocks (= partial rows) of the per-atom adjoint pass
+int fm_atom_rows(int n_atoms);    // rows of the per-atom passes' partial buffer
 // Energy term of the distillation loss for one frame (e_ref null: none).
 struct FmEnergy {
     const double* e_ref = nullptr;   // device scalar: the frame's reference energy
